@@ -1,0 +1,412 @@
+"""FP64 CPU oracle for the FFT polyspectrum estimator (arXiv 1705.06284).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import or run anything in this
+package.  It shares no code with the CUDA library and never imports it; the
+only module both sides use is the input generator package ``fields``.
+
+Two independent routes to the same numbers:
+
+* :func:`direct_bispectrum` -- the definition, Eq. bi_direct over full
+  shells: an all-pairs sum over modes of Re[D(m1) D(m2) D(m3)] with
+  m3 = -(m1+m2) (mod N), plus brute-force triangle counts (plain C in
+  ``direct.c``).
+* :func:`fft_estimator` -- the paper's own estimator, Eqs. delta_nr,
+  Jeong_gen, Jeong_PS and Jeong_BI, written literally in NumPy FP64: mask the
+  spectrum to each shell, inverse-FFT (unnormalised) to the shell fields
+  I_b(x) and count fields N_b(x), and take real-space products.
+
+Substituting the DFT form of the Kronecker delta (Sec. 2, the identity that
+turns Eq. gen_Nspec3 into Eq. gen_Nspec4) shows the two are equal up to
+rounding; the pins in ``tests/test_oracle.py`` check that and more.
+
+Readings of the paper (each is listed with its reason in the design notes):
+
+* Normalisation: B = V^2/N_pix^3 * num/(N_pix N_tri) as in Eq. Jeong_BI
+  (Eq. bi_direct's 1/(2 pi)^3 is the continuum form; the discrete derivation
+  of Eqs. gen_Nspec1-2 gives H^p/V with H = V/N_pix).  P uses V/N_pix^2
+  (Eq. Jeong_PS) and the trispectrum V^3/N_pix^4 (Eq. Jeong_gen, p = 4).
+* Shells: the scalar |m| (spherically averaged spectra), membership
+  lo <= |m| k_f < hi, evaluated as thr[b] <= |m|^2 < thr[b+1] on integers.
+* Closure: modulo the grid (the FFT's Kronecker delta), components reduced
+  into [-N/2, N/2).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile ``direct.c`` into ``liboracle.so`` (gcc, OpenMP)."""
+    src = os.path.join(_HERE, "direct.c")
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(src):
+        tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c99",
+                               src, "-o", tmp])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            dp = ctypes.POINTER(ctypes.c_double)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_count_modes.restype = ctypes.c_int64
+            lib.oracle_count_modes.argtypes = [ctypes.c_int, ctypes.c_int, i64p]
+            lib.oracle_direct_bispectrum.restype = ctypes.c_int64
+            lib.oracle_direct_bispectrum.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
+                                                     dp, dp, i64p, ctypes.c_int64, ctypes.c_int64]
+            lib.oracle_direct_triplets.restype = None
+            lib.oracle_direct_triplets.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
+                                                   ctypes.c_int, i32p, dp, dp, i64p]
+            lib.oracle_direct_trispectrum.restype = None
+            lib.oracle_direct_trispectrum.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
+                                                      dp, dp, i64p]
+            _lib = lib
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def num_threads() -> int:
+    """OpenMP threads the C oracle runs with."""
+    return int(_load().oracle_num_threads())
+
+
+# --------------------------------------------------------------------------
+# Units, bins and the spectrum (Eqs. FFTconventions, DeltaFFTtoDelta).
+# --------------------------------------------------------------------------
+
+def k_fundamental(L: float) -> float:
+    """k_f = 2 pi / L (Sec. 2)."""
+    return 2.0 * math.pi / L
+
+
+def thresholds(edges, L: float) -> np.ndarray:
+    """Integer thresholds on |m|^2 for physical bin edges.
+
+    Bin b holds the modes with edges[b] <= |m| k_f < edges[b+1].  With
+    s = (edge/k_f)^2 (FP64), the smallest integer |m|^2 meeting |m| k_f >=
+    edge is ceil(s).  Edges that are whole multiples of k_f give an s a few
+    ulps away from an integer; s is snapped to that integer first when
+    |s - round(s)| <= 1e-9 max(1, s), so that such edges fall exactly where
+    they were meant to.
+    """
+    kf = k_fundamental(L)
+    e = np.asarray(edges, dtype=np.float64)
+    out = np.empty(e.shape, dtype=np.int64)
+    for i, v in enumerate(e):
+        if v <= 0.0:
+            out[i] = 0
+            continue
+        s = (v / kf) * (v / kf)
+        r = round(s)
+        if abs(s - r) <= 1e-9 * max(1.0, s):
+            s = float(r)
+        out[i] = int(math.ceil(s))
+    if np.any(np.diff(out) < 0):
+        raise ValueError("edges must be ascending")
+    return out
+
+
+def spectrum(field: np.ndarray) -> np.ndarray:
+    """Unnormalised forward DFT, D(m) = sum_n delta(n) e^{-2 pi i m.n/N}
+    (Eq. DeltaFFTtoDelta), full complex box in FFT index order."""
+    return np.fft.fftn(np.asarray(field, dtype=np.float64))
+
+
+def mode_squares(N: int) -> np.ndarray:
+    """|m|^2 on the full grid, components wrapped into [-N/2, N/2)."""
+    f = np.fft.fftfreq(N, d=1.0 / N).astype(np.int64)
+    return f[:, None, None] ** 2 + f[None, :, None] ** 2 + f[None, None, :] ** 2
+
+
+def bin_index(N: int, thr) -> np.ndarray:
+    """Bin of every grid mode (-1 when in no bin)."""
+    thr = np.asarray(thr, dtype=np.int64)
+    m2 = mode_squares(N)
+    b = np.searchsorted(thr, m2, side="right") - 1
+    b[(m2 < thr[0]) | (m2 >= thr[-1])] = -1
+    return b
+
+
+def shell_sizes(N: int, thr) -> np.ndarray:
+    """|S_b|: number of modes in each bin."""
+    b = bin_index(N, thr)
+    nb = len(thr) - 1
+    return np.bincount(b[b >= 0].ravel(), minlength=nb).astype(np.int64)
+
+
+# --------------------------------------------------------------------------
+# Route 1: the direct-measurement definition (Eq. bi_direct, full shells).
+# --------------------------------------------------------------------------
+
+def direct_sums(field, thr, m1_start: int = 0, m1_stride: int = 1):
+    """Ordered all-pairs sums (num, num_im, cnt) of shape (nb, nb, nb).
+
+    Returns also the number of m1 modes processed (all of them unless a
+    sample is asked for with ``m1_stride > 1``).
+    """
+    lib = _load()
+    D = spectrum(field)
+    N = D.shape[0]
+    re = np.ascontiguousarray(D.real)
+    im = np.ascontiguousarray(D.imag)
+    thr = np.ascontiguousarray(thr, dtype=np.int64)
+    nb = len(thr) - 1
+    num = np.zeros(nb ** 3)
+    numi = np.zeros(nb ** 3)
+    cnt = np.zeros(nb ** 3, dtype=np.int64)
+    done = lib.oracle_direct_bispectrum(N, _p(re, ctypes.c_double), _p(im, ctypes.c_double), nb,
+                                        _p(thr, ctypes.c_int64), _p(num, ctypes.c_double),
+                                        _p(numi, ctypes.c_double), _p(cnt, ctypes.c_int64),
+                                        int(m1_start), int(m1_stride))
+    sh = (nb, nb, nb)
+    return num.reshape(sh), numi.reshape(sh), cnt.reshape(sh), int(done)
+
+
+def count_modes(N: int, thr) -> int:
+    thr = np.ascontiguousarray(thr, dtype=np.int64)
+    return int(_load().oracle_count_modes(N, len(thr) - 1, _p(thr, ctypes.c_int64)))
+
+
+def direct_bispectrum(field, L: float, edges):
+    """Bispectrum by direct measurement over full shells (Eq. bi_direct).
+
+    Returns a dict with
+      ``triplets`` (ntrip, 3) int32, lexicographic a <= b <= c with N_tri > 0;
+      ``N_tri``   (ntrip,) int64 ordered-triple counts;
+      ``B``       (ntrip,) FP64, V^2/N_pix^3 * num/N_tri;
+      ``num``     (ntrip,) FP64 ordered sums of Re[D1 D2 D3];
+      ``num_im``  (ntrip,) FP64 ordered sums of Im[D1 D2 D3] (zero in exact
+                  arithmetic);
+      ``P``       (nbins,) FP64 power spectrum (shell mode average);
+      ``shell``   (nbins,) int64 |S_b|.
+    """
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    thr = thresholds(edges, L)
+    num, numi, cnt, _ = direct_sums(field, thr)
+    nb = len(thr) - 1
+    trip, n, ni, c = [], [], [], []
+    for a in range(nb):
+        for b in range(a, nb):
+            for cc in range(b, nb):
+                if cnt[a, b, cc] > 0:
+                    trip.append((a, b, cc))
+                    n.append(num[a, b, cc])
+                    ni.append(numi[a, b, cc])
+                    c.append(cnt[a, b, cc])
+    V = float(L) ** 3
+    npix = float(N) ** 3
+    trip = np.array(trip, dtype=np.int32).reshape(-1, 3)
+    n = np.array(n)
+    c = np.array(c, dtype=np.int64)
+    B = (V * V / npix ** 3) * n / np.maximum(c, 1)
+    P, S = power_spectrum(field, L, edges)
+    return {"triplets": trip, "N_tri": c, "B": B, "num": n, "num_im": np.array(ni),
+            "P": P, "shell": S, "ordered_num": num, "ordered_cnt": cnt}
+
+
+def direct_triplets(field, L: float, edges, triplets):
+    """Direct sums for selected (a, b, c) only: cost sum |S_a||S_b|.
+
+    Returns (B, num, num_im, N_tri) for the requested triplets (ordered
+    triples with m1 in S_a, m2 in S_b, m3 in S_c).
+    """
+    lib = _load()
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    D = spectrum(field)
+    re = np.ascontiguousarray(D.real)
+    im = np.ascontiguousarray(D.imag)
+    thr = np.ascontiguousarray(thresholds(edges, L))
+    abc = np.ascontiguousarray(np.asarray(triplets, dtype=np.int32).reshape(-1, 3))
+    nt = abc.shape[0]
+    num = np.zeros(nt)
+    numi = np.zeros(nt)
+    cnt = np.zeros(nt, dtype=np.int64)
+    lib.oracle_direct_triplets(N, _p(re, ctypes.c_double), _p(im, ctypes.c_double), len(thr) - 1,
+                               _p(thr, ctypes.c_int64), nt, _p(abc, ctypes.c_int32),
+                               _p(num, ctypes.c_double), _p(numi, ctypes.c_double),
+                               _p(cnt, ctypes.c_int64))
+    V = float(L) ** 3
+    npix = float(N) ** 3
+    B = (V * V / npix ** 3) * num / np.maximum(cnt, 1)
+    return B, num, numi, cnt
+
+
+def direct_trispectrum(field, L: float, edges):
+    """Trispectrum by direct measurement (p = 4 case of Eq. gen_Nspec3) over
+    ordered quadruples; O(|M|^3), tiny grids only.
+
+    Returns dict with ``quads`` (nq, 4) a<=b<=c<=d with N_quad > 0,
+    ``N_quad``, ``T`` = V^3/N_pix^4 * num/N_quad, ``num``, ``num_im``.
+    """
+    lib = _load()
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    D = spectrum(field)
+    re = np.ascontiguousarray(D.real)
+    im = np.ascontiguousarray(D.imag)
+    thr = np.ascontiguousarray(thresholds(edges, L))
+    nb = len(thr) - 1
+    num = np.zeros(nb ** 4)
+    numi = np.zeros(nb ** 4)
+    cnt = np.zeros(nb ** 4, dtype=np.int64)
+    lib.oracle_direct_trispectrum(N, _p(re, ctypes.c_double), _p(im, ctypes.c_double), nb,
+                                  _p(thr, ctypes.c_int64), _p(num, ctypes.c_double),
+                                  _p(numi, ctypes.c_double), _p(cnt, ctypes.c_int64))
+    sh = (nb,) * 4
+    num, numi, cnt = num.reshape(sh), numi.reshape(sh), cnt.reshape(sh)
+    quads, n, ni, c = [], [], [], []
+    for a in range(nb):
+        for b in range(a, nb):
+            for cc in range(b, nb):
+                for d in range(cc, nb):
+                    if cnt[a, b, cc, d] > 0:
+                        quads.append((a, b, cc, d))
+                        n.append(num[a, b, cc, d])
+                        ni.append(numi[a, b, cc, d])
+                        c.append(cnt[a, b, cc, d])
+    V = float(L) ** 3
+    npix = float(N) ** 3
+    n = np.array(n)
+    c = np.array(c, dtype=np.int64)
+    T = (V ** 3 / npix ** 4) * n / np.maximum(c, 1)
+    return {"quads": np.array(quads, dtype=np.int32).reshape(-1, 4), "N_quad": c, "T": T,
+            "num": n, "num_im": np.array(ni), "ordered_num": num, "ordered_cnt": cnt}
+
+
+def power_spectrum(field, L: float, edges):
+    """Power spectrum by direct measurement: P_b = V/N_pix^2 * <|D(m)|^2>
+    over the modes of shell b (the textbook estimator the paper compares
+    against in Sec. 3.3).  Empty shells give NaN.  Returns (P, |S_b|)."""
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    thr = thresholds(edges, L)
+    D = spectrum(field)
+    b = bin_index(N, thr)
+    nb = len(thr) - 1
+    p2 = (D.real ** 2 + D.imag ** 2)
+    sel = b >= 0
+    s = np.bincount(b[sel].ravel(), weights=p2[sel].ravel(), minlength=nb)
+    S = np.bincount(b[sel].ravel(), minlength=nb).astype(np.int64)
+    V = float(L) ** 3
+    npix = float(N) ** 3
+    with np.errstate(invalid="ignore", divide="ignore"):
+        P = (V / npix ** 2) * s / S
+    P[S == 0] = np.nan
+    return P, S
+
+
+# --------------------------------------------------------------------------
+# Route 2: the paper's FFT estimator in FP64 (Eqs. delta_nr .. Jeong_BI).
+# --------------------------------------------------------------------------
+
+def shell_field(D: np.ndarray, bins: np.ndarray, b: int) -> np.ndarray:
+    """I_b(n) = sum_{m in S_b} D(m) e^{+2 pi i m.n/N} (Eq. delta_nr, first
+    line): mask the spectrum to the shell and apply the unnormalised inverse
+    DFT (NumPy's ifftn divides by N_pix, so multiply back)."""
+    npix = D.size
+    return (np.fft.ifftn(np.where(bins == b, D, 0.0)) * npix).real
+
+
+def count_field(bins: np.ndarray, b: int) -> np.ndarray:
+    """N_b(n) = sum_{m in S_b} e^{+2 pi i m.n/N} (Eq. delta_nr, second
+    line): the unnormalised inverse DFT of the shell indicator."""
+    npix = bins.size
+    return (np.fft.ifftn((bins == b).astype(np.complex128)) * npix).real
+
+
+def fft_estimator(field, L: float, edges, triplets=None, quads=None, bins_needed=None):
+    """The paper's FFT polyspectrum estimator, FP64 NumPy, literal.
+
+    Builds I_b and N_b for the bins in use, then
+      P_b  = V/N_pix^2   sum_x I_b^2      / sum_x N_b^2          (Eq. Jeong_PS)
+      B    = V^2/N_pix^3 sum_x I_a I_b I_c / sum_x N_a N_b N_c   (Eq. Jeong_BI)
+      T    = V^3/N_pix^4 sum_x I_a I_b I_c I_d / sum_x N_a..N_d  (Eq. Jeong_gen)
+    ``triplets`` / ``quads`` default to every a<=b<=c (a<=b<=c<=d) of
+    non-empty bins.  Returns a dict with the sums, the counts rounded from
+    sum N..N / N_pix, the estimates, and ``M`` (the cancellation-free scale
+    of each triplet, V^2/N_pix^3 sum_x |I_a I_b I_c| / sum_x N_a N_b N_c).
+    """
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    npix = float(N) ** 3
+    V = float(L) ** 3
+    thr = thresholds(edges, L)
+    nb = len(thr) - 1
+    D = spectrum(field)
+    bins = bin_index(N, thr)
+    S = np.bincount(bins[bins >= 0].ravel(), minlength=nb)
+    use = set()
+    if triplets is None:
+        triplets = [(a, b, c) for a in range(nb) for b in range(a, nb) for c in range(b, nb)
+                    if S[a] and S[b] and S[c]]
+    for t in triplets:
+        use.update(int(v) for v in t)
+    if quads is not None:
+        for q in quads:
+            use.update(int(v) for v in q)
+    if bins_needed is not None:
+        use.update(int(v) for v in bins_needed)
+    I, C = {}, {}
+    for b in sorted(use):
+        I[b] = shell_field(D, bins, b)
+        C[b] = count_field(bins, b)
+    out = {"bins": sorted(use)}
+    P = np.full(nb, np.nan)
+    for b in sorted(use):
+        if S[b]:
+            P[b] = (V / npix ** 2) * float(np.sum(I[b] * I[b])) / float(np.sum(C[b] * C[b]))
+    out["P"] = P
+    trip = np.asarray(triplets, dtype=np.int32).reshape(-1, 3)
+    num = np.zeros(len(trip))
+    den = np.zeros(len(trip))
+    mag = np.zeros(len(trip))
+    for i, (a, b, c) in enumerate(trip):
+        prod = I[a] * I[b] * I[c]
+        num[i] = float(np.sum(prod))
+        mag[i] = float(np.sum(np.abs(prod)))
+        den[i] = float(np.sum(C[a] * C[b] * C[c]))
+    out["triplets"] = trip
+    out["num"] = num
+    out["den"] = den
+    out["N_tri"] = np.rint(den / npix).astype(np.int64)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        out["B"] = (V * V / npix ** 3) * num / den
+        out["M"] = (V * V / npix ** 3) * mag / den
+    if quads is not None:
+        qd = np.asarray(quads, dtype=np.int32).reshape(-1, 4)
+        qn = np.zeros(len(qd))
+        qden = np.zeros(len(qd))
+        for i, (a, b, c, d) in enumerate(qd):
+            qn[i] = float(np.sum(I[a] * I[b] * I[c] * I[d]))
+            qden[i] = float(np.sum(C[a] * C[b] * C[c] * C[d]))
+        out["quads"] = qd
+        out["qnum"] = qn
+        out["qden"] = qden
+        out["N_quad"] = np.rint(qden / npix).astype(np.int64)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            out["T"] = (V ** 3 / npix ** 4) * qn / qden
+    return out

@@ -1,0 +1,382 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests touch the CUDA library.  Each pin is chosen so that a
+plausible slip in the oracle (a dropped term, a wrong sign or index, a
+transposed operand, a wrong normalisation power) fails at least one:
+
+* DFT convention  -- naive O(N^6) sum (Eq. DeltaFFTtoDelta).
+* Closure/binning -- pure-Python brute force over mode triples; hand-derived
+                     lattice counts on an 8^3 grid.
+* Estimator       -- direct sum == FFT estimator (the Kronecker-delta identity
+                     of Sec. 2 turning Eq. gen_Nspec3 into Eq. gen_Nspec4).
+* Normalisation   -- skewness sum rule (Eq. skew) pins V^2/N_pix^3; the
+                     variance sum rule pins V/N_pix^2 for P; the kurtosis sum
+                     rule pins V^3/N_pix^4 for T.
+* Count sum rule  -- full-cover shells give sum N_tri = N_pix^2.
+* Symmetry        -- ordered sums are invariant under bin permutations.
+* Closed forms    -- three/four plane waves with a closed triangle.
+* Statistics      -- Gaussian null; quadratic-local tree level 2f[P1P2+cyc].
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import fields
+import oracle
+
+
+def _full_cover_edges(N, L):
+    """Edges from 0 to beyond the corner of the grid: every mode in a bin."""
+    kf = 2 * math.pi / L
+    top = 3 * (N // 2) ** 2 + 1
+    sq = [0.0, 2.5, 6.5, 12.5, 24.5, float(top) + 0.5]
+    return [kf * math.sqrt(s) for s in sq]
+
+
+# ---------------------------------------------------------------- DFT pin
+@pytest.mark.parametrize("N", [4, 6, 8])
+def test_spectrum_matches_naive_dft(N):
+    rng = np.random.default_rng(N)
+    f = rng.standard_normal((N, N, N))
+    D = oracle.spectrum(f)
+    n = np.arange(N)
+    ph = np.exp(-2j * np.pi * np.outer(n, n) / N)  # [m, n]
+    naive = np.zeros((N, N, N), dtype=complex)
+    for mx in range(N):
+        for my in range(N):
+            for mz in range(N):
+                naive[mx, my, mz] = np.sum(f * ph[mx][:, None, None] * ph[my][None, :, None]
+                                           * ph[mz][None, None, :])
+    assert np.max(np.abs(D - naive)) <= 1e-12 * np.max(np.abs(naive))
+
+
+# ---------------------------------------------------------------- thresholds
+def test_thresholds_rule():
+    L = 2 * math.pi  # k_f = 1
+    # whole multiples of k_f land exactly; in-between values round up
+    thr = oracle.thresholds([1.0, 2.0, 2.5, 3.0 + 1e-13, 8.0], L)
+    assert list(thr) == [1, 4, 7, 9, 64]
+    L2 = 100.0
+    kf = 2 * math.pi / L2
+    e = np.linspace(kf, 8 * kf, 7)
+    thr2 = oracle.thresholds(e, L2)
+    # 1, (13/6)^2=4.69, (10/3)^2=11.1, 4.5^2=20.25, (17/3)^2=32.1, (41/6)^2=46.7, 64
+    assert list(thr2) == [1, 5, 12, 21, 33, 47, 64]
+
+
+# ---------------------------------------------------------------- brute force
+def _brute_counts(N, thr, D):
+    """Pure-Python enumeration of ordered closed triples over binned modes."""
+    nb = len(thr) - 1
+    f = np.fft.fftfreq(N, d=1.0 / N).astype(int)
+    modes = []
+    for ix in range(N):
+        for iy in range(N):
+            for iz in range(N):
+                m2 = f[ix] ** 2 + f[iy] ** 2 + f[iz] ** 2
+                for b in range(nb):
+                    if thr[b] <= m2 < thr[b + 1]:
+                        modes.append((ix, iy, iz, b))
+    cnt = np.zeros((nb,) * 3, dtype=np.int64)
+    num = np.zeros((nb,) * 3)
+    arr = np.array(modes)
+    key = {(m[0], m[1], m[2]): m[3] for m in modes}
+    for (ax, ay, az, ab) in modes:
+        for (bx, by, bz, bb) in modes:
+            c = ((-ax - bx) % N, (-ay - by) % N, (-az - bz) % N)
+            if c in key:
+                cnt[ab, bb, key[c]] += 1
+                num[ab, bb, key[c]] += (D[ax, ay, az] * D[bx, by, bz] * D[c]).real
+    return cnt, num, len(arr)
+
+
+def test_direct_sum_matches_brute_force():
+    N, L = 8, 2 * math.pi
+    f = fields.lognormal(N, 0.6, -1.0, seed=3)
+    edges = [1.0, 1.5, 2.2, 2.9]
+    thr = oracle.thresholds(edges, L)
+    num, numi, cnt, done = oracle.direct_sums(f, thr)
+    bc, bn, nm = _brute_counts(N, thr, oracle.spectrum(f))
+    assert done == nm
+    assert np.array_equal(cnt, bc)
+    assert np.allclose(num, bn, rtol=1e-12, atol=1e-9 * np.max(np.abs(bn)))
+
+
+# Hand-derived ordered triangle counts on an 8^3 grid with k_f = 1 and the
+# single-|m|^2 shells A = {|m|^2=1} (6 modes), B = {2} (12), C = {3} (8),
+# D = {4} (6).  With m3 = -(m1+m2): |m3|^2 = |m1|^2 + |m2|^2 + 2 m1.m2, so
+# each count is (#m1) x (#m2 with the required dot product).
+#   AAA: 1+1+2d=1 -> d=-1/2 impossible                       -> 0
+#   AAB: d=0, m2 one of 4 axes orthogonal to m1              -> 6*4  = 24
+#   AAD: d=1, m2 = m1                                         -> 6*1  = 6
+#   ABC: d=0, m2 of type (0,+-1,+-1) orthogonal to m1        -> 6*4  = 24
+#   BBB: 2+2+2d=2 -> d=-1, e.g. (1,1,0): (-1,0,+-1),(0,-1,+-1)-> 12*4 = 48
+#   BBD: d=0, (1,1,0) -> (1,-1,0),(-1,1,0)                    -> 12*2 = 24
+#   CCD: 3+3+2d=4 -> d=-1, two minus signs of three          -> 8*3  = 24
+#   ACD: d=0 impossible (m2 has no zero component)            -> 0
+#   BCC: 2+3+2d=3 -> d=-1 impossible for s1+s2 in {-2,0,2}   -> 0
+#   DDD: 4+4+2d=4 -> d=-2 impossible (d in {0,+-4})           -> 0
+HAND_COUNTS = {(0, 0, 0): 0, (0, 0, 1): 24, (0, 0, 3): 6, (0, 1, 2): 24, (1, 1, 1): 48,
+               (1, 1, 3): 24, (2, 2, 3): 24, (0, 2, 3): 0, (1, 2, 2): 0, (3, 3, 3): 0}
+
+
+def test_hand_derived_lattice_counts():
+    N, L = 8, 2 * math.pi
+    edges = [1.0, 1.2, 1.5, 1.8, 2.1]  # -> |m|^2 in {1},{2},{3},{4}
+    thr = oracle.thresholds(edges, L)
+    assert list(thr) == [1, 2, 3, 4, 5]
+    assert list(oracle.shell_sizes(N, thr)) == [6, 12, 8, 6]
+    f = fields.lognormal(N, 0.5, -2.0, seed=0)
+    _, _, cnt, _ = oracle.direct_sums(f, thr)
+    for (a, b, c), v in HAND_COUNTS.items():
+        for p in set(itertools.permutations((a, b, c))):
+            assert cnt[p] == v, (p, cnt[p], v)
+    fe = oracle.fft_estimator(f, L, edges, triplets=list(HAND_COUNTS))
+    assert [int(x) for x in fe["N_tri"]] == list(HAND_COUNTS.values())
+
+
+# ---------------------------------------------------------------- identity
+@pytest.mark.parametrize("N,nb,seed,kind", [(8, 3, 1, "lin"), (12, 4, 2, "lin"), (16, 5, 3, "log"),
+                                            (12, 3, 4, "full")])
+def test_direct_equals_fft_estimator(N, nb, seed, kind):
+    L = 50.0
+    f = fields.lognormal(N, 0.8, -1.5, seed=seed)
+    if kind == "lin":
+        edges = fields.linear_edges(N, L, nb)
+    elif kind == "log":
+        edges = fields.log_edges(N, L, nb)
+    else:
+        edges = _full_cover_edges(N, L)
+    d = oracle.direct_bispectrum(f, L, edges)
+    assert len(d["triplets"]) > 0
+    g = oracle.fft_estimator(f, L, edges, triplets=d["triplets"])
+    assert np.array_equal(d["N_tri"], g["N_tri"])
+    scale = np.max(np.abs(d["num"]))
+    assert np.max(np.abs(d["num"] - g["num"] / N ** 3)) <= 1e-12 * scale
+    ok = np.isfinite(d["P"])
+    assert np.allclose(d["P"][ok], g["P"][ok], rtol=1e-12)
+
+
+def test_imaginary_part_cancels():
+    N, L = 16, 80.0
+    f = fields.bubbles(N, 2.5, 0.4, seed=5)
+    d = oracle.direct_bispectrum(f, L, fields.linear_edges(N, L, 4))
+    assert np.max(np.abs(d["num_im"])) <= 1e-12 * np.max(np.abs(d["num"]))
+
+
+def test_permutation_symmetry():
+    N, L = 12, 30.0
+    f = fields.lognormal(N, 0.7, -2.0, seed=9)
+    thr = oracle.thresholds(fields.linear_edges(N, L, 4), L)
+    num, _, cnt, _ = oracle.direct_sums(f, thr)
+    for p in itertools.permutations(range(3)):
+        assert np.array_equal(cnt, np.transpose(cnt, p))
+        assert np.allclose(num, np.transpose(num, p), rtol=1e-12, atol=1e-12 * np.max(np.abs(num)))
+
+
+# ---------------------------------------------------------------- sum rules
+def test_count_sum_rule_full_cover():
+    N, L = 8, 10.0
+    thr = oracle.thresholds(_full_cover_edges(N, L), L)
+    f = fields.lognormal(N, 0.5, -2.0, seed=0)
+    _, _, cnt, _ = oracle.direct_sums(f, thr)
+    assert int(cnt.sum()) == (N ** 3) ** 2
+
+
+def test_skewness_sum_rule_pins_bispectrum_normalisation():
+    # Eq. skew: gamma = <delta^3> = int d3k1/(2pi)^3 int d3k2/(2pi)^3 B.  On the
+    # lattice int d3k/(2pi)^3 -> (1/V) sum_m, so mean(delta^3) =
+    # (1/V^2) sum over ordered (a,b,c) of N_tri(abc) * B(abc).
+    N, L = 8, 37.0
+    f = fields.lognormal(N, 0.9, -1.0, seed=4)
+    d = oracle.direct_bispectrum(f, L, _full_cover_edges(N, L))
+    num, cnt = d["ordered_num"], d["ordered_cnt"]
+    V, npix = L ** 3, float(N ** 3)
+    Bord = np.where(cnt > 0, (V * V / npix ** 3) * num / np.maximum(cnt, 1), 0.0)
+    lhs = float(np.sum(cnt * Bord)) / V ** 2
+    assert abs(lhs - float(np.mean(f ** 3))) <= 1e-11 * float(np.mean(np.abs(f) ** 3))
+
+
+def test_variance_sum_rule_pins_power_normalisation():
+    # sigma^2 = int d3k/(2pi)^3 P(k)  ->  mean(delta^2) = (1/V) sum_b |S_b| P_b
+    # for shells covering every mode (the mean of delta enters through m = 0).
+    N, L = 10, 21.0
+    f = fields.lognormal(N, 0.7, -1.5, seed=8)
+    edges = _full_cover_edges(N, L)
+    P, S = oracle.power_spectrum(f, L, edges)
+    ok = S > 0
+    lhs = float(np.sum(S[ok] * P[ok])) / L ** 3
+    assert abs(lhs - float(np.mean(f ** 2))) <= 1e-12 * float(np.mean(f ** 2))
+    g = oracle.fft_estimator(f, L, edges, triplets=[], bins_needed=np.nonzero(ok)[0])
+    assert np.allclose(g["P"][ok], P[ok], rtol=1e-12)
+
+
+def test_kurtosis_sum_rule_pins_trispectrum_normalisation():
+    # <delta^4> = (1/V^3) sum over ordered (a,b,c,d) N_quad T   (raw p = 4 estimator)
+    N, L = 6, 13.0
+    f = fields.lognormal(N, 0.8, -1.0, seed=6)
+    kf = 2 * math.pi / L
+    edges = [0.0, kf * 1.2, kf * 1.8, kf * 5.5]  # covers |m|^2 <= 27
+    t = oracle.direct_trispectrum(f, L, edges)
+    num, cnt = t["ordered_num"], t["ordered_cnt"]
+    assert int(cnt.sum()) == (N ** 3) ** 3
+    V, npix = L ** 3, float(N ** 3)
+    T = np.where(cnt > 0, (V ** 3 / npix ** 4) * num / np.maximum(cnt, 1), 0.0)
+    lhs = float(np.sum(cnt * T)) / V ** 3
+    assert abs(lhs - float(np.mean(f ** 4))) <= 1e-11 * float(np.mean(f ** 4))
+
+
+# ---------------------------------------------------------------- closed forms
+def test_three_plane_waves_closed_form():
+    # delta = sum_j A_j cos(2 pi m_j.n/N + phi_j), m1+m2+m3 = 0, |m_j| in
+    # distinct single-|m|^2 shells.  D(+-m_j) = (N^3 A_j/2) e^{+-i phi_j}, so
+    # the only closed ordered triples in the sorted bin triple (a,b,c) are
+    # (m1,m2,m3) and (-m1,-m2,-m3):  num = 2 (N^3/2)^3 A1A2A3 cos(phi1+phi2+phi3).
+    N, L = 16, 2 * math.pi
+    m1, m2 = (1, 0, 0), (0, 2, 0)
+    m3 = (-1, -2, 0)
+    A = (0.7, -0.4, 1.3)
+    phi = (0.3, -1.1, 2.0)
+    f = fields.plane_waves(N, [(m1, A[0], phi[0]), (m2, A[1], phi[1]), (m3, A[2], phi[2])])
+    edges = [0.9, 1.1, 1.9, 2.1, 2.2, 2.3]  # |m|^2: {1}, {2,3}, {4}, {}, {5}
+    thr = oracle.thresholds(edges, L)
+    assert list(thr) == [1, 2, 4, 5, 5, 6]
+    d = oracle.direct_bispectrum(f, L, edges)
+    # the triangle sits in bins (0, 2, 4); its count is the full lattice count
+    idx = [i for i, t in enumerate(d["triplets"]) if tuple(t) == (0, 2, 4)]
+    assert len(idx) == 1
+    i = idx[0]
+    npix = N ** 3
+    expect = 2 * (npix / 2) ** 3 * A[0] * A[1] * A[2] * math.cos(sum(phi))
+    assert abs(d["num"][i] - expect) <= 1e-10 * abs(expect)
+    V = L ** 3
+    assert abs(d["B"][i] - V * V / npix ** 3 * expect / d["N_tri"][i]) <= 1e-12 * abs(d["B"][i])
+    # every other triplet sees no closed wave triangle
+    others = np.delete(d["num"], i)
+    assert np.all(np.abs(others) <= 1e-9 * abs(expect))
+
+
+def test_four_plane_waves_closed_form_trispectrum():
+    N, L = 8, 2 * math.pi
+    ms = [(1, 0, 0), (0, 1, 0), (0, 0, 2), (-1, -1, -2)]
+    A = (0.5, 0.8, -0.6, 0.9)
+    phi = (0.2, 0.9, -0.4, 1.7)
+    f = fields.plane_waves(N, list(zip(ms, A, phi)))
+    edges = [0.9, 1.1, 1.9, 2.1, 2.4, 2.5]  # {1}, {2,3}, {4}, {5}, {6}
+    thr = oracle.thresholds(edges, L)
+    assert list(thr) == [1, 2, 4, 5, 6, 7]
+    t = oracle.direct_trispectrum(f, L, edges)
+    # (m1,m2,m3,m4) lies in bins (0,0,2,4): |m4|^2 = 6.  Ordered quadruples of
+    # the wave set closing in that sorted bin order: m1<->m2 swap and the global
+    # sign flip -> 4 terms, each (N^3/2)^4 A1A2A3A4 cos(sum phi).  Quadruples
+    # like (m1, -m1, m2, -m2) are in other bin patterns.
+    i = [k for k, q in enumerate(t["quads"]) if tuple(q) == (0, 0, 2, 4)][0]
+    npix = N ** 3
+    expect = 4 * (npix / 2) ** 4 * np.prod(A) * math.cos(sum(phi))
+    assert abs(t["num"][i] - expect) <= 1e-10 * abs(expect)
+    # the FFT estimator (Eq. Jeong_gen with p = 4) reaches the same number
+    g = oracle.fft_estimator(f, L, edges, triplets=[], quads=[(0, 0, 2, 4)])
+    assert abs(g["qnum"][0] / npix - expect) <= 1e-10 * abs(expect)
+    assert g["N_quad"][0] == t["N_quad"][i]
+
+
+def test_trispectrum_direct_equals_fft_estimator():
+    N, L = 8, 40.0
+    f = fields.lognormal(N, 0.8, -1.5, seed=12)
+    edges = fields.linear_edges(N, L, 3)
+    t = oracle.direct_trispectrum(f, L, edges)
+    g = oracle.fft_estimator(f, L, edges, triplets=[], quads=t["quads"])
+    assert np.array_equal(g["N_quad"], t["N_quad"])
+    assert np.allclose(g["qnum"] / N ** 3, t["num"], rtol=1e-10,
+                       atol=1e-12 * np.max(np.abs(t["num"])))
+
+
+# ---------------------------------------------------------------- statistics
+def test_gaussian_null():
+    # For a Gaussian field the bispectrum has zero mean and, to leading order,
+    # Var(B) = s V P_a P_b P_c / N_tri (s = 1, 2, 6 for scalene, isosceles,
+    # equilateral).  Pool z-scores over triplets and realisations.
+    N, L, slope = 24, 100.0, -1.0
+    edges = fields.linear_edges(N, L, 5)
+    zs = []
+    for seed in range(3):
+        g = fields.gaussian(N, slope, 1.0, seed=100 + seed)
+        d = oracle.direct_bispectrum(g, L, edges)
+        P = d["P"]
+        for (a, b, c), B, n in zip(d["triplets"], d["B"], d["N_tri"]):
+            if n < 200:
+                continue
+            s = 6 if a == b == c else (2 if (a == b or b == c) else 1)
+            var = s * L ** 3 * P[a] * P[b] * P[c] / n
+            zs.append(B / math.sqrt(var))
+    zs = np.array(zs)
+    assert len(zs) > 20
+    assert abs(zs.mean()) < 4.0 / math.sqrt(len(zs))
+    assert 0.5 < zs.std() < 2.0
+
+
+def test_quadratic_local_tree_level():
+    # delta = g + f (g^2 - <g^2>) has, at tree level, B = 2f[P1P2 + P2P3 + P3P1]
+    # with P the spectrum of g.  Average the theory over the exact closed
+    # triangles of each bin triple (as the paper does for its theory points),
+    # fit B_measured = r B_tree with Gaussian weights, and require r ~ 1.
+    N, L, slope, sg, fnl = 32, 200.0, -1.5, 0.1, 1.0
+    edges = fields.linear_edges(N, L, 5)
+    thr = oracle.thresholds(edges, L)
+    nb = len(thr) - 1
+    V, npix = L ** 3, float(N ** 3)
+    bins = oracle.bin_index(N, thr)
+    m = np.sqrt(oracle.mode_squares(N).astype(float))
+    num_r, den_r = 0.0, 0.0
+    for seed in range(3):
+        A = fields.gaussian_spectrum_amplitude(N, slope, sg, seed=200 + seed)
+        Pm = np.where(m > 0, (V / npix ** 2) * A * np.where(m > 0, m, 1.0) ** slope, 0.0)
+        # W_b(x) = unnormalised inverse DFT of P(m) on shell b; Sigma over
+        # closed triples of P(m1)P(m2) = (1/N_pix) sum_x W_a W_b N_c.
+        W = [np.fft.ifftn(np.where(bins == b, Pm, 0.0)).real * npix for b in range(nb)]
+        Cf = [np.fft.ifftn((bins == b).astype(float)).real * npix for b in range(nb)]
+        delta = fields.quadratic_local(N, fnl, slope, sg, seed=200 + seed)
+        d = oracle.direct_bispectrum(delta, L, edges)
+        for (a, b, c), B, n in zip(d["triplets"], d["B"], d["N_tri"]):
+            if n < 500:
+                continue
+            pp = (np.sum(W[a] * W[b] * Cf[c]) + np.sum(Cf[a] * W[b] * W[c])
+                  + np.sum(W[a] * Cf[b] * W[c])) / npix
+            Bt = 2 * fnl * pp / n
+            s = 6 if a == b == c else (2 if (a == b or b == c) else 1)
+            P = d["P"]
+            var = s * V * P[a] * P[b] * P[c] / n
+            num_r += B * Bt / var
+            den_r += Bt * Bt / var
+    r = num_r / den_r
+    sig = 1.0 / math.sqrt(den_r)
+    assert sig < 0.2
+    assert abs(r - 1.0) < 4 * sig + 0.05, (r, sig)
+
+
+# ---------------------------------------------------------------- stored values
+def _read_golden(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    meta, rows = {}, []
+    for line in open(path):
+        if line.startswith("# ") and line.split()[1] in ("edges", "P", "shell"):
+            k = line.split()[1]
+            meta[k] = [float(v) for v in line.split()[2:]]
+        elif not line.startswith("#"):
+            rows.append(line.split())
+    return meta, rows
+
+
+def test_golden_lognormal32_reproduces():
+    meta, rows = _read_golden("lognormal32_lin6.txt")
+    N, L = 32, 100.0
+    f = fields.lognormal(N, 0.5, -2.0, seed=0).astype(np.float32).astype(np.float64)
+    d = oracle.direct_bispectrum(f, L, meta["edges"])
+    assert len(rows) == len(d["triplets"]) == 49
+    for r, t, n, B in zip(rows, d["triplets"], d["N_tri"], d["B"]):
+        assert [int(v) for v in r[:4]] == [int(t[0]), int(t[1]), int(t[2]), int(n)]
+        assert abs(float(r[4]) - B) <= 1e-12 * abs(B)
+    assert [int(v) for v in meta["shell"]] == list(d["shell"])
