@@ -1,0 +1,179 @@
+/*
+ * fbs.h -- C ABI of the GB300 FFT polyspectrum estimator.
+ *
+ * The library computes the binned bispectrum B(k1,k2,k3), power spectrum
+ * P(k) and four-shell trispectrum T(k1..k4) of a real periodic N^3 field with
+ * the FFT estimator of Watkinson, Majumdar, Pritchard & Mondal (arXiv
+ * 1705.06284), Sec. 2:
+ *
+ *   I_b(n) = sum_{m in S_b} D(m) e^{+2 pi i m.n/N}      shell field   (Eq. delta_nr)
+ *   N_b(n) = sum_{m in S_b}      e^{+2 pi i m.n/N}      count field   (Eq. delta_nr)
+ *   P_b    = V/N_pix^2   sum_n I_b^2       / sum_n N_b^2            (Eq. Jeong_PS)
+ *   B_abc  = V^2/N_pix^3 sum_n I_a I_b I_c / sum_n N_a N_b N_c      (Eq. Jeong_BI)
+ *   T_abcd = V^3/N_pix^4 sum_n I_a..I_d    / sum_n N_a..N_d         (Eq. Jeong_gen, p=4)
+ *
+ * where D(m) = sum_n delta(n) e^{-2 pi i m.n/N} is the unnormalised forward
+ * DFT (Eq. DeltaFFTtoDelta), V = L^3 and N_pix = N^3.  Shell b holds the
+ * lattice modes m (components wrapped into [-N/2, N/2)) with
+ * edges[b] <= |m| k_f < edges[b+1], k_f = 2 pi / L.  sum_n N_a N_b N_c equals
+ * N_pix times the exact triangle count N_tri (the denominator of Eq.
+ * gen_Nspec3); it is computed once per plan in FP64 and rounded to int64.
+ *
+ * Everything runs on one CUDA device, on the plan's stream, in hand-written
+ * sm_103a kernels.  There is no CPU fallback: without a usable device every
+ * entry point that needs one returns FBS_ERR_CUDA.
+ *
+ * Conventions for every entry point:
+ *   - Return FBS_OK (0) or a negative fbs_status; no entry point exits or
+ *     aborts.  fbs_last_error() gives a message for the calling thread.
+ *   - "Device or host" pointers are classified with cudaPointerGetAttributes:
+ *     device (and managed) memory is used in place; host memory (pageable or
+ *     pinned) is staged through plan-owned device buffers.
+ *   - A plan is not thread-safe: calls on one plan must be serialised by the
+ *     caller.  Different plans may be used from different threads.
+ */
+#ifndef FBS_H
+#define FBS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fbs_plan fbs_plan; /* opaque; owns shell tables, counts and workspaces */
+
+typedef enum {
+    FBS_OK = 0,
+    FBS_ERR_ARG = -1,            /* bad argument (null pointer, edges not ascending, ...) */
+    FBS_ERR_UNSUPPORTED_N = -2,  /* N not even, not 2^a 3^b, or outside [8, 512] */
+    FBS_ERR_OOM = -3,            /* a device allocation failed */
+    FBS_ERR_CUDA = -4,           /* a CUDA call or kernel failed, or no device */
+    FBS_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
+    FBS_ERR_STATE = -6,          /* call not valid for this plan (e.g. T on a B-only plan) */
+    FBS_ERR_NUMERIC = -7         /* an FP64 count was not within 1e-3 of an integer */
+} fbs_status;
+
+/* Contraction precision (Sec. 2's real-space product sums). FFTs are FP32
+ * in every mode; counts are FP64 in every mode. */
+enum {
+    FBS_PREC_FP32 = 0,    /* CUDA-core FP32 products, FP64 cross-block sums      */
+    FBS_PREC_BF16X3 = 1,  /* tcgen05 tensor cores, BF16 hi/lo split, 3 products  */
+    FBS_PREC_BF16 = 2     /* tcgen05 tensor cores, plain BF16 (error reported)   */
+};
+
+/* Plan flags. */
+enum {
+    FBS_FLAG_TRISPECTRUM = 1u,   /* also enumerate closed quadruplets (needed by fbs_trispectrum) */
+    FBS_FLAG_ALLOW_ALIASED = 2u, /* allow edges beyond N k_f/4 (closure is then modulo N, Sec. 3.2) */
+    FBS_FLAG_TIMING = 4u         /* record CUDA events around every kernel (fbs_plan_kernel_times) */
+};
+
+/*
+ * fbs_plan_create -- build a plan for N^3 fields in a box of side L.
+ *   out        : receives the plan (set to NULL on failure).
+ *   N          : grid side; even, of the form 2^a 3^b, 8 <= N <= 512.
+ *   L          : box side (> 0), physical length units; k_f = 2 pi / L.
+ *   edges      : host array of nbins+1 ascending bin edges in physical k units.
+ *                Unless FBS_FLAG_ALLOW_ALIASED, edges[nbins] <= N k_f / 4 (every
+ *                closed triangle is then closed exactly, not only modulo N,
+ *                below the aliasing limit N k_f/3 of Sec. 3.2).
+ *   nbins      : 1 <= nbins <= 128.
+ *   precision  : FBS_PREC_*.
+ *   flags      : FBS_FLAG_* bits.
+ *   cuda_stream: cudaStream_t the plan launches on (NULL = legacy default stream).
+ * The plan runs the plan-time work on the device before returning: shell
+ * tables, the FP64 count fields N_b, exact N_tri (and N_quad) for every
+ * candidate bin triple, and the closed-triplet list (lexicographic a<=b<=c
+ * with N_tri > 0).  Empty bins give no triplets and P = NaN.
+ */
+fbs_status fbs_plan_create(fbs_plan **out, int N, double L, const double *edges, int nbins,
+                           int precision, unsigned flags, void *cuda_stream);
+
+/* fbs_plan_free -- release the plan and all its device memory (NULL is a no-op).
+ * Synchronises the plan's stream first. */
+void fbs_plan_free(fbs_plan *plan);
+
+/* Number of closed triplets (outputs of fbs_bispectrum), or a negative status. */
+int fbs_plan_num_triplets(const fbs_plan *plan);
+
+/* Number of closed quadruplets (outputs of fbs_trispectrum; 0 without
+ * FBS_FLAG_TRISPECTRUM), or a negative status. */
+int fbs_plan_num_quads(const fbs_plan *plan);
+
+/* Copy the closed-triplet table to host arrays: abc[3*ntrip] (int32 bin
+ * indices a<=b<=c, lexicographic) and ntri[ntrip] (exact ordered triangle
+ * counts).  Either pointer may be NULL. */
+fbs_status fbs_plan_triplets(const fbs_plan *plan, int32_t *abc, int64_t *ntri);
+
+/* Copy the closed-quadruplet table: abcd[4*nquad] (a<=b<=c<=d) and
+ * nquad_counts[nquad] (exact ordered quadruple counts).  Either may be NULL. */
+fbs_status fbs_plan_quads(const fbs_plan *plan, int32_t *abcd, int64_t *nquad_counts);
+
+/* Copy shell sizes |S_b| (int64[nbins]) and, if thr != NULL, the integer
+ * thresholds on |m|^2 (int64[nbins+1]): bin b holds thr[b] <= |m|^2 < thr[b+1]. */
+fbs_status fbs_plan_shells(const fbs_plan *plan, int64_t *sizes, int64_t *thr);
+
+/* Change the contraction precision of an existing plan (FBS_PREC_*). */
+fbs_status fbs_plan_set_precision(fbs_plan *plan, int precision);
+
+/* Rebind the plan to another cudaStream_t (NULL = legacy default stream). */
+fbs_status fbs_plan_set_stream(fbs_plan *plan, void *cuda_stream);
+
+/*
+ * fbs_bispectrum -- B for every closed triplet and P for every bin.
+ *   field : N^3 FP32 values, C order [x][y][z] (z fastest), device or host.
+ *           Caller-owned; read only.
+ *   B     : double[ntrip] (device or host), order of fbs_plan_triplets; may be NULL.
+ *   P     : double[nbins] (device or host); may be NULL.
+ * With device field and outputs the call only enqueues work on the plan's
+ * stream and returns (results are ready when the stream reaches them).  With
+ * any host pointer it synchronises the stream before returning.
+ */
+fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double *P);
+
+/*
+ * fbs_trispectrum -- T for every closed quadruplet, plus B and P from the
+ * same shell fields (Sec. 2: lower orders come at no extra FFT cost).
+ * Needs a plan created with FBS_FLAG_TRISPECTRUM (else FBS_ERR_STATE).
+ * T: double[nquad]; B: double[ntrip]; P: double[nbins]; each device or host
+ * or NULL.  Same stream semantics as fbs_bispectrum.  The estimator is the
+ * raw p = 4 form (no subtraction of disconnected parts).
+ */
+fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double *B, double *P);
+
+/*
+ * fbs_plan_sums -- the raw FP64 real-space sums of the last call, for
+ * diagnostics and tests: num_trip[ntrip] = sum_n I_a I_b I_c,
+ * num_quad[nquad] = sum_n I_a I_b I_c I_d, sumsq[nbins] = sum_n I_b^2.  Host
+ * arrays (any may be NULL); synchronises the stream.
+ */
+fbs_status fbs_plan_sums(fbs_plan *plan, double *num_trip, double *num_quad, double *sumsq);
+
+/*
+ * fbs_plan_kernel_times -- with FBS_FLAG_TIMING, the CUDA-event time (ms) and
+ * launch count accumulated per kernel class since the last reset, in the
+ * order of fbs_kernel_class_name(0..n-1).  ms and launches are host arrays of
+ * n entries (n = fbs_num_kernel_classes()).  reset != 0 zeroes the counters
+ * after reading.  Synchronises the stream.
+ */
+int fbs_num_kernel_classes(void);
+const char *fbs_kernel_class_name(int i);
+fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, int reset);
+
+/* Plan-time cost (ms of wall time spent in fbs_plan_create). */
+double fbs_plan_create_ms(const fbs_plan *plan);
+
+/* Device bytes owned by the plan. */
+int64_t fbs_plan_device_bytes(const fbs_plan *plan);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *fbs_last_error(void);
+
+/* ABI version (major*100 + minor). */
+int fbs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBS_H */

@@ -1,0 +1,266 @@
+"""GB300-native FFT polyspectrum estimator (arXiv 1705.06284).
+
+A thin ctypes binding over the C ABI in ``include/fbs.h`` (argument
+marshalling only: every step of the estimator runs in the hand-written
+sm_103a kernels of ``libfbs.so``).  The functions below carry the C names;
+:class:`Plan` is a small convenience wrapper over them.
+
+PyTorch is used only for device memory and streams: pass CUDA float32
+tensors to keep everything on the device, or NumPy arrays to let the
+library stage host buffers.
+
+There is no CPU fallback.  Loading fails loudly if ``libfbs.so`` has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+
+__all__ = [
+    "FBS_PREC_FP32", "FBS_PREC_BF16X3", "FBS_PREC_BF16",
+    "FBS_FLAG_TRISPECTRUM", "FBS_FLAG_ALLOW_ALIASED", "FBS_FLAG_TIMING",
+    "FbsError", "Plan", "lib", "kernel_class_names",
+    "fbs_plan_create", "fbs_plan_free", "fbs_bispectrum", "fbs_trispectrum",
+]
+
+FBS_PREC_FP32 = 0
+FBS_PREC_BF16X3 = 1
+FBS_PREC_BF16 = 2
+FBS_FLAG_TRISPECTRUM = 1
+FBS_FLAG_ALLOW_ALIASED = 2
+FBS_FLAG_TIMING = 4
+
+_PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
+
+_STATUS = {0: "FBS_OK", -1: "FBS_ERR_ARG", -2: "FBS_ERR_UNSUPPORTED_N", -3: "FBS_ERR_OOM",
+           -4: "FBS_ERR_CUDA", -5: "FBS_ERR_TIMEOUT", -6: "FBS_ERR_STATE", -7: "FBS_ERR_NUMERIC"}
+
+
+class FbsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (_STATUS.get(status, "?"), status, msg))
+        self.status = status
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/fbs.h
+_vp = ctypes.c_void_p
+_SIGS = [
+    ("fbs_plan_create", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_uint, _vp]),
+    ("fbs_plan_free", None, [_vp]),
+    ("fbs_plan_num_triplets", ctypes.c_int, [_vp]),
+    ("fbs_plan_num_quads", ctypes.c_int, [_vp]),
+    ("fbs_plan_triplets", ctypes.c_int, [_vp, _vp, _vp]),
+    ("fbs_plan_quads", ctypes.c_int, [_vp, _vp, _vp]),
+    ("fbs_plan_shells", ctypes.c_int, [_vp, _vp, _vp]),
+    ("fbs_plan_set_precision", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("fbs_plan_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("fbs_bispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("fbs_trispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    ("fbs_plan_sums", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("fbs_num_kernel_classes", ctypes.c_int, []),
+    ("fbs_kernel_class_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("fbs_plan_kernel_times", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
+    ("fbs_plan_create_ms", ctypes.c_double, [_vp]),
+    ("fbs_plan_device_bytes", ctypes.c_int64, [_vp]),
+    ("fbs_last_error", ctypes.c_char_p, []),
+    ("fbs_version", ctypes.c_int, []),
+]
+
+
+def lib():
+    """Load ``libfbs.so`` (built in-tree).  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError("libfbs.so is not built (%s); run __graft_entry__.build()" % _LIB_PATH)
+        L = ctypes.CDLL(_LIB_PATH)
+        for name, res, args in _SIGS:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        msg = lib().fbs_last_error().decode(errors="replace")
+        raise FbsError(status, msg)
+
+
+def kernel_class_names():
+    L = lib()
+    return [L.fbs_kernel_class_name(i).decode() for i in range(L.fbs_num_kernel_classes())]
+
+
+# ---------------------------------------------------------------- C-named calls
+def fbs_plan_create(N, L, edges, precision=FBS_PREC_FP32, flags=0, stream=None):
+    """Returns an opaque plan handle (int)."""
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    h = _vp()
+    _check(lib().fbs_plan_create(ctypes.byref(h), int(N), float(L),
+                                 e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(e) - 1,
+                                 int(precision), int(flags), _vp(stream or 0)))
+    return h.value
+
+
+def fbs_plan_free(h):
+    lib().fbs_plan_free(_vp(h))
+
+
+def fbs_bispectrum(h, field_ptr, B_ptr, P_ptr):
+    _check(lib().fbs_bispectrum(_vp(h), _vp(field_ptr), _vp(B_ptr or 0), _vp(P_ptr or 0)))
+
+
+def fbs_trispectrum(h, field_ptr, T_ptr, B_ptr, P_ptr):
+    _check(lib().fbs_trispectrum(_vp(h), _vp(field_ptr), _vp(T_ptr or 0), _vp(B_ptr or 0),
+                                 _vp(P_ptr or 0)))
+
+
+# ---------------------------------------------------------------- convenience
+def _ptr(a):
+    """(pointer, keepalive) for a torch tensor or NumPy array."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, a
+    return a.data_ptr(), a
+
+
+class Plan:
+    """Plan for N^3 fields in a box of side L with the given bin edges.
+
+    ``precision``: "fp32" | "bf16x3" | "bf16".  ``stream``: a torch CUDA
+    stream (default: torch's current stream, or the legacy default stream
+    without torch).
+    """
+
+    def __init__(self, N, L, edges, precision="fp32", trispectrum=False, allow_aliased=False,
+                 timing=False, stream=None):
+        flags = (FBS_FLAG_TRISPECTRUM if trispectrum else 0) | \
+                (FBS_FLAG_ALLOW_ALIASED if allow_aliased else 0) | (FBS_FLAG_TIMING if timing else 0)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream()
+            except Exception:
+                stream = None
+        sp = getattr(stream, "cuda_stream", stream) if stream is not None else 0
+        self.N, self.L = int(N), float(L)
+        self.edges = np.ascontiguousarray(edges, dtype=np.float64)
+        self.nbins = len(self.edges) - 1
+        self._h = fbs_plan_create(N, L, self.edges, _PREC[precision], flags, sp)
+        self.precision = precision
+        Lb = lib()
+        self.ntrip = Lb.fbs_plan_num_triplets(_vp(self._h))
+        self.nquad = Lb.fbs_plan_num_quads(_vp(self._h))
+        self.triplets = np.zeros((self.ntrip, 3), dtype=np.int32)
+        self.N_tri = np.zeros(self.ntrip, dtype=np.int64)
+        _check(Lb.fbs_plan_triplets(_vp(self._h), self.triplets.ctypes.data, self.N_tri.ctypes.data))
+        self.quads = np.zeros((self.nquad, 4), dtype=np.int32)
+        self.N_quad = np.zeros(self.nquad, dtype=np.int64)
+        _check(Lb.fbs_plan_quads(_vp(self._h), self.quads.ctypes.data, self.N_quad.ctypes.data))
+        self.shell = np.zeros(self.nbins, dtype=np.int64)
+        self.thresholds = np.zeros(self.nbins + 1, dtype=np.int64)
+        _check(Lb.fbs_plan_shells(_vp(self._h), self.shell.ctypes.data, self.thresholds.ctypes.data))
+        self.create_ms = Lb.fbs_plan_create_ms(_vp(self._h))
+        self.device_bytes = int(Lb.fbs_plan_device_bytes(_vp(self._h)))
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            fbs_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_precision(self, precision):
+        _check(lib().fbs_plan_set_precision(_vp(self._h), _PREC[precision]))
+        self.precision = precision
+
+    def set_stream(self, stream):
+        sp = getattr(stream, "cuda_stream", stream) or 0
+        _check(lib().fbs_plan_set_stream(_vp(self._h), _vp(sp)))
+
+    # -- estimators
+    def _outputs(self, like, n):
+        if isinstance(like, np.ndarray):
+            return np.empty(n, dtype=np.float64)
+        import torch
+        return torch.empty(n, dtype=torch.float64, device=like.device)
+
+    def bispectrum(self, field, B=None, P=None):
+        """B[ntrip], P[nbins] for an N^3 float32 field (torch CUDA tensor or
+        NumPy array).  Outputs live where the field lives unless given."""
+        self._check_field(field)
+        B = self._outputs(field, self.ntrip) if B is None else B
+        P = self._outputs(field, self.nbins) if P is None else P
+        fp, _k0 = _ptr(field)
+        bp, _k1 = _ptr(B)
+        pp, _k2 = _ptr(P)
+        fbs_bispectrum(self._h, fp, bp, pp)
+        return B, P
+
+    def trispectrum(self, field, T=None, B=None, P=None):
+        self._check_field(field)
+        T = self._outputs(field, self.nquad) if T is None else T
+        B = self._outputs(field, self.ntrip) if B is None else B
+        P = self._outputs(field, self.nbins) if P is None else P
+        fp, _k0 = _ptr(field)
+        tp, _k1 = _ptr(T)
+        bp, _k2 = _ptr(B)
+        pp, _k3 = _ptr(P)
+        fbs_trispectrum(self._h, fp, tp, bp, pp)
+        return T, B, P
+
+    def _check_field(self, f):
+        n = self.N
+        if tuple(f.shape) != (n, n, n):
+            raise ValueError("field must have shape (%d, %d, %d)" % (n, n, n))
+        if isinstance(f, np.ndarray):
+            if f.dtype != np.float32 or not f.flags["C_CONTIGUOUS"]:
+                raise ValueError("field must be C-contiguous float32")
+        else:
+            import torch
+            if f.dtype != torch.float32 or not f.is_contiguous():
+                raise ValueError("field must be a contiguous float32 tensor")
+
+    def sums(self):
+        """Raw FP64 sums of the last call: (num_trip, num_quad, sumsq)."""
+        a = np.zeros(self.ntrip)
+        q = np.zeros(self.nquad)
+        s = np.zeros(self.nbins)
+        _check(lib().fbs_plan_sums(_vp(self._h), a.ctypes.data, q.ctypes.data, s.ctypes.data))
+        return a, q, s
+
+    def kernel_times(self, reset=False):
+        """{class: (ms, launches)} accumulated with timing=True."""
+        n = lib().fbs_num_kernel_classes()
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        _check(lib().fbs_plan_kernel_times(_vp(self._h), ms.ctypes.data, cnt.ctypes.data,
+                                           1 if reset else 0))
+        return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(kernel_class_names())}

@@ -1,0 +1,191 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the public ABI (that is include/fbs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fbs.h"
+
+namespace fbs {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+struct Failure {
+    fbs_status status;
+    std::string msg;
+};
+// Throws Failure on CUDA error (caught at the ABI boundary).
+void check_cuda(cudaError_t e, const char *what);
+#define FBS_CUDA(call) ::fbs::check_cuda((call), #call)
+
+// ---------------------------------------------------------------- FFT plan
+// Radix factorisation of a length-n transform (n = 2^a 3^b <= 512).
+struct FftFactors {
+    int n;
+    int nst;
+    int r[12];
+};
+FftFactors make_factors(int n);
+
+// Per-bin geometry of the pruned inverse transform.
+//   Rb    : largest |m_j| a mode of the bin can have (clamped to N/2).
+//   Db    : bin box extent along x and y (2Rb+1, or N when it would exceed N).
+//   Dzb   : bin box extent along z (Rb+1, or N/2+1).
+//   A_off : offset (complex elements) of the bin's x-stage output A_b[x][jy][jz].
+//   G_off : offset (complex elements) of the bin's y-stage output per slab.
+struct BinGeom {
+    int Rb, Db, Dzb, empty;
+    long long thr_lo, thr_hi;
+    long long A_off, G_off;
+};
+
+// Device-side description of the spectrum box (forward output):
+//   Box[jx][jy][jz], jx,jy in [0, D), jz in [0, Dz), complex64.
+struct BoxGeom {
+    int N, R, D, Dz;
+};
+
+// Index <-> frequency for an axis of extent D holding m in [-R, R] (D = 2R+1)
+// or the whole FFT axis (D == N).
+__host__ __device__ inline int box_freq(int j, int D, int N) {
+    if (D == N) return j < N / 2 ? j : j - N;
+    return j <= D / 2 ? j : j - D;
+}
+__host__ __device__ inline int box_index(int m, int D) {
+    return m >= 0 ? m : m + D;
+}
+
+// ---------------------------------------------------------------- contraction tasks
+// Pair-grouped work list (host + device copies).  For bispectra an outer
+// pair (b, c) carries inner items a (single bins); for trispectra an outer
+// pair (c, d) carries inner pairs (a, b).  item_out is the output index.
+struct TaskList {
+    int npairs = 0, nitems = 0;
+    std::vector<int> pb, pc, pstart;        // outer pair bins, CSR start (npairs+1)
+    std::vector<int> ia, ib, iout;          // inner item bins (ib = -1 for triplets), output index
+};
+
+// ---------------------------------------------------------------- timing
+enum KernelClass {
+    KC_FWD_Z = 0,
+    KC_FWD_Y,
+    KC_FWD_X,
+    KC_INV_X,
+    KC_INV_Y,
+    KC_INV_Z,
+    KC_CONTRACT,
+    KC_CONTRACT_TC,
+    KC_QUAD,
+    KC_REDUCE,
+    KC_COUNT,
+    KC_NUM
+};
+
+struct Plan;
+
+// ---------------------------------------------------------------- kernels (launch wrappers)
+// fft.cu
+void upload_twiddles(Plan &p);
+void launch_forward(Plan &p, const float *d_field);
+void launch_inverse_x(Plan &p, bool indicator_fp64);
+void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab);
+void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
+                                   double2 *G64, const BinGeom *d_geom_grp);
+// contract.cu (FP64 count sums)
+void launch_count_contraction(Plan &p, const double *noct, int nb_in_group, int bin0,
+                              const int *d_items, int nitems, int arity, double *d_sums);
+// contract.cu
+void launch_contract_fp32(Plan &p, const float *islab, long long npts, long long slab_stride,
+                          bool quads);
+void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride);
+void launch_reduce_and_normalise(Plan &p, bool quads);
+void zero_partials(Plan &p, bool quads);
+std::vector<int> item_groups(const TaskList &t, int cap);
+int contract_blocks();
+
+// ---------------------------------------------------------------- plan
+struct Plan {
+    int N = 0;
+    double L = 0;
+    int nbins = 0;
+    int precision = 0;
+    unsigned flags = 0;
+    cudaStream_t stream = nullptr;
+    double create_ms = 0;
+
+    std::vector<long long> thr;  // nbins+1
+    std::vector<long long> shell;
+    std::vector<BinGeom> geom;
+    BoxGeom box{};
+    FftFactors fN{};
+
+    std::vector<int32_t> trip;   // 3*ntrip
+    std::vector<int64_t> ntri;
+    std::vector<int32_t> quad;   // 4*nquad
+    std::vector<int64_t> nquad;
+    TaskList ttask, qtask;
+    std::vector<int> tgrp, qgrp;  // item groups of the FP32 contraction (outer-pair ranges)
+    int *d_tgrp = nullptr, *d_qgrp = nullptr;
+
+    long long A_elems = 0;       // complex elements of the x-stage output (all bins)
+    long long G_plane = 0;       // complex elements of the y-stage output per x plane (all bins)
+    int slab = 0;                // x planes per slab
+    int nslabs = 0;
+
+    // device memory
+    std::vector<void *> allocs;
+    long long dev_bytes = 0;
+    float *d_field = nullptr;    // staging for host fields
+    float2 *d_zbuf = nullptr;    // forward scratch [N][N][Dz]
+    float2 *d_ybuf = nullptr;    // forward scratch [N][D][Dz]
+    float2 *d_box = nullptr;     // spectrum box [D][D][Dz]
+    float2 *d_A = nullptr;       // inverse x-stage output
+    float2 *d_G = nullptr;       // inverse y-stage output (one slab)
+    float *d_I = nullptr;        // shell fields (one slab) [bin][plane][y][z]
+    BinGeom *d_geom = nullptr;
+    float2 *d_tw = nullptr;      // e^{-2 pi i k/N}, k < N (FP32)
+    double2 *d_tw64 = nullptr;   // same in FP64 (count path)
+    // task lists on device
+    int *d_tpb = nullptr, *d_tpc = nullptr, *d_tps = nullptr, *d_tia = nullptr, *d_tout = nullptr;
+    int *d_qpb = nullptr, *d_qpc = nullptr, *d_qps = nullptr, *d_qia = nullptr, *d_qib = nullptr,
+        *d_qout = nullptr;
+    // accumulators
+    int part_blocks = 0;          // number of FP64 partial rows
+    double *d_tpart = nullptr;    // [part_blocks][ntrip]
+    double *d_qpart = nullptr;    // [part_blocks][nquad]
+    double *d_sumsq = nullptr;    // [nbins]
+    double *d_tnum = nullptr;     // [ntrip]
+    double *d_qnum = nullptr;     // [nquad]
+    double *d_B = nullptr, *d_P = nullptr, *d_T = nullptr;  // staging for host outputs
+    int64_t *d_ntri = nullptr, *d_nquad = nullptr;
+    long long *d_shell = nullptr;
+    // tensor-core path
+    void *tc = nullptr;           // opaque state of contract_tc.cu
+
+    // timing
+    std::vector<cudaEvent_t> evs;  // 2 per pending launch, created once and reused
+    double kt_ms[KC_NUM] = {};
+    long long kt_n[KC_NUM] = {};
+    std::vector<std::pair<int, int>> pending;  // (class, event pair index)
+
+    void *dalloc(size_t bytes);
+    void tic(int cls, int &slot);
+    void toc(int slot);
+    void flush_times();
+};
+
+// Bracket a launch with timing events when FBS_FLAG_TIMING is set.
+struct KTimer {
+    Plan &p;
+    int slot = -1;
+    KTimer(Plan &pl, int cls) : p(pl) { p.tic(cls, slot); }
+    ~KTimer() { p.toc(slot); }
+};
+
+void free_tc_state(Plan &p);
+
+}  // namespace fbs

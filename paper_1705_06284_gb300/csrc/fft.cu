@@ -1,0 +1,469 @@
+// Pruned 3D FFTs of the estimator (hand-written, no cuFFT).
+//
+// Forward (Eq. DeltaFFTtoDelta, unnormalised): three passes over the real
+// field delta[x][y][z] that keep only the spectrum box |m_j| <= R, mz >= 0,
+// where R is the largest component any bin can hold:
+//   z pass  (R2C, two real rows packed in one complex line) -> zbuf[x][y][jz]
+//   y pass  (complex, outputs pruned to |my| <= R)          -> ybuf[x][jy][jz]
+//   x pass  (complex, outputs pruned to |mx| <= R)          -> box[jx][jy][jz]
+//
+// Inverse per shell (Eq. delta_nr): for every bin b the spectrum is masked to
+// thr_lo <= |m|^2 < thr_hi while it is loaded (the "new FFT box" of Sec. 2
+// is never materialised) and transformed back, unnormalised:
+//   x stage: columns (my, mz) of the bin's disk -> A_b[x][jy][jz]   (all x)
+//   y stage: per x plane, columns mz            -> G_b[x][y][jz]    (one slab)
+//   z stage: C2R per row, two rows per complex line -> I_b[x][y][z] (one slab)
+// The z stage also accumulates sum_n I_b(n)^2 (numerator of Eq. Jeong_PS).
+//
+// The same stages run in FP64 on the shell indicator to build the count
+// fields N_b (plan time); that variant writes only the octant
+// 0 <= x, y, z <= N/2, which carries all of N_b's values because every shell
+// is symmetric under m_j -> -m_j.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "fbs_internal.h"
+#include "fft_core.cuh"
+
+namespace fbs {
+
+static constexpr int kThreads = 256;
+
+template <typename T>
+static int lines_per_cta(int N) {
+    // two ping-pong buffers of nl lines of N complex values, <= 64 KB (FP32) / 128 KB (FP64)
+    int budget = (int)(sizeof(T) == 4 ? 64 * 1024 : 128 * 1024);
+    int nl = budget / (2 * (N + 1) * (int)(2 * sizeof(T)));
+    if (nl > 16) nl = 16;
+    if (nl < 1) nl = 1;
+    return nl;
+}
+
+template <typename K>
+static void allow_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024)
+        FBS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+// ------------------------------------------------------------------ forward
+// z pass: rows r = x*N + y, packed pairs (r0, r0+1) as re/im of one line.
+__global__ void __launch_bounds__(kThreads) fwd_z_kernel(const float *__restrict__ field,
+                                                         float2 *__restrict__ zbuf, int N, int Dz,
+                                                         int nl, FftFactors f,
+                                                         const float2 *__restrict__ tw) {
+    extern __shared__ float2 sm[];
+    float2 *a = sm;
+    const int ld = N + 1;
+    float2 *b = sm + (size_t)nl * ld;
+    const long long nrows = (long long)N * N;
+    const long long row0 = (long long)blockIdx.x * nl * 2;
+    for (int i = threadIdx.x; i < nl * N; i += blockDim.x) {
+        int line = i / N, z = i - line * N;
+        long long r = row0 + 2 * line;
+        float v0 = r < nrows ? field[r * N + z] : 0.f;
+        float v1 = r + 1 < nrows ? field[(r + 1) * N + z] : 0.f;
+        a[line * ld + z] = make_float2(v0, v1);
+    }
+    __syncthreads();
+    float2 *res = smem_fft<float, -1>(a, b, nl, ld, f, tw);
+    for (int i = threadIdx.x; i < nl * Dz; i += blockDim.x) {
+        int line = i / Dz, m = i - line * Dz;
+        long long r = row0 + 2 * line;
+        float2 zm = res[line * ld + m];
+        float2 zn = res[line * ld + (m == 0 ? 0 : N - m)];
+        // X0 = (Z(m) + conj Z(N-m))/2,  X1 = (Z(m) - conj Z(N-m))/(2i)
+        float2 x0 = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
+        float2 x1 = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
+        if (r < nrows) zbuf[r * Dz + m] = x0;
+        if (r + 1 < nrows) zbuf[(r + 1) * Dz + m] = x1;
+    }
+}
+
+// y pass: lines (x, jz); input zbuf[x][y][jz], output ybuf[x][jy][jz].
+__global__ void __launch_bounds__(kThreads) fwd_y_kernel(const float2 *__restrict__ zbuf,
+                                                         float2 *__restrict__ ybuf, int N, int D,
+                                                         int Dz, int nl, FftFactors f,
+                                                         const float2 *__restrict__ tw) {
+    extern __shared__ float2 sm[];
+    float2 *a = sm;
+    const int ld = N + 1;
+    float2 *b = sm + (size_t)nl * ld;
+    const int x = blockIdx.y;
+    const int jz0 = blockIdx.x * nl;
+    const int nz = min(nl, Dz - jz0);
+    for (int i = threadIdx.x; i < nl * N; i += blockDim.x) {
+        int y = i / nl, l = i - y * nl;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < nz) v = zbuf[((long long)x * N + y) * Dz + jz0 + l];
+        a[l * ld + y] = v;
+    }
+    __syncthreads();
+    float2 *res = smem_fft<float, -1>(a, b, nl, ld, f, tw);
+    for (int i = threadIdx.x; i < nl * D; i += blockDim.x) {
+        int jy = i / nl, l = i - jy * nl;
+        if (l >= nz) continue;
+        int m = box_freq(jy, D, N);
+        ybuf[((long long)x * D + jy) * Dz + jz0 + l] = res[l * ld + (m + N) % N];
+    }
+}
+
+// x pass: lines (jy, jz); input ybuf[x][jy][jz], output box[jx][jy][jz].
+__global__ void __launch_bounds__(kThreads) fwd_x_kernel(const float2 *__restrict__ ybuf,
+                                                         float2 *__restrict__ box, int N, int D,
+                                                         int Dz, int nl, FftFactors f,
+                                                         const float2 *__restrict__ tw) {
+    extern __shared__ float2 sm[];
+    float2 *a = sm;
+    const int ld = N + 1;
+    float2 *b = sm + (size_t)nl * ld;
+    const int jy = blockIdx.y;
+    const int jz0 = blockIdx.x * nl;
+    const int nz = min(nl, Dz - jz0);
+    for (int i = threadIdx.x; i < nl * N; i += blockDim.x) {
+        int x = i / nl, l = i - x * nl;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < nz) v = ybuf[((long long)x * D + jy) * Dz + jz0 + l];
+        a[l * ld + x] = v;
+    }
+    __syncthreads();
+    float2 *res = smem_fft<float, -1>(a, b, nl, ld, f, tw);
+    for (int i = threadIdx.x; i < nl * D; i += blockDim.x) {
+        int jx = i / nl, l = i - jx * nl;
+        if (l >= nz) continue;
+        int m = box_freq(jx, D, N);
+        box[((long long)jx * D + jy) * Dz + jz0 + l] = res[l * ld + (m + N) % N];
+    }
+}
+
+// ------------------------------------------------------------------ inverse
+// x stage.  CTA = (bin b = bin0 + blockIdx.y, column jy, group of nl jz).
+// IND = true: the spectrum is the shell indicator (count fields, FP64).
+template <typename T, bool IND>
+__global__ void __launch_bounds__(kThreads) inv_x_kernel(const float2 *__restrict__ box, BoxGeom bg,
+                                                         const BinGeom *__restrict__ geom, int bin0,
+                                                         typename V2<T>::t *__restrict__ A, int nl,
+                                                         FftFactors f,
+                                                         const typename V2<T>::t *__restrict__ tw) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *a = reinterpret_cast<C *>(smraw);
+    const int ld = bg.N + 1;
+    C *b = a + (size_t)nl * ld;
+    const BinGeom g = geom[bin0 + blockIdx.y];
+    if (g.empty) return;
+    const int ngz = (g.Dzb + nl - 1) / nl;
+    if ((int)blockIdx.x >= g.Db * ngz) return;
+    const int jy = blockIdx.x / ngz;
+    const int jz0 = (blockIdx.x - jy * ngz) * nl;
+    const int nz = min(nl, g.Dzb - jz0);
+    const int N = bg.N;
+    const int my = box_freq(jy, g.Db, N);
+    // every line of this CTA empty?  (my^2 + mz^2 >= thr_hi for the smallest mz)
+    if ((long long)my * my + (long long)jz0 * jz0 >= g.thr_hi) return;
+    const int gjy = box_index(my, bg.D);
+    for (int i = threadIdx.x; i < nl * ld; i += blockDim.x) a[i] = C{T(0), T(0)};
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl * bg.D; i += blockDim.x) {
+        int jx = i / nl, l = i - jx * nl;
+        if (l >= nz) continue;
+        int mx = box_freq(jx, bg.D, N);
+        int mz = jz0 + l;
+        long long s = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
+        if (s < g.thr_lo || s >= g.thr_hi) continue;
+        C v;
+        if (IND) {
+            v = C{T(1), T(0)};
+        } else {
+            float2 d = box[((long long)jx * bg.D + gjy) * bg.Dz + mz];
+            v = C{T(d.x), T(d.y)};
+        }
+        a[l * ld + (mx + N) % N] = v;
+    }
+    __syncthreads();
+    C *res = smem_fft<T, +1>(a, b, nl, ld, f, tw);
+    C *out = A + g.A_off;
+    for (int i = threadIdx.x; i < nl * N; i += blockDim.x) {
+        int x = i / nl, l = i - x * nl;
+        if (l >= nz) continue;
+        out[((long long)x * g.Db + jy) * g.Dzb + jz0 + l] = res[l * ld + x];
+    }
+}
+
+// y stage over planes x0 .. x0+nx-1.  CTA = (jz group, plane, bin).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) inv_y_kernel(const typename V2<T>::t *__restrict__ A,
+                                                         const BinGeom *__restrict__ geom, int bin0,
+                                                         int N, int x0,
+                                                         typename V2<T>::t *__restrict__ G,
+                                                         long long G_stride_plane_unused, int nl,
+                                                         FftFactors f,
+                                                         const typename V2<T>::t *__restrict__ tw) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *a = reinterpret_cast<C *>(smraw);
+    const int ld = N + 1;
+    C *b = a + (size_t)nl * ld;
+    const BinGeom g = geom[bin0 + blockIdx.z];
+    if (g.empty) return;
+    const int jz0 = blockIdx.x * nl;
+    if (jz0 >= g.Dzb) return;
+    const int nz = min(nl, g.Dzb - jz0);
+    const int xl = blockIdx.y;
+    const int x = x0 + xl;
+    const C *in = A + g.A_off;
+    for (int i = threadIdx.x; i < nl * ld; i += blockDim.x) a[i] = C{T(0), T(0)};
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl * g.Db; i += blockDim.x) {
+        int jy = i / nl, l = i - jy * nl;
+        if (l >= nz) continue;
+        int my = box_freq(jy, g.Db, N);
+        int mz = jz0 + l;
+        if ((long long)my * my + (long long)mz * mz >= g.thr_hi) continue;  // column never written
+        a[l * ld + (my + N) % N] = in[((long long)x * g.Db + jy) * g.Dzb + mz];
+    }
+    __syncthreads();
+    C *res = smem_fft<T, +1>(a, b, nl, ld, f, tw);
+    C *out = G + g.G_off;
+    for (int i = threadIdx.x; i < nl * N; i += blockDim.x) {
+        int y = i / nl, l = i - y * nl;
+        if (l >= nz) continue;
+        out[((long long)xl * N + y) * g.Dzb + jz0 + l] = res[l * ld + y];
+    }
+}
+
+// z stage (C2R).  CTA = (row-pair group, plane, bin).  Rows (y, y+1) share a
+// complex line: Z = H_y + i H_{y+1}, H the Hermitian completion of the row.
+// OCT = false: write I_b[xl][y][z] (FP32) for all rows and accumulate sum I^2.
+// OCT = true : write only y <= N/2, z <= N/2 to out[b][xl][y][z] with side N/2+1.
+template <typename T, bool OCT>
+__global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t *__restrict__ G,
+                                                         const BinGeom *__restrict__ geom, int bin0,
+                                                         int N, T *__restrict__ out,
+                                                         long long out_bin_stride,
+                                                         double *__restrict__ sumsq, int nl,
+                                                         FftFactors f,
+                                                         const typename V2<T>::t *__restrict__ tw) {
+    typedef typename V2<T>::t C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *a = reinterpret_cast<C *>(smraw);
+    const int ld = N + 1;
+    C *b = a + (size_t)nl * ld;
+    __shared__ double red[kThreads / 32];
+    const int bl = blockIdx.z;
+    const BinGeom g = geom[bin0 + bl];
+    const int xl = blockIdx.y;
+    const int nrows = OCT ? N / 2 + 1 : N;
+    const int y0 = blockIdx.x * nl * 2;
+    if (y0 >= nrows) return;
+    T *ob = out + (long long)bl * out_bin_stride;
+    if (g.empty) {
+        if (!OCT) {
+            for (int i = threadIdx.x; i < nl * 2 * N; i += blockDim.x) {
+                int r = i / N, z = i - r * N;
+                int y = y0 + r;
+                if (y < nrows) ob[((long long)xl * N + y) * N + z] = T(0);
+            }
+        } else {
+            const int H = N / 2 + 1;
+            for (int i = threadIdx.x; i < nl * 2 * H; i += blockDim.x) {
+                int r = i / H, z = i - r * H;
+                int y = y0 + r;
+                if (y < nrows) ob[((long long)xl * H + y) * H + z] = T(0);
+            }
+        }
+        return;
+    }
+    const C *in = G + g.G_off;
+    const int Dzb = g.Dzb;
+    for (int i = threadIdx.x; i < nl * ld; i += blockDim.x) a[i] = C{T(0), T(0)};
+    __syncthreads();
+    for (int i = threadIdx.x; i < nl * Dzb; i += blockDim.x) {
+        int line = i / Dzb, m = i - line * Dzb;
+        int y = y0 + 2 * line;
+        C h1 = C{T(0), T(0)}, h2 = C{T(0), T(0)};
+        if (y < N) h1 = in[((long long)xl * N + y) * Dzb + m];
+        if (y + 1 < N) h2 = in[((long long)xl * N + y + 1) * Dzb + m];
+        const bool self_conj = (m == 0) || (2 * m == N);
+        if (self_conj) {  // DC and Nyquist of a real row are real
+            h1.y = T(0);
+            h2.y = T(0);
+        }
+        // Z(m) = H1(m) + i H2(m);  Z(N-m) = conj H1(m) + i conj H2(m)
+        C zp = C{h1.x - h2.y, h1.y + h2.x};
+        a[line * ld + m] = zp;
+        if (!self_conj) {
+            C zn = C{h1.x + h2.y, -h1.y + h2.x};
+            a[line * ld + (N - m)] = zn;
+        }
+    }
+    __syncthreads();
+    C *res = smem_fft<T, +1>(a, b, nl, ld, f, tw);
+    double acc = 0.0;
+    if (!OCT) {
+        for (int i = threadIdx.x; i < nl * 2 * N; i += blockDim.x) {
+            int r = i / N, z = i - r * N;
+            int y = y0 + r;
+            if (y >= nrows) continue;
+            C v = res[(r >> 1) * ld + z];
+            T val = (r & 1) ? v.y : v.x;
+            ob[((long long)xl * N + y) * N + z] = val;
+            acc += (double)(val * val);
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+            atomicAdd(&sumsq[bin0 + bl], s);
+        }
+    } else {
+        const int H = N / 2 + 1;
+        for (int i = threadIdx.x; i < nl * 2 * H; i += blockDim.x) {
+            int r = i / H, z = i - r * H;
+            int y = y0 + r;
+            if (y >= nrows) continue;
+            C v = res[(r >> 1) * ld + z];
+            ob[((long long)xl * H + y) * H + z] = (r & 1) ? v.y : v.x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+void upload_twiddles(Plan &p) {
+    const int N = p.N;
+    std::vector<float2> t32(N);
+    std::vector<double2> t64(N);
+    for (int k = 0; k < N; ++k) {
+        // e^{-2 pi i k/N} from exact octant reduction of k/N in FP64
+        double ang = -2.0 * M_PI * (double)k / (double)N;
+        double c = cos(ang), s = sin(ang);
+        if (4 * k == N) { c = 0.0; s = -1.0; }
+        if (2 * k == N) { c = -1.0; s = 0.0; }
+        if (4 * k == 3 * N) { c = 0.0; s = 1.0; }
+        t64[k] = make_double2(c, s);
+        t32[k] = make_float2((float)c, (float)s);
+    }
+    p.d_tw = (float2 *)p.dalloc(N * sizeof(float2));
+    p.d_tw64 = (double2 *)p.dalloc(N * sizeof(double2));
+    FBS_CUDA(cudaMemcpyAsync(p.d_tw, t32.data(), N * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
+    FBS_CUDA(cudaMemcpyAsync(p.d_tw64, t64.data(), N * sizeof(double2), cudaMemcpyHostToDevice, p.stream));
+}
+
+void launch_forward(Plan &p, const float *d_field) {
+    const int N = p.N, D = p.box.D, Dz = p.box.Dz;
+    const int nl = lines_per_cta<float>(N);
+    const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
+    {
+        KTimer t(p, KC_FWD_Z);
+        allow_smem(fwd_z_kernel, sm);
+        long long rows = (long long)N * N;
+        int grid = (int)((rows + 2 * nl - 1) / (2 * nl));
+        fwd_z_kernel<<<grid, kThreads, sm, p.stream>>>(d_field, p.d_zbuf, N, Dz, nl, p.fN, p.d_tw);
+        FBS_CUDA(cudaGetLastError());
+    }
+    {
+        KTimer t(p, KC_FWD_Y);
+        allow_smem(fwd_y_kernel, sm);
+        dim3 grid((Dz + nl - 1) / nl, N);
+        fwd_y_kernel<<<grid, kThreads, sm, p.stream>>>(p.d_zbuf, p.d_ybuf, N, D, Dz, nl, p.fN, p.d_tw);
+        FBS_CUDA(cudaGetLastError());
+    }
+    {
+        KTimer t(p, KC_FWD_X);
+        allow_smem(fwd_x_kernel, sm);
+        dim3 grid((Dz + nl - 1) / nl, D);
+        fwd_x_kernel<<<grid, kThreads, sm, p.stream>>>(p.d_ybuf, p.d_box, N, D, Dz, nl, p.fN, p.d_tw);
+        FBS_CUDA(cudaGetLastError());
+    }
+}
+
+static int max_inv_x_grid(const Plan &p, int bin0, int nb, int nl) {
+    int gx = 1;
+    for (int b = bin0; b < bin0 + nb; ++b) {
+        const BinGeom &g = p.geom[b];
+        if (g.empty) continue;
+        gx = std::max(gx, g.Db * ((g.Dzb + nl - 1) / nl));
+    }
+    return gx;
+}
+
+static int max_dzb(const Plan &p, int bin0, int nb) {
+    int m = 1;
+    for (int b = bin0; b < bin0 + nb; ++b)
+        if (!p.geom[b].empty) m = std::max(m, p.geom[b].Dzb);
+    return m;
+}
+
+void launch_inverse_x(Plan &p, bool) {
+    const int N = p.N;
+    const int nl = lines_per_cta<float>(N);
+    const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
+    KTimer t(p, KC_INV_X);
+    auto k = inv_x_kernel<float, false>;
+    allow_smem(k, sm);
+    dim3 grid(max_inv_x_grid(p, 0, p.nbins, nl), p.nbins);
+    k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.box, p.d_geom, 0, p.d_A, nl, p.fN, p.d_tw);
+    FBS_CUDA(cudaGetLastError());
+}
+
+void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
+    const int N = p.N;
+    const int nl = lines_per_cta<float>(N);
+    const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
+    {
+        KTimer t(p, KC_INV_Y);
+        auto k = inv_y_kernel<float>;
+        allow_smem(k, sm);
+        dim3 grid((max_dzb(p, 0, p.nbins) + nl - 1) / nl, nx, p.nbins);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_A, p.d_geom, 0, N, x0, p.d_G, 0, nl, p.fN, p.d_tw);
+        FBS_CUDA(cudaGetLastError());
+    }
+    {
+        KTimer t(p, KC_INV_Z);
+        auto k = inv_z_kernel<float, false>;
+        allow_smem(k, sm);
+        dim3 grid((N + 2 * nl - 1) / (2 * nl), nx, p.nbins);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_G, p.d_geom, 0, N, islab, (long long)p.slab * N * N,
+                                            p.d_sumsq, nl, p.fN, p.d_tw);
+        FBS_CUDA(cudaGetLastError());
+    }
+}
+
+// Count fields of bins [bin0, bin0+nb) in FP64, octant only, into noct
+// ([bin - bin0][x][y][z], side H = N/2+1).  Uses scratch A64/G64 sized for
+// the group (allocated by the caller through the plan, freed after).
+void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
+                                   double2 *G64, const BinGeom *d_geom_grp) {
+    const int N = p.N;
+    const int H = N / 2 + 1;
+    const int nl = lines_per_cta<double>(N);
+    const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(double2);
+    {
+        KTimer t(p, KC_COUNT);
+        auto k = inv_x_kernel<double, true>;
+        allow_smem(k, sm);
+        dim3 grid(max_inv_x_grid(p, bin0, nb, nl), nb);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.box, d_geom_grp, 0, A64, nl, p.fN, p.d_tw64);
+        FBS_CUDA(cudaGetLastError());
+    }
+    {
+        KTimer t(p, KC_COUNT);
+        auto k = inv_y_kernel<double>;
+        allow_smem(k, sm);
+        dim3 grid((max_dzb(p, bin0, nb) + nl - 1) / nl, H, nb);
+        k<<<grid, kThreads, sm, p.stream>>>(A64, d_geom_grp, 0, N, 0, G64, 0, nl, p.fN, p.d_tw64);
+        FBS_CUDA(cudaGetLastError());
+    }
+    {
+        KTimer t(p, KC_COUNT);
+        auto k = inv_z_kernel<double, true>;
+        allow_smem(k, sm);
+        dim3 grid((H + 2 * nl - 1) / (2 * nl), H, nb);
+        k<<<grid, kThreads, sm, p.stream>>>(G64, d_geom_grp, 0, N, noct, (long long)H * H * H,
+                                            nullptr, nl, p.fN, p.d_tw64);
+        FBS_CUDA(cudaGetLastError());
+    }
+}
+
+}  // namespace fbs

@@ -1,0 +1,779 @@
+// Plan construction, drivers and the C ABI of include/fbs.h.
+//
+// Plan time (once per (N, L, edges)):
+//   * integer thresholds on |m|^2 from the physical edges (the scalar reading
+//     of the bin-width rule of Eq. gen_Nspec3);
+//   * shell sizes |S_b| and the extreme |m|^2 of each shell, by enumerating
+//     the lattice;
+//   * candidate bin triples (and quadruples) that can close a polygon;
+//   * the count fields N_b of Eq. delta_nr in FP64 on the device, and the
+//     exact ordered counts N_tri = sum_n N_a N_b N_c / N_pix (the denominator
+//     of Eq. gen_Nspec3), rounded to int64 and checked for integrality;
+//   * the closed-triplet list and its pair-grouped work list.
+// Per field: forward FFT -> inverse per shell -> real-space product sums ->
+// FP64 normalisation (Eqs. Jeong_PS, Jeong_BI, Jeong_gen).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "fbs_internal.h"
+
+namespace fbs {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    cudaGetLastError();  // clear a sticky-free error so later calls can proceed
+    fbs_status st = (e == cudaErrorMemoryAllocation) ? FBS_ERR_OOM : FBS_ERR_CUDA;
+    throw Failure{st, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+FftFactors make_factors(int n) {
+    FftFactors f{};
+    f.n = n;
+    int m = n, a = 0, b = 0;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    while (m % 3 == 0) { m /= 3; ++b; }
+    if (m != 1 || n > 4096) throw Failure{FBS_ERR_UNSUPPORTED_N, "length is not 2^a 3^b"};
+    int k = 0;
+    for (int i = 0; i < a / 3; ++i) f.r[k++] = 8;
+    if (a % 3 == 1) f.r[k++] = 2;
+    if (a % 3 == 2) f.r[k++] = 4;
+    for (int i = 0; i < b; ++i) f.r[k++] = 3;
+    f.nst = k;
+    return f;
+}
+
+void *Plan::dalloc(size_t bytes) {
+    void *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Failure{e == cudaErrorMemoryAllocation ? FBS_ERR_OOM : FBS_ERR_CUDA,
+                      "cudaMalloc(" + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e)};
+    }
+    allocs.push_back(ptr);
+    dev_bytes += (long long)bytes;
+    return ptr;
+}
+
+// ---------------------------------------------------------------- timing
+static constexpr size_t kMaxPending = 2048;
+
+void Plan::tic(int cls, int &slot) {
+    slot = -1;
+    if (!(flags & FBS_FLAG_TIMING)) return;
+    if (pending.size() >= kMaxPending) flush_times();
+    const int idx = (int)pending.size();
+    while (evs.size() < 2 * (size_t)(idx + 1)) {
+        cudaEvent_t e;
+        FBS_CUDA(cudaEventCreate(&e));
+        evs.push_back(e);
+    }
+    FBS_CUDA(cudaEventRecord(evs[2 * idx], stream));
+    pending.push_back({cls, idx});
+    slot = idx;
+}
+
+void Plan::toc(int slot) {
+    if (slot < 0) return;
+    cudaEventRecord(evs[2 * slot + 1], stream);
+}
+
+void Plan::flush_times() {
+    if (pending.empty()) return;
+    cudaStreamSynchronize(stream);
+    for (auto &pr : pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, evs[2 * pr.second], evs[2 * pr.second + 1]) == cudaSuccess) {
+            kt_ms[pr.first] += ms;
+            kt_n[pr.first] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    pending.clear();
+}
+
+// ---------------------------------------------------------------- plan helpers
+// Smallest integer |m|^2 with |m| k_f >= edge: ceil((edge/k_f)^2), after
+// snapping values within 1e-9 (relative) of an integer onto it so that edges
+// at whole multiples of k_f land where they were meant to.
+static long long edge_threshold(double edge, double L) {
+    if (edge <= 0.0) return 0;
+    const double kf = 2.0 * M_PI / L;
+    const double q = edge / kf;
+    double s = q * q;
+    double r = nearbyint(s);
+    if (fabs(s - r) <= 1e-9 * fmax(1.0, s)) s = r;
+    return (long long)ceil(s);
+}
+
+static bool good_N(int N) {
+    if (N < 8 || N > 512 || (N & 1)) return false;
+    int m = N;
+    while (m % 2 == 0) m /= 2;
+    while (m % 3 == 0) m /= 3;
+    return m == 1;
+}
+
+static int isqrt_floor(long long v) {
+    if (v <= 0) return 0;
+    long long r = (long long)sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return (int)r;
+}
+
+template <typename T>
+static T *upload(Plan &p, const std::vector<T> &v) {
+    T *d = (T *)p.dalloc(std::max<size_t>(1, v.size()) * sizeof(T));
+    if (!v.empty())
+        FBS_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, p.stream));
+    return d;
+}
+
+static bool is_device_ptr(const void *ptr) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Shells: sizes and min/max |m|^2 by lattice enumeration over |m_j| <= Rmax
+// with components in [-N/2, N/2).
+static void enumerate_shells(Plan &p, std::vector<long long> &mn, std::vector<long long> &mx) {
+    const int N = p.N, nb = p.nbins;
+    const long long top = p.thr[nb];
+    int Rmax = std::min(isqrt_floor(top - 1), N / 2);
+    p.shell.assign(nb, 0);
+    mn.assign(nb, -1);
+    mx.assign(nb, -1);
+    std::vector<int> lut;  // bin of each |m|^2 < top
+    lut.assign((size_t)std::max<long long>(top, 1), -1);
+    for (int b = 0; b < nb; ++b)
+        for (long long s = p.thr[b]; s < p.thr[b + 1]; ++s) lut[s] = b;
+    const int lo = -Rmax, hi = std::min(Rmax, N / 2 - 1);
+    for (int x = lo; x <= hi; ++x)
+        for (int y = lo; y <= hi; ++y) {
+            long long r2 = (long long)x * x + (long long)y * y;
+            if (r2 >= top) continue;
+            for (int z = lo; z <= hi; ++z) {
+                long long s = r2 + (long long)z * z;
+                if (s >= top) continue;
+                int b = lut[s];
+                if (b < 0) continue;
+                p.shell[b] += 1;
+                if (mn[b] < 0 || s < mn[b]) mn[b] = s;
+                if (s > mx[b]) mx[b] = s;
+            }
+        }
+}
+
+static void build_geometry(Plan &p) {
+    const int N = p.N;
+    p.geom.assign(p.nbins, BinGeom{});
+    int R = 0;
+    long long aoff = 0;
+    for (int b = 0; b < p.nbins; ++b) {
+        BinGeom &g = p.geom[b];
+        g.thr_lo = p.thr[b];
+        g.thr_hi = p.thr[b + 1];
+        g.empty = p.shell[b] == 0;
+        if (g.empty) {
+            g.Rb = 0;
+            g.Db = 1;
+            g.Dzb = 1;
+            g.A_off = aoff;
+            continue;
+        }
+        g.Rb = std::min(isqrt_floor(g.thr_hi - 1), N / 2);
+        g.Db = (2 * g.Rb + 1 > N) ? N : 2 * g.Rb + 1;
+        g.Dzb = std::min(g.Rb, N / 2) + 1;
+        g.A_off = aoff;
+        aoff += (long long)N * g.Db * g.Dzb;
+        R = std::max(R, g.Rb);
+    }
+    p.A_elems = aoff;
+    p.box.N = N;
+    p.box.R = R;
+    p.box.D = (2 * R + 1 > N) ? N : 2 * R + 1;
+    p.box.Dz = std::min(R, N / 2) + 1;
+    long long gplane = 0;
+    for (int b = 0; b < p.nbins; ++b)
+        if (!p.geom[b].empty) gplane += (long long)N * p.geom[b].Dzb;
+    p.G_plane = gplane;
+}
+
+static void set_slab_offsets(Plan &p) {
+    long long goff = 0;
+    for (int b = 0; b < p.nbins; ++b) {
+        p.geom[b].G_off = goff;
+        if (!p.geom[b].empty) goff += (long long)p.slab * p.N * p.geom[b].Dzb;
+    }
+}
+
+// Candidate bin triples (a <= b <= c over non-empty bins).  Unless aliased
+// closure is allowed, every component is below N/4, so closure modulo N is
+// exact closure and needs |m_c| <= |m_a| + |m_b|: keep the triple when the
+// smallest |m| of c does not exceed the largest |m| of a plus that of b.
+static void candidates(const Plan &p, const std::vector<long long> &mn,
+                       const std::vector<long long> &mx, int arity, std::vector<int> &items) {
+    const int nb = p.nbins;
+    const bool all = (p.flags & FBS_FLAG_ALLOW_ALIASED) != 0;
+    items.clear();
+    auto hi = [&](int b) { return sqrt((double)mx[b]); };
+    auto lo = [&](int b) { return sqrt((double)mn[b]); };
+    for (int a = 0; a < nb; ++a) {
+        if (!p.shell[a]) continue;
+        for (int b = a; b < nb; ++b) {
+            if (!p.shell[b]) continue;
+            for (int c = b; c < nb; ++c) {
+                if (!p.shell[c]) continue;
+                if (arity == 3) {
+                    if (all || lo(c) <= hi(a) + hi(b) + 1e-9) {
+                        items.push_back(a);
+                        items.push_back(b);
+                        items.push_back(c);
+                    }
+                } else {
+                    for (int d = c; d < nb; ++d) {
+                        if (!p.shell[d]) continue;
+                        if (all || lo(d) <= hi(a) + hi(b) + hi(c) + 1e-9) {
+                            items.push_back(a);
+                            items.push_back(b);
+                            items.push_back(c);
+                            items.push_back(d);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// FP64 count fields on the octant, then the count sums of all candidates.
+static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<int> &qc,
+                         std::vector<double> &tden, std::vector<double> &qden) {
+    const int N = p.N, H = N / 2 + 1;
+    const long long H3 = (long long)H * H * H;
+    const int nb = p.nbins;
+    double *noct = nullptr;
+    if (cudaMallocAsync((void **)&noct, (size_t)nb * H3 * sizeof(double), p.stream) != cudaSuccess) {
+        cudaGetLastError();
+        throw Failure{FBS_ERR_OOM, "count fields: device allocation failed"};
+    }
+    // bin groups bounded by ~2 GB of FP64 scratch
+    const long long budget = 2LL << 30;
+    int b0 = 0;
+    while (b0 < nb) {
+        long long a_el = 0, g_el = 0;
+        int b1 = b0;
+        std::vector<BinGeom> gg;
+        while (b1 < nb) {
+            const BinGeom &g = p.geom[b1];
+            long long da = g.empty ? 0 : (long long)N * g.Db * g.Dzb;
+            long long dg = g.empty ? 0 : (long long)H * N * g.Dzb;
+            if (b1 > b0 && (a_el + da + g_el + dg) * 16 > budget) break;
+            BinGeom q = g;
+            q.A_off = a_el;
+            q.G_off = g_el;
+            gg.push_back(q);
+            a_el += da;
+            g_el += dg;
+            ++b1;
+        }
+        double2 *A64 = nullptr, *G64 = nullptr;
+        BinGeom *dgeom = nullptr;
+        if (cudaMallocAsync((void **)&A64, std::max<long long>(1, a_el) * 16, p.stream) != cudaSuccess ||
+            cudaMallocAsync((void **)&G64, std::max<long long>(1, g_el) * 16, p.stream) != cudaSuccess ||
+            cudaMallocAsync((void **)&dgeom, gg.size() * sizeof(BinGeom), p.stream) != cudaSuccess) {
+            cudaGetLastError();
+            throw Failure{FBS_ERR_OOM, "count scratch: device allocation failed"};
+        }
+        FBS_CUDA(cudaMemcpyAsync(dgeom, gg.data(), gg.size() * sizeof(BinGeom), cudaMemcpyHostToDevice,
+                                 p.stream));
+        launch_count_fields_fp64_impl(p, noct + (long long)b0 * H3, b0, b1 - b0, A64, G64, dgeom);
+        FBS_CUDA(cudaFreeAsync(A64, p.stream));
+        FBS_CUDA(cudaFreeAsync(G64, p.stream));
+        FBS_CUDA(cudaFreeAsync(dgeom, p.stream));
+        FBS_CUDA(cudaStreamSynchronize(p.stream));  // gg goes out of scope
+        b0 = b1;
+    }
+    auto run = [&](const std::vector<int> &items, int arity, std::vector<double> &den) {
+        int n = (int)(items.size() / arity);
+        den.assign(n, 0.0);
+        if (n == 0) return;
+        int *d_items = nullptr;
+        double *d_den = nullptr;
+        if (cudaMallocAsync((void **)&d_items, items.size() * sizeof(int), p.stream) != cudaSuccess ||
+            cudaMallocAsync((void **)&d_den, n * sizeof(double), p.stream) != cudaSuccess) {
+            cudaGetLastError();
+            throw Failure{FBS_ERR_OOM, "count items: device allocation failed"};
+        }
+        FBS_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice, p.stream));
+        launch_count_contraction(p, noct, nb, 0, d_items, n, arity, d_den);
+        FBS_CUDA(cudaMemcpyAsync(den.data(), d_den, n * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+        FBS_CUDA(cudaStreamSynchronize(p.stream));
+        FBS_CUDA(cudaFreeAsync(d_items, p.stream));
+        FBS_CUDA(cudaFreeAsync(d_den, p.stream));
+    };
+    run(tc, 3, tden);
+    run(qc, 4, qden);
+    FBS_CUDA(cudaFreeAsync(noct, p.stream));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));
+}
+
+static int64_t round_count(double den, double npix) {
+    double v = den / npix;
+    double r = nearbyint(v);
+    if (fabs(v - r) > 1e-2)
+        throw Failure{FBS_ERR_NUMERIC, "count sum " + std::to_string(v) + " is not an integer"};
+    return (int64_t)r;
+}
+
+static void build_tasks(Plan &p) {
+    // bispectrum: outer pair (b, c), inner a; items sorted by (b, c, a)
+    {
+        const int nt = (int)p.ntri.size();
+        std::vector<int> ord(nt);
+        for (int i = 0; i < nt; ++i) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](int u, int v) {
+            const int32_t *x = &p.trip[3 * u], *y = &p.trip[3 * v];
+            if (x[1] != y[1]) return x[1] < y[1];
+            if (x[2] != y[2]) return x[2] < y[2];
+            return x[0] < y[0];
+        });
+        TaskList &t = p.ttask;
+        t = TaskList{};
+        int lb = -1, lc = -1;
+        for (int i : ord) {
+            const int32_t *x = &p.trip[3 * i];
+            if (x[1] != lb || x[2] != lc) {
+                t.pb.push_back(x[1]);
+                t.pc.push_back(x[2]);
+                t.pstart.push_back((int)t.ia.size());
+                lb = x[1];
+                lc = x[2];
+            }
+            t.ia.push_back(x[0]);
+            t.ib.push_back(-1);
+            t.iout.push_back(i);
+        }
+        t.npairs = (int)t.pb.size();
+        t.nitems = (int)t.ia.size();
+        t.pstart.push_back(t.nitems);
+    }
+    // trispectrum: outer pair (c, d), inner (a, b)
+    {
+        const int nq = (int)p.nquad.size();
+        std::vector<int> ord(nq);
+        for (int i = 0; i < nq; ++i) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](int u, int v) {
+            const int32_t *x = &p.quad[4 * u], *y = &p.quad[4 * v];
+            if (x[2] != y[2]) return x[2] < y[2];
+            if (x[3] != y[3]) return x[3] < y[3];
+            if (x[0] != y[0]) return x[0] < y[0];
+            return x[1] < y[1];
+        });
+        TaskList &t = p.qtask;
+        t = TaskList{};
+        int lc = -1, ld = -1;
+        for (int i : ord) {
+            const int32_t *x = &p.quad[4 * i];
+            if (x[2] != lc || x[3] != ld) {
+                t.pb.push_back(x[2]);
+                t.pc.push_back(x[3]);
+                t.pstart.push_back((int)t.ia.size());
+                lc = x[2];
+                ld = x[3];
+            }
+            t.ia.push_back(x[0]);
+            t.ib.push_back(x[1]);
+            t.iout.push_back(i);
+        }
+        t.npairs = (int)t.pb.size();
+        t.nitems = (int)t.ia.size();
+        t.pstart.push_back(t.nitems);
+    }
+}
+
+static long long slab_budget_bytes() {
+    const char *e = getenv("FBS_SLAB_MB");
+    if (e && atoll(e) > 0) return atoll(e) << 20;
+    return 8LL << 30;
+}
+
+static void create_plan(Plan &p, const double *edges) {
+    const int N = p.N, nb = p.nbins;
+    p.fN = make_factors(N);
+    p.thr.resize(nb + 1);
+    for (int i = 0; i <= nb; ++i) p.thr[i] = edge_threshold(edges[i], p.L);
+    for (int i = 0; i < nb; ++i)
+        if (p.thr[i + 1] < p.thr[i]) throw Failure{FBS_ERR_ARG, "edges must be ascending"};
+    if (!(p.flags & FBS_FLAG_ALLOW_ALIASED)) {
+        // top edge <= N k_f / 4  <=>  thr[nb] <= (N/4)^2 (closure modulo N is exact closure)
+        // ceil(N^2/16): |m|^2 < thr[nb] <= ceil(N^2/16) keeps every |m_j| < N/4
+        const long long lim = ((long long)N * N + 15) / 16;
+        if (p.thr[nb] > lim)
+            throw Failure{FBS_ERR_ARG, "top edge beyond N k_f/4 (pass FBS_FLAG_ALLOW_ALIASED to allow)"};
+    }
+    std::vector<long long> mn, mx;
+    enumerate_shells(p, mn, mx);
+    build_geometry(p);
+
+    // device geometry + twiddles (needed by the count path)
+    upload_twiddles(p);
+    p.d_box = (float2 *)p.dalloc((size_t)p.box.D * p.box.D * p.box.Dz * sizeof(float2));
+    FBS_CUDA(cudaMemsetAsync(p.d_box, 0, (size_t)p.box.D * p.box.D * p.box.Dz * sizeof(float2), p.stream));
+
+    // candidates and exact counts
+    std::vector<int> tc, qc;
+    candidates(p, mn, mx, 3, tc);
+    if (p.flags & FBS_FLAG_TRISPECTRUM) candidates(p, mn, mx, 4, qc);
+    std::vector<double> tden, qden;
+    const double npix = (double)N * N * N;
+    exact_counts(p, tc, qc, tden, qden);
+    p.trip.clear();
+    p.ntri.clear();
+    for (size_t i = 0; i < tden.size(); ++i) {
+        int64_t c = round_count(tden[i], npix);
+        if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative triangle count"};
+        if (c == 0) continue;
+        p.trip.insert(p.trip.end(), {tc[3 * i], tc[3 * i + 1], tc[3 * i + 2]});
+        p.ntri.push_back(c);
+    }
+    p.quad.clear();
+    p.nquad.clear();
+    for (size_t i = 0; i < qden.size(); ++i) {
+        int64_t c = round_count(qden[i], npix);
+        if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative quadruple count"};
+        if (c == 0) continue;
+        p.quad.insert(p.quad.end(), {qc[4 * i], qc[4 * i + 1], qc[4 * i + 2], qc[4 * i + 3]});
+        p.nquad.push_back(c);
+    }
+    build_tasks(p);
+    p.tgrp = item_groups(p.ttask, 8192);
+    p.qgrp = item_groups(p.qtask, 8192);
+
+    // slab size: shell fields + y-stage scratch of one slab within the budget
+    const long long per_plane = (long long)nb * N * N * 4 + p.G_plane * 8;
+    long long budget = slab_budget_bytes();
+    int slab = (int)std::max<long long>(1, std::min<long long>(N, budget / std::max<long long>(1, per_plane)));
+    int nslabs = (N + slab - 1) / slab;
+    slab = (N + nslabs - 1) / nslabs;  // balance the slabs
+    p.slab = slab;
+    p.nslabs = nslabs;
+    set_slab_offsets(p);
+
+    // per-field buffers
+    p.d_geom = upload(p, p.geom);
+    p.d_field = (float *)p.dalloc((size_t)N * N * N * sizeof(float));
+    p.d_zbuf = (float2 *)p.dalloc((size_t)N * N * p.box.Dz * sizeof(float2));
+    p.d_ybuf = (float2 *)p.dalloc((size_t)N * p.box.D * p.box.Dz * sizeof(float2));
+    p.d_A = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.A_elems) * sizeof(float2));
+    p.d_G = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.G_plane * p.slab) * sizeof(float2));
+    p.d_I = (float *)p.dalloc((size_t)nb * p.slab * N * N * sizeof(float));
+    // work lists
+    p.d_tpb = upload(p, p.ttask.pb);
+    p.d_tpc = upload(p, p.ttask.pc);
+    p.d_tps = upload(p, p.ttask.pstart);
+    p.d_tia = upload(p, p.ttask.ia);
+    p.d_tout = upload(p, p.ttask.iout);
+    p.d_tgrp = upload(p, p.tgrp);
+    p.d_qpb = upload(p, p.qtask.pb);
+    p.d_qpc = upload(p, p.qtask.pc);
+    p.d_qps = upload(p, p.qtask.pstart);
+    p.d_qia = upload(p, p.qtask.ia);
+    p.d_qib = upload(p, p.qtask.ib);
+    p.d_qout = upload(p, p.qtask.iout);
+    p.d_qgrp = upload(p, p.qgrp);
+    // accumulators and outputs
+    const int ntrip = (int)p.ntri.size(), nquad = (int)p.nquad.size();
+    p.part_blocks = contract_blocks();
+    p.d_tpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, ntrip) * sizeof(double));
+    p.d_qpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, nquad) * sizeof(double));
+    p.d_sumsq = (double *)p.dalloc(nb * sizeof(double));
+    p.d_tnum = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
+    p.d_qnum = (double *)p.dalloc(std::max(1, nquad) * sizeof(double));
+    p.d_B = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
+    p.d_T = (double *)p.dalloc(std::max(1, nquad) * sizeof(double));
+    p.d_P = (double *)p.dalloc(nb * sizeof(double));
+    p.d_ntri = upload(p, p.ntri);
+    p.d_nquad = upload(p, p.nquad);
+    p.d_shell = upload(p, p.shell);
+    FBS_CUDA(cudaStreamSynchronize(p.stream));
+}
+
+static void run_field(Plan &p, const float *field, bool quads) {
+    const int N = p.N;
+    const float *d_in = field;
+    if (!is_device_ptr(field)) {
+        FBS_CUDA(cudaMemcpyAsync(p.d_field, field, (size_t)N * N * N * sizeof(float), cudaMemcpyDefault,
+                                 p.stream));
+        d_in = p.d_field;
+    }
+    zero_partials(p, quads);
+    launch_forward(p, d_in);
+    launch_inverse_x(p, false);
+    const long long plane = (long long)N * N;
+    for (int s = 0; s < p.nslabs; ++s) {
+        const int x0 = s * p.slab;
+        const int nx = std::min(p.slab, N - x0);
+        if (nx <= 0) break;
+        launch_inverse_yz_slab(p, x0, nx, p.d_I);
+        const long long npts = (long long)nx * plane;
+        const long long stride = (long long)p.slab * plane;
+        if (p.precision == FBS_PREC_FP32)
+            launch_contract_fp32(p, p.d_I, npts, stride, false);
+        else
+            launch_contract_tc(p, p.d_I, npts, stride);
+        if (quads) launch_contract_fp32(p, p.d_I, npts, stride, true);
+    }
+    launch_reduce_and_normalise(p, quads);
+}
+
+static void copy_out(Plan &p, double *dst, const double *src, size_t n, bool &host) {
+    if (!dst || n == 0) return;
+    if (!is_device_ptr(dst)) host = true;
+    FBS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, p.stream));
+}
+
+}  // namespace fbs
+
+using namespace fbs;
+
+struct fbs_plan : public fbs::Plan {};
+
+#define FBS_GUARD_BEGIN try {
+#define FBS_GUARD_END                                  \
+    }                                                  \
+    catch (const Failure &f) {                         \
+        set_error(f.msg);                              \
+        return f.status;                               \
+    }                                                  \
+    catch (const std::exception &e) {                  \
+        set_error(std::string("internal: ") + e.what()); \
+        return FBS_ERR_ARG;                            \
+    }
+
+extern "C" {
+
+int fbs_version(void) { return 100; }
+
+const char *fbs_last_error(void) { return g_last_error.c_str(); }
+
+static const char *kClassNames[KC_NUM] = {"fwd_z",   "fwd_y",       "fwd_x", "inv_x",
+                                          "inv_y",   "inv_z",       "contract_fp32",
+                                          "contract_tc", "contract_quad", "reduce", "count"};
+
+int fbs_num_kernel_classes(void) { return KC_NUM; }
+
+const char *fbs_kernel_class_name(int i) { return (i >= 0 && i < KC_NUM) ? kClassNames[i] : ""; }
+
+fbs_status fbs_plan_create(fbs_plan **out, int N, double L, const double *edges, int nbins,
+                           int precision, unsigned flags, void *cuda_stream) {
+    if (!out) {
+        set_error("out is NULL");
+        return FBS_ERR_ARG;
+    }
+    *out = nullptr;
+    if (!edges || nbins < 1 || nbins > 128 || !(L > 0.0) || !isfinite(L)) {
+        set_error("bad edges/nbins/L");
+        return FBS_ERR_ARG;
+    }
+    if (precision < FBS_PREC_FP32 || precision > FBS_PREC_BF16) {
+        set_error("unknown precision");
+        return FBS_ERR_ARG;
+    }
+    for (int i = 0; i <= nbins; ++i)
+        if (!isfinite(edges[i]) || edges[i] < 0.0 || (i > 0 && edges[i] < edges[i - 1])) {
+            set_error("edges must be finite, non-negative and ascending");
+            return FBS_ERR_ARG;
+        }
+    if (!good_N(N)) {
+        set_error("N must be even, of the form 2^a 3^b, and in [8, 512]");
+        return FBS_ERR_UNSUPPORTED_N;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device");
+        return FBS_ERR_CUDA;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    fbs_plan *p = new fbs_plan();
+    p->N = N;
+    p->L = L;
+    p->nbins = nbins;
+    p->precision = precision;
+    p->flags = flags;
+    p->stream = (cudaStream_t)cuda_stream;
+    try {
+        create_plan(*p, edges);
+    } catch (const Failure &f) {
+        set_error(f.msg);
+        fbs_plan_free(p);
+        return f.status;
+    } catch (const std::exception &e) {
+        set_error(std::string("internal: ") + e.what());
+        fbs_plan_free(p);
+        return FBS_ERR_ARG;
+    }
+    p->kt_ms[KC_COUNT] = 0;
+    p->kt_n[KC_COUNT] = 0;
+    p->pending.clear();
+    p->create_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return FBS_OK;
+}
+
+void fbs_plan_free(fbs_plan *plan) {
+    if (!plan) return;
+    cudaStreamSynchronize(plan->stream);
+    cudaGetLastError();
+    free_tc_state(*plan);
+    for (void *ptr : plan->allocs) cudaFree(ptr);
+    for (cudaEvent_t e : plan->evs) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete plan;
+}
+
+int fbs_plan_num_triplets(const fbs_plan *plan) {
+    if (!plan) return FBS_ERR_ARG;
+    return (int)plan->ntri.size();
+}
+
+int fbs_plan_num_quads(const fbs_plan *plan) {
+    if (!plan) return FBS_ERR_ARG;
+    return (int)plan->nquad.size();
+}
+
+fbs_status fbs_plan_triplets(const fbs_plan *plan, int32_t *abc, int64_t *ntri) {
+    if (!plan) return FBS_ERR_ARG;
+    if (abc && !plan->trip.empty()) memcpy(abc, plan->trip.data(), plan->trip.size() * sizeof(int32_t));
+    if (ntri && !plan->ntri.empty()) memcpy(ntri, plan->ntri.data(), plan->ntri.size() * sizeof(int64_t));
+    return FBS_OK;
+}
+
+fbs_status fbs_plan_quads(const fbs_plan *plan, int32_t *abcd, int64_t *nq) {
+    if (!plan) return FBS_ERR_ARG;
+    if (abcd && !plan->quad.empty()) memcpy(abcd, plan->quad.data(), plan->quad.size() * sizeof(int32_t));
+    if (nq && !plan->nquad.empty()) memcpy(nq, plan->nquad.data(), plan->nquad.size() * sizeof(int64_t));
+    return FBS_OK;
+}
+
+fbs_status fbs_plan_shells(const fbs_plan *plan, int64_t *sizes, int64_t *thr) {
+    if (!plan) return FBS_ERR_ARG;
+    for (int b = 0; b < plan->nbins && sizes; ++b) sizes[b] = plan->shell[b];
+    for (int b = 0; b <= plan->nbins && thr; ++b) thr[b] = plan->thr[b];
+    return FBS_OK;
+}
+
+fbs_status fbs_plan_set_precision(fbs_plan *plan, int precision) {
+    if (!plan || precision < FBS_PREC_FP32 || precision > FBS_PREC_BF16) {
+        set_error("bad plan or precision");
+        return FBS_ERR_ARG;
+    }
+    plan->precision = precision;
+    return FBS_OK;
+}
+
+fbs_status fbs_plan_set_stream(fbs_plan *plan, void *stream) {
+    if (!plan) return FBS_ERR_ARG;
+    FBS_GUARD_BEGIN
+    plan->flush_times();
+    FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    plan->stream = (cudaStream_t)stream;
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double *P) {
+    if (!plan || !field) {
+        set_error("plan or field is NULL");
+        return FBS_ERR_ARG;
+    }
+    FBS_GUARD_BEGIN
+    run_field(*plan, field, false);
+    bool host = false;
+    copy_out(*plan, B, plan->d_B, plan->ntri.size(), host);
+    copy_out(*plan, P, plan->d_P, plan->nbins, host);
+    if (host) FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double *B, double *P) {
+    if (!plan || !field) {
+        set_error("plan or field is NULL");
+        return FBS_ERR_ARG;
+    }
+    if (!(plan->flags & FBS_FLAG_TRISPECTRUM)) {
+        set_error("plan was created without FBS_FLAG_TRISPECTRUM");
+        return FBS_ERR_STATE;
+    }
+    FBS_GUARD_BEGIN
+    run_field(*plan, field, true);
+    bool host = false;
+    copy_out(*plan, T, plan->d_T, plan->nquad.size(), host);
+    copy_out(*plan, B, plan->d_B, plan->ntri.size(), host);
+    copy_out(*plan, P, plan->d_P, plan->nbins, host);
+    if (host) FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_plan_sums(fbs_plan *plan, double *num_trip, double *num_quad, double *sumsq) {
+    if (!plan) return FBS_ERR_ARG;
+    FBS_GUARD_BEGIN
+    if (num_trip && !plan->ntri.empty())
+        FBS_CUDA(cudaMemcpyAsync(num_trip, plan->d_tnum, plan->ntri.size() * sizeof(double),
+                                 cudaMemcpyDefault, plan->stream));
+    if (num_quad && !plan->nquad.empty())
+        FBS_CUDA(cudaMemcpyAsync(num_quad, plan->d_qnum, plan->nquad.size() * sizeof(double),
+                                 cudaMemcpyDefault, plan->stream));
+    if (sumsq)
+        FBS_CUDA(cudaMemcpyAsync(sumsq, plan->d_sumsq, plan->nbins * sizeof(double), cudaMemcpyDefault,
+                                 plan->stream));
+    FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, int reset) {
+    if (!plan) return FBS_ERR_ARG;
+    FBS_GUARD_BEGIN
+    plan->flush_times();
+    for (int i = 0; i < KC_NUM; ++i) {
+        if (ms) ms[i] = plan->kt_ms[i];
+        if (launches) launches[i] = plan->kt_n[i];
+        if (reset) {
+            plan->kt_ms[i] = 0;
+            plan->kt_n[i] = 0;
+        }
+    }
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+double fbs_plan_create_ms(const fbs_plan *plan) { return plan ? plan->create_ms : -1.0; }
+
+int64_t fbs_plan_device_bytes(const fbs_plan *plan) { return plan ? plan->dev_bytes : -1; }
+
+}  // extern "C"

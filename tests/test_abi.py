@@ -1,0 +1,78 @@
+"""The C ABI library builds, loads and exports every entry point of
+include/fbs.h; host-side argument checks work without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1705_06284_gb300 as fbs
+from paper_1705_06284_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "fbs.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fbs_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libfbs():
+    _build.build()
+    return fbs.lib()
+
+
+def test_every_declared_symbol_is_exported(libfbs):
+    names = _declared()
+    assert "fbs_bispectrum" in names and "fbs_plan_create" in names
+    for n in names:
+        assert hasattr(libfbs, n), n
+    # and the binding knows all of them (same names, argument marshalling only)
+    bound = {s[0] for s in fbs._SIGS}
+    assert set(names) == bound
+
+
+def test_version_and_errors(libfbs):
+    assert libfbs.fbs_version() == 100
+    assert isinstance(libfbs.fbs_last_error(), bytes)
+    assert len(fbs.kernel_class_names()) == libfbs.fbs_num_kernel_classes()
+
+
+@pytest.mark.parametrize("N", [7, 10, 20, 1024, 4, 15])
+def test_unsupported_N_rejected_on_host(libfbs, N):
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.fbs_plan_create(N, 100.0, [0.1, 0.2])
+    assert e.value.status == -2
+
+
+def test_bad_edges_rejected_on_host(libfbs):
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.fbs_plan_create(32, 100.0, [0.3, 0.2])
+    assert e.value.status == -1
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.fbs_plan_create(32, -1.0, [0.1, 0.2])
+    assert e.value.status == -1
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.fbs_plan_create(32, 100.0, [0.1, float("nan")])
+    assert e.value.status == -1
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.fbs_plan_create(32, 100.0, [0.1, 0.2], precision=7)
+    assert e.value.status == -1
+
+
+def test_null_arguments(libfbs):
+    assert libfbs.fbs_bispectrum(None, None, None, None) == -1
+    assert libfbs.fbs_plan_num_triplets(None) == -1
+    libfbs.fbs_plan_free(None)  # no-op
+
+
+def test_no_cpu_fallback_without_device(libfbs):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("device present")
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.fbs_plan_create(16, 100.0, [0.1, 0.5, 1.0])
+    assert e.value.status == -4

@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path through the C ABI versus the FP64 oracle.
+
+Counts are compared bit-exactly; B, P and T within the tolerances of the
+precision mode (FP32: 1e-4 relative on triplets with N_tri >= 100 and a
+non-negligible |B|; see tests/gpu_util.py)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import fields
+import oracle
+import paper_1705_06284_gb300 as fbs
+from gpu_util import check_bispectrum, gate_mask, rel_err, run
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _golden():
+    meta, rows = {}, []
+    for line in open(os.path.join(HERE, "golden", "lognormal32_lin6.txt")):
+        if line.startswith("# ") and line.split()[1] in ("edges", "P", "shell"):
+            meta[line.split()[1]] = [float(v) for v in line.split()[2:]]
+        elif not line.startswith("#"):
+            rows.append(line.split())
+    trip = np.array([[int(r[0]), int(r[1]), int(r[2])] for r in rows], dtype=np.int32)
+    ntri = np.array([int(r[3]) for r in rows], dtype=np.int64)
+    B = np.array([float(r[4]) for r in rows])
+    M = np.array([float(r[5]) for r in rows])
+    return meta, trip, ntri, B, M
+
+
+def test_lognormal32_golden_fp32():
+    """The 32^3 lognormal configuration against the stored oracle values."""
+    meta, trip, ntri, Bref, M = _golden()
+    N, L = 32, 100.0
+    f32 = fields.lognormal(N, 0.5, -2.0, seed=0).astype(np.float32)
+    with fbs.Plan(N, L, meta["edges"], precision="fp32") as plan:
+        assert plan.ntrip == 49
+        assert np.array_equal(plan.triplets, trip)
+        assert np.array_equal(plan.N_tri, ntri)
+        assert list(plan.shell) == [int(v) for v in meta["shell"]]
+        B, P = run(plan, f32)
+    g = gate_mask(Bref, M, ntri)
+    assert g.sum() >= 30
+    assert rel_err(B, Bref)[g].max() < 1e-4
+    assert np.all(rel_err(P, np.array(meta["P"])) < 1e-5)
+
+
+CASES = [
+    # (N, L, kind, nbins, field, seed)
+    (8, 10.0, "lin", 2, "lognormal", 1),
+    (12, 30.0, "lin", 3, "bubbles", 2),
+    (16, 50.0, "log", 5, "lognormal", 3),
+    (24, 80.0, "lin", 5, "quadratic", 4),      # radix 3
+    (32, 100.0, "log", 8, "bubbles", 5),
+    (48, 60.0, "lin", 6, "lognormal", 6),      # radix 3, several tiles
+    (64, 200.0, "lin", 8, "quadratic", 7),
+    (72, 72.0, "lin", 4, "lognormal", 8),      # 2^3 3^2
+]
+
+
+def _field(kind, N, seed):
+    if kind == "lognormal":
+        return fields.lognormal(N, 0.6, -1.5, seed=seed)
+    if kind == "bubbles":
+        return fields.bubbles(N, max(1.5, N / 10), 0.4, seed=seed)
+    return fields.quadratic_local(N, 0.5, -1.5, 0.3, seed=seed)
+
+
+@pytest.mark.parametrize("N,L,kind,nb,fk,seed", CASES)
+def test_fp32_matches_direct_oracle(N, L, kind, nb, fk, seed):
+    edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
+    f32 = _field(fk, N, seed).astype(np.float32)
+    with fbs.Plan(N, L, edges, precision="fp32") as plan:
+        B, P = run(plan, f32)
+        gmax, amax, ng = check_bispectrum(plan, B, P, f32, L, edges, "fp32")
+    print("N=%d gated=%d max gated rel %.2e, max rel %.2e" % (N, ng, gmax, amax))
+
+
+def test_small_slabs_and_ragged_chunks(monkeypatch):
+    """Force many thin slabs (slab point counts not multiples of the chunk)."""
+    monkeypatch.setenv("FBS_SLAB_MB", "1")
+    N, L = 24, 50.0
+    edges = fields.linear_edges(N, L, 4)
+    f32 = _field("lognormal", N, 11).astype(np.float32)
+    with fbs.Plan(N, L, edges, precision="fp32") as plan:
+        B, P = run(plan, f32)
+        check_bispectrum(plan, B, P, f32, L, edges, "fp32")
+
+
+def test_host_buffers_match_device_buffers():
+    N, L = 32, 100.0
+    edges = fields.linear_edges(N, L, 6)
+    f32 = _field("bubbles", N, 3).astype(np.float32)
+    with fbs.Plan(N, L, edges) as plan:
+        Bd, Pd = run(plan, f32, device=True)
+        Bh, Ph = run(plan, f32, device=False)
+        assert isinstance(Bh, np.ndarray)
+        assert np.array_equal(Bd, Bh) and np.array_equal(Pd, Ph)
+        # repeated calls are deterministic
+        Bd2, _ = run(plan, f32, device=True)
+        assert np.array_equal(Bd, Bd2)
+
+
+def test_empty_bins_and_nan_power():
+    # log bins on a small grid: the narrow low shells hold no lattice point
+    N, L = 32, 2 * math.pi
+    edges = np.geomspace(1.0, 8.0, 17)
+    f32 = _field("lognormal", N, 1).astype(np.float32)
+    with fbs.Plan(N, L, edges) as plan:
+        assert (plan.shell == 0).sum() >= 3
+        B, P = run(plan, f32)
+        check_bispectrum(plan, B, P, f32, L, edges, "fp32")
+        assert np.all(np.isnan(P[plan.shell == 0]))
+        assert not np.any(np.isin(plan.triplets, np.nonzero(plan.shell == 0)[0]))
+
+
+def test_aliased_full_cover_sum_rules():
+    """Shells covering every mode (closure modulo N): sum N_tri = N_pix^2 and
+    the skewness sum rule (Eq. skew) hold on the GPU path too."""
+    N, L = 12, 30.0
+    kf = 2 * math.pi / L
+    top = 3 * (N // 2) ** 2 + 1
+    edges = [kf * math.sqrt(s) for s in (0.0, 3.5, 10.5, 30.5, top + 0.5)]
+    f32 = _field("lognormal", N, 2).astype(np.float32)
+    with fbs.Plan(N, L, edges, allow_aliased=True) as plan:
+        B, P = run(plan, f32)
+        ref = oracle.direct_bispectrum(f32.astype(np.float64), L, edges)
+        check_bispectrum(plan, B, P, f32, L, edges, "fp32", ref=ref)
+        # ordered-sum rule: every ordered (m1, m2) closes with one m3
+        nb = len(edges) - 1
+        tot = 0
+        for (a, b, c), n in zip(plan.triplets, plan.N_tri):
+            perms = len({(a, b, c), (a, c, b), (b, a, c), (b, c, a), (c, a, b), (c, b, a)})
+            tot += perms * int(n)
+        assert tot == (N ** 3) ** 2
+        V, npix = L ** 3, float(N ** 3)
+        skew = 0.0
+        for (a, b, c), n, Bv in zip(plan.triplets, plan.N_tri, B):
+            perms = len({(a, b, c), (a, c, b), (b, a, c), (b, c, a), (c, a, b), (c, b, a)})
+            skew += perms * n * Bv
+        skew /= V * V
+        f = f32.astype(np.float64)
+        assert abs(skew - np.mean(f ** 3)) <= 1e-4 * np.mean(np.abs(f) ** 3)
+
+
+def test_trispectrum_matches_oracle():
+    N, L = 16, 40.0
+    edges = fields.linear_edges(N, L, 4)
+    f32 = _field("bubbles", N, 9).astype(np.float32)
+    with fbs.Plan(N, L, edges, trispectrum=True) as plan:
+        import torch
+        T, B, P = plan.trispectrum(torch.from_numpy(f32).cuda())
+        torch.cuda.synchronize()
+        T, B, P = T.cpu().numpy(), B.cpu().numpy(), P.cpu().numpy()
+        check_bispectrum(plan, B, P, f32, L, edges, "fp32")
+        g = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=[], quads=plan.quads)
+        assert np.array_equal(plan.N_quad, g["N_quad"])
+        # every candidate with a non-zero count is in the plan
+        nb = len(edges) - 1
+        allq = [(a, b, c, d) for a in range(nb) for b in range(a, nb) for c in range(b, nb)
+                for d in range(c, nb)]
+        ga = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=[], quads=allq)
+        closed = [q for q, n in zip(allq, ga["N_quad"]) if n > 0]
+        assert [tuple(q) for q in plan.quads] == closed
+        r = rel_err(T, g["T"])
+        assert np.all(r[plan.N_quad >= 100] < 1e-4), float(r.max())
+
+
+def test_trispectrum_direct_tiny():
+    N, L = 8, 20.0
+    edges = fields.linear_edges(N, L, 2)
+    f32 = _field("lognormal", N, 4).astype(np.float32)
+    t = oracle.direct_trispectrum(f32.astype(np.float64), L, edges)
+    with fbs.Plan(N, L, edges, trispectrum=True) as plan:
+        T, B, P = plan.trispectrum(f32)
+        assert np.array_equal(plan.quads, t["quads"])
+        assert np.array_equal(plan.N_quad, t["N_quad"])
+        assert np.all(rel_err(T, t["T"]) < 1e-4)
+
+
+def test_plane_waves_closed_form_on_gpu():
+    # B of three plane waves on a closed triangle (closed form in the oracle pins)
+    N, L = 16, 2 * math.pi
+    A, phi = (0.7, -0.4, 1.3), (0.3, -1.1, 2.0)
+    f = fields.plane_waves(N, [((1, 0, 0), A[0], phi[0]), ((0, 2, 0), A[1], phi[1]),
+                               ((-1, -2, 0), A[2], phi[2])])
+    edges = [0.9, 1.1, 1.9, 2.1, 2.2, 2.3]
+    f32 = f.astype(np.float32)
+    with fbs.Plan(N, L, edges, allow_aliased=True) as plan:
+        B, P = run(plan, f32)
+        num, _, _ = plan.sums()
+        i = [k for k, t in enumerate(plan.triplets) if tuple(t) == (0, 2, 4)][0]
+        npix = N ** 3
+        expect = 2 * (npix / 2) ** 3 * np.prod(A) * math.cos(sum(phi)) * npix
+        assert abs(num[i] - expect) <= 1e-4 * abs(expect)
