@@ -1,0 +1,418 @@
+"""Benchmark of the FFT polyspectrum estimator on one GB300 (or N replicas).
+
+Workload (one "step"): one 512^3 quadratic-local field (delta = g + f(g^2 -
+<g^2>), g Gaussian with P ~ k^-1.5, sigma_g = 0.1, f = 0.3), bispectrum over
+all closed triplets of 64 log bins from k_f to N k_f/4 with P(k), plus the
+four-shell trispectrum on 16 log bins (which also yields B and P on those
+bins).  Counts are plan-time (outside the step).  Inputs are resident in HBM
+when the timed region starts; the field (512 MiB) and the shell-field slabs
+(GiBs) are larger than L2, so no extra flush is needed.
+
+Metric: closed triplets of the 64-bin plan x fields / wall time
+(triangle-bins/s).  ``e2e`` repeats the measurement through the C ABI with
+a pinned host field and host outputs (host<->device copies inside the timed
+region).  ``--impl reference`` times the FP64 CPU oracle (direct
+measurement, Eq. bi_direct) on a bounded sample of the same workload.
+
+With --gpus N > 1 (torchrun, one process per GPU) every rank runs its own
+replica on its own field (the estimator has no exchange step); value is the
+total over ranks divided by the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID, L_BOX, NB_B, NB_T = 512, 1000.0, 64, 16
+FIELD_KW = dict(f=0.3, slope=-1.5, sigma_g=0.1)
+
+
+def workload(args):
+    return {"workload": "quadratic_local_%d^3_B%dlog_T%dlog" % (args.N, args.nb, args.nbt),
+            "N": args.N, "L": L_BOX, "bins_B": args.nb, "bins_T": args.nbt,
+            "field": "quadratic-local f=0.3 slope=-1.5 sigma_g=0.1 seed=2+rank",
+            "l2": "inputs larger than L2 (field %d MiB, shell-field slabs > 1 GiB)"
+                  % (4 * args.N ** 3 >> 20)}
+
+
+def edges(N, nb):
+    kf = 2 * math.pi / L_BOX
+    return np.geomspace(kf, 0.25 * N * kf, nb + 1)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _find(d, *keys):
+    for k in keys:
+        if k in d:
+            return float(d[k])
+    for v in d.values():
+        if isinstance(v, dict):
+            r = _find(v, *keys)
+            if r is not None:
+                return r
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, seconds=15.0):
+    """FP64 direct-measurement oracle on a bounded sample: every k-th m1 mode.
+
+    The full-workload time is the FP64 FFT of the field (timed once) plus the
+    all-pairs sum time per m1 mode (timed on the sample) times the number of
+    binned modes."""
+    import fields
+    import oracle
+    N = args.N
+    thr = oracle.thresholds(edges(N, args.nb), L_BOX)
+    nm = oracle.count_modes(N, thr)
+    f = fields.quadratic_local(N, seed=2, **FIELD_KW).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    D = oracle.spectrum(f)
+    t_fft = time.perf_counter() - t0
+    # probe the per-m1 rate on a tiny sample, then size the timed sample
+    stride = max(1, nm // 16)
+    t0 = time.perf_counter()
+    _, _, _, done = oracle.direct_sums_from_spectrum(D, thr, 0, stride)
+    per_m1 = (time.perf_counter() - t0) / max(1, done)
+    want = max(1, int(seconds / max(per_m1, 1e-9)))
+    stride = max(1, nm // want)
+    t0 = time.perf_counter()
+    _, _, _, done = oracle.direct_sums_from_spectrum(D, thr, 0, stride)
+    t_s = time.perf_counter() - t0
+    t_full = t_fft + t_s * nm / max(1, done)
+    return t_full, {"m1_sampled": int(done), "m1_total": int(nm), "sample_s": t_s,
+                    "fft_s": t_fft, "cores": oracle.num_threads()}
+
+
+def run_reference(args, ntrip_hint=None):
+    """--impl reference: the FP64 CPU oracle, each step a bounded sample."""
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import fields  # noqa: F401
+    secs = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+    times = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        t_full, info = cpu_baseline(args, seconds=secs)
+        if i >= args.warmup:
+            times.append(t_full)
+    ntrip = ntrip_hint
+    t = float(np.mean(times))
+    val = ntrip / t
+    line = {"impl": "reference", "metric": "bispectrum triangle-bins/s", "value": val,
+            "unit": "triangle-bins/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload(args),
+            "cpu_baseline": {"value": val, "unit": "triangle-bins/s", "cores": info["cores"],
+                             "kind": "oracle",
+                             "sample": "direct all-pairs sum over %d of %d m1 modes per step, "
+                                       "scaled to all modes" % (info["m1_sampled"], info["m1_total"])},
+            "e2e": {"value": val, "unit": "triangle-bins/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("FBS_BENCH_PRECISION", "fp32"))
+    ap.add_argument("--N", type=int, default=N_GRID)
+    ap.add_argument("--nb", type=int, default=NB_B)
+    ap.add_argument("--nbt", type=int, default=NB_T)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        # the closed-triplet count is the plan's; the oracle's all-pairs sum
+        # produces every triplet of the workload at once
+        import oracle
+        e = edges(args.N, args.nb)
+        thr = oracle.thresholds(e, L_BOX)
+        ntrip = _closed_triplets_oracle(args.N, thr)
+        run_reference(args, ntrip_hint=ntrip)
+        return
+
+    import torch
+    import fields
+    import paper_1705_06284_gb300 as fbs
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    N = args.N
+    f64 = fields.quadratic_local(N, seed=2 + rank, **FIELD_KW)
+    f32 = f64.astype(np.float32)
+    del f64
+    field = torch.from_numpy(f32).to(dev)
+    eB, eT = edges(N, args.nb), edges(N, args.nbt)
+    t0 = time.perf_counter()
+    planB = fbs.Plan(N, L_BOX, eB, precision=args.precision, timing=True, stream=stream)
+    planT = fbs.Plan(N, L_BOX, eT, precision="fp32", trispectrum=True, timing=True, stream=stream)
+    plan_s = time.perf_counter() - t0
+    B = torch.empty(planB.ntrip, dtype=torch.float64, device=dev)
+    P = torch.empty(planB.nbins, dtype=torch.float64, device=dev)
+    T = torch.empty(planT.nquad, dtype=torch.float64, device=dev)
+    B16 = torch.empty(planT.ntrip, dtype=torch.float64, device=dev)
+    P16 = torch.empty(planT.nbins, dtype=torch.float64, device=dev)
+
+    def step(fld, outs):
+        planB.bispectrum(fld, outs[0], outs[1])
+        planT.trispectrum(fld, outs[2], outs[3], outs[4])
+
+    outs_dev = (B, P, T, B16, P16)
+    for _ in range(args.warmup):
+        step(field, outs_dev)
+    torch.cuda.synchronize()
+    planB.kernel_times(reset=True)
+    planT.kernel_times(reset=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(field, outs_dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    kB = planB.kernel_times(reset=True)
+    kT = planT.kernel_times(reset=True)
+    launches = sum(v[1] for v in kB.values()) + sum(v[1] for v in kT.values())
+
+    # e2e: pinned host field in, host outputs back, through the C ABI
+    e2e = None
+    if not args.no_e2e:
+        hfield = torch.from_numpy(f32).pin_memory()
+        outs_host = (np.empty(planB.ntrip), np.empty(planB.nbins), np.empty(planT.nquad),
+                     np.empty(planT.ntrip), np.empty(planT.nbins))
+        for _ in range(2):
+            step(hfield, outs_host)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(hfield, outs_host)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        planB.kernel_times(reset=True)
+        planT.kernel_times(reset=True)
+        h2d = 2 * f32.nbytes
+        d2h = 8 * (planB.ntrip + planB.nbins + planT.nquad + planT.ntrip + planT.nbins)
+        e2e = {"value": None, "unit": "triangle-bins/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "_s": e2e_s}
+        # sanity: host outputs equal device outputs
+        if not np.allclose(outs_host[0], B.cpu().numpy(), rtol=0, atol=0):
+            e2e["mismatch"] = True
+
+    ms_max = ms
+    e2e_max = e2e["_s"] if e2e else None
+    if dist:
+        t = torch.tensor([ms, e2e_max or 0.0], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max, e2e_max = float(t[0]), float(t[1])
+    value = world * planB.ntrip / (ms_max / 1e3)
+
+    # roofline of the dominant kernel class (largest share of the timed region)
+    pk, pk_src = peaks()
+    allk = {("B:" + k): v for k, v in kB.items()}
+    allk.update({("T:" + k): v for k, v in kT.items()})
+    top = max(allk.items(), key=lambda kv: kv[1][0])
+    roof = roofline(top, planB, planT, N, pk, pk_src, clocks)
+
+    line = {"metric": "bispectrum triangle-bins/s", "value": value, "unit": "triangle-bins/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16"}[args.precision],
+            "data": "synthetic", "config": dict(workload(args), ntrip_B=planB.ntrip,
+                                                nquad_T=planT.nquad, precision_B=args.precision,
+                                                precision_T="fp32", parallelism="replicas%d" % world),
+            "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
+            "plan_s": plan_s,
+            "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in allk.items() if v[1]}}
+    if e2e:
+        e2e["value"] = world * planB.ntrip / e2e_max
+        e2e.pop("_s", None)
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        try:
+            t_full, info = cpu_baseline(args, seconds=15.0)
+            line["cpu_baseline"] = {"value": planB.ntrip / t_full, "unit": "triangle-bins/s",
+                                    "cores": info["cores"], "kind": "oracle",
+                                    "sample": "FP64 direct all-pairs sum (Eq. bi_direct) over %d of "
+                                              "%d m1 modes (%.1f s) scaled to all modes, plus the "
+                                              "FP64 FFT (%.1f s)" % (info["m1_sampled"], info["m1_total"],
+                                                                     info["sample_s"], info["fft_s"])}
+        except Exception as ex:  # the baseline must not sink the bench line
+            line["cpu_baseline"] = {"value": None, "error": str(ex)[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    planB.close()
+    planT.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _closed_triplets_oracle(N, thr):
+    """Closed-triplet count of the workload from the oracle alone (witness
+    search over the shells), so that the reference arm never loads the CUDA
+    library."""
+    import oracle
+    return len(oracle.closed_triplets(N, L_BOX, edges(N, len(thr) - 1)))
+
+
+def roofline(top, planB, planT, N, pk, pk_src, clocks):
+    """Algorithmic work of the dominant kernel class per launch / its mean
+    launch duration (CUDA events around each launch on the plan's stream)."""
+    name, (ms_tot, n) = top
+    which, cls = name.split(":", 1)
+    plan = planB if which == "B" else planT
+    npix = N ** 3
+    per_launch_ms = ms_tot / max(1, n)
+    out = {"kernel": name, "launches": n, "avg_ms": per_launch_ms}
+    hbm = _find(pk, "hbm_gbs", "hbm_GBs", "copy_gbs") or 6800.0
+    bf16 = _find(pk, "bf16_tflops_sustained") or 1700.0
+    pts_per_launch = plan_slab_points(plan, N)
+    if cls in ("contract_fp32", "contract_quad"):
+        # FP32 CUDA-core FMAs: 1 mul per outer pair + 2 flops per item, per point
+        nit = plan.ntrip if cls == "contract_fp32" else plan.nquad
+        npairs = len({(int(a[1]), int(a[2])) for a in plan.triplets}) if cls == "contract_fp32" else \
+            len({(int(q[2]), int(q[3])) for q in plan.quads})
+        per_pt = 2 * nit + npairs + (nit if cls == "contract_quad" else 0)
+        flops = per_pt * pts_per_launch
+        sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x clock
+        ach = flops / (per_launch_ms * 1e-3) / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (derived)" % sm_mhz})
+    elif cls == "contract_tc":
+        npairs = len({(int(a[1]), int(a[2])) for a in plan.triplets})
+        flops = (2 * plan.ntrip + npairs) * pts_per_launch
+        ach = flops / (per_launch_ms * 1e-3) / 1e12
+        out.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
+                    "frac": ach / bf16, "traffic": None,
+                    "peak_source": "bf16_tflops_sustained (%s)" % pk_src})
+    else:
+        # FFT stages: algorithmic bytes per launch (shell fields written, inputs read)
+        byts = fft_bytes(cls, plan, N, pts_per_launch)
+        ach = byts / (per_launch_ms * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "peak_source": "hbm_gbs (%s)" % pk_src})
+    return out
+
+
+def plan_slab_points(plan, N):
+    # the library balances slabs: ceil(N / nslabs) planes each
+    per_plane = plan.nbins * N * N * 4
+    budget = int(os.environ.get("FBS_SLAB_MB", "8192")) << 20
+    slab = max(1, min(N, budget // max(1, per_plane)))
+    nsl = -(-N // slab)
+    slab = -(-N // nsl)
+    return slab * N * N
+
+
+def fft_bytes(cls, plan, N, pts):
+    nonempty = int((plan.shell > 0).sum())
+    if cls == "inv_z":
+        return 4 * pts * nonempty  # shell-field writes dominate
+    if cls == "fwd_z":
+        return 4 * N ** 3
+    return 4 * pts * nonempty
+
+
+if __name__ == "__main__":
+    main()

@@ -76,6 +76,9 @@ def _load():
             lib.oracle_direct_triplets.restype = None
             lib.oracle_direct_triplets.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
                                                    ctypes.c_int, i32p, dp, dp, i64p]
+            lib.oracle_closed_triplets.restype = None
+            lib.oracle_closed_triplets.argtypes = [ctypes.c_int, ctypes.c_int, i64p, ctypes.c_int,
+                                                   i32p, i32p]
             lib.oracle_direct_trispectrum.restype = None
             lib.oracle_direct_trispectrum.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
                                                       dp, dp, i64p]
@@ -166,8 +169,12 @@ def direct_sums(field, thr, m1_start: int = 0, m1_stride: int = 1):
     Returns also the number of m1 modes processed (all of them unless a
     sample is asked for with ``m1_stride > 1``).
     """
+    return direct_sums_from_spectrum(spectrum(field), thr, m1_start, m1_stride)
+
+
+def direct_sums_from_spectrum(D, thr, m1_start: int = 0, m1_stride: int = 1):
+    """:func:`direct_sums` on a precomputed full spectrum D (FFT order)."""
     lib = _load()
-    D = spectrum(field)
     N = D.shape[0]
     re = np.ascontiguousarray(D.real)
     im = np.ascontiguousarray(D.imag)
@@ -253,6 +260,44 @@ def direct_triplets(field, L: float, edges, triplets):
     npix = float(N) ** 3
     B = (V * V / npix ** 3) * num / np.maximum(cnt, 1)
     return B, num, numi, cnt
+
+
+def closed_triplets(N: int, L: float, edges) -> np.ndarray:
+    """Every bin triple a <= b <= c with N_tri > 0, lexicographic.
+
+    Triples whose largest shell cannot be reached by the sum of the other two
+    (min |m_c| > max |m_a| + max |m_b|, the triangle inequality for exact
+    closure) are dropped without search; this holds when every component is
+    below N/4 (then closure modulo N is exact closure).  The rest are decided
+    by a witness search over the shells' modes.
+    """
+    thr = np.ascontiguousarray(thresholds(edges, L))
+    nb = len(thr) - 1
+    m2 = mode_squares(N)
+    b = bin_index(N, thr)
+    S = np.bincount(b[b >= 0].ravel(), minlength=nb)
+    lo = np.full(nb, np.inf)
+    hi = np.full(nb, -np.inf)
+    for k in range(nb):
+        if S[k]:
+            v = m2[b == k]
+            lo[k], hi[k] = math.sqrt(v.min()), math.sqrt(v.max())
+    exact = thr[-1] <= (N * N + 15) // 16
+    cand = []
+    for a in range(nb):
+        for bb in range(a, nb):
+            for c in range(bb, nb):
+                if not (S[a] and S[bb] and S[c]):
+                    continue
+                if exact and lo[c] > hi[a] + hi[bb] + 1e-9:
+                    continue
+                cand.append((a, bb, c))
+    abc = np.ascontiguousarray(np.array(cand, dtype=np.int32).reshape(-1, 3))
+    flag = np.zeros(len(abc), dtype=np.int32)
+    if len(abc):
+        _load().oracle_closed_triplets(N, nb, _p(thr, ctypes.c_int64), len(abc),
+                                       _p(abc, ctypes.c_int32), _p(flag, ctypes.c_int32))
+    return abc[flag > 0]
 
 
 def direct_trispectrum(field, L: float, edges):

@@ -289,3 +289,51 @@ void oracle_direct_trispectrum(int N, const double *re, const double *im, int nb
     }
     free(M);
 }
+
+/*
+ * Closure of bin triples (a, b, c): flag[t] = 1 when some ordered triple
+ * m1 in S_a, m2 in S_b, m3 = -(m1+m2) (mod N) in S_c exists, i.e. when
+ * N_tri > 0.  A witness search that stops at the first closed triple; the
+ * caller may skip triples the triangle inequality already rules out.
+ * Modes of each shell are visited from the largest |m| down, where closing
+ * triangles of wide bin triples are found first.
+ */
+static int cmp_desc_m2(const void *x, const void *y) {
+    const mode_t_ *a = (const mode_t_ *)x, *b = (const mode_t_ *)y;
+    long long sa = (long long)a->mx * a->mx + (long long)a->my * a->my + (long long)a->mz * a->mz;
+    long long sb = (long long)b->mx * b->mx + (long long)b->my * b->my + (long long)b->mz * b->mz;
+    if (a->bin != b->bin) return a->bin - b->bin;
+    return (sa < sb) - (sa > sb);
+}
+
+void oracle_closed_triplets(int N, int nbins, const int64_t *thr, int ntrip, const int32_t *abc,
+                            int32_t *flag) {
+    mode_t_ *M = NULL;
+    int64_t nm = collect_modes(N, nbins, thr, &M);
+    qsort(M, (size_t)nm, sizeof(mode_t_), cmp_desc_m2);
+    int64_t *start = (int64_t *)calloc((size_t)nbins + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < nm; ++i) start[M[i].bin + 1]++;
+    for (int b = 0; b < nbins; ++b) start[b + 1] += start[b];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int t = 0; t < ntrip; ++t) {
+        int A = abc[3 * t], B = abc[3 * t + 1], C = abc[3 * t + 2];
+        int found = 0;
+        for (int64_t p = start[A]; p < start[A + 1] && !found; ++p) {
+            const mode_t_ a = M[p];
+            for (int64_t q = start[B]; q < start[B + 1]; ++q) {
+                const mode_t_ b = M[q];
+                int x = wrap(-(a.mx + b.mx), N);
+                int y = wrap(-(a.my + b.my), N);
+                int z = wrap(-(a.mz + b.mz), N);
+                int64_t m2 = (int64_t)x * x + (int64_t)y * y + (int64_t)z * z;
+                if (m2 >= thr[C] && m2 < thr[C + 1]) {
+                    found = 1;
+                    break;
+                }
+            }
+        }
+        flag[t] = found;
+    }
+    free(start);
+    free(M);
+}

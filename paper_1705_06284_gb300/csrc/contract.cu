@@ -134,6 +134,16 @@ __global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, in
     out[i] = s;
 }
 
+// out[j] = sum_r part[j][r] in a fixed order (deterministic).
+__global__ void reduce_cols_kernel(const double *__restrict__ part, int rows, int n,
+                                   double *__restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += part[(long long)j * rows + r];
+    out[j] = s;
+}
+
 // ------------------------------------------------------------------ normalise
 // B = V^2/N_pix^3 num/(N_pix N_tri), P = V/N_pix^2 sumsq/(N_pix |S_b|)
 // (NaN for empty shells), T = V^3/N_pix^4 qnum/(N_pix N_quad).
@@ -283,7 +293,9 @@ void zero_partials(Plan &p, bool quads) {
     if (quads && p.d_qpart && p.qtask.nitems > 0)
         FBS_CUDA(cudaMemsetAsync(p.d_qpart, 0, (size_t)p.part_blocks * p.qtask.nitems * sizeof(double),
                                  p.stream));
-    FBS_CUDA(cudaMemsetAsync(p.d_sumsq, 0, (size_t)p.nbins * sizeof(double), p.stream));
+    // every sum-of-squares partial is overwritten by the z stage (empty bins: 0)
+    FBS_CUDA(cudaMemsetAsync(p.d_sumsq_part, 0,
+                             (size_t)p.nbins * p.N * zstage_row_groups(p.N) * sizeof(double), p.stream));
 }
 
 void launch_reduce_and_normalise(Plan &p, bool quads) {
@@ -299,6 +311,12 @@ void launch_reduce_and_normalise(Plan &p, bool quads) {
             int m = p.qtask.nitems;
             reduce_rows_kernel<<<(m + 255) / 256, 256, 0, p.stream>>>(p.d_qpart, p.part_blocks, m,
                                                                       p.d_qnum);
+            FBS_CUDA(cudaGetLastError());
+        }
+        {
+            const int rows = p.N * zstage_row_groups(p.N);
+            reduce_cols_kernel<<<(p.nbins + 127) / 128, 128, 0, p.stream>>>(p.d_sumsq_part, rows, p.nbins,
+                                                                             p.d_sumsq);
             FBS_CUDA(cudaGetLastError());
         }
         int ntrip = (int)p.ntri.size(), nquad = quads ? (int)p.nquad.size() : 0;

@@ -93,6 +93,7 @@ void upload_twiddles(Plan &p);
 void launch_forward(Plan &p, const float *d_field);
 void launch_inverse_x(Plan &p, bool indicator_fp64);
 void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab);
+int zstage_row_groups(int N);
 void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
                                    double2 *G64, const BinGeom *d_geom_grp);
 // contract.cu (FP64 count sums)
@@ -158,6 +159,7 @@ struct Plan {
     double *d_tpart = nullptr;    // [part_blocks][ntrip]
     double *d_qpart = nullptr;    // [part_blocks][nquad]
     double *d_sumsq = nullptr;    // [nbins]
+    double *d_sumsq_part = nullptr;  // [nbins][N][z-stage row groups]
     double *d_tnum = nullptr;     // [ntrip]
     double *d_qnum = nullptr;     // [nquad]
     double *d_B = nullptr, *d_P = nullptr, *d_T = nullptr;  // staging for host outputs

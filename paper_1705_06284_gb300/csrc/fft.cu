@@ -238,9 +238,9 @@ __global__ void __launch_bounds__(kThreads) inv_y_kernel(const typename V2<T>::t
 template <typename T, bool OCT>
 __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t *__restrict__ G,
                                                          const BinGeom *__restrict__ geom, int bin0,
-                                                         int N, T *__restrict__ out,
+                                                         int N, int x0, T *__restrict__ out,
                                                          long long out_bin_stride,
-                                                         double *__restrict__ sumsq, int nl,
+                                                         double *__restrict__ sumsq_part, int nl,
                                                          FftFactors f,
                                                          const typename V2<T>::t *__restrict__ tw) {
     typedef typename V2<T>::t C;
@@ -313,9 +313,10 @@ __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
         __syncthreads();
         if (threadIdx.x == 0) {
+            // one partial per (bin, plane, row group): summed in a fixed order later
             double s = 0.0;
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-            atomicAdd(&sumsq[bin0 + bl], s);
+            sumsq_part[((long long)(bin0 + bl) * N + x0 + xl) * gridDim.x + blockIdx.x] = s;
         }
     } else {
         const int H = N / 2 + 1;
@@ -330,6 +331,12 @@ __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t
 }
 
 // ------------------------------------------------------------------ host side
+// Row groups per plane of the FP32 z stage (one sum-of-squares partial each).
+int zstage_row_groups(int N) {
+    const int nl = lines_per_cta<float>(N);
+    return (N + 2 * nl - 1) / (2 * nl);
+}
+
 void upload_twiddles(Plan &p) {
     const int N = p.N;
     std::vector<float2> t32(N);
@@ -424,8 +431,9 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
         auto k = inv_z_kernel<float, false>;
         allow_smem(k, sm);
         dim3 grid((N + 2 * nl - 1) / (2 * nl), nx, p.nbins);
-        k<<<grid, kThreads, sm, p.stream>>>(p.d_G, p.d_geom, 0, N, islab, (long long)p.slab * N * N,
-                                            p.d_sumsq, nl, p.fN, p.d_tw);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_G, p.d_geom, 0, N, x0, islab,
+                                            (long long)p.slab * N * N, p.d_sumsq_part, nl, p.fN,
+                                            p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
 }
@@ -460,7 +468,7 @@ void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, doub
         auto k = inv_z_kernel<double, true>;
         allow_smem(k, sm);
         dim3 grid((H + 2 * nl - 1) / (2 * nl), H, nb);
-        k<<<grid, kThreads, sm, p.stream>>>(G64, d_geom_grp, 0, N, noct, (long long)H * H * H,
+        k<<<grid, kThreads, sm, p.stream>>>(G64, d_geom_grp, 0, N, 0, noct, (long long)H * H * H,
                                             nullptr, nl, p.fN, p.d_tw64);
         FBS_CUDA(cudaGetLastError());
     }

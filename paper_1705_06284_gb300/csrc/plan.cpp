@@ -508,6 +508,7 @@ static void create_plan(Plan &p, const double *edges) {
     p.d_tpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, ntrip) * sizeof(double));
     p.d_qpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, nquad) * sizeof(double));
     p.d_sumsq = (double *)p.dalloc(nb * sizeof(double));
+    p.d_sumsq_part = (double *)p.dalloc((size_t)nb * N * zstage_row_groups(N) * sizeof(double));
     p.d_tnum = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
     p.d_qnum = (double *)p.dalloc(std::max(1, nquad) * sizeof(double));
     p.d_B = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
