@@ -51,7 +51,7 @@ typedef enum {
     FBS_ERR_CUDA = -4,           /* a CUDA call or kernel failed, or no device */
     FBS_ERR_TIMEOUT = -5,        /* a bounded device wait gave up */
     FBS_ERR_STATE = -6,          /* call not valid for this plan (e.g. T on a B-only plan) */
-    FBS_ERR_NUMERIC = -7         /* an FP64 count was not within 1e-3 of an integer */
+    FBS_ERR_NUMERIC = -7         /* an FP64 count sum was more than 0.25 from an integer */
 } fbs_status;
 
 /* Contraction precision (Sec. 2's real-space product sums). FFTs are FP32
@@ -163,6 +163,11 @@ fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, 
 
 /* Plan-time cost (ms of wall time spent in fbs_plan_create). */
 double fbs_plan_create_ms(const fbs_plan *plan);
+
+/* Largest distance of sum_n N..N / N_pix from the nearest integer over all
+ * candidate triples/quadruples at plan time (FP64 rounding diagnostics; the
+ * plan fails with FBS_ERR_NUMERIC when it exceeds 0.25). */
+double fbs_plan_count_margin(const fbs_plan *plan);
 
 /* Device bytes owned by the plan. */
 int64_t fbs_plan_device_bytes(const fbs_plan *plan);

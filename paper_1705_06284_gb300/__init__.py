@@ -72,6 +72,7 @@ _SIGS = [
     ("fbs_plan_kernel_times", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
     ("fbs_plan_create_ms", ctypes.c_double, [_vp]),
     ("fbs_plan_device_bytes", ctypes.c_int64, [_vp]),
+    ("fbs_plan_count_margin", ctypes.c_double, [_vp]),
     ("fbs_last_error", ctypes.c_char_p, []),
     ("fbs_version", ctypes.c_int, []),
 ]
@@ -174,6 +175,7 @@ class Plan:
         _check(Lb.fbs_plan_shells(_vp(self._h), self.shell.ctypes.data, self.thresholds.ctypes.data))
         self.create_ms = Lb.fbs_plan_create_ms(_vp(self._h))
         self.device_bytes = int(Lb.fbs_plan_device_bytes(_vp(self._h)))
+        self.count_margin = float(Lb.fbs_plan_count_margin(_vp(self._h)))
 
     # -- lifetime
     def close(self):

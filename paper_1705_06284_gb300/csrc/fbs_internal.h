@@ -117,6 +117,7 @@ struct Plan {
     unsigned flags = 0;
     cudaStream_t stream = nullptr;
     double create_ms = 0;
+    double count_margin = 0;  // largest |sum N..N / N_pix - nearest integer| seen at plan time
 
     std::vector<long long> thr;  // nbins+1
     std::vector<long long> shell;

@@ -338,10 +338,15 @@ static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<
     FBS_CUDA(cudaStreamSynchronize(p.stream));
 }
 
-static int64_t round_count(double den, double npix) {
+// Round sum_n N..N / N_pix to the count.  The FP64 sum carries rounding
+// error that grows with the count (about 1e-15 relative); a distance above
+// 0.25 from the nearest integer means the rounding could be wrong.
+static int64_t round_count(Plan &p, double den, double npix) {
     double v = den / npix;
     double r = nearbyint(v);
-    if (fabs(v - r) > 1e-2)
+    double d = fabs(v - r);
+    if (d > p.count_margin) p.count_margin = d;
+    if (d > 0.25)
         throw Failure{FBS_ERR_NUMERIC, "count sum " + std::to_string(v) + " is not an integer"};
     return (int64_t)r;
 }
@@ -451,7 +456,7 @@ static void create_plan(Plan &p, const double *edges) {
     p.trip.clear();
     p.ntri.clear();
     for (size_t i = 0; i < tden.size(); ++i) {
-        int64_t c = round_count(tden[i], npix);
+        int64_t c = round_count(p, tden[i], npix);
         if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative triangle count"};
         if (c == 0) continue;
         p.trip.insert(p.trip.end(), {tc[3 * i], tc[3 * i + 1], tc[3 * i + 2]});
@@ -460,7 +465,7 @@ static void create_plan(Plan &p, const double *edges) {
     p.quad.clear();
     p.nquad.clear();
     for (size_t i = 0; i < qden.size(); ++i) {
-        int64_t c = round_count(qden[i], npix);
+        int64_t c = round_count(p, qden[i], npix);
         if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative quadruple count"};
         if (c == 0) continue;
         p.quad.insert(p.quad.end(), {qc[4 * i], qc[4 * i + 1], qc[4 * i + 2], qc[4 * i + 3]});
@@ -774,6 +779,8 @@ fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, 
 }
 
 double fbs_plan_create_ms(const fbs_plan *plan) { return plan ? plan->create_ms : -1.0; }
+
+double fbs_plan_count_margin(const fbs_plan *plan) { return plan ? plan->count_margin : -1.0; }
 
 int64_t fbs_plan_device_bytes(const fbs_plan *plan) { return plan ? plan->dev_bytes : -1; }
 
