@@ -322,6 +322,7 @@ def main():
                                                 precision_T="fp32", parallelism="replicas%d" % world),
             "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
             "plan_s": plan_s, "count_margin": [planB.count_margin, planT.count_margin],
+            "quad_counts_exact": planT.quad_counts_exact,
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in allk.items() if v[1]}}
     if e2e:
         e2e["value"] = world * planB.ntrip / e2e_max

@@ -107,8 +107,11 @@ int fbs_plan_num_quads(const fbs_plan *plan);
 fbs_status fbs_plan_triplets(const fbs_plan *plan, int32_t *abc, int64_t *ntri);
 
 /* Copy the closed-quadruplet table: abcd[4*nquad] (a<=b<=c<=d) and
- * nquad_counts[nquad] (exact ordered quadruple counts).  Either may be NULL. */
-fbs_status fbs_plan_quads(const fbs_plan *plan, int32_t *abcd, int64_t *nquad_counts);
+ * nquad_counts[nquad], the ordered quadruple counts sum_n N_a N_b N_c N_d / N_pix
+ * as FP64.  Below 2^53 they are rounded to exact integers (like triangle
+ * counts); wide shells on large grids give counts past 2^53 (even past int64),
+ * which are returned as the FP64 sum.  Either pointer may be NULL. */
+fbs_status fbs_plan_quads(const fbs_plan *plan, int32_t *abcd, double *nquad_counts);
 
 /* Copy shell sizes |S_b| (int64[nbins]) and, if thr != NULL, the integer
  * thresholds on |m|^2 (int64[nbins+1]): bin b holds thr[b] <= |m|^2 < thr[b+1]. */
@@ -164,10 +167,14 @@ fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, 
 /* Plan-time cost (ms of wall time spent in fbs_plan_create). */
 double fbs_plan_create_ms(const fbs_plan *plan);
 
-/* Largest distance of sum_n N..N / N_pix from the nearest integer over all
- * candidate triples/quadruples at plan time (FP64 rounding diagnostics; the
- * plan fails with FBS_ERR_NUMERIC when it exceeds 0.25). */
+/* Largest distance of sum_n N_a N_b N_c / N_pix from the nearest integer over
+ * all candidate triples at plan time (FP64 rounding diagnostics; the plan
+ * fails with FBS_ERR_NUMERIC when it exceeds 0.25). */
 double fbs_plan_count_margin(const fbs_plan *plan);
+
+/* 1 when every quadruple count of the plan is an exact integer (rounded
+ * within 0.25 and below 2^53), 0 when some are FP64 sums, <0 on error. */
+int fbs_plan_quad_counts_exact(const fbs_plan *plan);
 
 /* Device bytes owned by the plan. */
 int64_t fbs_plan_device_bytes(const fbs_plan *plan);

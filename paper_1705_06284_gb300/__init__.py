@@ -73,6 +73,7 @@ _SIGS = [
     ("fbs_plan_create_ms", ctypes.c_double, [_vp]),
     ("fbs_plan_device_bytes", ctypes.c_int64, [_vp]),
     ("fbs_plan_count_margin", ctypes.c_double, [_vp]),
+    ("fbs_plan_quad_counts_exact", ctypes.c_int, [_vp]),
     ("fbs_last_error", ctypes.c_char_p, []),
     ("fbs_version", ctypes.c_int, []),
 ]
@@ -168,7 +169,7 @@ class Plan:
         self.N_tri = np.zeros(self.ntrip, dtype=np.int64)
         _check(Lb.fbs_plan_triplets(_vp(self._h), self.triplets.ctypes.data, self.N_tri.ctypes.data))
         self.quads = np.zeros((self.nquad, 4), dtype=np.int32)
-        self.N_quad = np.zeros(self.nquad, dtype=np.int64)
+        self.N_quad = np.zeros(self.nquad, dtype=np.float64)
         _check(Lb.fbs_plan_quads(_vp(self._h), self.quads.ctypes.data, self.N_quad.ctypes.data))
         self.shell = np.zeros(self.nbins, dtype=np.int64)
         self.thresholds = np.zeros(self.nbins + 1, dtype=np.int64)
@@ -176,6 +177,7 @@ class Plan:
         self.create_ms = Lb.fbs_plan_create_ms(_vp(self._h))
         self.device_bytes = int(Lb.fbs_plan_device_bytes(_vp(self._h)))
         self.count_margin = float(Lb.fbs_plan_count_margin(_vp(self._h)))
+        self.quad_counts_exact = bool(Lb.fbs_plan_quad_counts_exact(_vp(self._h)) == 1)
 
     # -- lifetime
     def close(self):

@@ -149,7 +149,7 @@ __global__ void reduce_cols_kernel(const double *__restrict__ part, int rows, in
 // (NaN for empty shells), T = V^3/N_pix^4 qnum/(N_pix N_quad).
 __global__ void normalise_kernel(const double *__restrict__ tnum, const int64_t *__restrict__ ntri,
                                  int ntrip, const double *__restrict__ qnum,
-                                 const int64_t *__restrict__ nq, int nquad,
+                                 const double *__restrict__ nq, int nquad,
                                  const double *__restrict__ sumsq, const long long *__restrict__ shell,
                                  int nbins, double L, int N, double *__restrict__ B,
                                  double *__restrict__ P, double *__restrict__ T) {
@@ -161,7 +161,7 @@ __global__ void normalise_kernel(const double *__restrict__ tnum, const int64_t 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (B && i < ntrip) B[i] = cB * tnum[i] / (npix * (double)ntri[i]);
     if (P && i < nbins) P[i] = shell[i] > 0 ? cP * sumsq[i] / (npix * (double)shell[i]) : nan("");
-    if (T && i < nquad) T[i] = cT * qnum[i] / (npix * (double)nq[i]);
+    if (T && i < nquad) T[i] = cT * qnum[i] / (npix * nq[i]);
 }
 
 // ------------------------------------------------------------------ counts (FP64)

@@ -117,7 +117,8 @@ struct Plan {
     unsigned flags = 0;
     cudaStream_t stream = nullptr;
     double create_ms = 0;
-    double count_margin = 0;  // largest |sum N..N / N_pix - nearest integer| seen at plan time
+    double count_margin = 0;  // largest |sum N..N / N_pix - nearest integer| of the rounded counts
+    bool quad_counts_exact = true;  // false when some quadruple count is past 2^53
 
     std::vector<long long> thr;  // nbins+1
     std::vector<long long> shell;
@@ -128,7 +129,7 @@ struct Plan {
     std::vector<int32_t> trip;   // 3*ntrip
     std::vector<int64_t> ntri;
     std::vector<int32_t> quad;   // 4*nquad
-    std::vector<int64_t> nquad;
+    std::vector<double> nquad;   // FP64 ordered quadruple counts (exact integers below 2^53)
     TaskList ttask, qtask;
     std::vector<int> tgrp, qgrp;  // item groups of the FP32 contraction (outer-pair ranges)
     int *d_tgrp = nullptr, *d_qgrp = nullptr;
@@ -164,7 +165,8 @@ struct Plan {
     double *d_tnum = nullptr;     // [ntrip]
     double *d_qnum = nullptr;     // [nquad]
     double *d_B = nullptr, *d_P = nullptr, *d_T = nullptr;  // staging for host outputs
-    int64_t *d_ntri = nullptr, *d_nquad = nullptr;
+    int64_t *d_ntri = nullptr;
+    double *d_nquad = nullptr;
     long long *d_shell = nullptr;
     // tensor-core path
     void *tc = nullptr;           // opaque state of contract_tc.cu

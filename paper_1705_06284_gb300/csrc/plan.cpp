@@ -465,7 +465,18 @@ static void create_plan(Plan &p, const double *edges) {
     p.quad.clear();
     p.nquad.clear();
     for (size_t i = 0; i < qden.size(); ++i) {
-        int64_t c = round_count(p, qden[i], npix);
+        // Quadruple counts of wide shells reach 1e19 and more, past the exact
+        // integers of FP64 (2^53) and of int64: below 2^53 they are rounded
+        // like triangle counts, above it the FP64 sum itself is the count.
+        const double v = qden[i] / npix;
+        const double r = nearbyint(v);
+        double c;
+        if (v < 9007199254740992.0 && fabs(v - r) <= 0.25) {
+            c = r;
+        } else {
+            c = v;  // the FP64 sum is the count (rounding would not be reliable)
+            p.quad_counts_exact = false;
+        }
         if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative quadruple count"};
         if (c == 0) continue;
         p.quad.insert(p.quad.end(), {qc[4 * i], qc[4 * i + 1], qc[4 * i + 2], qc[4 * i + 3]});
@@ -677,10 +688,10 @@ fbs_status fbs_plan_triplets(const fbs_plan *plan, int32_t *abc, int64_t *ntri) 
     return FBS_OK;
 }
 
-fbs_status fbs_plan_quads(const fbs_plan *plan, int32_t *abcd, int64_t *nq) {
+fbs_status fbs_plan_quads(const fbs_plan *plan, int32_t *abcd, double *nq) {
     if (!plan) return FBS_ERR_ARG;
     if (abcd && !plan->quad.empty()) memcpy(abcd, plan->quad.data(), plan->quad.size() * sizeof(int32_t));
-    if (nq && !plan->nquad.empty()) memcpy(nq, plan->nquad.data(), plan->nquad.size() * sizeof(int64_t));
+    if (nq && !plan->nquad.empty()) memcpy(nq, plan->nquad.data(), plan->nquad.size() * sizeof(double));
     return FBS_OK;
 }
 
@@ -781,6 +792,11 @@ fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, 
 double fbs_plan_create_ms(const fbs_plan *plan) { return plan ? plan->create_ms : -1.0; }
 
 double fbs_plan_count_margin(const fbs_plan *plan) { return plan ? plan->count_margin : -1.0; }
+
+int fbs_plan_quad_counts_exact(const fbs_plan *plan) {
+    if (!plan) return FBS_ERR_ARG;
+    return plan->quad_counts_exact ? 1 : 0;
+}
 
 int64_t fbs_plan_device_bytes(const fbs_plan *plan) { return plan ? plan->dev_bytes : -1; }
 

@@ -159,6 +159,7 @@ def test_trispectrum_matches_oracle():
         T, B, P = T.cpu().numpy(), B.cpu().numpy(), P.cpu().numpy()
         check_bispectrum(plan, B, P, f32, L, edges, "fp32")
         g = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=[], quads=plan.quads)
+        assert plan.quad_counts_exact
         assert np.array_equal(plan.N_quad, g["N_quad"])
         # every candidate with a non-zero count is in the plan
         nb = len(edges) - 1
