@@ -152,14 +152,16 @@ __global__ void normalise_kernel(const double *__restrict__ tnum, const int64_t 
                                  const double *__restrict__ nq, int nquad,
                                  const double *__restrict__ sumsq, const long long *__restrict__ shell,
                                  int nbins, double L, int N, double *__restrict__ B,
-                                 double *__restrict__ P, double *__restrict__ T) {
+                                 double *__restrict__ P, double *__restrict__ T,
+                                 const int *__restrict__ err) {
     const double V = L * L * L;
     const double npix = (double)N * N * N;
     const double cB = V * V / (npix * npix * npix);
     const double cP = V / (npix * npix);
     const double cT = V * V * V / (npix * npix * npix * npix);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (B && i < ntrip) B[i] = cB * tnum[i] / (npix * (double)ntri[i]);
+    const bool bad = err && *err;  // a tensor-core wait gave up: the sums are incomplete
+    if (B && i < ntrip) B[i] = bad ? nan("") : cB * tnum[i] / (npix * (double)ntri[i]);
     if (P && i < nbins) P[i] = shell[i] > 0 ? cP * sumsq[i] / (npix * (double)shell[i]) : nan("");
     if (T && i < nquad) T[i] = cT * qnum[i] / (npix * nq[i]);
 }
@@ -323,7 +325,8 @@ void launch_reduce_and_normalise(Plan &p, bool quads) {
         int n_all = std::max(std::max(ntrip, nquad), p.nbins);
         normalise_kernel<<<(n_all + 255) / 256, 256, 0, p.stream>>>(
             p.d_tnum, p.d_ntri, ntrip, p.d_qnum, p.d_nquad, nquad, p.d_sumsq, p.d_shell, p.nbins,
-            p.L, p.N, p.d_B, p.d_P, quads ? p.d_T : nullptr);
+            p.L, p.N, p.d_B, p.d_P, quads ? p.d_T : nullptr,
+            p.precision != FBS_PREC_FP32 ? tc_error_flag(p) : nullptr);
         FBS_CUDA(cudaGetLastError());
     }
 }

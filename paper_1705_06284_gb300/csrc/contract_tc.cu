@@ -1,12 +1,480 @@
-// Tensor-core (tcgen05) contraction: placeholder until the kernel lands.
+// Triplet contraction on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// The real-space sums of Eq. Jeong_BI, num[a,b,c] = sum_x I_a I_b I_c, are
+// a matrix product D[(b,c)][a] = sum_x P_bc(x) I_a(x) with the pair products
+// P_bc = I_b I_c formed on the fly: M = outer pairs (tiles of 128), N = bins a,
+// K = points x.  Per K-chunk of 64 points:
+//   * the shell fields of all bins are staged in shared memory (cp.async,
+//     double-buffered);
+//   * CUDA cores split I_a into BF16 hi/lo (operand B) and form the pair
+//     products, also split into BF16 hi/lo (operand A), writing both in the
+//     128-byte-swizzled K-major layout the tensor core reads;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) for
+//     hi*hi + hi*lo + lo*hi (BF16x3; hi*hi alone for plain BF16) into FP32
+//     accumulators in tensor memory, one 128 x Npad block per pair tile;
+//   * every few chunks the accumulators are read back (tcgen05.ld) and added
+//     into FP64 per-triplet sums in shared memory.
+// Each CTA owns a contiguous range of points; its FP64 sums are added to its
+// own row of the partial buffer and reduced across CTAs in a fixed order.
+//
+// Every wait on an mbarrier is bounded (about one second of clock cycles);
+// on timeout the kernel records an error flag, waits (bounded) for its own
+// MMAs, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
 #include "fbs_internal.h"
 
 namespace fbs {
 
-void launch_contract_tc(Plan &, const float *, long long, long long) {
-    throw Failure{FBS_ERR_STATE, "tensor-core contraction not available in this build"};
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int KC = 64;              // points per chunk (one 128-byte swizzle row of BF16)
+constexpr int kStageLd = KC + 4;    // staged row stride in floats (bank spread)
+constexpr long long kWaitCycles = 2000000000LL;
+
+struct TcPair {
+    int b, c, first, pad;
+    unsigned mask[4];  // bits of the single bins a closing a triplet with (b, c)
+};
+
+struct TcState {
+    TcPair *d_pairs = nullptr;
+    int *d_err = nullptr;
+    int npairs = 0;
+    int ntiles = 0;
+    std::vector<int> grp;  // tile ranges of the CTA groups
+    int *d_grp = nullptr;
+    int maxloc = 0;
+    int Npad = 0;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-void free_tc_state(Plan &) {}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major, 128-byte swizzled operand tile: rows of 128 B (64 BF16 along K),
+// 8-row groups 1024 B apart.  Start address must sit in a 1024-B aligned tile
+// (plus the 32-B K-step offset).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;              // descriptor version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: BF16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gptr, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gptr), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Byte offset of (row, 16-byte chunk j) in a 128-byte swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128_off(int row, int j) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((j ^ (row & 7)) << 4));
+}
+
+// Split 8 FP32 values into BF16 hi (round to nearest) and lo = bf16(v - hi).
+__device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        float2 hf = __bfloat1622float2(hb);
+        __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * i] - hf.x, v[2 * i + 1] - hf.y);
+        h[i] = *reinterpret_cast<uint32_t *>(&hb);
+        l[i] = *reinterpret_cast<uint32_t *>(&lb);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+}  // namespace
+
+// grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM (smem).
+__global__ void __launch_bounds__(kThreads, 1)
+    contract_tc_kernel(const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
+                       int Npad, const TcPair *__restrict__ pairs, int npairs,
+                       const int *__restrict__ grp_tile0, const int *__restrict__ iout,
+                       int nitems_total, double *__restrict__ part, int x3, int flush_every,
+                       int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = blockIdx.y;
+    const int t0 = grp_tile0[g], t1 = grp_tile0[g + 1];
+    const int ntl = t1 - t0;  // tiles of this group
+    const int p_first = t0 * 128;
+    const int p_last = min(npairs, t1 * 128);  // exclusive
+    const int it0 = pairs[p_first].first;
+    const int nloc = (p_last > p_first)
+                         ? (pairs[p_last - 1].first + __popc(pairs[p_last - 1].mask[0]) +
+                            __popc(pairs[p_last - 1].mask[1]) + __popc(pairs[p_last - 1].mask[2]) +
+                            __popc(pairs[p_last - 1].mask[3]) - it0)
+                         : 0;
+
+    // ---- carve shared memory (1024-B aligned operand tiles first)
+    uintptr_t base = reinterpret_cast<uintptr_t>(smraw);
+    base = (base + 1023) & ~(uintptr_t)1023;
+    unsigned char *sm = reinterpret_cast<unsigned char *>(base);
+    const int a_tile = 128 * 128;            // bytes of one 128-row operand tile
+    const int b_tile = Npad * 128;           // bytes of one Npad-row operand tile
+    // operand tiles: Ah[2], Al[2] (pair products), Bh[2], Bl[2] (single bins)
+    unsigned char *const Ah0 = sm, *const Al0 = sm + 2 * a_tile;
+    unsigned char *const Bh0 = sm + 4 * a_tile, *const Bl0 = sm + 4 * a_tile + 2 * b_tile;
+    float *stage = reinterpret_cast<float *>(sm + 4 * a_tile + 4 * b_tile);
+    const int stage_floats = nbins * kStageLd;
+    double *acc = reinterpret_cast<double *>(stage + 2 * stage_floats);
+
+    const int tmem_cols_needed = ntl * Npad;
+    int ncols = 32;
+    while (ncols < tmem_cols_needed) ncols <<= 1;
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < nloc; i += kThreads) acc[i] = 0.0;
+    // padding rows of B (bins >= nbins) stay zero
+    for (int i = tid; i < 4 * b_tile / 16; i += kThreads) {
+        int buf = i / (b_tile / 16), o = i - buf * (b_tile / 16);
+        int row = (o * 16) / 128;
+        if (row >= nbins) reinterpret_cast<uint4 *>(sm + 4 * a_tile + buf * b_tile)[o] = make_uint4(0, 0, 0, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    const long long nchunks = (npts + KC - 1) / KC;
+    const long long c0 = nchunks * blockIdx.x / gridDim.x;
+    const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t idesc = idesc_bf16(128, Npad);
+
+    // stage a chunk: nbins rows of KC floats (16-B cp.async, zero fill past npts)
+    auto prefetch = [&](long long ch, int s) {
+        const long long q0 = ch * KC;
+        float *dst = stage + s * stage_floats;
+        for (int i = tid; i < nbins * (KC / 4); i += kThreads) {
+            int b = i / (KC / 4), k4 = i - b * (KC / 4);
+            long long q = q0 + 4LL * k4;
+            long long rem = npts - q;
+            int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+            const float *src = bytes ? (I + b * bin_stride + q) : I;
+            cp_async16(smem_u32(dst + b * kStageLd + 4 * k4), src, bytes);
+        }
+        cp_async_commit();
+    };
+
+    long long gcount = 0;  // tiles issued so far (commit number)
+    bool ok = true;
+    auto wait_commit = [&](long long n) {
+        if (n < 0 || !ok) return;
+        if (!mbar_wait(&bars[n & 1], (uint32_t)((n >> 1) & 1))) {
+            ok = false;
+            atomicExch(err, 1);
+            abort_flag = 1;
+        }
+    };
+
+    if (c0 < c1) prefetch(c0, 0);
+    bool fresh = true;
+    int since_flush = 0;
+    for (long long ci = c0; ci < c1; ++ci) {
+        const int s = (int)((ci - c0) & 1);
+        cp_async_wait_all();
+        __syncthreads();
+        if (abort_flag) break;
+        if (ci + 1 < c1) prefetch(ci + 1, s ^ 1);
+        // B buffer s was last read by the MMAs of chunk ci-2: covered by commit gcount-2
+        wait_commit(gcount - 2);
+        {
+            const float *st = stage + s * stage_floats;
+            for (int u = tid; u < nbins * 8; u += kThreads) {
+                int row = u % nbins, j = u / nbins;
+                const float4 *src = reinterpret_cast<const float4 *>(st + row * kStageLd + 8 * j);
+                float4 v0 = src[0], v1 = src[1];
+                float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                uint4 h, l;
+                split8(v, h, l);
+                uint32_t off = sw128_off(row, j);
+                *reinterpret_cast<uint4 *>(Bh0 + s * b_tile + off) = h;
+                *reinterpret_cast<uint4 *>(Bl0 + s * b_tile + off) = l;
+            }
+        }
+        for (int lt = 0; lt < ntl; ++lt) {
+            const int ab = (int)(gcount & 1);
+            wait_commit(gcount - 2);
+            // pair products of tile t0+lt: thread owns row r, K groups j = jb, jb+2, ..
+            {
+                const float *st = stage + s * stage_floats;
+                const int r = tid & 127;
+                const int p = (t0 + lt) * 128 + r;
+                int b = 0, c = 0;
+                const bool valid = p < npairs;
+                if (valid) {
+                    b = pairs[p].b;
+                    c = pairs[p].c;
+                }
+                for (int j = tid >> 7; j < 8; j += 2) {
+                    uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
+                    if (valid) {
+                        const float4 *rb = reinterpret_cast<const float4 *>(st + b * kStageLd + 8 * j);
+                        const float4 *rc = reinterpret_cast<const float4 *>(st + c * kStageLd + 8 * j);
+                        float4 b0 = rb[0], b1 = rb[1], e0 = rc[0], e1 = rc[1];
+                        float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
+                                      b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
+                        split8(v, h, l);
+                    }
+                    uint32_t off = sw128_off(r, j);
+                    *reinterpret_cast<uint4 *>(Ah0 + ab * a_tile + off) = h;
+                    *reinterpret_cast<uint4 *>(Al0 + ab * a_tile + off) = l;
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (abort_flag) break;
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(lt * Npad);
+                const uint32_t ah = smem_u32(Ah0 + ab * a_tile), al = smem_u32(Al0 + ab * a_tile);
+                const uint32_t bh = smem_u32(Bh0 + s * b_tile), bl = smem_u32(Bl0 + s * b_tile);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t ko = 32u * k;
+                    mma_bf16(d, sdesc_sw128(ah + ko), sdesc_sw128(bh + ko), idesc, (fresh && k == 0) ? 0u : 1u);
+                    if (x3) {
+                        mma_bf16(d, sdesc_sw128(ah + ko), sdesc_sw128(bl + ko), idesc, 1u);
+                        mma_bf16(d, sdesc_sw128(al + ko), sdesc_sw128(bh + ko), idesc, 1u);
+                    }
+                }
+                mma_commit(&bars[ab]);
+            }
+            ++gcount;
+        }
+        if (abort_flag) break;
+        fresh = false;
+        ++since_flush;
+        if (since_flush == flush_every || ci == c1 - 1) {
+            // all MMAs done -> read the accumulators, add to the FP64 sums
+            wait_commit(gcount - 1);
+            __syncthreads();
+            if (abort_flag) break;
+            tc_fence_after();
+            const int q = warp & 3, h = warp >> 2;
+            const int r = 32 * q + lane;
+            for (int lt = 0; lt < ntl; ++lt) {
+                const int p = (t0 + lt) * 128 + r;
+                const bool valid = p < npairs;
+                TcPair pi;
+                if (valid) pi = pairs[p];
+                for (int c8 = 8 * h; c8 < Npad; c8 += 16) {
+                    float v[8];
+                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * Npad + c8), v);
+                    if (!valid) continue;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int a = c8 + i;
+                        if (a >= 128) continue;
+                        const unsigned w = pi.mask[a >> 5];
+                        const unsigned bit = 1u << (a & 31);
+                        if (!(w & bit)) continue;
+                        int idx = pi.first - it0;
+                        for (int m = 0; m < (a >> 5); ++m) idx += __popc(pi.mask[m]);
+                        idx += __popc(w & (bit - 1u));
+                        acc[idx] += (double)v[i];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            fresh = true;
+            since_flush = 0;
+        }
+    }
+    // make sure no MMA is still in flight before the tensor memory goes away
+    if (gcount > 0) {
+        if (tid == 0 && !mbar_wait(&bars[(gcount - 1) & 1], (uint32_t)(((gcount - 1) >> 1) & 1))) atomicExch(err, 2);
+    }
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    double *row = part + (long long)blockIdx.x * nitems_total;
+    for (int i = tid; i < nloc; i += kThreads) row[iout[it0 + i]] += acc[i];
+}
+
+// ------------------------------------------------------------------ host side
+static size_t tc_smem_bytes(int nbins, int Npad, int nloc) {
+    return 1024 + 4 * 128 * 128 + 4 * (size_t)Npad * 128 + 2 * (size_t)nbins * kStageLd * 4 +
+           (size_t)nloc * 8;
+}
+
+static TcState &tc_state(Plan &p) {
+    if (p.tc) return *reinterpret_cast<TcState *>(p.tc);
+    TcState *st = new TcState();
+    p.tc = st;
+    const TaskList &t = p.ttask;
+    st->npairs = t.npairs;
+    st->ntiles = (t.npairs + 127) / 128;
+    st->Npad = std::max(16, ((p.nbins + 15) / 16) * 16);
+    std::vector<TcPair> hp(std::max(1, t.npairs));
+    for (int i = 0; i < t.npairs; ++i) {
+        TcPair q{};
+        q.b = t.pb[i];
+        q.c = t.pc[i];
+        q.first = t.pstart[i];
+        for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e) q.mask[t.ia[e] >> 5] |= 1u << (t.ia[e] & 31);
+        hp[i] = q;
+    }
+    // groups of tiles: tensor memory (512 columns) and the FP64 item sums bound a group
+    const size_t smem_cap = 220 * 1024;
+    st->grp.assign(1, 0);
+    int cur_tiles = 0, cur_items = 0;
+    st->maxloc = 0;
+    for (int tt = 0; tt < st->ntiles; ++tt) {
+        int pa = tt * 128, pe = std::min(t.npairs, pa + 128);
+        int items = t.pstart[pe] - t.pstart[pa];
+        bool fits = (cur_tiles + 1) * st->Npad <= 512 &&
+                    tc_smem_bytes(p.nbins, st->Npad, cur_items + items) <= smem_cap;
+        if (cur_tiles > 0 && !fits) {
+            st->grp.push_back(tt);
+            st->maxloc = std::max(st->maxloc, cur_items);
+            cur_tiles = 0;
+            cur_items = 0;
+        }
+        cur_tiles += 1;
+        cur_items += items;
+    }
+    st->maxloc = std::max(st->maxloc, cur_items);
+    st->grp.push_back(st->ntiles);
+    if (tc_smem_bytes(p.nbins, st->Npad, st->maxloc) > smem_cap)
+        throw Failure{FBS_ERR_ARG, "tensor-core contraction: a pair tile needs more shared memory than available"};
+    st->d_pairs = (TcPair *)p.dalloc(hp.size() * sizeof(TcPair));
+    FBS_CUDA(cudaMemcpyAsync(st->d_pairs, hp.data(), hp.size() * sizeof(TcPair), cudaMemcpyHostToDevice,
+                             p.stream));
+    st->d_grp = (int *)p.dalloc(st->grp.size() * sizeof(int));
+    FBS_CUDA(cudaMemcpyAsync(st->d_grp, st->grp.data(), st->grp.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, p.stream));
+    st->d_err = (int *)p.dalloc(sizeof(int));
+    FBS_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(int), p.stream));
+    return *st;
+}
+
+int *tc_error_flag(Plan &p) { return p.tc ? reinterpret_cast<TcState *>(p.tc)->d_err : nullptr; }
+
+void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride) {
+    const TaskList &t = p.ttask;
+    if (t.nitems == 0) return;
+    if (p.nbins > 128) throw Failure{FBS_ERR_ARG, "tensor-core contraction supports up to 128 bins"};
+    TcState &st = tc_state(p);
+    const int ngrp = (int)st.grp.size() - 1;
+    int sms = 0, dev = 0;
+    FBS_CUDA(cudaGetDevice(&dev));
+    FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int G = std::max(1, sms / ngrp);
+    if (G > p.part_blocks) G = p.part_blocks;
+    const size_t sm = tc_smem_bytes(p.nbins, st.Npad, st.maxloc);
+    KTimer tm(p, KC_CONTRACT_TC);
+    FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid(G, ngrp);
+    contract_tc_kernel<<<grid, kThreads, sm, p.stream>>>(
+        islab, slab_stride, npts, p.nbins, st.Npad, st.d_pairs, st.npairs, st.d_grp, p.d_tout,
+        t.nitems, p.d_tpart, p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
+    FBS_CUDA(cudaGetLastError());
+}
+
+void free_tc_state(Plan &p) {
+    if (!p.tc) return;
+    delete reinterpret_cast<TcState *>(p.tc);  // device buffers belong to the plan's allocation list
+    p.tc = nullptr;
+}
 
 }  // namespace fbs

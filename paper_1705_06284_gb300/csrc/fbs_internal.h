@@ -192,5 +192,6 @@ struct KTimer {
 };
 
 void free_tc_state(Plan &p);
+int *tc_error_flag(Plan &p);  // device flag set by a timed-out tensor-core wait (or nullptr)
 
 }  // namespace fbs

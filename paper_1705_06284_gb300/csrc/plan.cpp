@@ -545,6 +545,8 @@ static void run_field(Plan &p, const float *field, bool quads) {
         d_in = p.d_field;
     }
     zero_partials(p, quads);
+    if (p.precision != FBS_PREC_FP32 && tc_error_flag(p))
+        FBS_CUDA(cudaMemsetAsync(tc_error_flag(p), 0, sizeof(int), p.stream));
     launch_forward(p, d_in);
     launch_inverse_x(p, false);
     const long long plane = (long long)N * N;
@@ -562,6 +564,17 @@ static void run_field(Plan &p, const float *field, bool quads) {
         if (quads) launch_contract_fp32(p, p.d_I, npts, stride, true);
     }
     launch_reduce_and_normalise(p, quads);
+}
+
+// A tensor-core wait that gave up leaves a flag on the device; the outputs
+// are NaN then (see the normalisation) and host-synchronising calls report it.
+static void check_device_errors(Plan &p) {
+    int *f = tc_error_flag(p);
+    if (!f) return;
+    int v = 0;
+    FBS_CUDA(cudaMemcpyAsync(&v, f, sizeof(int), cudaMemcpyDeviceToHost, p.stream));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));
+    if (v) throw Failure{FBS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (code " + std::to_string(v) + ")"};
 }
 
 static void copy_out(Plan &p, double *dst, const double *src, size_t n, bool &host) {
@@ -731,7 +744,10 @@ fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double 
     bool host = false;
     copy_out(*plan, B, plan->d_B, plan->ntri.size(), host);
     copy_out(*plan, P, plan->d_P, plan->nbins, host);
-    if (host) FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    if (host) {
+        FBS_CUDA(cudaStreamSynchronize(plan->stream));
+        check_device_errors(*plan);
+    }
     return FBS_OK;
     FBS_GUARD_END
 }
@@ -751,7 +767,10 @@ fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double
     copy_out(*plan, T, plan->d_T, plan->nquad.size(), host);
     copy_out(*plan, B, plan->d_B, plan->ntri.size(), host);
     copy_out(*plan, P, plan->d_P, plan->nbins, host);
-    if (host) FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    if (host) {
+        FBS_CUDA(cudaStreamSynchronize(plan->stream));
+        check_device_errors(*plan);
+    }
     return FBS_OK;
     FBS_GUARD_END
 }
@@ -769,6 +788,7 @@ fbs_status fbs_plan_sums(fbs_plan *plan, double *num_trip, double *num_quad, dou
         FBS_CUDA(cudaMemcpyAsync(sumsq, plan->d_sumsq, plan->nbins * sizeof(double), cudaMemcpyDefault,
                                  plan->stream));
     FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    check_device_errors(*plan);
     return FBS_OK;
     FBS_GUARD_END
 }
