@@ -187,7 +187,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("FBS_BENCH_PRECISION", "fp32"))
+    ap.add_argument("--precision", default=os.environ.get("FBS_BENCH_PRECISION", "bf16x3"))
     ap.add_argument("--N", type=int, default=N_GRID)
     ap.add_argument("--nb", type=int, default=NB_B)
     ap.add_argument("--nbt", type=int, default=NB_T)
@@ -234,7 +234,7 @@ def main():
     eB, eT = edges(N, args.nb), edges(N, args.nbt)
     t0 = time.perf_counter()
     planB = fbs.Plan(N, L_BOX, eB, precision=args.precision, timing=True, stream=stream)
-    planT = fbs.Plan(N, L_BOX, eT, precision="fp32", trispectrum=True, timing=True, stream=stream)
+    planT = fbs.Plan(N, L_BOX, eT, precision=args.precision, trispectrum=True, timing=True, stream=stream)
     plan_s = time.perf_counter() - t0
     B = torch.empty(planB.ntrip, dtype=torch.float64, device=dev)
     P = torch.empty(planB.nbins, dtype=torch.float64, device=dev)
@@ -319,7 +319,7 @@ def main():
             "dtype": {"fp32": "f32", "bf16x3": "bf16x3", "bf16": "bf16"}[args.precision],
             "data": "synthetic", "config": dict(workload(args), ntrip_B=planB.ntrip,
                                                 nquad_T=planT.nquad, precision_B=args.precision,
-                                                precision_T="fp32", parallelism="replicas%d" % world),
+                                                precision_T=args.precision, parallelism="replicas%d" % world),
             "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
             "plan_s": plan_s, "count_margin": [planB.count_margin, planT.count_margin],
             "quad_counts_exact": planT.quad_counts_exact,
@@ -380,9 +380,14 @@ def roofline(top, planB, planT, N, pk, pk_src, clocks):
         out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None,
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (derived)" % sm_mhz})
-    elif cls == "contract_tc":
-        npairs = len({(int(a[1]), int(a[2])) for a in plan.triplets})
-        flops = (2 * plan.ntrip + npairs) * pts_per_launch
+    elif cls in ("contract_tc", "contract_quad_tc"):
+        if cls == "contract_tc":
+            npairs = len({(int(a[1]), int(a[2])) for a in plan.triplets})
+            flops = (2 * plan.ntrip + npairs) * pts_per_launch
+        else:
+            npairs = len({(int(q[2]), int(q[3])) for q in plan.quads})
+            ninner = len({(int(q[0]), int(q[1])) for q in plan.quads})
+            flops = (2 * plan.nquad + npairs + ninner) * pts_per_launch
         ach = flops / (per_launch_ms * 1e-3) / 1e12
         out.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
                     "frac": ach / bf16, "traffic": None,

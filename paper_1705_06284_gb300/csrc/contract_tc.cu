@@ -35,20 +35,29 @@ constexpr int KC = 64;              // points per chunk (one 128-byte swizzle ro
 constexpr int kStageLd = KC + 4;    // staged row stride in floats (bank spread)
 constexpr long long kWaitCycles = 2000000000LL;
 
+constexpr int kMaxInner = 256;       // operand-B rows (N of the MMA) at most
+
+// One outer pair (rows of operand A) and the inner rows it closes with.
 struct TcPair {
     int b, c, first, pad;
-    unsigned mask[4];  // bits of the single bins a closing a triplet with (b, c)
+    unsigned mask[kMaxInner / 32];  // bit n: inner row n closes a polygon with (b, c)
+};
+
+// One contraction: outer pairs x inner rows.  Inner row n is the single bin
+// in0[n] (in1[n] < 0, bispectrum) or the pair product in0[n] x in1[n]
+// (trispectrum).
+struct TcJob {
+    TcPair *d_pairs = nullptr;
+    int2 *d_inner = nullptr;
+    int npairs = 0, ntiles = 0, ninner = 0, Npad = 0, maxloc = 0;
+    std::vector<int> grp;  // tile ranges of the CTA groups
+    int *d_grp = nullptr;
+    bool built = false, usable = false;
 };
 
 struct TcState {
-    TcPair *d_pairs = nullptr;
+    TcJob trip, quad;
     int *d_err = nullptr;
-    int npairs = 0;
-    int ntiles = 0;
-    std::vector<int> grp;  // tile ranges of the CTA groups
-    int *d_grp = nullptr;
-    int maxloc = 0;
-    int Npad = 0;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -167,7 +176,8 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM (smem).
 __global__ void __launch_bounds__(kThreads, 1)
     contract_tc_kernel(const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
-                       int Npad, const TcPair *__restrict__ pairs, int npairs,
+                       int Npad, int ninner, const int2 *__restrict__ inner,
+                       const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
                        int *__restrict__ err) {
@@ -183,11 +193,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int p_first = t0 * 128;
     const int p_last = min(npairs, t1 * 128);  // exclusive
     const int it0 = pairs[p_first].first;
-    const int nloc = (p_last > p_first)
-                         ? (pairs[p_last - 1].first + __popc(pairs[p_last - 1].mask[0]) +
-                            __popc(pairs[p_last - 1].mask[1]) + __popc(pairs[p_last - 1].mask[2]) +
-                            __popc(pairs[p_last - 1].mask[3]) - it0)
-                         : 0;
+    int nloc = 0;
+    if (p_last > p_first) {
+        nloc = pairs[p_last - 1].first - it0;
+#pragma unroll
+        for (int w = 0; w < kMaxInner / 32; ++w) nloc += __popc(pairs[p_last - 1].mask[w]);
+    }
 
     // ---- carve shared memory (1024-B aligned operand tiles first)
     uintptr_t base = reinterpret_cast<uintptr_t>(smraw);
@@ -220,11 +231,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     for (int i = tid; i < nloc; i += kThreads) acc[i] = 0.0;
-    // padding rows of B (bins >= nbins) stay zero
+    // padding rows of B (rows >= ninner) stay zero
     for (int i = tid; i < 4 * b_tile / 16; i += kThreads) {
         int buf = i / (b_tile / 16), o = i - buf * (b_tile / 16);
         int row = (o * 16) / 128;
-        if (row >= nbins) reinterpret_cast<uint4 *>(sm + 4 * a_tile + buf * b_tile)[o] = make_uint4(0, 0, 0, 0);
+        if (row >= ninner) reinterpret_cast<uint4 *>(sm + 4 * a_tile + buf * b_tile)[o] = make_uint4(0, 0, 0, 0);
     }
     tc_fence_before();
     __syncthreads();
@@ -275,10 +286,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         wait_commit(gcount - 2);
         {
             const float *st = stage + s * stage_floats;
-            for (int u = tid; u < nbins * 8; u += kThreads) {
-                int row = u % nbins, j = u / nbins;
-                const float4 *src = reinterpret_cast<const float4 *>(st + row * kStageLd + 8 * j);
+            for (int u = tid; u < ninner * 8; u += kThreads) {
+                int row = u % ninner, j = u / ninner;
+                const int2 in = inner[row];
+                const float4 *src = reinterpret_cast<const float4 *>(st + in.x * kStageLd + 8 * j);
                 float4 v0 = src[0], v1 = src[1];
+                if (in.y >= 0) {  // inner pair product
+                    const float4 *s2 = reinterpret_cast<const float4 *>(st + in.y * kStageLd + 8 * j);
+                    float4 w0 = s2[0], w1 = s2[1];
+                    v0 = make_float4(v0.x * w0.x, v0.y * w0.y, v0.z * w0.z, v0.w * w0.w);
+                    v1 = make_float4(v1.x * w1.x, v1.y * w1.y, v1.z * w1.z, v1.w * w1.w);
+                }
                 float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                 uint4 h, l;
                 split8(v, h, l);
@@ -360,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int a = c8 + i;
-                        if (a >= 128) continue;
+                        if (a >= kMaxInner) continue;
                         const unsigned w = pi.mask[a >> 5];
                         const unsigned bit = 1u << (a & 31);
                         if (!(w & bit)) continue;
@@ -398,76 +416,120 @@ static size_t tc_smem_bytes(int nbins, int Npad, int nloc) {
 }
 
 static TcState &tc_state(Plan &p) {
-    if (p.tc) return *reinterpret_cast<TcState *>(p.tc);
-    TcState *st = new TcState();
-    p.tc = st;
-    const TaskList &t = p.ttask;
-    st->npairs = t.npairs;
-    st->ntiles = (t.npairs + 127) / 128;
-    st->Npad = std::max(16, ((p.nbins + 15) / 16) * 16);
+    if (!p.tc) {
+        TcState *st = new TcState();
+        p.tc = st;
+        st->d_err = (int *)p.dalloc(sizeof(int));
+        FBS_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(int), p.stream));
+    }
+    return *reinterpret_cast<TcState *>(p.tc);
+}
+
+// Build the device tables of one contraction from its pair-grouped task list.
+static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
+    job.built = true;
+    job.npairs = t.npairs;
+    job.ntiles = (t.npairs + 127) / 128;
+    // inner rows: single bins, or the distinct inner pairs of the quadruplets
+    std::vector<int2> inner;
+    std::vector<int> row_of;  // (a, b) -> inner row, a*nbins+b
+    if (!quads) {
+        for (int b = 0; b < p.nbins; ++b) inner.push_back(make_int2(b, -1));
+    } else {
+        row_of.assign((size_t)p.nbins * p.nbins, -1);
+        for (int e = 0; e < t.nitems; ++e) {
+            int key = t.ia[e] * p.nbins + t.ib[e];
+            if (row_of[key] < 0) row_of[key] = 0;
+        }
+        for (int a = 0; a < p.nbins; ++a)
+            for (int b = 0; b < p.nbins; ++b)
+                if (row_of[a * p.nbins + b] >= 0) {
+                    row_of[a * p.nbins + b] = (int)inner.size();
+                    inner.push_back(make_int2(a, b));
+                }
+    }
+    job.ninner = (int)inner.size();
+    if (job.ninner > kMaxInner || job.npairs == 0) return;  // not usable on the tensor cores
+    job.Npad = std::max(16, ((job.ninner + 15) / 16) * 16);
     std::vector<TcPair> hp(std::max(1, t.npairs));
     for (int i = 0; i < t.npairs; ++i) {
         TcPair q{};
         q.b = t.pb[i];
         q.c = t.pc[i];
         q.first = t.pstart[i];
-        for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e) q.mask[t.ia[e] >> 5] |= 1u << (t.ia[e] & 31);
+        int prev = -1;
+        for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e) {
+            int n = quads ? row_of[t.ia[e] * p.nbins + t.ib[e]] : t.ia[e];
+            if (n <= prev) throw Failure{FBS_ERR_ARG, "tensor-core task list not sorted by inner row"};
+            prev = n;
+            q.mask[n >> 5] |= 1u << (n & 31);
+        }
         hp[i] = q;
     }
     // groups of tiles: tensor memory (512 columns) and the FP64 item sums bound a group
     const size_t smem_cap = 220 * 1024;
-    st->grp.assign(1, 0);
+    job.grp.assign(1, 0);
     int cur_tiles = 0, cur_items = 0;
-    st->maxloc = 0;
-    for (int tt = 0; tt < st->ntiles; ++tt) {
+    job.maxloc = 0;
+    for (int tt = 0; tt < job.ntiles; ++tt) {
         int pa = tt * 128, pe = std::min(t.npairs, pa + 128);
         int items = t.pstart[pe] - t.pstart[pa];
-        bool fits = (cur_tiles + 1) * st->Npad <= 512 &&
-                    tc_smem_bytes(p.nbins, st->Npad, cur_items + items) <= smem_cap;
+        bool fits = (cur_tiles + 1) * job.Npad <= 512 &&
+                    tc_smem_bytes(p.nbins, job.Npad, cur_items + items) <= smem_cap;
         if (cur_tiles > 0 && !fits) {
-            st->grp.push_back(tt);
-            st->maxloc = std::max(st->maxloc, cur_items);
+            job.grp.push_back(tt);
+            job.maxloc = std::max(job.maxloc, cur_items);
             cur_tiles = 0;
             cur_items = 0;
         }
         cur_tiles += 1;
         cur_items += items;
     }
-    st->maxloc = std::max(st->maxloc, cur_items);
-    st->grp.push_back(st->ntiles);
-    if (tc_smem_bytes(p.nbins, st->Npad, st->maxloc) > smem_cap)
-        throw Failure{FBS_ERR_ARG, "tensor-core contraction: a pair tile needs more shared memory than available"};
-    st->d_pairs = (TcPair *)p.dalloc(hp.size() * sizeof(TcPair));
-    FBS_CUDA(cudaMemcpyAsync(st->d_pairs, hp.data(), hp.size() * sizeof(TcPair), cudaMemcpyHostToDevice,
+    job.maxloc = std::max(job.maxloc, cur_items);
+    job.grp.push_back(job.ntiles);
+    if (tc_smem_bytes(p.nbins, job.Npad, job.maxloc) > smem_cap) return;
+    job.d_pairs = (TcPair *)p.dalloc(hp.size() * sizeof(TcPair));
+    FBS_CUDA(cudaMemcpyAsync(job.d_pairs, hp.data(), hp.size() * sizeof(TcPair), cudaMemcpyHostToDevice,
                              p.stream));
-    st->d_grp = (int *)p.dalloc(st->grp.size() * sizeof(int));
-    FBS_CUDA(cudaMemcpyAsync(st->d_grp, st->grp.data(), st->grp.size() * sizeof(int),
+    job.d_inner = (int2 *)p.dalloc(inner.size() * sizeof(int2));
+    FBS_CUDA(cudaMemcpyAsync(job.d_inner, inner.data(), inner.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                             p.stream));
+    job.d_grp = (int *)p.dalloc(job.grp.size() * sizeof(int));
+    FBS_CUDA(cudaMemcpyAsync(job.d_grp, job.grp.data(), job.grp.size() * sizeof(int),
                              cudaMemcpyHostToDevice, p.stream));
-    st->d_err = (int *)p.dalloc(sizeof(int));
-    FBS_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(int), p.stream));
-    return *st;
+    job.usable = true;
 }
 
 int *tc_error_flag(Plan &p) { return p.tc ? reinterpret_cast<TcState *>(p.tc)->d_err : nullptr; }
 
-void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride) {
-    const TaskList &t = p.ttask;
-    if (t.nitems == 0) return;
-    if (p.nbins > 128) throw Failure{FBS_ERR_ARG, "tensor-core contraction supports up to 128 bins"};
+bool tc_quads_usable(Plan &p) {
     TcState &st = tc_state(p);
-    const int ngrp = (int)st.grp.size() - 1;
+    if (!st.quad.built) build_job(p, p.qtask, true, st.quad);
+    return st.quad.usable;
+}
+
+void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads) {
+    const TaskList &t = quads ? p.qtask : p.ttask;
+    if (t.nitems == 0) return;
+    TcState &st = tc_state(p);
+    TcJob &job = quads ? st.quad : st.trip;
+    if (!job.built) build_job(p, t, quads, job);
+    if (!job.usable)
+        throw Failure{FBS_ERR_ARG, "tensor-core contraction: more than 256 inner rows or shared memory exceeded"};
+    const int ngrp = (int)job.grp.size() - 1;
     int sms = 0, dev = 0;
     FBS_CUDA(cudaGetDevice(&dev));
     FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int G = std::max(1, sms / ngrp);
     if (G > p.part_blocks) G = p.part_blocks;
-    const size_t sm = tc_smem_bytes(p.nbins, st.Npad, st.maxloc);
-    KTimer tm(p, KC_CONTRACT_TC);
+    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc);
+    KTimer tm(p, quads ? KC_QUAD_TC : KC_CONTRACT_TC);
     FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid(G, ngrp);
     contract_tc_kernel<<<grid, kThreads, sm, p.stream>>>(
-        islab, slab_stride, npts, p.nbins, st.Npad, st.d_pairs, st.npairs, st.d_grp, p.d_tout,
-        t.nitems, p.d_tpart, p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
+        islab, slab_stride, npts, p.nbins, job.Npad, job.ninner, job.d_inner, job.d_pairs, job.npairs,
+        job.d_grp, quads ? p.d_qout : p.d_tout, t.nitems, quads ? p.d_qpart : p.d_tpart,
+        p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
     FBS_CUDA(cudaGetLastError());
 }
 

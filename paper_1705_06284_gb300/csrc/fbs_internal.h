@@ -80,6 +80,7 @@ enum KernelClass {
     KC_CONTRACT,
     KC_CONTRACT_TC,
     KC_QUAD,
+    KC_QUAD_TC,
     KC_REDUCE,
     KC_COUNT,
     KC_NUM
@@ -102,7 +103,8 @@ void launch_count_contraction(Plan &p, const double *noct, int nb_in_group, int 
 // contract.cu
 void launch_contract_fp32(Plan &p, const float *islab, long long npts, long long slab_stride,
                           bool quads);
-void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride);
+void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads);
+bool tc_quads_usable(Plan &p);
 void launch_reduce_and_normalise(Plan &p, bool quads);
 void zero_partials(Plan &p, bool quads);
 std::vector<int> item_groups(const TaskList &t, int cap);

@@ -557,11 +557,18 @@ static void run_field(Plan &p, const float *field, bool quads) {
         launch_inverse_yz_slab(p, x0, nx, p.d_I);
         const long long npts = (long long)nx * plane;
         const long long stride = (long long)p.slab * plane;
-        if (p.precision == FBS_PREC_FP32)
-            launch_contract_fp32(p, p.d_I, npts, stride, false);
+        const bool tc = p.precision != FBS_PREC_FP32;
+        if (tc)
+            launch_contract_tc(p, p.d_I, npts, stride, false);
         else
-            launch_contract_tc(p, p.d_I, npts, stride);
-        if (quads) launch_contract_fp32(p, p.d_I, npts, stride, true);
+            launch_contract_fp32(p, p.d_I, npts, stride, false);
+        if (quads) {
+            // quadruplets on the tensor cores when the inner pairs fit one MMA (N <= 256)
+            if (tc && tc_quads_usable(p))
+                launch_contract_tc(p, p.d_I, npts, stride, true);
+            else
+                launch_contract_fp32(p, p.d_I, npts, stride, true);
+        }
     }
     launch_reduce_and_normalise(p, quads);
 }
@@ -607,9 +614,10 @@ int fbs_version(void) { return 100; }
 
 const char *fbs_last_error(void) { return g_last_error.c_str(); }
 
-static const char *kClassNames[KC_NUM] = {"fwd_z",   "fwd_y",       "fwd_x", "inv_x",
-                                          "inv_y",   "inv_z",       "contract_fp32",
-                                          "contract_tc", "contract_quad", "reduce", "count"};
+static const char *kClassNames[KC_NUM] = {"fwd_z",         "fwd_y",          "fwd_x",  "inv_x",
+                                          "inv_y",         "inv_z",          "contract_fp32",
+                                          "contract_tc",   "contract_quad",  "contract_quad_tc",
+                                          "reduce",        "count"};
 
 int fbs_num_kernel_classes(void) { return KC_NUM; }
 

@@ -83,3 +83,31 @@ def test_bf16x3_deterministic_and_host_buffers():
         Bh, Ph = run(plan, f32, device=False)
         Bd2, _ = run(plan, f32, device=True)
         assert np.array_equal(Bd, Bh) and np.array_equal(Bd, Bd2)
+
+
+@pytest.mark.parametrize("N,nb,kind", [(16, 4, "lin"), (32, 6, "log"), (48, 8, "lin")])
+def test_trispectrum_bf16x3_matches_oracle(N, nb, kind):
+    """Quadruplets as a Gram of pair products on the tensor cores."""
+    import torch
+    L = 60.0
+    edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
+    f32 = _field("bubbles", N, 13).astype(np.float32)
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=True) as plan:
+        T, B, P = plan.trispectrum(torch.from_numpy(f32).cuda())
+        torch.cuda.synchronize()
+        T, B, P = T.cpu().numpy(), B.cpu().numpy(), P.cpu().numpy()
+        check_bispectrum(plan, B, P, f32, L, edges, "bf16x3")
+        g = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=[], quads=plan.quads)
+        assert plan.quad_counts_exact
+        assert np.array_equal(plan.N_quad, g["N_quad"])
+        # gate as for B: enough quadruples and |T| not lost in cancellation
+        f64 = f32.astype(np.float64)
+        D = oracle.spectrum(f64)
+        bins = oracle.bin_index(N, oracle.thresholds(edges, L))
+        I = {b: oracle.shell_field(D, bins, b) for b in set(plan.quads.ravel().tolist())}
+        mag = np.array([np.sum(np.abs(I[a] * I[b] * I[c] * I[d])) for a, b, c, d in plan.quads])
+        keep = (plan.N_quad >= 100) & (np.abs(g["qnum"]) >= 1e-3 * mag)
+        r = rel_err(T, g["T"])
+        assert keep.sum() > 0
+        assert np.all(r[keep] < 2e-4), float(r[keep].max())
+    print("T N=%d quads %d gated %d max %.2e" % (N, len(T), keep.sum(), r[keep].max()))
