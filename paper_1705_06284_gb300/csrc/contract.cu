@@ -134,14 +134,21 @@ __global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, in
     out[i] = s;
 }
 
-// out[j] = sum_r part[j][r] in a fixed order (deterministic).
-__global__ void reduce_cols_kernel(const double *__restrict__ part, int rows, int n,
-                                   double *__restrict__ out) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
+// out[j] = sum_r part[j][r]: one block per j, strided partial sums then a
+// fixed-shape tree (deterministic for a given launch shape).
+__global__ void __launch_bounds__(256) reduce_cols_kernel(const double *__restrict__ part, int rows,
+                                                          double *__restrict__ out) {
+    __shared__ double red[256];
+    const int j = blockIdx.x;
     double s = 0.0;
-    for (int r = 0; r < rows; ++r) s += part[(long long)j * rows + r];
-    out[j] = s;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += part[(long long)j * rows + r];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = red[0];
 }
 
 // ------------------------------------------------------------------ normalise
@@ -317,8 +324,7 @@ void launch_reduce_and_normalise(Plan &p, bool quads) {
         }
         {
             const int rows = p.N * zstage_row_groups(p.N);
-            reduce_cols_kernel<<<(p.nbins + 127) / 128, 128, 0, p.stream>>>(p.d_sumsq_part, rows, p.nbins,
-                                                                             p.d_sumsq);
+            reduce_cols_kernel<<<p.nbins, 256, 0, p.stream>>>(p.d_sumsq_part, rows, p.d_sumsq);
             FBS_CUDA(cudaGetLastError());
         }
         int ntrip = (int)p.ntri.size(), nquad = quads ? (int)p.nquad.size() : 0;
