@@ -179,6 +179,37 @@ int fbs_plan_quad_counts_exact(const fbs_plan *plan);
 /* Device bytes owned by the plan. */
 int64_t fbs_plan_device_bytes(const fbs_plan *plan);
 
+/*
+ * fbs_triple_sums_noalloc -- num[t] = sum_{p < npts} f_a[p] f_b[p] f_c[p] for
+ * (a, b, c) = abc[3t..3t+2], without allocating any device memory.
+ *
+ * The paper has no counterpart: this is for callers that already hold real
+ * fields on the device (for instance shell fields made by their own code) and
+ * cannot call cudaMalloc, because their device memory belongs to another
+ * allocator that must account for every byte, or because the process reserves
+ * all device memory up front.  The caller passes every input and output; the
+ * per-block FP64 partial sums live in a static device array of 152 x 4096
+ * doubles (4.75 MiB) that each GPU loading the library holds until exit.
+ *   fields    : device FP32, nfields fields, field i at fields + i*bin_stride.
+ *   nfields   : >= 1; triplet entries outside [0, nfields) give NaN sums.
+ *   bin_stride: elements between fields (>= npts).
+ *   npts      : points summed per field.
+ *   abc       : device int32[3*ntrip].
+ *   ntrip     : 0 <= ntrip <= 4096 (larger: FBS_ERR_ARG, nothing launched).
+ *   num       : device double[ntrip], written (FP32 products in runs of 64
+ *               terms, FP64 across runs and blocks, fixed reduction order).
+ *   cuda_stream: stream of both launches (NULL = legacy default stream).
+ * Asynchronous on the stream.  The first call on a device looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one scratch array, which keeps the last call's partials: calls that
+ * overlap on the GPU (different streams, different host threads) race, so
+ * serialise them.  Returns FBS_OK, FBS_ERR_ARG or FBS_ERR_CUDA.
+ */
+fbs_status fbs_triple_sums_noalloc(const float *fields, int nfields, long long bin_stride,
+                                   long long npts, const int32_t *abc, int ntrip, double *num,
+                                   void *cuda_stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *fbs_last_error(void);
 

@@ -74,6 +74,8 @@ _SIGS = [
     ("fbs_plan_device_bytes", ctypes.c_int64, [_vp]),
     ("fbs_plan_count_margin", ctypes.c_double, [_vp]),
     ("fbs_plan_quad_counts_exact", ctypes.c_int, [_vp]),
+    ("fbs_triple_sums_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
+                                                _vp, ctypes.c_int, _vp, _vp]),
     ("fbs_last_error", ctypes.c_char_p, []),
     ("fbs_version", ctypes.c_int, []),
 ]
@@ -127,6 +129,12 @@ def fbs_bispectrum(h, field_ptr, B_ptr, P_ptr):
 def fbs_trispectrum(h, field_ptr, T_ptr, B_ptr, P_ptr):
     _check(lib().fbs_trispectrum(_vp(h), _vp(field_ptr), _vp(T_ptr or 0), _vp(B_ptr or 0),
                                  _vp(P_ptr or 0)))
+
+
+def fbs_triple_sums_noalloc(fields_ptr, nfields, bin_stride, npts, abc_ptr, ntrip, num_ptr, stream=None):
+    """sum_p f_a f_b f_c per triplet with no device allocation (see fbs.h)."""
+    _check(lib().fbs_triple_sums_noalloc(_vp(fields_ptr), int(nfields), int(bin_stride), int(npts),
+                                         _vp(abc_ptr), int(ntrip), _vp(num_ptr), _vp(stream or 0)))
 
 
 # ---------------------------------------------------------------- convenience
