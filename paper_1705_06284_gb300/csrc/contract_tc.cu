@@ -30,7 +30,6 @@ namespace fbs {
 
 namespace {
 
-constexpr int kThreads = 256;
 constexpr int KC = 64;              // points per chunk (one 128-byte swizzle row of BF16)
 constexpr int kStageLd = KC + 4;    // staged row stride in floats (bank spread)
 constexpr long long kWaitCycles = 2000000000LL;
@@ -49,7 +48,7 @@ struct TcPair {
 struct TcJob {
     TcPair *d_pairs = nullptr;
     int2 *d_inner = nullptr;
-    int npairs = 0, ntiles = 0, ninner = 0, Npad = 0, maxloc = 0;
+    int npairs = 0, ntiles = 0, ninner = 0, Npad = 0, maxloc = 0, maxtiles = 0;
     std::vector<int> grp;  // tile ranges of the CTA groups
     int *d_grp = nullptr;
     bool built = false, usable = false;
@@ -173,25 +172,76 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
 
 }  // namespace
 
-// grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM (smem).
-__global__ void __launch_bounds__(kThreads, 1)
+// Warp roles: warps 0..7 produce (stage the fields, write operand B to
+// shared memory, form the pair products into tensor memory, flush the
+// accumulators); warp 8 allocates tensor memory and one of its threads issues
+// every MMA.  Hand-offs go through mbarriers, never through __syncthreads.
+constexpr int kProdWarps = 8;
+constexpr int kTcThreads = (kProdWarps + 1) * 32;
+constexpr int kAStages = 2;
+constexpr int kAStageCols = 64;  // 32 columns hi + 32 columns lo (64 BF16 per row each)
+
+struct TcBars {
+    uint64_t full[kAStages], empty[kAStages], bfull[2], bempty[2], accr, accf;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that gives up at once after any other wait of the CTA timed
+// out (the abort flag is sticky), so no role can strand another.
+__device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *err, int code) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitCycles) {
+            *abort_flag = 1;
+            atomicExch(err, code);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
+__global__ void __launch_bounds__(kTcThreads, 1)
     contract_tc_kernel(const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
-                       int Npad, int ninner, const int2 *__restrict__ inner,
+                       int Npad, int tstride, int ninner, const int2 *__restrict__ inner,
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
                        int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ uint64_t bars[2];
+    __shared__ TcBars bars;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g = blockIdx.y;
     const int t0 = grp_tile0[g], t1 = grp_tile0[g + 1];
-    const int ntl = t1 - t0;  // tiles of this group
+    const int ntl = t1 - t0;
     const int p_first = t0 * 128;
-    const int p_last = min(npairs, t1 * 128);  // exclusive
+    const int p_last = min(npairs, t1 * 128);
     const int it0 = pairs[p_first].first;
     int nloc = 0;
     if (p_last > p_first) {
@@ -200,98 +250,147 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int w = 0; w < kMaxInner / 32; ++w) nloc += __popc(pairs[p_last - 1].mask[w]);
     }
 
-    // ---- carve shared memory (1024-B aligned operand tiles first)
-    uintptr_t base = reinterpret_cast<uintptr_t>(smraw);
-    base = (base + 1023) & ~(uintptr_t)1023;
+    // ---- shared memory: B tiles (1024-aligned), staged fields, FP64 sums, pair bins
+    uintptr_t base = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023;
     unsigned char *sm = reinterpret_cast<unsigned char *>(base);
-    const int a_tile = 128 * 128;            // bytes of one 128-row operand tile
-    const int b_tile = Npad * 128;           // bytes of one Npad-row operand tile
-    // operand tiles: Ah[2], Al[2] (pair products), Bh[2], Bl[2] (single bins)
-    unsigned char *const Ah0 = sm, *const Al0 = sm + 2 * a_tile;
-    unsigned char *const Bh0 = sm + 4 * a_tile, *const Bl0 = sm + 4 * a_tile + 2 * b_tile;
-    float *stage = reinterpret_cast<float *>(sm + 4 * a_tile + 4 * b_tile);
+    const int b_tile = Npad * 128;
+    unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_tile;
+    float *stage = reinterpret_cast<float *>(sm + 4 * b_tile);
     const int stage_floats = nbins * kStageLd;
     double *acc = reinterpret_cast<double *>(stage + 2 * stage_floats);
+    int2 *pbc = reinterpret_cast<int2 *>(acc + nloc);  // (b, c) of every row of every tile
 
-    const int tmem_cols_needed = ntl * Npad;
+    const int acc_cols = ((ntl * tstride + 31) / 32) * 32;
+    const int tmem_cols_needed = acc_cols + kAStages * kAStageCols;
     int ncols = 32;
     while (ncols < tmem_cols_needed) ncols <<= 1;
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int i = 0; i < kAStages; ++i) {
+            mbar_init(&bars.full[i], kProdWarps);
+            mbar_init(&bars.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bars.bfull[i], kProdWarps);
+            mbar_init(&bars.bempty[i], 1);
+        }
+        mbar_init(&bars.accr, 1);
+        mbar_init(&bars.accf, kProdWarps);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
-    if (warp == 0) {
+    if (warp == kProdWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
                      "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < nloc; i += kThreads) acc[i] = 0.0;
-    // padding rows of B (rows >= ninner) stay zero
-    for (int i = tid; i < 4 * b_tile / 16; i += kThreads) {
-        int buf = i / (b_tile / 16), o = i - buf * (b_tile / 16);
-        int row = (o * 16) / 128;
-        if (row >= ninner) reinterpret_cast<uint4 *>(sm + 4 * a_tile + buf * b_tile)[o] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < nloc; i += kTcThreads) acc[i] = 0.0;
+    for (int i = tid; i < ntl * 128; i += kTcThreads) {
+        const int p = p_first + i;
+        pbc[i] = p < npairs ? make_int2(pairs[p].b, pairs[p].c) : make_int2(-1, -1);
+    }
+    for (int i = tid; i < 4 * b_tile / 16; i += kTcThreads) {  // padding rows of B stay zero
+        int o = i % (b_tile / 16);
+        if ((o * 16) / 128 >= ninner) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    volatile int *abortp = &abort_flag;
 
     const long long nchunks = (npts + KC - 1) / KC;
     const long long c0 = nchunks * blockIdx.x / gridDim.x;
     const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
-    const uint32_t idesc = idesc_bf16(128, Npad);
 
-    // stage a chunk: nbins rows of KC floats (16-B cp.async, zero fill past npts)
-    auto prefetch = [&](long long ch, int s) {
-        const long long q0 = ch * KC;
-        float *dst = stage + s * stage_floats;
-        for (int i = tid; i < nbins * (KC / 4); i += kThreads) {
-            int b = i / (KC / 4), k4 = i - b * (KC / 4);
-            long long q = q0 + 4LL * k4;
-            long long rem = npts - q;
-            int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
-            const float *src = bytes ? (I + b * bin_stride + q) : I;
-            cp_async16(smem_u32(dst + b * kStageLd + 4 * k4), src, bytes);
+    if (warp == kProdWarps) {
+        // ================= MMA issuer (one thread) =================
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, Npad);
+            long long gA = 0, gB = 0, nfl = 0;
+            bool fresh = true;
+            int since = 0;
+            for (long long ci = c0; ci < c1; ++ci) {
+                const int sb = (int)(gB & 1);
+                const bool okb = role_wait(&bars.bfull[sb], (uint32_t)((gB >> 1) & 1), abortp, err, 11);
+                const uint32_t bh = smem_u32(Bh0 + sb * b_tile), bl = smem_u32(Bl0 + sb * b_tile);
+                for (int lt = 0; lt < ntl; ++lt) {
+                    const int as = (int)(gA % kAStages);
+                    const bool oka = role_wait(&bars.full[as], (uint32_t)((gA / kAStages) & 1), abortp, err, 12);
+                    tc_fence_after();
+                    if (okb && oka && !*abortp) {
+                        const uint32_t d = tmem + (uint32_t)(lt * tstride);
+                        const uint32_t ah = tmem + (uint32_t)(acc_cols + as * kAStageCols);
+                        const uint32_t al = ah + 32u;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t ko = 32u * k;
+                            mma_bf16_ts(d, ah + 8u * k, sdesc_sw128(bh + ko), idesc, (fresh && k == 0) ? 0u : 1u);
+                            if (x3) {
+                                mma_bf16_ts(d, ah + 8u * k, sdesc_sw128(bl + ko), idesc, 1u);
+                                mma_bf16_ts(d, al + 8u * k, sdesc_sw128(bh + ko), idesc, 1u);
+                            }
+                        }
+                    }
+                    mma_commit(&bars.empty[as]);
+                    ++gA;
+                }
+                mma_commit(&bars.bempty[sb]);
+                ++gB;
+                fresh = false;
+                if (++since == flush_every || ci == c1 - 1) {
+                    mma_commit(&bars.accr);
+                    role_wait(&bars.accf, (uint32_t)(nfl & 1), abortp, err, 13);
+                    tc_fence_after();
+                    ++nfl;
+                    fresh = true;
+                    since = 0;
+                }
+            }
+            // drain: every MMA complete before tensor memory is released (own limit)
+            if (gA > 0) {
+                const int as = (int)((gA - 1) % kAStages);
+                if (!mbar_wait(&bars.empty[as], (uint32_t)(((gA - 1) / kAStages) & 1))) atomicExch(err, 14);
+            }
         }
-        cp_async_commit();
-    };
-
-    long long gcount = 0;  // tiles issued so far (commit number)
-    bool ok = true;
-    auto wait_commit = [&](long long n) {
-        if (n < 0 || !ok) return;
-        if (!mbar_wait(&bars[n & 1], (uint32_t)((n >> 1) & 1))) {
-            ok = false;
-            atomicExch(err, 1);
-            abort_flag = 1;
-        }
-    };
-
-    if (c0 < c1) prefetch(c0, 0);
-    bool fresh = true;
-    int since_flush = 0;
-    for (long long ci = c0; ci < c1; ++ci) {
-        const int s = (int)((ci - c0) & 1);
-        cp_async_wait_all();
-        __syncthreads();
-        if (abort_flag) break;
-        if (ci + 1 < c1) prefetch(ci + 1, s ^ 1);
-        // B buffer s was last read by the MMAs of chunk ci-2: covered by commit gcount-2
-        wait_commit(gcount - 2);
-        {
+    } else {
+        // ================= producers (warps 0..7) =================
+        const int q = warp & 3, kh = warp >> 2;
+        const int r = 32 * q + lane;  // operand-A row (TMEM lane) of this thread
+        const int ptid = tid;         // 0..255
+        auto prefetch = [&](long long ch, int s) {
+            const long long q0 = ch * KC;
+            float *dst = stage + s * stage_floats;
+            for (int i = ptid; i < nbins * (KC / 4); i += kProdWarps * 32) {
+                int b = i / (KC / 4), k4 = i - b * (KC / 4);
+                long long qq = q0 + 4LL * k4;
+                long long rem = npts - qq;
+                int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+                const float *src = bytes ? (I + b * bin_stride + qq) : I;
+                cp_async16(smem_u32(dst + b * kStageLd + 4 * k4), src, bytes);
+            }
+            cp_async_commit();
+        };
+        long long gA = 0, gB = 0, nfl = 0;
+        int since = 0;
+        if (c0 < c1) prefetch(c0, 0);
+        for (long long ci = c0; ci < c1; ++ci) {
+            const int s = (int)((ci - c0) & 1);
+            cp_async_wait_all();
+            asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
+            if (ci + 1 < c1) prefetch(ci + 1, s ^ 1);
             const float *st = stage + s * stage_floats;
-            for (int u = tid; u < ninner * 8; u += kThreads) {
+            // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
+            const int sb = (int)(gB & 1);
+            if (gB >= 2) role_wait(&bars.bempty[sb], (uint32_t)(((gB - 2) >> 1) & 1), abortp, err, 21);
+            for (int u = ptid; u < ninner * 8; u += kProdWarps * 32) {
                 int row = u % ninner, j = u / ninner;
                 const int2 in = inner[row];
                 const float4 *src = reinterpret_cast<const float4 *>(st + in.x * kStageLd + 8 * j);
                 float4 v0 = src[0], v1 = src[1];
-                if (in.y >= 0) {  // inner pair product
+                if (in.y >= 0) {
                     const float4 *s2 = reinterpret_cast<const float4 *>(st + in.y * kStageLd + 8 * j);
                     float4 w0 = s2[0], w1 = s2[1];
                     v0 = make_float4(v0.x * w0.x, v0.y * w0.y, v0.z * w0.z, v0.w * w0.w);
@@ -301,119 +400,103 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint4 h, l;
                 split8(v, h, l);
                 uint32_t off = sw128_off(row, j);
-                *reinterpret_cast<uint4 *>(Bh0 + s * b_tile + off) = h;
-                *reinterpret_cast<uint4 *>(Bl0 + s * b_tile + off) = l;
-            }
-        }
-        for (int lt = 0; lt < ntl; ++lt) {
-            const int ab = (int)(gcount & 1);
-            wait_commit(gcount - 2);
-            // pair products of tile t0+lt: thread owns row r, K groups j = jb, jb+2, ..
-            {
-                const float *st = stage + s * stage_floats;
-                const int r = tid & 127;
-                const int p = (t0 + lt) * 128 + r;
-                int b = 0, c = 0;
-                const bool valid = p < npairs;
-                if (valid) {
-                    b = pairs[p].b;
-                    c = pairs[p].c;
-                }
-                for (int j = tid >> 7; j < 8; j += 2) {
-                    uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
-                    if (valid) {
-                        const float4 *rb = reinterpret_cast<const float4 *>(st + b * kStageLd + 8 * j);
-                        const float4 *rc = reinterpret_cast<const float4 *>(st + c * kStageLd + 8 * j);
-                        float4 b0 = rb[0], b1 = rb[1], e0 = rc[0], e1 = rc[1];
-                        float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
-                                      b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
-                        split8(v, h, l);
-                    }
-                    uint32_t off = sw128_off(r, j);
-                    *reinterpret_cast<uint4 *>(Ah0 + ab * a_tile + off) = h;
-                    *reinterpret_cast<uint4 *>(Al0 + ab * a_tile + off) = l;
-                }
+                *reinterpret_cast<uint4 *>(Bh0 + sb * b_tile + off) = h;
+                *reinterpret_cast<uint4 *>(Bl0 + sb * b_tile + off) = l;
             }
             fence_proxy_async_smem();
-            __syncthreads();
-            if (abort_flag) break;
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(lt * Npad);
-                const uint32_t ah = smem_u32(Ah0 + ab * a_tile), al = smem_u32(Al0 + ab * a_tile);
-                const uint32_t bh = smem_u32(Bh0 + s * b_tile), bl = smem_u32(Bl0 + s * b_tile);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t ko = 32u * k;
-                    mma_bf16(d, sdesc_sw128(ah + ko), sdesc_sw128(bh + ko), idesc, (fresh && k == 0) ? 0u : 1u);
-                    if (x3) {
-                        mma_bf16(d, sdesc_sw128(ah + ko), sdesc_sw128(bl + ko), idesc, 1u);
-                        mma_bf16(d, sdesc_sw128(al + ko), sdesc_sw128(bh + ko), idesc, 1u);
-                    }
-                }
-                mma_commit(&bars[ab]);
-            }
-            ++gcount;
-        }
-        if (abort_flag) break;
-        fresh = false;
-        ++since_flush;
-        if (since_flush == flush_every || ci == c1 - 1) {
-            // all MMAs done -> read the accumulators, add to the FP64 sums
-            wait_commit(gcount - 1);
-            __syncthreads();
-            if (abort_flag) break;
-            tc_fence_after();
-            const int q = warp & 3, h = warp >> 2;
-            const int r = 32 * q + lane;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.bfull[sb]);
+            ++gB;
+            // ---- operand A: pair products of this thread's row, 32 points, into TMEM
             for (int lt = 0; lt < ntl; ++lt) {
-                const int p = (t0 + lt) * 128 + r;
-                const bool valid = p < npairs;
-                TcPair pi;
-                if (valid) pi = pairs[p];
-                for (int c8 = 8 * h; c8 < Npad; c8 += 16) {
-                    float v[8];
-                    tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * Npad + c8), v);
-                    if (!valid) continue;
+                const int as = (int)(gA % kAStages);
+                if (gA >= kAStages)
+                    role_wait(&bars.empty[as], (uint32_t)(((gA - kAStages) / kAStages) & 1), abortp, err, 22);
+                tc_fence_after();
+                const int2 bc = pbc[lt * 128 + r];
+                uint32_t hw[16], lw[16];
+                if (bc.x >= 0) {
+                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + 32 * kh);
+                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + 32 * kh);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const int a = c8 + i;
-                        if (a >= kMaxInner) continue;
-                        const unsigned w = pi.mask[a >> 5];
-                        const unsigned bit = 1u << (a & 31);
-                        if (!(w & bit)) continue;
-                        int idx = pi.first - it0;
-                        for (int m = 0; m < (a >> 5); ++m) idx += __popc(pi.mask[m]);
-                        idx += __popc(w & (bit - 1u));
-                        acc[idx] += (double)v[i];
+                    for (int j = 0; j < 4; ++j) {
+                        float4 b0 = rb[2 * j], b1 = rb[2 * j + 1], e0 = rc[2 * j], e1 = rc[2 * j + 1];
+                        float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
+                                      b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
+                        uint4 h, l;
+                        split8(v, h, l);
+                        hw[4 * j + 0] = h.x; hw[4 * j + 1] = h.y; hw[4 * j + 2] = h.z; hw[4 * j + 3] = h.w;
+                        lw[4 * j + 0] = l.x; lw[4 * j + 1] = l.y; lw[4 * j + 2] = l.z; lw[4 * j + 3] = l.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) hw[j] = lw[j] = 0u;
+                }
+                const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
+                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + 16 * kh);
+                tmem_st16(lanebase + col, hw);
+                tmem_st16(lanebase + col + 32u, lw);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.full[as]);
+                ++gA;
+            }
+            // ---- flush: accumulators -> FP64 sums
+            if (++since == flush_every || ci == c1 - 1) {
+                role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 23);
+                tc_fence_after();
+                if (!*abortp) {
+                    for (int lt = 0; lt < ntl; ++lt) {
+                        const int p = (t0 + lt) * 128 + r;
+                        const bool valid = p < npairs;
+                        TcPair pi;
+                        if (valid) pi = pairs[p];
+                        for (int c8 = 8 * kh; c8 < Npad; c8 += 16) {
+                            float v[8];
+                            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
+                            if (!valid) continue;
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                const int a = c8 + i;
+                                if (a >= kMaxInner) continue;
+                                const unsigned w = pi.mask[a >> 5];
+                                const unsigned bit = 1u << (a & 31);
+                                if (!(w & bit)) continue;
+                                int idx = pi.first - it0;
+                                for (int m = 0; m < (a >> 5); ++m) idx += __popc(pi.mask[m]);
+                                idx += __popc(w & (bit - 1u));
+                                acc[idx] += (double)v[i];
+                            }
+                        }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.accf);
+                ++nfl;
+                since = 0;
             }
-            tc_fence_before();
-            __syncthreads();
-            fresh = true;
-            since_flush = 0;
         }
+        cp_async_wait_all();
     }
-    // make sure no MMA is still in flight before the tensor memory goes away
-    if (gcount > 0) {
-        if (tid == 0 && !mbar_wait(&bars[(gcount - 1) & 1], (uint32_t)(((gcount - 1) >> 1) & 1))) atomicExch(err, 2);
-    }
-    cp_async_wait_all();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0)
+    if (warp == kProdWarps)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     double *row = part + (long long)blockIdx.x * nitems_total;
-    for (int i = tid; i < nloc; i += kThreads) row[iout[it0 + i]] += acc[i];
+    for (int i = tid; i < nloc; i += kTcThreads) row[iout[it0 + i]] += acc[i];
 }
 
 // ------------------------------------------------------------------ host side
-static size_t tc_smem_bytes(int nbins, int Npad, int nloc) {
-    return 1024 + 4 * 128 * 128 + 4 * (size_t)Npad * 128 + 2 * (size_t)nbins * kStageLd * 4 +
-           (size_t)nloc * 8;
+static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl) {
+    size_t b = 1024 + 4 * (size_t)Npad * 128 + 2 * (size_t)nbins * kStageLd * 4 + (size_t)nloc * 8 +
+               (size_t)ntl * 128 * 8;
+    return std::max<size_t>(b, 116 * 1024);  // > half the SM's shared memory: one CTA per SM
 }
+
+static int tile_stride(int Npad) { return ((Npad + 31) / 32) * 32; }
 
 static TcState &tc_state(Plan &p) {
     if (!p.tc) {
@@ -474,8 +557,9 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     for (int tt = 0; tt < job.ntiles; ++tt) {
         int pa = tt * 128, pe = std::min(t.npairs, pa + 128);
         int items = t.pstart[pe] - t.pstart[pa];
-        bool fits = (cur_tiles + 1) * job.Npad <= 512 &&
-                    tc_smem_bytes(p.nbins, job.Npad, cur_items + items) <= smem_cap;
+        const int acc_cols = (((cur_tiles + 1) * tile_stride(job.Npad) + 31) / 32) * 32;
+        bool fits = acc_cols + kAStages * kAStageCols <= 512 &&
+                    tc_smem_bytes(p.nbins, job.Npad, cur_items + items, cur_tiles + 1) <= smem_cap;
         if (cur_tiles > 0 && !fits) {
             job.grp.push_back(tt);
             job.maxloc = std::max(job.maxloc, cur_items);
@@ -487,7 +571,11 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     }
     job.maxloc = std::max(job.maxloc, cur_items);
     job.grp.push_back(job.ntiles);
-    if (tc_smem_bytes(p.nbins, job.Npad, job.maxloc) > smem_cap) return;
+    job.maxtiles = 0;
+    for (size_t gi = 0; gi + 1 < job.grp.size(); ++gi)
+        job.maxtiles = std::max(job.maxtiles, job.grp[gi + 1] - job.grp[gi]);
+    if (tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles) > smem_cap) return;
+    if ((((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32 + kAStages * kAStageCols > 512) return;
     job.d_pairs = (TcPair *)p.dalloc(hp.size() * sizeof(TcPair));
     FBS_CUDA(cudaMemcpyAsync(job.d_pairs, hp.data(), hp.size() * sizeof(TcPair), cudaMemcpyHostToDevice,
                              p.stream));
@@ -522,12 +610,13 @@ void launch_contract_tc(Plan &p, const float *islab, long long npts, long long s
     FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int G = std::max(1, sms / ngrp);
     if (G > p.part_blocks) G = p.part_blocks;
-    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc);
+    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles);
     KTimer tm(p, quads ? KC_QUAD_TC : KC_CONTRACT_TC);
     FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid(G, ngrp);
-    contract_tc_kernel<<<grid, kThreads, sm, p.stream>>>(
-        islab, slab_stride, npts, p.nbins, job.Npad, job.ninner, job.d_inner, job.d_pairs, job.npairs,
+    contract_tc_kernel<<<grid, kTcThreads, sm, p.stream>>>(
+        islab, slab_stride, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner,
+        job.d_pairs, job.npairs,
         job.d_grp, quads ? p.d_qout : p.d_tout, t.nitems, quads ? p.d_qpart : p.d_tpart,
         p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
     FBS_CUDA(cudaGetLastError());

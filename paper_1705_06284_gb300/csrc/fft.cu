@@ -330,9 +330,136 @@ __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t
     }
 }
 
+
+// ------------------------------------------------------------------ fast z stage
+// Compile-time radix-8 C2R for power-of-two N (64..512): N/8 threads per
+// complex line (two real rows), stage-0 inputs straight from G into registers,
+// radix-8/4 butterflies in registers, exchanges through a shared-memory line
+// padded by one slot per 8 (conflict-free for the stride-8 writes of the first
+// stage), and the last stage's outputs straight to global memory in natural
+// order (coalesced).
+__host__ __device__ constexpr int zpad(int i) { return i + (i >> 3); }
+
+template <int N, int R, int Ns, bool LAST>
+__device__ __forceinline__ void zfast_stage(float2 *__restrict__ buf, int t,
+                                            const float2 *__restrict__ tw, float *__restrict__ o0,
+                                            float *__restrict__ o1, bool w0, bool w1, double &acc) {
+    constexpr int T = N / 8;
+    constexpr int NB = N / R;       // butterflies per line
+    constexpr int PER = NB / T;     // butterflies per thread
+    float2 v[PER][R];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + T * u;
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[u][q] = buf[zpad(j + q * NB)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int j = t + T * u;
+        const int k = j % Ns;
+        if (Ns > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) v[u][q] = cmulc(v[u][q], tw[k * q * (N / (Ns * R))]);
+        }
+        dftR<+1, float, R>(v[u]);
+        if (!LAST) {
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) buf[zpad(base + q * Ns)] = v[u][q];
+        } else {
+            // Ns * R == N, so k == j and the outputs are j + q Ns
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int z = j + q * Ns;
+                if (w0) { o0[z] = v[u][q].x; acc += (double)(v[u][q].x * v[u][q].x); }
+                if (w1) { o1[z] = v[u][q].y; acc += (double)(v[u][q].y * v[u][q].y); }
+            }
+        }
+    }
+    if (!LAST) __syncthreads();
+}
+
+template <int N, int R1, int R2>
+__global__ void __launch_bounds__(256) inv_z_fast_kernel(const float2 *__restrict__ G,
+                                                         const BinGeom *__restrict__ geom, int x0,
+                                                         float *__restrict__ out, long long out_bin_stride,
+                                                         double *__restrict__ sumsq_part,
+                                                         const float2 *__restrict__ tw) {
+    constexpr int T = N / 8;
+    constexpr int L = 256 / T;  // complex lines (row pairs) per CTA
+    constexpr int NP = zpad(N - 1) + 1;
+    __shared__ float2 buf[L * NP];
+    __shared__ double red[8];
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const int bl = blockIdx.z;
+    const BinGeom g = geom[bl];
+    const int xl = blockIdx.y;
+    const int y = (blockIdx.x * L + line) * 2;
+    float *ob = out + (long long)bl * out_bin_stride;
+    float *o0 = ob + ((long long)xl * N + y) * N;
+    float *o1 = o0 + N;
+    const bool w0 = y < N, w1 = y + 1 < N;
+    double acc = 0.0;
+    if (g.empty) {
+        for (int z = t; z < N; z += T) {
+            if (w0) o0[z] = 0.f;
+            if (w1) o1[z] = 0.f;
+        }
+    } else {
+        const float2 *in0 = G + g.G_off + ((long long)xl * N + y) * g.Dzb;
+        const float2 *in1 = in0 + g.Dzb;
+        const int R = g.Dzb - 1;  // highest mz held (<= N/2)
+        // stage 0 (radix 8, Ns = 1): inputs n = t + q T of the packed line
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int n = t + q * T;
+            float2 h1 = make_float2(0.f, 0.f), h2 = make_float2(0.f, 0.f);
+            int m = -1;
+            bool cj = false;
+            if (n <= R) m = n;
+            else if (n >= N - R) { m = N - n; cj = true; }
+            if (m >= 0) {
+                if (w0) h1 = in0[m];
+                if (w1) h2 = in1[m];
+                if (m == 0 || 2 * m == N) { h1.y = 0.f; h2.y = 0.f; }
+                if (cj) { h1.y = -h1.y; h2.y = -h2.y; }
+            }
+            v[q] = make_float2(h1.x - h2.y, h1.y + h2.x);  // H1 + i H2
+        }
+        dftR<+1, float, 8>(v);
+        float2 *lb = buf + line * NP;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) lb[zpad(8 * t + q)] = v[q];
+        __syncthreads();
+        if constexpr (R2 == 0) {
+            zfast_stage<N, R1, 8, true>(lb, t, tw, o0, o1, w0, w1, acc);
+        } else {
+            zfast_stage<N, R1, 8, false>(lb, t, tw, o0, o1, w0, w1, acc);
+            zfast_stage<N, R2, 8 * R1, true>(lb, t, tw, o0, o1, w0, w1, acc);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        sumsq_part[((long long)bl * N + x0 + xl) * gridDim.x + blockIdx.x] = s;
+    }
+}
+
 // ------------------------------------------------------------------ host side
+static bool zfast_ok(int N) { return N == 64 || N == 128 || N == 256 || N == 512; }
+
 // Row groups per plane of the FP32 z stage (one sum-of-squares partial each).
 int zstage_row_groups(int N) {
+    if (zfast_ok(N)) {
+        const int L = 256 / (N / 8);
+        return (N + 2 * L - 1) / (2 * L);
+    }
     const int nl = lines_per_cta<float>(N);
     return (N + 2 * nl - 1) / (2 * nl);
 }
@@ -426,7 +553,18 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
         k<<<grid, kThreads, sm, p.stream>>>(p.d_A, p.d_geom, 0, N, x0, p.d_G, 0, nl, p.fN, p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
-    {
+    if (zfast_ok(N) && !getenv("FBS_GENERIC_Z")) {
+        KTimer t(p, KC_INV_Z);
+        dim3 grid(zstage_row_groups(N), nx, p.nbins);
+        const long long obs = (long long)p.slab * N * N;
+        switch (N) {
+            case 64: inv_z_fast_kernel<64, 8, 0><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
+            case 128: inv_z_fast_kernel<128, 4, 4><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
+            case 256: inv_z_fast_kernel<256, 8, 4><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
+            default: inv_z_fast_kernel<512, 8, 8><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
+        }
+        FBS_CUDA(cudaGetLastError());
+    } else {
         KTimer t(p, KC_INV_Z);
         auto k = inv_z_kernel<float, false>;
         allow_smem(k, sm);
