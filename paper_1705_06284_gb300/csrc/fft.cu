@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t
     }
     __syncthreads();
     C *res = smem_fft<T, +1>(a, b, nl, ld, f, tw);
-    double acc = 0.0;
+    T tacc = T(0);  // per-thread squares in the working precision, FP64 across threads
     if (!OCT) {
         for (int i = threadIdx.x; i < nl * 2 * N; i += blockDim.x) {
             int r = i / N, z = i - r * N;
@@ -307,8 +307,9 @@ __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t
             C v = res[(r >> 1) * ld + z];
             T val = (r & 1) ? v.y : v.x;
             ob[((long long)xl * N + y) * N + z] = val;
-            acc += (double)(val * val);
+            tacc += val * val;
         }
+        double acc = (double)tacc;
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
         __syncthreads();
@@ -343,7 +344,7 @@ __host__ __device__ constexpr int zpad(int i) { return i + (i >> 3); }
 template <int N, int R, int Ns, bool LAST>
 __device__ __forceinline__ void zfast_stage(float2 *__restrict__ buf, int t,
                                             const float2 *__restrict__ tw, float *__restrict__ o0,
-                                            float *__restrict__ o1, bool w0, bool w1, double &acc) {
+                                            float *__restrict__ o1, bool w0, bool w1, float &acc) {
     constexpr int T = N / 8;
     constexpr int NB = N / R;       // butterflies per line
     constexpr int PER = NB / T;     // butterflies per thread
@@ -373,8 +374,8 @@ __device__ __forceinline__ void zfast_stage(float2 *__restrict__ buf, int t,
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int z = j + q * Ns;
-                if (w0) { o0[z] = v[u][q].x; acc += (double)(v[u][q].x * v[u][q].x); }
-                if (w1) { o1[z] = v[u][q].y; acc += (double)(v[u][q].y * v[u][q].y); }
+                if (w0) { o0[z] = v[u][q].x; acc = fmaf(v[u][q].x, v[u][q].x, acc); }
+                if (w1) { o1[z] = v[u][q].y; acc = fmaf(v[u][q].y, v[u][q].y, acc); }
             }
         }
     }
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(256) inv_z_fast_kernel(const float2 *__restric
     float *o0 = ob + ((long long)xl * N + y) * N;
     float *o1 = o0 + N;
     const bool w0 = y < N, w1 = y + 1 < N;
-    double acc = 0.0;
+    float acc = 0.f;  // <= 16 squares per thread; FP64 from the warp sum on
     if (g.empty) {
         for (int z = t; z < N; z += T) {
             if (w0) o0[z] = 0.f;
@@ -441,8 +442,9 @@ __global__ void __launch_bounds__(256) inv_z_fast_kernel(const float2 *__restric
             zfast_stage<N, R2, 8 * R1, true>(lb, t, tw, o0, o1, w0, w1, acc);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    double dacc = (double)acc;
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dacc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
