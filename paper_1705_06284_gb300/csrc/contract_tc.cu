@@ -176,9 +176,9 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
 // shared memory, form the pair products into tensor memory, flush the
 // accumulators); warp 8 allocates tensor memory and one of its threads issues
 // every MMA.  Hand-offs go through mbarriers, never through __syncthreads.
-constexpr int kProdWarps = 8;
+constexpr int kProdWarps = 16;   // 4 per TMEM lane quarter, each 16 of the 64 points of a row
 constexpr int kTcThreads = (kProdWarps + 1) * 32;
-constexpr int kAStages = 2;
+constexpr int kAStages = 3;      // maximum; the launch picks 2 or 3 to fit tensor memory
 constexpr int kAStageCols = 64;  // 32 columns hi + 32 columns lo (64 BF16 per row each)
 
 struct TcBars {
@@ -191,10 +191,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // Bounded wait that gives up at once after any other wait of the CTA timed
 // out (the abort flag is sticky), so no role can strand another.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           int *err, int code) {
     long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
+    while (!mbar_try_wait_sleep(bar, parity)) {
         if (*abort_flag) return false;
         if (clock64() - t0 > kWaitCycles) {
             *abort_flag = 1;
@@ -205,12 +216,10 @@ __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volati
     return true;
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-            taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+        "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
         : "memory");
 }
 
@@ -230,9 +239,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
-                       int *__restrict__ err) {
+                       int nst, int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ TcBars bars;
+    __shared__ int2 s_inner[kMaxInner];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int2 *pbc = reinterpret_cast<int2 *>(acc + nloc);  // (b, c) of every row of every tile
 
     const int acc_cols = ((ntl * tstride + 31) / 32) * 32;
-    const int tmem_cols_needed = acc_cols + kAStages * kAStageCols;
+    const int tmem_cols_needed = acc_cols + nst * kAStageCols;
     int ncols = 32;
     while (ncols < tmem_cols_needed) ncols <<= 1;
 
@@ -287,6 +297,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     for (int i = tid; i < nloc; i += kTcThreads) acc[i] = 0.0;
+    for (int i = tid; i < ninner; i += kTcThreads) s_inner[i] = inner[i];
     for (int i = tid; i < ntl * 128; i += kTcThreads) {
         const int p = p_first + i;
         pbc[i] = p < npairs ? make_int2(pairs[p].b, pairs[p].c) : make_int2(-1, -1);
@@ -317,8 +328,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const bool okb = role_wait(&bars.bfull[sb], (uint32_t)((gB >> 1) & 1), abortp, err, 11);
                 const uint32_t bh = smem_u32(Bh0 + sb * b_tile), bl = smem_u32(Bl0 + sb * b_tile);
                 for (int lt = 0; lt < ntl; ++lt) {
-                    const int as = (int)(gA % kAStages);
-                    const bool oka = role_wait(&bars.full[as], (uint32_t)((gA / kAStages) & 1), abortp, err, 12);
+                    const int as = (int)(gA % nst);
+                    const bool oka = role_wait(&bars.full[as], (uint32_t)((gA / nst) & 1), abortp, err, 12);
                     tc_fence_after();
                     if (okb && oka && !*abortp) {
                         const uint32_t d = tmem + (uint32_t)(lt * tstride);
@@ -351,15 +362,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             // drain: every MMA complete before tensor memory is released (own limit)
             if (gA > 0) {
-                const int as = (int)((gA - 1) % kAStages);
-                if (!mbar_wait(&bars.empty[as], (uint32_t)(((gA - 1) / kAStages) & 1))) atomicExch(err, 14);
+                const int as = (int)((gA - 1) % nst);
+                if (!mbar_wait(&bars.empty[as], (uint32_t)(((gA - 1) / nst) & 1))) atomicExch(err, 14);
             }
         }
     } else {
         // ================= producers (warps 0..7) =================
-        const int q = warp & 3, kh = warp >> 2;
-        const int r = 32 * q + lane;  // operand-A row (TMEM lane) of this thread
-        const int ptid = tid;         // 0..255
+        const int q = warp & 3, kq = warp >> 2;  // lane quarter, 16-point slice of the chunk
+        const int r = 32 * q + lane;             // operand-A row (TMEM lane) of this thread
+        const int ptid = tid;                    // 0 .. 32*kProdWarps-1
         auto prefetch = [&](long long ch, int s) {
             const long long q0 = ch * KC;
             float *dst = stage + s * stage_floats;
@@ -387,7 +398,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (gB >= 2) role_wait(&bars.bempty[sb], (uint32_t)(((gB - 2) >> 1) & 1), abortp, err, 21);
             for (int u = ptid; u < ninner * 8; u += kProdWarps * 32) {
                 int row = u % ninner, j = u / ninner;
-                const int2 in = inner[row];
+                const int2 in = s_inner[row];
                 const float4 *src = reinterpret_cast<const float4 *>(st + in.x * kStageLd + 8 * j);
                 float4 v0 = src[0], v1 = src[1];
                 if (in.y >= 0) {
@@ -409,17 +420,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ++gB;
             // ---- operand A: pair products of this thread's row, 32 points, into TMEM
             for (int lt = 0; lt < ntl; ++lt) {
-                const int as = (int)(gA % kAStages);
-                if (gA >= kAStages)
-                    role_wait(&bars.empty[as], (uint32_t)(((gA - kAStages) / kAStages) & 1), abortp, err, 22);
+                const int as = (int)(gA % nst);
+                if (gA >= nst) role_wait(&bars.empty[as], (uint32_t)(((gA - nst) / nst) & 1), abortp, err, 22);
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
-                uint32_t hw[16], lw[16];
+                uint32_t hw[8], lw[8];
                 if (bc.x >= 0) {
-                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + 32 * kh);
-                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + 32 * kh);
+                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + 16 * kq);
+                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + 16 * kq);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < 2; ++j) {
                         float4 b0 = rb[2 * j], b1 = rb[2 * j + 1], e0 = rc[2 * j], e1 = rc[2 * j + 1];
                         float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
                                       b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
@@ -430,12 +440,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) hw[j] = lw[j] = 0u;
+                    for (int j = 0; j < 8; ++j) hw[j] = lw[j] = 0u;
                 }
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
-                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + 16 * kh);
-                tmem_st16(lanebase + col, hw);
-                tmem_st16(lanebase + col + 32u, lw);
+                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + 8 * kq);
+                tmem_st8(lanebase + col, hw);
+                tmem_st8(lanebase + col + 32u, lw);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
@@ -452,7 +462,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const bool valid = p < npairs;
                         TcPair pi;
                         if (valid) pi = pairs[p];
-                        for (int c8 = 8 * kh; c8 < Npad; c8 += 16) {
+                        for (int c8 = 8 * kq; c8 < Npad; c8 += 32) {
                             float v[8];
                             tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
                             if (!valid) continue;
@@ -558,7 +568,7 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
         int pa = tt * 128, pe = std::min(t.npairs, pa + 128);
         int items = t.pstart[pe] - t.pstart[pa];
         const int acc_cols = (((cur_tiles + 1) * tile_stride(job.Npad) + 31) / 32) * 32;
-        bool fits = acc_cols + kAStages * kAStageCols <= 512 &&
+        bool fits = acc_cols + 2 * kAStageCols <= 512 &&
                     tc_smem_bytes(p.nbins, job.Npad, cur_items + items, cur_tiles + 1) <= smem_cap;
         if (cur_tiles > 0 && !fits) {
             job.grp.push_back(tt);
@@ -575,7 +585,7 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     for (size_t gi = 0; gi + 1 < job.grp.size(); ++gi)
         job.maxtiles = std::max(job.maxtiles, job.grp[gi + 1] - job.grp[gi]);
     if (tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles) > smem_cap) return;
-    if ((((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32 + kAStages * kAStageCols > 512) return;
+    if ((((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32 + 2 * kAStageCols > 512) return;
     job.d_pairs = (TcPair *)p.dalloc(hp.size() * sizeof(TcPair));
     FBS_CUDA(cudaMemcpyAsync(job.d_pairs, hp.data(), hp.size() * sizeof(TcPair), cudaMemcpyHostToDevice,
                              p.stream));
@@ -614,11 +624,13 @@ void launch_contract_tc(Plan &p, const float *islab, long long npts, long long s
     KTimer tm(p, quads ? KC_QUAD_TC : KC_CONTRACT_TC);
     FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid(G, ngrp);
+    const int acc_cols_max = (((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32;
+    const int nst = std::min(kAStages, (512 - acc_cols_max) / kAStageCols);
     contract_tc_kernel<<<grid, kTcThreads, sm, p.stream>>>(
         islab, slab_stride, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner,
         job.d_pairs, job.npairs,
         job.d_grp, quads ? p.d_qout : p.d_tout, t.nitems, quads ? p.d_qpart : p.d_tpart,
-        p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
+        p.precision == FBS_PREC_BF16 ? 0 : 1, 16, nst, st.d_err);
     FBS_CUDA(cudaGetLastError());
 }
 

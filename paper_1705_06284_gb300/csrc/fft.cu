@@ -442,9 +442,8 @@ __global__ void __launch_bounds__(256) inv_z_fast_kernel(const float2 *__restric
             zfast_stage<N, R2, 8 * R1, true>(lb, t, tw, o0, o1, w0, w1, acc);
         }
     }
-    double dacc = (double)acc;
-    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dacc;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);  // <= 512 squares
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)acc;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
