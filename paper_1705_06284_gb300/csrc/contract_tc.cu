@@ -176,7 +176,7 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
 // shared memory, form the pair products into tensor memory, flush the
 // accumulators); warp 8 allocates tensor memory and one of its threads issues
 // every MMA.  Hand-offs go through mbarriers, never through __syncthreads.
-constexpr int kProdWarps = 16;   // 4 per TMEM lane quarter, each 16 of the 64 points of a row
+constexpr int kProdWarps = 8;    // 2 per TMEM lane quarter, each 32 of the 64 points of a row
 constexpr int kTcThreads = (kProdWarps + 1) * 32;
 constexpr int kAStages = 3;      // maximum; the launch picks 2 or 3 to fit tensor memory
 constexpr int kAStageCols = 64;  // 32 columns hi + 32 columns lo (64 BF16 per row each)
@@ -216,11 +216,30 @@ __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volati
     return true;
 }
 
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r) {
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
-        "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
         : "memory");
+}
+
+// MMA with a compile-time accumulate flag (no predicate setup in the issue loop).
+template <bool ACC>
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc) {
+    if (ACC)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.eq.u32 p, 1, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "r"(a_tmem), "l"(b), "r"(idesc)
+            : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
@@ -326,7 +345,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (long long ci = c0; ci < c1; ++ci) {
                 const int sb = (int)(gB & 1);
                 const bool okb = role_wait(&bars.bfull[sb], (uint32_t)((gB >> 1) & 1), abortp, err, 11);
-                const uint32_t bh = smem_u32(Bh0 + sb * b_tile), bl = smem_u32(Bl0 + sb * b_tile);
+                const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + sb * b_tile));
+                const uint64_t dbl = sdesc_sw128(smem_u32(Bl0 + sb * b_tile));
                 for (int lt = 0; lt < ntl; ++lt) {
                     const int as = (int)(gA % nst);
                     const bool oka = role_wait(&bars.full[as], (uint32_t)((gA / nst) & 1), abortp, err, 12);
@@ -335,13 +355,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const uint32_t d = tmem + (uint32_t)(lt * tstride);
                         const uint32_t ah = tmem + (uint32_t)(acc_cols + as * kAStageCols);
                         const uint32_t al = ah + 32u;
+                        // descriptors of k-step k: start address field + 2k (32 bytes)
+                        if (fresh) mma_ts<false>(d, ah, dbh, idesc);
+                        else mma_ts<true>(d, ah, dbh, idesc);
+                        if (x3) {
+                            mma_ts<true>(d, ah, dbl, idesc);
+                            mma_ts<true>(d, al, dbh, idesc);
+                        }
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const uint32_t ko = 32u * k;
-                            mma_bf16_ts(d, ah + 8u * k, sdesc_sw128(bh + ko), idesc, (fresh && k == 0) ? 0u : 1u);
+                        for (int k = 1; k < 4; ++k) {
+                            mma_ts<true>(d, ah + 8u * k, dbh + 2u * k, idesc);
                             if (x3) {
-                                mma_bf16_ts(d, ah + 8u * k, sdesc_sw128(bl + ko), idesc, 1u);
-                                mma_bf16_ts(d, al + 8u * k, sdesc_sw128(bh + ko), idesc, 1u);
+                                mma_ts<true>(d, ah + 8u * k, dbl + 2u * k, idesc);
+                                mma_ts<true>(d, al + 8u * k, dbh + 2u * k, idesc);
                             }
                         }
                     }
@@ -368,7 +394,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {
         // ================= producers (warps 0..7) =================
-        const int q = warp & 3, kq = warp >> 2;  // lane quarter, 16-point slice of the chunk
+        const int q = warp & 3, kq = warp >> 2;  // lane quarter, 32-point half of the chunk
         const int r = 32 * q + lane;             // operand-A row (TMEM lane) of this thread
         const int ptid = tid;                    // 0 .. 32*kProdWarps-1
         auto prefetch = [&](long long ch, int s) {
@@ -424,12 +450,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (gA >= nst) role_wait(&bars.empty[as], (uint32_t)(((gA - nst) / nst) & 1), abortp, err, 22);
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
-                uint32_t hw[8], lw[8];
+                uint32_t hw[16], lw[16];
                 if (bc.x >= 0) {
-                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + 16 * kq);
-                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + 16 * kq);
+                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + 32 * kq);
+                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + 32 * kq);
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) {
+                    for (int j = 0; j < 4; ++j) {
                         float4 b0 = rb[2 * j], b1 = rb[2 * j + 1], e0 = rc[2 * j], e1 = rc[2 * j + 1];
                         float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
                                       b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
@@ -440,12 +466,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) hw[j] = lw[j] = 0u;
+                    for (int j = 0; j < 16; ++j) hw[j] = lw[j] = 0u;
                 }
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
-                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + 8 * kq);
-                tmem_st8(lanebase + col, hw);
-                tmem_st8(lanebase + col + 32u, lw);
+                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + 16 * kq);
+                tmem_st16(lanebase + col, hw);
+                tmem_st16(lanebase + col + 32u, lw);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
@@ -462,7 +488,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const bool valid = p < npairs;
                         TcPair pi;
                         if (valid) pi = pairs[p];
-                        for (int c8 = 8 * kq; c8 < Npad; c8 += 32) {
+                        for (int c8 = 8 * kq; c8 < Npad; c8 += 16) {
                             float v[8];
                             tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
                             if (!valid) continue;
