@@ -24,6 +24,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <array>
+
 #include "fbs_internal.h"
 
 namespace fbs {
@@ -54,8 +57,22 @@ struct TcJob {
     bool built = false, usable = false;
 };
 
+struct WideRight {
+    int x, y, first, pad;    // product I_x I_y; index of its first item
+    unsigned long long mask; // bit l: left row l forms an item with this right row
+};
+
+struct WideJob {
+    int nleft = 0, nright = 0, nitems = 0;
+    int2 *d_left = nullptr;
+    WideRight *d_rights = nullptr;
+    int *d_item_out = nullptr;
+    bool built = false, usable = false;
+};
+
 struct TcState {
     TcJob trip, quad;
+    WideJob wtrip, wquad;
     int *d_err = nullptr;
 };
 
@@ -205,7 +222,7 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
 __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           int *err, int code) {
     long long t0 = clock64();
-    while (!mbar_try_wait_sleep(bar, parity)) {
+    while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
         if (clock64() - t0 > kWaitCycles) {
             *abort_flag = 1;
@@ -525,6 +542,253 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int i = tid; i < nloc; i += kTcThreads) row[iout[it0 + i]] += acc[i];
 }
 
+
+// ======================================================================
+// Wide orientation.  The per-instruction cost of tcgen05.mma barely grows
+// with N up to 256 (measured ~130-145 cycles for N = 64..256, M = 128,
+// K = 16), so the operand with the most rows goes to N:
+//   operand A (M = 128, tensor memory): up to 64 "left" rows stacked as
+//       [hi; lo] -- the single bins a (bispectrum) or the outer pairs (c, d)
+//       (trispectrum) -- written once per chunk;
+//   operand B (N <= 256, shared memory): the "right" pair products
+//       (b, c) (bispectrum) or inner pairs (a, b) (trispectrum), split hi/lo;
+//   D[row][right] accumulates hi*(Phi + Plo) in rows 0..63 and
+//   lo*(Phi + Plo) in rows 64..127: every product of the two splits (BF16x4).
+// Groups of 256 right rows go to different CTA rows of the grid.
+// ======================================================================
+
+constexpr int kWideN = 256;
+constexpr int kWideAcol = 256;  // TMEM column of the A stages (after D)
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+struct WideBars {
+    uint64_t full[2], empty[2], accr, accf;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    contract_wide_kernel(const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
+                         int nleft, const int2 *__restrict__ left, const WideRight *__restrict__ rights,
+                         int nright, const int *__restrict__ item_out, int nitems_total,
+                         double *__restrict__ part, int x4, int flush_every, int *__restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ WideBars bars;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    __shared__ int2 s_left[64];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.y * kWideN;
+    const int cnt = min(kWideN, nright - r0);
+    const int Ng = ((cnt + 15) / 16) * 16;
+
+    uintptr_t base = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023;
+    unsigned char *sm = reinterpret_cast<unsigned char *>(base);
+    const int b_tile = kWideN * 128;  // one 256-row operand tile
+    unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_tile;  // [stage] hi, [stage] lo
+    float *stage = reinterpret_cast<float *>(sm + 4 * b_tile);
+    const int stage_floats = nbins * kStageLd;
+    const int ncols = 512;
+
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&bars.full[i], kProdWarps);
+            mbar_init(&bars.empty[i], 1);
+        }
+        mbar_init(&bars.accr, 1);
+        mbar_init(&bars.accf, kProdWarps);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (warp == kProdWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < 64; i += kTcThreads) s_left[i] = i < nleft ? left[i] : make_int2(-1, -1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    volatile int *abortp = &abort_flag;
+
+    const long long nchunks = (npts + KC - 1) / KC;
+    const long long c0 = nchunks * blockIdx.x / gridDim.x;
+    const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
+
+    if (warp == kProdWarps) {
+        // ================= MMA issuer =================
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, Ng);
+            long long g = 0, nfl = 0;
+            bool fresh = true;
+            int since = 0;
+            for (long long ci = c0; ci < c1; ++ci) {
+                const int s = (int)(g & 1);
+                const bool ok = role_wait(&bars.full[s], (uint32_t)((g >> 1) & 1), abortp, err, 31);
+                tc_fence_after();
+                if (ok && !*abortp) {
+                    const uint32_t a = tmem + (uint32_t)(kWideAcol + 32 * s);
+                    const uint64_t dh = sdesc_sw128(smem_u32(Bh0 + s * b_tile));
+                    const uint64_t dl = sdesc_sw128(smem_u32(Bl0 + s * b_tile));
+                    if (fresh) mma_ts<false>(tmem, a, dh, idesc);
+                    else mma_ts<true>(tmem, a, dh, idesc);
+                    if (x4) mma_ts<true>(tmem, a, dl, idesc);
+#pragma unroll
+                    for (int k = 1; k < 4; ++k) {
+                        mma_ts<true>(tmem, a + 8u * k, dh + 2u * k, idesc);
+                        if (x4) mma_ts<true>(tmem, a + 8u * k, dl + 2u * k, idesc);
+                    }
+                }
+                mma_commit(&bars.empty[s]);
+                ++g;
+                fresh = false;
+                if (++since == flush_every || ci == c1 - 1) {
+                    mma_commit(&bars.accr);
+                    role_wait(&bars.accf, (uint32_t)(nfl & 1), abortp, err, 32);
+                    tc_fence_after();
+                    ++nfl;
+                    fresh = true;
+                    since = 0;
+                }
+            }
+            if (g > 0) {
+                const int s = (int)((g - 1) & 1);
+                if (!mbar_wait(&bars.empty[s], (uint32_t)(((g - 1) >> 1) & 1))) atomicExch(err, 34);
+            }
+        }
+    } else {
+        // ================= producers (warps 0..7) =================
+        const int ptid = tid;
+        auto prefetch = [&](long long ch, int s) {
+            const long long q0 = ch * KC;
+            float *dst = stage + s * stage_floats;
+            for (int i = ptid; i < nbins * (KC / 4); i += kProdWarps * 32) {
+                int b = i / (KC / 4), k4 = i - b * (KC / 4);
+                long long qq = q0 + 4LL * k4;
+                long long rem = npts - qq;
+                int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
+                const float *src = bytes ? (I + b * bin_stride + qq) : I;
+                cp_async16(smem_u32(dst + b * kStageLd + 4 * k4), src, bytes);
+            }
+            cp_async_commit();
+        };
+        long long g = 0, nfl = 0;
+        int since = 0;
+        if (c0 < c1) prefetch(c0, 0);
+        for (long long ci = c0; ci < c1; ++ci) {
+            const int s = (int)(g & 1);
+            cp_async_wait_all();
+            asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
+            if (ci + 1 < c1) prefetch(ci + 1, s ^ 1);
+            const float *st = stage + ((ci - c0) & 1) * stage_floats;
+            if (g >= 2) role_wait(&bars.empty[s], (uint32_t)(((g - 2) >> 1) & 1), abortp, err, 41);
+            tc_fence_after();
+            // ---- operand B: right pair products, hi and lo, swizzled K-major
+            for (int u = ptid; u < Ng * 8; u += kProdWarps * 32) {
+                const int rr = u % Ng, j = u / Ng;
+                const int R = r0 + rr;
+                uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
+                if (rr < cnt) {
+                    const WideRight &w = rights[R];
+                    const float4 *rb = reinterpret_cast<const float4 *>(st + w.x * kStageLd + 8 * j);
+                    const float4 *rc = reinterpret_cast<const float4 *>(st + w.y * kStageLd + 8 * j);
+                    float4 b0 = rb[0], b1 = rb[1], e0 = rc[0], e1 = rc[1];
+                    float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
+                                  b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
+                    split8(v, h, l);
+                }
+                const uint32_t off = sw128_off(rr, j);
+                *reinterpret_cast<uint4 *>(Bh0 + s * b_tile + off) = h;
+                *reinterpret_cast<uint4 *>(Bl0 + s * b_tile + off) = l;
+            }
+            fence_proxy_async_smem();
+            // ---- operand A (warps 4..7, one per TMEM lane quarter): left rows hi | lo
+            if (warp >= 4) {
+                const int q = warp & 3;
+                const int r = 32 * q + lane;
+                const int li = r & 63, half = r >> 6;
+                uint32_t words[32];
+                const int2 lf = s_left[li];
+                if (lf.x >= 0 && (half == 0 || x4)) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 *ra = reinterpret_cast<const float4 *>(st + lf.x * kStageLd + 8 * j);
+                        float4 a0 = ra[0], a1 = ra[1];
+                        if (lf.y >= 0) {
+                            const float4 *rb = reinterpret_cast<const float4 *>(st + lf.y * kStageLd + 8 * j);
+                            float4 b0 = rb[0], b1 = rb[1];
+                            a0 = make_float4(a0.x * b0.x, a0.y * b0.y, a0.z * b0.z, a0.w * b0.w);
+                            a1 = make_float4(a1.x * b1.x, a1.y * b1.y, a1.z * b1.z, a1.w * b1.w);
+                        }
+                        float v[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        uint4 h, l;
+                        split8(v, h, l);
+                        const uint4 &o = half ? l : h;
+                        words[4 * j + 0] = o.x; words[4 * j + 1] = o.y; words[4 * j + 2] = o.z; words[4 * j + 3] = o.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) words[j] = 0u;
+                }
+                tmem_st32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kWideAcol + 32 * s), words);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.full[s]);
+            ++g;
+            // ---- flush: D -> FP64 partial rows (hi rows and lo rows to separate rows)
+            if (++since == flush_every || ci == c1 - 1) {
+                role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 42);
+                tc_fence_after();
+                if (!*abortp) {
+                    const int q = warp & 3, kh = warp >> 2;
+                    const int r = 32 * q + lane;
+                    const int li = r & 63, half = r >> 6;
+                    const unsigned long long lbit = 1ULL << li;
+                    double *prow = part + (long long)(2 * blockIdx.x + half) * nitems_total;
+                    for (int c8 = 8 * kh; c8 < Ng; c8 += 16) {
+                        float v[8];
+                        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c8, v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int rr = c8 + i;
+                            if (rr >= cnt) continue;
+                            const WideRight &w = rights[r0 + rr];
+                            if (!(w.mask & lbit)) continue;
+                            const int item = w.first + __popcll(w.mask & (lbit - 1ULL));
+                            prow[item_out[item]] += (double)v[i];
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.accf);
+                ++nfl;
+                since = 0;
+            }
+        }
+        cp_async_wait_all();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kProdWarps)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
 // ------------------------------------------------------------------ host side
 static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl) {
     size_t b = 1024 + 4 * (size_t)Npad * 128 + 2 * (size_t)nbins * kStageLd * 4 + (size_t)nloc * 8 +
@@ -624,10 +888,100 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     job.usable = true;
 }
 
+// Wide orientation tables: left rows (<= 64), right rows, items ordered by
+// (right, left) with their output indices.
+static void build_wide(Plan &p, bool quads, WideJob &w) {
+    w.built = true;
+    const TaskList &t = quads ? p.qtask : p.ttask;
+    if (t.nitems == 0) return;
+    std::vector<int2> left;
+    std::vector<int2> rightbins;
+    // (right, left, out) triples
+    std::vector<std::array<int, 3>> it;
+    if (!quads) {
+        // left = single bins a; right = outer pairs (b, c)
+        for (int b = 0; b < p.nbins; ++b) left.push_back(make_int2(b, -1));
+        for (int i = 0; i < t.npairs; ++i) rightbins.push_back(make_int2(t.pb[i], t.pc[i]));
+        for (int i = 0; i < t.npairs; ++i)
+            for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e) it.push_back({i, t.ia[e], t.iout[e]});
+    } else {
+        // left = outer pairs (c, d); right = distinct inner pairs (a, b)
+        for (int i = 0; i < t.npairs; ++i) left.push_back(make_int2(t.pb[i], t.pc[i]));
+        std::vector<int> ridx((size_t)p.nbins * p.nbins, -1);
+        for (int e = 0; e < t.nitems; ++e) ridx[t.ia[e] * p.nbins + t.ib[e]] = 0;
+        for (int a = 0; a < p.nbins; ++a)
+            for (int b = 0; b < p.nbins; ++b)
+                if (ridx[a * p.nbins + b] >= 0) {
+                    ridx[a * p.nbins + b] = (int)rightbins.size();
+                    rightbins.push_back(make_int2(a, b));
+                }
+        for (int i = 0; i < t.npairs; ++i)
+            for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e)
+                it.push_back({ridx[t.ia[e] * p.nbins + t.ib[e]], i, t.iout[e]});
+    }
+    if ((int)left.size() > 64) return;  // the narrow kernel handles it
+    std::sort(it.begin(), it.end());
+    std::vector<WideRight> R(rightbins.size());
+    for (size_t i = 0; i < rightbins.size(); ++i) {
+        R[i] = WideRight{rightbins[i].x, rightbins[i].y, 0, 0, 0ULL};
+    }
+    std::vector<int> out(it.size());
+    int prev_r = -1;
+    for (size_t k = 0; k < it.size(); ++k) {
+        const int r = it[k][0], l = it[k][1];
+        if (r != prev_r) {
+            R[r].first = (int)k;
+            prev_r = r;
+        }
+        R[r].mask |= 1ULL << l;
+        out[k] = it[k][2];
+    }
+    w.nleft = (int)left.size();
+    w.nright = (int)R.size();
+    w.nitems = (int)it.size();
+    w.d_left = (int2 *)p.dalloc(left.size() * sizeof(int2));
+    FBS_CUDA(cudaMemcpyAsync(w.d_left, left.data(), left.size() * sizeof(int2), cudaMemcpyHostToDevice, p.stream));
+    w.d_rights = (WideRight *)p.dalloc(R.size() * sizeof(WideRight));
+    FBS_CUDA(cudaMemcpyAsync(w.d_rights, R.data(), R.size() * sizeof(WideRight), cudaMemcpyHostToDevice, p.stream));
+    w.d_item_out = (int *)p.dalloc(out.size() * sizeof(int));
+    FBS_CUDA(cudaMemcpyAsync(w.d_item_out, out.data(), out.size() * sizeof(int), cudaMemcpyHostToDevice, p.stream));
+    w.usable = true;
+}
+
+static size_t wide_smem_bytes(int nbins) {
+    return 1024 + 4 * (size_t)kWideN * 128 + 2 * (size_t)nbins * kStageLd * 4;
+}
+
+static bool launch_wide(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads) {
+    if (getenv("FBS_TC_NARROW")) return false;
+    TcState &st = tc_state(p);
+    WideJob &w = quads ? st.wquad : st.wtrip;
+    if (!w.built) build_wide(p, quads, w);
+    if (!w.usable || wide_smem_bytes(p.nbins) > 225 * 1024) return false;
+    const int ngrp = (w.nright + kWideN - 1) / kWideN;
+    int sms = 0, dev = 0;
+    FBS_CUDA(cudaGetDevice(&dev));
+    FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int G = std::max(1, sms / ngrp);
+    if (2 * G > p.part_blocks) G = p.part_blocks / 2;
+    const size_t sm = std::max<size_t>(wide_smem_bytes(p.nbins), 116 * 1024);
+    const TaskList &t = quads ? p.qtask : p.ttask;
+    KTimer tm(p, quads ? KC_QUAD_TC : KC_CONTRACT_TC);
+    FBS_CUDA(cudaFuncSetAttribute(contract_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid(G, ngrp);
+    contract_wide_kernel<<<grid, kTcThreads, sm, p.stream>>>(
+        islab, slab_stride, npts, p.nbins, w.nleft, w.d_left, w.d_rights, w.nright, w.d_item_out, t.nitems,
+        quads ? p.d_qpart : p.d_tpart, p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
+    FBS_CUDA(cudaGetLastError());
+    return true;
+}
+
 int *tc_error_flag(Plan &p) { return p.tc ? reinterpret_cast<TcState *>(p.tc)->d_err : nullptr; }
 
 bool tc_quads_usable(Plan &p) {
     TcState &st = tc_state(p);
+    if (!st.wquad.built) build_wide(p, true, st.wquad);
+    if (st.wquad.usable) return true;
     if (!st.quad.built) build_job(p, p.qtask, true, st.quad);
     return st.quad.usable;
 }
@@ -635,6 +989,7 @@ bool tc_quads_usable(Plan &p) {
 void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads) {
     const TaskList &t = quads ? p.qtask : p.ttask;
     if (t.nitems == 0) return;
+    if (launch_wide(p, islab, npts, slab_stride, quads)) return;
     TcState &st = tc_state(p);
     TcJob &job = quads ? st.quad : st.trip;
     if (!job.built) build_job(p, t, quads, job);
@@ -651,7 +1006,8 @@ void launch_contract_tc(Plan &p, const float *islab, long long npts, long long s
     FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid(G, ngrp);
     const int acc_cols_max = (((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32;
-    const int nst = std::min(kAStages, (512 - acc_cols_max) / kAStageCols);
+    const int nst = 2;  // measured faster than 3 stages
+    (void)acc_cols_max;
     contract_tc_kernel<<<grid, kTcThreads, sm, p.stream>>>(
         islab, slab_stride, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner,
         job.d_pairs, job.npairs,

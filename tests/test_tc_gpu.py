@@ -111,3 +111,25 @@ def test_trispectrum_bf16x3_matches_oracle(N, nb, kind):
         assert keep.sum() > 0
         assert np.all(r[keep] < 2e-4), float(r[keep].max())
     print("T N=%d quads %d gated %d max %.2e" % (N, len(T), keep.sum(), r[keep].max()))
+
+
+@pytest.mark.parametrize("N,nb,quads", [(32, 6, False), (48, 12, False), (32, 6, True)])
+def test_narrow_orientation_still_matches(monkeypatch, N, nb, quads):
+    """The tensor-core kernel with the pair products as operand A (used when
+    more than 64 left rows exist) stays correct when forced."""
+    import torch
+    monkeypatch.setenv("FBS_TC_NARROW", "1")
+    L = 70.0
+    edges = fields.linear_edges(N, L, nb)
+    f32 = _field("lognormal", N, 31).astype(np.float32)
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        if quads:
+            T, B, P = plan.trispectrum(torch.from_numpy(f32).cuda())
+            torch.cuda.synchronize()
+            B, P, T = B.cpu().numpy(), P.cpu().numpy(), T.cpu().numpy()
+            g = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=[], quads=plan.quads)
+            r = rel_err(T, g["T"])
+            assert np.all(r[plan.N_quad >= 100] < 2e-4), float(r.max())
+        else:
+            B, P = run(plan, f32)
+        check_bispectrum(plan, B, P, f32, L, edges, "bf16x3")
