@@ -63,7 +63,7 @@ struct WideRight {
 };
 
 struct WideJob {
-    int nleft = 0, nright = 0, nitems = 0;
+    int nleft = 0, nright = 0, nitems = 0, maxloc = 0;
     int2 *d_left = nullptr;
     WideRight *d_rights = nullptr;
     int *d_item_out = nullptr;
@@ -598,6 +598,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float *stage = reinterpret_cast<float *>(sm + 4 * b_tile);
     const int stage_floats = nbins * kStageLd;
     const int ncols = 512;
+    // items of this group (right rows r0 .. r0+cnt-1): FP32 per-flush sums and
+    // FP64 totals in shared memory, right-row masks cached next to them
+    const int first0 = rights[r0].first;
+    int nloc = rights[r0 + cnt - 1].first + __popcll(rights[r0 + cnt - 1].mask) - first0;
+    double *acc64 = reinterpret_cast<double *>(stage + 2 * stage_floats);
+    float *acc32 = reinterpret_cast<float *>(acc64 + nloc);
+    WideRight *s_r = reinterpret_cast<WideRight *>(acc32 + ((nloc + 3) & ~3));
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
@@ -617,6 +624,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     for (int i = tid; i < 64; i += kTcThreads) s_left[i] = i < nleft ? left[i] : make_int2(-1, -1);
+    for (int i = tid; i < nloc; i += kTcThreads) {
+        acc64[i] = 0.0;
+        acc32[i] = 0.f;
+    }
+    for (int i = tid; i < cnt; i += kTcThreads) s_r[i] = rights[r0 + i];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -698,10 +710,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // ---- operand B: right pair products, hi and lo, swizzled K-major
             for (int u = ptid; u < Ng * 8; u += kProdWarps * 32) {
                 const int rr = u % Ng, j = u / Ng;
-                const int R = r0 + rr;
                 uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
                 if (rr < cnt) {
-                    const WideRight &w = rights[R];
+                    const WideRight &w = s_r[rr];
                     const float4 *rb = reinterpret_cast<const float4 *>(st + w.x * kStageLd + 8 * j);
                     const float4 *rc = reinterpret_cast<const float4 *>(st + w.y * kStageLd + 8 * j);
                     float4 b0 = rb[0], b1 = rb[1], e0 = rc[0], e1 = rc[1];
@@ -749,16 +760,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.full[s]);
             ++g;
-            // ---- flush: D -> FP64 partial rows (hi rows and lo rows to separate rows)
+            // ---- flush: D -> FP32 shared sums (rows li and li+64 add to the same item)
             if (++since == flush_every || ci == c1 - 1) {
                 role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 42);
                 tc_fence_after();
                 if (!*abortp) {
                     const int q = warp & 3, kh = warp >> 2;
                     const int r = 32 * q + lane;
-                    const int li = r & 63, half = r >> 6;
+                    const int li = r & 63;
                     const unsigned long long lbit = 1ULL << li;
-                    double *prow = part + (long long)(2 * blockIdx.x + half) * nitems_total;
                     for (int c8 = 8 * kh; c8 < Ng; c8 += 16) {
                         float v[8];
                         tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c8, v);
@@ -766,10 +776,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int i = 0; i < 8; ++i) {
                             const int rr = c8 + i;
                             if (rr >= cnt) continue;
-                            const WideRight &w = rights[r0 + rr];
-                            if (!(w.mask & lbit)) continue;
-                            const int item = w.first + __popcll(w.mask & (lbit - 1ULL));
-                            prow[item_out[item]] += (double)v[i];
+                            const unsigned long long m = s_r[rr].mask;
+                            if (!(m & lbit)) continue;
+                            atomicAdd(&acc32[s_r[rr].first - first0 + __popcll(m & (lbit - 1ULL))], v[i]);
                         }
                     }
                 }
@@ -778,6 +787,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (lane == 0) mbar_arrive(&bars.accf);
                 ++nfl;
                 since = 0;
+                // every 8 flushes (and at the end) fold the FP32 sums into FP64
+                if ((nfl & 7) == 0 || ci == c1 - 1) {
+                    asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
+                    for (int i = ptid; i < nloc; i += kProdWarps * 32) {
+                        acc64[i] += (double)acc32[i];
+                        acc32[i] = 0.f;
+                    }
+                    asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
+                }
             }
         }
         cp_async_wait_all();
@@ -787,6 +805,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     if (warp == kProdWarps)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    double *prow = part + (long long)blockIdx.x * nitems_total;
+    for (int i = tid; i < nloc; i += kTcThreads) prow[item_out[first0 + i]] += acc64[i];
 }
 
 // ------------------------------------------------------------------ host side
@@ -939,6 +959,11 @@ static void build_wide(Plan &p, bool quads, WideJob &w) {
     w.nleft = (int)left.size();
     w.nright = (int)R.size();
     w.nitems = (int)it.size();
+    for (int r0 = 0; r0 < w.nright; r0 += kWideN) {
+        const int r1 = std::min(w.nright, r0 + kWideN) - 1;
+        const int n = R[r1].first + __builtin_popcountll(R[r1].mask) - R[r0].first;
+        w.maxloc = std::max(w.maxloc, n);
+    }
     w.d_left = (int2 *)p.dalloc(left.size() * sizeof(int2));
     FBS_CUDA(cudaMemcpyAsync(w.d_left, left.data(), left.size() * sizeof(int2), cudaMemcpyHostToDevice, p.stream));
     w.d_rights = (WideRight *)p.dalloc(R.size() * sizeof(WideRight));
@@ -948,8 +973,9 @@ static void build_wide(Plan &p, bool quads, WideJob &w) {
     w.usable = true;
 }
 
-static size_t wide_smem_bytes(int nbins) {
-    return 1024 + 4 * (size_t)kWideN * 128 + 2 * (size_t)nbins * kStageLd * 4;
+static size_t wide_smem_bytes(int nbins, int maxloc) {
+    return 1024 + 4 * (size_t)kWideN * 128 + 2 * (size_t)nbins * kStageLd * 4 + (size_t)maxloc * 12 + 16 +
+           (size_t)kWideN * sizeof(WideRight);
 }
 
 static bool launch_wide(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads) {
@@ -957,14 +983,14 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
     TcState &st = tc_state(p);
     WideJob &w = quads ? st.wquad : st.wtrip;
     if (!w.built) build_wide(p, quads, w);
-    if (!w.usable || wide_smem_bytes(p.nbins) > 225 * 1024) return false;
+    if (!w.usable || wide_smem_bytes(p.nbins, w.maxloc) > 225 * 1024) return false;
     const int ngrp = (w.nright + kWideN - 1) / kWideN;
     int sms = 0, dev = 0;
     FBS_CUDA(cudaGetDevice(&dev));
     FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int G = std::max(1, sms / ngrp);
-    if (2 * G > p.part_blocks) G = p.part_blocks / 2;
-    const size_t sm = std::max<size_t>(wide_smem_bytes(p.nbins), 116 * 1024);
+    if (G > p.part_blocks) G = p.part_blocks;
+    const size_t sm = std::max<size_t>(wide_smem_bytes(p.nbins, w.maxloc), 116 * 1024);
     const TaskList &t = quads ? p.qtask : p.ttask;
     KTimer tm(p, quads ? KC_QUAD_TC : KC_CONTRACT_TC);
     FBS_CUDA(cudaFuncSetAttribute(contract_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
