@@ -575,7 +575,17 @@ struct WideBars {
     uint64_t full[2], empty[2], accr, accf;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+constexpr int kWideProd = 16;  // producer warps of the wide kernel (4 per TMEM lane quarter)
+constexpr int kWideThreads = (kWideProd + 1) * 32;
+
+__device__ __forceinline__ void tmem_st8w(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+        "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kWideThreads, 1)
     contract_wide_kernel(const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
                          int nleft, const int2 *__restrict__ left, const WideRight *__restrict__ rights,
                          int nright, const int *__restrict__ item_out, int nitems_total,
@@ -593,42 +603,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     uintptr_t base = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023;
     unsigned char *sm = reinterpret_cast<unsigned char *>(base);
-    const int b_tile = kWideN * 128;  // one 256-row operand tile
-    unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_tile;  // [stage] hi, [stage] lo
+    const int b_tile = kWideN * 128;
+    unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_tile;
     float *stage = reinterpret_cast<float *>(sm + 4 * b_tile);
     const int stage_floats = nbins * kStageLd;
     const int ncols = 512;
-    // items of this group (right rows r0 .. r0+cnt-1): FP32 per-flush sums and
-    // FP64 totals in shared memory, right-row masks cached next to them
+    // items of this group: FP32 per-flush sums, one per (item, row half): no
+    // two threads ever add to the same word, so the result is deterministic
     const int first0 = rights[r0].first;
-    int nloc = rights[r0 + cnt - 1].first + __popcll(rights[r0 + cnt - 1].mask) - first0;
-    double *acc64 = reinterpret_cast<double *>(stage + 2 * stage_floats);
-    float *acc32 = reinterpret_cast<float *>(acc64 + nloc);
-    WideRight *s_r = reinterpret_cast<WideRight *>(acc32 + ((nloc + 3) & ~3));
+    const int nloc = rights[r0 + cnt - 1].first + __popcll(rights[r0 + cnt - 1].mask) - first0;
+    float *acc32 = stage + 2 * stage_floats;                       // [2][nloc]
+    WideRight *s_r = reinterpret_cast<WideRight *>(acc32 + ((2 * nloc + 3) & ~3));
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&bars.full[i], kProdWarps);
+            mbar_init(&bars.full[i], kWideProd);
             mbar_init(&bars.empty[i], 1);
         }
         mbar_init(&bars.accr, 1);
-        mbar_init(&bars.accf, kProdWarps);
+        mbar_init(&bars.accf, kWideProd);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
-    if (warp == kProdWarps) {
+    if (warp == kWideProd) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
                      "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < 64; i += kTcThreads) s_left[i] = i < nleft ? left[i] : make_int2(-1, -1);
-    for (int i = tid; i < nloc; i += kTcThreads) {
-        acc64[i] = 0.0;
-        acc32[i] = 0.f;
-    }
-    for (int i = tid; i < cnt; i += kTcThreads) s_r[i] = rights[r0 + i];
+    for (int i = tid; i < 64; i += kWideThreads) s_left[i] = i < nleft ? left[i] : make_int2(-1, -1);
+    for (int i = tid; i < 2 * nloc; i += kWideThreads) acc32[i] = 0.f;
+    for (int i = tid; i < cnt; i += kWideThreads) s_r[i] = rights[r0 + i];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -638,8 +644,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const long long nchunks = (npts + KC - 1) / KC;
     const long long c0 = nchunks * blockIdx.x / gridDim.x;
     const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
+    double *prow = part + (long long)blockIdx.x * nitems_total;
 
-    if (warp == kProdWarps) {
+    if (warp == kWideProd) {
         // ================= MMA issuer =================
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(128, Ng);
@@ -681,12 +688,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
     } else {
-        // ================= producers (warps 0..7) =================
+        // ================= producers (warps 0..15) =================
         const int ptid = tid;
+        constexpr int NP = kWideProd * 32;
+        const int q = warp & 3, kq = warp >> 2;  // TMEM lane quarter; 16-point slice of the chunk
+        const int r = 32 * q + lane;             // operand-A row written by this thread
+        const int li = r & 63, half = r >> 6;
         auto prefetch = [&](long long ch, int s) {
             const long long q0 = ch * KC;
             float *dst = stage + s * stage_floats;
-            for (int i = ptid; i < nbins * (KC / 4); i += kProdWarps * 32) {
+            for (int i = ptid; i < nbins * (KC / 4); i += NP) {
                 int b = i / (KC / 4), k4 = i - b * (KC / 4);
                 long long qq = q0 + 4LL * k4;
                 long long rem = npts - qq;
@@ -702,39 +713,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (long long ci = c0; ci < c1; ++ci) {
             const int s = (int)(g & 1);
             cp_async_wait_all();
-            asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(NP) : "memory");
             if (ci + 1 < c1) prefetch(ci + 1, s ^ 1);
-            const float *st = stage + ((ci - c0) & 1) * stage_floats;
+            const float *st = stage + s * stage_floats;
             if (g >= 2) role_wait(&bars.empty[s], (uint32_t)(((g - 2) >> 1) & 1), abortp, err, 41);
             tc_fence_after();
-            // ---- operand B: right pair products, hi and lo, swizzled K-major
-            for (int u = ptid; u < Ng * 8; u += kProdWarps * 32) {
-                const int rr = u % Ng, j = u / Ng;
-                uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
-                if (rr < cnt) {
-                    const WideRight &w = s_r[rr];
-                    const float4 *rb = reinterpret_cast<const float4 *>(st + w.x * kStageLd + 8 * j);
-                    const float4 *rc = reinterpret_cast<const float4 *>(st + w.y * kStageLd + 8 * j);
-                    float4 b0 = rb[0], b1 = rb[1], e0 = rc[0], e1 = rc[1];
-                    float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
-                                  b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
-                    split8(v, h, l);
-                }
-                const uint32_t off = sw128_off(rr, j);
-                *reinterpret_cast<uint4 *>(Bh0 + s * b_tile + off) = h;
-                *reinterpret_cast<uint4 *>(Bl0 + s * b_tile + off) = l;
-            }
-            fence_proxy_async_smem();
-            // ---- operand A (warps 4..7, one per TMEM lane quarter): left rows hi | lo
-            if (warp >= 4) {
-                const int q = warp & 3;
-                const int r = 32 * q + lane;
-                const int li = r & 63, half = r >> 6;
-                uint32_t words[32];
+            // ---- operand A: left row li, points 16kq .. 16kq+15, hi (rows 0..63) or lo (64..127)
+            {
+                uint32_t words[8];
                 const int2 lf = s_left[li];
                 if (lf.x >= 0 && (half == 0 || x4)) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int j = 2 * kq + jj;
                         const float4 *ra = reinterpret_cast<const float4 *>(st + lf.x * kStageLd + 8 * j);
                         float4 a0 = ra[0], a1 = ra[1];
                         if (lf.y >= 0) {
@@ -746,30 +737,47 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         float v[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
                         uint4 h, l;
                         split8(v, h, l);
-                        const uint4 &o = half ? l : h;
-                        words[4 * j + 0] = o.x; words[4 * j + 1] = o.y; words[4 * j + 2] = o.z; words[4 * j + 3] = o.w;
+                        const uint4 o = half ? l : h;
+                        words[4 * jj + 0] = o.x; words[4 * jj + 1] = o.y;
+                        words[4 * jj + 2] = o.z; words[4 * jj + 3] = o.w;
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) words[j] = 0u;
+                    for (int j = 0; j < 8; ++j) words[j] = 0u;
                 }
-                tmem_st32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kWideAcol + 32 * s), words);
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tmem_st8w(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kWideAcol + 32 * s + 8 * kq), words);
             }
+            // ---- operand B: right pair products, hi and lo, swizzled K-major
+            for (int u = ptid; u < Ng * 8; u += NP) {
+                const int rr = u % Ng, j = u / Ng;
+                uint4 h = make_uint4(0, 0, 0, 0), l = make_uint4(0, 0, 0, 0);
+                if (rr < cnt) {
+                    const int2 xy = *reinterpret_cast<const int2 *>(&s_r[rr]);
+                    const float4 *rb = reinterpret_cast<const float4 *>(st + xy.x * kStageLd + 8 * j);
+                    const float4 *rc = reinterpret_cast<const float4 *>(st + xy.y * kStageLd + 8 * j);
+                    float4 b0 = rb[0], b1 = rb[1], e0 = rc[0], e1 = rc[1];
+                    float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
+                                  b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
+                    split8(v, h, l);
+                }
+                const uint32_t off = sw128_off(rr, j);
+                *reinterpret_cast<uint4 *>(Bh0 + s * b_tile + off) = h;
+                *reinterpret_cast<uint4 *>(Bl0 + s * b_tile + off) = l;
+            }
+            fence_proxy_async_smem();
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.full[s]);
             ++g;
-            // ---- flush: D -> FP32 shared sums (rows li and li+64 add to the same item)
+            // ---- flush: D -> FP32 shared sums of (item, half)
             if (++since == flush_every || ci == c1 - 1) {
                 role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 42);
                 tc_fence_after();
                 if (!*abortp) {
-                    const int q = warp & 3, kh = warp >> 2;
-                    const int r = 32 * q + lane;
-                    const int li = r & 63;
                     const unsigned long long lbit = 1ULL << li;
-                    for (int c8 = 8 * kh; c8 < Ng; c8 += 16) {
+                    float *a32 = acc32 + half * nloc;
+                    for (int c8 = 8 * kq; c8 < Ng; c8 += 32) {
                         float v[8];
                         tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c8, v);
 #pragma unroll
@@ -778,7 +786,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             if (rr >= cnt) continue;
                             const unsigned long long m = s_r[rr].mask;
                             if (!(m & lbit)) continue;
-                            atomicAdd(&acc32[s_r[rr].first - first0 + __popcll(m & (lbit - 1ULL))], v[i]);
+                            a32[s_r[rr].first - first0 + __popcll(m & (lbit - 1ULL))] += v[i];
                         }
                     }
                 }
@@ -787,14 +795,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (lane == 0) mbar_arrive(&bars.accf);
                 ++nfl;
                 since = 0;
-                // every 8 flushes (and at the end) fold the FP32 sums into FP64
+                // every 8 flushes (and at the end) add the FP32 sums to the FP64 row
                 if ((nfl & 7) == 0 || ci == c1 - 1) {
-                    asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
-                    for (int i = ptid; i < nloc; i += kProdWarps * 32) {
-                        acc64[i] += (double)acc32[i];
+                    asm volatile("bar.sync 1, %0;" ::"n"(NP) : "memory");
+                    for (int i = ptid; i < nloc; i += NP) {
+                        prow[item_out[first0 + i]] += (double)acc32[i] + (double)acc32[nloc + i];
                         acc32[i] = 0.f;
+                        acc32[nloc + i] = 0.f;
                     }
-                    asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
+                    asm volatile("bar.sync 1, %0;" ::"n"(NP) : "memory");
                 }
             }
         }
@@ -803,10 +812,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kProdWarps)
+    if (warp == kWideProd)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
-    double *prow = part + (long long)blockIdx.x * nitems_total;
-    for (int i = tid; i < nloc; i += kTcThreads) prow[item_out[first0 + i]] += acc64[i];
 }
 
 // ------------------------------------------------------------------ host side
@@ -974,7 +981,7 @@ static void build_wide(Plan &p, bool quads, WideJob &w) {
 }
 
 static size_t wide_smem_bytes(int nbins, int maxloc) {
-    return 1024 + 4 * (size_t)kWideN * 128 + 2 * (size_t)nbins * kStageLd * 4 + (size_t)maxloc * 12 + 16 +
+    return 1024 + 4 * (size_t)kWideN * 128 + 2 * (size_t)nbins * kStageLd * 4 + (size_t)maxloc * 8 + 16 +
            (size_t)kWideN * sizeof(WideRight);
 }
 
@@ -995,7 +1002,7 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
     KTimer tm(p, quads ? KC_QUAD_TC : KC_CONTRACT_TC);
     FBS_CUDA(cudaFuncSetAttribute(contract_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid(G, ngrp);
-    contract_wide_kernel<<<grid, kTcThreads, sm, p.stream>>>(
+    contract_wide_kernel<<<grid, kWideThreads, sm, p.stream>>>(
         islab, slab_stride, npts, p.nbins, w.nleft, w.d_left, w.d_rights, w.nright, w.d_item_out, t.nitems,
         quads ? p.d_qpart : p.d_tpart, p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
     FBS_CUDA(cudaGetLastError());
