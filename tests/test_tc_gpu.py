@@ -114,11 +114,11 @@ def test_trispectrum_bf16x3_matches_oracle(N, nb, kind):
 
 
 @pytest.mark.parametrize("N,nb,quads", [(32, 6, False), (48, 12, False), (32, 6, True)])
-def test_narrow_orientation_still_matches(monkeypatch, N, nb, quads):
-    """The tensor-core kernel with the pair products as operand A (used when
-    more than 64 left rows exist) stays correct when forced."""
+def test_wide_orientation_matches(monkeypatch, N, nb, quads):
+    """The wide tensor-core kernel (left rows [hi; lo] as operand A, right
+    pair products as operand B with N <= 256; BF16x4) matches the oracle."""
     import torch
-    monkeypatch.setenv("FBS_TC_NARROW", "1")
+    monkeypatch.setenv("FBS_TC_WIDE", "1")
     L = 70.0
     edges = fields.linear_edges(N, L, nb)
     f32 = _field("lognormal", N, 31).astype(np.float32)
