@@ -193,6 +193,8 @@ def main():
     ap.add_argument("--nbt", type=int, default=NB_T)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -328,6 +330,33 @@ def main():
         e2e["value"] = world * planB.ntrip / e2e_max
         e2e.pop("_s", None)
         line["e2e"] = e2e
+    if rank == 0 and not args.no_plain and world == 1:
+        # plain FP32 GPU path on the same field (comparison only)
+        try:
+            thrB = np.asarray(planB.thresholds)
+            plain_fp32_gpu(field, N, L_BOX, thrB, planB.triplets, dev)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            numP = plain_fp32_gpu(field, N, L_BOX, thrB, planB.triplets, dev)
+            torch.cuda.synchronize()
+            tp = time.perf_counter() - t0
+            planB.bispectrum(field, B, P)
+            ours, _, _ = planB.sums()
+            numP = numP.cpu().numpy()
+            big = np.abs(ours) > 1e-3 * np.abs(ours).max()
+            line["plain_fp32_gpu"] = {
+                "value": planB.ntrip / tp, "unit": "triangle-bins/s", "ms_per_field": 1e3 * tp,
+                "what": "cuFFT R2C + per-bin mask + cuFFT C2R, FP32 pair products x FP32 GEMV per "
+                        "outer pair, FP64 across x chunks (torch.fft / torch matmul)",
+                "speedup_of_ours": (planB.ntrip / (ms_max / 1e3)) / (planB.ntrip / tp),
+                "max_rel_diff_vs_ours": float(np.max(np.abs(numP[big] - ours[big]) / np.abs(ours[big])))}
+        except Exception as ex:
+            line["plain_fp32_gpu"] = {"value": None, "error": str(ex)[:200]}
+    if rank == 0 and not args.no_serve and world == 1:
+        try:
+            line["serving"] = serving_run(precision=args.precision)
+        except Exception as ex:
+            line["serving"] = {"value": None, "error": str(ex)[:200]}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         try:
             t_full, info = cpu_baseline(args, seconds=15.0)
@@ -345,6 +374,75 @@ def main():
     planT.close()
     if dist:
         dist.destroy_process_group()
+
+
+def serving_run(n_req=40, rate=200.0, seed=7, budget=120 << 30, slots=4, precision="bf16x3"):
+    """Continuous-batching serving of a Poisson request stream: grids from
+    {64, 128, 192, 256, 384}, lognormal or bubble fields (50/50), 8..48 linear
+    bins, 120 GiB budget.  A small pool of fields per grid is generated up
+    front (synthetic); requests differ in field, bins and arrival."""
+    import torch
+    import fields
+    from paper_1705_06284_gb300.serve import EstimatorServer, Request, latency_percentiles
+    rng = np.random.default_rng(seed)
+    grids = [64, 128, 192, 256, 384]
+    pool = {}
+    for N in grids:
+        pool[N] = [torch.from_numpy(fields.lognormal(N, 0.6, -2.0, seed=seed + N).astype(np.float32)).pin_memory(),
+                   torch.from_numpy(fields.bubbles(N, max(3.0, N / 40), 0.5, seed=seed + 2 * N)
+                                    .astype(np.float32)).pin_memory()]
+    t, reqs = 0.0, []
+    for i in range(n_req):
+        t += rng.exponential(1.0 / rate)
+        N = int(rng.choice(grids))
+        nb = int(rng.integers(8, 49))
+        L = float(N)
+        reqs.append(Request(i, pool[N][int(rng.integers(0, 2))].numpy(), L,
+                            tuple(np.linspace(2 * math.pi / L, 0.25 * N * 2 * math.pi / L, nb + 1)),
+                            arrival=t, precision=precision))
+    srv = EstimatorServer(hbm_budget=budget, slots=slots)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    creations = srv.plan_creations
+    srv.close()
+    tri = sum(len(r.B) for r in res)
+    out = {"requests": n_req, "arrival_rate_per_s": rate, "slots": slots, "hbm_budget_gib": budget >> 30,
+           "value": tri / wall, "unit": "triangle-bins/s", "wall_s": wall, "plans_created": creations}
+    out.update(latency_percentiles(res))
+    return out
+
+
+def plain_fp32_gpu(field, N, L, thr, triplets, dev):
+    """The plain FP32 GPU comparator (not the product): cuFFT R2C of the field,
+    per bin a mask and a cuFFT C2R (unnormalised) to I_b, then for every
+    outer pair (b, c) the FP32 product I_b I_c and FP32 dot products with the
+    I_a of its triplets over x chunks, summed across chunks in FP64."""
+    import torch
+    f = torch.fft.rfftn(field)                     # cuFFT, unnormalised forward
+    fx = torch.fft.fftfreq(N, d=1.0 / N, device=dev)
+    fz = torch.arange(N // 2 + 1, device=dev, dtype=fx.dtype)
+    m2 = (fx[:, None, None] ** 2 + fx[None, :, None] ** 2 + fz[None, None, :] ** 2).round().to(torch.int64)
+    nb = len(thr) - 1
+    I = torch.empty((nb, N * N * N), dtype=torch.float32, device=dev)
+    npix = float(N) ** 3
+    for b in range(nb):
+        mask = (m2 >= int(thr[b])) & (m2 < int(thr[b + 1]))
+        I[b] = (torch.fft.irfftn(torch.where(mask, f, torch.zeros_like(f)), s=(N, N, N)) * npix).reshape(-1)
+    num = torch.zeros(len(triplets), dtype=torch.float64, device=dev)
+    groups = {}
+    for t, (a, b, c) in enumerate(triplets):
+        groups.setdefault((int(b), int(c)), []).append((int(a), t))
+    CH = 1 << 24
+    for (b, c), lst in groups.items():
+        aidx = torch.tensor([a for a, _ in lst], device=dev)
+        tidx = torch.tensor([t for _, t in lst], device=dev)
+        acc = torch.zeros(len(lst), dtype=torch.float64, device=dev)
+        for x0 in range(0, N ** 3, CH):
+            P = I[b, x0:x0 + CH] * I[c, x0:x0 + CH]
+            acc += (I[aidx, x0:x0 + CH] @ P).double()
+        num[tidx] = acc
+    return num
 
 
 def _closed_triplets_oracle(N, thr):

@@ -1,0 +1,197 @@
+"""Continuous-batching serving loop for estimator requests.
+
+Requests arrive over time (a likelihood sampler asking for the bispectrum of
+one field after another, with mixed grid sizes and bin sets).  The server
+keeps plans resident on the device, admits a request as soon as a slot (a
+CUDA stream) is free and its plan fits the HBM budget, overlaps the work of
+all admitted requests on the device, and reports per-request latency from
+arrival to a host-visible result.
+
+Every estimator step runs in ``libfbs.so`` through the C ABI; this module
+only schedules: host->device copy of the field on the slot's stream, one
+``fbs_bispectrum`` call, device->host copy of the outputs, and a CUDA event
+that is polled without blocking.  Results are bit-identical to running each
+request alone (the kernels use fixed reduction orders).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+from . import Plan
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    field: np.ndarray          # float32 [N][N][N] on the host
+    L: float
+    edges: Tuple[float, ...]
+    arrival: float = 0.0       # seconds after the start of the run
+    precision: str = "bf16x3"
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    triplets: np.ndarray
+    N_tri: np.ndarray
+    B: np.ndarray
+    P: np.ndarray
+    arrival: float
+    admitted: float
+    done: float
+
+    @property
+    def latency(self) -> float:
+        return self.done - self.arrival
+
+
+def plan_bytes_estimate(N: int, nbins: int, slab_budget: int = 8 << 30) -> int:
+    """Device bytes a plan needs at its peak (plan-time FP64 count fields
+    included), used for admission before the plan exists."""
+    planes = max(1, min(N, slab_budget // max(1, nbins * N * N * 4)))
+    shell = nbins * planes * N * N * 4
+    scratch = 3 * N * N * (N // 4 + 1) * 8 + N ** 3 * 4
+    counts = nbins * (N // 2 + 1) ** 3 * 8
+    return shell + scratch + counts + (64 << 20)
+
+
+class _Slot:
+    def __init__(self, torch, dev):
+        self.stream = torch.cuda.Stream(device=dev)
+        self.busy = None  # (request, plan entry, event, outputs, t_admit)
+
+
+class EstimatorServer:
+    """Serve bispectrum requests with overlap on one GPU.
+
+    hbm_budget: bytes of device memory the server's plans and buffers may hold.
+    slots: concurrent requests in flight (one CUDA stream each).
+    """
+
+    def __init__(self, hbm_budget: int = 120 << 30, slots: int = 4, device: int = 0):
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.budget = int(hbm_budget)
+        self.slots = [_Slot(torch, self.dev) for _ in range(slots)]
+        # key -> list of entries {"plan", "bytes", "busy", "last"}
+        self.plans: Dict[tuple, List[dict]] = collections.defaultdict(list)
+        self.held = 0
+        self.plan_creations = 0
+
+    # -- plan cache under the budget
+    def _key(self, req: Request):
+        return (req.field.shape[0], float(req.L), tuple(float(e) for e in req.edges), req.precision)
+
+    def _evict_for(self, need: int) -> bool:
+        idle = [(e["last"], k, e) for k, lst in self.plans.items() for e in lst if not e["busy"]]
+        idle.sort(key=lambda t: t[0])
+        while self.held + need > self.budget and idle:
+            _, k, e = idle.pop(0)
+            e["plan"].close()
+            self.plans[k].remove(e)
+            self.held -= e["bytes"]
+        return self.held + need <= self.budget
+
+    def _plan_for(self, req: Request, stream) -> Optional[dict]:
+        key = self._key(req)
+        for e in self.plans[key]:
+            if not e["busy"]:
+                e["plan"].set_stream(stream)
+                return e
+        N = req.field.shape[0]
+        need = plan_bytes_estimate(N, len(req.edges) - 1) + 2 * req.field.nbytes
+        if not self._evict_for(need):
+            return None
+        plan = Plan(N, req.L, np.asarray(req.edges), precision=req.precision, stream=stream)
+        self.plan_creations += 1
+        e = {"plan": plan, "bytes": plan.device_bytes + 2 * req.field.nbytes, "busy": False,
+             "last": time.perf_counter(), "dfield": None}
+        self.held += e["bytes"]
+        self.plans[key].append(e)
+        return e
+
+    # -- one request on one slot
+    def _submit(self, slot: _Slot, req: Request, entry: dict, t0: float):
+        torch = self.torch
+        plan = entry["plan"]
+        N = req.field.shape[0]
+        entry["busy"] = True
+        with torch.cuda.stream(slot.stream):
+            if entry["dfield"] is None or entry["dfield"].shape[0] != N:
+                entry["dfield"] = torch.empty((N, N, N), dtype=torch.float32, device=self.dev)
+            host = torch.from_numpy(req.field)
+            if not host.is_pinned():
+                host = host.pin_memory()
+            entry["dfield"].copy_(host, non_blocking=True)
+            B = torch.empty(plan.ntrip, dtype=torch.float64, device=self.dev)
+            P = torch.empty(plan.nbins, dtype=torch.float64, device=self.dev)
+            plan.bispectrum(entry["dfield"], B, P)
+            Bh = torch.empty(plan.ntrip, dtype=torch.float64, pin_memory=True)
+            Ph = torch.empty(plan.nbins, dtype=torch.float64, pin_memory=True)
+            Bh.copy_(B, non_blocking=True)
+            Ph.copy_(P, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+        slot.busy = (req, entry, ev, (B, P, Bh, Ph, host), time.perf_counter() - t0)
+
+    def run(self, requests: Sequence[Request], realtime: bool = True) -> List[Result]:
+        """Serve ``requests`` (sorted by arrival).  With ``realtime`` a request
+        is not admitted before its arrival time; otherwise arrivals are
+        ignored (all requests are available at once)."""
+        pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting: collections.deque = collections.deque()
+        results: List[Result] = []
+        t0 = time.perf_counter()
+        while pending or waiting or any(s.busy for s in self.slots):
+            now = time.perf_counter() - t0
+            while pending and (not realtime or pending[0].arrival <= now):
+                waiting.append(pending.popleft())
+            # completions (non-blocking)
+            for s in self.slots:
+                if s.busy and s.busy[2].query():
+                    req, entry, ev, bufs, t_adm = s.busy
+                    _, _, Bh, Ph, _ = bufs
+                    plan = entry["plan"]
+                    results.append(Result(req.rid, plan.triplets.copy(), plan.N_tri.copy(),
+                                          Bh.numpy().copy(), Ph.numpy().copy(),
+                                          req.arrival if realtime else 0.0, t_adm,
+                                          time.perf_counter() - t0))
+                    entry["busy"] = False
+                    entry["last"] = time.perf_counter()
+                    s.busy = None
+            # admissions: first-come first-served over the free slots
+            progressed = False
+            for s in self.slots:
+                if s.busy or not waiting:
+                    continue
+                req = waiting[0]
+                entry = self._plan_for(req, s.stream)
+                if entry is None:
+                    break  # no memory until something finishes
+                waiting.popleft()
+                self._submit(s, req, entry, t0)
+                progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+        return sorted(results, key=lambda r: r.rid)
+
+    def close(self):
+        self.torch.cuda.synchronize()
+        for lst in self.plans.values():
+            for e in lst:
+                e["plan"].close()
+        self.plans.clear()
+        self.held = 0
+
+
+def latency_percentiles(results: Sequence[Result]) -> Dict[str, float]:
+    lat = np.array([r.latency for r in results])
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3)}
