@@ -47,3 +47,22 @@ def check_bispectrum(plan, B, P, field32, L, edges, precision, ref=None, M=None)
     if precision in TOL:
         assert gmax < TOL[precision], ("B mismatch", gmax, int(np.argmax(np.where(g, r, 0))))
     return gmax, float(r.max()) if len(r) else 0.0, int(g.sum())
+
+
+def check_trispectrum(plan, T, field32, L, edges, tol):
+    """T against the FP64 FFT estimator on quadruplets with N_quad >= 100 and
+    |T| >= 1e-3 of the cancellation-free scale sum_x |I_a I_b I_c I_d|.
+    Returns (max gated rel err, n gated)."""
+    f64 = field32.astype(np.float64)
+    g = oracle.fft_estimator(f64, L, edges, triplets=[], quads=plan.quads)
+    assert np.array_equal(plan.N_quad, g["N_quad"])
+    N = field32.shape[0]
+    D = oracle.spectrum(f64)
+    bins = oracle.bin_index(N, oracle.thresholds(edges, L))
+    I = {b: oracle.shell_field(D, bins, b) for b in set(plan.quads.ravel().tolist())}
+    mag = np.array([np.sum(np.abs(I[a] * I[b] * I[c] * I[d])) for a, b, c, d in plan.quads])
+    keep = (plan.N_quad >= 100) & (np.abs(g["qnum"]) >= 1e-3 * mag)
+    r = rel_err(T, g["T"])
+    assert keep.sum() > 0
+    assert np.all(r[keep] < tol), float(r[keep].max())
+    return float(r[keep].max()), int(keep.sum())

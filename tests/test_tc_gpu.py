@@ -7,7 +7,7 @@ import pytest
 import fields
 import oracle
 import paper_1705_06284_gb300 as fbs
-from gpu_util import check_bispectrum, gate_mask, rel_err, run
+from gpu_util import check_bispectrum, check_trispectrum, gate_mask, rel_err, run
 
 pytestmark = pytest.mark.gpu
 
@@ -97,20 +97,9 @@ def test_trispectrum_bf16x3_matches_oracle(N, nb, kind):
         torch.cuda.synchronize()
         T, B, P = T.cpu().numpy(), B.cpu().numpy(), P.cpu().numpy()
         check_bispectrum(plan, B, P, f32, L, edges, "bf16x3")
-        g = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=[], quads=plan.quads)
         assert plan.quad_counts_exact
-        assert np.array_equal(plan.N_quad, g["N_quad"])
-        # gate as for B: enough quadruples and |T| not lost in cancellation
-        f64 = f32.astype(np.float64)
-        D = oracle.spectrum(f64)
-        bins = oracle.bin_index(N, oracle.thresholds(edges, L))
-        I = {b: oracle.shell_field(D, bins, b) for b in set(plan.quads.ravel().tolist())}
-        mag = np.array([np.sum(np.abs(I[a] * I[b] * I[c] * I[d])) for a, b, c, d in plan.quads])
-        keep = (plan.N_quad >= 100) & (np.abs(g["qnum"]) >= 1e-3 * mag)
-        r = rel_err(T, g["T"])
-        assert keep.sum() > 0
-        assert np.all(r[keep] < 2e-4), float(r[keep].max())
-    print("T N=%d quads %d gated %d max %.2e" % (N, len(T), keep.sum(), r[keep].max()))
+        m, n = check_trispectrum(plan, T, f32, L, edges, 2e-4)
+    print("T N=%d quads %d gated %d max %.2e" % (N, len(T), n, m))
 
 
 @pytest.mark.parametrize("N,nb,quads", [(32, 6, False), (48, 12, False), (32, 6, True)])
@@ -127,9 +116,7 @@ def test_wide_orientation_matches(monkeypatch, N, nb, quads):
             T, B, P = plan.trispectrum(torch.from_numpy(f32).cuda())
             torch.cuda.synchronize()
             B, P, T = B.cpu().numpy(), P.cpu().numpy(), T.cpu().numpy()
-            g = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=[], quads=plan.quads)
-            r = rel_err(T, g["T"])
-            assert np.all(r[plan.N_quad >= 100] < 2e-4), float(r.max())
+            check_trispectrum(plan, T, f32, L, edges, 2e-4)
         else:
             B, P = run(plan, f32)
         check_bispectrum(plan, B, P, f32, L, edges, "bf16x3")
