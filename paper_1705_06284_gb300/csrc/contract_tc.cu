@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int2 *pbc = reinterpret_cast<int2 *>(acc + nloc);  // (b, c) of every row of every tile
 
     const int acc_cols = ((ntl * tstride + 31) / 32) * 32;
-    const int tmem_cols_needed = acc_cols + nst * kAStageCols;
+    const int tmem_cols_needed = acc_cols + 2 * kAStageCols;
     int ncols = 32;
     while (ncols < tmem_cols_needed) ncols <<= 1;
 
@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + sb * b_tile));
                 const uint64_t dbl = sdesc_sw128(smem_u32(Bl0 + sb * b_tile));
                 for (int lt = 0; lt < ntl; ++lt) {
-                    const int as = (int)(gA % nst);
-                    const bool oka = role_wait(&bars.full[as], (uint32_t)((gA / nst) & 1), abortp, err, 12);
+                    const int as = (int)(gA & 1);
+                    const bool oka = role_wait(&bars.full[as], (uint32_t)((gA >> 1) & 1), abortp, err, 12);
                     tc_fence_after();
                     if (okb && oka && !*abortp) {
                         const uint32_t d = tmem + (uint32_t)(lt * tstride);
@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             // drain: every MMA complete before tensor memory is released (own limit)
             if (gA > 0) {
-                const int as = (int)((gA - 1) % nst);
-                if (!mbar_wait(&bars.empty[as], (uint32_t)(((gA - 1) / nst) & 1))) atomicExch(err, 14);
+                const int as = (int)((gA - 1) & 1);
+                if (!mbar_wait(&bars.empty[as], (uint32_t)(((gA - 1) >> 1) & 1))) atomicExch(err, 14);
             }
         }
     } else {
@@ -463,8 +463,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ++gB;
             // ---- operand A: pair products of this thread's row, 32 points, into TMEM
             for (int lt = 0; lt < ntl; ++lt) {
-                const int as = (int)(gA % nst);
-                if (gA >= nst) role_wait(&bars.empty[as], (uint32_t)(((gA - nst) / nst) & 1), abortp, err, 22);
+                const int as = (int)(gA & 1);
+                if (gA >= 2) role_wait(&bars.empty[as], (uint32_t)(((gA - 2) >> 1) & 1), abortp, err, 22);
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
                 uint32_t hw[16], lw[16];
