@@ -120,6 +120,18 @@ fbs_status fbs_plan_shells(const fbs_plan *plan, int64_t *sizes, int64_t *thr);
 /* Change the contraction precision of an existing plan (FBS_PREC_*). */
 fbs_status fbs_plan_set_precision(fbs_plan *plan, int precision);
 
+/* Plan options (fbs_plan_set_option). */
+enum {
+    FBS_OPT_TC_WIDE = 1 /* 0: tensor-core contraction with the pair products as
+                           operand A (M = 128 outer pairs, N = bins; default);
+                           1: "wide" orientation with the <= 64 left rows stacked
+                           [hi; lo] as operand A and up to 256 right pair
+                           products as operand B (BF16x4).  Ignored for FP32. */
+};
+
+/* Set a plan option; FBS_ERR_ARG for an unknown option or value. */
+fbs_status fbs_plan_set_option(fbs_plan *plan, int option, int value);
+
 /* Rebind the plan to another cudaStream_t (NULL = legacy default stream). */
 fbs_status fbs_plan_set_stream(fbs_plan *plan, void *cuda_stream);
 

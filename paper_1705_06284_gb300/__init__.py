@@ -35,6 +35,7 @@ FBS_PREC_BF16 = 2
 FBS_FLAG_TRISPECTRUM = 1
 FBS_FLAG_ALLOW_ALIASED = 2
 FBS_FLAG_TIMING = 4
+FBS_OPT_TC_WIDE = 1
 
 _PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
 
@@ -64,6 +65,7 @@ _SIGS = [
     ("fbs_plan_shells", ctypes.c_int, [_vp, _vp, _vp]),
     ("fbs_plan_set_precision", ctypes.c_int, [_vp, ctypes.c_int]),
     ("fbs_plan_set_stream", ctypes.c_int, [_vp, _vp]),
+    ("fbs_plan_set_option", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     ("fbs_bispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("fbs_trispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("fbs_plan_sums", ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -212,6 +214,14 @@ class Plan:
     def set_precision(self, precision):
         _check(lib().fbs_plan_set_precision(_vp(self._h), _PREC[precision]))
         self.precision = precision
+
+    def set_option(self, option, value):
+        _check(lib().fbs_plan_set_option(_vp(self._h), int(option), int(value)))
+
+    def set_tc_wide(self, wide: bool):
+        """Tensor-core orientation: False = pair products as operand A
+        (default), True = the wide orientation (see FBS_OPT_TC_WIDE)."""
+        self.set_option(FBS_OPT_TC_WIDE, 1 if wide else 0)
 
     def set_stream(self, stream):
         sp = getattr(stream, "cuda_stream", stream) or 0

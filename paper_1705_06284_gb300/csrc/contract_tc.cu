@@ -989,9 +989,8 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
     // The narrow orientation measured faster on the headline workload (shared
     // memory and tensor-memory contention slow the wide N = 256 MMAs to about
     // twice their isolated cost, and each right-row group re-reads the shell
-    // fields); the wide kernel is selected with FBS_TC_WIDE=1.
-    const char *w_env = getenv("FBS_TC_WIDE");
-    if (!w_env || w_env[0] != '1' || getenv("FBS_TC_NARROW")) return false;
+    // fields); the wide kernel is selected per plan with FBS_OPT_TC_WIDE.
+    if (!p.tc_wide) return false;
     TcState &st = tc_state(p);
     WideJob &w = quads ? st.wquad : st.wtrip;
     if (!w.built) build_wide(p, quads, w);

@@ -117,6 +117,7 @@ struct Plan {
     int nbins = 0;
     int precision = 0;
     unsigned flags = 0;
+    int tc_wide = 0;             // FBS_OPT_TC_WIDE
     cudaStream_t stream = nullptr;
     double create_ms = 0;
     double count_margin = 0;  // largest |sum N..N / N_pix - nearest integer| of the rounded counts

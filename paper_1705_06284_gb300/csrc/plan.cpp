@@ -732,6 +732,16 @@ fbs_status fbs_plan_set_precision(fbs_plan *plan, int precision) {
     return FBS_OK;
 }
 
+fbs_status fbs_plan_set_option(fbs_plan *plan, int option, int value) {
+    if (!plan) return FBS_ERR_ARG;
+    if (option == FBS_OPT_TC_WIDE && (value == 0 || value == 1)) {
+        plan->tc_wide = value;
+        return FBS_OK;
+    }
+    set_error("unknown option or value");
+    return FBS_ERR_ARG;
+}
+
 fbs_status fbs_plan_set_stream(fbs_plan *plan, void *stream) {
     if (!plan) return FBS_ERR_ARG;
     FBS_GUARD_BEGIN

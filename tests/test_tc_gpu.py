@@ -107,11 +107,11 @@ def test_wide_orientation_matches(monkeypatch, N, nb, quads):
     """The wide tensor-core kernel (left rows [hi; lo] as operand A, right
     pair products as operand B with N <= 256; BF16x4) matches the oracle."""
     import torch
-    monkeypatch.setenv("FBS_TC_WIDE", "1")
     L = 70.0
     edges = fields.linear_edges(N, L, nb)
     f32 = _field("lognormal", N, 31).astype(np.float32)
     with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        plan.set_tc_wide(True)
         if quads:
             T, B, P = plan.trispectrum(torch.from_numpy(f32).cuda())
             torch.cuda.synchronize()
