@@ -193,7 +193,8 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
 // shared memory, form the pair products into tensor memory, flush the
 // accumulators); warp 8 allocates tensor memory and one of its threads issues
 // every MMA.  Hand-offs go through mbarriers, never through __syncthreads.
-constexpr int kProdWarps = 8;    // 2 per TMEM lane quarter, each 32 of the 64 points of a row
+constexpr int kProdWarps = 16;   // 4 per TMEM lane quarter, each 16 of the 64 points of a row
+constexpr int kPPT = 4 * KC / kProdWarps;  // points of a row per producer thread per tile
 constexpr int kTcThreads = (kProdWarps + 1) * 32;
 constexpr int kAStages = 3;      // maximum; the launch picks 2 or 3 to fit tensor memory
 constexpr int kAStageCols = 64;  // 32 columns hi + 32 columns lo (64 BF16 per row each)
@@ -231,6 +232,13 @@ __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volati
         }
     }
     return true;
+}
+
+__device__ __forceinline__ void tmem_st8a(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+        "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
@@ -411,7 +419,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else {
         // ================= producers (warps 0..7) =================
-        const int q = warp & 3, kq = warp >> 2;  // lane quarter, 32-point half of the chunk
+        const int q = warp & 3, kq = warp >> 2;  // lane quarter, kPPT-point slice of the chunk
         const int r = 32 * q + lane;             // operand-A row (TMEM lane) of this thread
         const int ptid = tid;                    // 0 .. 32*kProdWarps-1
         auto prefetch = [&](long long ch, int s) {
@@ -467,12 +475,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (gA >= 2) role_wait(&bars.empty[as], (uint32_t)(((gA - 2) >> 1) & 1), abortp, err, 22);
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
-                uint32_t hw[16], lw[16];
+                uint32_t hw[kPPT / 2], lw[kPPT / 2];
                 if (bc.x >= 0) {
-                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + 32 * kq);
-                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + 32 * kq);
+                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + kPPT * kq);
+                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + kPPT * kq);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int j = 0; j < kPPT / 8; ++j) {
                         float4 b0 = rb[2 * j], b1 = rb[2 * j + 1], e0 = rc[2 * j], e1 = rc[2 * j + 1];
                         float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
                                       b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
@@ -483,12 +491,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) hw[j] = lw[j] = 0u;
+                    for (int j = 0; j < kPPT / 2; ++j) hw[j] = lw[j] = 0u;
                 }
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
-                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + 16 * kq);
-                tmem_st16(lanebase + col, hw);
-                tmem_st16(lanebase + col + 32u, lw);
+                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + (kPPT / 2) * kq);
+                if constexpr (kPPT == 32) {
+                    tmem_st16(lanebase + col, hw);
+                    tmem_st16(lanebase + col + 32u, lw);
+                } else {
+                    tmem_st8a(lanebase + col, hw);
+                    tmem_st8a(lanebase + col + 32u, lw);
+                }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
@@ -505,7 +518,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const bool valid = p < npairs;
                         TcPair pi;
                         if (valid) pi = pairs[p];
-                        for (int c8 = 8 * kq; c8 < Npad; c8 += 16) {
+                        for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (kProdWarps / 4)) {
                             float v[8];
                             tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
                             if (!valid) continue;
