@@ -66,7 +66,9 @@ enum {
 enum {
     FBS_FLAG_TRISPECTRUM = 1u,   /* also enumerate closed quadruplets (needed by fbs_trispectrum) */
     FBS_FLAG_ALLOW_ALIASED = 2u, /* allow edges beyond N k_f/4 (closure is then modulo N, Sec. 3.2) */
-    FBS_FLAG_TIMING = 4u         /* record CUDA events around every kernel (fbs_plan_kernel_times) */
+    FBS_FLAG_TIMING = 4u,        /* record CUDA events around every kernel (fbs_plan_kernel_times) */
+    FBS_FLAG_FULL_GRID = 8u      /* evaluate the shell fields and their products on the input
+                                    N^3 grid instead of the smallest M^3 grid that gives the same sums */
 };
 
 /*
@@ -82,6 +84,13 @@ enum {
  *   precision  : FBS_PREC_*.
  *   flags      : FBS_FLAG_* bits.
  *   cuda_stream: cudaStream_t the plan launches on (NULL = legacy default stream).
+ * Evaluation grid: every shell field holds only modes with |m_j| <= R, so a
+ * product of p of them is a trigonometric polynomial of degree <= pR per
+ * axis and its sum over the N^3 grid equals (N/M)^3 times its sum over any
+ * M^3 grid with M > pR (p = 3, or 4 with FBS_FLAG_TRISPECTRUM).  Unless
+ * FBS_FLAG_FULL_GRID or FBS_FLAG_ALLOW_ALIASED is given, the plan evaluates
+ * the shell fields and their products on the smallest even M = 2^a 3^b > pR
+ * (M <= N): the same sums up to rounding, with (M/N)^3 of the points.
  * The plan runs the plan-time work on the device before returning: shell
  * tables, the FP64 count fields N_b, exact N_tri (and N_quad) for every
  * candidate bin triple, and the closed-triplet list (lexicographic a<=b<=c
@@ -187,6 +196,9 @@ double fbs_plan_count_margin(const fbs_plan *plan);
 /* 1 when every quadruple count of the plan is an exact integer (rounded
  * within 0.25 and below 2^53), 0 when some are FP64 sums, <0 on error. */
 int fbs_plan_quad_counts_exact(const fbs_plan *plan);
+
+/* Side M of the grid the plan evaluates shell fields and products on. */
+int fbs_plan_eval_grid(const fbs_plan *plan);
 
 /* Device bytes owned by the plan. */
 int64_t fbs_plan_device_bytes(const fbs_plan *plan);

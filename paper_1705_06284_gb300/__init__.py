@@ -35,6 +35,7 @@ FBS_PREC_BF16 = 2
 FBS_FLAG_TRISPECTRUM = 1
 FBS_FLAG_ALLOW_ALIASED = 2
 FBS_FLAG_TIMING = 4
+FBS_FLAG_FULL_GRID = 8
 FBS_OPT_TC_WIDE = 1
 
 _PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
@@ -76,6 +77,7 @@ _SIGS = [
     ("fbs_plan_device_bytes", ctypes.c_int64, [_vp]),
     ("fbs_plan_count_margin", ctypes.c_double, [_vp]),
     ("fbs_plan_quad_counts_exact", ctypes.c_int, [_vp]),
+    ("fbs_plan_eval_grid", ctypes.c_int, [_vp]),
     ("fbs_triple_sums_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                                 _vp, ctypes.c_int, _vp, _vp]),
     ("fbs_last_error", ctypes.c_char_p, []),
@@ -156,9 +158,10 @@ class Plan:
     """
 
     def __init__(self, N, L, edges, precision="fp32", trispectrum=False, allow_aliased=False,
-                 timing=False, stream=None):
+                 timing=False, stream=None, full_grid=False):
         flags = (FBS_FLAG_TRISPECTRUM if trispectrum else 0) | \
-                (FBS_FLAG_ALLOW_ALIASED if allow_aliased else 0) | (FBS_FLAG_TIMING if timing else 0)
+                (FBS_FLAG_ALLOW_ALIASED if allow_aliased else 0) | (FBS_FLAG_TIMING if timing else 0) | \
+                (FBS_FLAG_FULL_GRID if full_grid else 0)
         if stream is None:
             try:
                 import torch
@@ -188,6 +191,7 @@ class Plan:
         self.device_bytes = int(Lb.fbs_plan_device_bytes(_vp(self._h)))
         self.count_margin = float(Lb.fbs_plan_count_margin(_vp(self._h)))
         self.quad_counts_exact = bool(Lb.fbs_plan_quad_counts_exact(_vp(self._h)) == 1)
+        self.eval_grid = int(Lb.fbs_plan_eval_grid(_vp(self._h)))
 
     # -- lifetime
     def close(self):

@@ -126,18 +126,18 @@ __global__ void __launch_bounds__(kCThreads) contract_fp32_kernel(
 // ------------------------------------------------------------------ reduce
 // out[i] = sum_r part[r][i] in a fixed order (deterministic).
 __global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, int n,
-                                   double *__restrict__ out) {
+                                   double *__restrict__ out, double scale) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
     for (int r = 0; r < rows; ++r) s += part[(long long)r * n + i];
-    out[i] = s;
+    out[i] = scale * s;
 }
 
 // out[j] = sum_r part[j][r]: one block per j, strided partial sums then a
 // fixed-shape tree (deterministic for a given launch shape).
 __global__ void __launch_bounds__(256) reduce_cols_kernel(const double *__restrict__ part, int rows,
-                                                          double *__restrict__ out) {
+                                                          double *__restrict__ out, double scale) {
     __shared__ double red[256];
     const int j = blockIdx.x;
     double s = 0.0;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) reduce_cols_kernel(const double *__restri
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[j] = red[0];
+    if (threadIdx.x == 0) out[j] = scale * red[0];
 }
 
 // ------------------------------------------------------------------ normalise
@@ -304,27 +304,30 @@ void zero_partials(Plan &p, bool quads) {
                                  p.stream));
     // every sum-of-squares partial is overwritten by the z stage (empty bins: 0)
     FBS_CUDA(cudaMemsetAsync(p.d_sumsq_part, 0,
-                             (size_t)p.nbins * p.N * zstage_row_groups(p.N) * sizeof(double), p.stream));
+                             (size_t)p.nbins * p.M * zstage_row_groups(p.M) * sizeof(double), p.stream));
 }
 
 void launch_reduce_and_normalise(Plan &p, bool quads) {
     {
         KTimer tm(p, KC_REDUCE);
+        // sums over the M^3 evaluation grid -> sums over the N^3 grid
+        const double r = (double)p.N / (double)p.M;
+        const double scale = r * r * r;
         int n = p.ttask.nitems;
         if (n > 0) {
             reduce_rows_kernel<<<(n + 255) / 256, 256, 0, p.stream>>>(p.d_tpart, p.part_blocks, n,
-                                                                      p.d_tnum);
+                                                                      p.d_tnum, scale);
             FBS_CUDA(cudaGetLastError());
         }
         if (quads && p.qtask.nitems > 0) {
             int m = p.qtask.nitems;
             reduce_rows_kernel<<<(m + 255) / 256, 256, 0, p.stream>>>(p.d_qpart, p.part_blocks, m,
-                                                                      p.d_qnum);
+                                                                      p.d_qnum, scale);
             FBS_CUDA(cudaGetLastError());
         }
         {
-            const int rows = p.N * zstage_row_groups(p.N);
-            reduce_cols_kernel<<<p.nbins, 256, 0, p.stream>>>(p.d_sumsq_part, rows, p.d_sumsq);
+            const int rows = p.M * zstage_row_groups(p.M);
+            reduce_cols_kernel<<<p.nbins, 256, 0, p.stream>>>(p.d_sumsq_part, rows, p.d_sumsq, scale);
             FBS_CUDA(cudaGetLastError());
         }
         int ntrip = (int)p.ntri.size(), nquad = quads ? (int)p.nquad.size() : 0;
@@ -362,7 +365,7 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
     dim3 g(blocks, ngrp);
     count_kernel<<<g, 256, sm, p.stream>>>(noct, nbins_all, H, d_items, arity, nitems, grp, part);
     FBS_CUDA(cudaGetLastError());
-    reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, d_den);
+    reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, d_den, 1.0);
     FBS_CUDA(cudaGetLastError());
     FBS_CUDA(cudaFreeAsync(part, p.stream));
 }

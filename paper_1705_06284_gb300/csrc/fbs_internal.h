@@ -126,8 +126,12 @@ struct Plan {
     std::vector<long long> thr;  // nbins+1
     std::vector<long long> shell;
     std::vector<BinGeom> geom;
-    BoxGeom box{};
+    BoxGeom box{};               // forward spectrum box (transform length N)
     FftFactors fN{};
+    int M = 0;                   // evaluation grid of the shell fields (M <= N)
+    BoxGeom boxM{};              // the box seen by the inverse stages (transform length M)
+    FftFactors fM{};
+    float2 *d_twM = nullptr;     // e^{-2 pi i k/M}, k < M (FP32)
 
     std::vector<int32_t> trip;   // 3*ntrip
     std::vector<int64_t> ntri;
@@ -138,7 +142,7 @@ struct Plan {
     int *d_tgrp = nullptr, *d_qgrp = nullptr;
 
     long long A_elems = 0;       // complex elements of the x-stage output (all bins)
-    long long G_plane = 0;       // complex elements of the y-stage output per x plane (all bins)
+    long long G_plane = 0;       // complex elements of the y-stage output per plane (all bins)
     int slab = 0;                // x planes per slab
     int nslabs = 0;
 

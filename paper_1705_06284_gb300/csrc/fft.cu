@@ -341,13 +341,13 @@ __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t
 // order (coalesced).
 __host__ __device__ constexpr int zpad(int i) { return i + (i >> 3); }
 
-template <int N, int R, int Ns, bool LAST>
+template <int N, int T, int R, int Ns, bool LAST>
 __device__ __forceinline__ void zfast_stage(float2 *__restrict__ buf, int t,
                                             const float2 *__restrict__ tw, float *__restrict__ o0,
                                             float *__restrict__ o1, bool w0, bool w1, float &acc) {
-    constexpr int T = N / 8;
     constexpr int NB = N / R;       // butterflies per line
     constexpr int PER = NB / T;     // butterflies per thread
+    static_assert(PER * T == NB, "threads must divide the butterflies of every stage");
     float2 v[PER][R];
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
@@ -382,64 +382,76 @@ __device__ __forceinline__ void zfast_stage(float2 *__restrict__ buf, int t,
     if (!LAST) __syncthreads();
 }
 
-template <int N, int R1, int R2>
-__global__ void __launch_bounds__(256) inv_z_fast_kernel(const float2 *__restrict__ G,
-                                                         const BinGeom *__restrict__ geom, int x0,
-                                                         float *__restrict__ out, long long out_bin_stride,
-                                                         double *__restrict__ sumsq_part,
-                                                         const float2 *__restrict__ tw) {
-    constexpr int T = N / 8;
-    constexpr int L = 256 / T;  // complex lines (row pairs) per CTA
+// N = R0 R1 R2 R3 (R3, R2 may be 1 = absent); T threads per complex line,
+// LP lines per CTA.
+template <int N, int T, int LP, int R0, int R1, int R2, int R3>
+__global__ void __launch_bounds__(T *LP) inv_z_fast_kernel(const float2 *__restrict__ G,
+                                                           const BinGeom *__restrict__ geom, int x0,
+                                                           float *__restrict__ out,
+                                                           long long out_bin_stride,
+                                                           double *__restrict__ sumsq_part,
+                                                           const float2 *__restrict__ tw) {
+    static_assert(R0 * R1 * R2 * R3 == N, "radices must multiply to N");
     constexpr int NP = zpad(N - 1) + 1;
-    __shared__ float2 buf[L * NP];
-    __shared__ double red[8];
+    constexpr int NB0 = N / R0, PER0 = NB0 / T;
+    static_assert(PER0 * T == NB0, "threads must divide the first stage");
+    __shared__ float2 buf[LP * NP];
+    __shared__ double red[(T * LP + 31) / 32];
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int bl = blockIdx.z;
     const BinGeom g = geom[bl];
     const int xl = blockIdx.y;
-    const int y = (blockIdx.x * L + line) * 2;
+    const int y = (blockIdx.x * LP + line) * 2;
     float *ob = out + (long long)bl * out_bin_stride;
-    float *o0 = ob + ((long long)xl * N + y) * N;
-    float *o1 = o0 + N;
     const bool w0 = y < N, w1 = y + 1 < N;
-    float acc = 0.f;  // <= 16 squares per thread; FP64 from the warp sum on
+    float *o0 = ob + ((long long)xl * N + (w0 ? y : 0)) * N;
+    float *o1 = o0 + N;
+    float acc = 0.f;  // a few squares per thread; FP64 from the warp sums on
     if (g.empty) {
         for (int z = t; z < N; z += T) {
             if (w0) o0[z] = 0.f;
             if (w1) o1[z] = 0.f;
         }
     } else {
-        const float2 *in0 = G + g.G_off + ((long long)xl * N + y) * g.Dzb;
+        const float2 *in0 = G + g.G_off + ((long long)xl * N + (w0 ? y : 0)) * g.Dzb;
         const float2 *in1 = in0 + g.Dzb;
         const int R = g.Dzb - 1;  // highest mz held (<= N/2)
-        // stage 0 (radix 8, Ns = 1): inputs n = t + q T of the packed line
-        float2 v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int n = t + q * T;
-            float2 h1 = make_float2(0.f, 0.f), h2 = make_float2(0.f, 0.f);
-            int m = -1;
-            bool cj = false;
-            if (n <= R) m = n;
-            else if (n >= N - R) { m = N - n; cj = true; }
-            if (m >= 0) {
-                if (w0) h1 = in0[m];
-                if (w1) h2 = in1[m];
-                if (m == 0 || 2 * m == N) { h1.y = 0.f; h2.y = 0.f; }
-                if (cj) { h1.y = -h1.y; h2.y = -h2.y; }
-            }
-            v[q] = make_float2(h1.x - h2.y, h1.y + h2.x);  // H1 + i H2
-        }
-        dftR<+1, float, 8>(v);
         float2 *lb = buf + line * NP;
+        // stage 0 (Ns = 1): butterflies j = t + T u over inputs j + q N/R0 of the packed line
 #pragma unroll
-        for (int q = 0; q < 8; ++q) lb[zpad(8 * t + q)] = v[q];
+        for (int u = 0; u < PER0; ++u) {
+            const int j = t + T * u;
+            float2 v[R0];
+#pragma unroll
+            for (int q = 0; q < R0; ++q) {
+                const int n = j + q * NB0;
+                float2 h1 = make_float2(0.f, 0.f), h2 = make_float2(0.f, 0.f);
+                int m = -1;
+                bool cj = false;
+                if (n <= R) m = n;
+                else if (n >= N - R) { m = N - n; cj = true; }
+                if (m >= 0) {
+                    if (w0) h1 = in0[m];
+                    if (w1) h2 = in1[m];
+                    if (m == 0 || 2 * m == N) { h1.y = 0.f; h2.y = 0.f; }
+                    if (cj) { h1.y = -h1.y; h2.y = -h2.y; }
+                }
+                v[q] = make_float2(h1.x - h2.y, h1.y + h2.x);  // H1 + i H2
+            }
+            dftR<+1, float, R0>(v);
+#pragma unroll
+            for (int q = 0; q < R0; ++q) lb[zpad(R0 * j + q)] = v[q];
+        }
         __syncthreads();
-        if constexpr (R2 == 0) {
-            zfast_stage<N, R1, 8, true>(lb, t, tw, o0, o1, w0, w1, acc);
+        if constexpr (R2 == 1) {
+            zfast_stage<N, T, R1, R0, true>(lb, t, tw, o0, o1, w0, w1, acc);
+        } else if constexpr (R3 == 1) {
+            zfast_stage<N, T, R1, R0, false>(lb, t, tw, o0, o1, w0, w1, acc);
+            zfast_stage<N, T, R2, R0 * R1, true>(lb, t, tw, o0, o1, w0, w1, acc);
         } else {
-            zfast_stage<N, R1, 8, false>(lb, t, tw, o0, o1, w0, w1, acc);
-            zfast_stage<N, R2, 8 * R1, true>(lb, t, tw, o0, o1, w0, w1, acc);
+            zfast_stage<N, T, R1, R0, false>(lb, t, tw, o0, o1, w0, w1, acc);
+            zfast_stage<N, T, R2, R0 * R1, false>(lb, t, tw, o0, o1, w0, w1, acc);
+            zfast_stage<N, T, R3, R0 * R1 * R2, true>(lb, t, tw, o0, o1, w0, w1, acc);
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);  // <= 512 squares
@@ -447,18 +459,35 @@ __global__ void __launch_bounds__(256) inv_z_fast_kernel(const float2 *__restric
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
-        for (int w = 0; w < 8; ++w) s += red[w];
+        for (int w = 0; w < (T * LP + 31) / 32; ++w) s += red[w];
         sumsq_part[((long long)bl * N + x0 + xl) * gridDim.x + blockIdx.x] = s;
     }
 }
 
+// Fast z-stage configurations: (N, threads per line, lines per CTA, radices).
+#define FBS_ZFAST_LIST(X)            \
+    X(64, 8, 32, 8, 8, 1, 1)         \
+    X(96, 4, 32, 8, 4, 3, 1)         \
+    X(128, 16, 16, 8, 4, 4, 1)       \
+    X(192, 8, 16, 8, 8, 3, 1)        \
+    X(256, 32, 8, 8, 8, 4, 1)        \
+    X(384, 16, 8, 8, 4, 4, 3)        \
+    X(512, 64, 4, 8, 8, 8, 1)
+
 // ------------------------------------------------------------------ host side
-static bool zfast_ok(int N) { return N == 64 || N == 128 || N == 256 || N == 512; }
+static int zfast_lines(int N) {
+#define FBS_ZL(n, t, lp, a, b, c, d) \
+    if (N == n) return lp;
+    FBS_ZFAST_LIST(FBS_ZL)
+#undef FBS_ZL
+    return 0;
+}
+static bool zfast_ok(int N) { return zfast_lines(N) > 0; }
 
 // Row groups per plane of the FP32 z stage (one sum-of-squares partial each).
 int zstage_row_groups(int N) {
     if (zfast_ok(N)) {
-        const int L = 256 / (N / 8);
+        const int L = zfast_lines(N);
         return (N + 2 * L - 1) / (2 * L);
     }
     const int nl = lines_per_cta<float>(N);
@@ -483,6 +512,19 @@ void upload_twiddles(Plan &p) {
     p.d_tw64 = (double2 *)p.dalloc(N * sizeof(double2));
     FBS_CUDA(cudaMemcpyAsync(p.d_tw, t32.data(), N * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
     FBS_CUDA(cudaMemcpyAsync(p.d_tw64, t64.data(), N * sizeof(double2), cudaMemcpyHostToDevice, p.stream));
+    // twiddles of the evaluation grid
+    const int M = p.M;
+    std::vector<float2> tm(M);
+    for (int k = 0; k < M; ++k) {
+        double ang = -2.0 * M_PI * (double)k / (double)M;
+        double c = cos(ang), s = sin(ang);
+        if (4 * k == M) { c = 0.0; s = -1.0; }
+        if (2 * k == M) { c = -1.0; s = 0.0; }
+        if (4 * k == 3 * M) { c = 0.0; s = 1.0; }
+        tm[k] = make_float2((float)c, (float)s);
+    }
+    p.d_twM = (float2 *)p.dalloc(M * sizeof(float2));
+    FBS_CUDA(cudaMemcpyAsync(p.d_twM, tm.data(), M * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
 }
 
 void launch_forward(Plan &p, const float *d_field) {
@@ -531,19 +573,19 @@ static int max_dzb(const Plan &p, int bin0, int nb) {
 }
 
 void launch_inverse_x(Plan &p, bool) {
-    const int N = p.N;
+    const int N = p.M;  // inverse transforms run on the evaluation grid
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
     KTimer t(p, KC_INV_X);
     auto k = inv_x_kernel<float, false>;
     allow_smem(k, sm);
     dim3 grid(max_inv_x_grid(p, 0, p.nbins, nl), p.nbins);
-    k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.box, p.d_geom, 0, p.d_A, nl, p.fN, p.d_tw);
+    k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, p.d_geom, 0, p.d_A, nl, p.fM, p.d_twM);
     FBS_CUDA(cudaGetLastError());
 }
 
 void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
-    const int N = p.N;
+    const int N = p.M;  // evaluation grid
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
     {
@@ -551,19 +593,19 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
         auto k = inv_y_kernel<float>;
         allow_smem(k, sm);
         dim3 grid((max_dzb(p, 0, p.nbins) + nl - 1) / nl, nx, p.nbins);
-        k<<<grid, kThreads, sm, p.stream>>>(p.d_A, p.d_geom, 0, N, x0, p.d_G, 0, nl, p.fN, p.d_tw);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_A, p.d_geom, 0, N, x0, p.d_G, 0, nl, p.fM, p.d_twM);
         FBS_CUDA(cudaGetLastError());
     }
     if (zfast_ok(N) && !getenv("FBS_GENERIC_Z")) {
         KTimer t(p, KC_INV_Z);
         dim3 grid(zstage_row_groups(N), nx, p.nbins);
         const long long obs = (long long)p.slab * N * N;
-        switch (N) {
-            case 64: inv_z_fast_kernel<64, 8, 0><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
-            case 128: inv_z_fast_kernel<128, 4, 4><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
-            case 256: inv_z_fast_kernel<256, 8, 4><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
-            default: inv_z_fast_kernel<512, 8, 8><<<grid, 256, 0, p.stream>>>(p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_tw); break;
-        }
+#define FBS_ZL(n, t, lp, a, b, c, d)                                                          \
+    if (N == n)                                                                               \
+        inv_z_fast_kernel<n, t, lp, a, b, c, d><<<grid, t * lp, 0, p.stream>>>(                \
+            p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_twM);
+        FBS_ZFAST_LIST(FBS_ZL)
+#undef FBS_ZL
         FBS_CUDA(cudaGetLastError());
     } else {
         KTimer t(p, KC_INV_Z);
@@ -571,8 +613,8 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
         allow_smem(k, sm);
         dim3 grid((N + 2 * nl - 1) / (2 * nl), nx, p.nbins);
         k<<<grid, kThreads, sm, p.stream>>>(p.d_G, p.d_geom, 0, N, x0, islab,
-                                            (long long)p.slab * N * N, p.d_sumsq_part, nl, p.fN,
-                                            p.d_tw);
+                                            (long long)p.slab * N * N, p.d_sumsq_part, nl, p.fM,
+                                            p.d_twM);
         FBS_CUDA(cudaGetLastError());
     }
 }

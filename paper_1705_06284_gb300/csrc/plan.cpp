@@ -183,8 +183,17 @@ static void enumerate_shells(Plan &p, std::vector<long long> &mn, std::vector<lo
         }
 }
 
+// Smallest even 2^a 3^b grid M with M > order * R (the degree of a product of
+// `order` shell fields), at most N; N itself for aliased or full-grid plans.
+static int eval_grid(int N, int R, int order, unsigned flags) {
+    if (flags & (FBS_FLAG_FULL_GRID | FBS_FLAG_ALLOW_ALIASED)) return N;
+    for (int M = std::max(8, order * R + 1); M < N; ++M)
+        if (good_N(M)) return M;
+    return N;
+}
+
 static void build_geometry(Plan &p) {
-    const int N = p.N;
+    const int N = p.M;  // the inverse stages run on the evaluation grid
     p.geom.assign(p.nbins, BinGeom{});
     int R = 0;
     long long aoff = 0;
@@ -208,10 +217,13 @@ static void build_geometry(Plan &p) {
         R = std::max(R, g.Rb);
     }
     p.A_elems = aoff;
-    p.box.N = N;
+    const int NF = p.N;  // forward transforms run on the input grid
+    p.box.N = NF;
     p.box.R = R;
-    p.box.D = (2 * R + 1 > N) ? N : 2 * R + 1;
-    p.box.Dz = std::min(R, N / 2) + 1;
+    p.box.D = (2 * R + 1 > NF) ? NF : 2 * R + 1;
+    p.box.Dz = std::min(R, NF / 2) + 1;
+    p.boxM = p.box;
+    p.boxM.N = N;
     long long gplane = 0;
     for (int b = 0; b < p.nbins; ++b)
         if (!p.geom[b].empty) gplane += (long long)N * p.geom[b].Dzb;
@@ -222,7 +234,7 @@ static void set_slab_offsets(Plan &p) {
     long long goff = 0;
     for (int b = 0; b < p.nbins; ++b) {
         p.geom[b].G_off = goff;
-        if (!p.geom[b].empty) goff += (long long)p.slab * p.N * p.geom[b].Dzb;
+        if (!p.geom[b].empty) goff += (long long)p.slab * p.M * p.geom[b].Dzb;
     }
 }
 
@@ -439,6 +451,13 @@ static void create_plan(Plan &p, const double *edges) {
     }
     std::vector<long long> mn, mx;
     enumerate_shells(p, mn, mx);
+    {
+        int R = 0;
+        for (int b = 0; b < nb; ++b)
+            if (p.shell[b]) R = std::max(R, std::min(isqrt_floor(p.thr[b + 1] - 1), N / 2));
+        p.M = eval_grid(N, R, (p.flags & FBS_FLAG_TRISPECTRUM) ? 4 : 3, p.flags);
+        p.fM = make_factors(p.M);
+    }
     build_geometry(p);
 
     // device geometry + twiddles (needed by the count path)
@@ -487,11 +506,12 @@ static void create_plan(Plan &p, const double *edges) {
     p.qgrp = item_groups(p.qtask, 8192);
 
     // slab size: shell fields + y-stage scratch of one slab within the budget
-    const long long per_plane = (long long)nb * N * N * 4 + p.G_plane * 8;
+    const int M = p.M;
+    const long long per_plane = (long long)nb * M * M * 4 + p.G_plane * 8;
     long long budget = slab_budget_bytes();
-    int slab = (int)std::max<long long>(1, std::min<long long>(N, budget / std::max<long long>(1, per_plane)));
-    int nslabs = (N + slab - 1) / slab;
-    slab = (N + nslabs - 1) / nslabs;  // balance the slabs
+    int slab = (int)std::max<long long>(1, std::min<long long>(M, budget / std::max<long long>(1, per_plane)));
+    int nslabs = (M + slab - 1) / slab;
+    slab = (M + nslabs - 1) / nslabs;  // balance the slabs
     p.slab = slab;
     p.nslabs = nslabs;
     set_slab_offsets(p);
@@ -503,7 +523,7 @@ static void create_plan(Plan &p, const double *edges) {
     p.d_ybuf = (float2 *)p.dalloc((size_t)N * p.box.D * p.box.Dz * sizeof(float2));
     p.d_A = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.A_elems) * sizeof(float2));
     p.d_G = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.G_plane * p.slab) * sizeof(float2));
-    p.d_I = (float *)p.dalloc((size_t)nb * p.slab * N * N * sizeof(float));
+    p.d_I = (float *)p.dalloc((size_t)nb * p.slab * M * M * sizeof(float));
     // work lists
     p.d_tpb = upload(p, p.ttask.pb);
     p.d_tpc = upload(p, p.ttask.pc);
@@ -524,7 +544,7 @@ static void create_plan(Plan &p, const double *edges) {
     p.d_tpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, ntrip) * sizeof(double));
     p.d_qpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, nquad) * sizeof(double));
     p.d_sumsq = (double *)p.dalloc(nb * sizeof(double));
-    p.d_sumsq_part = (double *)p.dalloc((size_t)nb * N * zstage_row_groups(N) * sizeof(double));
+    p.d_sumsq_part = (double *)p.dalloc((size_t)nb * M * zstage_row_groups(M) * sizeof(double));
     p.d_tnum = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
     p.d_qnum = (double *)p.dalloc(std::max(1, nquad) * sizeof(double));
     p.d_B = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
@@ -549,10 +569,11 @@ static void run_field(Plan &p, const float *field, bool quads) {
         FBS_CUDA(cudaMemsetAsync(tc_error_flag(p), 0, sizeof(int), p.stream));
     launch_forward(p, d_in);
     launch_inverse_x(p, false);
-    const long long plane = (long long)N * N;
+    const int M = p.M;
+    const long long plane = (long long)M * M;
     for (int s = 0; s < p.nslabs; ++s) {
         const int x0 = s * p.slab;
-        const int nx = std::min(p.slab, N - x0);
+        const int nx = std::min(p.slab, M - x0);
         if (nx <= 0) break;
         launch_inverse_yz_slab(p, x0, nx, p.d_I);
         const long long npts = (long long)nx * plane;
@@ -830,6 +851,8 @@ fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, 
 double fbs_plan_create_ms(const fbs_plan *plan) { return plan ? plan->create_ms : -1.0; }
 
 double fbs_plan_count_margin(const fbs_plan *plan) { return plan ? plan->count_margin : -1.0; }
+
+int fbs_plan_eval_grid(const fbs_plan *plan) { return plan ? plan->M : FBS_ERR_ARG; }
 
 int fbs_plan_quad_counts_exact(const fbs_plan *plan) {
     if (!plan) return FBS_ERR_ARG;

@@ -380,3 +380,46 @@ def test_golden_lognormal32_reproduces():
         assert [int(v) for v in r[:4]] == [int(t[0]), int(t[1]), int(t[2]), int(n)]
         assert abs(float(r[4]) - B) <= 1e-12 * abs(B)
     assert [int(v) for v in meta["shell"]] == list(d["shell"])
+
+
+# ---------------------------------------------------------------- evaluation grid
+def _embed_shell_field(D, bins, b, M):
+    """Shell field of bin b evaluated on an M^3 grid: the same modes (all with
+    |m_j| < M/2) placed at m mod M, unnormalised inverse DFT of length M."""
+    N = D.shape[0]
+    f = np.fft.fftfreq(N, 1.0 / N).astype(int)
+    idx = np.nonzero(bins == b)
+    E = np.zeros((M, M, M), dtype=np.complex128)
+    E[f[idx[0]] % M, f[idx[1]] % M, f[idx[2]] % M] = D[idx]
+    return (np.fft.ifftn(E) * M ** 3).real
+
+
+@pytest.mark.parametrize("order,M", [(3, 20), (3, 24), (4, 28)])
+def test_products_sum_on_reduced_grid(order, M):
+    """A product of `order` shell fields holding only modes with |m_j| <= R is a
+    trigonometric polynomial of degree <= order*R per axis, so its sum over the
+    N^3 grid is (N/M)^3 times its sum over any M^3 grid with M > order*R (the
+    device path evaluates on such an M).  Checked in FP64 on every triplet /
+    quadruplet of a small plan; M = order*R exactly (aliased) must differ."""
+    N, L = 32, 100.0
+    kf = 2 * math.pi / L
+    edges = kf * np.array([0.5, 2.5, 4.5, 6.5])  # R = 6
+    R = 6
+    f = fields.quadratic_local(N, 0.5, -1.5, 0.3, seed=5)
+    D = oracle.spectrum(f)
+    bins = oracle.bin_index(N, oracle.thresholds(edges, L))
+    nb = 3
+    full = [oracle.shell_field(D, bins, b) for b in range(nb)]
+    red = [_embed_shell_field(D, bins, b, M) for b in range(nb)]
+    alias = [_embed_shell_field(D, bins, b, order * R) for b in range(nb)]
+    scale = (N / M) ** 3
+    worst_alias = 0.0
+    for combo in itertools.combinations_with_replacement(range(nb), order):
+        pf = np.prod([full[b] for b in combo], axis=0)
+        pr = np.prod([red[b] for b in combo], axis=0)
+        pa = np.prod([alias[b] for b in combo], axis=0)
+        ref = pf.sum()
+        mag = np.abs(pf).sum()
+        assert abs(scale * pr.sum() - ref) <= 1e-12 * mag, combo
+        worst_alias = max(worst_alias, abs((N / (order * R)) ** 3 * pa.sum() - ref) / mag)
+    assert worst_alias > 1e-6  # one grid point too few aliases some product

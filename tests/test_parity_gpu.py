@@ -199,3 +199,43 @@ def test_plane_waves_closed_form_on_gpu():
         npix = N ** 3
         expect = 2 * (npix / 2) ** 3 * np.prod(A) * math.cos(sum(phi)) * npix
         assert abs(num[i] - expect) <= 1e-4 * abs(expect)
+
+
+@pytest.mark.parametrize("N,L,nb,precision,quads,M", [
+    (64, 200.0, 8, "fp32", False, 48),
+    (72, 72.0, 4, "bf16x3", False, 54),      # M = 2 * 3^3: radix-3 only inverse stages
+    (32, 100.0, 6, "fp32", True, 32),        # 4R + 1 > 24: no smaller grid
+    (48, 60.0, 6, "bf16x3", False, 36),
+])
+def test_reduced_grid_matches_full_grid(N, L, nb, precision, quads, M):
+    """The default plan evaluates the shell fields on M^3 (M > 3R, or 4R with
+    quadruplets) and rescales the sums by (N/M)^3; a FULL_GRID plan evaluates
+    on N^3.  Both must agree with each other and with the oracle."""
+    edges = fields.linear_edges(N, L, nb)
+    f32 = _field("quadratic", N, 11).astype(np.float32)
+    with fbs.Plan(N, L, edges, precision=precision, trispectrum=quads) as red, \
+            fbs.Plan(N, L, edges, precision=precision, trispectrum=quads, full_grid=True) as full:
+        assert red.eval_grid == M
+        assert full.eval_grid == N
+        assert np.array_equal(red.N_tri, full.N_tri)
+        if quads:
+            import torch
+            f = torch.from_numpy(f32).cuda()
+            Tr, Br, Pr = red.trispectrum(f)
+            Tf, Bf, Pf = full.trispectrum(f)
+            torch.cuda.synchronize()
+            Br, Bf, Pr, Pf, Tr, Tf = (x.cpu().numpy() for x in (Br, Bf, Pr, Pf, Tr, Tf))
+            assert np.array_equal(Tr, Tf)  # same grid, same kernels: bit-identical
+        else:
+            Br, Pr = run(red, f32)
+            Bf, Pf = run(full, f32)
+        check_bispectrum(red, Br, Pr, f32, L, edges, precision)
+        check_bispectrum(full, Bf, Pf, f32, L, edges, precision)
+    assert np.all(rel_err(Pr, Pf)[np.isfinite(Pf)] < 2e-5)
+
+
+def test_aliased_plans_use_the_input_grid():
+    N, L = 32, 100.0
+    edges = fields.linear_edges(N, L, 4)
+    with fbs.Plan(N, L, edges, allow_aliased=True) as plan:
+        assert plan.eval_grid == N
