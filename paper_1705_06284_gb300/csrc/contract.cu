@@ -125,12 +125,13 @@ __global__ void __launch_bounds__(kCThreads) contract_fp32_kernel(
 
 // ------------------------------------------------------------------ reduce
 // out[i] = sum_r part[r][i] in a fixed order (deterministic).
-__global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, int n,
+// out[i] = scale * sum_r part[r*ld + i], i < n (rows summed in a fixed order).
+__global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, int n, int ld,
                                    double *__restrict__ out, double scale) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
-    for (int r = 0; r < rows; ++r) s += part[(long long)r * n + i];
+    for (int r = 0; r < rows; ++r) s += part[(long long)r * ld + i];
     out[i] = scale * s;
 }
 
@@ -296,13 +297,18 @@ void launch_contract_fp32(Plan &p, const float *islab, long long npts, long long
 }
 
 void zero_partials(Plan &p, bool quads) {
-    if (p.d_tpart && p.ttask.nitems > 0)
-        FBS_CUDA(cudaMemsetAsync(p.d_tpart, 0, (size_t)p.part_blocks * p.ttask.nitems * sizeof(double),
+    if (p.fused_active) {
+        FBS_CUDA(cudaMemsetAsync(p.d_fpart, 0,
+                                 (size_t)p.part_blocks * (p.ttask.nitems + p.qtask.nitems) * sizeof(double),
                                  p.stream));
-    if (quads && p.d_qpart && p.qtask.nitems > 0)
-        FBS_CUDA(cudaMemsetAsync(p.d_qpart, 0, (size_t)p.part_blocks * p.qtask.nitems * sizeof(double),
-                                 p.stream));
-    // every sum-of-squares partial is overwritten by the z stage (empty bins: 0)
+    } else {
+        if (p.d_tpart && p.ttask.nitems > 0)
+            FBS_CUDA(cudaMemsetAsync(p.d_tpart, 0, (size_t)p.part_blocks * p.ttask.nitems * sizeof(double),
+                                     p.stream));
+        if (quads && p.d_qpart && p.qtask.nitems > 0)
+            FBS_CUDA(cudaMemsetAsync(p.d_qpart, 0, (size_t)p.part_blocks * p.qtask.nitems * sizeof(double),
+                                     p.stream));
+    }
     FBS_CUDA(cudaMemsetAsync(p.d_sumsq_part, 0,
                              (size_t)p.nbins * p.M * zstage_row_groups(p.M) * sizeof(double), p.stream));
 }
@@ -315,14 +321,18 @@ void launch_reduce_and_normalise(Plan &p, bool quads) {
         const double scale = r * r * r;
         int n = p.ttask.nitems;
         if (n > 0) {
-            reduce_rows_kernel<<<(n + 255) / 256, 256, 0, p.stream>>>(p.d_tpart, p.part_blocks, n,
-                                                                      p.d_tnum, scale);
+            const double *src = p.fused_active ? p.d_fpart : p.d_tpart;
+            const int ld = p.fused_active ? n + p.qtask.nitems : n;
+            reduce_rows_kernel<<<(n + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, n, ld, p.d_tnum,
+                                                                      scale);
             FBS_CUDA(cudaGetLastError());
         }
         if (quads && p.qtask.nitems > 0) {
             int m = p.qtask.nitems;
-            reduce_rows_kernel<<<(m + 255) / 256, 256, 0, p.stream>>>(p.d_qpart, p.part_blocks, m,
-                                                                      p.d_qnum, scale);
+            const double *src = p.fused_active ? p.d_fpart + p.ttask.nitems : p.d_qpart;
+            const int ld = p.fused_active ? m + p.ttask.nitems : m;
+            reduce_rows_kernel<<<(m + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, m, ld, p.d_qnum,
+                                                                      scale);
             FBS_CUDA(cudaGetLastError());
         }
         {
@@ -365,7 +375,7 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
     dim3 g(blocks, ngrp);
     count_kernel<<<g, 256, sm, p.stream>>>(noct, nbins_all, H, d_items, arity, nitems, grp, part);
     FBS_CUDA(cudaGetLastError());
-    reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, d_den, 1.0);
+    reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, nitems, d_den, 1.0);
     FBS_CUDA(cudaGetLastError());
     FBS_CUDA(cudaFreeAsync(part, p.stream));
 }

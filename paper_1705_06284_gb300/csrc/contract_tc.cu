@@ -20,12 +20,16 @@
 // Every wait on an mbarrier is bounded (about one second of clock cycles);
 // on timeout the kernel records an error flag, waits (bounded) for its own
 // MMAs, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <array>
+#include <map>
+#include <utility>
 
 #include "fbs_internal.h"
 
@@ -51,6 +55,7 @@ struct TcPair {
 struct TcJob {
     TcPair *d_pairs = nullptr;
     int2 *d_inner = nullptr;
+    int *d_iout = nullptr;   // job item (pair-major, inner rows ascending) -> output column
     int npairs = 0, ntiles = 0, ninner = 0, Npad = 0, maxloc = 0, maxtiles = 0;
     std::vector<int> grp;  // tile ranges of the CTA groups
     int *d_grp = nullptr;
@@ -71,7 +76,7 @@ struct WideJob {
 };
 
 struct TcState {
-    TcJob trip, quad;
+    TcJob trip, quad, fused;
     WideJob wtrip, wquad;
     int *d_err = nullptr;
 };
@@ -132,15 +137,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
@@ -189,39 +185,51 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
 
 }  // namespace
 
-// Warp roles: warps 0..7 produce (stage the fields, write operand B to
-// shared memory, form the pair products into tensor memory, flush the
-// accumulators); warp 8 allocates tensor memory and one of its threads issues
-// every MMA.  Hand-offs go through mbarriers, never through __syncthreads.
-constexpr int kProdWarps = 16;   // 4 per TMEM lane quarter, each 16 of the 64 points of a row
+// Warp roles of the narrow kernel: warps 0..15 produce (operand B into
+// shared memory, the pair products into tensor memory, the accumulator
+// flushes); warp 16 allocates tensor memory and one of its threads issues
+// every MMA; one thread of warp 17 streams the shell fields of each chunk
+// into a ring of shared-memory stages with TMA.  Every hand-off is an
+// mbarrier; no role waits on a CTA-wide barrier inside the main loop.
+constexpr int kProdWarps = 16;            // 4 per TMEM lane quarter, 16 of the 64 points of a row each
 constexpr int kPPT = 4 * KC / kProdWarps;  // points of a row per producer thread per tile
-constexpr int kTcThreads = (kProdWarps + 1) * 32;
-constexpr int kAStages = 3;      // maximum; the launch picks 2 or 3 to fit tensor memory
-constexpr int kAStageCols = 64;  // 32 columns hi + 32 columns lo (64 BF16 per row each)
+constexpr int kMmaWarp = kProdWarps;
+constexpr int kLoadWarp = kProdWarps + 1;
+constexpr int kTcThreads = (kProdWarps + 2) * 32;
+constexpr int kAStageCols = 64;           // 32 columns hi + 32 columns lo (64 BF16 per row each)
+constexpr int kMaxAStages = 3;
+constexpr int kMaxFieldStages = 4;
 
 struct TcBars {
-    uint64_t full[kAStages], empty[kAStages], bfull[2], bempty[2], accr, accf;
+    uint64_t sfull[kMaxFieldStages], sempty[kMaxFieldStages];
+    uint64_t full[kMaxAStages], empty[kMaxAStages], bfull[2], bempty[2], accr, accf;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait that gives up at once after any other wait of the CTA timed
-// out (the abort flag is sticky), so no role can strand another.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
-        : "memory");
-    return ok != 0;
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
 }
 
+// 2-D tiled TMA load (x = point, y = bin) into shared memory; completion is
+// counted in bytes on the mbarrier.  Points past the tensor's end read zero.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait that gives up at once after any other wait of the CTA timed
+// out (the abort flag is sticky), so no role can strand another.
 __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                           int *err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;  // ready: no clock read, no flag read
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
@@ -234,19 +242,27 @@ __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volati
     return true;
 }
 
+// Position in a ring of S slots: the slot and the parity of its use count
+// (the phase a consumer waits for; a producer refilling the slot waits for
+// the opposite parity once every slot has been used).
+template <int S>
+struct Ring {
+    int slot = 0;
+    uint32_t phase = 0;
+    bool warm = false;
+    __device__ __forceinline__ void next() {
+        if (++slot == S) {
+            slot = 0;
+            phase ^= 1u;
+            warm = true;
+        }
+    }
+};
+
 __device__ __forceinline__ void tmem_st8a(uint32_t taddr, const uint32_t *r) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
         "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-            taddr),
-        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
         : "memory");
 }
 
@@ -276,14 +292,34 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         : "memory");
 }
 
+// Compensated (Kahan) FP32 running sum: x = sum, y = compensation; the
+// value is x - y.  Explicit round-to-nearest operations keep the compiler
+// from contracting or reassociating them.
+__device__ __forceinline__ void kahan_add(float2 &a, float v) {
+    const float y = __fsub_rn(v, a.y);
+    const float t = __fadd_rn(a.x, y);
+    a.y = __fsub_rn(__fsub_rn(t, a.x), y);
+    a.x = t;
+}
+
+// Address of points 4j..4j+3 of bin row b in a field stage: two halves of 32
+// points, each [rows][128 B] in the TMA 128-byte swizzle (16-byte chunk j of
+// row b stored at chunk j ^ (b mod 8)).
+__device__ __forceinline__ const float4 *stage_at(const unsigned char *st, int half_bytes, int b, int j) {
+    return reinterpret_cast<const float4 *>(st + (j >> 3) * half_bytes + b * 128 +
+                                            (((j & 7) ^ (b & 7)) << 4));
+}
+
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
+// NST: A stages in tensor memory; NSTG: field stages in shared memory.
+template <int NST, int NSTG>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    contract_tc_kernel(const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
-                       int Npad, int tstride, int ninner, const int2 *__restrict__ inner,
+    contract_tc_kernel(const __grid_constant__ CUtensorMap fmap, long long npts, int nbins, int Npad,
+                       int tstride, int ninner, const int2 *__restrict__ inner,
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
-                       int nst, int *__restrict__ err) {
+                       int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ TcBars bars;
     __shared__ int2 s_inner[kMaxInner];
@@ -304,23 +340,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int w = 0; w < kMaxInner / 32; ++w) nloc += __popc(pairs[p_last - 1].mask[w]);
     }
 
-    // ---- shared memory: B tiles (1024-aligned), staged fields, FP64 sums, pair bins
+    // ---- shared memory: B tiles and field stages (1024-aligned), sums, pair bins
     uintptr_t base = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023;
     unsigned char *sm = reinterpret_cast<unsigned char *>(base);
     const int b_tile = Npad * 128;
     unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_tile;
-    float *stage = reinterpret_cast<float *>(sm + 4 * b_tile);
-    const int stage_floats = nbins * kStageLd;
-    double *acc = reinterpret_cast<double *>(stage + 2 * stage_floats);
+    const int half_bytes = ((nbins + 7) & ~7) * 128;
+    unsigned char *const stg = sm + 4 * b_tile;
+    float2 *acc = reinterpret_cast<float2 *>(stg + NSTG * 2 * half_bytes);
     int2 *pbc = reinterpret_cast<int2 *>(acc + nloc);  // (b, c) of every row of every tile
 
     const int acc_cols = ((ntl * tstride + 31) / 32) * 32;
-    const int tmem_cols_needed = acc_cols + 2 * kAStageCols;
+    const int tmem_cols_needed = acc_cols + NST * kAStageCols;
     int ncols = 32;
     while (ncols < tmem_cols_needed) ncols <<= 1;
 
     if (tid == 0) {
-        for (int i = 0; i < kAStages; ++i) {
+        for (int i = 0; i < NSTG; ++i) {
+            mbar_init(&bars.sfull[i], 1);
+            mbar_init(&bars.sempty[i], kProdWarps);
+        }
+        for (int i = 0; i < NST; ++i) {
             mbar_init(&bars.full[i], kProdWarps);
             mbar_init(&bars.empty[i], 1);
         }
@@ -333,14 +373,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
-    if (warp == kProdWarps) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
                      "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < nloc; i += kTcThreads) acc[i] = 0.0;
+    for (int i = tid; i < nloc; i += kTcThreads) acc[i] = make_float2(0.f, 0.f);
     for (int i = tid; i < ninner; i += kTcThreads) s_inner[i] = inner[i];
     for (int i = tid; i < ntl * 128; i += kTcThreads) {
         const int p = p_first + i;
@@ -360,23 +400,50 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const long long c0 = nchunks * blockIdx.x / gridDim.x;
     const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
 
-    if (warp == kProdWarps) {
+    if (warp == kLoadWarp) {
+        // ================= field loader (one thread) =================
+        if (lane == 0 && c0 < c1) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&fmap)) : "memory");
+            const uint32_t bytes = 2u * (uint32_t)nbins * 128u;
+            Ring<NSTG> rs;
+            long long issued = 0;
+            for (long long ci = c0; ci < c1; ++ci) {
+                if (rs.warm && !role_wait(&bars.sempty[rs.slot], rs.phase ^ 1u, abortp, err, 10)) break;
+                const uint32_t dst = smem_u32(stg + rs.slot * 2 * half_bytes);
+                const int x = (int)(ci * KC);
+                mbar_expect_tx(&bars.sfull[rs.slot], bytes);
+                tma_load_2d(dst, &fmap, x, 0, &bars.sfull[rs.slot]);
+                tma_load_2d(dst + half_bytes, &fmap, x + 32, 0, &bars.sfull[rs.slot]);
+                rs.next();
+                ++issued;
+            }
+            // every copy into this CTA's shared memory has landed before it exits (own limit)
+            for (long long j = issued > NSTG ? issued - NSTG : 0; j < issued; ++j) {
+                const int slot = (int)(j % NSTG);
+                if (!mbar_wait(&bars.sfull[slot], (uint32_t)((j / NSTG) & 1))) atomicExch(err, 16);
+            }
+        }
+    } else if (warp == kMmaWarp) {
         // ================= MMA issuer (one thread) =================
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(128, Npad);
-            long long gA = 0, gB = 0, nfl = 0;
+            Ring<NST> ra;
+            Ring<2> rb;
+            long long nfl = 0;
+            int last_slot = -1;
+            uint32_t last_phase = 0;
             bool fresh = true;
             int since = 0;
             for (long long ci = c0; ci < c1; ++ci) {
-                const int sb = (int)(gB & 1);
-                const bool okb = role_wait(&bars.bfull[sb], (uint32_t)((gB >> 1) & 1), abortp, err, 11);
+                const int sb = rb.slot;
+                const bool okb = role_wait(&bars.bfull[sb], rb.phase, abortp, err, 11);
                 const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + sb * b_tile));
                 const uint64_t dbl = sdesc_sw128(smem_u32(Bl0 + sb * b_tile));
                 for (int lt = 0; lt < ntl; ++lt) {
-                    const int as = (int)(gA & 1);
-                    const bool oka = role_wait(&bars.full[as], (uint32_t)((gA >> 1) & 1), abortp, err, 12);
+                    const int as = ra.slot;
+                    const bool oka = role_wait(&bars.full[as], ra.phase, abortp, err, 12);
                     tc_fence_after();
-                    if (okb && oka && !*abortp) {
+                    if (okb && oka) {  // a failed wait leaves ok false (the abort flag is sticky)
                         const uint32_t d = tmem + (uint32_t)(lt * tstride);
                         const uint32_t ah = tmem + (uint32_t)(acc_cols + as * kAStageCols);
                         const uint32_t al = ah + 32u;
@@ -397,10 +464,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         }
                     }
                     mma_commit(&bars.empty[as]);
-                    ++gA;
+                    last_slot = as;
+                    last_phase = ra.phase;
+                    ra.next();
                 }
                 mma_commit(&bars.bempty[sb]);
-                ++gB;
+                rb.next();
                 fresh = false;
                 if (++since == flush_every || ci == c1 - 1) {
                     mma_commit(&bars.accr);
@@ -412,76 +481,61 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
             // drain: every MMA complete before tensor memory is released (own limit)
-            if (gA > 0) {
-                const int as = (int)((gA - 1) & 1);
-                if (!mbar_wait(&bars.empty[as], (uint32_t)(((gA - 1) >> 1) & 1))) atomicExch(err, 14);
-            }
+            if (last_slot >= 0 && !mbar_wait(&bars.empty[last_slot], last_phase)) atomicExch(err, 14);
         }
     } else {
-        // ================= producers (warps 0..7) =================
+        // ================= producers (warps 0..15) =================
         const int q = warp & 3, kq = warp >> 2;  // lane quarter, kPPT-point slice of the chunk
         const int r = 32 * q + lane;             // operand-A row (TMEM lane) of this thread
         const int ptid = tid;                    // 0 .. 32*kProdWarps-1
-        auto prefetch = [&](long long ch, int s) {
-            const long long q0 = ch * KC;
-            float *dst = stage + s * stage_floats;
-            for (int i = ptid; i < nbins * (KC / 4); i += kProdWarps * 32) {
-                int b = i / (KC / 4), k4 = i - b * (KC / 4);
-                long long qq = q0 + 4LL * k4;
-                long long rem = npts - qq;
-                int bytes = rem >= 4 ? 16 : (rem > 0 ? (int)rem * 4 : 0);
-                const float *src = bytes ? (I + b * bin_stride + qq) : I;
-                cp_async16(smem_u32(dst + b * kStageLd + 4 * k4), src, bytes);
-            }
-            cp_async_commit();
-        };
-        long long gA = 0, gB = 0, nfl = 0;
+        Ring<NSTG> rs;
+        Ring<NST> ra;
+        Ring<2> rb;
+        long long nfl = 0;
         int since = 0;
-        if (c0 < c1) prefetch(c0, 0);
         for (long long ci = c0; ci < c1; ++ci) {
-            const int s = (int)((ci - c0) & 1);
-            cp_async_wait_all();
-            asm volatile("bar.sync 1, %0;" ::"n"(kProdWarps * 32) : "memory");
-            if (ci + 1 < c1) prefetch(ci + 1, s ^ 1);
-            const float *st = stage + s * stage_floats;
+            role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 20);
+            const unsigned char *st = stg + rs.slot * 2 * half_bytes;
             // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
-            const int sb = (int)(gB & 1);
-            if (gB >= 2) role_wait(&bars.bempty[sb], (uint32_t)(((gB - 2) >> 1) & 1), abortp, err, 21);
+            const int sb = rb.slot;
+            if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21);
             for (int u = ptid; u < ninner * 8; u += kProdWarps * 32) {
-                int row = u % ninner, j = u / ninner;
+                const int row = u % ninner, j = u / ninner;
                 const int2 in = s_inner[row];
-                const float4 *src = reinterpret_cast<const float4 *>(st + in.x * kStageLd + 8 * j);
-                float4 v0 = src[0], v1 = src[1];
+                float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
+                float4 v1 = *stage_at(st, half_bytes, in.x, 2 * j + 1);
                 if (in.y >= 0) {
-                    const float4 *s2 = reinterpret_cast<const float4 *>(st + in.y * kStageLd + 8 * j);
-                    float4 w0 = s2[0], w1 = s2[1];
+                    const float4 w0 = *stage_at(st, half_bytes, in.y, 2 * j);
+                    const float4 w1 = *stage_at(st, half_bytes, in.y, 2 * j + 1);
                     v0 = make_float4(v0.x * w0.x, v0.y * w0.y, v0.z * w0.z, v0.w * w0.w);
                     v1 = make_float4(v1.x * w1.x, v1.y * w1.y, v1.z * w1.z, v1.w * w1.w);
                 }
                 float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                 uint4 h, l;
                 split8(v, h, l);
-                uint32_t off = sw128_off(row, j);
+                const uint32_t off = sw128_off(row, j);
                 *reinterpret_cast<uint4 *>(Bh0 + sb * b_tile + off) = h;
                 *reinterpret_cast<uint4 *>(Bl0 + sb * b_tile + off) = l;
             }
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.bfull[sb]);
-            ++gB;
-            // ---- operand A: pair products of this thread's row, 32 points, into TMEM
+            rb.next();
+            // ---- operand A: pair products of this thread's row, kPPT points, into TMEM
             for (int lt = 0; lt < ntl; ++lt) {
-                const int as = (int)(gA & 1);
-                if (gA >= 2) role_wait(&bars.empty[as], (uint32_t)(((gA - 2) >> 1) & 1), abortp, err, 22);
+                const int as = ra.slot;
+                if (ra.warm) role_wait(&bars.empty[as], ra.phase ^ 1u, abortp, err, 22);
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
                 uint32_t hw[kPPT / 2], lw[kPPT / 2];
                 if (bc.x >= 0) {
-                    const float4 *rb = reinterpret_cast<const float4 *>(st + bc.x * kStageLd + kPPT * kq);
-                    const float4 *rc = reinterpret_cast<const float4 *>(st + bc.y * kStageLd + kPPT * kq);
 #pragma unroll
                     for (int j = 0; j < kPPT / 8; ++j) {
-                        float4 b0 = rb[2 * j], b1 = rb[2 * j + 1], e0 = rc[2 * j], e1 = rc[2 * j + 1];
+                        const int jj = (kPPT / 4) * kq + 2 * j;
+                        const float4 b0 = *stage_at(st, half_bytes, bc.x, jj);
+                        const float4 b1 = *stage_at(st, half_bytes, bc.x, jj + 1);
+                        const float4 e0 = *stage_at(st, half_bytes, bc.y, jj);
+                        const float4 e1 = *stage_at(st, half_bytes, bc.y, jj + 1);
                         float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
                                       b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
                         uint4 h, l;
@@ -495,20 +549,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
                 const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + (kPPT / 2) * kq);
-                if constexpr (kPPT == 32) {
-                    tmem_st16(lanebase + col, hw);
-                    tmem_st16(lanebase + col + 32u, lw);
-                } else {
-                    tmem_st8a(lanebase + col, hw);
-                    tmem_st8a(lanebase + col + 32u, lw);
-                }
+                tmem_st8a(lanebase + col, hw);
+                tmem_st8a(lanebase + col + 32u, lw);
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.full[as]);
-                ++gA;
+                ra.next();
             }
-            // ---- flush: accumulators -> FP64 sums
+            // ---- the stage is consumed: hand it back to the loader
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.sempty[rs.slot]);
+            rs.next();
+            // ---- flush: accumulators -> compensated FP32 sums
             if (++since == flush_every || ci == c1 - 1) {
                 role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 23);
                 tc_fence_after();
@@ -516,24 +569,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     for (int lt = 0; lt < ntl; ++lt) {
                         const int p = (t0 + lt) * 128 + r;
                         const bool valid = p < npairs;
-                        TcPair pi;
-                        if (valid) pi = pairs[p];
+                        const TcPair *pp = pairs + (valid ? p : 0);
                         for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (kProdWarps / 4)) {
                             float v[8];
                             tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
                             if (!valid) continue;
+                            const int wsel = c8 >> 5;
+                            const unsigned wm = __ldg(&pp->mask[wsel]);
+                            const unsigned w = (wm >> (c8 & 31)) & 0xffu;
+                            if (!w) continue;
+                            int idx = __ldg(&pp->first) - it0 + __popc(wm & ((1u << (c8 & 31)) - 1u));
+                            for (int m = 0; m < wsel; ++m) idx += __popc(__ldg(&pp->mask[m]));
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                const int a = c8 + i;
-                                if (a >= kMaxInner) continue;
-                                const unsigned w = pi.mask[a >> 5];
-                                const unsigned bit = 1u << (a & 31);
-                                if (!(w & bit)) continue;
-                                int idx = pi.first - it0;
-                                for (int m = 0; m < (a >> 5); ++m) idx += __popc(pi.mask[m]);
-                                idx += __popc(w & (bit - 1u));
-                                acc[idx] += (double)v[i];
-                            }
+                            for (int i = 0; i < 8; ++i)
+                                if ((w >> i) & 1u) kahan_add(acc[idx++], v[i]);
                         }
                     }
                 }
@@ -544,15 +593,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 since = 0;
             }
         }
-        cp_async_wait_all();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kProdWarps)
+    if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     double *row = part + (long long)blockIdx.x * nitems_total;
-    for (int i = tid; i < nloc; i += kTcThreads) row[iout[it0 + i]] += acc[i];
+    for (int i = tid; i < nloc; i += kTcThreads) row[iout[it0 + i]] += (double)acc[i].x - (double)acc[i].y;
 }
 
 
@@ -830,8 +878,11 @@ __global__ void __launch_bounds__(kWideThreads, 1)
 }
 
 // ------------------------------------------------------------------ host side
-static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl) {
-    size_t b = 1024 + 4 * (size_t)Npad * 128 + 2 * (size_t)nbins * kStageLd * 4 + (size_t)nloc * 8 +
+// Dynamic shared memory of the narrow kernel: B tiles, nstg field stages,
+// compensated sums, pair bins.
+static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl, int nstg) {
+    const size_t half = (size_t)((nbins + 7) & ~7) * 128;
+    size_t b = 1024 + 4 * (size_t)Npad * 128 + (size_t)nstg * 2 * half + (size_t)nloc * 8 +
                (size_t)ntl * 128 * 8;
     return std::max<size_t>(b, 116 * 1024);  // > half the SM's shared memory: one CTA per SM
 }
@@ -848,58 +899,32 @@ static TcState &tc_state(Plan &p) {
     return *reinterpret_cast<TcState *>(p.tc);
 }
 
-// Build the device tables of one contraction from its pair-grouped task list.
-static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
-    job.built = true;
-    job.npairs = t.npairs;
-    job.ntiles = (t.npairs + 127) / 128;
-    // inner rows: single bins, or the distinct inner pairs of the quadruplets
-    std::vector<int2> inner;
-    std::vector<int> row_of;  // (a, b) -> inner row, a*nbins+b
-    if (!quads) {
-        for (int b = 0; b < p.nbins; ++b) inner.push_back(make_int2(b, -1));
-    } else {
-        row_of.assign((size_t)p.nbins * p.nbins, -1);
-        for (int e = 0; e < t.nitems; ++e) {
-            int key = t.ia[e] * p.nbins + t.ib[e];
-            if (row_of[key] < 0) row_of[key] = 0;
-        }
-        for (int a = 0; a < p.nbins; ++a)
-            for (int b = 0; b < p.nbins; ++b)
-                if (row_of[a * p.nbins + b] >= 0) {
-                    row_of[a * p.nbins + b] = (int)inner.size();
-                    inner.push_back(make_int2(a, b));
-                }
-    }
+// Group the pair tiles of a job (tensor memory and the compensated item sums
+// bound a group) and upload its tables.  hp: outer pairs (masks, first item),
+// inner: inner rows, iout: output column of every item in job order.
+static void finish_job(Plan &p, TcJob &job, const std::vector<TcPair> &hp, const std::vector<int2> &inner,
+                       const std::vector<int> &iout) {
+    job.npairs = (int)hp.size();
+    job.ntiles = (job.npairs + 127) / 128;
     job.ninner = (int)inner.size();
     if (job.ninner > kMaxInner || job.npairs == 0) return;  // not usable on the tensor cores
     job.Npad = std::max(16, ((job.ninner + 15) / 16) * 16);
-    std::vector<TcPair> hp(std::max(1, t.npairs));
-    for (int i = 0; i < t.npairs; ++i) {
-        TcPair q{};
-        q.b = t.pb[i];
-        q.c = t.pc[i];
-        q.first = t.pstart[i];
-        int prev = -1;
-        for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e) {
-            int n = quads ? row_of[t.ia[e] * p.nbins + t.ib[e]] : t.ia[e];
-            if (n <= prev) throw Failure{FBS_ERR_ARG, "tensor-core task list not sorted by inner row"};
-            prev = n;
-            q.mask[n >> 5] |= 1u << (n & 31);
-        }
-        hp[i] = q;
-    }
-    // groups of tiles: tensor memory (512 columns) and the FP64 item sums bound a group
+    auto items_of = [&](int pa, int pe) {
+        int n = 0;
+        for (int i = pa; i < pe; ++i)
+            for (int w = 0; w < kMaxInner / 32; ++w) n += __builtin_popcount(hp[i].mask[w]);
+        return n;
+    };
     const size_t smem_cap = 220 * 1024;
     job.grp.assign(1, 0);
     int cur_tiles = 0, cur_items = 0;
     job.maxloc = 0;
     for (int tt = 0; tt < job.ntiles; ++tt) {
-        int pa = tt * 128, pe = std::min(t.npairs, pa + 128);
-        int items = t.pstart[pe] - t.pstart[pa];
+        int pa = tt * 128, pe = std::min(job.npairs, pa + 128);
+        int items = items_of(pa, pe);
         const int acc_cols = (((cur_tiles + 1) * tile_stride(job.Npad) + 31) / 32) * 32;
         bool fits = acc_cols + 2 * kAStageCols <= 512 &&
-                    tc_smem_bytes(p.nbins, job.Npad, cur_items + items, cur_tiles + 1) <= smem_cap;
+                    tc_smem_bytes(p.nbins, job.Npad, cur_items + items, cur_tiles + 1, 2) <= smem_cap;
         if (cur_tiles > 0 && !fits) {
             job.grp.push_back(tt);
             job.maxloc = std::max(job.maxloc, cur_items);
@@ -914,7 +939,8 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     job.maxtiles = 0;
     for (size_t gi = 0; gi + 1 < job.grp.size(); ++gi)
         job.maxtiles = std::max(job.maxtiles, job.grp[gi + 1] - job.grp[gi]);
-    if (tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles) > smem_cap) return;
+    if (p.nbins > 256) return;  // one TMA box spans every bin
+    if (tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 2) > smem_cap) return;
     if ((((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32 + 2 * kAStageCols > 512) return;
     job.d_pairs = (TcPair *)p.dalloc(hp.size() * sizeof(TcPair));
     FBS_CUDA(cudaMemcpyAsync(job.d_pairs, hp.data(), hp.size() * sizeof(TcPair), cudaMemcpyHostToDevice,
@@ -922,10 +948,109 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     job.d_inner = (int2 *)p.dalloc(inner.size() * sizeof(int2));
     FBS_CUDA(cudaMemcpyAsync(job.d_inner, inner.data(), inner.size() * sizeof(int2), cudaMemcpyHostToDevice,
                              p.stream));
+    job.d_iout = (int *)p.dalloc(std::max<size_t>(1, iout.size()) * sizeof(int));
+    FBS_CUDA(cudaMemcpyAsync(job.d_iout, iout.data(), iout.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             p.stream));
     job.d_grp = (int *)p.dalloc(job.grp.size() * sizeof(int));
     FBS_CUDA(cudaMemcpyAsync(job.d_grp, job.grp.data(), job.grp.size() * sizeof(int),
                              cudaMemcpyHostToDevice, p.stream));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));  // host tables go out of scope
     job.usable = true;
+}
+
+// One contraction from its pair-grouped task list: inner rows are the single
+// bins (bispectrum) or the distinct inner pairs (trispectrum).
+static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
+    job.built = true;
+    std::vector<int2> inner;
+    std::vector<int> row_of;  // (a, b) -> inner row, a*nbins+b
+    if (!quads) {
+        for (int b = 0; b < p.nbins; ++b) inner.push_back(make_int2(b, -1));
+    } else {
+        row_of.assign((size_t)p.nbins * p.nbins, -1);
+        for (int e = 0; e < t.nitems; ++e) row_of[(size_t)t.ia[e] * p.nbins + t.ib[e]] = 0;
+        for (int a = 0; a < p.nbins; ++a)
+            for (int b = 0; b < p.nbins; ++b)
+                if (row_of[(size_t)a * p.nbins + b] >= 0) {
+                    row_of[(size_t)a * p.nbins + b] = (int)inner.size();
+                    inner.push_back(make_int2(a, b));
+                }
+    }
+    if ((int)inner.size() > kMaxInner) return;
+    std::vector<TcPair> hp(t.npairs);
+    for (int i = 0; i < t.npairs; ++i) {
+        TcPair q{};
+        q.b = t.pb[i];
+        q.c = t.pc[i];
+        q.first = t.pstart[i];
+        int prev = -1;
+        for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e) {
+            int n = quads ? row_of[(size_t)t.ia[e] * p.nbins + t.ib[e]] : t.ia[e];
+            if (n <= prev) throw Failure{FBS_ERR_ARG, "tensor-core task list not sorted by inner row"};
+            prev = n;
+            q.mask[n >> 5] |= 1u << (n & 31);
+        }
+        hp[i] = q;
+    }
+    finish_job(p, job, hp, inner, t.iout);
+}
+
+// The triplets and quadruplets of a trispectrum plan as one contraction over
+// the same shell fields: outer rows are the union of the triplets' pairs
+// (b, c) and the quadruplets' pairs (c, d); inner rows are the triplets'
+// single bins a followed by the quadruplets' inner pairs (a, b).  Output
+// column of a triplet: its index; of a quadruplet: ntrip + its index.
+static void build_fused_job(Plan &p, TcJob &job) {
+    job.built = true;
+    const TaskList &tt = p.ttask, &qt = p.qtask;
+    const int nb = p.nbins;
+    std::vector<int> bin_row(nb, -1), pair_row((size_t)nb * nb, -1);
+    for (int e = 0; e < tt.nitems; ++e) bin_row[tt.ia[e]] = 0;
+    for (int e = 0; e < qt.nitems; ++e) pair_row[(size_t)qt.ia[e] * nb + qt.ib[e]] = 0;
+    std::vector<int2> inner;
+    for (int b = 0; b < nb; ++b)
+        if (bin_row[b] >= 0) {
+            bin_row[b] = (int)inner.size();
+            inner.push_back(make_int2(b, -1));
+        }
+    for (int a = 0; a < nb; ++a)
+        for (int b = 0; b < nb; ++b)
+            if (pair_row[(size_t)a * nb + b] >= 0) {
+                pair_row[(size_t)a * nb + b] = (int)inner.size();
+                inner.push_back(make_int2(a, b));
+            }
+    if ((int)inner.size() > kMaxInner) return;
+    std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> outer;  // (x, y) -> (inner row, column)
+    for (int i = 0; i < tt.npairs; ++i)
+        for (int e = tt.pstart[i]; e < tt.pstart[i + 1]; ++e)
+            outer[{tt.pb[i], tt.pc[i]}].push_back({bin_row[tt.ia[e]], tt.iout[e]});
+    for (int i = 0; i < qt.npairs; ++i)
+        for (int e = qt.pstart[i]; e < qt.pstart[i + 1]; ++e)
+            outer[{qt.pb[i], qt.pc[i]}].push_back({pair_row[(size_t)qt.ia[e] * nb + qt.ib[e]],
+                                                    tt.nitems + qt.iout[e]});
+    std::vector<TcPair> hp;
+    std::vector<int> iout;
+    hp.reserve(outer.size());
+    iout.reserve((size_t)tt.nitems + qt.nitems);
+    for (auto &kv : outer) {
+        auto &items = kv.second;
+        std::sort(items.begin(), items.end());
+        TcPair q{};
+        q.b = kv.first.first;
+        q.c = kv.first.second;
+        q.first = (int)iout.size();
+        int prev = -1;
+        for (auto &it : items) {
+            if (it.first <= prev) throw Failure{FBS_ERR_ARG, "fused contraction: repeated item"};
+            prev = it.first;
+            q.mask[it.first >> 5] |= 1u << (it.first & 31);
+            iout.push_back(it.second);
+        }
+        hp.push_back(q);
+    }
+    finish_job(p, job, hp, inner, iout);
+    if (job.usable)
+        p.d_fpart = (double *)p.dalloc((size_t)p.part_blocks * (tt.nitems + qt.nitems) * sizeof(double));
 }
 
 // Wide orientation tables: left rows (<= 64), right rows, items ordered by
@@ -1036,6 +1161,77 @@ bool tc_quads_usable(Plan &p) {
     return st.quad.usable;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of one slab of shell fields: x = point (npts valid, contiguous),
+// y = bin (stride slab_stride floats); boxes of 32 points x all bins in the
+// 128-byte swizzle; points past npts read as zero.
+static CUtensorMap field_tensor_map(const float *islab, long long npts, long long slab_stride, int nbins) {
+    auto enc = tensor_map_encoder();
+    if (!enc) throw Failure{FBS_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
+    if ((reinterpret_cast<uintptr_t>(islab) & 15) || ((slab_stride * 4) & 15) || nbins < 1 || nbins > 256 ||
+        npts < 1 || npts >= (1LL << 31))
+        throw Failure{FBS_ERR_ARG, "shell-field slab does not meet the TMA layout rules"};
+    CUtensorMap m;
+    cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)nbins};
+    cuuint64_t strides[1] = {(cuuint64_t)slab_stride * 4};
+    cuuint32_t box[2] = {32u, (cuuint32_t)nbins};
+    cuuint32_t es[2] = {1u, 1u};
+    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(islab), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Failure{FBS_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+    return m;
+}
+
+static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, long long slab_stride,
+                       double *part, int nitems_total, int kclass) {
+    TcState &st = tc_state(p);
+    const int ngrp = (int)job.grp.size() - 1;
+    int sms = 0, dev = 0;
+    FBS_CUDA(cudaGetDevice(&dev));
+    FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int G = std::max(1, sms / ngrp);
+    if (G > p.part_blocks) G = p.part_blocks;
+    // pipeline depths: 3 A stages when tensor memory allows, 4 field stages
+    // when shared memory allows
+    const int acc_cols_max = (((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32;
+    const int nst = acc_cols_max + 3 * kAStageCols <= 512 ? 3 : 2;
+    const int nstg = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 4) <= 220 * 1024 ? 4 : 2;
+    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, nstg);
+    const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins);
+    KTimer tm(p, kclass);
+    dim3 grid(G, ngrp);
+    const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
+#define FBS_TC_LAUNCH(A, S)                                                                           \
+    if (nst == A && nstg == S) {                                                                      \
+        FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S>,                                       \
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));          \
+        contract_tc_kernel<A, S><<<grid, kTcThreads, sm, p.stream>>>(                                \
+            fmap, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner, job.d_pairs, \
+            job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, 16, st.d_err);                 \
+    }
+    FBS_TC_LAUNCH(2, 2)
+    FBS_TC_LAUNCH(2, 4)
+    FBS_TC_LAUNCH(3, 2)
+    FBS_TC_LAUNCH(3, 4)
+#undef FBS_TC_LAUNCH
+    FBS_CUDA(cudaGetLastError());
+}
+
 void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads) {
     const TaskList &t = quads ? p.qtask : p.ttask;
     if (t.nitems == 0) return;
@@ -1045,25 +1241,21 @@ void launch_contract_tc(Plan &p, const float *islab, long long npts, long long s
     if (!job.built) build_job(p, t, quads, job);
     if (!job.usable)
         throw Failure{FBS_ERR_ARG, "tensor-core contraction: more than 256 inner rows or shared memory exceeded"};
-    const int ngrp = (int)job.grp.size() - 1;
-    int sms = 0, dev = 0;
-    FBS_CUDA(cudaGetDevice(&dev));
-    FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int G = std::max(1, sms / ngrp);
-    if (G > p.part_blocks) G = p.part_blocks;
-    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles);
-    KTimer tm(p, quads ? KC_QUAD_TC : KC_CONTRACT_TC);
-    FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid(G, ngrp);
-    const int acc_cols_max = (((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32;
-    const int nst = 2;  // measured faster than 3 stages
-    (void)acc_cols_max;
-    contract_tc_kernel<<<grid, kTcThreads, sm, p.stream>>>(
-        islab, slab_stride, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner,
-        job.d_pairs, job.npairs,
-        job.d_grp, quads ? p.d_qout : p.d_tout, t.nitems, quads ? p.d_qpart : p.d_tpart,
-        p.precision == FBS_PREC_BF16 ? 0 : 1, 16, nst, st.d_err);
-    FBS_CUDA(cudaGetLastError());
+    launch_job(p, job, islab, npts, slab_stride, quads ? p.d_qpart : p.d_tpart, t.nitems,
+               quads ? KC_QUAD_TC : KC_CONTRACT_TC);
+}
+
+bool tc_fused_usable(Plan &p) {
+    if (p.tc_wide || p.ttask.nitems == 0 || p.qtask.nitems == 0) return false;
+    TcState &st = tc_state(p);
+    if (!st.fused.built) build_fused_job(p, st.fused);
+    return st.fused.usable;
+}
+
+void launch_contract_tc_fused(Plan &p, const float *islab, long long npts, long long slab_stride) {
+    TcState &st = tc_state(p);
+    launch_job(p, st.fused, islab, npts, slab_stride, p.d_fpart, p.ttask.nitems + p.qtask.nitems,
+               KC_QUAD_TC);
 }
 
 void free_tc_state(Plan &p) {

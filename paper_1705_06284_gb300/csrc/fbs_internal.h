@@ -105,6 +105,9 @@ void launch_contract_fp32(Plan &p, const float *islab, long long npts, long long
                           bool quads);
 void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads);
 bool tc_quads_usable(Plan &p);
+// Triplets and quadruplets of a trispectrum plan in one tensor-core pass.
+bool tc_fused_usable(Plan &p);
+void launch_contract_tc_fused(Plan &p, const float *islab, long long npts, long long slab_stride);
 void launch_reduce_and_normalise(Plan &p, bool quads);
 void zero_partials(Plan &p, bool quads);
 std::vector<int> item_groups(const TaskList &t, int cap);
@@ -167,6 +170,8 @@ struct Plan {
     int part_blocks = 0;          // number of FP64 partial rows
     double *d_tpart = nullptr;    // [part_blocks][ntrip]
     double *d_qpart = nullptr;    // [part_blocks][nquad]
+    double *d_fpart = nullptr;    // [part_blocks][ntrip + nquad] of the fused tensor-core pass
+    bool fused_active = false;    // this evaluation uses the fused pass
     double *d_sumsq = nullptr;    // [nbins]
     double *d_sumsq_part = nullptr;  // [nbins][N][z-stage row groups]
     double *d_tnum = nullptr;     // [ntrip]

@@ -564,6 +564,8 @@ static void run_field(Plan &p, const float *field, bool quads) {
                                  p.stream));
         d_in = p.d_field;
     }
+    const bool tc = p.precision != FBS_PREC_FP32;
+    p.fused_active = quads && tc && tc_fused_usable(p);
     zero_partials(p, quads);
     if (p.precision != FBS_PREC_FP32 && tc_error_flag(p))
         FBS_CUDA(cudaMemsetAsync(tc_error_flag(p), 0, sizeof(int), p.stream));
@@ -578,7 +580,10 @@ static void run_field(Plan &p, const float *field, bool quads) {
         launch_inverse_yz_slab(p, x0, nx, p.d_I);
         const long long npts = (long long)nx * plane;
         const long long stride = (long long)p.slab * plane;
-        const bool tc = p.precision != FBS_PREC_FP32;
+        if (p.fused_active) {
+            launch_contract_tc_fused(p, p.d_I, npts, stride);
+            continue;
+        }
         if (tc)
             launch_contract_tc(p, p.d_I, npts, stride, false);
         else
