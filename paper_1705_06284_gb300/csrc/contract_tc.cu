@@ -1218,17 +1218,20 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
 #define FBS_TC_LAUNCH(A, S)                                                                           \
     if (nst == A && nstg == S) {                                                                      \
+        launched = true;                                                                              \
         FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S>,                                       \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));          \
         contract_tc_kernel<A, S><<<grid, kTcThreads, sm, p.stream>>>(                                \
             fmap, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner, job.d_pairs, \
             job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, 16, st.d_err);                 \
     }
+    bool launched = false;
     FBS_TC_LAUNCH(2, 2)
     FBS_TC_LAUNCH(2, 4)
     FBS_TC_LAUNCH(3, 2)
     FBS_TC_LAUNCH(3, 4)
 #undef FBS_TC_LAUNCH
+    if (!launched) throw Failure{FBS_ERR_STATE, "tensor-core contraction: no kernel for this pipeline shape"};
     FBS_CUDA(cudaGetLastError());
 }
 
