@@ -516,6 +516,17 @@ def _closed_triplets_oracle(N, thr):
     return len(oracle.closed_triplets(N, L_BOX, edges(N, len(thr) - 1)))
 
 
+# DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture of the current kernel) per algorithmic byte of the launch
+# (every bin's shell-field value of the slab read once); scaled to the bench's
+# launch by its points.  Source: the profile summary named beside the value.
+NCU_TRAFFIC_RATIO = {
+    "contract_quad_tc": ((540.102144e6 + 3.027712e6) / (16 * 8388608 * 4.0),
+                         "ncu: fused triplet+quadruplet pass, 256^3, 16 log bins, 8.39M points "
+                         "(profiles/contract_tc_fused_quadratic256_T16log.md), scaled by points"),
+}
+
+
 def roofline(top, planB, planT, N, pk, pk_src, clocks):
     """Algorithmic work of the dominant kernel class per launch / its mean
     launch duration (CUDA events around each launch on the plan's stream)."""
@@ -542,16 +553,23 @@ def roofline(top, planB, planT, N, pk, pk_src, clocks):
                     "frac": ach / peak, "traffic": None,
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (derived)" % sm_mhz})
     elif cls in ("contract_tc", "contract_quad_tc"):
+        # per point: 2 flops (multiply-add) per item, 1 multiply per distinct
+        # outer pair and per distinct inner pair; the trispectrum plan's pass
+        # ("contract_quad_tc") also contracts the plan's triplets
+        tpairs = {(int(a[1]), int(a[2])) for a in plan.triplets}
         if cls == "contract_tc":
-            npairs = len({(int(a[1]), int(a[2])) for a in plan.triplets})
-            flops = (2 * plan.ntrip + npairs) * pts_per_launch
+            flops = (2 * plan.ntrip + len(tpairs)) * pts_per_launch
         else:
-            npairs = len({(int(q[2]), int(q[3])) for q in plan.quads})
+            qpairs = {(int(q[2]), int(q[3])) for q in plan.quads}
             ninner = len({(int(q[0]), int(q[1])) for q in plan.quads})
-            flops = (2 * plan.nquad + npairs + ninner) * pts_per_launch
+            flops = (2 * (plan.nquad + plan.ntrip) + len(qpairs | tpairs) + ninner) * pts_per_launch
         ach = flops / (per_launch_ms * 1e-3) / 1e12
+        ratio = NCU_TRAFFIC_RATIO.get(cls)
+        # the TMA ring reads every bin's row of the slab
+        traffic = ratio[0] * 4.0 * plan.nbins * pts_per_launch if ratio else None
         out.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
-                    "frac": ach / bf16, "traffic": None,
+                    "frac": ach / bf16, "traffic": traffic,
+                    "traffic_source": ratio[1] if ratio else None,
                     "peak_source": "bf16_tflops_sustained (%s)" % pk_src})
     else:
         # FFT stages: algorithmic bytes per launch (shell fields written, inputs read)
@@ -563,13 +581,9 @@ def roofline(top, planB, planT, N, pk, pk_src, clocks):
 
 
 def plan_slab_points(plan, N):
-    # the library balances slabs: ceil(N / nslabs) planes each
-    per_plane = plan.nbins * N * N * 4
-    budget = int(os.environ.get("FBS_SLAB_MB", "8192")) << 20
-    slab = max(1, min(N, budget // max(1, per_plane)))
-    nsl = -(-N // slab)
-    slab = -(-N // nsl)
-    return slab * N * N
+    """Points of the evaluation grid in one (full) slab of the plan."""
+    M = plan.eval_grid
+    return plan.slab_planes * M * M
 
 
 def fft_bytes(cls, plan, N, pts):

@@ -200,6 +200,12 @@ int fbs_plan_quad_counts_exact(const fbs_plan *plan);
 /* Side M of the grid the plan evaluates shell fields and products on. */
 int fbs_plan_eval_grid(const fbs_plan *plan);
 
+/* Planes of the evaluation grid per slab (the shell fields of one slab are
+ * resident at a time; slabs are balanced, the last may be shorter) and the
+ * number of slabs per evaluation; <0 on error. */
+int fbs_plan_slab_planes(const fbs_plan *plan);
+int fbs_plan_num_slabs(const fbs_plan *plan);
+
 /* Device bytes owned by the plan. */
 int64_t fbs_plan_device_bytes(const fbs_plan *plan);
 

@@ -78,6 +78,8 @@ _SIGS = [
     ("fbs_plan_count_margin", ctypes.c_double, [_vp]),
     ("fbs_plan_quad_counts_exact", ctypes.c_int, [_vp]),
     ("fbs_plan_eval_grid", ctypes.c_int, [_vp]),
+    ("fbs_plan_slab_planes", ctypes.c_int, [_vp]),
+    ("fbs_plan_num_slabs", ctypes.c_int, [_vp]),
     ("fbs_triple_sums_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                                 _vp, ctypes.c_int, _vp, _vp]),
     ("fbs_last_error", ctypes.c_char_p, []),
@@ -192,6 +194,8 @@ class Plan:
         self.count_margin = float(Lb.fbs_plan_count_margin(_vp(self._h)))
         self.quad_counts_exact = bool(Lb.fbs_plan_quad_counts_exact(_vp(self._h)) == 1)
         self.eval_grid = int(Lb.fbs_plan_eval_grid(_vp(self._h)))
+        self.slab_planes = int(Lb.fbs_plan_slab_planes(_vp(self._h)))
+        self.num_slabs = int(Lb.fbs_plan_num_slabs(_vp(self._h)))
 
     # -- lifetime
     def close(self):

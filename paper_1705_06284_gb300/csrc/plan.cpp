@@ -859,6 +859,10 @@ double fbs_plan_count_margin(const fbs_plan *plan) { return plan ? plan->count_m
 
 int fbs_plan_eval_grid(const fbs_plan *plan) { return plan ? plan->M : FBS_ERR_ARG; }
 
+int fbs_plan_slab_planes(const fbs_plan *plan) { return plan ? plan->slab : FBS_ERR_ARG; }
+
+int fbs_plan_num_slabs(const fbs_plan *plan) { return plan ? plan->nslabs : FBS_ERR_ARG; }
+
 int fbs_plan_quad_counts_exact(const fbs_plan *plan) {
     if (!plan) return FBS_ERR_ARG;
     return plan->quad_counts_exact ? 1 : 0;
