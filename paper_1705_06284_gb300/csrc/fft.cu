@@ -257,13 +257,10 @@ __global__ void __launch_bounds__(kThreads) inv_z_kernel(const typename V2<T>::t
     if (y0 >= nrows) return;
     T *ob = out + (long long)bl * out_bin_stride;
     if (g.empty) {
-        if (!OCT) {
-            for (int i = threadIdx.x; i < nl * 2 * N; i += blockDim.x) {
-                int r = i / N, z = i - r * N;
-                int y = y0 + r;
-                if (y < nrows) ob[((long long)xl * N + y) * N + z] = T(0);
-            }
-        } else {
+        // shell fields: an empty bin's rows are never read by any item (its
+        // sum-of-squares partials stay at their zeroed value); count fields
+        // of the octant are zero-filled
+        if (OCT) {
             const int H = N / 2 + 1;
             for (int i = threadIdx.x; i < nl * 2 * H; i += blockDim.x) {
                 int r = i / H, z = i - r * H;
@@ -392,11 +389,13 @@ __global__ void __launch_bounds__(T *LP) inv_z_fast_kernel(const float2 *__restr
                                                            double *__restrict__ sumsq_part,
                                                            const float2 *__restrict__ tw) {
     static_assert(R0 * R1 * R2 * R3 == N, "radices must multiply to N");
-    constexpr int NP = zpad(N - 1) + 1;
+    // line stride: padded line, rounded to 8 mod 16 slots so that the two
+    // lines a warp spans (T = 16) sit on opposite halves of the banks
+    constexpr int NP = ((zpad(N - 1) + 1 + 7) / 16) * 16 + 8;
     constexpr int NB0 = N / R0, PER0 = NB0 / T;
     static_assert(PER0 * T == NB0, "threads must divide the first stage");
     __shared__ float2 buf[LP * NP];
-    __shared__ double red[(T * LP + 31) / 32];
+    __shared__ float red[(T * LP + 31) / 32];
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const int bl = blockIdx.z;
     const BinGeom g = geom[bl];
@@ -406,13 +405,9 @@ __global__ void __launch_bounds__(T *LP) inv_z_fast_kernel(const float2 *__restr
     const bool w0 = y < N, w1 = y + 1 < N;
     float *o0 = ob + ((long long)xl * N + (w0 ? y : 0)) * N;
     float *o1 = o0 + N;
-    float acc = 0.f;  // a few squares per thread; FP64 from the warp sums on
-    if (g.empty) {
-        for (int z = t; z < N; z += T) {
-            if (w0) o0[z] = 0.f;
-            if (w1) o1[z] = 0.f;
-        }
-    } else {
+    float acc = 0.f;  // a few squares per thread; FP64 per CTA
+    // an empty bin's rows are never read by any item: nothing to write
+    if (!g.empty) {
         const float2 *in0 = G + g.G_off + ((long long)xl * N + (w0 ? y : 0)) * g.Dzb;
         const float2 *in1 = in0 + g.Dzb;
         const int R = g.Dzb - 1;  // highest mz held (<= N/2)
@@ -455,12 +450,12 @@ __global__ void __launch_bounds__(T *LP) inv_z_fast_kernel(const float2 *__restr
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);  // <= 512 squares
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)acc;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0.0;
+        float s = 0.f;  // at most 16 rows of N squares per CTA
         for (int w = 0; w < (T * LP + 31) / 32; ++w) s += red[w];
-        sumsq_part[((long long)bl * N + x0 + xl) * gridDim.x + blockIdx.x] = s;
+        sumsq_part[((long long)bl * N + x0 + xl) * gridDim.x + blockIdx.x] = (double)s;
     }
 }
 
