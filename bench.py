@@ -301,13 +301,8 @@ def main():
         if not np.allclose(outs_host[0], B.cpu().numpy(), rtol=0, atol=0):
             e2e["mismatch"] = True
 
-    ms_max = ms
-    e2e_max = e2e["_s"] if e2e else None
-    if dist:
-        t = torch.tensor([ms, e2e_max or 0.0], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max, e2e_max = float(t[0]), float(t[1])
-    value = world * planB.ntrip / (ms_max / 1e3)
+    ms_max, e2e_max = max_over_ranks(dist, [ms, e2e["_s"] if e2e else 0.0], device=dev)
+    value = whole_job_rate(world, planB.ntrip, ms_max / 1e3)
 
     # roofline of the dominant kernel class (largest share of the timed region)
     pk, pk_src = peaks()
@@ -328,7 +323,7 @@ def main():
             "quad_counts_exact": planT.quad_counts_exact,
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in allk.items() if v[1]}}
     if e2e:
-        e2e["value"] = world * planB.ntrip / e2e_max
+        e2e["value"] = whole_job_rate(world, planB.ntrip, e2e_max)
         e2e.pop("_s", None)
         line["e2e"] = e2e
     if rank == 0 and not args.no_plain and world == 1:
@@ -528,6 +523,24 @@ NCU_TRAFFIC_RATIO = {
                          "ncu: fused triplet+quadruplet pass, 256^3, 16 log bins, 8.39M points "
                          "(profiles/contract_tc_fused_quadratic256_T16log.md), scaled by points"),
 }
+
+
+def max_over_ranks(dist, values, device=None):
+    """Each value's maximum over the ranks (the slowest replica's time); the
+    values unchanged without a process group.  NCCL groups need a CUDA
+    device, gloo groups a CPU tensor (device=None)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(world, units_per_rank, seconds_max):
+    """Units all replicas processed (each rank the same workload on its own
+    field) over the slowest rank's time: weak scaling."""
+    return world * units_per_rank / seconds_max
 
 
 def roofline(top, planB, planT, N, pk, pk_src, clocks):
