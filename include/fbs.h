@@ -131,11 +131,17 @@ fbs_status fbs_plan_set_precision(fbs_plan *plan, int precision);
 
 /* Plan options (fbs_plan_set_option). */
 enum {
-    FBS_OPT_TC_WIDE = 1 /* 0: tensor-core contraction with the pair products as
+    FBS_OPT_TC_WIDE = 1, /* 0: tensor-core contraction with the pair products as
                            operand A (M = 128 outer pairs, N = bins; default);
                            1: "wide" orientation with the <= 64 left rows stacked
                            [hi; lo] as operand A and up to 256 right pair
                            products as operand B (BF16x4).  Ignored for FP32. */
+    FBS_OPT_TC_ROLES = 2 /* warp roles of the default tensor-core contraction:
+                            0 (default) or 1: 16 warps form the pair products
+                            and build operand B in turn; 2: 8 warps form the
+                            pair products while 8 others build operand B.  The
+                            results are identical; only the speed differs
+                            (2 measured about 4% slower at 512^3). */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */

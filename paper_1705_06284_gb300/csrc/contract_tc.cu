@@ -191,8 +191,7 @@ __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
 // every MMA; one thread of warp 17 streams the shell fields of each chunk
 // into a ring of shared-memory stages with TMA.  Every hand-off is an
 // mbarrier; no role waits on a CTA-wide barrier inside the main loop.
-constexpr int kProdWarps = 16;            // 4 per TMEM lane quarter, 16 of the 64 points of a row each
-constexpr int kPPT = 4 * KC / kProdWarps;  // points of a row per producer thread per tile
+constexpr int kProdWarps = 16;            // A-operand warps (AW) + operand-B warps (16 - AW)
 constexpr int kMmaWarp = kProdWarps;
 constexpr int kLoadWarp = kProdWarps + 1;
 constexpr int kTcThreads = (kProdWarps + 2) * 32;
@@ -310,9 +309,35 @@ __device__ __forceinline__ const float4 *stage_at(const unsigned char *st, int h
                                             (((j & 7) ^ (b & 7)) << 4));
 }
 
+// One operand-B unit u = (inner row, 8-point group): the row's values (a
+// single bin, or the product of two bins) split into BF16 hi/lo, stored in
+// the 128-byte-swizzled K-major tiles.
+__device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_bytes, const int2 *s_inner,
+                                             int ninner, int u, unsigned char *bh, unsigned char *bl) {
+    const int row = u % ninner, j = u / ninner;
+    const int2 in = s_inner[row];
+    float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
+    float4 v1 = *stage_at(st, half_bytes, in.x, 2 * j + 1);
+    if (in.y >= 0) {
+        const float4 w0 = *stage_at(st, half_bytes, in.y, 2 * j);
+        const float4 w1 = *stage_at(st, half_bytes, in.y, 2 * j + 1);
+        v0 = make_float4(v0.x * w0.x, v0.y * w0.y, v0.z * w0.z, v0.w * w0.w);
+        v1 = make_float4(v1.x * w1.x, v1.y * w1.y, v1.z * w1.z, v1.w * w1.w);
+    }
+    float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+    uint4 h, l;
+    split8(v, h, l);
+    const uint32_t off = sw128_off(row, j);
+    *reinterpret_cast<uint4 *>(bh + off) = h;
+    *reinterpret_cast<uint4 *>(bl + off) = l;
+}
+
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
 // NST: A stages in tensor memory; NSTG: field stages in shared memory.
-template <int NST, int NSTG>
+// AW: warps forming the pair products of operand A (4 per TMEM lane quarter
+// x 16 points, or 2 x 32 points); with AW = 16 they also build operand B,
+// with AW = 8 the other 8 producer warps build operand B concurrently.
+template <int NST, int NSTG, int AW>
 __global__ void __launch_bounds__(kTcThreads, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap fmap, long long npts, int nbins, int Npad,
                        int tstride, int ninner, const int2 *__restrict__ inner,
@@ -320,6 +345,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
                        int *__restrict__ err) {
+    static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
+    constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
+    constexpr int PPT = 4 * KC / AW;      // points of a row per A thread per tile
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ TcBars bars;
     __shared__ int2 s_inner[kMaxInner];
@@ -361,15 +389,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&bars.sempty[i], kProdWarps);
         }
         for (int i = 0; i < NST; ++i) {
-            mbar_init(&bars.full[i], kProdWarps);
+            mbar_init(&bars.full[i], AW);
             mbar_init(&bars.empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&bars.bfull[i], kProdWarps);
+            mbar_init(&bars.bfull[i], BW > 0 ? BW : AW);
             mbar_init(&bars.bempty[i], 1);
         }
         mbar_init(&bars.accr, 1);
-        mbar_init(&bars.accf, kProdWarps);
+        mbar_init(&bars.accf, AW);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
@@ -483,11 +511,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // drain: every MMA complete before tensor memory is released (own limit)
             if (last_slot >= 0 && !mbar_wait(&bars.empty[last_slot], last_phase)) atomicExch(err, 14);
         }
+    } else if (BW > 0 && warp >= AW) {
+        // ================= operand-B warps (AW .. 15) =================
+        const int btid = tid - AW * 32;  // 0 .. 32*BW-1
+        Ring<NSTG> rs;
+        Ring<2> rb;
+        for (long long ci = c0; ci < c1; ++ci) {
+            role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 24);
+            const unsigned char *st = stg + rs.slot * 2 * half_bytes;
+            const int sb = rb.slot;
+            if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 25);
+            for (int u = btid; u < ninner * 8; u += BW * 32)
+                build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_tile, Bl0 + sb * b_tile);
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.bfull[sb]);
+            rb.next();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.sempty[rs.slot]);
+            rs.next();
+        }
     } else {
-        // ================= producers (warps 0..15) =================
-        const int q = warp & 3, kq = warp >> 2;  // lane quarter, kPPT-point slice of the chunk
+        // ================= operand-A warps (0 .. AW-1) =================
+        const int q = warp & 3, kq = warp >> 2;  // lane quarter, PPT-point slice of the chunk
         const int r = 32 * q + lane;             // operand-A row (TMEM lane) of this thread
-        const int ptid = tid;                    // 0 .. 32*kProdWarps-1
+        const int ptid = tid;                    // 0 .. 32*AW-1
         Ring<NSTG> rs;
         Ring<NST> ra;
         Ring<2> rb;
@@ -496,61 +544,51 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (long long ci = c0; ci < c1; ++ci) {
             role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 20);
             const unsigned char *st = stg + rs.slot * 2 * half_bytes;
-            // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
-            const int sb = rb.slot;
-            if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21);
-            for (int u = ptid; u < ninner * 8; u += kProdWarps * 32) {
-                const int row = u % ninner, j = u / ninner;
-                const int2 in = s_inner[row];
-                float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
-                float4 v1 = *stage_at(st, half_bytes, in.x, 2 * j + 1);
-                if (in.y >= 0) {
-                    const float4 w0 = *stage_at(st, half_bytes, in.y, 2 * j);
-                    const float4 w1 = *stage_at(st, half_bytes, in.y, 2 * j + 1);
-                    v0 = make_float4(v0.x * w0.x, v0.y * w0.y, v0.z * w0.z, v0.w * w0.w);
-                    v1 = make_float4(v1.x * w1.x, v1.y * w1.y, v1.z * w1.z, v1.w * w1.w);
-                }
-                float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-                uint4 h, l;
-                split8(v, h, l);
-                const uint32_t off = sw128_off(row, j);
-                *reinterpret_cast<uint4 *>(Bh0 + sb * b_tile + off) = h;
-                *reinterpret_cast<uint4 *>(Bl0 + sb * b_tile + off) = l;
+            if constexpr (BW == 0) {
+                // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
+                const int sb = rb.slot;
+                if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21);
+                for (int u = ptid; u < ninner * 8; u += AW * 32)
+                    build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_tile, Bl0 + sb * b_tile);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars.bfull[sb]);
+                rb.next();
             }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bars.bfull[sb]);
-            rb.next();
-            // ---- operand A: pair products of this thread's row, kPPT points, into TMEM
+            // ---- operand A: pair products of this thread's row, PPT points, into TMEM
             for (int lt = 0; lt < ntl; ++lt) {
                 const int as = ra.slot;
                 if (ra.warm) role_wait(&bars.empty[as], ra.phase ^ 1u, abortp, err, 22);
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
-                uint32_t hw[kPPT / 2], lw[kPPT / 2];
-                if (bc.x >= 0) {
-#pragma unroll
-                    for (int j = 0; j < kPPT / 8; ++j) {
-                        const int jj = (kPPT / 4) * kq + 2 * j;
-                        const float4 b0 = *stage_at(st, half_bytes, bc.x, jj);
-                        const float4 b1 = *stage_at(st, half_bytes, bc.x, jj + 1);
-                        const float4 e0 = *stage_at(st, half_bytes, bc.y, jj);
-                        const float4 e1 = *stage_at(st, half_bytes, bc.y, jj + 1);
-                        float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
-                                      b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
-                        uint4 h, l;
-                        split8(v, h, l);
-                        hw[4 * j + 0] = h.x; hw[4 * j + 1] = h.y; hw[4 * j + 2] = h.z; hw[4 * j + 3] = h.w;
-                        lw[4 * j + 0] = l.x; lw[4 * j + 1] = l.y; lw[4 * j + 2] = l.z; lw[4 * j + 3] = l.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < kPPT / 2; ++j) hw[j] = lw[j] = 0u;
-                }
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
-                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + (kPPT / 2) * kq);
-                tmem_st8a(lanebase + col, hw);
-                tmem_st8a(lanebase + col + 32u, lw);
+                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + (PPT / 2) * kq);
+                // 16 points (8 columns of hi, 8 of lo) at a time
+#pragma unroll
+                for (int c = 0; c < PPT / 16; ++c) {
+                    uint32_t hw[8], lw[8];
+                    if (bc.x >= 0) {
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int jj = (PPT / 4) * kq + 4 * c + 2 * j;
+                            const float4 b0 = *stage_at(st, half_bytes, bc.x, jj);
+                            const float4 b1 = *stage_at(st, half_bytes, bc.x, jj + 1);
+                            const float4 e0 = *stage_at(st, half_bytes, bc.y, jj);
+                            const float4 e1 = *stage_at(st, half_bytes, bc.y, jj + 1);
+                            float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
+                                          b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
+                            uint4 h, l;
+                            split8(v, h, l);
+                            hw[4 * j + 0] = h.x; hw[4 * j + 1] = h.y; hw[4 * j + 2] = h.z; hw[4 * j + 3] = h.w;
+                            lw[4 * j + 0] = l.x; lw[4 * j + 1] = l.y; lw[4 * j + 2] = l.z; lw[4 * j + 3] = l.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) hw[j] = lw[j] = 0u;
+                    }
+                    tmem_st8a(lanebase + col + 8u * c, hw);
+                    tmem_st8a(lanebase + col + 32u + 8u * c, lw);
+                }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 __syncwarp();
@@ -570,7 +608,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const int p = (t0 + lt) * 128 + r;
                         const bool valid = p < npairs;
                         const TcPair *pp = pairs + (valid ? p : 0);
-                        for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (kProdWarps / 4)) {
+                        for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (AW / 4)) {
                             float v[8];
                             tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
                             if (!valid) continue;
@@ -1216,20 +1254,27 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     KTimer tm(p, kclass);
     dim3 grid(G, ngrp);
     const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
-#define FBS_TC_LAUNCH(A, S)                                                                           \
-    if (nst == A && nstg == S) {                                                                      \
+#define FBS_TC_LAUNCH(A, S, W)                                                                        \
+    if (nst == A && nstg == S && aw == W) {                                                           \
         launched = true;                                                                              \
-        FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S>,                                       \
+        FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S, W>,                                    \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));          \
-        contract_tc_kernel<A, S><<<grid, kTcThreads, sm, p.stream>>>(                                \
+        contract_tc_kernel<A, S, W><<<grid, kTcThreads, sm, p.stream>>>(                             \
             fmap, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner, job.d_pairs, \
             job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, 16, st.d_err);                 \
     }
+    // 16 warps form the pair products and build operand B in turn (measured
+    // faster at both headline passes); 8 + 8 concurrent roles on request
+    const int aw = p.tc_roles == 2 ? 8 : 16;
     bool launched = false;
-    FBS_TC_LAUNCH(2, 2)
-    FBS_TC_LAUNCH(2, 4)
-    FBS_TC_LAUNCH(3, 2)
-    FBS_TC_LAUNCH(3, 4)
+    FBS_TC_LAUNCH(2, 2, 16)
+    FBS_TC_LAUNCH(2, 4, 16)
+    FBS_TC_LAUNCH(3, 2, 16)
+    FBS_TC_LAUNCH(3, 4, 16)
+    FBS_TC_LAUNCH(2, 2, 8)
+    FBS_TC_LAUNCH(2, 4, 8)
+    FBS_TC_LAUNCH(3, 2, 8)
+    FBS_TC_LAUNCH(3, 4, 8)
 #undef FBS_TC_LAUNCH
     if (!launched) throw Failure{FBS_ERR_STATE, "tensor-core contraction: no kernel for this pipeline shape"};
     FBS_CUDA(cudaGetLastError());

@@ -764,6 +764,10 @@ fbs_status fbs_plan_set_option(fbs_plan *plan, int option, int value) {
         plan->tc_wide = value;
         return FBS_OK;
     }
+    if (option == FBS_OPT_TC_ROLES && value >= 0 && value <= 2) {
+        plan->tc_roles = value;
+        return FBS_OK;
+    }
     set_error("unknown option or value");
     return FBS_ERR_ARG;
 }

@@ -120,3 +120,32 @@ def test_wide_orientation_matches(monkeypatch, N, nb, quads):
         else:
             B, P = run(plan, f32)
         check_bispectrum(plan, B, P, f32, L, edges, "bf16x3")
+
+
+@pytest.mark.parametrize("quads", [False, True])
+def test_warp_roles_give_identical_results(quads):
+    """FBS_OPT_TC_ROLES 1 (16 warps form the pair products and build operand B
+    in turn) and 2 (8 + 8 warps concurrently) issue the same MMAs in the same
+    order: bit-identical sums, and both match the oracle."""
+    import torch
+    N, L, nb = 48, 60.0, 10
+    edges = fields.linear_edges(N, L, nb)
+    f32 = _field("quadratic", N, 31).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    out = {}
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        for roles in (1, 2):
+            plan.set_option(fbs.FBS_OPT_TC_ROLES, roles)
+            if quads:
+                T, B, P = plan.trispectrum(f)
+            else:
+                B, P = plan.bispectrum(f)
+                T = None
+            torch.cuda.synchronize()
+            out[roles] = (B.cpu().numpy(), P.cpu().numpy(), None if T is None else T.cpu().numpy())
+        assert np.array_equal(out[1][0], out[2][0])
+        assert np.array_equal(out[1][1], out[2][1])
+        if quads:
+            assert np.array_equal(out[1][2], out[2][2])
+            check_trispectrum(plan, out[2][2], f32, L, edges, 2e-4)
+        check_bispectrum(plan, out[2][0], out[2][1], f32, L, edges, "bf16x3")
