@@ -90,7 +90,8 @@ enum {
  * M^3 grid with M > pR (p = 3, or 4 with FBS_FLAG_TRISPECTRUM).  Unless
  * FBS_FLAG_FULL_GRID or FBS_FLAG_ALLOW_ALIASED is given, the plan evaluates
  * the shell fields and their products on the smallest even M = 2^a 3^b > pR
- * (M <= N): the same sums up to rounding, with (M/N)^3 of the points.
+ * (M <= N): the same sums up to rounding, with (M/N)^3 of the points.  The
+ * plan-time count sums use the same grid (N_tri = sum_M N_a N_b N_c / M^3).
  * The plan runs the plan-time work on the device before returning: shell
  * tables, the FP64 count fields N_b, exact N_tri (and N_quad) for every
  * candidate bin triple, and the closed-triplet list (lexicographic a<=b<=c

@@ -355,7 +355,7 @@ void launch_reduce_and_normalise(Plan &p, bool quads) {
 void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, const int *d_items,
                               int nitems, int arity, double *d_den) {
     if (nitems == 0) return;
-    const int H = p.N / 2 + 1;
+    const int H = p.M / 2 + 1;  // count fields are on the evaluation grid's octant
     int grp = 4096;
     size_t sm = (size_t)grp * 8 + (size_t)nbins_all * kCntChunk * 8 + kCntChunk * 8;
     while (sm > 200 * 1024 && grp > 256) {

@@ -162,7 +162,7 @@ struct Plan {
     float *d_I = nullptr;        // shell fields (one slab) [bin][plane][y][z]
     BinGeom *d_geom = nullptr;
     float2 *d_tw = nullptr;      // e^{-2 pi i k/N}, k < N (FP32)
-    double2 *d_tw64 = nullptr;   // same in FP64 (count path)
+    double2 *d_tw64 = nullptr;   // e^{-2 pi i k/M}, k < M, in FP64 (count fields)
     // task lists on device
     int *d_tpb = nullptr, *d_tpc = nullptr, *d_tps = nullptr, *d_tia = nullptr, *d_tout = nullptr;
     int *d_qpb = nullptr, *d_qpc = nullptr, *d_qps = nullptr, *d_qia = nullptr, *d_qib = nullptr,

@@ -489,37 +489,36 @@ int zstage_row_groups(int N) {
     return (N + 2 * nl - 1) / (2 * nl);
 }
 
+// e^{-2 pi i k/n}, k < n, in FP64 with the quarter turns exact.
+static std::vector<double2> twiddles64(int n) {
+    std::vector<double2> t(n);
+    for (int k = 0; k < n; ++k) {
+        double ang = -2.0 * M_PI * (double)k / (double)n;
+        double c = cos(ang), s = sin(ang);
+        if (4 * k == n) { c = 0.0; s = -1.0; }
+        if (2 * k == n) { c = -1.0; s = 0.0; }
+        if (4 * k == 3 * n) { c = 0.0; s = 1.0; }
+        t[k] = make_double2(c, s);
+    }
+    return t;
+}
+
+// FP32 twiddles of the input grid (forward transforms) and of the evaluation
+// grid (inverse transforms of the shell fields); FP64 twiddles of the
+// evaluation grid (plan-time count fields).
 void upload_twiddles(Plan &p) {
-    const int N = p.N;
-    std::vector<float2> t32(N);
-    std::vector<double2> t64(N);
-    for (int k = 0; k < N; ++k) {
-        // e^{-2 pi i k/N} from exact octant reduction of k/N in FP64
-        double ang = -2.0 * M_PI * (double)k / (double)N;
-        double c = cos(ang), s = sin(ang);
-        if (4 * k == N) { c = 0.0; s = -1.0; }
-        if (2 * k == N) { c = -1.0; s = 0.0; }
-        if (4 * k == 3 * N) { c = 0.0; s = 1.0; }
-        t64[k] = make_double2(c, s);
-        t32[k] = make_float2((float)c, (float)s);
-    }
+    const int N = p.N, M = p.M;
+    const std::vector<double2> tn = twiddles64(N), tmv = twiddles64(M);
+    std::vector<float2> t32(N), tm32(M);
+    for (int k = 0; k < N; ++k) t32[k] = make_float2((float)tn[k].x, (float)tn[k].y);
+    for (int k = 0; k < M; ++k) tm32[k] = make_float2((float)tmv[k].x, (float)tmv[k].y);
     p.d_tw = (float2 *)p.dalloc(N * sizeof(float2));
-    p.d_tw64 = (double2 *)p.dalloc(N * sizeof(double2));
-    FBS_CUDA(cudaMemcpyAsync(p.d_tw, t32.data(), N * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
-    FBS_CUDA(cudaMemcpyAsync(p.d_tw64, t64.data(), N * sizeof(double2), cudaMemcpyHostToDevice, p.stream));
-    // twiddles of the evaluation grid
-    const int M = p.M;
-    std::vector<float2> tm(M);
-    for (int k = 0; k < M; ++k) {
-        double ang = -2.0 * M_PI * (double)k / (double)M;
-        double c = cos(ang), s = sin(ang);
-        if (4 * k == M) { c = 0.0; s = -1.0; }
-        if (2 * k == M) { c = -1.0; s = 0.0; }
-        if (4 * k == 3 * M) { c = 0.0; s = 1.0; }
-        tm[k] = make_float2((float)c, (float)s);
-    }
     p.d_twM = (float2 *)p.dalloc(M * sizeof(float2));
-    FBS_CUDA(cudaMemcpyAsync(p.d_twM, tm.data(), M * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
+    p.d_tw64 = (double2 *)p.dalloc(M * sizeof(double2));
+    FBS_CUDA(cudaMemcpyAsync(p.d_tw, t32.data(), N * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
+    FBS_CUDA(cudaMemcpyAsync(p.d_twM, tm32.data(), M * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
+    FBS_CUDA(cudaMemcpyAsync(p.d_tw64, tmv.data(), M * sizeof(double2), cudaMemcpyHostToDevice, p.stream));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));  // host tables go out of scope
 }
 
 void launch_forward(Plan &p, const float *d_field) {
@@ -619,7 +618,7 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
 // the group (allocated by the caller through the plan, freed after).
 void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
                                    double2 *G64, const BinGeom *d_geom_grp) {
-    const int N = p.N;
+    const int N = p.M;  // count fields live on the evaluation grid
     const int H = N / 2 + 1;
     const int nl = lines_per_cta<double>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(double2);
@@ -628,7 +627,7 @@ void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, doub
         auto k = inv_x_kernel<double, true>;
         allow_smem(k, sm);
         dim3 grid(max_inv_x_grid(p, bin0, nb, nl), nb);
-        k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.box, d_geom_grp, 0, A64, nl, p.fN, p.d_tw64);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, d_geom_grp, 0, A64, nl, p.fM, p.d_tw64);
         FBS_CUDA(cudaGetLastError());
     }
     {
@@ -636,7 +635,7 @@ void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, doub
         auto k = inv_y_kernel<double>;
         allow_smem(k, sm);
         dim3 grid((max_dzb(p, bin0, nb) + nl - 1) / nl, H, nb);
-        k<<<grid, kThreads, sm, p.stream>>>(A64, d_geom_grp, 0, N, 0, G64, 0, nl, p.fN, p.d_tw64);
+        k<<<grid, kThreads, sm, p.stream>>>(A64, d_geom_grp, 0, N, 0, G64, 0, nl, p.fM, p.d_tw64);
         FBS_CUDA(cudaGetLastError());
     }
     {
@@ -645,7 +644,7 @@ void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, doub
         allow_smem(k, sm);
         dim3 grid((H + 2 * nl - 1) / (2 * nl), H, nb);
         k<<<grid, kThreads, sm, p.stream>>>(G64, d_geom_grp, 0, N, 0, noct, (long long)H * H * H,
-                                            nullptr, nl, p.fN, p.d_tw64);
+                                            nullptr, nl, p.fM, p.d_tw64);
         FBS_CUDA(cudaGetLastError());
     }
 }

@@ -280,7 +280,7 @@ static void candidates(const Plan &p, const std::vector<long long> &mn,
 // FP64 count fields on the octant, then the count sums of all candidates.
 static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<int> &qc,
                          std::vector<double> &tden, std::vector<double> &qden) {
-    const int N = p.N, H = N / 2 + 1;
+    const int N = p.M, H = N / 2 + 1;  // the evaluation grid (exact for these products)
     const long long H3 = (long long)H * H * H;
     const int nb = p.nbins;
     double *noct = nullptr;
@@ -470,7 +470,9 @@ static void create_plan(Plan &p, const double *edges) {
     candidates(p, mn, mx, 3, tc);
     if (p.flags & FBS_FLAG_TRISPECTRUM) candidates(p, mn, mx, 4, qc);
     std::vector<double> tden, qden;
-    const double npix = (double)N * N * N;
+    // the count sums run on the evaluation grid: sum_M N_a N_b N_c / M^3 is
+    // the same integer as sum_N N_a N_b N_c / N^3
+    const double npix = (double)p.M * p.M * p.M;
     exact_counts(p, tc, qc, tden, qden);
     p.trip.clear();
     p.ntri.clear();
