@@ -28,7 +28,11 @@
  *     aborts.  fbs_last_error() gives a message for the calling thread.
  *   - "Device or host" pointers are classified with cudaPointerGetAttributes:
  *     device (and managed) memory is used in place; host memory (pageable or
- *     pinned) is staged through plan-owned device buffers.
+ *     pinned) is staged through plan-owned device buffers.  A host field is
+ *     copied on a plan-owned copy stream that does not wait for work queued
+ *     earlier on the plan's stream (so the copy overlaps it): the host buffer
+ *     must hold the field when the call is made, not only once earlier work
+ *     on the plan's stream (a device-to-host copy into it, say) completes.
  *   - A plan is not thread-safe: calls on one plan must be serialised by the
  *     caller.  Different plans may be used from different threads.
  */
@@ -157,9 +161,12 @@ fbs_status fbs_plan_set_stream(fbs_plan *plan, void *cuda_stream);
  *           Caller-owned; read only.
  *   B     : double[ntrip] (device or host), order of fbs_plan_triplets; may be NULL.
  *   P     : double[nbins] (device or host); may be NULL.
- * With device field and outputs the call only enqueues work on the plan's
- * stream and returns (results are ready when the stream reaches them).  With
- * any host pointer it synchronises the stream before returning.
+ * With device or page-locked (pinned) host outputs the call only enqueues
+ * work on the plan's stream and returns: the results are there once the
+ * stream reaches them (synchronise it before reading pinned outputs).  With
+ * pageable host outputs it synchronises the stream before returning.  A
+ * pinned host field is read asynchronously (on the plan's copy stream):
+ * leave it unchanged until the plan's stream has passed the call.
  */
 fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double *P);
 

@@ -154,6 +154,10 @@ struct Plan {
     std::vector<void *> allocs;
     long long dev_bytes = 0;
     float *d_field = nullptr;    // staging for host fields
+    cudaStream_t copy_stream = nullptr;   // host-field copies (overlap work queued on `stream`)
+    cudaEvent_t ev_field_ready = nullptr; // staged copy landed (the plan's stream waits on it)
+    cudaEvent_t ev_field_free = nullptr;  // the forward transform is done with the staging buffer
+    bool field_free_recorded = false;
     float2 *d_zbuf = nullptr;    // forward scratch [N][N][Dz]
     float2 *d_ybuf = nullptr;    // forward scratch [N][D][Dz]
     float2 *d_box = nullptr;     // spectrum box [D][D][Dz]

@@ -521,6 +521,9 @@ static void create_plan(Plan &p, const double *edges) {
     // per-field buffers
     p.d_geom = upload(p, p.geom);
     p.d_field = (float *)p.dalloc((size_t)N * N * N * sizeof(float));
+    FBS_CUDA(cudaStreamCreateWithFlags(&p.copy_stream, cudaStreamNonBlocking));
+    FBS_CUDA(cudaEventCreateWithFlags(&p.ev_field_ready, cudaEventDisableTiming));
+    FBS_CUDA(cudaEventCreateWithFlags(&p.ev_field_free, cudaEventDisableTiming));
     p.d_zbuf = (float2 *)p.dalloc((size_t)N * N * p.box.Dz * sizeof(float2));
     p.d_ybuf = (float2 *)p.dalloc((size_t)N * p.box.D * p.box.Dz * sizeof(float2));
     p.d_A = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.A_elems) * sizeof(float2));
@@ -561,9 +564,16 @@ static void create_plan(Plan &p, const double *edges) {
 static void run_field(Plan &p, const float *field, bool quads) {
     const int N = p.N;
     const float *d_in = field;
-    if (!is_device_ptr(field)) {
+    const bool staged = !is_device_ptr(field);
+    if (staged) {
+        // Copy on the plan's own copy stream: it need not wait for kernels
+        // already queued on the plan's stream (another plan's evaluation, say),
+        // only for the previous forward transform to be done with the buffer.
+        if (p.field_free_recorded) FBS_CUDA(cudaStreamWaitEvent(p.copy_stream, p.ev_field_free, 0));
         FBS_CUDA(cudaMemcpyAsync(p.d_field, field, (size_t)N * N * N * sizeof(float), cudaMemcpyDefault,
-                                 p.stream));
+                                 p.copy_stream));
+        FBS_CUDA(cudaEventRecord(p.ev_field_ready, p.copy_stream));
+        FBS_CUDA(cudaStreamWaitEvent(p.stream, p.ev_field_ready, 0));
         d_in = p.d_field;
     }
     const bool tc = p.precision != FBS_PREC_FP32;
@@ -572,6 +582,10 @@ static void run_field(Plan &p, const float *field, bool quads) {
     if (p.precision != FBS_PREC_FP32 && tc_error_flag(p))
         FBS_CUDA(cudaMemsetAsync(tc_error_flag(p), 0, sizeof(int), p.stream));
     launch_forward(p, d_in);
+    if (staged) {
+        FBS_CUDA(cudaEventRecord(p.ev_field_free, p.stream));
+        p.field_free_recorded = true;
+    }
     launch_inverse_x(p, false);
     const int M = p.M;
     const long long plane = (long long)M * M;
@@ -612,9 +626,20 @@ static void check_device_errors(Plan &p) {
     if (v) throw Failure{FBS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (code " + std::to_string(v) + ")"};
 }
 
+// Pageable host memory (not registered with CUDA): the copy cannot run
+// asynchronously, so the call waits for its results.
+static bool is_pageable(const void *ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered;
+}
+
 static void copy_out(Plan &p, double *dst, const double *src, size_t n, bool &host) {
     if (!dst || n == 0) return;
-    if (!is_device_ptr(dst)) host = true;
+    if (!is_device_ptr(dst) && is_pageable(dst)) host = true;
     FBS_CUDA(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, p.stream));
 }
 
@@ -712,10 +737,14 @@ fbs_status fbs_plan_create(fbs_plan **out, int N, double L, const double *edges,
 void fbs_plan_free(fbs_plan *plan) {
     if (!plan) return;
     cudaStreamSynchronize(plan->stream);
+    if (plan->copy_stream) cudaStreamSynchronize(plan->copy_stream);
     cudaGetLastError();
     free_tc_state(*plan);
     for (void *ptr : plan->allocs) cudaFree(ptr);
     for (cudaEvent_t e : plan->evs) cudaEventDestroy(e);
+    if (plan->ev_field_ready) cudaEventDestroy(plan->ev_field_ready);
+    if (plan->ev_field_free) cudaEventDestroy(plan->ev_field_free);
+    if (plan->copy_stream) cudaStreamDestroy(plan->copy_stream);
     cudaGetLastError();
     delete plan;
 }

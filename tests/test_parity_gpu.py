@@ -239,3 +239,59 @@ def test_aliased_plans_use_the_input_grid():
     edges = fields.linear_edges(N, L, 4)
     with fbs.Plan(N, L, edges, allow_aliased=True) as plan:
         assert plan.eval_grid == N
+
+
+def test_host_fields_back_to_back_without_waiting():
+    """Pinned host fields with device outputs: each call only enqueues work and
+    returns.  The host copy runs on the plan's copy stream, which overlaps the
+    other plan's kernels but must not overwrite the staging buffer before the
+    previous forward transform has read it: every result equals the
+    device-field result bit for bit."""
+    import torch
+    N, L = 48, 60.0
+    eB, eT = fields.linear_edges(N, L, 6), fields.linear_edges(N, L, 4)
+    fs = {"1": _field("quadratic", N, 41).astype(np.float32), "2": _field("lognormal", N, 42).astype(np.float32)}
+    dev = torch.device("cuda")
+    with fbs.Plan(N, L, eB, precision="bf16x3") as pb, \
+            fbs.Plan(N, L, eT, precision="bf16x3", trispectrum=True) as pt:
+        ref = {}
+        for k, f in fs.items():
+            d = torch.from_numpy(f).to(dev)
+            B, P = pb.bispectrum(d)
+            T, B4, P4 = pt.trispectrum(d)
+            torch.cuda.synchronize()
+            ref[k] = (B.cpu().numpy(), T.cpu().numpy())
+        hosts = {k: torch.from_numpy(f).pin_memory() for k, f in fs.items()}
+        outs = []
+        for _ in range(3):
+            for k in ("1", "2"):
+                B = torch.empty(pb.ntrip, dtype=torch.float64, device=dev)
+                P = torch.empty(pb.nbins, dtype=torch.float64, device=dev)
+                pb.bispectrum(hosts[k], B, P)
+                T = torch.empty(pt.nquad, dtype=torch.float64, device=dev)
+                B4 = torch.empty(pt.ntrip, dtype=torch.float64, device=dev)
+                P4 = torch.empty(pt.nbins, dtype=torch.float64, device=dev)
+                pt.trispectrum(hosts[k], T, B4, P4)
+                outs.append((k, B, T))
+        torch.cuda.synchronize()
+        for k, B, T in outs:
+            assert np.array_equal(B.cpu().numpy(), ref[k][0])
+            assert np.array_equal(T.cpu().numpy(), ref[k][1])
+
+
+def test_pinned_host_outputs_filled_once_the_stream_passes():
+    """Page-locked host outputs: the call enqueues the copies and returns; after
+    the plan's stream is synchronised they hold the device-output results."""
+    import torch
+    N, L = 32, 100.0
+    edges = fields.linear_edges(N, L, 6)
+    f32 = _field("lognormal", N, 51).astype(np.float32)
+    with fbs.Plan(N, L, edges, precision="bf16x3") as plan:
+        Bd, Pd = plan.bispectrum(torch.from_numpy(f32).cuda())
+        torch.cuda.synchronize()
+        Bh = torch.full((plan.ntrip,), float("nan"), dtype=torch.float64).pin_memory()
+        Ph = torch.full((plan.nbins,), float("nan"), dtype=torch.float64).pin_memory()
+        plan.bispectrum(torch.from_numpy(f32).pin_memory(), Bh, Ph)
+        torch.cuda.current_stream().synchronize()
+        assert np.array_equal(Bh.numpy(), Bd.cpu().numpy())
+        assert np.array_equal(Ph.numpy(), Pd.cpu().numpy(), equal_nan=True)
