@@ -141,12 +141,19 @@ enum {
                            1: "wide" orientation with the <= 64 left rows stacked
                            [hi; lo] as operand A and up to 256 right pair
                            products as operand B (BF16x4).  Ignored for FP32. */
-    FBS_OPT_TC_ROLES = 2 /* warp roles of the default tensor-core contraction:
+    FBS_OPT_TC_ROLES = 2, /* warp roles of the default tensor-core contraction:
                             0 (default) or 1: 16 warps form the pair products
                             and build operand B in turn; 2: 8 warps form the
-                            pair products while 8 others build operand B.  The
-                            results are identical; only the speed differs
-                            (2 measured about 4% slower at 512^3). */
+                            pair products while 8 others build operand B
+                            (64-point steps only).  At equal steps the results
+                            are identical; only the speed differs (2 measured
+                            about 4% slower at 512^3). */
+    FBS_OPT_TC_CHUNK = 3  /* points per pipeline step of the default tensor-core
+                            contraction: 0 (default) or 2: 128 when two
+                            128-column A stages fit beside the accumulators
+                            in tensor memory (and 16 product warps are in
+                            use), else 64; 1: always 64.  Sums agree within
+                            rounding (the CTAs' point ranges differ). */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */

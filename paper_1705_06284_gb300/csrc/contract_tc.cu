@@ -195,7 +195,7 @@ constexpr int kProdWarps = 16;            // A-operand warps (AW) + operand-B wa
 constexpr int kMmaWarp = kProdWarps;
 constexpr int kLoadWarp = kProdWarps + 1;
 constexpr int kTcThreads = (kProdWarps + 2) * 32;
-constexpr int kAStageCols = 64;           // 32 columns hi + 32 columns lo (64 BF16 per row each)
+constexpr int kAStageCols = 64;           // per K-atom: 32 columns hi + 32 columns lo (64 BF16 per row each)
 constexpr int kMaxAStages = 3;
 constexpr int kMaxFieldStages = 4;
 
@@ -309,11 +309,12 @@ __device__ __forceinline__ const float4 *stage_at(const unsigned char *st, int h
                                             (((j & 7) ^ (b & 7)) << 4));
 }
 
-// One operand-B unit u = (inner row, 8-point group): the row's values (a
-// single bin, or the product of two bins) split into BF16 hi/lo, stored in
-// the 128-byte-swizzled K-major tiles.
+// One operand-B unit u = (inner row, 8-point group j of the chunk): the
+// row's values (a single bin, or the product of two bins) split into BF16
+// hi/lo, stored in the 128-byte-swizzled K-major tile of K-atom j / 8.
 __device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_bytes, const int2 *s_inner,
-                                             int ninner, int u, unsigned char *bh, unsigned char *bl) {
+                                             int ninner, int u, unsigned char *bh, unsigned char *bl,
+                                             int b_tile) {
     const int row = u % ninner, j = u / ninner;
     const int2 in = s_inner[row];
     float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
@@ -327,7 +328,7 @@ __device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_b
     float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
     uint4 h, l;
     split8(v, h, l);
-    const uint32_t off = sw128_off(row, j);
+    const uint32_t off = (uint32_t)((j >> 3) * b_tile) + sw128_off(row, j & 7);
     *reinterpret_cast<uint4 *>(bh + off) = h;
     *reinterpret_cast<uint4 *>(bl + off) = l;
 }
@@ -337,7 +338,10 @@ __device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_b
 // AW: warps forming the pair products of operand A (4 per TMEM lane quarter
 // x 16 points, or 2 x 32 points); with AW = 16 they also build operand B,
 // with AW = 8 the other 8 producer warps build operand B concurrently.
-template <int NST, int NSTG, int AW>
+// KA: 64-point K-atoms per chunk (1 or 2): a chunk is 64 KA points, staged as
+// 2 KA TMA boxes of 32 points, with one swizzled B tile per atom and A stages
+// of 64 KA tensor-memory columns.
+template <int NST, int NSTG, int AW, int KA>
 __global__ void __launch_bounds__(kTcThreads, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap fmap, long long npts, int nbins, int Npad,
                        int tstride, int ninner, const int2 *__restrict__ inner,
@@ -346,8 +350,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
                        int *__restrict__ err) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
+    static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
-    constexpr int PPT = 4 * KC / AW;      // points of a row per A thread per tile
+    constexpr int KCH = KC * KA;          // points per chunk
+    constexpr int PPT = 4 * KCH / AW;     // points of a row per A thread per tile
+    constexpr int ACOLS = kAStageCols * KA;  // tensor-memory columns of one A stage
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ TcBars bars;
     __shared__ int2 s_inner[kMaxInner];
@@ -371,15 +378,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- shared memory: B tiles and field stages (1024-aligned), sums, pair bins
     uintptr_t base = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023;
     unsigned char *sm = reinterpret_cast<unsigned char *>(base);
-    const int b_tile = Npad * 128;
-    unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_tile;
-    const int half_bytes = ((nbins + 7) & ~7) * 128;
-    unsigned char *const stg = sm + 4 * b_tile;
-    float2 *acc = reinterpret_cast<float2 *>(stg + NSTG * 2 * half_bytes);
+    const int b_tile = Npad * 128;      // one K-atom of operand B (hi or lo)
+    const int b_stage = KA * b_tile;    // one B stage (hi or lo), atoms consecutive
+    unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_stage;
+    const int half_bytes = ((nbins + 7) & ~7) * 128;  // one 32-point TMA box of all bins
+    const int stage_bytes = 2 * KA * half_bytes;
+    unsigned char *const stg = sm + 4 * b_stage;
+    float2 *acc = reinterpret_cast<float2 *>(stg + NSTG * stage_bytes);
     int2 *pbc = reinterpret_cast<int2 *>(acc + nloc);  // (b, c) of every row of every tile
 
     const int acc_cols = ((ntl * tstride + 31) / 32) * 32;
-    const int tmem_cols_needed = acc_cols + NST * kAStageCols;
+    const int tmem_cols_needed = acc_cols + NST * ACOLS;
     int ncols = 32;
     while (ncols < tmem_cols_needed) ncols <<= 1;
 
@@ -414,7 +423,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int p = p_first + i;
         pbc[i] = p < npairs ? make_int2(pairs[p].b, pairs[p].c) : make_int2(-1, -1);
     }
-    for (int i = tid; i < 4 * b_tile / 16; i += kTcThreads) {  // padding rows of B stay zero
+    for (int i = tid; i < 4 * b_stage / 16; i += kTcThreads) {  // padding rows of B stay zero
         int o = i % (b_tile / 16);
         if ((o * 16) / 128 >= ninner) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     }
@@ -424,7 +433,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tmem = tmem_slot;
     volatile int *abortp = &abort_flag;
 
-    const long long nchunks = (npts + KC - 1) / KC;
+    const long long nchunks = (npts + KCH - 1) / KCH;
     const long long c0 = nchunks * blockIdx.x / gridDim.x;
     const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
 
@@ -432,16 +441,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ================= field loader (one thread) =================
         if (lane == 0 && c0 < c1) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&fmap)) : "memory");
-            const uint32_t bytes = 2u * (uint32_t)nbins * 128u;
+            const uint32_t bytes = 2u * KA * (uint32_t)nbins * 128u;
             Ring<NSTG> rs;
             long long issued = 0;
             for (long long ci = c0; ci < c1; ++ci) {
                 if (rs.warm && !role_wait(&bars.sempty[rs.slot], rs.phase ^ 1u, abortp, err, 10)) break;
-                const uint32_t dst = smem_u32(stg + rs.slot * 2 * half_bytes);
-                const int x = (int)(ci * KC);
+                const uint32_t dst = smem_u32(stg + rs.slot * stage_bytes);
+                const int x = (int)(ci * KCH);
                 mbar_expect_tx(&bars.sfull[rs.slot], bytes);
-                tma_load_2d(dst, &fmap, x, 0, &bars.sfull[rs.slot]);
-                tma_load_2d(dst + half_bytes, &fmap, x + 32, 0, &bars.sfull[rs.slot]);
+#pragma unroll
+                for (int h = 0; h < 2 * KA; ++h)
+                    tma_load_2d(dst + h * half_bytes, &fmap, x + 32 * h, 0, &bars.sfull[rs.slot]);
                 rs.next();
                 ++issued;
             }
@@ -465,17 +475,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (long long ci = c0; ci < c1; ++ci) {
                 const int sb = rb.slot;
                 const bool okb = role_wait(&bars.bfull[sb], rb.phase, abortp, err, 11);
-                const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + sb * b_tile));
-                const uint64_t dbl = sdesc_sw128(smem_u32(Bl0 + sb * b_tile));
+                const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + sb * b_stage));
+                const uint64_t dbl = sdesc_sw128(smem_u32(Bl0 + sb * b_stage));
+                const uint64_t datom = (uint64_t)((unsigned)b_tile >> 4);  // next K-atom's tile
                 for (int lt = 0; lt < ntl; ++lt) {
                     const int as = ra.slot;
                     const bool oka = role_wait(&bars.full[as], ra.phase, abortp, err, 12);
                     tc_fence_after();
                     if (okb && oka) {  // a failed wait leaves ok false (the abort flag is sticky)
                         const uint32_t d = tmem + (uint32_t)(lt * tstride);
-                        const uint32_t ah = tmem + (uint32_t)(acc_cols + as * kAStageCols);
-                        const uint32_t al = ah + 32u;
-                        // descriptors of k-step k: start address field + 2k (32 bytes)
+                        const uint32_t ah = tmem + (uint32_t)(acc_cols + as * ACOLS);
+                        const uint32_t al = ah + 32u * KA;
+                        // k-step k: A columns 8k; B atom k/4 (tile start + b_tile),
+                        // start address field + 2 (k mod 4) within the atom (32 bytes)
                         if (fresh) mma_ts<false>(d, ah, dbh, idesc);
                         else mma_ts<true>(d, ah, dbh, idesc);
                         if (x3) {
@@ -483,11 +495,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             mma_ts<true>(d, al, dbh, idesc);
                         }
 #pragma unroll
-                        for (int k = 1; k < 4; ++k) {
-                            mma_ts<true>(d, ah + 8u * k, dbh + 2u * k, idesc);
+                        for (int k = 1; k < 4 * KA; ++k) {
+                            const uint64_t bo = datom * (uint64_t)(k >> 2) + 2u * (k & 3);
+                            mma_ts<true>(d, ah + 8u * k, dbh + bo, idesc);
                             if (x3) {
-                                mma_ts<true>(d, ah + 8u * k, dbl + 2u * k, idesc);
-                                mma_ts<true>(d, al + 8u * k, dbh + 2u * k, idesc);
+                                mma_ts<true>(d, ah + 8u * k, dbl + bo, idesc);
+                                mma_ts<true>(d, al + 8u * k, dbh + bo, idesc);
                             }
                         }
                     }
@@ -518,11 +531,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         Ring<2> rb;
         for (long long ci = c0; ci < c1; ++ci) {
             role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 24);
-            const unsigned char *st = stg + rs.slot * 2 * half_bytes;
+            const unsigned char *st = stg + rs.slot * stage_bytes;
             const int sb = rb.slot;
             if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 25);
-            for (int u = btid; u < ninner * 8; u += BW * 32)
-                build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_tile, Bl0 + sb * b_tile);
+            for (int u = btid; u < ninner * 8 * KA; u += BW * 32)
+                build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_stage, Bl0 + sb * b_stage, b_tile);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.bfull[sb]);
@@ -543,13 +556,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int since = 0;
         for (long long ci = c0; ci < c1; ++ci) {
             role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 20);
-            const unsigned char *st = stg + rs.slot * 2 * half_bytes;
+            const unsigned char *st = stg + rs.slot * stage_bytes;
             if constexpr (BW == 0) {
                 // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
                 const int sb = rb.slot;
                 if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21);
-                for (int u = ptid; u < ninner * 8; u += AW * 32)
-                    build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_tile, Bl0 + sb * b_tile);
+                for (int u = ptid; u < ninner * 8 * KA; u += AW * 32)
+                    build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_stage, Bl0 + sb * b_stage,
+                                 b_tile);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.bfull[sb]);
@@ -562,7 +576,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
-                const uint32_t col = (uint32_t)(acc_cols + as * kAStageCols + (PPT / 2) * kq);
+                const uint32_t col = (uint32_t)(acc_cols + as * ACOLS + (PPT / 2) * kq);
                 // 16 points (8 columns of hi, 8 of lo) at a time
 #pragma unroll
                 for (int c = 0; c < PPT / 16; ++c) {
@@ -587,7 +601,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int j = 0; j < 8; ++j) hw[j] = lw[j] = 0u;
                     }
                     tmem_st8a(lanebase + col + 8u * c, hw);
-                    tmem_st8a(lanebase + col + 32u + 8u * c, lw);
+                    tmem_st8a(lanebase + col + 32u * KA + 8u * c, lw);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
@@ -918,9 +932,9 @@ __global__ void __launch_bounds__(kWideThreads, 1)
 // ------------------------------------------------------------------ host side
 // Dynamic shared memory of the narrow kernel: B tiles, nstg field stages,
 // compensated sums, pair bins.
-static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl, int nstg) {
+static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl, int nstg, int ka = 1) {
     const size_t half = (size_t)((nbins + 7) & ~7) * 128;
-    size_t b = 1024 + 4 * (size_t)Npad * 128 + (size_t)nstg * 2 * half + (size_t)nloc * 8 +
+    size_t b = 1024 + 4 * (size_t)ka * Npad * 128 + (size_t)nstg * 2 * ka * half + (size_t)nloc * 8 +
                (size_t)ntl * 128 * 8;
     return std::max<size_t>(b, 116 * 1024);  // > half the SM's shared memory: one CTA per SM
 }
@@ -1244,37 +1258,48 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int G = std::max(1, sms / ngrp);
     if (G > p.part_blocks) G = p.part_blocks;
+    // 16 warps form the pair products and build operand B in turn (measured
+    // faster at both headline passes); 8 + 8 concurrent roles on request
+    const int aw = p.tc_roles == 2 ? 8 : 16;
+    // 128-point chunks (half the hand-offs per point) when two 128-column A
+    // stages fit beside the accumulators in tensor memory and shared memory
+    // holds the doubled stages; 64-point chunks otherwise
+    const int acc_cols_max = (((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32;
+    const bool fits2 = acc_cols_max + 2 * 2 * kAStageCols <= 512 &&
+                       tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 2, 2) <= 220 * 1024;
+    const int ka = (fits2 && p.tc_chunk != 1 && aw == 16) ? 2 : 1;
     // pipeline depths: 3 A stages when tensor memory allows, 4 field stages
     // when shared memory allows
-    const int acc_cols_max = (((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32;
-    const int nst = acc_cols_max + 3 * kAStageCols <= 512 ? 3 : 2;
-    const int nstg = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 4) <= 220 * 1024 ? 4 : 2;
-    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, nstg);
+    const int nst = acc_cols_max + 3 * ka * kAStageCols <= 512 ? 3 : 2;
+    const int nstg = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 4, ka) <= 220 * 1024 ? 4 : 2;
+    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, nstg, ka);
+    const int flush_every = 16 / ka;  // 1024 points in FP32 per flush
     const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins);
     KTimer tm(p, kclass);
     dim3 grid(G, ngrp);
     const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
-#define FBS_TC_LAUNCH(A, S, W)                                                                        \
-    if (nst == A && nstg == S && aw == W) {                                                           \
+#define FBS_TC_LAUNCH(A, S, W, K)                                                                     \
+    if (nst == A && nstg == S && aw == W && ka == K) {                                                \
         launched = true;                                                                              \
-        FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S, W>,                                    \
+        FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S, W, K>,                                 \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));          \
-        contract_tc_kernel<A, S, W><<<grid, kTcThreads, sm, p.stream>>>(                             \
+        contract_tc_kernel<A, S, W, K><<<grid, kTcThreads, sm, p.stream>>>(                          \
             fmap, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner, job.d_pairs, \
-            job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, 16, st.d_err);                 \
+            job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err);        \
     }
-    // 16 warps form the pair products and build operand B in turn (measured
-    // faster at both headline passes); 8 + 8 concurrent roles on request
-    const int aw = p.tc_roles == 2 ? 8 : 16;
     bool launched = false;
-    FBS_TC_LAUNCH(2, 2, 16)
-    FBS_TC_LAUNCH(2, 4, 16)
-    FBS_TC_LAUNCH(3, 2, 16)
-    FBS_TC_LAUNCH(3, 4, 16)
-    FBS_TC_LAUNCH(2, 2, 8)
-    FBS_TC_LAUNCH(2, 4, 8)
-    FBS_TC_LAUNCH(3, 2, 8)
-    FBS_TC_LAUNCH(3, 4, 8)
+    FBS_TC_LAUNCH(2, 2, 16, 1)
+    FBS_TC_LAUNCH(2, 4, 16, 1)
+    FBS_TC_LAUNCH(3, 2, 16, 1)
+    FBS_TC_LAUNCH(3, 4, 16, 1)
+    FBS_TC_LAUNCH(2, 2, 8, 1)
+    FBS_TC_LAUNCH(2, 4, 8, 1)
+    FBS_TC_LAUNCH(3, 2, 8, 1)
+    FBS_TC_LAUNCH(3, 4, 8, 1)
+    FBS_TC_LAUNCH(2, 2, 16, 2)
+    FBS_TC_LAUNCH(2, 4, 16, 2)
+    FBS_TC_LAUNCH(3, 2, 16, 2)
+    FBS_TC_LAUNCH(3, 4, 16, 2)
 #undef FBS_TC_LAUNCH
     if (!launched) throw Failure{FBS_ERR_STATE, "tensor-core contraction: no kernel for this pipeline shape"};
     FBS_CUDA(cudaGetLastError());

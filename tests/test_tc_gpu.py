@@ -125,8 +125,9 @@ def test_wide_orientation_matches(monkeypatch, N, nb, quads):
 @pytest.mark.parametrize("quads", [False, True])
 def test_warp_roles_give_identical_results(quads):
     """FBS_OPT_TC_ROLES 1 (16 warps form the pair products and build operand B
-    in turn) and 2 (8 + 8 warps concurrently) issue the same MMAs in the same
-    order: bit-identical sums, and both match the oracle."""
+    in turn) and 2 (8 + 8 warps concurrently), at the same 64-point pipeline
+    steps, issue the same MMAs in the same order: bit-identical sums, and
+    both match the oracle."""
     import torch
     N, L, nb = 48, 60.0, 10
     edges = fields.linear_edges(N, L, nb)
@@ -134,6 +135,7 @@ def test_warp_roles_give_identical_results(quads):
     f = torch.from_numpy(f32).cuda()
     out = {}
     with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        plan.set_option(fbs.FBS_OPT_TC_CHUNK, 1)  # the same 64-point steps for both
         for roles in (1, 2):
             plan.set_option(fbs.FBS_OPT_TC_ROLES, roles)
             if quads:
@@ -149,3 +151,35 @@ def test_warp_roles_give_identical_results(quads):
             assert np.array_equal(out[1][2], out[2][2])
             check_trispectrum(plan, out[2][2], f32, L, edges, 2e-4)
         check_bispectrum(plan, out[2][0], out[2][1], f32, L, edges, "bf16x3")
+
+
+@pytest.mark.parametrize("quads", [False, True])
+def test_chunk_sizes_agree(quads):
+    """FBS_OPT_TC_CHUNK 1 (64-point pipeline steps) and 2 (128-point steps,
+    two K-atoms per step) both match the oracle and agree with each other to
+    rounding (the CTAs' point ranges differ, so the sums are grouped
+    differently)."""
+    import torch
+    N, L, nb = 48, 60.0, 10
+    edges = fields.linear_edges(N, L, nb)
+    f32 = _field("lognormal", N, 33).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    out = {}
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        for chunk in (1, 2):
+            plan.set_option(fbs.FBS_OPT_TC_CHUNK, chunk)
+            if quads:
+                T, B, P = plan.trispectrum(f)
+            else:
+                B, P = plan.bispectrum(f)
+                T = None
+            torch.cuda.synchronize()
+            out[chunk] = (B.cpu().numpy(), P.cpu().numpy(), None if T is None else T.cpu().numpy())
+            check_bispectrum(plan, out[chunk][0], out[chunk][1], f32, L, edges, "bf16x3")
+            if quads:
+                check_trispectrum(plan, out[chunk][2], f32, L, edges, 2e-4)
+        ref = oracle.direct_bispectrum(f32.astype(np.float64), L, edges)
+        M = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=ref["triplets"])["M"]
+        g = gate_mask(ref["B"], M, ref["N_tri"])
+        # each is within the BF16x3 gate of the oracle; so is their difference
+        assert np.all(np.abs(out[1][0] - out[2][0])[g] <= 2e-4 * np.abs(ref["B"][g]))
