@@ -148,12 +148,18 @@ enum {
                             (64-point steps only).  At equal steps the results
                             are identical; only the speed differs (2 measured
                             about 4% slower at 512^3). */
-    FBS_OPT_TC_CHUNK = 3  /* points per pipeline step of the default tensor-core
+    FBS_OPT_TC_CHUNK = 3, /* points per pipeline step of the default tensor-core
                             contraction: 0 (default) or 2: 128 when two
                             128-column A stages fit beside the accumulators
                             in tensor memory (and 16 product warps are in
                             use), else 64; 1: always 64.  Sums agree within
                             rounding (the CTAs' point ranges differ). */
+    FBS_OPT_TC_PAIRS = 4  /* outer rows of the bispectrum's tensor-core
+                            contraction: 0 (default): each triplet is carried
+                            by one of its three pairs, chosen by a greedy set
+                            cover (fewer 128-row tiles); 1: by its pair of
+                            the two largest bins (b, c).  Sums agree within
+                            rounding. */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */

@@ -39,6 +39,7 @@ FBS_FLAG_FULL_GRID = 8
 FBS_OPT_TC_WIDE = 1
 FBS_OPT_TC_ROLES = 2
 FBS_OPT_TC_CHUNK = 3
+FBS_OPT_TC_PAIRS = 4
 
 _PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
 

@@ -60,6 +60,7 @@ struct TcJob {
     std::vector<int> grp;  // tile ranges of the CTA groups
     int *d_grp = nullptr;
     bool built = false, usable = false;
+    int variant = 0;       // pair assignment the tables were built with (FBS_OPT_TC_PAIRS)
 };
 
 struct WideRight {
@@ -1010,10 +1011,104 @@ static void finish_job(Plan &p, TcJob &job, const std::vector<TcPair> &hp, const
     job.usable = true;
 }
 
+// Bispectrum job with every triplet (a <= b <= c) carried by one of its three
+// pairs: sum_x I_a I_b I_c is the same whichever two fields form the product
+// and which one is the inner row.  A greedy set cover (the pair that carries
+// the most uncovered triplets first, ties to the smaller pair) keeps the
+// outer rows, and so the 128-row tiles, few: 378 instead of 546 pairs for 64
+// log bins at 512^3.
+static void build_covered_job(Plan &p, const TaskList &t, TcJob &job) {
+    const int nb = p.nbins;
+    std::vector<std::array<int, 3>> trip;
+    std::vector<int> out;
+    for (int i = 0; i < t.npairs; ++i)
+        for (int e = t.pstart[i]; e < t.pstart[i + 1]; ++e) {
+            std::array<int, 3> tr = {t.ia[e], t.pb[i], t.pc[i]};
+            std::sort(tr.begin(), tr.end());
+            trip.push_back(tr);
+            out.push_back(t.iout[e]);
+        }
+    const int T = (int)trip.size();
+    auto keys = [&](const std::array<int, 3> &tr, int *k) {  // distinct pairs of a triplet
+        int n = 0;
+        const int cand[3] = {tr[0] * nb + tr[1], tr[0] * nb + tr[2], tr[1] * nb + tr[2]};
+        for (int j = 0; j < 3; ++j) {
+            bool seen = false;
+            for (int m = 0; m < n; ++m) seen |= (k[m] == cand[j]);
+            if (!seen) k[n++] = cand[j];
+        }
+        return n;
+    };
+    std::vector<int> cnt((size_t)nb * nb, 0);
+    std::vector<std::vector<int>> of((size_t)nb * nb);
+    for (int i = 0; i < T; ++i) {
+        int k[3];
+        const int n = keys(trip[i], k);
+        for (int m = 0; m < n; ++m) {
+            of[k[m]].push_back(i);
+            ++cnt[k[m]];
+        }
+    }
+    std::vector<int> assigned(T, -1);
+    int left = T;
+    while (left > 0) {
+        int best = -1;
+        for (int q = 0; q < nb * nb; ++q)
+            if (cnt[q] > 0 && (best < 0 || cnt[q] > cnt[best])) best = q;
+        for (int i : of[best]) {
+            if (assigned[i] >= 0) continue;
+            assigned[i] = best;
+            --left;
+            int k[3];
+            const int n = keys(trip[i], k);
+            for (int m = 0; m < n; ++m) --cnt[k[m]];
+        }
+    }
+    // outer rows in pair order; items of a row: the remaining bin, ascending
+    std::map<int, std::vector<std::pair<int, int>>> rows;  // pair key -> (inner bin, output)
+    for (int i = 0; i < T; ++i) {
+        const int x = assigned[i] / nb, y = assigned[i] % nb;
+        std::array<int, 3> rest = trip[i];
+        auto it = std::find(rest.begin(), rest.end(), x);
+        *it = -1;
+        it = std::find(rest.begin(), rest.end(), y);
+        *it = -1;
+        int z = -1;
+        for (int v : rest) if (v >= 0) z = v;
+        rows[assigned[i]].push_back({z, out[i]});
+    }
+    std::vector<int2> inner;
+    for (int b = 0; b < nb; ++b) inner.push_back(make_int2(b, -1));
+    std::vector<TcPair> hp;
+    std::vector<int> iout;
+    for (auto &kv : rows) {
+        auto &items = kv.second;
+        std::sort(items.begin(), items.end());
+        TcPair q{};
+        q.b = kv.first / nb;
+        q.c = kv.first % nb;
+        q.first = (int)iout.size();
+        int prev = -1;
+        for (auto &it : items) {
+            if (it.first <= prev) throw Failure{FBS_ERR_ARG, "pair cover: repeated inner bin"};
+            prev = it.first;
+            q.mask[it.first >> 5] |= 1u << (it.first & 31);
+            iout.push_back(it.second);
+        }
+        hp.push_back(q);
+    }
+    finish_job(p, job, hp, inner, iout);
+}
+
 // One contraction from its pair-grouped task list: inner rows are the single
 // bins (bispectrum) or the distinct inner pairs (trispectrum).
 static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     job.built = true;
+    job.variant = quads ? 0 : p.tc_pairs;
+    if (!quads && p.tc_pairs == 0 && p.nbins <= kMaxInner) {
+        build_covered_job(p, t, job);
+        return;
+    }
     std::vector<int2> inner;
     std::vector<int> row_of;  // (a, b) -> inner row, a*nbins+b
     if (!quads) {
@@ -1311,6 +1406,7 @@ void launch_contract_tc(Plan &p, const float *islab, long long npts, long long s
     if (launch_wide(p, islab, npts, slab_stride, quads)) return;
     TcState &st = tc_state(p);
     TcJob &job = quads ? st.quad : st.trip;
+    if (job.built && !quads && job.variant != p.tc_pairs) job = TcJob{};  // option changed: rebuild
     if (!job.built) build_job(p, t, quads, job);
     if (!job.usable)
         throw Failure{FBS_ERR_ARG, "tensor-core contraction: more than 256 inner rows or shared memory exceeded"};

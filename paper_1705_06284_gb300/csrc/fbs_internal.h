@@ -123,6 +123,7 @@ struct Plan {
     int tc_wide = 0;             // FBS_OPT_TC_WIDE
     int tc_roles = 0;            // FBS_OPT_TC_ROLES: 0 auto, 1 = 16 A warps, 2 = 8 A + 8 B warps
     int tc_chunk = 0;            // FBS_OPT_TC_CHUNK: 0 auto, 1 = 64-point chunks, 2 = 128 where they fit
+    int tc_pairs = 0;            // FBS_OPT_TC_PAIRS: 0 greedy pair cover, 1 = pairs (b, c)
     cudaStream_t stream = nullptr;
     double create_ms = 0;
     double count_margin = 0;  // largest |sum N..N / N_pix - nearest integer| of the rounded counts

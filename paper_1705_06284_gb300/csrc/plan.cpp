@@ -803,6 +803,10 @@ fbs_status fbs_plan_set_option(fbs_plan *plan, int option, int value) {
         plan->tc_chunk = value;
         return FBS_OK;
     }
+    if (option == FBS_OPT_TC_PAIRS && (value == 0 || value == 1)) {
+        plan->tc_pairs = value;
+        return FBS_OK;
+    }
     set_error("unknown option or value");
     return FBS_ERR_ARG;
 }

@@ -183,3 +183,26 @@ def test_chunk_sizes_agree(quads):
         g = gate_mask(ref["B"], M, ref["N_tri"])
         # each is within the BF16x3 gate of the oracle; so is their difference
         assert np.all(np.abs(out[1][0] - out[2][0])[g] <= 2e-4 * np.abs(ref["B"][g]))
+
+
+@pytest.mark.parametrize("N,L,nb,kind", [(48, 60.0, 12, "lin"), (64, 200.0, 16, "log")])
+def test_pair_cover_matches_oracle(N, L, nb, kind):
+    """FBS_OPT_TC_PAIRS 0 (each triplet carried by one of its three pairs,
+    greedy set cover) and 1 (by its two largest bins): both match the oracle
+    and agree with each other within the BF16x3 gate."""
+    import torch
+    edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
+    f32 = _field("bubbles", N, 61).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    out = {}
+    ref = oracle.direct_bispectrum(f32.astype(np.float64), L, edges)
+    with fbs.Plan(N, L, edges, precision="bf16x3") as plan:
+        for pairs in (0, 1):
+            plan.set_option(fbs.FBS_OPT_TC_PAIRS, pairs)
+            B, P = plan.bispectrum(f)
+            torch.cuda.synchronize()
+            out[pairs] = B.cpu().numpy()
+            check_bispectrum(plan, out[pairs], P.cpu().numpy(), f32, L, edges, "bf16x3", ref=ref)
+    M = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=ref["triplets"])["M"]
+    g = gate_mask(ref["B"], M, ref["N_tri"])
+    assert np.all(np.abs(out[0] - out[1])[g] <= 2e-4 * np.abs(ref["B"][g]))
