@@ -206,3 +206,25 @@ def test_pair_cover_matches_oracle(N, L, nb, kind):
     M = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=ref["triplets"])["M"]
     g = gate_mask(ref["B"], M, ref["N_tri"])
     assert np.all(np.abs(out[0] - out[1])[g] <= 2e-4 * np.abs(ref["B"][g]))
+
+
+def test_pair_cover_trispectrum_matches_oracle():
+    """Trispectrum pass with FBS_OPT_TC_PAIRS 0 (each quadruplet's pairing and
+    inner/outer roles chosen by a cover that keeps one 128-row outer tile and
+    few inner rows) and 1 (inner (a, b), outer (c, d)): both match the FP64
+    estimator for T and the oracle for B."""
+    import torch
+    N, L, nb = 48, 60.0, 10
+    edges = fields.log_edges(N, L, nb)
+    f32 = _field("quadratic", N, 71).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    ref = oracle.direct_bispectrum(f32.astype(np.float64), L, edges)
+    out = {}
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=True) as plan:
+        for pairs in (0, 1):
+            plan.set_option(fbs.FBS_OPT_TC_PAIRS, pairs)
+            T, B, P = plan.trispectrum(f)
+            torch.cuda.synchronize()
+            out[pairs] = T.cpu().numpy()
+            check_trispectrum(plan, out[pairs], f32, L, edges, 2e-4)
+            check_bispectrum(plan, B.cpu().numpy(), P.cpu().numpy(), f32, L, edges, "bf16x3", ref=ref)
