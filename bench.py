@@ -536,12 +536,12 @@ def _closed_triplets_oracle(N, thr):
 # (every bin's shell-field value of the slab read once); scaled to the bench's
 # launch by its points.  Source: the profile summary named beside the value.
 NCU_TRAFFIC_RATIO = {
-    "contract_tc": ((916.518656e6 + 2.985472e6) / (64 * 3538944 * 4.0),
+    "contract_tc": ((916.344576e6 + 3.036160e6) / (64 * 3538944 * 4.0),
                     "ncu: bispectrum pass, 256^3, 64 log bins, 3.54M points "
-                    "(profiles/contract_tc_quadratic256_B64log_traffic.md), scaled by points"),
-    "contract_quad_tc": ((540.102144e6 + 3.027712e6) / (16 * 8388608 * 4.0),
+                    "(profiles/contract_tc_quadratic256_B64log_T16log_traffic.md), scaled by points"),
+    "contract_quad_tc": ((540.110080e6 + 0.122624e6) / (16 * 8388608 * 4.0),
                          "ncu: fused triplet+quadruplet pass, 256^3, 16 log bins, 8.39M points "
-                         "(profiles/contract_tc_fused_quadratic256_T16log.md), scaled by points"),
+                         "(profiles/contract_tc_quadratic256_B64log_T16log_traffic.md), scaled by points"),
 }
 
 
