@@ -81,7 +81,11 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index)
+        # samples go to a per-process file under the system temporary directory
+        # (FBS_CLOCKS_DIR overrides it, e.g. to keep the samples of a run)
+        import tempfile
+        d = os.environ.get("FBS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, "fbs_clocks_gpu%d_pid%d.csv" % (index, os.getpid()))
 
     def start(self):
         try:

@@ -1449,8 +1449,8 @@ bool tc_quads_usable(Plan &p) {
     return st.quad.usable;
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library).
+// cuTensorMapEncodeTiled through cudaGetDriverEntryPointByVersion, so the
+// library links only the CUDA runtime (not libcuda directly).
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void *f = nullptr;
