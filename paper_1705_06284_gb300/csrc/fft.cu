@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(kThreads) inv_x_kernel(const float2 *__restric
 }
 
 // y stage over planes x0 .. x0+nx-1.  CTA = (jz group, plane, bin).
-template <typename T>
+// Rs...: compile-time radices of the transform length (empty: the run-time
+// factors f).
+template <typename T, int... Rs>
 __global__ void __launch_bounds__(kThreads) inv_y_kernel(const typename V2<T>::t *__restrict__ A,
                                                          const BinGeom *__restrict__ geom, int bin0,
                                                          int N, int x0,
@@ -222,7 +224,13 @@ __global__ void __launch_bounds__(kThreads) inv_y_kernel(const typename V2<T>::t
         a[l * ld + (my + N) % N] = in[((long long)x * g.Db + jy) * g.Dzb + mz];
     }
     __syncthreads();
-    C *res = smem_fft<T, +1>(a, b, nl, ld, f, tw);
+    C *res;
+    if constexpr (sizeof...(Rs) > 0) {
+        constexpr int NC = (Rs * ...);
+        res = smem_fft_ct<T, +1, NC, 1, Rs...>(a, b, nl, ld, tw);
+    } else {
+        res = smem_fft<T, +1>(a, b, nl, ld, f, tw);
+    }
     C *out = G + g.G_off;
     for (int i = threadIdx.x; i < nl * N; i += blockDim.x) {
         int y = i / nl, l = i - y * nl;
@@ -584,7 +592,16 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
     {
         KTimer t(p, KC_INV_Y);
+        // compile-time radices for the common evaluation grids, run-time otherwise
         auto k = inv_y_kernel<float>;
+        if (N == 512) k = inv_y_kernel<float, 8, 8, 8>;
+        if (N == 384) k = inv_y_kernel<float, 8, 8, 2, 3>;
+        if (N == 256) k = inv_y_kernel<float, 8, 8, 4>;
+        if (N == 192) k = inv_y_kernel<float, 8, 8, 3>;
+        if (N == 128) k = inv_y_kernel<float, 8, 8, 2>;
+        if (N == 96) k = inv_y_kernel<float, 8, 4, 3>;
+        if (N == 64) k = inv_y_kernel<float, 8, 8>;
+        if (getenv("FBS_GENERIC_Y")) k = inv_y_kernel<float>;
         allow_smem(k, sm);
         dim3 grid((max_dzb(p, 0, p.nbins) + nl - 1) / nl, nx, p.nbins);
         k<<<grid, kThreads, sm, p.stream>>>(p.d_A, p.d_geom, 0, N, x0, p.d_G, 0, nl, p.fM, p.d_twM);

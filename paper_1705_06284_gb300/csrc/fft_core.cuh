@@ -124,6 +124,57 @@ __device__ __forceinline__ void stockham_stage(const typename V2<T>::t *__restri
 }
 
 // Full transform; returns the buffer holding the result (a or b).
+// The same Stockham stage with the transform length, radix and stride as
+// compile-time constants (the line/butterfly split and twiddle strides need
+// no run-time division).
+template <typename T, int DIR, int N, int R, int NS>
+__device__ __forceinline__ void stockham_stage_ct(const typename V2<T>::t *__restrict__ a,
+                                                  typename V2<T>::t *__restrict__ b, int nl, int ld,
+                                                  const typename V2<T>::t *__restrict__ tw) {
+    typedef typename V2<T>::t C;
+    constexpr int nbf = N / R;
+    constexpr int twstep = N / (NS * R);
+    const int tot = nl * nbf;
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+        const int line = idx / nbf;
+        const int j = idx - line * nbf;
+        const int k = j % NS;
+        const C *src = a + (size_t)line * ld;
+        C v[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[q] = src[j + q * nbf];
+        if (NS > 1) {
+#pragma unroll
+            for (int q = 1; q < R; ++q) {
+                C w = tw[k * q * twstep];
+                v[q] = DIR < 0 ? cmul(v[q], w) : cmulc(v[q], w);
+            }
+        }
+        dftR<DIR, T, R>(v);
+        C *dst = b + (size_t)line * ld;
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int q = 0; q < R; ++q) dst[base + q * NS] = v[q];
+    }
+}
+
+// Length-N transform of nl lines through compile-time radices R, Rest...
+// (their product is N); ping-pongs a <-> b like smem_fft and returns the
+// buffer holding the result.
+template <typename T, int DIR, int N, int NS, int R, int... Rest>
+__device__ __forceinline__ typename V2<T>::t *smem_fft_ct(typename V2<T>::t *a, typename V2<T>::t *b,
+                                                          int nl, int ld,
+                                                          const typename V2<T>::t *__restrict__ tw) {
+    stockham_stage_ct<T, DIR, N, R, NS>(a, b, nl, ld, tw);
+    __syncthreads();
+    if constexpr (sizeof...(Rest) == 0) {
+        static_assert(NS * R == N, "radices must multiply to N");
+        return b;
+    } else {
+        return smem_fft_ct<T, DIR, N, NS * R, Rest...>(b, a, nl, ld, tw);
+    }
+}
+
 template <typename T, int DIR>
 __device__ typename V2<T>::t *smem_fft(typename V2<T>::t *a, typename V2<T>::t *b, int nl, int ld,
                                        const FftFactors &f, const typename V2<T>::t *__restrict__ tw) {
