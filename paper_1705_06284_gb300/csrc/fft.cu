@@ -47,6 +47,7 @@ static void allow_smem(K kernel, size_t bytes) {
 
 // ------------------------------------------------------------------ forward
 // z pass: rows r = x*N + y, packed pairs (r0, r0+1) as re/im of one line.
+template <int... Rs>
 __global__ void __launch_bounds__(kThreads) fwd_z_kernel(const float *__restrict__ field,
                                                          float2 *__restrict__ zbuf, int N, int Dz,
                                                          int nl, FftFactors f,
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) fwd_z_kernel(const float *__restrict
         a[line * ld + z] = make_float2(v0, v1);
     }
     __syncthreads();
-    float2 *res = smem_fft<float, -1>(a, b, nl, ld, f, tw);
+    float2 *res = smem_fft_sel<float, -1, Rs...>(a, b, nl, ld, f, tw);
     for (int i = threadIdx.x; i < nl * Dz; i += blockDim.x) {
         int line = i / Dz, m = i - line * Dz;
         long long r = row0 + 2 * line;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(kThreads) fwd_z_kernel(const float *__restrict
 }
 
 // y pass: lines (x, jz); input zbuf[x][y][jz], output ybuf[x][jy][jz].
+template <int... Rs>
 __global__ void __launch_bounds__(kThreads) fwd_y_kernel(const float2 *__restrict__ zbuf,
                                                          float2 *__restrict__ ybuf, int N, int D,
                                                          int Dz, int nl, FftFactors f,
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(kThreads) fwd_y_kernel(const float2 *__restric
         a[l * ld + y] = v;
     }
     __syncthreads();
-    float2 *res = smem_fft<float, -1>(a, b, nl, ld, f, tw);
+    float2 *res = smem_fft_sel<float, -1, Rs...>(a, b, nl, ld, f, tw);
     for (int i = threadIdx.x; i < nl * D; i += blockDim.x) {
         int jy = i / nl, l = i - jy * nl;
         if (l >= nz) continue;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(kThreads) fwd_y_kernel(const float2 *__restric
 }
 
 // x pass: lines (jy, jz); input ybuf[x][jy][jz], output box[jx][jy][jz].
+template <int... Rs>
 __global__ void __launch_bounds__(kThreads) fwd_x_kernel(const float2 *__restrict__ ybuf,
                                                          float2 *__restrict__ box, int N, int D,
                                                          int Dz, int nl, FftFactors f,
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(kThreads) fwd_x_kernel(const float2 *__restric
         a[l * ld + x] = v;
     }
     __syncthreads();
-    float2 *res = smem_fft<float, -1>(a, b, nl, ld, f, tw);
+    float2 *res = smem_fft_sel<float, -1, Rs...>(a, b, nl, ld, f, tw);
     for (int i = threadIdx.x; i < nl * D; i += blockDim.x) {
         int jx = i / nl, l = i - jx * nl;
         if (l >= nz) continue;
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(kThreads) fwd_x_kernel(const float2 *__restric
 // ------------------------------------------------------------------ inverse
 // x stage.  CTA = (bin b = bin0 + blockIdx.y, column jy, group of nl jz).
 // IND = true: the spectrum is the shell indicator (count fields, FP64).
-template <typename T, bool IND>
+template <typename T, bool IND, int... Rs>
 __global__ void __launch_bounds__(kThreads) inv_x_kernel(const float2 *__restrict__ box, BoxGeom bg,
                                                          const BinGeom *__restrict__ geom, int bin0,
                                                          typename V2<T>::t *__restrict__ A, int nl,
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) inv_x_kernel(const float2 *__restric
         a[l * ld + (mx + N) % N] = v;
     }
     __syncthreads();
-    C *res = smem_fft<T, +1>(a, b, nl, ld, f, tw);
+    C *res = smem_fft_sel<T, +1, Rs...>(a, b, nl, ld, f, tw);
     C *out = A + g.A_off;
     for (int i = threadIdx.x; i < nl * N; i += blockDim.x) {
         int x = i / nl, l = i - x * nl;
@@ -529,30 +532,51 @@ void upload_twiddles(Plan &p) {
     FBS_CUDA(cudaStreamSynchronize(p.stream));  // host tables go out of scope
 }
 
+// Transform lengths with compile-time radices (the rest use run-time factors).
+#define FBS_RADICES(X) \
+    X(512, 8, 8, 8)    \
+    X(384, 8, 8, 2, 3) \
+    X(256, 8, 8, 4)    \
+    X(192, 8, 8, 3)    \
+    X(128, 8, 8, 2)    \
+    X(96, 8, 4, 3)     \
+    X(64, 8, 8)
+
 void launch_forward(Plan &p, const float *d_field) {
     const int N = p.N, D = p.box.D, Dz = p.box.Dz;
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
+    auto kz = fwd_z_kernel<>;
+    auto ky = fwd_y_kernel<>;
+    auto kx = fwd_x_kernel<>;
+#define FBS_PICK(n, ...)                 \
+    if (N == n) {                        \
+        kz = fwd_z_kernel<__VA_ARGS__>;  \
+        ky = fwd_y_kernel<__VA_ARGS__>;  \
+        kx = fwd_x_kernel<__VA_ARGS__>;  \
+    }
+    FBS_RADICES(FBS_PICK)
+#undef FBS_PICK
     {
         KTimer t(p, KC_FWD_Z);
-        allow_smem(fwd_z_kernel, sm);
+        allow_smem(kz, sm);
         long long rows = (long long)N * N;
         int grid = (int)((rows + 2 * nl - 1) / (2 * nl));
-        fwd_z_kernel<<<grid, kThreads, sm, p.stream>>>(d_field, p.d_zbuf, N, Dz, nl, p.fN, p.d_tw);
+        kz<<<grid, kThreads, sm, p.stream>>>(d_field, p.d_zbuf, N, Dz, nl, p.fN, p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
     {
         KTimer t(p, KC_FWD_Y);
-        allow_smem(fwd_y_kernel, sm);
+        allow_smem(ky, sm);
         dim3 grid((Dz + nl - 1) / nl, N);
-        fwd_y_kernel<<<grid, kThreads, sm, p.stream>>>(p.d_zbuf, p.d_ybuf, N, D, Dz, nl, p.fN, p.d_tw);
+        ky<<<grid, kThreads, sm, p.stream>>>(p.d_zbuf, p.d_ybuf, N, D, Dz, nl, p.fN, p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
     {
         KTimer t(p, KC_FWD_X);
-        allow_smem(fwd_x_kernel, sm);
+        allow_smem(kx, sm);
         dim3 grid((Dz + nl - 1) / nl, D);
-        fwd_x_kernel<<<grid, kThreads, sm, p.stream>>>(p.d_ybuf, p.d_box, N, D, Dz, nl, p.fN, p.d_tw);
+        kx<<<grid, kThreads, sm, p.stream>>>(p.d_ybuf, p.d_box, N, D, Dz, nl, p.fN, p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
 }
@@ -580,6 +604,10 @@ void launch_inverse_x(Plan &p, bool) {
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
     KTimer t(p, KC_INV_X);
     auto k = inv_x_kernel<float, false>;
+#define FBS_PICK(n, ...) \
+    if (N == n) k = inv_x_kernel<float, false, __VA_ARGS__>;
+    FBS_RADICES(FBS_PICK)
+#undef FBS_PICK
     allow_smem(k, sm);
     dim3 grid(max_inv_x_grid(p, 0, p.nbins, nl), p.nbins);
     k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, p.d_geom, 0, p.d_A, nl, p.fM, p.d_twM);

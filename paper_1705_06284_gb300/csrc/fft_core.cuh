@@ -196,4 +196,17 @@ __device__ typename V2<T>::t *smem_fft(typename V2<T>::t *a, typename V2<T>::t *
     return a;
 }
 
+// Compile-time radices when given (their product is the length), else the
+// run-time factors f.
+template <typename T, int DIR, int... Rs>
+__device__ __forceinline__ typename V2<T>::t *smem_fft_sel(typename V2<T>::t *a, typename V2<T>::t *b, int nl,
+                                                           int ld, const FftFactors &f,
+                                                           const typename V2<T>::t *__restrict__ tw) {
+    if constexpr (sizeof...(Rs) > 0) {
+        return smem_fft_ct<T, DIR, (Rs * ...), 1, Rs...>(a, b, nl, ld, tw);
+    } else {
+        return smem_fft<T, DIR>(a, b, nl, ld, f, tw);
+    }
+}
+
 }  // namespace fbs
