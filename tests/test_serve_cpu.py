@@ -1,0 +1,70 @@
+"""Admission control of the serving loop on CPU: plans held under an HBM
+budget, idle plans evicted least-recently-used first, busy plans never
+evicted, and no admission while nothing can be freed.  The plan object is a
+stand-in recording its size and closure; no GPU and no estimator work."""
+import collections
+
+import numpy as np
+import pytest
+
+pytest.importorskip("torch")
+from paper_1705_06284_gb300 import serve
+
+
+class FakePlan:
+    closed = []
+
+    def __init__(self, N, L, edges, precision="bf16x3", stream=None):
+        self.N, self.device_bytes = N, 1000 * N
+        self.stream = stream
+
+    def set_stream(self, s):
+        self.stream = s
+
+    def close(self):
+        FakePlan.closed.append(self.N)
+
+
+def _server(budget, monkeypatch):
+    monkeypatch.setattr(serve, "Plan", FakePlan)
+    monkeypatch.setattr(serve, "plan_bytes_estimate", lambda N, nbins, slab_budget=0: 1000 * N)
+    srv = serve.EstimatorServer.__new__(serve.EstimatorServer)
+    srv.budget, srv.held, srv.plan_creations = budget, 0, 0
+    srv.plans = collections.defaultdict(list)
+    FakePlan.closed = []
+    return srv
+
+
+def _req(rid, N, nb=4):
+    return serve.Request(rid, np.zeros((N, N, N), dtype=np.float32), 100.0, tuple(range(nb + 1)))
+
+
+def test_admission_eviction_and_reuse(monkeypatch):
+    f8 = 2 * 8 ** 3 * 4  # two staging copies of an 8^3 field
+    srv = _server(3 * (8000 + f8), monkeypatch)
+    e1 = srv._plan_for(_req(1, 8), "s1")
+    e1["last"] = 1.0
+    e2 = srv._plan_for(_req(2, 8, nb=5), "s2")
+    e2["last"] = 2.0
+    e3 = srv._plan_for(_req(3, 8, nb=6), "s3")
+    e3["last"] = 3.0
+    assert srv.plan_creations == 3 and srv.held == 3 * (8000 + f8)
+    # the same key reuses its idle plan on the new stream
+    again = srv._plan_for(_req(4, 8), "s4")
+    assert again is e1 and e1["plan"].stream == "s4" and srv.plan_creations == 3
+    # a fourth key: the least recently used idle plan (e1) is evicted
+    e4 = srv._plan_for(_req(5, 8, nb=7), "s5")
+    assert e4 is not None and FakePlan.closed == [8] and srv.held == 3 * (8000 + f8)
+    assert srv.plans[(8, 100.0, tuple(float(v) for v in range(5)), "bf16x3")] == []
+
+
+def test_busy_plans_are_never_evicted(monkeypatch):
+    f8 = 2 * 8 ** 3 * 4
+    srv = _server(2 * (8000 + f8), monkeypatch)
+    a = srv._plan_for(_req(1, 8), "s1")
+    b = srv._plan_for(_req(2, 8, nb=5), "s2")
+    a["busy"] = b["busy"] = True
+    assert srv._plan_for(_req(3, 8, nb=6), "s3") is None  # nothing idle to free
+    assert FakePlan.closed == [] and srv.held == 2 * (8000 + f8)
+    b["busy"] = False
+    assert srv._plan_for(_req(4, 8, nb=6), "s4") is not None and FakePlan.closed == [8]
