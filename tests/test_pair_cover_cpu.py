@@ -65,12 +65,28 @@ def _run(exe, text):
     return r.stdout.split()
 
 
+def _shell_sizes(thr):
+    """|S_b| for thresholds below (N/2)^2: for every (x, y) count the integers
+    z with thr[b] <= x^2 + y^2 + z^2 < thr[b+1] (O(R^2), no N^3 arrays)."""
+    top = int(thr[-1])
+    R = int(np.ceil(np.sqrt(top)))
+    r2 = (np.arange(-R, R + 1)[:, None] ** 2 + np.arange(-R, R + 1)[None, :] ** 2).ravel()
+
+    def below(t):  # number of (x, y, z) with x^2 + y^2 + z^2 < t
+        rem = t - r2
+        ok = rem > 0
+        zmax = np.floor(np.sqrt(np.maximum(rem - 1, 0))).astype(np.int64)  # z^2 <= rem - 1
+        return int(np.sum(np.where(ok, 2 * zmax + 1, 0)))
+    c = [below(int(t)) for t in thr]
+    return np.diff(c)
+
+
 def _interval_sets(N, L, nb):
     e = fields.log_edges(N, L, nb)
     thr = oracle.thresholds(e, L)
     lo = np.sqrt(thr[:-1].astype(float))
     hi = np.sqrt(np.maximum(thr[1:].astype(float) - 1, 0))
-    sizes = oracle.shell_sizes(N, thr)
+    sizes = _shell_sizes(thr)
     ok = [b for b in range(nb) if sizes[b] > 0]
     trips = [t for t in itertools.combinations_with_replacement(ok, 3) if hi[t[0]] + hi[t[1]] >= lo[t[2]]]
     quads = [q for q in itertools.combinations_with_replacement(ok, 4)
