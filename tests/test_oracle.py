@@ -423,3 +423,75 @@ def test_products_sum_on_reduced_grid(order, M):
         assert abs(scale * pr.sum() - ref) <= 1e-12 * mag, combo
         worst_alias = max(worst_alias, abs((N / (order * R)) ** 3 * pa.sum() - ref) / mag)
     assert worst_alias > 1e-6  # one grid point too few aliases some product
+
+
+# ---------------------------------------------------------------- triplet subsets
+# The full-size GPU tests take their closed-triplet set from
+# oracle.closed_triplets (a pruned witness search) and their reference sums
+# from oracle.direct_triplets (per-triplet loops over S_a x S_b).  Both are
+# pinned here to the all-pairs definition (direct_sums) on grids small enough
+# for it: linear bins, log bins with empty shells, and plans whose top edge
+# passes N k_f/4 so that closure modulo N differs from exact closure.
+def _subset_case(kind, N, L, nb):
+    kf = 2 * math.pi / L
+    if kind == "lin":
+        return fields.linear_edges(N, L, nb)
+    if kind == "log":
+        return fields.log_edges(N, L, nb)
+    if kind == "aliased":  # up to 0.45 N k_f: wrapped sums close modulo N
+        return np.linspace(kf, 0.45 * N * kf, nb + 1)
+    return _full_cover_edges(N, L)
+
+
+SUBSET_CASES = [("lin", 12, 50.0, 5, 1), ("log", 16, 60.0, 12, 2), ("log", 20, 30.0, 9, 3),
+                ("aliased", 10, 20.0, 4, 4), ("aliased", 12, 7.0, 6, 5), ("full", 8, 10.0, None, 6)]
+
+
+@pytest.mark.parametrize("kind,N,L,nb,seed", SUBSET_CASES)
+def test_closed_triplets_equals_all_pairs_counts(kind, N, L, nb, seed):
+    edges = _subset_case(kind, N, L, nb)
+    thr = oracle.thresholds(edges, L)
+    S = oracle.shell_sizes(N, thr)
+    if kind == "log":
+        assert np.any(S == 0)  # the pin must cover empty shells
+    f = fields.lognormal(N, 0.6, -1.5, seed=seed)
+    _, _, cnt, _ = oracle.direct_sums(f, thr)
+    k = len(thr) - 1
+    expect = [(a, b, c) for a in range(k) for b in range(a, k) for c in range(b, k) if cnt[a, b, c] > 0]
+    got = [tuple(int(v) for v in t) for t in oracle.closed_triplets(N, L, edges)]
+    assert len(expect) > 0
+    assert got == expect
+
+
+@pytest.mark.parametrize("kind,N,L,nb,seed", SUBSET_CASES)
+def test_direct_triplets_equals_all_pairs_sums(kind, N, L, nb, seed):
+    edges = _subset_case(kind, N, L, nb)
+    thr = oracle.thresholds(edges, L)
+    f = fields.bubbles(N, 2.0, 0.4, seed=seed) if seed % 2 else fields.lognormal(N, 0.8, -1.0, seed=seed)
+    num, numi, cnt, _ = oracle.direct_sums(f, thr)
+    k = len(thr) - 1
+    S = oracle.shell_sizes(N, thr)
+    # every sorted triple of non-empty bins (closed or not), plus every
+    # ordering of a few of them (the ordered sum is over m1 in S_a, m2 in S_b)
+    trip = [(a, b, c) for a in range(k) for b in range(a, k) for c in range(b, k) if S[a] and S[b] and S[c]]
+    extra = [p for t in trip[:: max(1, len(trip) // 6)] for p in set(itertools.permutations(t))]
+    allt = np.array(trip + extra, dtype=np.int32)
+    B, n, ni, c = oracle.direct_triplets(f, L, edges, allt)
+    ref_n = np.array([num[a, b, cc] for a, b, cc in allt])
+    ref_i = np.array([numi[a, b, cc] for a, b, cc in allt])
+    ref_c = np.array([cnt[a, b, cc] for a, b, cc in allt])
+    assert np.array_equal(c, ref_c)
+    assert ref_c.sum() > 0
+    scale = np.max(np.abs(ref_n))
+    assert np.max(np.abs(n - ref_n)) <= 1e-12 * scale
+    assert np.max(np.abs(ni - ref_i)) <= 1e-12 * scale
+    V, npix = L ** 3, float(N ** 3)
+    closed = ref_c > 0
+    assert np.allclose(B[closed], (V * V / npix ** 3) * ref_n[closed] / ref_c[closed], rtol=1e-12,
+                       atol=1e-12 * np.max(np.abs(B)))
+
+
+def test_count_modes_equals_shell_sizes():
+    for N, L, nb in [(12, 50.0, 5), (16, 30.0, 9)]:
+        thr = oracle.thresholds(fields.log_edges(N, L, nb), L)
+        assert oracle.count_modes(N, thr) == int(oracle.shell_sizes(N, thr).sum())
