@@ -541,11 +541,11 @@ def _closed_triplets_oracle(N, thr):
 # launch by its points.  Source: the profile summary named beside the value.
 NCU_TRAFFIC_RATIO = {
     "contract_tc": ((916.344576e6 + 3.036160e6) / (64 * 3538944 * 4.0),
-                    "ncu: bispectrum pass, 256^3, 64 log bins, 3.54M points "
-                    "(profiles/contract_tc_quadratic256_B64log_T16log_traffic.md), scaled by points"),
+                    "ncu DRAM bytes of the bispectrum pass at 256^3, 64 log bins, 3.54M points "
+                    "(the contraction traffic capture), scaled by points"),
     "contract_quad_tc": ((540.110080e6 + 0.122624e6) / (16 * 8388608 * 4.0),
-                         "ncu: fused triplet+quadruplet pass, 256^3, 16 log bins, 8.39M points "
-                         "(profiles/contract_tc_quadratic256_B64log_T16log_traffic.md), scaled by points"),
+                         "ncu DRAM bytes of the fused triplet+quadruplet pass at 256^3, 16 log bins, "
+                         "8.39M points (the contraction traffic capture), scaled by points"),
 }
 
 

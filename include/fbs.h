@@ -154,12 +154,22 @@ enum {
                             in tensor memory (and 16 product warps are in
                             use), else 64; 1: always 64.  Sums agree within
                             rounding (the CTAs' point ranges differ). */
-    FBS_OPT_TC_PAIRS = 4  /* outer rows of the bispectrum's tensor-core
+    FBS_OPT_TC_PAIRS = 4, /* outer rows of the bispectrum's tensor-core
                             contraction: 0 (default): each triplet is carried
                             by one of its three pairs, chosen by a greedy set
                             cover (fewer 128-row tiles); 1: by its pair of
                             the two largest bins (b, c).  Sums agree within
                             rounding. */
+    FBS_OPT_TC_WAIT_LIMIT = 5 /* clock cycles a warp role of the tensor-core
+                            contraction waits for a hand-off from another role
+                            before it gives up (0, the default: 2e9 cycles,
+                            about one second).  A wait that gives up makes the
+                            whole CTA stop issuing work, finish what is in
+                            flight (those drain waits keep the default limit),
+                            free its tensor memory and return; the evaluation's
+                            B and T are then NaN and FBS_ERR_TIMEOUT is
+                            reported (see fbs_plan_check).  Meant for testing
+                            that path; any value >= 0 is accepted. */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */
@@ -200,6 +210,32 @@ fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double
  * arrays (any may be NULL); synchronises the stream.
  */
 fbs_status fbs_plan_sums(fbs_plan *plan, double *num_trip, double *num_quad, double *sumsq);
+
+/*
+ * fbs_plan_check -- wait for the plan's stream and report whether an
+ * evaluation since the last report gave up a tensor-core wait
+ * (FBS_ERR_TIMEOUT; the outputs of that evaluation are NaN).  The report is
+ * given once and then cleared.  Asynchronous callers (device or pinned
+ * outputs) learn of a timeout here, from fbs_plan_sums, or from a later
+ * fbs_bispectrum / fbs_trispectrum: an estimator call first checks, without
+ * waiting, whether an earlier evaluation on the plan is already known to have
+ * timed out, and if so returns FBS_ERR_TIMEOUT without enqueuing anything
+ * (the check is skipped while the plan's stream is being captured).
+ * Calls with pageable host outputs wait for their results and report a
+ * timeout directly.
+ */
+fbs_status fbs_plan_check(fbs_plan *plan);
+
+/*
+ * fbs_set_device_budget -- process-wide cap (bytes) on the device memory all
+ * plans together may hold, plan-time scratch included (0, the default: no
+ * cap).  An allocation that would pass the cap fails as a failed cudaMalloc
+ * does: the call returns FBS_ERR_OOM and a failed fbs_plan_create leaves no
+ * plan and no memory behind.  Existing plans are not affected by lowering it.
+ * fbs_device_bytes_in_use -- bytes the library's plans hold now.
+ */
+fbs_status fbs_set_device_budget(int64_t bytes);
+int64_t fbs_device_bytes_in_use(void);
 
 /*
  * fbs_plan_kernel_times -- with FBS_FLAG_TIMING, the CUDA-event time (ms) and
@@ -258,7 +294,10 @@ int64_t fbs_plan_device_bytes(const fbs_plan *plan);
  *   cuda_stream: stream of both launches (NULL = legacy default stream).
  * Asynchronous on the stream.  The first call on a device looks up the
  * scratch array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
+ * current; make that first call before any stream capture.  The address is
+ * kept for the life of the process: do not use this entry point after a
+ * cudaDeviceReset (or another teardown of the device's primary context) in
+ * the same process, because the array may then sit elsewhere.  All calls share
  * the one scratch array, which keeps the last call's partials: calls that
  * overlap on the GPU (different streams, different host threads) race, so
  * serialise them.  Returns FBS_OK, FBS_ERR_ARG or FBS_ERR_CUDA.

@@ -20,7 +20,7 @@ Substituting the DFT form of the Kronecker delta (Sec. 2, the identity that
 turns Eq. gen_Nspec3 into Eq. gen_Nspec4) shows the two are equal up to
 rounding; the pins in ``tests/test_oracle.py`` check that and more.
 
-Readings of the paper (each is listed with its reason in the design notes):
+Readings of the paper this oracle takes where the text is silent or garbled:
 
 * Normalisation: B = V^2/N_pix^3 * num/(N_pix N_tri) as in Eq. Jeong_BI
   (Eq. bi_direct's 1/(2 pi)^3 is the continuum form; the discrete derivation

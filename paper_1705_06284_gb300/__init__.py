@@ -40,6 +40,7 @@ FBS_OPT_TC_WIDE = 1
 FBS_OPT_TC_ROLES = 2
 FBS_OPT_TC_CHUNK = 3
 FBS_OPT_TC_PAIRS = 4
+FBS_OPT_TC_WAIT_LIMIT = 5
 
 _PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
 
@@ -83,6 +84,9 @@ _SIGS = [
     ("fbs_plan_eval_grid", ctypes.c_int, [_vp]),
     ("fbs_plan_slab_planes", ctypes.c_int, [_vp]),
     ("fbs_plan_num_slabs", ctypes.c_int, [_vp]),
+    ("fbs_plan_check", ctypes.c_int, [_vp]),
+    ("fbs_set_device_budget", ctypes.c_int, [ctypes.c_int64]),
+    ("fbs_device_bytes_in_use", ctypes.c_int64, []),
     ("fbs_triple_sums_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                                 _vp, ctypes.c_int, _vp, _vp]),
     ("fbs_last_error", ctypes.c_char_p, []),
@@ -138,6 +142,21 @@ def fbs_bispectrum(h, field_ptr, B_ptr, P_ptr):
 def fbs_trispectrum(h, field_ptr, T_ptr, B_ptr, P_ptr):
     _check(lib().fbs_trispectrum(_vp(h), _vp(field_ptr), _vp(T_ptr or 0), _vp(B_ptr or 0),
                                  _vp(P_ptr or 0)))
+
+
+def fbs_plan_check(h):
+    """Wait for the plan's stream; raise FbsError(FBS_ERR_TIMEOUT) if an
+    evaluation since the last report gave up a tensor-core wait."""
+    _check(lib().fbs_plan_check(_vp(h)))
+
+
+def fbs_set_device_budget(nbytes):
+    """Process-wide cap on the device bytes all plans may hold (0: none)."""
+    _check(lib().fbs_set_device_budget(int(nbytes)))
+
+
+def fbs_device_bytes_in_use():
+    return int(lib().fbs_device_bytes_in_use())
 
 
 def fbs_triple_sums_noalloc(fields_ptr, nfields, bin_stride, npts, abc_ptr, ntrip, num_ptr, stream=None):
@@ -280,6 +299,10 @@ class Plan:
             import torch
             if f.dtype != torch.float32 or not f.is_contiguous():
                 raise ValueError("field must be a contiguous float32 tensor")
+
+    def check(self):
+        """Wait for the plan's stream; raise on a timed-out evaluation."""
+        fbs_plan_check(self._h)
 
     def sums(self):
         """Raw FP64 sums of the last call: (num_trip, num_quad, sumsq)."""

@@ -21,8 +21,24 @@ from . import Plan
 _TUNE_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
+_BUILD_ID = None
+
+
+def _build_id():
+    """Library build (hash of libfbs.so) and device name: a choice timed on
+    another build or another GPU model is not reused."""
+    global _BUILD_ID
+    if _BUILD_ID is None:
+        import hashlib
+        import torch
+        from ._build import LIB
+        h = hashlib.sha1(open(LIB, "rb").read()).hexdigest()[:16]
+        _BUILD_ID = "%s|%s" % (h, torch.cuda.get_device_name())
+    return _BUILD_ID
+
+
 def _key(N, L, edges, precision):
-    return "%d|%r|%s|%s" % (N, float(L), ",".join("%.12g" % e for e in edges), precision)
+    return "%d|%r|%s|%s|%s" % (N, float(L), ",".join("%.12g" % e for e in edges), precision, _build_id())
 
 
 def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> Dict[str, float]:

@@ -161,7 +161,7 @@ __global__ void normalise_kernel(const double *__restrict__ tnum, const int64_t 
                                  const double *__restrict__ sumsq, const long long *__restrict__ shell,
                                  int nbins, double L, int N, double *__restrict__ B,
                                  double *__restrict__ P, double *__restrict__ T,
-                                 const int *__restrict__ err) {
+                                 const int *__restrict__ err, int *__restrict__ sticky) {
     const double V = L * L * L;
     const double npix = (double)N * N * N;
     const double cB = V * V / (npix * npix * npix);
@@ -169,9 +169,10 @@ __global__ void normalise_kernel(const double *__restrict__ tnum, const int64_t 
     const double cT = V * V * V / (npix * npix * npix * npix);
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool bad = err && *err;  // a tensor-core wait gave up: the sums are incomplete
+    if (bad && sticky && i == 0) *sticky = *err;  // kept until the host reports it
     if (B && i < ntrip) B[i] = bad ? nan("") : cB * tnum[i] / (npix * (double)ntri[i]);
     if (P && i < nbins) P[i] = shell[i] > 0 ? cP * sumsq[i] / (npix * (double)shell[i]) : nan("");
-    if (T && i < nquad) T[i] = cT * qnum[i] / (npix * nq[i]);
+    if (T && i < nquad) T[i] = bad ? nan("") : cT * qnum[i] / (npix * nq[i]);
 }
 
 // ------------------------------------------------------------------ counts (FP64)
@@ -345,8 +346,14 @@ void launch_reduce_and_normalise(Plan &p, bool quads) {
         normalise_kernel<<<(n_all + 255) / 256, 256, 0, p.stream>>>(
             p.d_tnum, p.d_ntri, ntrip, p.d_qnum, p.d_nquad, nquad, p.d_sumsq, p.d_shell, p.nbins,
             p.L, p.N, p.d_B, p.d_P, quads ? p.d_T : nullptr,
-            p.precision != FBS_PREC_FP32 ? tc_error_flag(p) : nullptr);
+            p.precision != FBS_PREC_FP32 ? tc_error_flag(p) : nullptr,
+            p.precision != FBS_PREC_FP32 ? tc_sticky_flag(p) : nullptr);
         FBS_CUDA(cudaGetLastError());
+        if (p.precision != FBS_PREC_FP32 && tc_sticky_flag(p) && p.h_err) {
+            FBS_CUDA(cudaMemcpyAsync(p.h_err, tc_sticky_flag(p), sizeof(int), cudaMemcpyDeviceToHost, p.stream));
+            FBS_CUDA(cudaEventRecord(p.ev_err, p.stream));
+            p.err_recorded = true;
+        }
     }
 }
 
@@ -365,11 +372,8 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
     if (sm > 220 * 1024) throw Failure{FBS_ERR_ARG, "too many bins for the count kernel"};
     const int ngrp = (nitems + grp - 1) / grp;
     const int blocks = 2 * num_sms();
-    double *part = nullptr;
-    if (cudaMallocAsync((void **)&part, (size_t)blocks * nitems * sizeof(double), p.stream) != cudaSuccess) {
-        cudaGetLastError();
-        throw Failure{FBS_ERR_OOM, "count partials: device allocation failed"};
-    }
+    AsyncBuf pbuf((size_t)blocks * nitems * sizeof(double), p.stream, "count partials");
+    double *part = pbuf.as<double>();
     KTimer tm(p, KC_COUNT);
     FBS_CUDA(cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 g(blocks, ngrp);
@@ -377,7 +381,6 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
     FBS_CUDA(cudaGetLastError());
     reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, nitems, d_den, 1.0);
     FBS_CUDA(cudaGetLastError());
-    FBS_CUDA(cudaFreeAsync(part, p.stream));
 }
 
 }  // namespace fbs

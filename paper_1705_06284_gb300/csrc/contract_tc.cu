@@ -1,25 +1,33 @@
-// Triplet contraction on the 5th-generation tensor cores (tcgen05, sm_103a).
+// Triplet and quadruplet contractions on the 5th-generation tensor cores
+// (tcgen05, sm_103a).
 //
-// The real-space sums of Eq. Jeong_BI, num[a,b,c] = sum_x I_a I_b I_c, are
-// a matrix product D[(b,c)][a] = sum_x P_bc(x) I_a(x) with the pair products
-// P_bc = I_b I_c formed on the fly: M = outer pairs (tiles of 128), N = bins a,
-// K = points x.  Per K-chunk of 64 points:
-//   * the shell fields of all bins are staged in shared memory (cp.async,
-//     double-buffered);
-//   * CUDA cores split I_a into BF16 hi/lo (operand B) and form the pair
-//     products, also split into BF16 hi/lo (operand A), writing both in the
-//     128-byte-swizzled K-major layout the tensor core reads;
+// The real-space sums of Eq. Jeong_BI, num[a,b,c] = sum_x I_a I_b I_c, are a
+// matrix product D[(b,c)][n] = sum_x P_bc(x) R_n(x) with the outer pair
+// products P_bc = I_b I_c formed on the fly (M = 128 outer pairs per tile),
+// inner rows R_n that are single bins (bispectrum) or pair products I_a I_b
+// (trispectrum, Eq. Jeong_gen with p = 4) on N, and K = points x.  Per
+// pipeline step of 64 or 128 points:
+//   * one loader thread streams every bin's shell field of the step into a
+//     ring of shared-memory stages with 2-D TMA loads (128-byte swizzle);
+//   * producer warps split the inner rows into BF16 hi/lo (operand B, 128-byte
+//     swizzled K-major tiles in shared memory) and form the outer pair products
+//     of their tensor-memory lane, split them into BF16 hi/lo and store them
+//     into tensor memory (operand A) with tcgen05.st;
 //   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) for
 //     hi*hi + hi*lo + lo*hi (BF16x3; hi*hi alone for plain BF16) into FP32
 //     accumulators in tensor memory, one 128 x Npad block per pair tile;
-//   * every few chunks the accumulators are read back (tcgen05.ld) and added
-//     into FP64 per-triplet sums in shared memory.
-// Each CTA owns a contiguous range of points; its FP64 sums are added to its
-// own row of the partial buffer and reduced across CTAs in a fixed order.
+//   * every 1,024 points the producers read the accumulators back
+//     (tcgen05.ld) into compensated (Kahan) FP32 sums per item in shared
+//     memory.
+// Each CTA owns a contiguous range of points; its sums go to its own row of
+// the FP64 partial buffer, reduced across CTAs in a fixed order.  Which of a
+// triplet's (or quadruplet's) pairs forms the outer row is chosen by a greedy
+// set cover (pair_cover.cpp) to keep the 128-row tiles few.
 //
-// Every wait on an mbarrier is bounded (about one second of clock cycles);
-// on timeout the kernel records an error flag, waits (bounded) for its own
-// MMAs, frees its tensor memory and returns.
+// Every wait on an mbarrier is bounded (about one second of clock cycles by
+// default, FBS_OPT_TC_WAIT_LIMIT for the hand-offs between roles); on
+// timeout the CTA records an error code, stops issuing loads and MMAs, waits
+// (bounded) for those in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -80,7 +88,7 @@ struct WideJob {
 struct TcState {
     TcJob trip, quad, fused;
     WideJob wtrip, wquad;
-    int *d_err = nullptr;
+    int *d_err = nullptr;     // [0]: this evaluation's wait-timeout code; [1]: sticky copy
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -228,13 +236,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
 
 // Bounded wait that gives up at once after any other wait of the CTA timed
 // out (the abort flag is sticky), so no role can strand another.
+// `limit` is the launch's hand-off wait limit in clock cycles (about one
+// second by default; a plan option shortens it to exercise this path).
 __device__ __forceinline__ bool role_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          int *err, int code) {
+                                          int *err, int code, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;  // ready: no clock read, no flag read
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             *abort_flag = 1;
             atomicExch(err, code);
             return false;
@@ -341,7 +351,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
-                       int *__restrict__ err) {
+                       int *__restrict__ err, long long wait_limit) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
     static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
@@ -438,7 +448,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             Ring<NSTG> rs;
             long long issued = 0;
             for (long long ci = c0; ci < c1; ++ci) {
-                if (rs.warm && !role_wait(&bars.sempty[rs.slot], rs.phase ^ 1u, abortp, err, 10)) break;
+                if (rs.warm && !role_wait(&bars.sempty[rs.slot], rs.phase ^ 1u, abortp, err, 10, wait_limit)) break;
+                // After an abort a producer warp may hand a stage back before its load
+                // landed (it set the flag before arriving, so the flag is visible
+                // here): never issue a second load into a slot, so every slot has
+                // at most one copy in flight and the drain below covers all of them.
+                if (*abortp) break;
                 const uint32_t dst = smem_u32(stg + rs.slot * stage_bytes);
                 const int x = (int)(ci * KCH);
                 mbar_expect_tx(&bars.sfull[rs.slot], bytes);
@@ -467,13 +482,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int since = 0;
             for (long long ci = c0; ci < c1; ++ci) {
                 const int sb = rb.slot;
-                const bool okb = role_wait(&bars.bfull[sb], rb.phase, abortp, err, 11);
+                const bool okb = role_wait(&bars.bfull[sb], rb.phase, abortp, err, 11, wait_limit);
                 const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + sb * b_stage));
                 const uint64_t dbl = sdesc_sw128(smem_u32(Bl0 + sb * b_stage));
                 const uint64_t datom = (uint64_t)((unsigned)b_tile >> 4);  // next K-atom's tile
                 for (int lt = 0; lt < ntl; ++lt) {
                     const int as = ra.slot;
-                    const bool oka = role_wait(&bars.full[as], ra.phase, abortp, err, 12);
+                    const bool oka = role_wait(&bars.full[as], ra.phase, abortp, err, 12, wait_limit);
                     tc_fence_after();
                     if (okb && oka) {  // a failed wait leaves ok false (the abort flag is sticky)
                         const uint32_t d = tmem + (uint32_t)(lt * tstride);
@@ -507,7 +522,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 fresh = false;
                 if (++since == flush_every || ci == c1 - 1) {
                     mma_commit(&bars.accr);
-                    role_wait(&bars.accf, (uint32_t)(nfl & 1), abortp, err, 13);
+                    role_wait(&bars.accf, (uint32_t)(nfl & 1), abortp, err, 13, wait_limit);
                     tc_fence_after();
                     ++nfl;
                     fresh = true;
@@ -523,10 +538,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         Ring<NSTG> rs;
         Ring<2> rb;
         for (long long ci = c0; ci < c1; ++ci) {
-            role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 24);
+            role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 24, wait_limit);
             const unsigned char *st = stg + rs.slot * stage_bytes;
             const int sb = rb.slot;
-            if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 25);
+            if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 25, wait_limit);
             for (int u = btid; u < ninner * 8 * KA; u += BW * 32)
                 build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_stage, Bl0 + sb * b_stage, b_tile);
             fence_proxy_async_smem();
@@ -548,12 +563,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         long long nfl = 0;
         int since = 0;
         for (long long ci = c0; ci < c1; ++ci) {
-            role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 20);
+            role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 20, wait_limit);
             const unsigned char *st = stg + rs.slot * stage_bytes;
             if constexpr (BW == 0) {
                 // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
                 const int sb = rb.slot;
-                if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21);
+                if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21, wait_limit);
                 for (int u = ptid; u < ninner * 8 * KA; u += AW * 32)
                     build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_stage, Bl0 + sb * b_stage,
                                  b_tile);
@@ -565,7 +580,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             // ---- operand A: pair products of this thread's row, PPT points, into TMEM
             for (int lt = 0; lt < ntl; ++lt) {
                 const int as = ra.slot;
-                if (ra.warm) role_wait(&bars.empty[as], ra.phase ^ 1u, abortp, err, 22);
+                if (ra.warm) role_wait(&bars.empty[as], ra.phase ^ 1u, abortp, err, 22, wait_limit);
                 tc_fence_after();
                 const int2 bc = pbc[lt * 128 + r];
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
@@ -608,7 +623,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             rs.next();
             // ---- flush: accumulators -> compensated FP32 sums
             if (++since == flush_every || ci == c1 - 1) {
-                role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 23);
+                role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 23, wait_limit);
                 tc_fence_after();
                 if (!*abortp) {
                     for (int lt = 0; lt < ntl; ++lt) {
@@ -684,7 +699,8 @@ __global__ void __launch_bounds__(kWideThreads, 1)
     contract_wide_kernel(const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
                          int nleft, const int2 *__restrict__ left, const WideRight *__restrict__ rights,
                          int nright, const int *__restrict__ item_out, int nitems_total,
-                         double *__restrict__ part, int x4, int flush_every, int *__restrict__ err) {
+                         double *__restrict__ part, int x4, int flush_every, int *__restrict__ err,
+                         long long wait_limit) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ WideBars bars;
     __shared__ uint32_t tmem_slot;
@@ -750,7 +766,7 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             int since = 0;
             for (long long ci = c0; ci < c1; ++ci) {
                 const int s = (int)(g & 1);
-                const bool ok = role_wait(&bars.full[s], (uint32_t)((g >> 1) & 1), abortp, err, 31);
+                const bool ok = role_wait(&bars.full[s], (uint32_t)((g >> 1) & 1), abortp, err, 31, wait_limit);
                 tc_fence_after();
                 if (ok && !*abortp) {
                     const uint32_t a = tmem + (uint32_t)(kWideAcol + 32 * s);
@@ -770,7 +786,7 @@ __global__ void __launch_bounds__(kWideThreads, 1)
                 fresh = false;
                 if (++since == flush_every || ci == c1 - 1) {
                     mma_commit(&bars.accr);
-                    role_wait(&bars.accf, (uint32_t)(nfl & 1), abortp, err, 32);
+                    role_wait(&bars.accf, (uint32_t)(nfl & 1), abortp, err, 32, wait_limit);
                     tc_fence_after();
                     ++nfl;
                     fresh = true;
@@ -811,7 +827,7 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             asm volatile("bar.sync 1, %0;" ::"n"(NP) : "memory");
             if (ci + 1 < c1) prefetch(ci + 1, s ^ 1);
             const float *st = stage + s * stage_floats;
-            if (g >= 2) role_wait(&bars.empty[s], (uint32_t)(((g - 2) >> 1) & 1), abortp, err, 41);
+            if (g >= 2) role_wait(&bars.empty[s], (uint32_t)(((g - 2) >> 1) & 1), abortp, err, 41, wait_limit);
             tc_fence_after();
             // ---- operand A: left row li, points 16kq .. 16kq+15, hi (rows 0..63) or lo (64..127)
             {
@@ -867,7 +883,7 @@ __global__ void __launch_bounds__(kWideThreads, 1)
             ++g;
             // ---- flush: D -> FP32 shared sums of (item, half)
             if (++since == flush_every || ci == c1 - 1) {
-                role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 42);
+                role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 42, wait_limit);
                 tc_fence_after();
                 if (!*abortp) {
                     const unsigned long long lbit = 1ULL << li;
@@ -923,12 +939,15 @@ static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl, int nstg, in
 
 static int tile_stride(int Npad) { return ((Npad + 31) / 32) * 32; }
 
+// Hand-off wait limit of the plan's launches (FBS_OPT_TC_WAIT_LIMIT; 0 = the default).
+static long long tc_wait_limit(const Plan &p) { return p.tc_wait_limit > 0 ? p.tc_wait_limit : kWaitCycles; }
+
 static TcState &tc_state(Plan &p) {
     if (!p.tc) {
         TcState *st = new TcState();
         p.tc = st;
-        st->d_err = (int *)p.dalloc(sizeof(int));
-        FBS_CUDA(cudaMemsetAsync(st->d_err, 0, sizeof(int), p.stream));
+        st->d_err = (int *)p.dalloc(2 * sizeof(int));
+        FBS_CUDA(cudaMemsetAsync(st->d_err, 0, 2 * sizeof(int), p.stream));
     }
     return *reinterpret_cast<TcState *>(p.tc);
 }
@@ -1257,12 +1276,13 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
     dim3 grid(G, ngrp);
     contract_wide_kernel<<<grid, kWideThreads, sm, p.stream>>>(
         islab, slab_stride, npts, p.nbins, w.nleft, w.d_left, w.d_rights, w.nright, w.d_item_out, t.nitems,
-        quads ? p.d_qpart : p.d_tpart, p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err);
+        quads ? p.d_qpart : p.d_tpart, p.precision == FBS_PREC_BF16 ? 0 : 1, 16, st.d_err, tc_wait_limit(p));
     FBS_CUDA(cudaGetLastError());
     return true;
 }
 
 int *tc_error_flag(Plan &p) { return p.tc ? reinterpret_cast<TcState *>(p.tc)->d_err : nullptr; }
+int *tc_sticky_flag(Plan &p) { return p.tc ? reinterpret_cast<TcState *>(p.tc)->d_err + 1 : nullptr; }
 
 bool tc_quads_usable(Plan &p) {
     TcState &st = tc_state(p);
@@ -1344,7 +1364,8 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));          \
         contract_tc_kernel<A, S, W, K><<<grid, kTcThreads, sm, p.stream>>>(                          \
             fmap, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner, job.d_pairs, \
-            job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err);        \
+            job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err,         \
+            tc_wait_limit(p));                                                                        \
     }
     bool launched = false;
     FBS_TC_LAUNCH(2, 2, 16, 1)

@@ -124,6 +124,7 @@ struct Plan {
     int tc_roles = 0;            // FBS_OPT_TC_ROLES: 0 auto, 1 = 16 A warps, 2 = 8 A + 8 B warps
     int tc_chunk = 0;            // FBS_OPT_TC_CHUNK: 0 auto, 1 = 64-point chunks, 2 = 128 where they fit
     int tc_pairs = 0;            // FBS_OPT_TC_PAIRS: 0 greedy pair cover, 1 = pairs (b, c)
+    long long tc_wait_limit = 0; // FBS_OPT_TC_WAIT_LIMIT: hand-off wait limit in cycles (0 = default)
     cudaStream_t stream = nullptr;
     double create_ms = 0;
     double count_margin = 0;  // largest |sum N..N / N_pix - nearest integer| of the rounded counts
@@ -155,6 +156,12 @@ struct Plan {
     // device memory
     std::vector<void *> allocs;
     long long dev_bytes = 0;
+    // timeout reporting: the normalisation copies the device's sticky flag
+    // into h_err (pinned) at the end of every tensor-core evaluation and
+    // records ev_err, so later calls can see a timeout without waiting
+    int *h_err = nullptr;
+    cudaEvent_t ev_err = nullptr;
+    bool err_recorded = false;
     float *d_field = nullptr;    // staging for host fields
     cudaStream_t copy_stream = nullptr;   // host-field copies (overlap work queued on `stream`)
     cudaEvent_t ev_field_ready = nullptr; // staged copy landed (the plan's stream waits on it)
@@ -211,6 +218,26 @@ struct KTimer {
 };
 
 void free_tc_state(Plan &p);
-int *tc_error_flag(Plan &p);  // device flag set by a timed-out tensor-core wait (or nullptr)
+int *tc_error_flag(Plan &p);   // device flag set by a timed-out tensor-core wait (or nullptr)
+int *tc_sticky_flag(Plan &p);  // device copy of that flag kept until reported (or nullptr)
+
+// Process-wide device-memory budget of all plans (fbs_set_device_budget):
+// reserve before an allocation (throws FBS_ERR_OOM past the budget), release
+// after a free.
+void budget_reserve(long long bytes);
+void budget_release(long long bytes);
+
+// Transient stream-ordered device buffer counted against the budget; freed
+// (on the stream) when it goes out of scope.
+struct AsyncBuf {
+    void *ptr = nullptr;
+    long long bytes = 0;
+    cudaStream_t stream = nullptr;
+    AsyncBuf(size_t n, cudaStream_t s, const char *what);
+    ~AsyncBuf();
+    AsyncBuf(const AsyncBuf &) = delete;
+    AsyncBuf &operator=(const AsyncBuf &) = delete;
+    template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
+};
 
 }  // namespace fbs

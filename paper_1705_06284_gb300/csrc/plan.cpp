@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <string>
 #include <vector>
@@ -53,12 +54,50 @@ FftFactors make_factors(int n) {
     return f;
 }
 
+// ---------------------------------------------------------------- device budget
+static std::atomic<long long> g_budget{0};   // 0: no budget
+static std::atomic<long long> g_in_use{0};   // bytes held by all plans (and their transient buffers)
+
+void budget_reserve(long long bytes) {
+    const long long prev = g_in_use.fetch_add(bytes);
+    const long long cap = g_budget.load();
+    if (cap > 0 && prev + bytes > cap) {
+        g_in_use.fetch_sub(bytes);
+        throw Failure{FBS_ERR_OOM, "device budget: " + std::to_string(prev) + " + " + std::to_string(bytes) +
+                                       " bytes exceeds " + std::to_string(cap)};
+    }
+}
+
+void budget_release(long long bytes) { g_in_use.fetch_sub(bytes); }
+
+AsyncBuf::AsyncBuf(size_t n, cudaStream_t s, const char *what) : stream(s) {
+    if (n == 0) n = 16;
+    budget_reserve((long long)n);
+    if (cudaMallocAsync(&ptr, n, s) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+        budget_release((long long)n);
+        throw Failure{FBS_ERR_OOM, std::string(what) + ": device allocation failed"};
+    }
+    bytes = (long long)n;
+}
+
+AsyncBuf::~AsyncBuf() {
+    if (ptr) {
+        cudaFreeAsync(ptr, stream);
+        cudaGetLastError();
+        budget_release(bytes);
+    }
+}
+
 void *Plan::dalloc(size_t bytes) {
     void *ptr = nullptr;
     if (bytes == 0) bytes = 16;
+    budget_reserve((long long)bytes);
     cudaError_t e = cudaMalloc(&ptr, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        budget_release((long long)bytes);
         throw Failure{e == cudaErrorMemoryAllocation ? FBS_ERR_OOM : FBS_ERR_CUDA,
                       "cudaMalloc(" + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e)};
     }
@@ -283,11 +322,8 @@ static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<
     const int N = p.M, H = N / 2 + 1;  // the evaluation grid (exact for these products)
     const long long H3 = (long long)H * H * H;
     const int nb = p.nbins;
-    double *noct = nullptr;
-    if (cudaMallocAsync((void **)&noct, (size_t)nb * H3 * sizeof(double), p.stream) != cudaSuccess) {
-        cudaGetLastError();
-        throw Failure{FBS_ERR_OOM, "count fields: device allocation failed"};
-    }
+    AsyncBuf noct_buf((size_t)nb * H3 * sizeof(double), p.stream, "count fields");
+    double *noct = noct_buf.as<double>();
     // bin groups bounded by ~2 GB of FP64 scratch
     const long long budget = 2LL << 30;
     int b0 = 0;
@@ -308,20 +344,15 @@ static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<
             g_el += dg;
             ++b1;
         }
-        double2 *A64 = nullptr, *G64 = nullptr;
-        BinGeom *dgeom = nullptr;
-        if (cudaMallocAsync((void **)&A64, std::max<long long>(1, a_el) * 16, p.stream) != cudaSuccess ||
-            cudaMallocAsync((void **)&G64, std::max<long long>(1, g_el) * 16, p.stream) != cudaSuccess ||
-            cudaMallocAsync((void **)&dgeom, gg.size() * sizeof(BinGeom), p.stream) != cudaSuccess) {
-            cudaGetLastError();
-            throw Failure{FBS_ERR_OOM, "count scratch: device allocation failed"};
+        {
+            AsyncBuf A64(std::max<long long>(1, a_el) * 16, p.stream, "count scratch");
+            AsyncBuf G64(std::max<long long>(1, g_el) * 16, p.stream, "count scratch");
+            AsyncBuf dgeom(gg.size() * sizeof(BinGeom), p.stream, "count scratch");
+            FBS_CUDA(cudaMemcpyAsync(dgeom.ptr, gg.data(), gg.size() * sizeof(BinGeom), cudaMemcpyHostToDevice,
+                                     p.stream));
+            launch_count_fields_fp64_impl(p, noct + (long long)b0 * H3, b0, b1 - b0, A64.as<double2>(),
+                                          G64.as<double2>(), dgeom.as<BinGeom>());
         }
-        FBS_CUDA(cudaMemcpyAsync(dgeom, gg.data(), gg.size() * sizeof(BinGeom), cudaMemcpyHostToDevice,
-                                 p.stream));
-        launch_count_fields_fp64_impl(p, noct + (long long)b0 * H3, b0, b1 - b0, A64, G64, dgeom);
-        FBS_CUDA(cudaFreeAsync(A64, p.stream));
-        FBS_CUDA(cudaFreeAsync(G64, p.stream));
-        FBS_CUDA(cudaFreeAsync(dgeom, p.stream));
         FBS_CUDA(cudaStreamSynchronize(p.stream));  // gg goes out of scope
         b0 = b1;
     }
@@ -329,24 +360,16 @@ static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<
         int n = (int)(items.size() / arity);
         den.assign(n, 0.0);
         if (n == 0) return;
-        int *d_items = nullptr;
-        double *d_den = nullptr;
-        if (cudaMallocAsync((void **)&d_items, items.size() * sizeof(int), p.stream) != cudaSuccess ||
-            cudaMallocAsync((void **)&d_den, n * sizeof(double), p.stream) != cudaSuccess) {
-            cudaGetLastError();
-            throw Failure{FBS_ERR_OOM, "count items: device allocation failed"};
-        }
-        FBS_CUDA(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int),
+        AsyncBuf items_buf(items.size() * sizeof(int), p.stream, "count items");
+        AsyncBuf den_buf(n * sizeof(double), p.stream, "count items");
+        FBS_CUDA(cudaMemcpyAsync(items_buf.ptr, items.data(), items.size() * sizeof(int),
                                  cudaMemcpyHostToDevice, p.stream));
-        launch_count_contraction(p, noct, nb, 0, d_items, n, arity, d_den);
-        FBS_CUDA(cudaMemcpyAsync(den.data(), d_den, n * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+        launch_count_contraction(p, noct, nb, 0, items_buf.as<int>(), n, arity, den_buf.as<double>());
+        FBS_CUDA(cudaMemcpyAsync(den.data(), den_buf.ptr, n * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
         FBS_CUDA(cudaStreamSynchronize(p.stream));
-        FBS_CUDA(cudaFreeAsync(d_items, p.stream));
-        FBS_CUDA(cudaFreeAsync(d_den, p.stream));
     };
     run(tc, 3, tden);
     run(qc, 4, qden);
-    FBS_CUDA(cudaFreeAsync(noct, p.stream));
     FBS_CUDA(cudaStreamSynchronize(p.stream));
 }
 
@@ -524,6 +547,9 @@ static void create_plan(Plan &p, const double *edges) {
     FBS_CUDA(cudaStreamCreateWithFlags(&p.copy_stream, cudaStreamNonBlocking));
     FBS_CUDA(cudaEventCreateWithFlags(&p.ev_field_ready, cudaEventDisableTiming));
     FBS_CUDA(cudaEventCreateWithFlags(&p.ev_field_free, cudaEventDisableTiming));
+    FBS_CUDA(cudaEventCreateWithFlags(&p.ev_err, cudaEventDisableTiming));
+    FBS_CUDA(cudaHostAlloc((void **)&p.h_err, sizeof(int), cudaHostAllocDefault));
+    *p.h_err = 0;
     p.d_zbuf = (float2 *)p.dalloc((size_t)N * N * p.box.Dz * sizeof(float2));
     p.d_ybuf = (float2 *)p.dalloc((size_t)N * p.box.D * p.box.Dz * sizeof(float2));
     p.d_A = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.A_elems) * sizeof(float2));
@@ -617,13 +643,41 @@ static void run_field(Plan &p, const float *field, bool quads) {
 
 // A tensor-core wait that gave up leaves a flag on the device; the outputs
 // are NaN then (see the normalisation) and host-synchronising calls report it.
+// Report (once) a timeout of any evaluation since the last report: waits for
+// the plan's stream, reads the sticky flag and clears it.
 static void check_device_errors(Plan &p) {
-    int *f = tc_error_flag(p);
+    int *f = tc_sticky_flag(p);
     if (!f) return;
     int v = 0;
     FBS_CUDA(cudaMemcpyAsync(&v, f, sizeof(int), cudaMemcpyDeviceToHost, p.stream));
     FBS_CUDA(cudaStreamSynchronize(p.stream));
-    if (v) throw Failure{FBS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out (code " + std::to_string(v) + ")"};
+    if (v) {
+        FBS_CUDA(cudaMemsetAsync(f, 0, sizeof(int), p.stream));
+        FBS_CUDA(cudaStreamSynchronize(p.stream));
+        if (p.h_err) *p.h_err = 0;
+        throw Failure{FBS_ERR_TIMEOUT, "a tensor-core pipeline wait of an evaluation on this plan timed out "
+                                       "(code " + std::to_string(v) + "); its outputs are NaN"};
+    }
+}
+
+// Without waiting: if an earlier evaluation is already known to have timed
+// out (its status copy has landed in pinned host memory), report it now,
+// before this call enqueues anything.  Skipped while the stream is being
+// captured into a graph.
+static void poll_device_errors(Plan &p) {
+    if (!p.err_recorded || !p.h_err) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(p.stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return;
+    const cudaError_t q = cudaEventQuery(p.ev_err);
+    if (q != cudaSuccess) {
+        cudaGetLastError();  // cudaErrorNotReady: not known yet
+        return;
+    }
+    if (*(volatile int *)p.h_err) check_device_errors(p);
 }
 
 // Pageable host memory (not registered with CUDA): the copy cannot run
@@ -741,6 +795,9 @@ void fbs_plan_free(fbs_plan *plan) {
     cudaGetLastError();
     free_tc_state(*plan);
     for (void *ptr : plan->allocs) cudaFree(ptr);
+    budget_release(plan->dev_bytes);
+    if (plan->h_err) cudaFreeHost(plan->h_err);
+    if (plan->ev_err) cudaEventDestroy(plan->ev_err);
     for (cudaEvent_t e : plan->evs) cudaEventDestroy(e);
     if (plan->ev_field_ready) cudaEventDestroy(plan->ev_field_ready);
     if (plan->ev_field_free) cudaEventDestroy(plan->ev_field_free);
@@ -807,6 +864,10 @@ fbs_status fbs_plan_set_option(fbs_plan *plan, int option, int value) {
         plan->tc_pairs = value;
         return FBS_OK;
     }
+    if (option == FBS_OPT_TC_WAIT_LIMIT && value >= 0) {
+        plan->tc_wait_limit = value;
+        return FBS_OK;
+    }
     set_error("unknown option or value");
     return FBS_ERR_ARG;
 }
@@ -827,6 +888,7 @@ fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double 
         return FBS_ERR_ARG;
     }
     FBS_GUARD_BEGIN
+    poll_device_errors(*plan);
     run_field(*plan, field, false);
     bool host = false;
     copy_out(*plan, B, plan->d_B, plan->ntri.size(), host);
@@ -849,6 +911,7 @@ fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double
         return FBS_ERR_STATE;
     }
     FBS_GUARD_BEGIN
+    poll_device_errors(*plan);
     run_field(*plan, field, true);
     bool host = false;
     copy_out(*plan, T, plan->d_T, plan->nquad.size(), host);
@@ -879,6 +942,26 @@ fbs_status fbs_plan_sums(fbs_plan *plan, double *num_trip, double *num_quad, dou
     return FBS_OK;
     FBS_GUARD_END
 }
+
+fbs_status fbs_plan_check(fbs_plan *plan) {
+    if (!plan) return FBS_ERR_ARG;
+    FBS_GUARD_BEGIN
+    FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    check_device_errors(*plan);
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_set_device_budget(int64_t bytes) {
+    if (bytes < 0) {
+        set_error("budget must be >= 0");
+        return FBS_ERR_ARG;
+    }
+    g_budget.store(bytes);
+    return FBS_OK;
+}
+
+int64_t fbs_device_bytes_in_use(void) { return g_in_use.load(); }
 
 fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, int reset) {
     if (!plan) return FBS_ERR_ARG;

@@ -45,6 +45,7 @@ class Result:
     arrival: float
     admitted: float
     done: float
+    error: Optional[str] = None   # set when the request was refused or cancelled (no B, P)
 
     @property
     def latency(self) -> float:
@@ -84,6 +85,7 @@ class EstimatorServer:
         self.plans: Dict[tuple, List[dict]] = collections.defaultdict(list)
         self.held = 0
         self.plan_creations = 0
+        self._cancelled = set()
 
     # -- plan cache under the budget
     def _key(self, req: Request):
@@ -99,7 +101,11 @@ class EstimatorServer:
             self.held -= e["bytes"]
         return self.held + need <= self.budget
 
-    def _plan_for(self, req: Request, stream) -> Optional[dict]:
+    NEVER = "never"  # _plan_for: the request cannot fit even with every idle plan evicted
+
+    def _plan_for(self, req: Request, stream):
+        """An idle plan for the request (created if needed), None when it must
+        wait for busy work to finish, or NEVER when it can never fit."""
         key = self._key(req)
         for e in self.plans[key]:
             if not e["busy"]:
@@ -107,14 +113,25 @@ class EstimatorServer:
                 return e
         N = req.field.shape[0]
         need = plan_bytes_estimate(N, len(req.edges) - 1) + 2 * req.field.nbytes
+        if need > self.budget:
+            return self.NEVER
         if not self._evict_for(need):
-            return None
+            busy = any(e["busy"] for lst in self.plans.values() for e in lst)
+            return None if busy else self.NEVER
         plan = Plan(N, req.L, np.asarray(req.edges), precision=req.precision, stream=stream)
         self.plan_creations += 1
         e = {"plan": plan, "bytes": plan.device_bytes + 2 * req.field.nbytes, "busy": False,
              "last": time.perf_counter(), "dfield": None}
         self.held += e["bytes"]
         self.plans[key].append(e)
+        # the estimate admitted it; if the real plan is larger, make room or undo
+        if self.held > self.budget and not self._evict_for(0):
+            e["busy"] = True  # keep it out of its own eviction while we decide
+            busy = any(x["busy"] for lst in self.plans.values() for x in lst if x is not e)
+            plan.close()
+            self.plans[key].remove(e)
+            self.held -= e["bytes"]
+            return None if busy else self.NEVER
         return e
 
     # -- one request on one slot
@@ -141,18 +158,41 @@ class EstimatorServer:
             ev.record(slot.stream)
         slot.busy = (req, entry, ev, (B, P, Bh, Ph, host), time.perf_counter() - t0)
 
+    def cancel(self, rid: int):
+        """Cancel a request that has not been admitted yet (it returns a
+        Result with error "cancelled"); admitted requests run to the end."""
+        self._cancelled.add(rid)
+
+    def _refuse(self, req: Request, why: str, realtime: bool, t0: float) -> Result:
+        empty = np.zeros(0)
+        t = time.perf_counter() - t0
+        return Result(req.rid, np.zeros((0, 3), dtype=np.int32), np.zeros(0, dtype=np.int64), empty, empty,
+                      req.arrival if realtime else 0.0, t, t, error=why)
+
     def run(self, requests: Sequence[Request], realtime: bool = True) -> List[Result]:
         """Serve ``requests`` (sorted by arrival).  With ``realtime`` a request
         is not admitted before its arrival time; otherwise arrivals are
-        ignored (all requests are available at once)."""
+        ignored (all requests are available at once).  A request whose plan
+        and buffers cannot fit the budget even with every idle plan evicted
+        is refused (Result.error) instead of holding up the queue."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: collections.deque = collections.deque()
         results: List[Result] = []
         t0 = time.perf_counter()
+        if not hasattr(self, "_cancelled"):
+            self._cancelled = set()
         while pending or waiting or any(s.busy for s in self.slots):
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
+            if self._cancelled and waiting:
+                keep = collections.deque()
+                for r in waiting:
+                    if r.rid in self._cancelled:
+                        results.append(self._refuse(r, "cancelled", realtime, t0))
+                    else:
+                        keep.append(r)
+                waiting = keep
             # completions (non-blocking)
             for s in self.slots:
                 if s.busy and s.busy[2].query():
@@ -173,6 +213,11 @@ class EstimatorServer:
                     continue
                 req = waiting[0]
                 entry = self._plan_for(req, s.stream)
+                if entry is self.NEVER:
+                    waiting.popleft()
+                    results.append(self._refuse(req, "does not fit the HBM budget", realtime, t0))
+                    progressed = True
+                    continue
                 if entry is None:
                     break  # no memory until something finishes
                 waiting.popleft()

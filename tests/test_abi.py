@@ -76,3 +76,12 @@ def test_no_cpu_fallback_without_device(libfbs):
     with pytest.raises(fbs.FbsError) as e:
         fbs.fbs_plan_create(16, 100.0, [0.1, 0.5, 1.0])
     assert e.value.status == -4
+
+
+def test_device_budget_arguments(libfbs):
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.fbs_set_device_budget(-1)
+    assert e.value.status == -1
+    fbs.fbs_set_device_budget(0)
+    assert fbs.fbs_device_bytes_in_use() >= 0
+    assert libfbs.fbs_plan_check(None) == -1

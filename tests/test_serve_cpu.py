@@ -31,6 +31,7 @@ def _server(budget, monkeypatch):
     srv = serve.EstimatorServer.__new__(serve.EstimatorServer)
     srv.budget, srv.held, srv.plan_creations = budget, 0, 0
     srv.plans = collections.defaultdict(list)
+    srv.slots, srv._cancelled = [], set()
     FakePlan.closed = []
     return srv
 
@@ -68,3 +69,39 @@ def test_busy_plans_are_never_evicted(monkeypatch):
     assert FakePlan.closed == [] and srv.held == 2 * (8000 + f8)
     b["busy"] = False
     assert srv._plan_for(_req(4, 8, nb=6), "s4") is not None and FakePlan.closed == [8]
+
+
+def test_request_larger_than_the_budget_is_refused_not_stuck(monkeypatch):
+    f8 = 2 * 8 ** 3 * 4
+    srv = _server(8000 + f8, monkeypatch)
+    # needs 16000 + its field copies: more than the whole budget
+    assert srv._plan_for(_req(1, 16), "s1") is srv.NEVER
+    # fits the budget but not beside a busy plan: wait, do not refuse
+    a = srv._plan_for(_req(2, 8), "s2")
+    a["busy"] = True
+    assert srv._plan_for(_req(3, 8, nb=5), "s3") is None
+    a["busy"] = False
+    assert srv._plan_for(_req(4, 8, nb=5), "s4") is not None
+
+
+class _FakeSlot:
+    def __init__(self):
+        self.stream, self.busy = "s", None
+
+
+def test_run_refuses_oversize_and_cancelled_requests(monkeypatch):
+    f8 = 2 * 8 ** 3 * 4
+    srv = _server(8000 + f8, monkeypatch)
+    srv.slots = [_FakeSlot()]
+    served = []
+
+    def fake_submit(slot, req, entry, t0):  # completes at once, no GPU
+        served.append(req.rid)
+
+    monkeypatch.setattr(srv, "_submit", fake_submit)
+    srv.cancel(3)
+    res = srv.run([_req(1, 16), _req(2, 8), _req(3, 8, nb=5)], realtime=False)
+    errs = {r.rid: r.error for r in res}
+    assert errs[1] == "does not fit the HBM budget"
+    assert errs[3] == "cancelled"
+    assert served == [2]
