@@ -41,6 +41,17 @@ import threading
 
 import numpy as np
 
+try:  # the same library transforms, multithreaded, where scipy is present
+    import scipy.fft as _sfft
+
+    def _fftn(a):
+        return _sfft.fftn(a, workers=-1)
+
+    def _ifftn(a):
+        return _sfft.ifftn(a, workers=-1)
+except Exception:  # pragma: no cover
+    _fftn, _ifftn = np.fft.fftn, np.fft.ifftn
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
@@ -134,7 +145,7 @@ def thresholds(edges, L: float) -> np.ndarray:
 def spectrum(field: np.ndarray) -> np.ndarray:
     """Unnormalised forward DFT, D(m) = sum_n delta(n) e^{-2 pi i m.n/N}
     (Eq. DeltaFFTtoDelta), full complex box in FFT index order."""
-    return np.fft.fftn(np.asarray(field, dtype=np.float64))
+    return _fftn(np.asarray(field, dtype=np.float64))
 
 
 def mode_squares(N: int) -> np.ndarray:
@@ -373,14 +384,14 @@ def shell_field(D: np.ndarray, bins: np.ndarray, b: int) -> np.ndarray:
     line): mask the spectrum to the shell and apply the unnormalised inverse
     DFT (NumPy's ifftn divides by N_pix, so multiply back)."""
     npix = D.size
-    return (np.fft.ifftn(np.where(bins == b, D, 0.0)) * npix).real
+    return (_ifftn(np.where(bins == b, D, 0.0)) * npix).real
 
 
 def count_field(bins: np.ndarray, b: int) -> np.ndarray:
     """N_b(n) = sum_{m in S_b} e^{+2 pi i m.n/N} (Eq. delta_nr, second
     line): the unnormalised inverse DFT of the shell indicator."""
     npix = bins.size
-    return (np.fft.ifftn((bins == b).astype(np.complex128)) * npix).real
+    return (_ifftn((bins == b).astype(np.complex128)) * npix).real
 
 
 def fft_estimator(field, L: float, edges, triplets=None, quads=None, bins_needed=None):
@@ -392,8 +403,9 @@ def fft_estimator(field, L: float, edges, triplets=None, quads=None, bins_needed
       T    = V^3/N_pix^4 sum_x I_a I_b I_c I_d / sum_x N_a..N_d  (Eq. Jeong_gen)
     ``triplets`` / ``quads`` default to every a<=b<=c (a<=b<=c<=d) of
     non-empty bins.  Returns a dict with the sums, the counts rounded from
-    sum N..N / N_pix, the estimates, and ``M`` (the cancellation-free scale
-    of each triplet, V^2/N_pix^3 sum_x |I_a I_b I_c| / sum_x N_a N_b N_c).
+    sum N..N / N_pix, the estimates, ``M`` (the cancellation-free scale of
+    each triplet, V^2/N_pix^3 sum_x |I_a I_b I_c| / sum_x N_a N_b N_c) and,
+    for quadruplets, ``qM`` (the same with four fields and V^3/N_pix^4).
     """
     field = np.asarray(field, dtype=np.float64)
     N = field.shape[0]
@@ -444,14 +456,20 @@ def fft_estimator(field, L: float, edges, triplets=None, quads=None, bins_needed
     if quads is not None:
         qd = np.asarray(quads, dtype=np.int32).reshape(-1, 4)
         qn = np.zeros(len(qd))
+        qmag = np.zeros(len(qd))
         qden = np.zeros(len(qd))
         for i, (a, b, c, d) in enumerate(qd):
-            qn[i] = float(np.sum(I[a] * I[b] * I[c] * I[d]))
+            prod = I[a] * I[b] * I[c] * I[d]
+            qn[i] = float(np.sum(prod))
+            qmag[i] = float(np.sum(np.abs(prod)))
             qden[i] = float(np.sum(C[a] * C[b] * C[c] * C[d]))
         out["quads"] = qd
         out["qnum"] = qn
         out["qden"] = qden
-        out["N_quad"] = np.rint(qden / npix).astype(np.int64)
+        # counts past 2^63 do not fit int64: there N_quad is the FP64 sum
+        q = qden / npix
+        out["N_quad"] = np.where(q < 9.2e18, np.rint(np.minimum(q, 9.2e18)), q).astype(np.float64)
         with np.errstate(invalid="ignore", divide="ignore"):
             out["T"] = (V ** 3 / npix ** 4) * qn / qden
+            out["qM"] = (V ** 3 / npix ** 4) * qmag / qden
     return out
