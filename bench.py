@@ -200,6 +200,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -333,7 +334,8 @@ def main():
     allk = {("B:" + k): v for k, v in kB.items()}
     allk.update({("T:" + k): v for k, v in kT.items()})
     top = max(allk.items(), key=lambda kv: kv[1][0])
-    roof = roofline(top, planB, planT, N, pk, pk_src, clocks)
+    roof = roofline(top, planB, planT, N, pk, pk_src, clocks, args.steps)
+    roof_fft = roofline_fft(kB, kT, planB, planT, N, pk, pk_src, args.steps)
 
     line = {"metric": "bispectrum triangle-bins/s", "value": value, "unit": "triangle-bins/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -342,7 +344,8 @@ def main():
             "data": "synthetic", "config": dict(workload(args), ntrip_B=planB.ntrip,
                                                 nquad_T=planT.nquad, precision_B=args.precision,
                                                 precision_T=args.precision, parallelism="replicas%d" % world),
-            "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
+            "roofline": roof, "roofline_fft": roof_fft, "clocks": clocks, "gpu_launches": int(launches),
+            "levels": {"B": [l["M"] for l in planB.levels], "T": [l["M"] for l in planT.levels]},
             "plan_s": plan_s, "count_margin": [planB.count_margin, planT.count_margin],
             "quad_counts_exact": planT.quad_counts_exact,
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in allk.items() if v[1]}}
@@ -372,6 +375,30 @@ def main():
                 "max_rel_diff_vs_ours": float(np.max(np.abs(numP[big] - ours[big]) / np.abs(ours[big])))}
         except Exception as ex:
             line["plain_fp32_gpu"] = {"value": None, "error": str(ex)[:200]}
+    if rank == 0 and not args.no_plain and world == 1:
+        try:
+            ms_cu, nb_cu = cufft_fft_stage(field, N, np.asarray(planB.thresholds), dev)
+            ours_fft = sum(kB.get(c, (0, 0))[0] for c in FFT_CLASSES) / args.steps
+            line["cufft_fft_stage"] = {
+                "ms_per_field": ms_cu, "bins": nb_cu, "ours_ms_per_field": ours_fft,
+                "speedup_of_ours": ms_cu / ours_fft if ours_fft else None,
+                "what": "cuFFT R2C of the field + one masked C2R per non-empty bin of the 64-bin plan on "
+                        "the full N^3 grid (torch.fft); ours: the FFT kernels of the same plan"}
+        except Exception as ex:
+            line["cufft_fft_stage"] = {"value": None, "error": str(ex)[:200]}
+    if rank == 0 and not args.no_workloads and world == 1:
+        try:
+            import fields
+            wl = {}
+            f1 = fields.lognormal(32, 0.5, -2.0, seed=0).astype(np.float32)
+            wl["lognormal_32^3_lin6"] = workload_line(32, 100.0, fields.linear_edges(32, 100.0, 6), f1,
+                                                      args.precision, steps=50)
+            f2 = fields.bubbles(256, 6.0, 0.5, seed=1).astype(np.float32)
+            wl["bubbles_256^3_lin32"] = workload_line(256, 256.0, fields.linear_edges(256, 256.0, 32), f2,
+                                                      args.precision, steps=10)
+            line["workloads"] = wl
+        except Exception as ex:
+            line["workloads"] = {"error": str(ex)[:200]}
     if rank == 0 and not args.no_batch and world == 1:
         try:
             line["batched"] = batched_run(precision=args.precision)
@@ -567,72 +594,164 @@ def whole_job_rate(world, units_per_rank, seconds_max):
     return world * units_per_rank / seconds_max
 
 
-def roofline(top, planB, planT, N, pk, pk_src, clocks):
-    """Algorithmic work of the dominant kernel class per launch / its mean
-    launch duration (CUDA events around each launch on the plan's stream)."""
+def _level_sets(plan):
+    """Per evaluation level: (M, bins, triplets, quadruplets) of the plan."""
+    out = []
+    for li, lv in enumerate(plan.levels):
+        tr = plan.triplets[plan.trip_level == li]
+        qd = plan.quads[plan.quad_level == li] if plan.nquad else np.zeros((0, 4), dtype=np.int32)
+        out.append((lv["M"], lv["nbins"], tr, qd))
+    return out
+
+
+def contraction_flops_per_step(plan, quads):
+    """Algorithmic flops of one evaluation's contractions: per point of each
+    level's grid, 2 (multiply-add) per item, plus one multiply per distinct
+    outer pair product (b, c) of the triplets (and (c, d) of the quadruplets)
+    and per distinct inner pair (a, b) of the quadruplets."""
+    tot = 0.0
+    for M, nb, tr, qd in _level_sets(plan):
+        pairs = {(int(t[1]), int(t[2])) for t in tr}
+        items = len(tr)
+        inner = 0
+        if quads:
+            pairs |= {(int(q[2]), int(q[3])) for q in qd}
+            inner = len({(int(q[0]), int(q[1])) for q in qd})
+            items += len(qd)
+        tot += float(M) ** 3 * (2 * items + len(pairs) + inner)
+    return tot
+
+
+def shell_field_bytes_per_step(plan):
+    """Bytes of the shell fields of one evaluation (FP32, every level's bins on
+    its grid): what the z stage writes and the contraction reads."""
+    return sum(4.0 * nb * float(M) ** 3 for M, nb, _, _ in _level_sets(plan))
+
+
+def fft_stage_bytes_per_step(plan, N):
+    """Algorithmic HBM bytes of one evaluation's FFT stage (forward R2C of the
+    field, the pruned spectrum box written, every shell's modes read once per
+    level that evaluates it, every shell field written)."""
+    thr = np.asarray(plan.thresholds)
+    R = int(np.floor(np.sqrt(max(int(thr[-1]) - 1, 0))))
+    box = (2 * R + 1) ** 2 * (R + 1) * 8.0
+    shell_read = 0.0
+    for M, nb, tr, qd in _level_sets(plan):  # the modes of every bin a level's items use
+        bins = set(np.unique(tr).tolist()) | set(np.unique(qd).tolist())
+        shell_read += 8.0 * sum(int(plan.shell[b]) for b in bins)
+    return 4.0 * N ** 3 + box + shell_read + shell_field_bytes_per_step(plan)
+
+
+def roofline(top, planB, planT, N, pk, pk_src, clocks, steps):
+    """Algorithmic work of the dominant kernel class in one step / its CUDA-event
+    time in one step (the sum of its launches on the plan's stream): the same
+    ratio as work per launch over mean launch duration, with launches of
+    several evaluation levels of different sizes."""
     name, (ms_tot, n) = top
     which, cls = name.split(":", 1)
     plan = planB if which == "B" else planT
-    npix = N ** 3
-    per_launch_ms = ms_tot / max(1, n)
-    out = {"kernel": name, "launches": n, "avg_ms": per_launch_ms}
+    ms_step = ms_tot / steps
+    out = {"kernel": name, "launches": n, "avg_ms": ms_tot / max(1, n), "ms_per_step": ms_step,
+           "launches_per_step": n / steps}
     hbm = _find(pk, "hbm_gbs", "hbm_GBs", "copy_gbs") or 6800.0
     bf16 = _find(pk, "bf16_tflops_sustained") or 1700.0
-    pts_per_launch = plan_slab_points(plan, N)
     if cls in ("contract_fp32", "contract_quad"):
-        # FP32 CUDA-core FMAs: 1 mul per outer pair + 2 flops per item, per point
-        nit = plan.ntrip if cls == "contract_fp32" else plan.nquad
-        npairs = len({(int(a[1]), int(a[2])) for a in plan.triplets}) if cls == "contract_fp32" else \
-            len({(int(q[2]), int(q[3])) for q in plan.quads})
-        per_pt = 2 * nit + npairs + (nit if cls == "contract_quad" else 0)
-        flops = per_pt * pts_per_launch
+        flops = contraction_flops_per_step(plan, cls == "contract_quad")
         sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flop x clock
-        ach = flops / (per_launch_ms * 1e-3) / 1e12
+        ach = flops / (ms_step * 1e-3) / 1e12
         out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": None,
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (derived)" % sm_mhz})
     elif cls in ("contract_tc", "contract_quad_tc"):
-        # per point: 2 flops (multiply-add) per item, 1 multiply per distinct
-        # outer pair and per distinct inner pair; the trispectrum plan's pass
-        # ("contract_quad_tc") also contracts the plan's triplets
-        tpairs = {(int(a[1]), int(a[2])) for a in plan.triplets}
-        if cls == "contract_tc":
-            flops = (2 * plan.ntrip + len(tpairs)) * pts_per_launch
-        else:
-            qpairs = {(int(q[2]), int(q[3])) for q in plan.quads}
-            ninner = len({(int(q[0]), int(q[1])) for q in plan.quads})
-            flops = (2 * (plan.nquad + plan.ntrip) + len(qpairs | tpairs) + ninner) * pts_per_launch
-        ach = flops / (per_launch_ms * 1e-3) / 1e12
+        # the trispectrum plan's pass ("contract_quad_tc") also contracts the plan's triplets
+        flops = contraction_flops_per_step(plan, cls == "contract_quad_tc")
+        ach = flops / (ms_step * 1e-3) / 1e12
         ratio = NCU_TRAFFIC_RATIO.get(cls)
-        # the TMA ring reads every bin's row of the slab
-        traffic = ratio[0] * 4.0 * plan.nbins * pts_per_launch if ratio else None
+        # per launch, like `achieved`: the TMA ring reads every evaluated shell field once
+        traffic = ratio[0] * shell_field_bytes_per_step(plan) * steps / max(1, n) if ratio else None
         out.update({"bound": "tensor", "achieved": ach, "peak": bf16, "unit": "TFLOP/s",
                     "frac": ach / bf16, "traffic": traffic,
                     "traffic_source": ratio[1] if ratio else None,
                     "peak_source": "bf16_tflops_sustained (%s)" % pk_src})
     else:
-        # FFT stages: algorithmic bytes per launch (shell fields written, inputs read)
-        byts = fft_bytes(cls, plan, N, pts_per_launch)
-        ach = byts / (per_launch_ms * 1e-3) / 1e9
+        byts = shell_field_bytes_per_step(plan) if cls == "inv_z" else fft_stage_bytes_per_step(plan, N)
+        ach = byts / (ms_step * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                     "frac": ach / hbm, "traffic": None, "peak_source": "hbm_gbs (%s)" % pk_src})
     return out
 
 
-def plan_slab_points(plan, N):
-    """Points of the evaluation grid in one (full) slab of the plan."""
-    M = plan.eval_grid
-    return plan.slab_planes * M * M
+FFT_CLASSES = ("fwd_z", "fwd_y", "fwd_x", "inv_x", "inv_y", "inv_z")
 
 
-def fft_bytes(cls, plan, N, pts):
-    nonempty = int((plan.shell > 0).sum())
-    if cls == "inv_z":
-        return 4 * pts * nonempty  # shell-field writes dominate
-    if cls == "fwd_z":
-        return 4 * N ** 3
-    return 4 * pts * nonempty
+def roofline_fft(kB, kT, planB, planT, N, pk, pk_src, steps):
+    """The FFT stage of a step (forward and pruned inverse transforms of both
+    plans) against HBM: algorithmic bytes / summed FFT kernel time."""
+    hbm = _find(pk, "hbm_gbs", "hbm_GBs", "copy_gbs") or 6800.0
+    ms = sum(kB.get(c, (0, 0))[0] + kT.get(c, (0, 0))[0] for c in FFT_CLASSES) / steps
+    byts = fft_stage_bytes_per_step(planB, N) + fft_stage_bytes_per_step(planT, N)
+    ach = byts / (ms * 1e-3) / 1e9
+    zb = shell_field_bytes_per_step(planB) + shell_field_bytes_per_step(planT)
+    zms = (kB.get("inv_z", (0, 0))[0] + kT.get("inv_z", (0, 0))[0]) / steps
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "bytes_per_step": byts, "ms_per_step": ms,
+            "inv_z": {"achieved": zb / (zms * 1e-3) / 1e9, "frac": zb / (zms * 1e-3) / 1e9 / hbm,
+                      "bytes_per_step": zb, "ms_per_step": zms},
+            "peak_source": "hbm_gbs (%s)" % pk_src,
+            "what": "fwd_z/y/x + inv_x/y/z of both plans; bytes: field read, spectrum box written, "
+                    "shell modes read per level, shell fields written"}
+
+
+def cufft_fft_stage(field, N, thr, dev, reps=3):
+    """cuFFT alone doing the FFT work of the plain method for the bispectrum
+    plan's bins (comparison only): R2C of the field, then per bin a masked
+    C2R on the full N^3 grid.  Returns ms per field."""
+    import torch
+    fx = torch.fft.fftfreq(N, d=1.0 / N, device=dev)
+    fz = torch.arange(N // 2 + 1, device=dev, dtype=fx.dtype)
+    m2 = (fx[:, None, None] ** 2 + fx[None, :, None] ** 2 + fz[None, None, :] ** 2).round().to(torch.int64)
+    masks = [((m2 >= int(thr[b])) & (m2 < int(thr[b + 1]))) for b in range(len(thr) - 1)]
+    masks = [m for m in masks if bool(m.any())]
+    out = torch.empty((N, N, N), dtype=torch.float32, device=dev)
+
+    def once():
+        f = torch.fft.rfftn(field)
+        for m in masks:
+            out.copy_(torch.fft.irfftn(f * m, s=(N, N, N)))
+    once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, len(masks)
+
+
+def workload_line(N, L, edges, field32, precision, steps=10, warmup=3):
+    """Throughput of one workload through the library (device field and
+    outputs): closed triplets x fields / time, CUDA events on the plan's stream."""
+    import torch
+    import paper_1705_06284_gb300 as fbs
+    f = torch.from_numpy(field32).cuda()
+    with fbs.Plan(N, L, edges, precision=precision) as plan:
+        B = torch.empty(plan.ntrip, dtype=torch.float64, device=f.device)
+        P = torch.empty(plan.nbins, dtype=torch.float64, device=f.device)
+        for _ in range(warmup):
+            plan.bispectrum(f, B, P)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            plan.bispectrum(f, B, P)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        ms = e0.elapsed_time(e1) / steps
+        return {"value": plan.ntrip / (ms * 1e-3), "unit": "triangle-bins/s", "ms_per_field": ms,
+                "ntrip": plan.ntrip, "precision": precision, "levels": [l["M"] for l in plan.levels]}
 
 
 if __name__ == "__main__":

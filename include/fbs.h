@@ -71,8 +71,9 @@ enum {
     FBS_FLAG_TRISPECTRUM = 1u,   /* also enumerate closed quadruplets (needed by fbs_trispectrum) */
     FBS_FLAG_ALLOW_ALIASED = 2u, /* allow edges beyond N k_f/4 (closure is then modulo N, Sec. 3.2) */
     FBS_FLAG_TIMING = 4u,        /* record CUDA events around every kernel (fbs_plan_kernel_times) */
-    FBS_FLAG_FULL_GRID = 8u      /* evaluate the shell fields and their products on the input
+    FBS_FLAG_FULL_GRID = 8u,     /* evaluate the shell fields and their products on the input
                                     N^3 grid instead of the smallest M^3 grid that gives the same sums */
+    FBS_FLAG_SINGLE_GRID = 16u   /* one evaluation grid M > pR for every item (no levels) */
 };
 
 /*
@@ -88,14 +89,20 @@ enum {
  *   precision  : FBS_PREC_*.
  *   flags      : FBS_FLAG_* bits.
  *   cuda_stream: cudaStream_t the plan launches on (NULL = legacy default stream).
- * Evaluation grid: every shell field holds only modes with |m_j| <= R, so a
- * product of p of them is a trigonometric polynomial of degree <= pR per
- * axis and its sum over the N^3 grid equals (N/M)^3 times its sum over any
- * M^3 grid with M > pR (p = 3, or 4 with FBS_FLAG_TRISPECTRUM).  Unless
- * FBS_FLAG_FULL_GRID or FBS_FLAG_ALLOW_ALIASED is given, the plan evaluates
- * the shell fields and their products on the smallest even M = 2^a 3^b > pR
- * (M <= N): the same sums up to rounding, with (M/N)^3 of the points.  The
- * plan-time count sums use the same grid (N_tri = sum_M N_a N_b N_c / M^3).
+ * Evaluation grids: the shell field of bin b holds only modes with
+ * |m_j| <= R_b, so the product of an item's fields (a triplet or quadruplet)
+ * is a trigonometric polynomial of degree <= R_a + R_b + R_c (+ R_d) per axis,
+ * and its sum over the N^3 grid equals (N/M)^3 times its sum over any M^3 grid
+ * with M above that degree.  The plan groups the items into up to four
+ * levels, each an even M = 2^a 3^b <= N above the degree of every item in it
+ * (and above 2 R_b of each of its bins), chosen to minimise a work model of
+ * the transforms and contractions; each level evaluates only the bins its
+ * items use: the same sums up to rounding, with far fewer points than one
+ * grid for all.  FBS_FLAG_SINGLE_GRID keeps one level on the smallest
+ * M > pR (R the largest component of any bin, p = 3, or 4 with
+ * FBS_FLAG_TRISPECTRUM); FBS_FLAG_FULL_GRID and FBS_FLAG_ALLOW_ALIASED keep
+ * one level on M = N.  The plan-time count sums use each item's own grid
+ * (N_tri = sum_M N_a N_b N_c / M^3).
  * The plan runs the plan-time work on the device before returning: shell
  * tables, the FP64 count fields N_b, exact N_tri (and N_quad) for every
  * candidate bin triple, and the closed-triplet list (lexicographic a<=b<=c
@@ -260,14 +267,27 @@ double fbs_plan_count_margin(const fbs_plan *plan);
  * within 0.25 and below 2^53), 0 when some are FP64 sums, <0 on error. */
 int fbs_plan_quad_counts_exact(const fbs_plan *plan);
 
-/* Side M of the grid the plan evaluates shell fields and products on. */
+/* Side M of the largest evaluation grid of the plan (its last level). */
 int fbs_plan_eval_grid(const fbs_plan *plan);
 
-/* Planes of the evaluation grid per slab (the shell fields of one slab are
- * resident at a time; slabs are balanced, the last may be shorter) and the
+/* Planes per slab of that level's grid (the shell fields of one slab are
+ * resident at a time; slabs are balanced, the last may be shorter) and its
  * number of slabs per evaluation; <0 on error. */
 int fbs_plan_slab_planes(const fbs_plan *plan);
 int fbs_plan_num_slabs(const fbs_plan *plan);
+
+/* Number of evaluation levels (grids ascending), or <0 on error. */
+int fbs_plan_num_levels(const fbs_plan *plan);
+
+/* Level i (0 <= i < fbs_plan_num_levels): its grid M, the bins it evaluates,
+ * the closed triplets and quadruplets it contracts, and its slab planes and
+ * slabs per evaluation.  Any output pointer may be NULL. */
+fbs_status fbs_plan_level(const fbs_plan *plan, int i, int *M, int *nbins, int *ntrip, int *nquad,
+                          int *slab_planes, int *nslabs);
+
+/* The level of every closed triplet (trip_level[ntrip], order of
+ * fbs_plan_triplets) and quadruplet (quad_level[nquad]); either may be NULL. */
+fbs_status fbs_plan_item_levels(const fbs_plan *plan, int32_t *trip_level, int32_t *quad_level);
 
 /* Device bytes owned by the plan. */
 int64_t fbs_plan_device_bytes(const fbs_plan *plan);

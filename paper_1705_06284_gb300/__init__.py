@@ -36,6 +36,7 @@ FBS_FLAG_TRISPECTRUM = 1
 FBS_FLAG_ALLOW_ALIASED = 2
 FBS_FLAG_TIMING = 4
 FBS_FLAG_FULL_GRID = 8
+FBS_FLAG_SINGLE_GRID = 16
 FBS_OPT_TC_WIDE = 1
 FBS_OPT_TC_ROLES = 2
 FBS_OPT_TC_CHUNK = 3
@@ -84,6 +85,9 @@ _SIGS = [
     ("fbs_plan_eval_grid", ctypes.c_int, [_vp]),
     ("fbs_plan_slab_planes", ctypes.c_int, [_vp]),
     ("fbs_plan_num_slabs", ctypes.c_int, [_vp]),
+    ("fbs_plan_num_levels", ctypes.c_int, [_vp]),
+    ("fbs_plan_level", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 6),
+    ("fbs_plan_item_levels", ctypes.c_int, [_vp, _vp, _vp]),
     ("fbs_plan_check", ctypes.c_int, [_vp]),
     ("fbs_set_device_budget", ctypes.c_int, [ctypes.c_int64]),
     ("fbs_device_bytes_in_use", ctypes.c_int64, []),
@@ -182,10 +186,10 @@ class Plan:
     """
 
     def __init__(self, N, L, edges, precision="fp32", trispectrum=False, allow_aliased=False,
-                 timing=False, stream=None, full_grid=False):
+                 timing=False, stream=None, full_grid=False, single_grid=False):
         flags = (FBS_FLAG_TRISPECTRUM if trispectrum else 0) | \
                 (FBS_FLAG_ALLOW_ALIASED if allow_aliased else 0) | (FBS_FLAG_TIMING if timing else 0) | \
-                (FBS_FLAG_FULL_GRID if full_grid else 0)
+                (FBS_FLAG_FULL_GRID if full_grid else 0) | (FBS_FLAG_SINGLE_GRID if single_grid else 0)
         if stream is None:
             try:
                 import torch
@@ -218,6 +222,15 @@ class Plan:
         self.eval_grid = int(Lb.fbs_plan_eval_grid(_vp(self._h)))
         self.slab_planes = int(Lb.fbs_plan_slab_planes(_vp(self._h)))
         self.num_slabs = int(Lb.fbs_plan_num_slabs(_vp(self._h)))
+        self.levels = []
+        for i in range(Lb.fbs_plan_num_levels(_vp(self._h))):
+            v = [ctypes.c_int() for _ in range(6)]
+            _check(Lb.fbs_plan_level(_vp(self._h), i, *[ctypes.byref(x) for x in v]))
+            self.levels.append(dict(zip(("M", "nbins", "ntrip", "nquad", "slab_planes", "nslabs"),
+                                        (x.value for x in v))))
+        self.trip_level = np.zeros(self.ntrip, dtype=np.int32)
+        self.quad_level = np.zeros(self.nquad, dtype=np.int32)
+        _check(Lb.fbs_plan_item_levels(_vp(self._h), self.trip_level.ctypes.data, self.quad_level.ctypes.data))
 
     # -- lifetime
     def close(self):

@@ -124,23 +124,26 @@ __global__ void __launch_bounds__(kCThreads) contract_fp32_kernel(
 }
 
 // ------------------------------------------------------------------ reduce
-// out[i] = sum_r part[r][i] in a fixed order (deterministic).
-// out[i] = scale * sum_r part[r*ld + i], i < n (rows summed in a fixed order).
+// out[map[i]] = scale * sum_r part[r*ld + i], i < n (rows summed in a fixed
+// order, deterministic); map == nullptr: out[i].
 __global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, int n, int ld,
-                                   double *__restrict__ out, double scale) {
+                                   double *__restrict__ out, double scale, const int *__restrict__ map) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
     for (int r = 0; r < rows; ++r) s += part[(long long)r * ld + i];
-    out[i] = scale * s;
+    out[map ? map[i] : i] = scale * s;
 }
 
-// out[j] = sum_r part[j][r]: one block per j, strided partial sums then a
-// fixed-shape tree (deterministic for a given launch shape).
+// out[map[j]] = scale * sum_r part[j][r] for every j with map[j] >= 0: one
+// block per j, strided partial sums then a fixed-shape tree (deterministic
+// for a given launch shape).
 __global__ void __launch_bounds__(256) reduce_cols_kernel(const double *__restrict__ part, int rows,
-                                                          double *__restrict__ out, double scale) {
+                                                          double *__restrict__ out, double scale,
+                                                          const int *__restrict__ map) {
     __shared__ double red[256];
     const int j = blockIdx.x;
+    if (map[j] < 0) return;
     double s = 0.0;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) s += part[(long long)j * rows + r];
     red[threadIdx.x] = s;
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(256) reduce_cols_kernel(const double *__restri
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[j] = scale * red[0];
+    if (threadIdx.x == 0) out[map[j]] = scale * red[0];
 }
 
 // ------------------------------------------------------------------ normalise
@@ -314,46 +317,49 @@ void zero_partials(Plan &p, bool quads) {
                              (size_t)p.nbins * p.M * zstage_row_groups(p.M) * sizeof(double), p.stream));
 }
 
-void launch_reduce_and_normalise(Plan &p, bool quads) {
-    {
-        KTimer tm(p, KC_REDUCE);
-        // sums over the M^3 evaluation grid -> sums over the N^3 grid
-        const double r = (double)p.N / (double)p.M;
-        const double scale = r * r * r;
-        int n = p.ttask.nitems;
-        if (n > 0) {
-            const double *src = p.fused_active ? p.d_fpart : p.d_tpart;
-            const int ld = p.fused_active ? n + p.qtask.nitems : n;
-            reduce_rows_kernel<<<(n + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, n, ld, p.d_tnum,
-                                                                      scale);
-            FBS_CUDA(cudaGetLastError());
-        }
-        if (quads && p.qtask.nitems > 0) {
-            int m = p.qtask.nitems;
-            const double *src = p.fused_active ? p.d_fpart + p.ttask.nitems : p.d_qpart;
-            const int ld = p.fused_active ? m + p.ttask.nitems : m;
-            reduce_rows_kernel<<<(m + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, m, ld, p.d_qnum,
-                                                                      scale);
-            FBS_CUDA(cudaGetLastError());
-        }
-        {
-            const int rows = p.M * zstage_row_groups(p.M);
-            reduce_cols_kernel<<<p.nbins, 256, 0, p.stream>>>(p.d_sumsq_part, rows, p.d_sumsq, scale);
-            FBS_CUDA(cudaGetLastError());
-        }
-        int ntrip = (int)p.ntri.size(), nquad = quads ? (int)p.nquad.size() : 0;
-        int n_all = std::max(std::max(ntrip, nquad), p.nbins);
-        normalise_kernel<<<(n_all + 255) / 256, 256, 0, p.stream>>>(
-            p.d_tnum, p.d_ntri, ntrip, p.d_qnum, p.d_nquad, nquad, p.d_sumsq, p.d_shell, p.nbins,
-            p.L, p.N, p.d_B, p.d_P, quads ? p.d_T : nullptr,
-            p.precision != FBS_PREC_FP32 ? tc_error_flag(p) : nullptr,
-            p.precision != FBS_PREC_FP32 ? tc_sticky_flag(p) : nullptr);
+// A level's sums over its M^3 grid -> sums over the N^3 grid ((N/M)^3), into
+// the root's global arrays: triplet and quadruplet sums through the level's
+// output maps, sums of squares of the bins whose P this level provides.
+void launch_level_reduce(Plan &p, bool quads) {
+    Plan &R = p.root();
+    KTimer tm(p, KC_REDUCE);
+    const double r = (double)R.N / (double)p.M;
+    const double scale = r * r * r;
+    int n = p.ttask.nitems;
+    if (n > 0) {
+        const double *src = p.fused_active ? p.d_fpart : p.d_tpart;
+        const int ld = p.fused_active ? n + p.qtask.nitems : n;
+        reduce_rows_kernel<<<(n + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, n, ld, R.d_tnum, scale,
+                                                                  p.d_gtrip);
         FBS_CUDA(cudaGetLastError());
-        if (p.precision != FBS_PREC_FP32 && tc_sticky_flag(p) && p.h_err) {
-            FBS_CUDA(cudaMemcpyAsync(p.h_err, tc_sticky_flag(p), sizeof(int), cudaMemcpyDeviceToHost, p.stream));
-            FBS_CUDA(cudaEventRecord(p.ev_err, p.stream));
-            p.err_recorded = true;
-        }
+    }
+    if (quads && p.qtask.nitems > 0) {
+        int m = p.qtask.nitems;
+        const double *src = p.fused_active ? p.d_fpart + p.ttask.nitems : p.d_qpart;
+        const int ld = p.fused_active ? m + p.ttask.nitems : m;
+        reduce_rows_kernel<<<(m + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, m, ld, R.d_qnum, scale,
+                                                                  p.d_gquad);
+        FBS_CUDA(cudaGetLastError());
+    }
+    const int rows = p.M * zstage_row_groups(p.M);
+    reduce_cols_kernel<<<p.nbins, 256, 0, p.stream>>>(p.d_sumsq_part, rows, R.d_sumsq, scale, p.d_pbin);
+    FBS_CUDA(cudaGetLastError());
+}
+
+void launch_normalise(Plan &p, bool quads) {
+    KTimer tm(p, KC_REDUCE);
+    int ntrip = (int)p.ntri.size(), nquad = quads ? (int)p.nquad.size() : 0;
+    int n_all = std::max(std::max(ntrip, nquad), p.nbins);
+    normalise_kernel<<<(n_all + 255) / 256, 256, 0, p.stream>>>(
+        p.d_tnum, p.d_ntri, ntrip, p.d_qnum, p.d_nquad, nquad, p.d_sumsq, p.d_shell, p.nbins,
+        p.L, p.N, p.d_B, p.d_P, quads ? p.d_T : nullptr,
+        p.precision != FBS_PREC_FP32 ? tc_error_flag(p) : nullptr,
+        p.precision != FBS_PREC_FP32 ? tc_sticky_flag(p) : nullptr);
+    FBS_CUDA(cudaGetLastError());
+    if (p.precision != FBS_PREC_FP32 && tc_sticky_flag(p) && p.h_err) {
+        FBS_CUDA(cudaMemcpyAsync(p.h_err, tc_sticky_flag(p), sizeof(int), cudaMemcpyDeviceToHost, p.stream));
+        FBS_CUDA(cudaEventRecord(p.ev_err, p.stream));
+        p.err_recorded = true;
     }
 }
 
@@ -379,7 +385,8 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
     dim3 g(blocks, ngrp);
     count_kernel<<<g, 256, sm, p.stream>>>(noct, nbins_all, H, d_items, arity, nitems, grp, part);
     FBS_CUDA(cudaGetLastError());
-    reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, nitems, d_den, 1.0);
+    reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, nitems, d_den, 1.0,
+                                                                   nullptr);
     FBS_CUDA(cudaGetLastError());
 }
 

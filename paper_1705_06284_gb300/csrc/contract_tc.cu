@@ -88,7 +88,7 @@ struct WideJob {
 struct TcState {
     TcJob trip, quad, fused;
     WideJob wtrip, wquad;
-    int *d_err = nullptr;     // [0]: this evaluation's wait-timeout code; [1]: sticky copy
+    int *d_err = nullptr;     // the root plan's flags: [0] this evaluation's wait-timeout code, [1] sticky copy
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -946,8 +946,7 @@ static TcState &tc_state(Plan &p) {
     if (!p.tc) {
         TcState *st = new TcState();
         p.tc = st;
-        st->d_err = (int *)p.dalloc(2 * sizeof(int));
-        FBS_CUDA(cudaMemsetAsync(st->d_err, 0, 2 * sizeof(int), p.stream));
+        st->d_err = p.root().d_errbuf;
     }
     return *reinterpret_cast<TcState *>(p.tc);
 }
@@ -1281,8 +1280,8 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
     return true;
 }
 
-int *tc_error_flag(Plan &p) { return p.tc ? reinterpret_cast<TcState *>(p.tc)->d_err : nullptr; }
-int *tc_sticky_flag(Plan &p) { return p.tc ? reinterpret_cast<TcState *>(p.tc)->d_err + 1 : nullptr; }
+int *tc_error_flag(Plan &p) { return p.root().d_errbuf; }
+int *tc_sticky_flag(Plan &p) { return p.root().d_errbuf ? p.root().d_errbuf + 1 : nullptr; }
 
 bool tc_quads_usable(Plan &p) {
     TcState &st = tc_state(p);

@@ -90,7 +90,8 @@ struct Plan;
 
 // ---------------------------------------------------------------- kernels (launch wrappers)
 // fft.cu
-void upload_twiddles(Plan &p);
+void upload_forward_twiddles(Plan &root);
+void upload_eval_twiddles(Plan &level);
 void launch_forward(Plan &p, const float *d_field);
 void launch_inverse_x(Plan &p, bool indicator_fp64);
 void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab);
@@ -108,13 +109,33 @@ bool tc_quads_usable(Plan &p);
 // Triplets and quadruplets of a trispectrum plan in one tensor-core pass.
 bool tc_fused_usable(Plan &p);
 void launch_contract_tc_fused(Plan &p, const float *islab, long long npts, long long slab_stride);
-void launch_reduce_and_normalise(Plan &p, bool quads);
+void launch_level_reduce(Plan &level, bool quads);
+void launch_normalise(Plan &root, bool quads);
+std::vector<int> fast_grids();  // grids with compile-time-radix kernels for every inverse stage
 void zero_partials(Plan &p, bool quads);
 std::vector<int> item_groups(const TaskList &t, int cap);
 int contract_blocks();
 
 // ---------------------------------------------------------------- plan
+// A plan is a root plus one or more evaluation levels.  The root owns the
+// forward transform of the field, the spectrum box, the global tables (bins,
+// closed triplets and quadruplets in output order, counts) and the outputs.
+// A level (also a Plan, with root_ set) evaluates a subset of the bins on its
+// own grid M and contracts the items assigned to it: every item's product of
+// shell fields is a trigonometric polynomial of degree <= the sum of its
+// bins' largest components R, so its sum is exact on any M above that sum.
+// Local bin b of a level is global bin gbin[b]; local triplet t is global
+// output gtrip[t] (quadruplets: gquad).  Levels allocate through the root and
+// time their launches through it; they share the root's scratch buffers for
+// the per-slab stages, since they run one after another on the root's stream.
 struct Plan {
+    Plan *root_ = nullptr;        // null for the root
+    std::vector<Plan *> levels;   // root only
+    std::vector<int> gbin, gtrip, gquad;   // level only: local -> global maps
+    std::vector<int> pbin;        // level only: global bin of local bin b if its P is taken here, else -1
+    int *d_gtrip = nullptr, *d_gquad = nullptr, *d_pbin = nullptr;
+    int *d_errbuf = nullptr;      // root only: [0] this evaluation's wait-timeout code, [1] sticky copy
+    Plan &root() { return root_ ? *root_ : *this; }
     int N = 0;
     double L = 0;
     int nbins = 0;

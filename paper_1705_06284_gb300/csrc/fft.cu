@@ -22,6 +22,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "fbs_internal.h"
 #include "fft_core.cuh"
 
@@ -514,19 +517,26 @@ static std::vector<double2> twiddles64(int n) {
     return t;
 }
 
-// FP32 twiddles of the input grid (forward transforms) and of the evaluation
-// grid (inverse transforms of the shell fields); FP64 twiddles of the
-// evaluation grid (plan-time count fields).
-void upload_twiddles(Plan &p) {
-    const int N = p.N, M = p.M;
-    const std::vector<double2> tn = twiddles64(N), tmv = twiddles64(M);
-    std::vector<float2> t32(N), tm32(M);
+// FP32 twiddles of the input grid (forward transforms).
+void upload_forward_twiddles(Plan &p) {
+    const int N = p.N;
+    const std::vector<double2> tn = twiddles64(N);
+    std::vector<float2> t32(N);
     for (int k = 0; k < N; ++k) t32[k] = make_float2((float)tn[k].x, (float)tn[k].y);
-    for (int k = 0; k < M; ++k) tm32[k] = make_float2((float)tmv[k].x, (float)tmv[k].y);
     p.d_tw = (float2 *)p.dalloc(N * sizeof(float2));
+    FBS_CUDA(cudaMemcpyAsync(p.d_tw, t32.data(), N * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));  // host tables go out of scope
+}
+
+// FP32 twiddles of an evaluation grid (inverse transforms of the shell
+// fields) and FP64 twiddles of it (plan-time count fields).
+void upload_eval_twiddles(Plan &p) {
+    const int M = p.M;
+    const std::vector<double2> tmv = twiddles64(M);
+    std::vector<float2> tm32(M);
+    for (int k = 0; k < M; ++k) tm32[k] = make_float2((float)tmv[k].x, (float)tmv[k].y);
     p.d_twM = (float2 *)p.dalloc(M * sizeof(float2));
     p.d_tw64 = (double2 *)p.dalloc(M * sizeof(double2));
-    FBS_CUDA(cudaMemcpyAsync(p.d_tw, t32.data(), N * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
     FBS_CUDA(cudaMemcpyAsync(p.d_twM, tm32.data(), M * sizeof(float2), cudaMemcpyHostToDevice, p.stream));
     FBS_CUDA(cudaMemcpyAsync(p.d_tw64, tmv.data(), M * sizeof(double2), cudaMemcpyHostToDevice, p.stream));
     FBS_CUDA(cudaStreamSynchronize(p.stream));  // host tables go out of scope
@@ -541,6 +551,16 @@ void upload_twiddles(Plan &p) {
     X(128, 8, 8, 2)    \
     X(96, 8, 4, 3)     \
     X(64, 8, 8)
+
+std::vector<int> fast_grids() {
+    std::vector<int> g;
+#define FBS_HAS(n, ...) \
+    if (zfast_ok(n)) g.push_back(n);
+    FBS_RADICES(FBS_HAS)
+#undef FBS_HAS
+    std::sort(g.begin(), g.end());
+    return g;
+}
 
 void launch_forward(Plan &p, const float *d_field) {
     const int N = p.N, D = p.box.D, Dz = p.box.Dz;

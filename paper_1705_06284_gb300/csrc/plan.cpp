@@ -18,12 +18,14 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <string>
 #include <vector>
 
 #include "fbs_internal.h"
+#include "levels.h"
 
 namespace fbs {
 
@@ -91,6 +93,7 @@ AsyncBuf::~AsyncBuf() {
 }
 
 void *Plan::dalloc(size_t bytes) {
+    if (root_) return root_->dalloc(bytes);  // a level's memory belongs to its root
     void *ptr = nullptr;
     if (bytes == 0) bytes = 16;
     budget_reserve((long long)bytes);
@@ -110,6 +113,10 @@ void *Plan::dalloc(size_t bytes) {
 static constexpr size_t kMaxPending = 2048;
 
 void Plan::tic(int cls, int &slot) {
+    if (root_) {  // a level's launches are timed by its root
+        root_->tic(cls, slot);
+        return;
+    }
     slot = -1;
     if (!(flags & FBS_FLAG_TIMING)) return;
     if (pending.size() >= kMaxPending) flush_times();
@@ -125,6 +132,10 @@ void Plan::tic(int cls, int &slot) {
 }
 
 void Plan::toc(int slot) {
+    if (root_) {
+        root_->toc(slot);
+        return;
+    }
     if (slot < 0) return;
     cudaEventRecord(evs[2 * slot + 1], stream);
 }
@@ -222,51 +233,35 @@ static void enumerate_shells(Plan &p, std::vector<long long> &mn, std::vector<lo
         }
 }
 
-// Smallest even 2^a 3^b grid M with M > order * R (the degree of a product of
-// `order` shell fields), at most N; N itself for aliased or full-grid plans.
-static int eval_grid(int N, int R, int order, unsigned flags) {
-    if (flags & (FBS_FLAG_FULL_GRID | FBS_FLAG_ALLOW_ALIASED)) return N;
-    for (int M = std::max(8, order * R + 1); M < N; ++M)
-        if (good_N(M)) return M;
-    return N;
-}
+// Largest component |m_j| a mode of global bin b can have.
+static int bin_R(const Plan &root, int b) { return std::min(isqrt_floor(root.thr[b + 1] - 1), root.N / 2); }
 
-static void build_geometry(Plan &p) {
-    const int N = p.M;  // the inverse stages run on the evaluation grid
-    p.geom.assign(p.nbins, BinGeom{});
-    int R = 0;
+// Geometry of a level: its bins' boxes on the level's grid M.  The spectrum
+// box (forward output, transform length N) is the root's.
+static void build_level_geometry(Plan &root, Plan &lv) {
+    const int M = lv.M;
+    lv.nbins = (int)lv.gbin.size();
+    lv.geom.assign(lv.nbins, BinGeom{});
     long long aoff = 0;
-    for (int b = 0; b < p.nbins; ++b) {
-        BinGeom &g = p.geom[b];
-        g.thr_lo = p.thr[b];
-        g.thr_hi = p.thr[b + 1];
-        g.empty = p.shell[b] == 0;
-        if (g.empty) {
-            g.Rb = 0;
-            g.Db = 1;
-            g.Dzb = 1;
-            g.A_off = aoff;
-            continue;
-        }
-        g.Rb = std::min(isqrt_floor(g.thr_hi - 1), N / 2);
-        g.Db = (2 * g.Rb + 1 > N) ? N : 2 * g.Rb + 1;
-        g.Dzb = std::min(g.Rb, N / 2) + 1;
+    for (int b = 0; b < lv.nbins; ++b) {
+        const int gb = lv.gbin[b];
+        BinGeom &g = lv.geom[b];
+        g.thr_lo = root.thr[gb];
+        g.thr_hi = root.thr[gb + 1];
+        g.empty = 0;  // levels hold non-empty bins only
+        g.Rb = std::min(isqrt_floor(g.thr_hi - 1), M / 2);
+        g.Db = (2 * g.Rb + 1 > M) ? M : 2 * g.Rb + 1;
+        g.Dzb = std::min(g.Rb, M / 2) + 1;
         g.A_off = aoff;
-        aoff += (long long)N * g.Db * g.Dzb;
-        R = std::max(R, g.Rb);
+        aoff += (long long)M * g.Db * g.Dzb;
     }
-    p.A_elems = aoff;
-    const int NF = p.N;  // forward transforms run on the input grid
-    p.box.N = NF;
-    p.box.R = R;
-    p.box.D = (2 * R + 1 > NF) ? NF : 2 * R + 1;
-    p.box.Dz = std::min(R, NF / 2) + 1;
-    p.boxM = p.box;
-    p.boxM.N = N;
+    lv.A_elems = aoff;
+    lv.box = root.box;
+    lv.boxM = root.box;
+    lv.boxM.N = M;
     long long gplane = 0;
-    for (int b = 0; b < p.nbins; ++b)
-        if (!p.geom[b].empty) gplane += (long long)N * p.geom[b].Dzb;
-    p.G_plane = gplane;
+    for (int b = 0; b < lv.nbins; ++b) gplane += (long long)M * lv.geom[b].Dzb;
+    lv.G_plane = gplane;
 }
 
 static void set_slab_offsets(Plan &p) {
@@ -458,8 +453,30 @@ static long long slab_budget_bytes() {
     return 8LL << 30;
 }
 
+// ---------------------------------------------------------------- levels
+static Plan *new_level(Plan &root, int M) {
+    Plan *lv = new Plan();
+    lv->root_ = &root;
+    lv->N = root.N;
+    lv->L = root.L;
+    lv->M = M;
+    lv->fM = make_factors(M);
+    lv->precision = root.precision;
+    lv->flags = root.flags;
+    lv->stream = root.stream;
+    lv->tc_wide = root.tc_wide;
+    lv->tc_roles = root.tc_roles;
+    lv->tc_chunk = root.tc_chunk;
+    lv->tc_pairs = root.tc_pairs;
+    lv->tc_wait_limit = root.tc_wait_limit;
+    lv->d_box = root.d_box;
+    root.levels.push_back(lv);
+    return lv;
+}
+
 static void create_plan(Plan &p, const double *edges) {
     const int N = p.N, nb = p.nbins;
+    const bool quads_on = (p.flags & FBS_FLAG_TRISPECTRUM) != 0;
     p.fN = make_factors(N);
     p.thr.resize(nb + 1);
     for (int i = 0; i <= nb; ++i) p.thr[i] = edge_threshold(edges[i], p.L);
@@ -474,75 +491,219 @@ static void create_plan(Plan &p, const double *edges) {
     }
     std::vector<long long> mn, mx;
     enumerate_shells(p, mn, mx);
-    {
-        int R = 0;
-        for (int b = 0; b < nb; ++b)
-            if (p.shell[b]) R = std::max(R, std::min(isqrt_floor(p.thr[b + 1] - 1), N / 2));
-        p.M = eval_grid(N, R, (p.flags & FBS_FLAG_TRISPECTRUM) ? 4 : 3, p.flags);
-        p.fM = make_factors(p.M);
-    }
-    build_geometry(p);
+    std::vector<int> R(nb, 0);
+    int Rmax = 0;
+    for (int b = 0; b < nb; ++b)
+        if (p.shell[b]) {
+            R[b] = bin_R(p, b);
+            Rmax = std::max(Rmax, R[b]);
+        }
+    // the spectrum box of the forward transform: every mode of every bin
+    p.box.N = N;
+    p.box.R = Rmax;
+    p.box.D = (2 * Rmax + 1 > N) ? N : 2 * Rmax + 1;
+    p.box.Dz = std::min(Rmax, N / 2) + 1;
+    p.M = N;
 
-    // device geometry + twiddles (needed by the count path)
-    upload_twiddles(p);
+    // forward twiddles, spectrum box, timeout flags
+    upload_forward_twiddles(p);
     p.d_box = (float2 *)p.dalloc((size_t)p.box.D * p.box.D * p.box.Dz * sizeof(float2));
     FBS_CUDA(cudaMemsetAsync(p.d_box, 0, (size_t)p.box.D * p.box.D * p.box.Dz * sizeof(float2), p.stream));
+    p.d_errbuf = (int *)p.dalloc(2 * sizeof(int));
+    FBS_CUDA(cudaMemsetAsync(p.d_errbuf, 0, 2 * sizeof(int), p.stream));
 
-    // candidates and exact counts
+    // candidate items and the grid each needs
     std::vector<int> tc, qc;
     candidates(p, mn, mx, 3, tc);
-    if (p.flags & FBS_FLAG_TRISPECTRUM) candidates(p, mn, mx, 4, qc);
-    std::vector<double> tden, qden;
-    // the count sums run on the evaluation grid: sum_M N_a N_b N_c / M^3 is
-    // the same integer as sum_N N_a N_b N_c / N^3
-    const double npix = (double)p.M * p.M * p.M;
-    exact_counts(p, tc, qc, tden, qden);
+    if (quads_on) candidates(p, mn, mx, 4, qc);
+    std::vector<int> admissible;
+    for (int M = 8; M <= N; ++M)
+        if (good_N(M)) admissible.push_back(M);
+    std::vector<LevelItem> items;
+    const bool one_grid_N = (p.flags & (FBS_FLAG_FULL_GRID | FBS_FLAG_ALLOW_ALIASED)) != 0;
+    const int single_M = one_grid_N ? N
+                         : (p.flags & FBS_FLAG_SINGLE_GRID) ? grid_above(admissible, (quads_on ? 4 : 3) * Rmax, N)
+                                                            : 0;
+    for (int ar : {3, 4}) {
+        const std::vector<int> &src = ar == 3 ? tc : qc;
+        for (size_t i = 0; i < src.size() / ar; ++i) {
+            LevelItem it{ar, {0, 0, 0, 0}, 0};
+            int sum = 0, mxR = 0;
+            for (int k = 0; k < ar; ++k) {
+                it.b[k] = src[ar * i + k];
+                sum += R[it.b[k]];
+                mxR = std::max(mxR, R[it.b[k]]);
+            }
+            it.need = grid_above(admissible, std::max(sum, 2 * mxR), N);
+            items.push_back(it);
+        }
+    }
+    std::vector<int> Rb(nb, -1);
+    for (int b = 0; b < nb; ++b)
+        if (p.shell[b]) Rb[b] = R[b];
+    // FBS_LEVEL_COST overrides the model's fixed cost per level (0 lets small
+    // plans split into levels too, as tests do)
+    double per_level = 1e8;
+    if (const char *e = getenv("FBS_LEVEL_COST")) per_level = atof(e);
+    const LevelChoice lc = choose_levels(N, nb, Rb, items, single_M, fast_grids(), 4, per_level);
+    const std::vector<int> &grids = lc.grids;
+    for (int M : grids) new_level(p, M);
+    std::vector<std::vector<int>> lt(grids.size()), lq(grids.size());  // candidate (global) items per level
+    for (size_t i = 0; i < items.size(); ++i) {
+        auto &dst = items[i].arity == 3 ? lt[lc.item_level[i]] : lq[lc.item_level[i]];
+        dst.insert(dst.end(), items[i].b, items[i].b + items[i].arity);
+    }
+
+    // per level: geometry, twiddles, FP64 count fields and exact counts
+    struct Closed {
+        int level, local;  // index in the level's candidate list
+    };
+    std::vector<std::array<int, 4>> ctrip, cquad;   // closed items (global bins)
+    std::vector<int64_t> ctri_cnt;
+    std::vector<double> cquad_cnt;
+    std::vector<Closed> ctrip_src, cquad_src;
+    std::vector<std::vector<int>> loc_of(grids.size());
+    for (size_t l = 0; l < grids.size(); ++l) {
+        Plan &lv = *p.levels[l];
+        loc_of[l].assign(nb, -1);
+        for (int b : lc.bins[l]) {
+            loc_of[l][b] = (int)lv.gbin.size();
+            lv.gbin.push_back(b);
+        }
+        build_level_geometry(p, lv);
+        upload_eval_twiddles(lv);
+        std::vector<int> ltc, lqc;
+        for (int v : lt[l]) ltc.push_back(loc_of[l][v]);
+        for (int v : lq[l]) lqc.push_back(loc_of[l][v]);
+        std::vector<double> tden, qden;
+        // sum_M N_a N_b N_c / M^3 is the same integer as sum_N N_a N_b N_c / N^3
+        const double npix = (double)lv.M * lv.M * lv.M;
+        exact_counts(lv, ltc, lqc, tden, qden);
+        for (size_t i = 0; i < tden.size(); ++i) {
+            int64_t c = round_count(p, tden[i], npix);
+            if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative triangle count"};
+            if (c == 0) continue;
+            ctrip.push_back({lt[l][3 * i], lt[l][3 * i + 1], lt[l][3 * i + 2], -1});
+            ctri_cnt.push_back(c);
+            ctrip_src.push_back({(int)l, (int)i});
+        }
+        for (size_t i = 0; i < qden.size(); ++i) {
+            // Quadruple counts of wide shells reach 1e19 and more, past the exact
+            // integers of FP64 (2^53) and of int64: below 2^53 they are rounded
+            // like triangle counts, above it the FP64 sum itself is the count.
+            const double v = qden[i] / npix;
+            const double r = nearbyint(v);
+            double c;
+            if (v < 9007199254740992.0 && fabs(v - r) <= 0.25) {
+                c = r;
+            } else {
+                c = v;  // the FP64 sum is the count (rounding would not be reliable)
+                p.quad_counts_exact = false;
+            }
+            if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative quadruple count"};
+            if (c == 0) continue;
+            cquad.push_back({lq[l][4 * i], lq[l][4 * i + 1], lq[l][4 * i + 2], lq[l][4 * i + 3]});
+            cquad_cnt.push_back(c);
+            cquad_src.push_back({(int)l, (int)i});
+        }
+    }
+    // global output order: lexicographic over all levels
+    std::vector<int> ot(ctrip.size()), oq(cquad.size());
+    for (size_t i = 0; i < ot.size(); ++i) ot[i] = (int)i;
+    for (size_t i = 0; i < oq.size(); ++i) oq[i] = (int)i;
+    std::sort(ot.begin(), ot.end(), [&](int u, int v) { return ctrip[u] < ctrip[v]; });
+    std::sort(oq.begin(), oq.end(), [&](int u, int v) { return cquad[u] < cquad[v]; });
     p.trip.clear();
     p.ntri.clear();
-    for (size_t i = 0; i < tden.size(); ++i) {
-        int64_t c = round_count(p, tden[i], npix);
-        if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative triangle count"};
-        if (c == 0) continue;
-        p.trip.insert(p.trip.end(), {tc[3 * i], tc[3 * i + 1], tc[3 * i + 2]});
-        p.ntri.push_back(c);
-    }
     p.quad.clear();
     p.nquad.clear();
-    for (size_t i = 0; i < qden.size(); ++i) {
-        // Quadruple counts of wide shells reach 1e19 and more, past the exact
-        // integers of FP64 (2^53) and of int64: below 2^53 they are rounded
-        // like triangle counts, above it the FP64 sum itself is the count.
-        const double v = qden[i] / npix;
-        const double r = nearbyint(v);
-        double c;
-        if (v < 9007199254740992.0 && fabs(v - r) <= 0.25) {
-            c = r;
-        } else {
-            c = v;  // the FP64 sum is the count (rounding would not be reliable)
-            p.quad_counts_exact = false;
-        }
-        if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative quadruple count"};
-        if (c == 0) continue;
-        p.quad.insert(p.quad.end(), {qc[4 * i], qc[4 * i + 1], qc[4 * i + 2], qc[4 * i + 3]});
-        p.nquad.push_back(c);
+    for (size_t g = 0; g < ot.size(); ++g) {
+        const int i = ot[g];
+        p.trip.insert(p.trip.end(), {ctrip[i][0], ctrip[i][1], ctrip[i][2]});
+        p.ntri.push_back(ctri_cnt[i]);
+        Plan &lv = *p.levels[ctrip_src[i].level];
+        const auto &lo = loc_of[ctrip_src[i].level];
+        lv.trip.insert(lv.trip.end(), {lo[ctrip[i][0]], lo[ctrip[i][1]], lo[ctrip[i][2]]});
+        lv.ntri.push_back(ctri_cnt[i]);
+        lv.gtrip.push_back((int)g);
     }
-    build_tasks(p);
-    p.tgrp = item_groups(p.ttask, 8192);
-    p.qgrp = item_groups(p.qtask, 8192);
+    for (size_t g = 0; g < oq.size(); ++g) {
+        const int i = oq[g];
+        p.quad.insert(p.quad.end(), {cquad[i][0], cquad[i][1], cquad[i][2], cquad[i][3]});
+        p.nquad.push_back(cquad_cnt[i]);
+        Plan &lv = *p.levels[cquad_src[i].level];
+        const auto &lo = loc_of[cquad_src[i].level];
+        lv.quad.insert(lv.quad.end(), {lo[cquad[i][0]], lo[cquad[i][1]], lo[cquad[i][2]], lo[cquad[i][3]]});
+        lv.nquad.push_back(cquad_cnt[i]);
+        lv.gquad.push_back((int)g);
+    }
 
-    // slab size: shell fields + y-stage scratch of one slab within the budget
-    const int M = p.M;
-    const long long per_plane = (long long)nb * M * M * 4 + p.G_plane * 8;
-    long long budget = slab_budget_bytes();
-    int slab = (int)std::max<long long>(1, std::min<long long>(M, budget / std::max<long long>(1, per_plane)));
-    int nslabs = (M + slab - 1) / slab;
-    slab = (M + nslabs - 1) / nslabs;  // balance the slabs
-    p.slab = slab;
-    p.nslabs = nslabs;
-    set_slab_offsets(p);
+    // per level: tasks, slabs, buffers.  The per-slab stages of the levels run
+    // one after another on the plan's stream, so they share one set of
+    // scratch buffers sized for the largest level.
+    long long maxA = 1, maxG = 1, maxI = 1;
+    for (size_t l = 0; l < grids.size(); ++l) {
+        Plan &lv = *p.levels[l];
+        build_tasks(lv);
+        lv.tgrp = item_groups(lv.ttask, 8192);
+        lv.qgrp = item_groups(lv.qtask, 8192);
+        const int M = lv.M, lnb = lv.nbins;
+        const long long per_plane = (long long)lnb * M * M * 4 + lv.G_plane * 8;
+        const long long budget = slab_budget_bytes();
+        int slab = (int)std::max<long long>(1, std::min<long long>(M, budget / std::max<long long>(1, per_plane)));
+        const int nslabs = (M + slab - 1) / slab;
+        slab = (M + nslabs - 1) / nslabs;  // balance the slabs
+        lv.slab = slab;
+        lv.nslabs = nslabs;
+        set_slab_offsets(lv);
+        maxA = std::max(maxA, lv.A_elems);
+        maxG = std::max(maxG, lv.G_plane * lv.slab);
+        maxI = std::max(maxI, (long long)lnb * lv.slab * M * M);
+        lv.pbin.assign(lnb, -1);
+        for (int b = 0; b < lnb; ++b)
+            if (lc.bin_level[lv.gbin[b]] == (int)l) lv.pbin[b] = lv.gbin[b];
+    }
+    float2 *sA = (float2 *)p.dalloc((size_t)maxA * sizeof(float2));
+    float2 *sG = (float2 *)p.dalloc((size_t)maxG * sizeof(float2));
+    float *sI = (float *)p.dalloc((size_t)maxI * sizeof(float));
+    p.part_blocks = contract_blocks();
+    for (Plan *lp : p.levels) {
+        Plan &lv = *lp;
+        lv.d_box = p.d_box;
+        lv.d_A = sA;
+        lv.d_G = sG;
+        lv.d_I = sI;
+        lv.d_geom = upload(lv, lv.geom);
+        lv.d_tpb = upload(lv, lv.ttask.pb);
+        lv.d_tpc = upload(lv, lv.ttask.pc);
+        lv.d_tps = upload(lv, lv.ttask.pstart);
+        lv.d_tia = upload(lv, lv.ttask.ia);
+        lv.d_tout = upload(lv, lv.ttask.iout);
+        lv.d_tgrp = upload(lv, lv.tgrp);
+        lv.d_qpb = upload(lv, lv.qtask.pb);
+        lv.d_qpc = upload(lv, lv.qtask.pc);
+        lv.d_qps = upload(lv, lv.qtask.pstart);
+        lv.d_qia = upload(lv, lv.qtask.ia);
+        lv.d_qib = upload(lv, lv.qtask.ib);
+        lv.d_qout = upload(lv, lv.qtask.iout);
+        lv.d_qgrp = upload(lv, lv.qgrp);
+        lv.d_gtrip = upload(lv, lv.gtrip);
+        lv.d_gquad = upload(lv, lv.gquad);
+        lv.d_pbin = upload(lv, lv.pbin);
+        const int ntl = (int)lv.ntri.size(), nql = (int)lv.nquad.size();
+        lv.part_blocks = p.part_blocks;
+        lv.d_tpart = (double *)lv.dalloc((size_t)lv.part_blocks * std::max(1, ntl) * sizeof(double));
+        lv.d_qpart = (double *)lv.dalloc((size_t)lv.part_blocks * std::max(1, nql) * sizeof(double));
+        lv.d_sumsq_part = (double *)lv.dalloc((size_t)lv.nbins * lv.M * zstage_row_groups(lv.M) * sizeof(double));
+    }
+    // the largest level stands for the plan in the single-grid queries
+    int top = 0;
+    for (size_t l = 1; l < grids.size(); ++l) top = (int)l;
+    p.M = p.levels.empty() ? N : p.levels[top]->M;
+    p.slab = p.levels.empty() ? 0 : p.levels[top]->slab;
+    p.nslabs = p.levels.empty() ? 0 : p.levels[top]->nslabs;
 
-    // per-field buffers
-    p.d_geom = upload(p, p.geom);
+    // per-field buffers of the root
     p.d_field = (float *)p.dalloc((size_t)N * N * N * sizeof(float));
     FBS_CUDA(cudaStreamCreateWithFlags(&p.copy_stream, cudaStreamNonBlocking));
     FBS_CUDA(cudaEventCreateWithFlags(&p.ev_field_ready, cudaEventDisableTiming));
@@ -552,30 +713,8 @@ static void create_plan(Plan &p, const double *edges) {
     *p.h_err = 0;
     p.d_zbuf = (float2 *)p.dalloc((size_t)N * N * p.box.Dz * sizeof(float2));
     p.d_ybuf = (float2 *)p.dalloc((size_t)N * p.box.D * p.box.Dz * sizeof(float2));
-    p.d_A = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.A_elems) * sizeof(float2));
-    p.d_G = (float2 *)p.dalloc((size_t)std::max<long long>(1, p.G_plane * p.slab) * sizeof(float2));
-    p.d_I = (float *)p.dalloc((size_t)nb * p.slab * M * M * sizeof(float));
-    // work lists
-    p.d_tpb = upload(p, p.ttask.pb);
-    p.d_tpc = upload(p, p.ttask.pc);
-    p.d_tps = upload(p, p.ttask.pstart);
-    p.d_tia = upload(p, p.ttask.ia);
-    p.d_tout = upload(p, p.ttask.iout);
-    p.d_tgrp = upload(p, p.tgrp);
-    p.d_qpb = upload(p, p.qtask.pb);
-    p.d_qpc = upload(p, p.qtask.pc);
-    p.d_qps = upload(p, p.qtask.pstart);
-    p.d_qia = upload(p, p.qtask.ia);
-    p.d_qib = upload(p, p.qtask.ib);
-    p.d_qout = upload(p, p.qtask.iout);
-    p.d_qgrp = upload(p, p.qgrp);
-    // accumulators and outputs
     const int ntrip = (int)p.ntri.size(), nquad = (int)p.nquad.size();
-    p.part_blocks = contract_blocks();
-    p.d_tpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, ntrip) * sizeof(double));
-    p.d_qpart = (double *)p.dalloc((size_t)p.part_blocks * std::max(1, nquad) * sizeof(double));
     p.d_sumsq = (double *)p.dalloc(nb * sizeof(double));
-    p.d_sumsq_part = (double *)p.dalloc((size_t)nb * M * zstage_row_groups(M) * sizeof(double));
     p.d_tnum = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
     p.d_qnum = (double *)p.dalloc(std::max(1, nquad) * sizeof(double));
     p.d_B = (double *)p.dalloc(std::max(1, ntrip) * sizeof(double));
@@ -603,42 +742,45 @@ static void run_field(Plan &p, const float *field, bool quads) {
         d_in = p.d_field;
     }
     const bool tc = p.precision != FBS_PREC_FP32;
-    p.fused_active = quads && tc && tc_fused_usable(p);
-    zero_partials(p, quads);
-    if (p.precision != FBS_PREC_FP32 && tc_error_flag(p))
-        FBS_CUDA(cudaMemsetAsync(tc_error_flag(p), 0, sizeof(int), p.stream));
+    if (tc) FBS_CUDA(cudaMemsetAsync(p.d_errbuf, 0, sizeof(int), p.stream));
     launch_forward(p, d_in);
     if (staged) {
         FBS_CUDA(cudaEventRecord(p.ev_field_free, p.stream));
         p.field_free_recorded = true;
     }
-    launch_inverse_x(p, false);
-    const int M = p.M;
-    const long long plane = (long long)M * M;
-    for (int s = 0; s < p.nslabs; ++s) {
-        const int x0 = s * p.slab;
-        const int nx = std::min(p.slab, M - x0);
-        if (nx <= 0) break;
-        launch_inverse_yz_slab(p, x0, nx, p.d_I);
-        const long long npts = (long long)nx * plane;
-        const long long stride = (long long)p.slab * plane;
-        if (p.fused_active) {
-            launch_contract_tc_fused(p, p.d_I, npts, stride);
-            continue;
-        }
-        if (tc)
-            launch_contract_tc(p, p.d_I, npts, stride, false);
-        else
-            launch_contract_fp32(p, p.d_I, npts, stride, false);
-        if (quads) {
-            // quadruplets on the tensor cores when the inner pairs fit one MMA (N <= 256)
-            if (tc && tc_quads_usable(p))
-                launch_contract_tc(p, p.d_I, npts, stride, true);
+    for (Plan *lp : p.levels) {
+        Plan &lv = *lp;
+        lv.fused_active = quads && tc && tc_fused_usable(lv);
+        zero_partials(lv, quads);
+        launch_inverse_x(lv, false);
+        const int M = lv.M;
+        const long long plane = (long long)M * M;
+        for (int s = 0; s < lv.nslabs; ++s) {
+            const int x0 = s * lv.slab;
+            const int nx = std::min(lv.slab, M - x0);
+            if (nx <= 0) break;
+            launch_inverse_yz_slab(lv, x0, nx, lv.d_I);
+            const long long npts = (long long)nx * plane;
+            const long long stride = (long long)lv.slab * plane;
+            if (lv.fused_active) {
+                launch_contract_tc_fused(lv, lv.d_I, npts, stride);
+                continue;
+            }
+            if (tc)
+                launch_contract_tc(lv, lv.d_I, npts, stride, false);
             else
-                launch_contract_fp32(p, p.d_I, npts, stride, true);
+                launch_contract_fp32(lv, lv.d_I, npts, stride, false);
+            if (quads) {
+                // quadruplets on the tensor cores when the inner pairs fit one MMA (N <= 256)
+                if (tc && tc_quads_usable(lv))
+                    launch_contract_tc(lv, lv.d_I, npts, stride, true);
+                else
+                    launch_contract_fp32(lv, lv.d_I, npts, stride, true);
+            }
         }
+        launch_level_reduce(lv, quads);
     }
-    launch_reduce_and_normalise(p, quads);
+    launch_normalise(p, quads);
 }
 
 // A tensor-core wait that gave up leaves a flag on the device; the outputs
@@ -794,6 +936,11 @@ void fbs_plan_free(fbs_plan *plan) {
     if (plan->copy_stream) cudaStreamSynchronize(plan->copy_stream);
     cudaGetLastError();
     free_tc_state(*plan);
+    for (Plan *lv : plan->levels) {
+        free_tc_state(*lv);
+        delete lv;
+    }
+    plan->levels.clear();
     for (void *ptr : plan->allocs) cudaFree(ptr);
     budget_release(plan->dev_bytes);
     if (plan->h_err) cudaFreeHost(plan->h_err);
@@ -843,33 +990,44 @@ fbs_status fbs_plan_set_precision(fbs_plan *plan, int precision) {
         return FBS_ERR_ARG;
     }
     plan->precision = precision;
+    for (Plan *lv : plan->levels) lv->precision = precision;
     return FBS_OK;
 }
 
+static bool set_plan_option(Plan *plan, int option, int value);
+
 fbs_status fbs_plan_set_option(fbs_plan *plan, int option, int value) {
     if (!plan) return FBS_ERR_ARG;
+    if (!set_plan_option(plan, option, value)) {
+        set_error("unknown option or value");
+        return FBS_ERR_ARG;
+    }
+    for (Plan *lv : plan->levels) set_plan_option(lv, option, value);
+    return FBS_OK;
+}
+
+static bool set_plan_option(Plan *plan, int option, int value) {
     if (option == FBS_OPT_TC_WIDE && (value == 0 || value == 1)) {
         plan->tc_wide = value;
-        return FBS_OK;
+        return true;
     }
     if (option == FBS_OPT_TC_ROLES && value >= 0 && value <= 2) {
         plan->tc_roles = value;
-        return FBS_OK;
+        return true;
     }
     if (option == FBS_OPT_TC_CHUNK && value >= 0 && value <= 2) {
         plan->tc_chunk = value;
-        return FBS_OK;
+        return true;
     }
     if (option == FBS_OPT_TC_PAIRS && (value == 0 || value == 1)) {
         plan->tc_pairs = value;
-        return FBS_OK;
+        return true;
     }
     if (option == FBS_OPT_TC_WAIT_LIMIT && value >= 0) {
         plan->tc_wait_limit = value;
-        return FBS_OK;
+        return true;
     }
-    set_error("unknown option or value");
-    return FBS_ERR_ARG;
+    return false;
 }
 
 fbs_status fbs_plan_set_stream(fbs_plan *plan, void *stream) {
@@ -878,6 +1036,7 @@ fbs_status fbs_plan_set_stream(fbs_plan *plan, void *stream) {
     plan->flush_times();
     FBS_CUDA(cudaStreamSynchronize(plan->stream));
     plan->stream = (cudaStream_t)stream;
+    for (Plan *lv : plan->levels) lv->stream = plan->stream;
     return FBS_OK;
     FBS_GUARD_END
 }
@@ -984,6 +1143,36 @@ double fbs_plan_create_ms(const fbs_plan *plan) { return plan ? plan->create_ms 
 double fbs_plan_count_margin(const fbs_plan *plan) { return plan ? plan->count_margin : -1.0; }
 
 int fbs_plan_eval_grid(const fbs_plan *plan) { return plan ? plan->M : FBS_ERR_ARG; }
+
+fbs_status fbs_plan_item_levels(const fbs_plan *plan, int32_t *trip_level, int32_t *quad_level) {
+    if (!plan) return FBS_ERR_ARG;
+    for (size_t l = 0; l < plan->levels.size(); ++l) {
+        const Plan &lv = *plan->levels[l];
+        if (trip_level)
+            for (int g : lv.gtrip) trip_level[g] = (int32_t)l;
+        if (quad_level)
+            for (int g : lv.gquad) quad_level[g] = (int32_t)l;
+    }
+    return FBS_OK;
+}
+
+int fbs_plan_num_levels(const fbs_plan *plan) { return plan ? (int)plan->levels.size() : FBS_ERR_ARG; }
+
+fbs_status fbs_plan_level(const fbs_plan *plan, int i, int *M, int *nbins, int *ntrip, int *nquad,
+                          int *slab_planes, int *nslabs) {
+    if (!plan || i < 0 || i >= (int)plan->levels.size()) {
+        set_error("bad plan or level index");
+        return FBS_ERR_ARG;
+    }
+    const Plan &lv = *plan->levels[i];
+    if (M) *M = lv.M;
+    if (nbins) *nbins = lv.nbins;
+    if (ntrip) *ntrip = (int)lv.ntri.size();
+    if (nquad) *nquad = (int)lv.nquad.size();
+    if (slab_planes) *slab_planes = lv.slab;
+    if (nslabs) *nslabs = lv.nslabs;
+    return FBS_OK;
+}
 
 int fbs_plan_slab_planes(const fbs_plan *plan) { return plan ? plan->slab : FBS_ERR_ARG; }
 

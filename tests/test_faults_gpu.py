@@ -84,7 +84,7 @@ def test_device_budget_refuses_a_plan_with_no_leak():
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     try:
-        fbs.fbs_set_device_budget(before + (1 << 20))  # 1 MiB more than the plans hold now
+        fbs.fbs_set_device_budget(before + 4096)  # 4 KiB more than the plans hold now
         with pytest.raises(fbs.FbsError) as e:
             fbs.Plan(N, L, edges, precision="bf16x3")
         assert e.value.status == FBS_ERR_OOM

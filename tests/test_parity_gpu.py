@@ -12,7 +12,7 @@ import pytest
 import fields
 import oracle
 import paper_1705_06284_gb300 as fbs
-from gpu_util import check_bispectrum, gate_mask, rel_err, run
+from gpu_util import TOL, check_bispectrum, check_trispectrum, gate_mask, rel_err, run
 
 pytestmark = pytest.mark.gpu
 
@@ -208,12 +208,12 @@ def test_plane_waves_closed_form_on_gpu():
     (48, 60.0, 6, "bf16x3", False, 36),
 ])
 def test_reduced_grid_matches_full_grid(N, L, nb, precision, quads, M):
-    """The default plan evaluates the shell fields on M^3 (M > 3R, or 4R with
+    """A SINGLE_GRID plan evaluates the shell fields on M^3 (M > 3R, or 4R with
     quadruplets) and rescales the sums by (N/M)^3; a FULL_GRID plan evaluates
     on N^3.  Both must agree with each other and with the oracle."""
     edges = fields.linear_edges(N, L, nb)
     f32 = _field("quadratic", N, 11).astype(np.float32)
-    with fbs.Plan(N, L, edges, precision=precision, trispectrum=quads) as red, \
+    with fbs.Plan(N, L, edges, precision=precision, trispectrum=quads, single_grid=True) as red, \
             fbs.Plan(N, L, edges, precision=precision, trispectrum=quads, full_grid=True) as full:
         assert red.eval_grid == M
         assert full.eval_grid == N
@@ -295,3 +295,47 @@ def test_pinned_host_outputs_filled_once_the_stream_passes():
         torch.cuda.current_stream().synchronize()
         assert np.array_equal(Bh.numpy(), Bd.cpu().numpy())
         assert np.array_equal(Ph.numpy(), Pd.cpu().numpy(), equal_nan=True)
+
+
+@pytest.mark.parametrize("N,L,kind,nb,precision,quads", [
+    (64, 200.0, "log", 12, "fp32", False),
+    (64, 200.0, "log", 12, "bf16x3", False),
+    (96, 96.0, "lin", 10, "bf16x3", False),
+    (48, 60.0, "log", 8, "bf16x3", True),
+    (48, 60.0, "log", 8, "fp32", True),
+])
+def test_levels_match_single_grid_and_oracle(monkeypatch, N, L, kind, nb, precision, quads):
+    """Items summed on per-level grids (each M above the item's degree
+    R_a + R_b + R_c (+ R_d)) give the same B, P, T as one grid for all, and the
+    oracle's.  FBS_LEVEL_COST=0 lets these small plans split into levels."""
+    import torch
+    monkeypatch.setenv("FBS_LEVEL_COST", "0")
+    edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
+    f32 = _field("quadratic", N, 61).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    with fbs.Plan(N, L, edges, precision=precision, trispectrum=quads) as lv, \
+            fbs.Plan(N, L, edges, precision=precision, trispectrum=quads, single_grid=True) as one:
+        assert len(lv.levels) >= 2 and len(one.levels) == 1
+        assert np.array_equal(lv.triplets, one.triplets) and np.array_equal(lv.N_tri, one.N_tri)
+        assert sum(l["ntrip"] for l in lv.levels) == lv.ntrip
+        if quads:
+            assert np.array_equal(lv.quads, one.quads) and np.array_equal(lv.N_quad, one.N_quad)
+            assert sum(l["nquad"] for l in lv.levels) == lv.nquad
+            Tl, Bl, Pl = lv.trispectrum(f)
+            To, Bo, Po = one.trispectrum(f)
+        else:
+            Bl, Pl = lv.bispectrum(f)
+            Bo, Po = one.bispectrum(f)
+        lv.check()
+        one.check()
+        Bl, Pl, Bo, Po = (x.cpu().numpy() for x in (Bl, Pl, Bo, Po))
+        ok = np.isfinite(Po)
+        assert np.array_equal(np.isnan(Pl), np.isnan(Po))
+        assert np.all(rel_err(Pl[ok], Po[ok]) < 2e-5)
+        gmax, amax, ng = check_bispectrum(lv, Bl, Pl, f32, L, edges, precision)
+        if quads:
+            tol = TOL[precision] if precision in TOL else 1e-3
+            m, n = check_trispectrum(lv, Tl.cpu().numpy(), f32, L, edges, tol)
+            print("levels %s T: %d gated, max rel %.2e" % ([l["M"] for l in lv.levels], n, m))
+    print("levels %s (N=%d %s %s): %d gated, max rel %.2e" % ([l["M"] for l in lv.levels], N, kind,
+                                                              precision, ng, gmax))
