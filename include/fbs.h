@@ -211,6 +211,30 @@ fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double 
 fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double *B, double *P);
 
 /*
+ * fbs_trispectrum_connected -- the connected trispectrum Tc of every closed
+ * quadruplet, with T, B and P of the same evaluation (FBS_FLAG_TRISPECTRUM
+ * plans).  The paper's four-shell estimator (Eq. Jeong_gen with p = 4) sums
+ * every closed quadruple of modes; for shells a = b, c = d that includes the
+ * paired quadruples (m1 + m2 = 0, or another pair of modes summing to zero),
+ * whose terms |D(m1)|^2 |D(m3)|^2 carry the disconnected P x P part of the
+ * four-point function.  Tc leaves every paired quadruple out:
+ *   Tc = V^3/N_pix^4 (sum_n I_a I_b I_c I_d / N_pix - paired sum) / N_conn
+ * with the paired sum from per-shell sums over the spectrum (inclusion-
+ * exclusion over the three pairings; a = b < c = d: S2_a S2_c, a = b = c = d:
+ * 3 S2^2 - 3 S4 + the self-conjugate modes' D^4, S2/S4 the shell's sums of
+ * |D|^2 and |D|^4) and N_conn the unpaired count (fbs_plan_quads_connected).
+ * A Gaussian field's Tc has zero mean.  Tc is NaN where a quadruplet has no
+ * unpaired quadruple.  Tc[nquad], T[nquad], B[ntrip], P[nbins]: device or
+ * host or NULL; same stream semantics as fbs_bispectrum.
+ */
+fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double *Tc, double *T, double *B,
+                                     double *P);
+
+/* Unpaired ordered quadruple counts N_conn[nquad] of the connected
+ * trispectrum (FP64; exact integers where the quadruple counts are). */
+fbs_status fbs_plan_quads_connected(const fbs_plan *plan, double *nconn);
+
+/*
  * fbs_plan_sums -- the raw FP64 real-space sums of the last call, for
  * diagnostics and tests: num_trip[ntrip] = sum_n I_a I_b I_c,
  * num_quad[nquad] = sum_n I_a I_b I_c I_d, sumsq[nbins] = sum_n I_b^2.  Host

@@ -92,7 +92,7 @@ def _load():
                                                    i32p, i32p]
             lib.oracle_direct_trispectrum.restype = None
             lib.oracle_direct_trispectrum.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
-                                                      dp, dp, i64p]
+                                                      dp, dp, i64p, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -311,9 +311,15 @@ def closed_triplets(N: int, L: float, edges) -> np.ndarray:
     return abc[flag > 0]
 
 
-def direct_trispectrum(field, L: float, edges):
+def direct_trispectrum(field, L: float, edges, connected: bool = False):
     """Trispectrum by direct measurement (p = 4 case of Eq. gen_Nspec3) over
     ordered quadruples; O(|M|^3), tiny grids only.
+
+    ``connected``: leave out every quadruple in which a pair of its modes sums
+    to zero modulo N (the pairing terms, which carry the disconnected P x P
+    parts of a Gaussian field); the paper is silent on this part of the
+    four-shell estimator, and this exclusion is the reading taken for the
+    connected trispectrum.
 
     Returns dict with ``quads`` (nq, 4) a<=b<=c<=d with N_quad > 0,
     ``N_quad``, ``T`` = V^3/N_pix^4 * num/N_quad, ``num``, ``num_im``.
@@ -331,7 +337,7 @@ def direct_trispectrum(field, L: float, edges):
     cnt = np.zeros(nb ** 4, dtype=np.int64)
     lib.oracle_direct_trispectrum(N, _p(re, ctypes.c_double), _p(im, ctypes.c_double), nb,
                                   _p(thr, ctypes.c_int64), _p(num, ctypes.c_double),
-                                  _p(numi, ctypes.c_double), _p(cnt, ctypes.c_int64))
+                                  _p(numi, ctypes.c_double), _p(cnt, ctypes.c_int64), 1 if connected else 0)
     sh = (nb,) * 4
     num, numi, cnt = num.reshape(sh), numi.reshape(sh), cnt.reshape(sh)
     quads, n, ni, c = [], [], [], []
@@ -351,6 +357,47 @@ def direct_trispectrum(field, L: float, edges):
     T = (V ** 3 / npix ** 4) * n / np.maximum(c, 1)
     return {"quads": np.array(quads, dtype=np.int32).reshape(-1, 4), "N_quad": c, "T": T,
             "num": n, "num_im": np.array(ni), "ordered_num": num, "ordered_cnt": cnt}
+
+
+def pairing_terms(D: np.ndarray, bins: np.ndarray, quads):
+    """Sum and count of the paired ordered quadruples of each (a<=b<=c<=d).
+
+    A closed quadruple (m1, m2, m3, m4) in S_a x S_b x S_c x S_d is paired when
+    m1 + m2, m1 + m3 or m2 + m3 is 0 modulo N (with the closure, the three
+    pairings).  Since |-m| = |m|, m1 + m2 = 0 needs a = b and then c = d; the
+    other two pairings need a = b = c = d.  By inclusion-exclusion over the
+    three events, with S2_b = sum_{S_b} |D|^2, S4_b = sum_{S_b} |D|^4 and Z_b
+    the self-conjugate modes of S_b (m = -m mod N, where D is real):
+      a = b < c = d :  sum = S2_a S2_c,                count = |S_a| |S_c|
+      a = b = c = d :  sum = 3 S2^2 - 3 S4 + sum_Z D^4, count = 3|S|^2 - 3|S| + |Z|
+      otherwise     :  0.
+    Returns (sums, counts) as FP64 arrays."""
+    N = D.shape[0]
+    q = np.asarray(quads, dtype=np.int64).reshape(-1, 4)
+    nb = max(int(bins.max()) + 1, int(q.max()) + 1 if len(q) else 0)
+    a2 = D.real ** 2 + D.imag ** 2
+    sel = bins >= 0
+    S = np.bincount(bins[sel].ravel(), minlength=nb).astype(np.float64)
+    S2 = np.bincount(bins[sel].ravel(), weights=a2[sel].ravel(), minlength=nb)
+    S4 = np.bincount(bins[sel].ravel(), weights=(a2 * a2)[sel].ravel(), minlength=nb)
+    # self-conjugate modes: every component 0 or N/2
+    idx = np.arange(N)
+    sc1 = (idx == 0) | (2 * idx == N)
+    sc = sc1[:, None, None] & sc1[None, :, None] & sc1[None, None, :] & sel
+    Zc = np.bincount(bins[sc].ravel(), minlength=nb).astype(np.float64)
+    Z4 = np.bincount(bins[sc].ravel(), weights=(D.real ** 4)[sc].ravel(), minlength=nb)
+    sums = np.zeros(len(q))
+    cnts = np.zeros(len(q))
+    for i, (a, b, c, d) in enumerate(q):
+        if a != b or c != d:
+            continue
+        if a != c:
+            sums[i] = S2[a] * S2[c]
+            cnts[i] = S[a] * S[c]
+        else:
+            sums[i] = 3 * S2[a] ** 2 - 3 * S4[a] + Z4[a]
+            cnts[i] = 3 * S[a] ** 2 - 3 * S[a] + Zc[a]
+    return sums, cnts
 
 
 def power_spectrum(field, L: float, edges):
@@ -405,7 +452,10 @@ def fft_estimator(field, L: float, edges, triplets=None, quads=None, bins_needed
     non-empty bins.  Returns a dict with the sums, the counts rounded from
     sum N..N / N_pix, the estimates, ``M`` (the cancellation-free scale of
     each triplet, V^2/N_pix^3 sum_x |I_a I_b I_c| / sum_x N_a N_b N_c) and,
-    for quadruplets, ``qM`` (the same with four fields and V^3/N_pix^4).
+    for quadruplets, ``qM`` (the same with four fields and V^3/N_pix^4), and
+    the connected trispectrum ``Tc`` = V^3/N_pix^4 (sum_x prod I / N_pix -
+    paired sum) / N_conn, ``N_conn`` the unpaired quadruple count (see
+    :func:`pairing_terms`), with its cancellation-free scale ``Tc_M``.
     """
     field = np.asarray(field, dtype=np.float64)
     N = field.shape[0]
@@ -472,4 +522,12 @@ def fft_estimator(field, L: float, edges, triplets=None, quads=None, bins_needed
         with np.errstate(invalid="ignore", divide="ignore"):
             out["T"] = (V ** 3 / npix ** 4) * qn / qden
             out["qM"] = (V ** 3 / npix ** 4) * qmag / qden
+        # connected part: the sum of Eq. gen_Nspec4 over closed quadruples is
+        # sum_x prod I / N_pix; remove the paired quadruples (pairing_terms)
+        psum, pcnt = pairing_terms(D, bins, qd)
+        out["pair_sum"], out["pair_cnt"] = psum, pcnt
+        out["N_conn"] = qden / npix - pcnt
+        with np.errstate(invalid="ignore", divide="ignore"):
+            out["Tc"] = (V ** 3 / npix ** 4) * (qn / npix - psum) / out["N_conn"]
+            out["Tc_M"] = (V ** 3 / npix ** 4) * qmag / npix / out["N_conn"]
     return out

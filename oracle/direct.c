@@ -234,13 +234,22 @@ void oracle_direct_triplets(int N, const double *re, const double *im, int nbins
     free(order); free(fill); free(start); free(M);
 }
 
+/* m1 + m2 = 0 (mod N) in every component. */
+static int opposite(const mode_t_ *a, const mode_t_ *b, int N) {
+    return wrap(a->mx + b->mx, N) == 0 && wrap(a->my + b->my, N) == 0 && wrap(a->mz + b->mz, N) == 0;
+}
+
 /*
  * All-triples direct trispectrum over ordered bin quadruples (tiny grids):
  * m4 = -(m1+m2+m3) (mod N).  num, num_im, cnt have nbins^4 entries.
+ * connected != 0: leave out every quadruple in which some pair of modes sums
+ * to zero (m1+m2, m1+m3 or m2+m3 = 0 mod N; with the closure these are all
+ * three pairings).  Those are the only terms a Gaussian field's expectation
+ * keeps (Wick pairings, the P x P parts); what remains is the connected part.
  */
 void oracle_direct_trispectrum(int N, const double *re, const double *im, int nbins,
                                const int64_t *thr, double *num, double *num_im,
-                               int64_t *cnt) {
+                               int64_t *cnt, int connected) {
     mode_t_ *M = NULL;
     int64_t nm = collect_modes(N, nbins, thr, &M);
     const int64_t nb4 = (int64_t)nbins * nbins * nbins * nbins;
@@ -259,8 +268,10 @@ void oracle_direct_trispectrum(int N, const double *re, const double *im, int nb
                 const mode_t_ b = M[j];
                 double pr = re[a.idx] * re[b.idx] - im[a.idx] * im[b.idx];
                 double pi = re[a.idx] * im[b.idx] + im[a.idx] * re[b.idx];
+                const int ab = connected && opposite(&a, &b, N);
                 for (int64_t k = 0; k < nm; ++k) {
                     const mode_t_ c = M[k];
+                    if (connected && (ab || opposite(&a, &c, N) || opposite(&b, &c, N))) continue;
                     int x = wrap(-(a.mx + b.mx + c.mx), N);
                     int y = wrap(-(a.my + b.my + c.my), N);
                     int z = wrap(-(a.mz + b.mz + c.mz), N);

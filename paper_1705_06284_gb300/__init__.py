@@ -75,6 +75,8 @@ _SIGS = [
     ("fbs_bispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("fbs_trispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("fbs_plan_sums", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("fbs_trispectrum_connected", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("fbs_plan_quads_connected", ctypes.c_int, [_vp, _vp]),
     ("fbs_num_kernel_classes", ctypes.c_int, []),
     ("fbs_kernel_class_name", ctypes.c_char_p, [ctypes.c_int]),
     ("fbs_plan_kernel_times", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
@@ -228,6 +230,8 @@ class Plan:
             _check(Lb.fbs_plan_level(_vp(self._h), i, *[ctypes.byref(x) for x in v]))
             self.levels.append(dict(zip(("M", "nbins", "ntrip", "nquad", "slab_planes", "nslabs"),
                                         (x.value for x in v))))
+        self.N_conn = np.zeros(self.nquad, dtype=np.float64)
+        _check(Lb.fbs_plan_quads_connected(_vp(self._h), self.N_conn.ctypes.data))
         self.trip_level = np.zeros(self.ntrip, dtype=np.int32)
         self.quad_level = np.zeros(self.nquad, dtype=np.int32)
         _check(Lb.fbs_plan_item_levels(_vp(self._h), self.trip_level.ctypes.data, self.quad_level.ctypes.data))
@@ -300,6 +304,18 @@ class Plan:
         pp, _k3 = _ptr(P)
         fbs_trispectrum(self._h, fp, tp, bp, pp)
         return T, B, P
+
+    def trispectrum_connected(self, field, Tc=None, T=None, B=None, P=None):
+        """(Tc, T, B, P): the connected trispectrum (paired quadruples left
+        out) with the raw T, B and P of the same evaluation."""
+        self._check_field(field)
+        Tc = self._outputs(field, self.nquad) if Tc is None else Tc
+        T = self._outputs(field, self.nquad) if T is None else T
+        B = self._outputs(field, self.ntrip) if B is None else B
+        P = self._outputs(field, self.nbins) if P is None else P
+        ptrs = [_ptr(x) for x in (field, Tc, T, B, P)]
+        _check(lib().fbs_trispectrum_connected(_vp(self._h), *[_vp(p) for p, _ in ptrs]))
+        return Tc, T, B, P
 
     def _check_field(self, f):
         n = self.N

@@ -178,6 +178,101 @@ __global__ void normalise_kernel(const double *__restrict__ tnum, const int64_t 
     if (T && i < nquad) T[i] = bad ? nan("") : cT * qnum[i] / (npix * nq[i]);
 }
 
+// ------------------------------------------------------------------ connected trispectrum
+// Per-shell moments of the spectrum box (the forward output): for bin b
+// (blockIdx.y) and one of gridDim.x chunks of its sub-box |m_j| <= R_b,
+//   S2 = sum |D|^2, S4 = sum |D|^4 over the shell's modes,
+//   Z4 = sum D^4 over its self-conjugate modes (m = -m mod N, D real there).
+// The box holds mz >= 0 only: a mode with 0 < mz < N/2 stands for itself and
+// its conjugate at -mz (weight 2); the planes mz = 0 and mz = N/2 hold both.
+// One partial per (bin, chunk, moment), from a fixed-shape block reduction.
+__global__ void __launch_bounds__(256) shell_moments_kernel(const float2 *__restrict__ box, BoxGeom bg,
+                                                            const BinGeom *__restrict__ gb,
+                                                            double *__restrict__ part) {
+    __shared__ double red[3][256];
+    const int b = blockIdx.y, N = bg.N;
+    const BinGeom g = gb[b];
+    double s2 = 0.0, s4 = 0.0, z4 = 0.0;
+    if (!g.empty) {
+        const long long n = (long long)g.Db * g.Db * g.Dzb;
+        const long long c0 = n * blockIdx.x / gridDim.x, c1 = n * (blockIdx.x + 1) / gridDim.x;
+        for (long long e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+            const int jz = (int)(e % g.Dzb);
+            const long long r = e / g.Dzb;
+            const int jy = (int)(r % g.Db), jx = (int)(r / g.Db);
+            const int mx = box_freq(jx, g.Db, N), my = box_freq(jy, g.Db, N), mz = jz;
+            const long long s = (long long)mx * mx + (long long)my * my + (long long)mz * mz;
+            if (s < g.thr_lo || s >= g.thr_hi) continue;
+            const float2 d = box[((long long)box_index(mx, bg.D) * bg.D + box_index(my, bg.D)) * bg.Dz + mz];
+            const double a2 = (double)d.x * d.x + (double)d.y * d.y;
+            const double w = (mz == 0 || 2 * mz == N) ? 1.0 : 2.0;
+            s2 += w * a2;
+            s4 += w * a2 * a2;
+            const bool scx = mx == 0 || 2 * mx == -N, scy = my == 0 || 2 * my == -N;
+            if (scx && scy && (mz == 0 || 2 * mz == N)) z4 += (double)d.x * d.x * d.x * d.x;
+        }
+    }
+    red[0][threadIdx.x] = s2;
+    red[1][threadIdx.x] = s4;
+    red[2][threadIdx.x] = z4;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 3; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[((long long)b * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// Connected trispectrum of each closed quadruplet (a <= b <= c <= d): the sum
+// over its closed quadruples with the paired ones (m_i + m_j = 0 mod N for
+// two of the modes) left out, by inclusion-exclusion over the three pairings:
+//   a = b < c = d : paired sum S2_a S2_c
+//   a = b = c = d : 3 S2^2 - 3 S4 + Z4
+//   otherwise     : 0,
+// Tc = V^3/N_pix^4 (qnum/N_pix - paired sum) / N_conn, N_conn the unpaired
+// count (plan time).  NaN where a wait timed out or no unpaired quadruple is left.
+__global__ void connected_kernel(const double *__restrict__ qnum, const int *__restrict__ quad,
+                                 const double *__restrict__ nconn, int nquad,
+                                 const double *__restrict__ mom_part, int chunks, double L, int N,
+                                 double *__restrict__ Tc, const int *__restrict__ err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nquad) return;
+    const double V = L * L * L, npix = (double)N * N * N;
+    const double cT = V * V * V / (npix * npix * npix * npix);
+    const int a = quad[4 * i], b = quad[4 * i + 1], c = quad[4 * i + 2], d = quad[4 * i + 3];
+    auto mom = [&](int bin, int k) {  // chunks summed in a fixed order
+        double s = 0.0;
+        for (int j = 0; j < chunks; ++j) s += mom_part[((long long)bin * chunks + j) * 3 + k];
+        return s;
+    };
+    double paired = 0.0;
+    if (a == b && c == d) {
+        if (a != c) {
+            paired = mom(a, 0) * mom(c, 0);
+        } else {
+            const double s2 = mom(a, 0);
+            paired = 3.0 * s2 * s2 - 3.0 * mom(a, 1) + mom(a, 2);
+        }
+    }
+    const bool bad = (err && *err) || !(nconn[i] > 0.0);
+    Tc[i] = bad ? nan("") : cT * (qnum[i] / npix - paired) / nconn[i];
+}
+
+void launch_connected(Plan &p, double *d_Tc) {
+    KTimer tm(p, KC_REDUCE);
+    const int chunks = 16;
+    dim3 grid(chunks, p.nbins);
+    shell_moments_kernel<<<grid, 256, 0, p.stream>>>(p.d_box, p.box, p.d_geom, p.d_mom_part);
+    FBS_CUDA(cudaGetLastError());
+    const int nq = (int)p.nquad.size();
+    if (nq == 0) return;
+    connected_kernel<<<(nq + 255) / 256, 256, 0, p.stream>>>(
+        p.d_qnum, p.d_quadtab, p.d_nconn, nq, p.d_mom_part, chunks, p.L, p.N, d_Tc,
+        p.precision != FBS_PREC_FP32 ? tc_error_flag(p) : nullptr);
+    FBS_CUDA(cudaGetLastError());
+}
+
 // ------------------------------------------------------------------ counts (FP64)
 // den[item] = sum over the octant 0 <= x,y,z <= N/2 of w(x)w(y)w(z) prod N_i,
 // w(v) = 1 for v in {0, N/2} and 2 otherwise (the reflections m_j -> -m_j map

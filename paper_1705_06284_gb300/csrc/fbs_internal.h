@@ -111,6 +111,8 @@ bool tc_fused_usable(Plan &p);
 void launch_contract_tc_fused(Plan &p, const float *islab, long long npts, long long slab_stride);
 void launch_level_reduce(Plan &level, bool quads);
 void launch_normalise(Plan &root, bool quads);
+// Connected trispectrum of the last evaluation into d_Tc[nquad] (root).
+void launch_connected(Plan &root, double *d_Tc);
 std::vector<int> fast_grids();  // grids with compile-time-radix kernels for every inverse stage
 void zero_partials(Plan &p, bool quads);
 std::vector<int> item_groups(const TaskList &t, int cap);
@@ -135,6 +137,13 @@ struct Plan {
     std::vector<int> pbin;        // level only: global bin of local bin b if its P is taken here, else -1
     int *d_gtrip = nullptr, *d_gquad = nullptr, *d_pbin = nullptr;
     int *d_errbuf = nullptr;      // root only: [0] this evaluation's wait-timeout code, [1] sticky copy
+    // root only, connected trispectrum: per-bin geometry on the input grid (for
+    // the shell moments of the spectrum box), unpaired quadruple counts,
+    // the quadruplet table, moment partials [nbins][16][3], output staging
+    std::vector<long long> selfconj;  // self-conjugate modes of each bin
+    std::vector<double> nconn;
+    double *d_nconn = nullptr, *d_mom_part = nullptr, *d_Tc = nullptr;
+    int *d_quadtab = nullptr;
     Plan &root() { return root_ ? *root_ : *this; }
     int N = 0;
     double L = 0;

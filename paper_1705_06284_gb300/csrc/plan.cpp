@@ -210,6 +210,7 @@ static void enumerate_shells(Plan &p, std::vector<long long> &mn, std::vector<lo
     const long long top = p.thr[nb];
     int Rmax = std::min(isqrt_floor(top - 1), N / 2);
     p.shell.assign(nb, 0);
+    p.selfconj.assign(nb, 0);
     mn.assign(nb, -1);
     mx.assign(nb, -1);
     std::vector<int> lut;  // bin of each |m|^2 < top
@@ -227,6 +228,9 @@ static void enumerate_shells(Plan &p, std::vector<long long> &mn, std::vector<lo
                 int b = lut[s];
                 if (b < 0) continue;
                 p.shell[b] += 1;
+                // m = -m (mod N): every component 0 or -N/2
+                if ((x == 0 || 2 * x == -N) && (y == 0 || 2 * y == -N) && (z == 0 || 2 * z == -N))
+                    p.selfconj[b] += 1;
                 if (mn[b] < 0 || s < mn[b]) mn[b] = s;
                 if (s > mx[b]) mx[b] = s;
             }
@@ -723,6 +727,36 @@ static void create_plan(Plan &p, const double *edges) {
     p.d_ntri = upload(p, p.ntri);
     p.d_nquad = upload(p, p.nquad);
     p.d_shell = upload(p, p.shell);
+    // every bin on the input grid (the shell moments of the spectrum box)
+    p.geom.assign(nb, BinGeom{});
+    for (int b = 0; b < nb; ++b) {
+        BinGeom &g = p.geom[b];
+        g.thr_lo = p.thr[b];
+        g.thr_hi = p.thr[b + 1];
+        g.empty = p.shell[b] == 0;
+        g.Rb = g.empty ? 0 : bin_R(p, b);
+        g.Db = (2 * g.Rb + 1 > N) ? N : 2 * g.Rb + 1;
+        g.Dzb = std::min(g.Rb, N / 2) + 1;
+    }
+    p.d_geom = upload(p, p.geom);
+    // unpaired quadruple counts of the connected trispectrum: N_quad minus the
+    // paired ones (a = b < c = d: |S_a||S_c|; a = b = c = d: 3|S|^2 - 3|S| + Z)
+    p.nconn.assign(nquad, 0.0);
+    for (int i = 0; i < nquad; ++i) {
+        const int32_t *q = &p.quad[4 * i];
+        double c = 0.0;
+        if (q[0] == q[1] && q[2] == q[3]) {
+            const double sa = (double)p.shell[q[0]], sc = (double)p.shell[q[2]];
+            c = q[0] != q[2] ? sa * sc : 3.0 * sa * sa - 3.0 * sa + (double)p.selfconj[q[0]];
+        }
+        p.nconn[i] = p.nquad[i] - c;
+    }
+    if (nquad > 0) {
+        p.d_nconn = upload(p, p.nconn);
+        p.d_quadtab = upload(p, p.quad);
+        p.d_Tc = (double *)p.dalloc((size_t)nquad * sizeof(double));
+    }
+    p.d_mom_part = (double *)p.dalloc((size_t)nb * 16 * 3 * sizeof(double));
     FBS_CUDA(cudaStreamSynchronize(p.stream));
 }
 
@@ -1082,6 +1116,39 @@ fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double
     }
     return FBS_OK;
     FBS_GUARD_END
+}
+
+fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double *Tc, double *T, double *B,
+                                     double *P) {
+    if (!plan || !field) {
+        set_error("plan or field is NULL");
+        return FBS_ERR_ARG;
+    }
+    if (!(plan->flags & FBS_FLAG_TRISPECTRUM)) {
+        set_error("plan was created without FBS_FLAG_TRISPECTRUM");
+        return FBS_ERR_STATE;
+    }
+    FBS_GUARD_BEGIN
+    poll_device_errors(*plan);
+    run_field(*plan, field, true);
+    if (!plan->nquad.empty()) launch_connected(*plan, plan->d_Tc);
+    bool host = false;
+    copy_out(*plan, Tc, plan->d_Tc, plan->nquad.size(), host);
+    copy_out(*plan, T, plan->d_T, plan->nquad.size(), host);
+    copy_out(*plan, B, plan->d_B, plan->ntri.size(), host);
+    copy_out(*plan, P, plan->d_P, plan->nbins, host);
+    if (host) {
+        FBS_CUDA(cudaStreamSynchronize(plan->stream));
+        check_device_errors(*plan);
+    }
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_plan_quads_connected(const fbs_plan *plan, double *nconn) {
+    if (!plan) return FBS_ERR_ARG;
+    if (nconn && !plan->nconn.empty()) memcpy(nconn, plan->nconn.data(), plan->nconn.size() * sizeof(double));
+    return FBS_OK;
 }
 
 fbs_status fbs_plan_sums(fbs_plan *plan, double *num_trip, double *num_quad, double *sumsq) {

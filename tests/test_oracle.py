@@ -495,3 +495,113 @@ def test_count_modes_equals_shell_sizes():
     for N, L, nb in [(12, 50.0, 5), (16, 30.0, 9)]:
         thr = oracle.thresholds(fields.log_edges(N, L, nb), L)
         assert oracle.count_modes(N, thr) == int(oracle.shell_sizes(N, thr).sum())
+
+
+# ---------------------------------------------------------------- connected trispectrum
+def _brute_quads(N, thr, D, connected):
+    """Pure-Python ordered quadruple sums over binned modes, pairings left out
+    when `connected` (m_i + m_j = 0 mod N for any two of the four modes)."""
+    nb = len(thr) - 1
+    f = np.fft.fftfreq(N, d=1.0 / N).astype(int)
+    modes = []
+    for ix in range(N):
+        for iy in range(N):
+            for iz in range(N):
+                m2 = f[ix] ** 2 + f[iy] ** 2 + f[iz] ** 2
+                for b in range(nb):
+                    if thr[b] <= m2 < thr[b + 1]:
+                        modes.append(((ix, iy, iz), b))
+    key = dict(modes)
+    num = np.zeros((nb,) * 4)
+    cnt = np.zeros((nb,) * 4, dtype=np.int64)
+    neg = lambda m: ((-m[0]) % N, (-m[1]) % N, (-m[2]) % N)
+    for m1, b1 in modes:
+        for m2, b2 in modes:
+            for m3, b3 in modes:
+                m4 = ((-m1[0] - m2[0] - m3[0]) % N, (-m1[1] - m2[1] - m3[1]) % N, (-m1[2] - m2[2] - m3[2]) % N)
+                if m4 not in key:
+                    continue
+                ms = (m1, m2, m3, m4)
+                if connected and any(ms[j] == neg(ms[i]) for i in range(4) for j in range(i + 1, 4)):
+                    continue
+                k = (b1, b2, b3, key[m4])
+                cnt[k] += 1
+                num[k] += (D[m1] * D[m2] * D[m3] * D[m4]).real
+    return num, cnt
+
+
+def test_connected_trispectrum_matches_brute_force():
+    N, L = 6, 2 * math.pi
+    f = fields.lognormal(N, 0.7, -1.0, seed=21)
+    edges = [0.9, 1.2, 1.5, 1.8]  # |m|^2 in {1}, {2}, {3}: includes a = b = c = d and a = b < c = d
+    thr = oracle.thresholds(edges, L)
+    D = oracle.spectrum(f)
+    bn, bc = _brute_quads(N, thr, D, connected=True)
+    t = oracle.direct_trispectrum(f, L, edges, connected=True)
+    assert np.array_equal(t["ordered_cnt"], bc)
+    assert np.allclose(t["ordered_num"], bn, rtol=1e-12, atol=1e-12 * np.max(np.abs(bn)))
+    raw = oracle.direct_trispectrum(f, L, edges)
+    assert np.any(raw["ordered_cnt"] > t["ordered_cnt"])  # pairings were present and removed
+
+
+@pytest.mark.parametrize("N,L,kind,seed", [(8, 40.0, "lin", 22), (6, 13.0, "full", 23), (8, 2 * math.pi, "fine", 24)])
+def test_connected_direct_equals_fft_minus_pairings(N, L, kind, seed):
+    """The two routes to the connected trispectrum: the direct sum with the
+    paired quadruples left out, and the FFT estimator (Eq. Jeong_gen, p = 4)
+    minus the pairing terms from S2, S4 and the self-conjugate modes."""
+    f = fields.lognormal(N, 0.8, -1.5, seed=seed)
+    if kind == "lin":
+        edges = fields.linear_edges(N, L, 3)
+    elif kind == "full":
+        kf = 2 * math.pi / L
+        edges = [0.0, kf * 1.2, kf * 1.8, kf * 5.5]  # every mode, DC and Nyquist corners included
+    else:
+        edges = [0.9, 1.1, 1.5, 1.8, 2.1]  # single |m|^2 shells {1}, {2}, {3}, {4}
+    t = oracle.direct_trispectrum(f, L, edges, connected=True)
+    allq = oracle.direct_trispectrum(f, L, edges)["quads"]
+    g = oracle.fft_estimator(f, L, edges, triplets=[], quads=allq)
+    conn = np.array([tuple(q) in {tuple(x) for x in t["quads"]} for q in allq])
+    assert np.allclose(g["N_conn"][~conn], 0.0)
+    assert np.array_equal(np.rint(g["N_conn"][conn]).astype(np.int64), t["N_quad"])
+    scale = np.max(np.abs(g["qnum"])) / N ** 3
+    assert np.max(np.abs(g["qnum"][conn] / N ** 3 - g["pair_sum"][conn] - t["num"])) <= 1e-10 * scale
+    assert np.allclose(g["Tc"][conn], t["T"], rtol=1e-8, atol=1e-10 * np.max(np.abs(g["T"])))
+
+
+def test_connected_kurtosis_sum_rule():
+    # With shells covering every mode, the unpaired ordered quadruples add up
+    # to N_pix^3 sum delta^4 - 3 N_pix^2 (sum delta^2)^2 + 3 sum |D|^4 - sum_Z D^4
+    # (Parseval for the paired sums), i.e. the fourth cumulant on the grid.
+    N, L = 6, 13.0
+    f = fields.lognormal(N, 0.9, -1.0, seed=25)
+    kf = 2 * math.pi / L
+    edges = [0.0, kf * 1.2, kf * 1.8, kf * 5.5]
+    t = oracle.direct_trispectrum(f, L, edges, connected=True)
+    D = oracle.spectrum(f)
+    npix = float(N ** 3)
+    a2 = np.abs(D) ** 2
+    i = np.arange(N)
+    sc1 = (i == 0) | (2 * i == N)
+    sc = sc1[:, None, None] & sc1[None, :, None] & sc1[None, None, :]
+    rhs = npix ** 3 * np.sum(f ** 4) - 3 * npix ** 2 * np.sum(f ** 2) ** 2 + 3 * np.sum(a2 ** 2) \
+        - np.sum(D.real[sc] ** 4)
+    lhs = np.sum(t["ordered_num"])
+    assert abs(lhs - rhs) <= 1e-10 * npix ** 3 * np.sum(f ** 4)
+
+
+def test_connected_trispectrum_gaussian_null():
+    # For a Gaussian field every closed quadruple's expectation is a sum of
+    # pairings, so the connected part has zero mean while the raw T of
+    # (a, a, c, c) carries the P_a P_c part.
+    N, L = 16, 50.0
+    edges = fields.linear_edges(N, L, 3)
+    raw, conn = [], []
+    for seed in range(6):
+        g = fields.gaussian(N, -1.0, 1.0, seed=300 + seed)
+        qd = [(0, 0, 1, 1), (0, 0, 2, 2), (1, 1, 2, 2), (1, 1, 1, 1), (2, 2, 2, 2)]
+        e = oracle.fft_estimator(g, L, edges, triplets=[], quads=qd)
+        raw.append(e["T"])
+        conn.append(e["Tc"])
+    raw, conn = np.array(raw), np.array(conn)
+    assert np.all(raw.mean(0) > 0)
+    assert np.all(np.abs(conn.mean(0)) < 0.1 * raw.mean(0))
