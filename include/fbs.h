@@ -350,6 +350,43 @@ fbs_status fbs_triple_sums_noalloc(const float *fields, int nfields, long long b
                                    long long npts, const int32_t *abc, int ntrip, double *num,
                                    void *cuda_stream);
 
+/*
+ * Fine bins, then (k1, k2, cos theta) cells.  The paper advises measuring with
+ * one-pixel bins and binning further afterwards (Sec. 3.1), and shows the
+ * bispectrum against theta, the triangle's internal angle between k1 and k2
+ * (k3 = -k1 - k2 closes it):  cos theta = (k1^2 + k2^2 - k3^2) / (2 k1 k2),
+ * clamped to [-1, 1] (the representative sides of a closed triplet can break
+ * the triangle inequality by up to a bin width: the degenerate end).
+ * A rebin regroups a plan's closed triplets: each distinct assignment of a
+ * triplet's three bins to the sides (k1, k2, k3), with the bins'
+ * representative k, is one configuration; a cell (K1, K2, MU) collects the
+ * ordered closed triples (count N_tri, FP64 sum) of every configuration with
+ * k1 in k bin K1, k2 in k bin K2 and cos theta in bin MU, and its estimate is
+ * the direct estimator over that union of triangle sets:
+ *   B_cell = V^2/N_pix^3 sum num / (N_pix sum N_tri)    (Eq. bi_direct).
+ *
+ * fbs_rebin_create
+ *   plan     : the fine-bin plan (its closed triplets are read; the rebin stays
+ *              valid while the plan lives).
+ *   k_rep    : host double[nbins], the k of each fine bin (physical units), or
+ *              NULL for the midpoint of each bin's edges.
+ *   k_edges  : host double[nk+1] ascending, the cells' k bins (both k1 and k2).
+ *   mu_edges : host double[nmu+1] ascending, the cells' cos theta bins.
+ *   Cells are ordered (K1 * nk + K2) * nmu + MU; nk * nk * nmu <= 2^26.
+ *   Configurations outside the edges are left out.
+ * fbs_rebin_bispectrum -- after an evaluation on the plan (fbs_bispectrum or
+ *   fbs_trispectrum): B[nk*nk*nmu] (device or host; NaN for empty cells), on
+ *   the plan's stream, with the same stream semantics as fbs_bispectrum.
+ * fbs_rebin_counts -- ordered triple count of every cell (host int64).
+ * fbs_rebin_free -- release it (NULL is a no-op).
+ */
+typedef struct fbs_rebin fbs_rebin;
+fbs_status fbs_rebin_create(fbs_rebin **out, const fbs_plan *plan, const double *k_rep, const double *k_edges,
+                            int nk, const double *mu_edges, int nmu);
+fbs_status fbs_rebin_bispectrum(fbs_rebin *rebin, fbs_plan *plan, double *B);
+fbs_status fbs_rebin_counts(const fbs_rebin *rebin, int64_t *counts);
+void fbs_rebin_free(fbs_rebin *rebin);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *fbs_last_error(void);
 

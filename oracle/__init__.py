@@ -400,6 +400,56 @@ def pairing_terms(D: np.ndarray, bins: np.ndarray, quads):
     return sums, cnts
 
 
+def rebinned_bispectrum(field, L: float, edges, k_edges, mu_edges, k_rep=None):
+    """Fine bins, then (k1, k2, cos theta) cells (Sec. 3.1: bin finely, then
+    rebin; theta is the triangle's internal angle between k1 and k2, the
+    reading of Fig. theta_illus taken here: cos theta = (k1^2 + k2^2 -
+    k3^2)/(2 k1 k2)).  Every ordered bin triple (a, b, c) with closed triples
+    is the configuration k1 = k_rep[a], k2 = k_rep[b], k3 = k_rep[c]; a cell
+    sums the ordered direct sums and counts (Eq. bi_direct) of the
+    configurations inside it.  The representative sides of a closed triplet
+    can break the triangle inequality by up to a bin width; cos theta is then
+    clamped to [-1, 1] (the degenerate, squeezed or folded, end).  ``k_rep`` defaults to the midpoint of each fine
+    bin's edges on the integer shells (sqrt(thr[b]) and sqrt(thr[b+1]) in k_f
+    units).  Returns (B, counts, num) of shape (nk, nk, nmu); empty cells NaN."""
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    thr = thresholds(edges, L)
+    nb = len(thr) - 1
+    kf = k_fundamental(L)
+    if k_rep is None:
+        k_rep = 0.5 * kf * (np.sqrt(thr[:-1].astype(np.float64)) + np.sqrt(thr[1:].astype(np.float64)))
+    ke = np.asarray(k_edges, dtype=np.float64)
+    me = np.asarray(mu_edges, dtype=np.float64)
+    nk, nmu = len(ke) - 1, len(me) - 1
+    num, _, cnt, _ = direct_sums(field, thr)
+    cn = np.zeros((nk, nk, nmu))
+    cc = np.zeros((nk, nk, nmu), dtype=np.int64)
+
+    def cell(v, e):
+        if not (e[0] <= v < e[-1]):
+            return -1
+        return int(np.searchsorted(e, v, side="right")) - 1
+    for a in range(nb):
+        for b in range(nb):
+            for c in range(nb):
+                if cnt[a, b, c] == 0:
+                    continue
+                k1, k2, k3 = k_rep[a], k_rep[b], k_rep[c]
+                K1, K2 = cell(k1, ke), cell(k2, ke)
+                mu = min(1.0, max(-1.0, (k1 * k1 + k2 * k2 - k3 * k3) / (2 * k1 * k2)))
+                MU = cell(mu, me)
+                if K1 < 0 or K2 < 0 or MU < 0:
+                    continue
+                cn[K1, K2, MU] += num[a, b, c]
+                cc[K1, K2, MU] += cnt[a, b, c]
+    V = float(L) ** 3
+    npix = float(N) ** 3
+    with np.errstate(invalid="ignore", divide="ignore"):
+        B = np.where(cc > 0, (V * V / npix ** 3) * cn / np.maximum(cc, 1), np.nan)
+    return B, cc, cn
+
+
 def power_spectrum(field, L: float, edges):
     """Power spectrum by direct measurement: P_b = V/N_pix^2 * <|D(m)|^2>
     over the modes of shell b (the textbook estimator the paper compares

@@ -91,6 +91,10 @@ _SIGS = [
     ("fbs_plan_level", ctypes.c_int, [_vp, ctypes.c_int] + [ctypes.POINTER(ctypes.c_int)] * 6),
     ("fbs_plan_item_levels", ctypes.c_int, [_vp, _vp, _vp]),
     ("fbs_plan_check", ctypes.c_int, [_vp]),
+    ("fbs_rebin_create", ctypes.c_int, [ctypes.POINTER(_vp), _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int]),
+    ("fbs_rebin_bispectrum", ctypes.c_int, [_vp, _vp, _vp]),
+    ("fbs_rebin_counts", ctypes.c_int, [_vp, _vp]),
+    ("fbs_rebin_free", None, [_vp]),
     ("fbs_set_device_budget", ctypes.c_int, [ctypes.c_int64]),
     ("fbs_device_bytes_in_use", ctypes.c_int64, []),
     ("fbs_triple_sums_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
@@ -349,3 +353,48 @@ class Plan:
         _check(lib().fbs_plan_kernel_times(_vp(self._h), ms.ctypes.data, cnt.ctypes.data,
                                            1 if reset else 0))
         return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(kernel_class_names())}
+
+
+class Rebin:
+    """Cells (k1 bin, k2 bin, cos theta bin) over a fine-bin plan's triplets
+    (see fbs_rebin_create).  ``k_rep``: the k of each fine bin (default: the
+    midpoint of its edges)."""
+
+    def __init__(self, plan, k_edges, mu_edges, k_rep=None):
+        ke = np.ascontiguousarray(k_edges, dtype=np.float64)
+        me = np.ascontiguousarray(mu_edges, dtype=np.float64)
+        kr = None if k_rep is None else np.ascontiguousarray(k_rep, dtype=np.float64)
+        self.nk, self.nmu = len(ke) - 1, len(me) - 1
+        self.plan = plan
+        h = _vp()
+        _check(lib().fbs_rebin_create(ctypes.byref(h), _vp(plan.handle), _vp(kr.ctypes.data if kr is not None else 0),
+                                      _vp(ke.ctypes.data), self.nk, _vp(me.ctypes.data), self.nmu))
+        self._h = h.value
+        self.counts = np.zeros(self.nk * self.nk * self.nmu, dtype=np.int64)
+        _check(lib().fbs_rebin_counts(_vp(self._h), self.counts.ctypes.data))
+        self.counts = self.counts.reshape(self.nk, self.nk, self.nmu)
+
+    def bispectrum(self, out=None):
+        """B of every cell from the plan's last evaluation, shape (nk, nk, nmu)."""
+        if out is None:
+            out = np.empty(self.nk * self.nk * self.nmu)
+        p, _k = _ptr(out)
+        _check(lib().fbs_rebin_bispectrum(_vp(self._h), _vp(self.plan.handle), _vp(p)))
+        return out.reshape(self.nk, self.nk, self.nmu)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fbs_rebin_free(_vp(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libfbs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["plan.cpp", "pair_cover.cpp", "levels.cpp", "fft.cu", "contract.cu", "contract_tc.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "pair_cover.cpp", "levels.cpp", "fft.cu", "contract.cu", "contract_tc.cu", "rebin.cu",
+           "noalloc.cu"]
 
 
 def _nvcc() -> str:

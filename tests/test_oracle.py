@@ -605,3 +605,63 @@ def test_connected_trispectrum_gaussian_null():
     raw, conn = np.array(raw), np.array(conn)
     assert np.all(raw.mean(0) > 0)
     assert np.all(np.abs(conn.mean(0)) < 0.1 * raw.mean(0))
+
+
+# ---------------------------------------------------------------- (k1, k2, theta) cells
+def test_rebinned_bispectrum_matches_brute_force():
+    # every closed ordered triple of modes, put in its cell by its bins'
+    # representative k, in plain Python
+    N, L = 8, 2 * math.pi
+    f = fields.lognormal(N, 0.6, -1.0, seed=31)
+    edges = [1.0, 1.5, 2.2, 2.9, 3.4]
+    thr = oracle.thresholds(edges, L)
+    k_rep = np.array([1.2, 1.8, 2.5, 3.1])
+    ke = [1.0, 2.0, 3.5]
+    me = [-1.0, -0.5, 0.0, 0.5, 1.0001]
+    B, cc, cn = oracle.rebinned_bispectrum(f, L, edges, ke, me, k_rep=k_rep)
+    D = oracle.spectrum(f)
+    fr = np.fft.fftfreq(N, d=1.0 / N).astype(int)
+    modes = {}
+    for ix in range(N):
+        for iy in range(N):
+            for iz in range(N):
+                m2 = fr[ix] ** 2 + fr[iy] ** 2 + fr[iz] ** 2
+                for b in range(len(thr) - 1):
+                    if thr[b] <= m2 < thr[b + 1]:
+                        modes[(ix, iy, iz)] = b
+    bn = np.zeros_like(cn)
+    bc = np.zeros_like(cc)
+    for m1, a in modes.items():
+        for m2, b in modes.items():
+            m3 = ((-m1[0] - m2[0]) % N, (-m1[1] - m2[1]) % N, (-m1[2] - m2[2]) % N)
+            if m3 not in modes:
+                continue
+            k1, k2, k3 = k_rep[a], k_rep[b], k_rep[modes[m3]]
+            mu = min(1.0, max(-1.0, (k1 * k1 + k2 * k2 - k3 * k3) / (2 * k1 * k2)))
+            K1 = np.searchsorted(ke, k1, side="right") - 1
+            K2 = np.searchsorted(ke, k2, side="right") - 1
+            MU = np.searchsorted(me, mu, side="right") - 1
+            if 0 <= K1 < 2 and 0 <= K2 < 2 and 0 <= MU < 4:
+                bc[K1, K2, MU] += 1
+                bn[K1, K2, MU] += (D[m1] * D[m2] * D[m3]).real
+    assert np.array_equal(cc, bc)
+    assert np.allclose(cn, bn, rtol=1e-12, atol=1e-12 * np.max(np.abs(bn)))
+    assert cc.sum() > 0 and np.isnan(B[cc == 0]).all()
+
+
+def test_rebinned_single_cell_is_the_count_weighted_mean():
+    # one cell holding every configuration: the direct estimator over all
+    # ordered closed triples, i.e. the N_tri-weighted mean of the fine B
+    N, L = 12, 40.0
+    f = fields.bubbles(N, 2.0, 0.4, seed=32)
+    edges = fields.linear_edges(N, L, 4)
+    B, cc, cn = oracle.rebinned_bispectrum(f, L, edges, [0.0, 10.0], [-1.0, 1.0001])
+    d = oracle.direct_bispectrum(f, L, edges)
+    cnt, num = d["ordered_cnt"], d["ordered_num"]
+    V, npix = L ** 3, float(N ** 3)
+    assert cc[0, 0, 0] == cnt.sum()
+    assert abs(B[0, 0, 0] - (V * V / npix ** 3) * num.sum() / cnt.sum()) <= 1e-12 * abs(B[0, 0, 0])
+    # and the weighted mean over sorted triplets with their permutation multiplicity
+    w = sum(len(set(itertools.permutations(t))) * n * b for t, n, b in zip(d["triplets"], d["N_tri"], d["B"]))
+    c = sum(len(set(itertools.permutations(t))) * n for t, n in zip(d["triplets"], d["N_tri"]))
+    assert abs(B[0, 0, 0] - w / c) <= 1e-12 * abs(B[0, 0, 0])
