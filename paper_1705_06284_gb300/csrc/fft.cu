@@ -474,12 +474,19 @@ __global__ void __launch_bounds__(T *LP) inv_z_fast_kernel(const float2 *__restr
 }
 
 // Fast z-stage configurations: (N, threads per line, lines per CTA, radices).
+// Threads per line divide N/R of every stage; threads per CTA are whole warps
+// (the sum-of-squares reduction shuffles across full warps).
 #define FBS_ZFAST_LIST(X)            \
     X(64, 8, 32, 8, 8, 1, 1)         \
+    X(72, 3, 32, 8, 3, 3, 1)         \
     X(96, 4, 32, 8, 4, 3, 1)         \
+    X(108, 9, 32, 4, 3, 3, 3)        \
     X(128, 16, 16, 8, 4, 4, 1)       \
+    X(144, 6, 16, 8, 2, 3, 3)        \
     X(192, 8, 16, 8, 8, 3, 1)        \
+    X(216, 9, 32, 8, 3, 3, 3)        \
     X(256, 32, 8, 8, 8, 4, 1)        \
+    X(288, 12, 8, 8, 4, 3, 3)        \
     X(384, 16, 8, 8, 4, 4, 3)        \
     X(512, 64, 4, 8, 8, 8, 1)
 
@@ -543,13 +550,18 @@ void upload_eval_twiddles(Plan &p) {
 }
 
 // Transform lengths with compile-time radices (the rest use run-time factors).
-#define FBS_RADICES(X) \
-    X(512, 8, 8, 8)    \
-    X(384, 8, 8, 2, 3) \
-    X(256, 8, 8, 4)    \
-    X(192, 8, 8, 3)    \
-    X(128, 8, 8, 2)    \
-    X(96, 8, 4, 3)     \
+#define FBS_RADICES(X)    \
+    X(512, 8, 8, 8)       \
+    X(384, 8, 8, 2, 3)    \
+    X(288, 8, 4, 3, 3)    \
+    X(256, 8, 8, 4)       \
+    X(216, 8, 3, 3, 3)    \
+    X(192, 8, 8, 3)       \
+    X(144, 8, 2, 3, 3)    \
+    X(128, 8, 8, 2)       \
+    X(108, 4, 3, 3, 3)    \
+    X(96, 8, 4, 3)        \
+    X(72, 8, 3, 3)        \
     X(64, 8, 8)
 
 std::vector<int> fast_grids() {
@@ -642,13 +654,10 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
         KTimer t(p, KC_INV_Y);
         // compile-time radices for the common evaluation grids, run-time otherwise
         auto k = inv_y_kernel<float>;
-        if (N == 512) k = inv_y_kernel<float, 8, 8, 8>;
-        if (N == 384) k = inv_y_kernel<float, 8, 8, 2, 3>;
-        if (N == 256) k = inv_y_kernel<float, 8, 8, 4>;
-        if (N == 192) k = inv_y_kernel<float, 8, 8, 3>;
-        if (N == 128) k = inv_y_kernel<float, 8, 8, 2>;
-        if (N == 96) k = inv_y_kernel<float, 8, 4, 3>;
-        if (N == 64) k = inv_y_kernel<float, 8, 8>;
+#define FBS_PICK(n, ...) \
+    if (N == n) k = inv_y_kernel<float, __VA_ARGS__>;
+        FBS_RADICES(FBS_PICK)
+#undef FBS_PICK
         if (getenv("FBS_GENERIC_Y")) k = inv_y_kernel<float>;
         allow_smem(k, sm);
         dim3 grid((max_dzb(p, 0, p.nbins) + nl - 1) / nl, nx, p.nbins);

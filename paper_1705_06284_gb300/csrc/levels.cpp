@@ -2,6 +2,7 @@
 #include "levels.h"
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 namespace fbs {
@@ -25,31 +26,45 @@ int popc(const std::vector<uint64_t> &v) {
     return n;
 }
 
-// Work model of one level on grid M: every bin is inverse transformed
-// (weight 4 per bin and point on grids with compile-time-radix stages, 8
-// otherwise) and every contraction row costs 1 per point: outer pairs ~0.7 of
-// the distinct (b, c) pairs after the pair cover, the single-bin rows, inner
-// pairs ~0.4 after the quadruplet cover; plus a fixed cost for the level's
-// launches.  The weights are the measured per-point times of these stages
-// (inverse stages ~2.7 ps per bin and point, contraction ~0.65 ps per row and
-// point at 512^3), rounded; `per_level` (1e8 by default, about 60 us of
-// contraction) stands for a level's launches.
+// Work model of one level on grid M, in units of one contraction row over one
+// point (~0.62 ps at 512^3): every bin is inverse transformed (4.5 units per
+// point on grids with compile-time-radix stages, 12.7 otherwise); the
+// tensor-core pass costs a full 128-row tile per point for every tile of
+// outer pairs (~0.7 of the distinct (b, c) pairs remain after the pair cover)
+// plus one unit per inner row (the single bins, and ~0.4 of the distinct
+// inner pairs after the quadruplet cover); plus `per_level` for the level's
+// launches (1e8 by default, about 60 us).  The weights are the measured
+// per-point times of these stages at 512^3 (inverse stages 2.8 ps per bin and
+// point, 7.9 ps on grids with run-time factors; 78 ps per tile and 0.66 ps per
+// inner row in the contraction), rounded.
 double level_cost(int M, const Sets &s, const std::vector<int> &fast, double per_level) {
     const double pts = (double)M * M * M;
     const int nbins = __builtin_popcountll(s.bins[0]) + __builtin_popcountll(s.bins[1]);
-    const double rows = 0.7 * popc(s.outer) + nbins + 0.4 * popc(s.inner);
+    const int outer = popc(s.outer), inner_pairs = popc(s.inner);
+    const double tiles = outer > 0 ? std::ceil(0.7 * outer / 128.0) : 0.0;
+    const double rows = 128.0 * tiles + (outer > 0 ? nbins + 0.4 * inner_pairs : 0.0);
     const bool f = std::find(fast.begin(), fast.end(), M) != fast.end();
-    return pts * ((f ? 4.0 : 8.0) * nbins + rows) + per_level;
+    return pts * ((f ? 4.5 : 12.7) * nbins + rows) + per_level;
 }
 
 }  // namespace
 
 LevelChoice choose_levels(int N, int nb, const std::vector<int> &R, std::vector<LevelItem> items, int single_M,
-                          const std::vector<int> &fast, int max_levels, double per_level) {
+                          const std::vector<int> &fast, int max_levels, double per_level, int min_grid) {
     LevelChoice out;
+    std::vector<int> admissible;
+    for (int M = 8; M <= N; ++M) {
+        int m = M;
+        if (m % 2) continue;
+        while (m % 2 == 0) m /= 2;
+        while (m % 3 == 0) m /= 3;
+        if (m == 1) admissible.push_back(M);
+    }
+    const int floor_M = min_grid > 0 ? grid_above(admissible, min_grid - 1, N) : 0;
     std::vector<int> needs;
     for (auto &it : items) {
         if (single_M > 0) it.need = single_M;
+        it.need = std::max(it.need, floor_M);
         needs.push_back(it.need);
     }
     std::sort(needs.begin(), needs.end());
@@ -126,17 +141,9 @@ LevelChoice choose_levels(int N, int nb, const std::vector<int> &R, std::vector<
     }
     // a non-empty bin in no item still needs P: the lowest grid above 2 R
     // (a new level when every chosen grid is too small)
-    std::vector<int> admissible;
-    for (int M = 8; M <= N; ++M) {
-        int m = M;
-        if (m % 2) continue;
-        while (m % 2 == 0) m /= 2;
-        while (m % 3 == 0) m /= 3;
-        if (m == 1) admissible.push_back(M);
-    }
     for (int b = 0; b < nb; ++b) {
         if (R[b] < 0 || out.bin_level[b] >= 0) continue;
-        const int need = single_M > 0 ? single_M : grid_above(admissible, 2 * R[b], N);
+        const int need = single_M > 0 ? single_M : std::max(floor_M, grid_above(admissible, 2 * R[b], N));
         int l = level_of(need);
         if (l == (int)out.grids.size()) {
             out.grids.push_back(need);

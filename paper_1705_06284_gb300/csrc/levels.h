@@ -35,9 +35,12 @@ int grid_above(const std::vector<int> &grids, int S, int N);
 // single_M > 0 every item and bin goes to that one grid.  `fast` lists the
 // grids with compile-time-radix inverse stages (cheaper in the model);
 // `per_level` is the model's fixed cost of a level (its launches), in the
-// units of one contraction row over one point.
+// units of one contraction row over one point.  No level grid is below
+// `min_grid` (rounded up to an admissible grid, at most N): a sum over fewer
+// points averages the per-product rounding of the split-precision
+// contraction over fewer terms.
 LevelChoice choose_levels(int N, int nb, const std::vector<int> &R, std::vector<LevelItem> items,
                           int single_M, const std::vector<int> &fast, int max_levels = 4,
-                          double per_level = 1e8);
+                          double per_level = 1e8, int min_grid = 0);
 
 }  // namespace fbs

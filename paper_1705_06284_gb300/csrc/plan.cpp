@@ -458,6 +458,8 @@ static long long slab_budget_bytes() {
 }
 
 // ---------------------------------------------------------------- levels
+static constexpr int kMinLevelGrid = 128;
+
 static Plan *new_level(Plan &root, int M) {
     Plan *lv = new Plan();
     lv->root_ = &root;
@@ -549,7 +551,12 @@ static void create_plan(Plan &p, const double *edges) {
     // plans split into levels too, as tests do)
     double per_level = 1e8;
     if (const char *e = getenv("FBS_LEVEL_COST")) per_level = atof(e);
-    const LevelChoice lc = choose_levels(N, nb, Rb, items, single_M, fast_grids(), 4, per_level);
+    // the smallest level grid (FBS_MIN_LEVEL_GRID overrides): BF16 split
+    // products carry ~2^-17 relative rounding each, so a level's sums must run
+    // over enough points for it to average out on cancelling items
+    int min_grid = kMinLevelGrid;
+    if (const char *e = getenv("FBS_MIN_LEVEL_GRID")) min_grid = atoi(e);
+    const LevelChoice lc = choose_levels(N, nb, Rb, items, single_M, fast_grids(), 4, per_level, min_grid);
     const std::vector<int> &grids = lc.grids;
     for (int M : grids) new_level(p, M);
     std::vector<std::vector<int>> lt(grids.size()), lq(grids.size());  // candidate (global) items per level

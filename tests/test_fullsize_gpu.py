@@ -3,7 +3,8 @@
 At 256^3 and 512^3 the all-pairs oracle is out of reach, so:
 * the closed-triplet set is compared with the oracle's witness search;
 * exact counts and B are compared on sampled triplets whose shells are small
-  enough for the direct sum (Eq. bi_direct) triplet by triplet;
+  enough for the direct sum (Eq. bi_direct) triplet by triplet, gated on the
+  cancellation-free scale M of the FP64 fields of their (few) bins;
 * the wide high-k shells (up to 1.8M modes, where the FP32 inverse transforms
   carry their largest error) are compared with the oracle's FP64 FFT
   estimator restricted to a few top bins, gated on the cancellation-free
@@ -26,24 +27,34 @@ from gpu_util import TOL, gate_mask, rel_err
 pytestmark = pytest.mark.gpu
 
 
-def _sample(plan, shell, budget=4e7, n=40, seed=0):
-    """Triplets with |S_a||S_b| <= budget, spread over the list."""
+def _sample(plan, shell, budget=4e7, n=40, maxbins=10, seed=0):
+    """Triplets with |S_a||S_b| <= budget (direct sums triplet by triplet),
+    drawn at random but only over a few distinct bins (the FP64 FFT estimator
+    then needs only their fields for the cancellation-free scale)."""
     cand = [i for i, (a, b, c) in enumerate(plan.triplets) if shell[a] * shell[b] <= budget]
     rng = np.random.default_rng(seed)
-    if len(cand) > n:
-        cand = sorted(rng.choice(cand, size=n, replace=False).tolist())
-    return cand
+    rng.shuffle(cand)
+    out, bins = [], set()
+    for i in cand:
+        t = set(int(v) for v in plan.triplets[i])
+        if len(bins | t) <= maxbins:
+            out.append(i)
+            bins |= t
+        if len(out) == n:
+            break
+    return sorted(out)
 
 
-def _run_fullsize(N, L, edges, field64, precision, nsample=40):
+def _run_fullsize(N, L, edges, field64, precision, nsample=40, maxbins=10):
     import torch
     f32 = field64.astype(np.float32)
     f64 = f32.astype(np.float64)
     with fbs.Plan(N, L, edges, precision=precision) as plan:
         B, P = plan.bispectrum(torch.from_numpy(f32).cuda())
-        torch.cuda.synchronize()
+        plan.check()
         B, P = B.cpu().numpy(), P.cpu().numpy()
         trip, ntri, shell = plan.triplets.copy(), plan.N_tri.copy(), plan.shell.copy()
+        lev = np.array([plan.levels[i]["M"] for i in plan.trip_level])
         # the full closed-triplet set equals the oracle's
         closed = oracle.closed_triplets(N, L, edges)
         assert np.array_equal(trip, closed)
@@ -51,16 +62,18 @@ def _run_fullsize(N, L, edges, field64, precision, nsample=40):
         assert np.array_equal(shell, S)
         ok = S > 0
         assert np.all(rel_err(P[ok], Pref[ok]) < 1e-4)
-        idx = _sample(plan, shell, n=nsample)
+        idx = _sample(plan, shell, n=nsample, maxbins=maxbins)
         assert len(idx) >= 10
         Bref, num, numi, cnt = oracle.direct_triplets(f64, L, edges, trip[idx])
         assert np.array_equal(cnt, ntri[idx])
+        # the cancellation-free scale of each sampled triplet from the FP64 fields
+        M = oracle.fft_estimator(f64, L, edges, triplets=trip[idx])["M"]
+        g = gate_mask(Bref, M, ntri[idx])
         r = rel_err(B[idx], Bref)
-        big = ntri[idx] >= 100
-        # no cancellation-free scale from the sampled sums: gate on |B| relative
-        # to the sampled triplets' typical magnitude
-        scale = np.median(np.abs(Bref[big])) if big.any() else 0.0
-        g = big & (np.abs(Bref) >= 1e-3 * scale)
+        for m in sorted(set(lev[idx].tolist())):
+            sel = g & (lev[idx] == m)
+            if sel.any():
+                print("   level M=%d: %d gated, max rel %.2e" % (m, int(sel.sum()), float(r[sel].max())))
         assert g.sum() >= 5
         assert np.all(r[g] < TOL[precision]), (float(r[g].max()))
         return float(r[g].max()), int(g.sum())
