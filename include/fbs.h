@@ -111,6 +111,27 @@ enum {
 fbs_status fbs_plan_create(fbs_plan **out, int N, double L, const double *edges, int nbins,
                            int precision, unsigned flags, void *cuda_stream);
 
+/*
+ * Plan-time counts carried between plans (and processes).  The FP64 count
+ * pass of fbs_plan_create depends only on (N, L, edges, flags); a caller that
+ * builds the same plan again (a server evicting and re-creating plans, a new
+ * process) can skip it:
+ * fbs_plan_export_counts -- serialise the plan's closed triplets and
+ *   quadruplets with their exact counts into buf (native byte order).  With
+ *   buf == NULL only *size is set; otherwise *size is the buffer's capacity on
+ *   entry (FBS_ERR_ARG and the needed size when too small) and the bytes
+ *   written on return.
+ * fbs_plan_create_from_counts -- fbs_plan_create with those results instead
+ *   of the count pass.  The blob must come from a plan with the same N, L,
+ *   integer bin thresholds and FBS_FLAG_TRISPECTRUM / FBS_FLAG_ALLOW_ALIASED
+ *   flags (FBS_ERR_ARG otherwise, no plan).  The plan is the same as one built
+ *   from scratch: same items, counts, levels and results.
+ */
+fbs_status fbs_plan_export_counts(const fbs_plan *plan, void *buf, int64_t *size);
+fbs_status fbs_plan_create_from_counts(fbs_plan **out, int N, double L, const double *edges, int nbins,
+                                       int precision, unsigned flags, void *cuda_stream, const void *counts,
+                                       int64_t size);
+
 /* fbs_plan_free -- release the plan and all its device memory (NULL is a no-op).
  * Synchronises the plan's stream first. */
 void fbs_plan_free(fbs_plan *plan);

@@ -64,6 +64,10 @@ _SIGS = [
                                        ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                                        ctypes.c_uint, _vp]),
     ("fbs_plan_free", None, [_vp]),
+    ("fbs_plan_export_counts", ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_int64)]),
+    ("fbs_plan_create_from_counts", ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double,
+                                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_uint, _vp, _vp, ctypes.c_int64]),
     ("fbs_plan_num_triplets", ctypes.c_int, [_vp]),
     ("fbs_plan_num_quads", ctypes.c_int, [_vp]),
     ("fbs_plan_triplets", ctypes.c_int, [_vp, _vp, _vp]),
@@ -131,14 +135,30 @@ def kernel_class_names():
 
 
 # ---------------------------------------------------------------- C-named calls
-def fbs_plan_create(N, L, edges, precision=FBS_PREC_FP32, flags=0, stream=None):
-    """Returns an opaque plan handle (int)."""
+def fbs_plan_create(N, L, edges, precision=FBS_PREC_FP32, flags=0, stream=None, counts=None):
+    """Returns an opaque plan handle (int).  ``counts``: bytes from
+    fbs_plan_export_counts of an equal plan (skips the plan-time count pass)."""
     e = np.ascontiguousarray(edges, dtype=np.float64)
     h = _vp()
-    _check(lib().fbs_plan_create(ctypes.byref(h), int(N), float(L),
-                                 e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(e) - 1,
-                                 int(precision), int(flags), _vp(stream or 0)))
+    ep = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if counts is None:
+        _check(lib().fbs_plan_create(ctypes.byref(h), int(N), float(L), ep, len(e) - 1,
+                                     int(precision), int(flags), _vp(stream or 0)))
+    else:
+        buf = ctypes.create_string_buffer(bytes(counts), len(counts))
+        _check(lib().fbs_plan_create_from_counts(ctypes.byref(h), int(N), float(L), ep, len(e) - 1,
+                                                 int(precision), int(flags), _vp(stream or 0),
+                                                 ctypes.cast(buf, _vp), len(counts)))
     return h.value
+
+
+def fbs_plan_export_counts(h):
+    """The plan's closed items and exact counts, serialised (bytes)."""
+    n = ctypes.c_int64(0)
+    _check(lib().fbs_plan_export_counts(_vp(h), None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().fbs_plan_export_counts(_vp(h), ctypes.cast(buf, _vp), ctypes.byref(n)))
+    return buf.raw[:n.value]
 
 
 def fbs_plan_free(h):
@@ -192,7 +212,7 @@ class Plan:
     """
 
     def __init__(self, N, L, edges, precision="fp32", trispectrum=False, allow_aliased=False,
-                 timing=False, stream=None, full_grid=False, single_grid=False):
+                 timing=False, stream=None, full_grid=False, single_grid=False, counts=None):
         flags = (FBS_FLAG_TRISPECTRUM if trispectrum else 0) | \
                 (FBS_FLAG_ALLOW_ALIASED if allow_aliased else 0) | (FBS_FLAG_TIMING if timing else 0) | \
                 (FBS_FLAG_FULL_GRID if full_grid else 0) | (FBS_FLAG_SINGLE_GRID if single_grid else 0)
@@ -207,7 +227,7 @@ class Plan:
         self.N, self.L = int(N), float(L)
         self.edges = np.ascontiguousarray(edges, dtype=np.float64)
         self.nbins = len(self.edges) - 1
-        self._h = fbs_plan_create(N, L, self.edges, _PREC[precision], flags, sp)
+        self._h = fbs_plan_create(N, L, self.edges, _PREC[precision], flags, sp, counts=counts)
         self.precision = precision
         Lb = lib()
         self.ntrip = Lb.fbs_plan_num_triplets(_vp(self._h))
@@ -332,6 +352,10 @@ class Plan:
             import torch
             if f.dtype != torch.float32 or not f.is_contiguous():
                 raise ValueError("field must be a contiguous float32 tensor")
+
+    def export_counts(self):
+        """Serialised closed items and exact counts (see fbs_plan_export_counts)."""
+        return fbs_plan_export_counts(self._h)
 
     def check(self):
         """Wait for the plan's stream; raise on a timed-out evaluation."""

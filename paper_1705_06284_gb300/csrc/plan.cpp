@@ -21,6 +21,8 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -460,6 +462,96 @@ static long long slab_budget_bytes() {
 // ---------------------------------------------------------------- levels
 static constexpr int kMinLevelGrid = 128;
 
+// Plan-time results carried over from an exported plan: the closed items
+// (global bins, ascending) and their exact counts.
+struct CountCache {
+    std::map<std::array<int, 4>, double> counts;  // triplets have b[3] = -1
+    double margin = 0;
+    bool quad_exact = true;
+};
+
+// Serialised form (native byte order): "FBSC", version, N, flags, nbins,
+// L, thr[nbins+1], ntrip, ntrip x (a, b, c, N_tri), nquad,
+// nquad x (a, b, c, d, N_quad), count margin, quad-counts-exact flag.
+static constexpr uint32_t kCacheMagic = 0x43534246u;  // "FBSC"
+static constexpr uint32_t kCacheVersion = 1u;
+
+struct Writer {
+    std::vector<unsigned char> b;
+    template <typename T> void put(const T &v) {
+        const unsigned char *p = reinterpret_cast<const unsigned char *>(&v);
+        b.insert(b.end(), p, p + sizeof(T));
+    }
+};
+
+struct Reader {
+    const unsigned char *p;
+    size_t n, off = 0;
+    template <typename T> T get() {
+        if (off + sizeof(T) > n) throw Failure{FBS_ERR_ARG, "plan counts blob is truncated"};
+        T v;
+        memcpy(&v, p + off, sizeof(T));
+        off += sizeof(T);
+        return v;
+    }
+};
+
+static std::vector<unsigned char> export_counts(const Plan &p) {
+    Writer w;
+    w.put(kCacheMagic);
+    w.put(kCacheVersion);
+    w.put((int32_t)p.N);
+    w.put((uint32_t)(p.flags & (FBS_FLAG_TRISPECTRUM | FBS_FLAG_ALLOW_ALIASED)));
+    w.put((int32_t)p.nbins);
+    w.put(p.L);
+    for (long long t : p.thr) w.put((int64_t)t);
+    w.put((int64_t)p.ntri.size());
+    for (size_t i = 0; i < p.ntri.size(); ++i) {
+        for (int k = 0; k < 3; ++k) w.put((int32_t)p.trip[3 * i + k]);
+        w.put((int64_t)p.ntri[i]);
+    }
+    w.put((int64_t)p.nquad.size());
+    for (size_t i = 0; i < p.nquad.size(); ++i) {
+        for (int k = 0; k < 4; ++k) w.put((int32_t)p.quad[4 * i + k]);
+        w.put(p.nquad[i]);
+    }
+    w.put(p.count_margin);
+    w.put((int32_t)(p.quad_counts_exact ? 1 : 0));
+    return w.b;
+}
+
+// Parse a blob and check it describes this plan's bins (same N, L, flags
+// that change the item set, and the same integer thresholds).
+static void import_counts(const Plan &p, const void *blob, int64_t size, CountCache &c) {
+    if (!blob || size <= 0) throw Failure{FBS_ERR_ARG, "empty plan counts blob"};
+    Reader r{reinterpret_cast<const unsigned char *>(blob), (size_t)size};
+    if (r.get<uint32_t>() != kCacheMagic || r.get<uint32_t>() != kCacheVersion)
+        throw Failure{FBS_ERR_ARG, "not a plan counts blob of this library version"};
+    const int N = r.get<int32_t>();
+    const uint32_t fl = r.get<uint32_t>();
+    const int nb = r.get<int32_t>();
+    const double L = r.get<double>();
+    if (N != p.N || nb != p.nbins || L != p.L ||
+        fl != (p.flags & (FBS_FLAG_TRISPECTRUM | FBS_FLAG_ALLOW_ALIASED)))
+        throw Failure{FBS_ERR_ARG, "plan counts blob is for another grid, box, bin count or flags"};
+    for (int i = 0; i <= nb; ++i)
+        if (r.get<int64_t>() != p.thr[i]) throw Failure{FBS_ERR_ARG, "plan counts blob is for other bin edges"};
+    const int64_t nt = r.get<int64_t>();
+    if (nt < 0) throw Failure{FBS_ERR_ARG, "bad plan counts blob"};
+    for (int64_t i = 0; i < nt; ++i) {
+        std::array<int, 4> k{r.get<int32_t>(), r.get<int32_t>(), r.get<int32_t>(), -1};
+        c.counts[k] = (double)r.get<int64_t>();
+    }
+    const int64_t nq = r.get<int64_t>();
+    if (nq < 0) throw Failure{FBS_ERR_ARG, "bad plan counts blob"};
+    for (int64_t i = 0; i < nq; ++i) {
+        std::array<int, 4> k{r.get<int32_t>(), r.get<int32_t>(), r.get<int32_t>(), r.get<int32_t>()};
+        c.counts[k] = r.get<double>();
+    }
+    c.margin = r.get<double>();
+    c.quad_exact = r.get<int32_t>() != 0;
+}
+
 static Plan *new_level(Plan &root, int M) {
     Plan *lv = new Plan();
     lv->root_ = &root;
@@ -480,7 +572,7 @@ static Plan *new_level(Plan &root, int M) {
     return lv;
 }
 
-static void create_plan(Plan &p, const double *edges) {
+static void create_plan(Plan &p, const double *edges, const void *blob = nullptr, int64_t blob_size = 0) {
     const int N = p.N, nb = p.nbins;
     const bool quads_on = (p.flags & FBS_FLAG_TRISPECTRUM) != 0;
     p.fN = make_factors(N);
@@ -494,6 +586,11 @@ static void create_plan(Plan &p, const double *edges) {
         const long long lim = ((long long)N * N + 15) / 16;
         if (p.thr[nb] > lim)
             throw Failure{FBS_ERR_ARG, "top edge beyond N k_f/4 (pass FBS_FLAG_ALLOW_ALIASED to allow)"};
+    }
+    std::unique_ptr<CountCache> cache;
+    if (blob) {
+        cache.reset(new CountCache());
+        import_counts(p, blob, blob_size, *cache);
     }
     std::vector<long long> mn, mx;
     enumerate_shells(p, mn, mx);
@@ -589,7 +686,21 @@ static void create_plan(Plan &p, const double *edges) {
         std::vector<double> tden, qden;
         // sum_M N_a N_b N_c / M^3 is the same integer as sum_N N_a N_b N_c / N^3
         const double npix = (double)lv.M * lv.M * lv.M;
-        exact_counts(lv, ltc, lqc, tden, qden);
+        if (cache) {
+            // counts carried over: the closed items and their exact counts, no count pass
+            tden.assign(ltc.size() / 3, 0.0);
+            qden.assign(lqc.size() / 4, 0.0);
+            for (size_t i = 0; i < tden.size(); ++i) {
+                auto it = cache->counts.find({lt[l][3 * i], lt[l][3 * i + 1], lt[l][3 * i + 2], -1});
+                if (it != cache->counts.end()) tden[i] = it->second * npix;
+            }
+            for (size_t i = 0; i < qden.size(); ++i) {
+                auto it = cache->counts.find({lq[l][4 * i], lq[l][4 * i + 1], lq[l][4 * i + 2], lq[l][4 * i + 3]});
+                if (it != cache->counts.end()) qden[i] = it->second * npix;
+            }
+        } else {
+            exact_counts(lv, ltc, lqc, tden, qden);
+        }
         for (size_t i = 0; i < tden.size(); ++i) {
             int64_t c = round_count(p, tden[i], npix);
             if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative triangle count"};
@@ -617,6 +728,12 @@ static void create_plan(Plan &p, const double *edges) {
             cquad_cnt.push_back(c);
             cquad_src.push_back({(int)l, (int)i});
         }
+    }
+    if (cache) {
+        if (ctrip.size() + cquad.size() != cache->counts.size())
+            throw Failure{FBS_ERR_ARG, "plan counts blob does not match this plan's candidate items"};
+        p.count_margin = cache->margin;
+        p.quad_counts_exact = cache->quad_exact;
     }
     // global output order: lexicographic over all levels
     std::vector<int> ot(ctrip.size()), oq(cquad.size());
@@ -913,8 +1030,44 @@ int fbs_num_kernel_classes(void) { return KC_NUM; }
 
 const char *fbs_kernel_class_name(int i) { return (i >= 0 && i < KC_NUM) ? kClassNames[i] : ""; }
 
+static fbs_status plan_create_impl(fbs_plan **out, int N, double L, const double *edges, int nbins,
+                                   int precision, unsigned flags, void *cuda_stream, const void *blob,
+                                   int64_t blob_size);
+
 fbs_status fbs_plan_create(fbs_plan **out, int N, double L, const double *edges, int nbins,
                            int precision, unsigned flags, void *cuda_stream) {
+    return plan_create_impl(out, N, L, edges, nbins, precision, flags, cuda_stream, nullptr, 0);
+}
+
+fbs_status fbs_plan_create_from_counts(fbs_plan **out, int N, double L, const double *edges, int nbins,
+                                       int precision, unsigned flags, void *cuda_stream, const void *counts,
+                                       int64_t size) {
+    if (!counts || size <= 0) {
+        if (out) *out = nullptr;
+        set_error("counts blob is NULL or empty");
+        return FBS_ERR_ARG;
+    }
+    return plan_create_impl(out, N, L, edges, nbins, precision, flags, cuda_stream, counts, size);
+}
+
+fbs_status fbs_plan_export_counts(const fbs_plan *plan, void *buf, int64_t *size) {
+    if (!plan || !size) return FBS_ERR_ARG;
+    const std::vector<unsigned char> b = export_counts(*plan);
+    if (buf) {
+        if (*size < (int64_t)b.size()) {
+            set_error("buffer too small for the plan counts");
+            *size = (int64_t)b.size();
+            return FBS_ERR_ARG;
+        }
+        memcpy(buf, b.data(), b.size());
+    }
+    *size = (int64_t)b.size();
+    return FBS_OK;
+}
+
+static fbs_status plan_create_impl(fbs_plan **out, int N, double L, const double *edges, int nbins,
+                                   int precision, unsigned flags, void *cuda_stream, const void *blob,
+                                   int64_t blob_size) {
     if (!out) {
         set_error("out is NULL");
         return FBS_ERR_ARG;
@@ -952,7 +1105,7 @@ fbs_status fbs_plan_create(fbs_plan **out, int N, double L, const double *edges,
     p->flags = flags;
     p->stream = (cudaStream_t)cuda_stream;
     try {
-        create_plan(*p, edges);
+        create_plan(*p, edges, blob, blob_size);
     } catch (const Failure &f) {
         set_error(f.msg);
         fbs_plan_free(p);

@@ -7,6 +7,15 @@ CUDA stream) is free and its plan fits the HBM budget, overlaps the work of
 all admitted requests on the device, and reports per-request latency from
 arrival to a host-visible result.
 
+Plans are built off the admission loop: a builder thread runs the library's
+plan creation (its host work and its device work on a stream of its own) while
+the loop keeps polling completions and admitting requests whose plans are
+ready.  The plan-time results of every plan built (the closed items and their
+exact counts, fbs_plan_export_counts) are kept by key (N, L, edges,
+precision), so a plan evicted under the budget and needed again is rebuilt
+without the FP64 count pass; ``count_cache_dir`` also keeps them on disk
+across processes.
+
 Every estimator step runs in ``libfbs.so`` through the C ABI; this module
 only schedules: host->device copy of the field on the slot's stream, one
 ``fbs_bispectrum`` call, device->host copy of the outputs, and a CUDA event
@@ -16,7 +25,10 @@ request alone (the kernels use fixed reduction orders).
 from __future__ import annotations
 
 import collections
+import concurrent.futures
 import dataclasses
+import hashlib
+import os
 import time
 from typing import Dict, List, Optional, Sequence, Tuple
 
@@ -73,19 +85,32 @@ class EstimatorServer:
 
     hbm_budget: bytes of device memory the server's plans and buffers may hold.
     slots: concurrent requests in flight (one CUDA stream each).
+    build_async: build plans on a builder thread (default) instead of inline.
+    count_cache_dir: directory for the plan-time counts (optional).
     """
 
-    def __init__(self, hbm_budget: int = 120 << 30, slots: int = 4, device: int = 0):
+    NEVER = "never"  # _plan_for: the request cannot fit even with every idle plan evicted
+
+    def __init__(self, hbm_budget: int = 120 << 30, slots: int = 4, device: int = 0,
+                 build_async: bool = True, count_cache_dir: Optional[str] = None):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
         self.budget = int(hbm_budget)
         self.slots = [_Slot(torch, self.dev) for _ in range(slots)]
-        # key -> list of entries {"plan", "bytes", "busy", "last"}
+        # key -> list of entries {"plan", "bytes", "busy", "last", "dfield"}
         self.plans: Dict[tuple, List[dict]] = collections.defaultdict(list)
         self.held = 0
         self.plan_creations = 0
+        self.plans_from_cache = 0
+        self.counts_cache: Dict[tuple, bytes] = {}
+        self.count_cache_dir = count_cache_dir
         self._cancelled = set()
+        self._failed: Dict[tuple, str] = {}  # key -> why its plan could not be built
+        # key -> (future, bytes reserved for it, bytes of its field copies)
+        self._building: Dict[tuple, Tuple[concurrent.futures.Future, int, int]] = {}
+        self._pool = concurrent.futures.ThreadPoolExecutor(max_workers=1) if build_async else None
+        self._build_stream = torch.cuda.Stream(device=self.dev) if build_async else None
 
     # -- plan cache under the budget
     def _key(self, req: Request):
@@ -101,29 +126,83 @@ class EstimatorServer:
             self.held -= e["bytes"]
         return self.held + need <= self.budget
 
-    NEVER = "never"  # _plan_for: the request cannot fit even with every idle plan evicted
+    def _count_file(self, key):
+        h = hashlib.sha1(repr(key[:3]).encode()).hexdigest()[:24]
+        return os.path.join(self.count_cache_dir, "plan_counts_%s.bin" % h)
+
+    def _cached_counts(self, key):
+        c = self.counts_cache.get(key[:3])
+        if c is None and self.count_cache_dir:
+            p = self._count_file(key)
+            if os.path.exists(p):
+                c = open(p, "rb").read()
+                self.counts_cache[key[:3]] = c
+        return c
+
+    def _build(self, req: Request, key, stream):
+        """Create the plan (runs on the builder thread, or inline)."""
+        counts = self._cached_counts(key)
+        plan = Plan(req.field.shape[0], req.L, np.asarray(req.edges), precision=req.precision, stream=stream,
+                    counts=counts)
+        if counts is None:
+            blob = plan.export_counts()
+            self.counts_cache[key[:3]] = blob
+            if self.count_cache_dir:
+                os.makedirs(self.count_cache_dir, exist_ok=True)
+                tmp = self._count_file(key) + ".tmp%d" % os.getpid()
+                with open(tmp, "wb") as fh:
+                    fh.write(blob)
+                os.replace(tmp, self._count_file(key))
+        return plan, counts is not None
+
+    def _register(self, key, plan, from_cache, reserved, field_bytes):
+        self.plan_creations += 1
+        self.plans_from_cache += int(from_cache)
+        e = {"plan": plan, "bytes": plan.device_bytes + field_bytes, "busy": False,
+             "last": time.perf_counter(), "dfield": None}
+        self.held += e["bytes"] - reserved
+        self.plans[key].append(e)
+        return e
+
+    def _poll_builds(self):
+        for key, (fut, reserved, fbytes) in list(self._building.items()):
+            if fut.done():
+                del self._building[key]
+                try:
+                    plan, from_cache = fut.result()
+                except Exception as ex:  # its requests are refused, the loop goes on
+                    self.held -= reserved
+                    self._failed[key] = "plan creation failed: %s" % str(ex)[:200]
+                    continue
+                self._register(key, plan, from_cache, reserved, fbytes)
 
     def _plan_for(self, req: Request, stream):
-        """An idle plan for the request (created if needed), None when it must
-        wait for busy work to finish, or NEVER when it can never fit."""
+        """An idle plan for the request, None when it must wait (for busy work
+        to finish, or for its plan to be built), or NEVER when it can never
+        fit."""
         key = self._key(req)
         for e in self.plans[key]:
             if not e["busy"]:
                 e["plan"].set_stream(stream)
                 return e
+        if key in self._building:
+            return None
+        if key in self._failed:
+            return self.NEVER
         N = req.field.shape[0]
         need = plan_bytes_estimate(N, len(req.edges) - 1) + 2 * req.field.nbytes
         if need > self.budget:
             return self.NEVER
         if not self._evict_for(need):
-            busy = any(e["busy"] for lst in self.plans.values() for e in lst)
+            busy = any(e["busy"] for lst in self.plans.values() for e in lst) or bool(self._building)
             return None if busy else self.NEVER
-        plan = Plan(N, req.L, np.asarray(req.edges), precision=req.precision, stream=stream)
-        self.plan_creations += 1
-        e = {"plan": plan, "bytes": plan.device_bytes + 2 * req.field.nbytes, "busy": False,
-             "last": time.perf_counter(), "dfield": None}
-        self.held += e["bytes"]
-        self.plans[key].append(e)
+        if self._pool is not None:
+            self.held += need  # reserved until the plan exists
+            self._building[key] = (self._pool.submit(self._build, req, key, self._build_stream), need,
+                                   2 * req.field.nbytes)
+            return None
+        plan, from_cache = self._build(req, key, stream)
+        e = self._register(key, plan, from_cache, 0, 2 * req.field.nbytes)
         # the estimate admitted it; if the real plan is larger, make room or undo
         if self.held > self.budget and not self._evict_for(0):
             e["busy"] = True  # keep it out of its own eviction while we decide
@@ -174,25 +253,27 @@ class EstimatorServer:
         is not admitted before its arrival time; otherwise arrivals are
         ignored (all requests are available at once).  A request whose plan
         and buffers cannot fit the budget even with every idle plan evicted
-        is refused (Result.error) instead of holding up the queue."""
+        is refused (Result.error) instead of holding up the queue.  Requests
+        wait in arrival order for a free slot; one whose plan is being built
+        lets later requests with ready plans go first."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
-        waiting: collections.deque = collections.deque()
+        waiting: List[Request] = []
         results: List[Result] = []
         t0 = time.perf_counter()
-        if not hasattr(self, "_cancelled"):
-            self._cancelled = set()
-        while pending or waiting or any(s.busy for s in self.slots):
+        while pending or waiting or any(s.busy for s in self.slots) or self._building:
             now = time.perf_counter() - t0
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
             if self._cancelled and waiting:
-                keep = collections.deque()
+                keep = []
                 for r in waiting:
                     if r.rid in self._cancelled:
                         results.append(self._refuse(r, "cancelled", realtime, t0))
                     else:
                         keep.append(r)
                 waiting = keep
+            if self._building:
+                self._poll_builds()
             # completions (non-blocking)
             for s in self.slots:
                 if s.busy and s.busy[2].query():
@@ -206,22 +287,26 @@ class EstimatorServer:
                     entry["busy"] = False
                     entry["last"] = time.perf_counter()
                     s.busy = None
-            # admissions: first-come first-served over the free slots
+            # admissions: in arrival order over the free slots; a request whose
+            # plan is not ready (being built, or waiting for memory) does not
+            # block the ones behind it
             progressed = False
-            for s in self.slots:
-                if s.busy or not waiting:
-                    continue
-                req = waiting[0]
-                entry = self._plan_for(req, s.stream)
+            free = [s for s in self.slots if not s.busy]
+            i = 0
+            while free and i < len(waiting):
+                req = waiting[i]
+                entry = self._plan_for(req, free[0].stream)
                 if entry is self.NEVER:
-                    waiting.popleft()
-                    results.append(self._refuse(req, "does not fit the HBM budget", realtime, t0))
+                    waiting.pop(i)
+                    why = self._failed.get(self._key(req), "does not fit the HBM budget")
+                    results.append(self._refuse(req, why, realtime, t0))
                     progressed = True
                     continue
                 if entry is None:
-                    break  # no memory until something finishes
-                waiting.popleft()
-                self._submit(s, req, entry, t0)
+                    i += 1
+                    continue
+                waiting.pop(i)
+                self._submit(free.pop(0), req, entry, t0)
                 progressed = True
             if not progressed:
                 time.sleep(0.0002)
@@ -229,6 +314,15 @@ class EstimatorServer:
 
     def close(self):
         self.torch.cuda.synchronize()
+        if self._pool is not None:
+            for key, (fut, reserved, fbytes) in list(self._building.items()):
+                try:
+                    plan, _ = fut.result()
+                    plan.close()
+                except Exception:  # a failed build left nothing to close
+                    pass
+            self._building.clear()
+            self._pool.shutdown(wait=True)
         for lst in self.plans.values():
             for e in lst:
                 e["plan"].close()
@@ -237,6 +331,8 @@ class EstimatorServer:
 
 
 def latency_percentiles(results: Sequence[Result]) -> Dict[str, float]:
-    lat = np.array([r.latency for r in results])
+    lat = np.array([r.latency for r in results if r.error is None])
+    if lat.size == 0:
+        return {"p50_ms": None, "p99_ms": None, "mean_ms": None}
     return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3)}

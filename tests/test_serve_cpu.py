@@ -3,6 +3,7 @@ budget, idle plans evicted least-recently-used first, busy plans never
 evicted, and no admission while nothing can be freed.  The plan object is a
 stand-in recording its size and closure; no GPU and no estimator work."""
 import collections
+import time
 
 import numpy as np
 import pytest
@@ -13,10 +14,20 @@ from paper_1705_06284_gb300 import serve
 
 class FakePlan:
     closed = []
+    counts_seen = []
+    gate = None  # a threading.Event the constructor waits on (slow builds)
 
-    def __init__(self, N, L, edges, precision="bf16x3", stream=None):
+    def __init__(self, N, L, edges, precision="bf16x3", stream=None, counts=None):
+        if FakePlan.gate is not None and N == 16:
+            FakePlan.gate.wait(5.0)
         self.N, self.device_bytes = N, 1000 * N
         self.stream = stream
+        self.triplets = np.zeros((0, 3), dtype=np.int32)
+        self.N_tri = np.zeros(0, dtype=np.int64)
+        FakePlan.counts_seen.append(counts)
+
+    def export_counts(self):
+        return b"counts-%d" % self.N
 
     def set_stream(self, s):
         self.stream = s
@@ -25,14 +36,16 @@ class FakePlan:
         FakePlan.closed.append(self.N)
 
 
-def _server(budget, monkeypatch):
+def _server(budget, monkeypatch, pool=None):
     monkeypatch.setattr(serve, "Plan", FakePlan)
     monkeypatch.setattr(serve, "plan_bytes_estimate", lambda N, nbins, slab_budget=0: 1000 * N)
     srv = serve.EstimatorServer.__new__(serve.EstimatorServer)
-    srv.budget, srv.held, srv.plan_creations = budget, 0, 0
+    srv.budget, srv.held, srv.plan_creations, srv.plans_from_cache = budget, 0, 0, 0
     srv.plans = collections.defaultdict(list)
     srv.slots, srv._cancelled = [], set()
-    FakePlan.closed = []
+    srv.counts_cache, srv.count_cache_dir = {}, None
+    srv._building, srv._pool, srv._build_stream, srv._failed = {}, pool, None, {}
+    FakePlan.closed, FakePlan.counts_seen, FakePlan.gate = [], [], None
     return srv
 
 
@@ -105,3 +118,52 @@ def test_run_refuses_oversize_and_cancelled_requests(monkeypatch):
     assert errs[1] == "does not fit the HBM budget"
     assert errs[3] == "cancelled"
     assert served == [2]
+
+
+class _Done:
+    def query(self):
+        return True
+
+
+def test_plan_builds_do_not_hold_up_admission(monkeypatch):
+    """A request whose plan is being built (slowly, on the builder thread)
+    does not stop the loop: a later request with a ready plan is admitted and
+    completes first; the first is admitted once its plan exists."""
+    import concurrent.futures
+    import threading
+    import torch
+    pool = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+    srv = _server(10 ** 9, monkeypatch, pool=pool)
+    srv.slots = [_FakeSlot(), _FakeSlot()]
+    order = []
+
+    def fake_submit(slot, req, entry, t0):
+        order.append(req.rid)
+        entry["busy"] = True
+        slot.busy = (req, entry, _Done(), (None, None, torch.zeros(0), torch.zeros(0), None), 0.0)
+
+    monkeypatch.setattr(srv, "_submit", fake_submit)
+    srv._plan_for(_req(0, 8), "s")  # the 8^3 plan is built and resident before the run
+    deadline = time.time() + 5
+    while srv._building and time.time() < deadline:
+        srv._poll_builds()
+    FakePlan.gate = threading.Event()
+    timer = threading.Timer(0.3, FakePlan.gate.set)
+    timer.start()
+    res = srv.run([_req(1, 16), _req(2, 8)], realtime=False)
+    timer.join()
+    pool.shutdown()
+    assert order == [2, 1]  # 2 went ahead while 1's plan was being built
+    assert sorted(r.rid for r in res) == [1, 2] and all(r.error is None for r in res)
+    assert srv.plan_creations == 2
+
+
+def test_rebuilt_plans_take_their_counts_from_the_cache(monkeypatch):
+    f8 = 2 * 8 ** 3 * 4
+    srv = _server(8000 + f8, monkeypatch)
+    e1 = srv._plan_for(_req(1, 8), "s1")          # built from scratch, counts kept
+    assert FakePlan.counts_seen == [None] and srv.plans_from_cache == 0
+    e2 = srv._plan_for(_req(2, 8, nb=5), "s2")    # another key evicts the first
+    assert e2 is not None and FakePlan.closed == [8]
+    e3 = srv._plan_for(_req(3, 8), "s3")          # the first key again: from its counts
+    assert FakePlan.counts_seen[-1] == b"counts-8" and srv.plans_from_cache == 1
