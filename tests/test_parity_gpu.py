@@ -341,3 +341,28 @@ def test_levels_match_single_grid_and_oracle(monkeypatch, N, L, kind, nb, precis
             print("levels %s T: %d gated, max rel %.2e" % ([l["M"] for l in lv.levels], n, m))
     print("levels %s (N=%d %s %s): %d gated, max rel %.2e" % ([l["M"] for l in lv.levels], N, kind,
                                                               precision, ng, gmax))
+
+
+def test_plan_from_exported_counts_equals_fresh_plan():
+    """fbs_plan_create_from_counts skips the plan-time count pass with the
+    closed items and exact counts of an equal plan: the same tables, levels
+    and results bit for bit; a blob for other edges is refused."""
+    import torch
+    N, L = 48, 60.0
+    edges = fields.log_edges(N, L, 8)
+    f = torch.from_numpy(_field("quadratic", N, 91).astype(np.float32)).cuda()
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=True) as a:
+        blob = a.export_counts()
+        Ta, Ba, Pa = (x.cpu().numpy() for x in a.trispectrum(f))
+        with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=True, counts=blob) as b:
+            assert np.array_equal(a.triplets, b.triplets) and np.array_equal(a.N_tri, b.N_tri)
+            assert np.array_equal(a.quads, b.quads) and np.array_equal(a.N_quad, b.N_quad)
+            assert a.levels == b.levels and np.array_equal(a.N_conn, b.N_conn)
+            Tb, Bb, Pb = (x.cpu().numpy() for x in b.trispectrum(f))
+            assert np.array_equal(Ta, Tb) and np.array_equal(Ba, Bb)
+            assert np.array_equal(Pa, Pb, equal_nan=True)
+    with pytest.raises(fbs.FbsError) as e:
+        fbs.Plan(N, L, fields.log_edges(N, L, 9), precision="bf16x3", trispectrum=True, counts=blob)
+    assert e.value.status == -1
+    with pytest.raises(fbs.FbsError):
+        fbs.Plan(N, L, edges, precision="bf16x3", counts=blob)  # flags differ (no trispectrum)
