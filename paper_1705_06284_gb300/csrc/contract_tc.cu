@@ -178,6 +178,26 @@ __device__ __forceinline__ uint32_t sw128_off(int row, int j) {
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((j ^ (row & 7)) << 4));
 }
 
+// Split two FP32 values into BF16 hi (round to nearest) and lo = bf16(v - hi)
+// with packed FP32x2 arithmetic: v - hi is exact in FP32 (hi is v rounded to
+// 8 significant bits), so one fused multiply-add by -1 gives it; the packed
+// and the scalar forms round identically.
+__device__ __forceinline__ void split2(float2 v, uint32_t &h, uint32_t &l) {
+    const __nv_bfloat162 hb = __float22bfloat162_rn(v);
+    h = *reinterpret_cast<const uint32_t *>(&hb);
+    const float2 hf = make_float2(__uint_as_float(h << 16), __uint_as_float(h & 0xffff0000u));
+    const __nv_bfloat162 lb = __float22bfloat162_rn(__ffma2_rn(hf, make_float2(-1.f, -1.f), v));
+    l = *reinterpret_cast<const uint32_t *>(&lb);
+}
+
+// Products a*b of 8 values (two float4 pairs) split into BF16 hi/lo words.
+__device__ __forceinline__ void mul_split8(float4 a0, float4 a1, float4 b0, float4 b1, uint32_t *h, uint32_t *l) {
+    split2(__fmul2_rn(make_float2(a0.x, a0.y), make_float2(b0.x, b0.y)), h[0], l[0]);
+    split2(__fmul2_rn(make_float2(a0.z, a0.w), make_float2(b0.z, b0.w)), h[1], l[1]);
+    split2(__fmul2_rn(make_float2(a1.x, a1.y), make_float2(b1.x, b1.y)), h[2], l[2]);
+    split2(__fmul2_rn(make_float2(a1.z, a1.w), make_float2(b1.z, b1.w)), h[3], l[3]);
+}
+
 // Split 8 FP32 values into BF16 hi (round to nearest) and lo = bf16(v - hi).
 __device__ __forceinline__ void split8(const float *v, uint4 &hi, uint4 &lo) {
     uint32_t h[4], l[4];
@@ -312,28 +332,41 @@ __device__ __forceinline__ const float4 *stage_at(const unsigned char *st, int h
                                             (((j & 7) ^ (b & 7)) << 4));
 }
 
-// One operand-B unit u = (inner row, 8-point group j of the chunk): the
+// One operand-B unit (inner row `row`, 8-point group j of the step): the
 // row's values (a single bin, or the product of two bins) split into BF16
 // hi/lo, stored in the 128-byte-swizzled K-major tile of K-atom j / 8.
-__device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_bytes, const int2 *s_inner,
-                                             int ninner, int u, unsigned char *bh, unsigned char *bl,
-                                             int b_tile) {
-    const int row = u % ninner, j = u / ninner;
+__device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_bytes, const int2 *s_inner, int row,
+                                             int j, unsigned char *bh, unsigned char *bl, int b_tile) {
     const int2 in = s_inner[row];
-    float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
-    float4 v1 = *stage_at(st, half_bytes, in.x, 2 * j + 1);
+    const float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
+    const float4 v1 = *stage_at(st, half_bytes, in.x, 2 * j + 1);
+    uint32_t h[4], l[4];
     if (in.y >= 0) {
         const float4 w0 = *stage_at(st, half_bytes, in.y, 2 * j);
         const float4 w1 = *stage_at(st, half_bytes, in.y, 2 * j + 1);
-        v0 = make_float4(v0.x * w0.x, v0.y * w0.y, v0.z * w0.z, v0.w * w0.w);
-        v1 = make_float4(v1.x * w1.x, v1.y * w1.y, v1.z * w1.z, v1.w * w1.w);
+        mul_split8(v0, v1, w0, w1, h, l);
+    } else {
+        split2(make_float2(v0.x, v0.y), h[0], l[0]);
+        split2(make_float2(v0.z, v0.w), h[1], l[1]);
+        split2(make_float2(v1.x, v1.y), h[2], l[2]);
+        split2(make_float2(v1.z, v1.w), h[3], l[3]);
     }
-    float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-    uint4 h, l;
-    split8(v, h, l);
     const uint32_t off = (uint32_t)((j >> 3) * b_tile) + sw128_off(row, j & 7);
-    *reinterpret_cast<uint4 *>(bh + off) = h;
-    *reinterpret_cast<uint4 *>(bl + off) = l;
+    *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Operand B of one pipeline step by W warps (wb = 0..W-1 among them): the
+// C = 8 KA eight-point groups go to the warps (W / C warps per group), the
+// inner rows to their lanes, with no division in the loop.
+template <int W, int KA>
+__device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes, const int2 *s_inner, int ninner,
+                                        int wb, int lane, unsigned char *bh, unsigned char *bl, int b_tile) {
+    constexpr int C = 8 * KA;
+    static_assert(W % C == 0, "operand-B warps must cover the eight-point groups evenly");
+    const int j = wb % C;
+    for (int row = lane + 32 * (wb / C); row < ninner; row += 32 * (W / C))
+        build_b_unit(st, half_bytes, s_inner, row, j, bh, bl, b_tile);
 }
 
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
@@ -345,7 +378,7 @@ __device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_b
 // 2 KA TMA boxes of 32 points, with one swizzled B tile per atom and A stages
 // of 64 KA tensor-memory columns.
 template <int NST, int NSTG, int AW, int KA>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __maxnreg__(112)  // 576 threads x 112 registers fit one SM
     contract_tc_kernel(const __grid_constant__ CUtensorMap fmap, long long npts, int nbins, int Npad,
                        int tstride, int ninner, const int2 *__restrict__ inner,
                        const TcPair *__restrict__ pairs, int npairs,
@@ -534,7 +567,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
     } else if (BW > 0 && warp >= AW) {
         // ================= operand-B warps (AW .. 15) =================
-        const int btid = tid - AW * 32;  // 0 .. 32*BW-1
         Ring<NSTG> rs;
         Ring<2> rb;
         for (long long ci = c0; ci < c1; ++ci) {
@@ -542,8 +574,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const unsigned char *st = stg + rs.slot * stage_bytes;
             const int sb = rb.slot;
             if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 25, wait_limit);
-            for (int u = btid; u < ninner * 8 * KA; u += BW * 32)
-                build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_stage, Bl0 + sb * b_stage, b_tile);
+            // (8 KA when BW = 0 only keeps the never-taken instantiation well formed)
+            build_b<(BW > 0 ? BW : 8 * KA), KA>(st, half_bytes, s_inner, ninner, warp - AW, lane,
+                                                 Bh0 + sb * b_stage, Bl0 + sb * b_stage, b_tile);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.bfull[sb]);
@@ -569,9 +602,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
                 const int sb = rb.slot;
                 if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21, wait_limit);
-                for (int u = ptid; u < ninner * 8 * KA; u += AW * 32)
-                    build_b_unit(st, half_bytes, s_inner, ninner, u, Bh0 + sb * b_stage, Bl0 + sb * b_stage,
-                                 b_tile);
+                build_b<AW, KA>(st, half_bytes, s_inner, ninner, warp, lane, Bh0 + sb * b_stage, Bl0 + sb * b_stage,
+                                b_tile);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.bfull[sb]);
@@ -585,6 +617,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int2 bc = pbc[lt * 128 + r];
                 const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
                 const uint32_t col = (uint32_t)(acc_cols + as * ACOLS + (PPT / 2) * kq);
+                // This thread's 16-byte chunks of the step are J0 + k, k < PPT / 4,
+                // J0 = (PPT/4) kq a multiple of 4 that never carries into the next
+                // 32-point box.  The stage row of bin b holds chunk J at
+                // ((J & 7) ^ (b & 7)) << 4 of box J >> 3, so every address is the
+                // row's base XOR a compile-time offset.
+                const int J0 = (PPT / 4) * kq;
+                const unsigned char *rb0 = st + (J0 >> 3) * half_bytes + (bc.x >= 0 ? bc.x : 0) * 128;
+                const unsigned char *rc0 = st + (J0 >> 3) * half_bytes + (bc.y >= 0 ? bc.y : 0) * 128;
+                const uint32_t xb = (uint32_t)(((bc.x & 7) ^ (J0 & 7)) << 4);
+                const uint32_t xc = (uint32_t)(((bc.y & 7) ^ (J0 & 7)) << 4);
                 // 16 points (8 columns of hi, 8 of lo) at a time
 #pragma unroll
                 for (int c = 0; c < PPT / 16; ++c) {
@@ -592,17 +634,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (bc.x >= 0) {
 #pragma unroll
                         for (int j = 0; j < 2; ++j) {
-                            const int jj = (PPT / 4) * kq + 4 * c + 2 * j;
-                            const float4 b0 = *stage_at(st, half_bytes, bc.x, jj);
-                            const float4 b1 = *stage_at(st, half_bytes, bc.x, jj + 1);
-                            const float4 e0 = *stage_at(st, half_bytes, bc.y, jj);
-                            const float4 e1 = *stage_at(st, half_bytes, bc.y, jj + 1);
-                            float v[8] = {b0.x * e0.x, b0.y * e0.y, b0.z * e0.z, b0.w * e0.w,
-                                          b1.x * e1.x, b1.y * e1.y, b1.z * e1.z, b1.w * e1.w};
-                            uint4 h, l;
-                            split8(v, h, l);
-                            hw[4 * j + 0] = h.x; hw[4 * j + 1] = h.y; hw[4 * j + 2] = h.z; hw[4 * j + 3] = h.w;
-                            lw[4 * j + 0] = l.x; lw[4 * j + 1] = l.y; lw[4 * j + 2] = l.z; lw[4 * j + 3] = l.w;
+                            const uint32_t k0 = (uint32_t)((4 * c + 2 * j) << 4), k1 = k0 + 16u;
+                            const float4 b0 = *reinterpret_cast<const float4 *>(rb0 + (k0 ^ xb));
+                            const float4 b1 = *reinterpret_cast<const float4 *>(rb0 + (k1 ^ xb));
+                            const float4 e0 = *reinterpret_cast<const float4 *>(rc0 + (k0 ^ xc));
+                            const float4 e1 = *reinterpret_cast<const float4 *>(rc0 + (k1 ^ xc));
+                            mul_split8(b0, b1, e0, e1, hw + 4 * j, lw + 4 * j);
                         }
                     } else {
 #pragma unroll
