@@ -188,6 +188,11 @@ enum {
                             cover (fewer 128-row tiles); 1: by its pair of
                             the two largest bins (b, c).  Sums agree within
                             rounding. */
+    FBS_OPT_SLAB_PLANES = 6,  /* planes of the evaluation grid per slab: 0 (default)
+                            the planned slab (as many planes as the slab budget
+                            allows); n >= 1: at most n planes per slab (more,
+                            thinner slabs in the same buffers).  Sums agree within
+                            rounding.  Waits for the plan's stream. */
     FBS_OPT_TC_WAIT_LIMIT = 5 /* clock cycles a warp role of the tensor-core
                             contraction waits for a hand-off from another role
                             before it gives up (0, the default: 2e9 cycles,

@@ -4,8 +4,9 @@ All realisations of a batch are enqueued once, captured into one CUDA graph
 (one plan per distinct (N, L, edges), every launch of every realisation in
 order on one stream), and the graph is replayed: the host issues a single
 launch for the whole batch.  Every kernel is the library's; this module only
-captures and replays.  A small autotuner picks, per plan, the tensor-core
-orientation that runs fastest on the plan's own problem and caches it.
+captures and replays.  An autotuner picks, per plan, the contraction's
+orientation, pipeline step, pair assignment, warp roles and slab size that
+run fastest on the plan's own problem, and caches the choice.
 """
 from __future__ import annotations
 
@@ -41,9 +42,27 @@ def _key(N, L, edges, precision):
     return "%d|%r|%s|%s|%s" % (N, float(L), ",".join("%.12g" % e for e in edges), precision, _build_id())
 
 
+# Tunable options of a plan (fbs_plan_set_option) and the values tried; the
+# first value of each is the library's default.
+TUNABLE = (
+    ("chunk", 3, (0, 1)),       # FBS_OPT_TC_CHUNK: 128-point steps where they fit / 64-point steps
+    ("pairs", 4, (0, 1)),       # FBS_OPT_TC_PAIRS: greedy pair cover / plain (b, c) pairs
+    ("wide", 1, (0, 1)),        # FBS_OPT_TC_WIDE: pair products on M / stacked left rows on M
+    ("roles", 2, (0, 2)),       # FBS_OPT_TC_ROLES: 16 product warps / 8 + 8 concurrent roles
+    ("slab", 6, (0, 32, 8)),    # FBS_OPT_SLAB_PLANES: planned slabs / at most 32 or 8 planes
+)
+
+
+def _apply(plan, choice):
+    for name, opt, _ in TUNABLE:
+        plan.set_option(opt, int(choice.get(name, 0)))
+
+
 def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> Dict[str, float]:
-    """Time the plan's tensor-core orientations on ``field`` (a device tensor)
-    and keep the fastest; the choice is cached per (N, L, edges, precision)."""
+    """Pick the plan's options by timing them on ``field`` (a device tensor):
+    coordinate descent over TUNABLE from the defaults, keeping a change only
+    when it is faster by more than 2%.  The choice is cached per (N, L, edges,
+    precision, library build, device)."""
     import torch
     key = _key(plan.N, plan.L, plan.edges, plan.precision)
     table = {}
@@ -53,25 +72,45 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> D
         except Exception:
             table = {}
     if key in table:
-        plan.set_tc_wide(bool(table[key]["wide"]))
+        _apply(plan, table[key]["choice"])
         return table[key]
-    if plan.precision == "fp32":
-        return {"wide": False, "ms": {}}
     B = torch.empty(plan.ntrip, dtype=torch.float64, device=field.device)
     P = torch.empty(plan.nbins, dtype=torch.float64, device=field.device)
-    ms = {}
-    for wide in (False, True):
-        plan.set_tc_wide(wide)
-        plan.bispectrum(field, B, P)  # warm-up (builds the orientation's tables)
+
+    def timed(choice):
+        _apply(plan, choice)
+        plan.bispectrum(field, B, P)  # warm-up (builds the option's tables)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
         for _ in range(repeats):
             plan.bispectrum(field, B, P)
+        e1.record()
         torch.cuda.synchronize()
-        ms["wide" if wide else "narrow"] = 1e3 * (time.perf_counter() - t0) / repeats
-    best = ms["wide"] < ms["narrow"]
-    plan.set_tc_wide(best)
-    table[key] = {"wide": best, "ms": ms}
+        plan.check()
+        return e0.elapsed_time(e1) / repeats
+
+    best = {name: vals[0] for name, _, vals in TUNABLE}
+    tried = {}
+    best_ms = timed(best)
+    tried[json.dumps(best, sort_keys=True)] = best_ms
+    if plan.precision != "fp32":
+        for name, _, vals in TUNABLE:
+            for v in vals[1:]:
+                cand = dict(best, **{name: v})
+                k = json.dumps(cand, sort_keys=True)
+                if k not in tried:
+                    tried[k] = timed(cand)
+                if tried[k] < 0.98 * best_ms:
+                    best, best_ms = cand, tried[k]
+    else:  # the FP32 contraction has no tensor-core options: slabs only
+        for v in TUNABLE[-1][2][1:]:
+            cand = dict(best, slab=v)
+            ms = timed(cand)
+            if ms < 0.98 * best_ms:
+                best, best_ms = cand, ms
+    _apply(plan, best)
+    table[key] = {"choice": best, "ms": best_ms, "tried": len(tried)}
     try:
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         with open(cache + ".tmp", "w") as fh:

@@ -182,6 +182,7 @@ struct Plan {
     long long G_plane = 0;       // complex elements of the y-stage output per plane (all bins)
     int slab = 0;                // x planes per slab
     int nslabs = 0;
+    int slab_planned = 0;        // planes per slab the buffers were sized for
 
     // device memory
     std::vector<void *> allocs;

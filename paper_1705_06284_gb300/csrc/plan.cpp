@@ -782,6 +782,7 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
         const int nslabs = (M + slab - 1) / slab;
         slab = (M + nslabs - 1) / nslabs;  // balance the slabs
         lv.slab = slab;
+        lv.slab_planned = slab;
         lv.nslabs = nslabs;
         set_slab_offsets(lv);
         maxA = std::max(maxA, lv.A_elems);
@@ -1196,8 +1197,15 @@ fbs_status fbs_plan_set_option(fbs_plan *plan, int option, int value) {
         set_error("unknown option or value");
         return FBS_ERR_ARG;
     }
+    FBS_GUARD_BEGIN
+    if (option == FBS_OPT_SLAB_PLANES) FBS_CUDA(cudaStreamSynchronize(plan->stream));  // in-flight work uses the old layout
     for (Plan *lv : plan->levels) set_plan_option(lv, option, value);
+    if (option == FBS_OPT_SLAB_PLANES && !plan->levels.empty()) {
+        plan->slab = plan->levels.back()->slab;
+        plan->nslabs = plan->levels.back()->nslabs;
+    }
     return FBS_OK;
+    FBS_GUARD_END
 }
 
 static bool set_plan_option(Plan *plan, int option, int value) {
@@ -1219,6 +1227,14 @@ static bool set_plan_option(Plan *plan, int option, int value) {
     }
     if (option == FBS_OPT_TC_WAIT_LIMIT && value >= 0) {
         plan->tc_wait_limit = value;
+        return true;
+    }
+    if (option == FBS_OPT_SLAB_PLANES && value >= 0) {
+        if (plan->root_) {  // a level: fewer planes per slab in the same buffers
+            plan->slab = value > 0 ? std::min(value, plan->slab_planned) : plan->slab_planned;
+            plan->nslabs = (plan->M + plan->slab - 1) / plan->slab;
+            set_slab_offsets(*plan);
+        }
         return true;
     }
     return false;
