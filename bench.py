@@ -533,12 +533,14 @@ def serving_run(n_req=1000, n_warm=200, rate=200.0, seed=7, budget=120 << 30, sl
 
 
 def batched_run(n_real=256, seed=1000, reps=3, precision="bf16x3"):
-    """256 realisations with grids uniform over {64, 96, 128}^3 (half
+    """Config 4: 256 realisations with grids uniform over {64, 96, 128}^3 (half
     lognormal with sigma in [0.3, 1.0], half bubbles with R in [3, 8] cells and
-    ionised fraction in [0.2, 0.8]), 24 linear bins each, captured into one
-    CUDA graph and replayed, against one-at-a-time eager calls in FP32.  The
-    fields come from a seeded pool of 8 per grid size, cycled over the
-    realisations (the work per realisation does not depend on the values)."""
+    ionised fraction in [0.2, 0.8]), 24 linear bins each.  Batched launches
+    (one fbs_bispectrum_batch per grid size) captured into one CUDA graph,
+    against the same realisations one call at a time, at equal precision (the
+    bench precision, then FP32).  The fields come from a seeded pool of 8 per
+    grid size, cycled over the realisations (the work per realisation does not
+    depend on the values)."""
     import torch
     import fields
     from paper_1705_06284_gb300.batch import GraphBatch
@@ -556,36 +558,41 @@ def batched_run(n_real=256, seed=1000, reps=3, precision="bf16x3"):
             lst.append(torch.from_numpy(f.astype(np.float32)).cuda())
         pool[N] = lst
     order = [int(rng.choice(grids)) for _ in range(n_real)]
-    fl = [pool[N][i % 8] for i, N in enumerate(order)]
+    # distinct tensors (cycled values): every realisation is its own field in memory
+    fl = [pool[N][i % 8].clone() for i, N in enumerate(order)]
     L_for = lambda N: float(N)
     edges_for = lambda N: np.linspace(2 * math.pi / N, 0.25 * N * 2 * math.pi / N, 25)
     out = {"realisations": n_real, "grids": grids, "bins": 24}
-    gb = GraphBatch(fl, L_for, edges_for, precision=precision, tune=True)
-    ntri = sum(pl.ntrip for pl, _, _, _ in gb.items)
-    gb.capture()
-    gb.replay()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(gb.stream)
-    for _ in range(reps):
-        gb.replay()
-    e1.record(gb.stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    out["graph"] = {"value": ntri / (ms / 1e3), "unit": "triangle-bins/s", "ms_per_batch": ms,
-                    "precision": precision, "tuning": {str(k): v for k, v in gb.tuning.items()}}
-    gb.close()
-    gf = GraphBatch(fl, L_for, edges_for, precision="fp32", tune=False)
-    gf.run_eager()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        gf.run_eager()
-    torch.cuda.synchronize()
-    ms32 = 1e3 * (time.perf_counter() - t0) / reps
-    gf.close()
-    out["one_at_a_time_fp32"] = {"value": ntri / (ms32 / 1e3), "unit": "triangle-bins/s",
-                                 "ms_per_batch": ms32}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(gb.stream)
+        for _ in range(reps):
+            fn()
+        e1.record(gb.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for prec in ([precision, "fp32"] if precision != "fp32" else ["fp32"]):
+        gb = GraphBatch(fl, L_for, edges_for, precision=prec, tune=(prec != "fp32"))
+        ntri = sum(gb.groups[N]["plan"].ntrip for N, _ in gb.where)
+        ms_one = timed(gb.run_one_at_a_time)
+        ms_eager = timed(gb.run_eager)
+        gb.capture()
+        ms_graph = timed(gb.replay)
+        d = {"graph_batched": {"value": ntri / (ms_graph / 1e3), "unit": "triangle-bins/s", "ms_per_batch": ms_graph},
+             "eager_batched": {"value": ntri / (ms_eager / 1e3), "unit": "triangle-bins/s", "ms_per_batch": ms_eager},
+             "one_at_a_time": {"value": ntri / (ms_one / 1e3), "unit": "triangle-bins/s", "ms_per_batch": ms_one},
+             "graph_vs_one_at_a_time": ms_one / ms_graph,
+             "launch_groups": len(gb.groups)}
+        if prec != "fp32":
+            d["tuning"] = {str(k): v for k, v in gb.tuning.items()}
+        out[prec] = d
+        gb.close()
+    out["value"] = out[precision]["graph_batched"]["value"]
+    out["unit"] = "triangle-bins/s"
     return out
 
 

@@ -227,6 +227,25 @@ fbs_status fbs_plan_set_stream(fbs_plan *plan, void *cuda_stream);
 fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double *P);
 
 /*
+ * fbs_bispectrum_batch -- fbs_bispectrum of nfields fields of this plan's grid
+ * in one set of launches: every stage (forward transforms, each level's
+ * pruned inverse transforms and contraction, the reductions) runs once for
+ * all fields, the field taken from a grid dimension, so small grids fill the
+ * GPU.  Per field the results equal fbs_bispectrum's (up to rounding: the
+ * contraction's point ranges per CTA differ).
+ *   fields : host array of nfields DEVICE pointers (N^3 FP32, C order each).
+ *   B      : double[nfields * ntrip], field f at B + f*ntrip (device or host).
+ *   P      : double[nfields * nbins], field f at P + f*nbins.
+ *   nfields: 1 <= nfields, nfields * nbins <= 65535.
+ * Bispectra only (no quadruplets).  The first call with a larger nfields than
+ * before allocates the batch buffers (plan-owned, kept); the first call with
+ * a new list of field pointers uploads it and waits for the stream.  Neither
+ * may happen during stream capture; later calls with the same list can be
+ * captured.  Same stream semantics as fbs_bispectrum otherwise.
+ */
+fbs_status fbs_bispectrum_batch(fbs_plan *plan, const float *const *fields, int nfields, double *B, double *P);
+
+/*
  * fbs_trispectrum -- T for every closed quadruplet, plus B and P from the
  * same shell fields (Sec. 2: lower orders come at no extra FFT cost).
  * Needs a plan created with FBS_FLAG_TRISPECTRUM (else FBS_ERR_STATE).

@@ -81,6 +81,7 @@ _SIGS = [
     ("fbs_trispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("fbs_plan_sums", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("fbs_trispectrum_connected", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("fbs_bispectrum_batch", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
     ("fbs_plan_quads_connected", ctypes.c_int, [_vp, _vp]),
     ("fbs_num_kernel_classes", ctypes.c_int, []),
     ("fbs_kernel_class_name", ctypes.c_char_p, [ctypes.c_int]),
@@ -329,6 +330,21 @@ class Plan:
         pp, _k3 = _ptr(P)
         fbs_trispectrum(self._h, fp, tp, bp, pp)
         return T, B, P
+
+    def bispectrum_batch(self, fields, B=None, P=None):
+        """B[nf, ntrip], P[nf, nbins] of a list of N^3 float32 CUDA tensors in
+        one set of launches (see fbs_bispectrum_batch)."""
+        import torch
+        nf = len(fields)
+        for f in fields:
+            self._check_field(f)
+        dev = fields[0].device
+        B = torch.empty((nf, self.ntrip), dtype=torch.float64, device=dev) if B is None else B
+        P = torch.empty((nf, self.nbins), dtype=torch.float64, device=dev) if P is None else P
+        ptrs = (ctypes.c_void_p * nf)(*[f.data_ptr() for f in fields])
+        _check(lib().fbs_bispectrum_batch(_vp(self._h), ctypes.cast(ptrs, _vp), nf, _vp(B.data_ptr()),
+                                          _vp(P.data_ptr())))
+        return B, P
 
     def trispectrum_connected(self, field, Tc=None, T=None, B=None, P=None):
         """(Tc, T, B, P): the connected trispectrum (paired quadruples left

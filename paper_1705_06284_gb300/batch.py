@@ -1,10 +1,10 @@
 """Batched estimation of many realisations with uneven grid sizes.
 
-All realisations of a batch are enqueued once, captured into one CUDA graph
-(one plan per distinct (N, L, edges), every launch of every realisation in
-order on one stream), and the graph is replayed: the host issues a single
-launch for the whole batch.  Every kernel is the library's; this module only
-captures and replays.  An autotuner picks, per plan, the contraction's
+Realisations are grouped by grid size, each group evaluated by one batched
+library call (fbs_bispectrum_batch: one launch per stage for all of the
+group's fields), and those calls are captured into one CUDA graph and
+replayed: the host issues a single launch for the whole batch.  Every kernel
+is the library's; this module only groups, captures and replays.  An autotuner picks, per plan, the contraction's
 orientation, pipeline step, pair assignment, warp roles and slab size that
 run fastest on the plan's own problem, and caches the choice.
 """
@@ -58,13 +58,15 @@ def _apply(plan, choice):
         plan.set_option(opt, int(choice.get(name, 0)))
 
 
-def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> Dict[str, float]:
-    """Pick the plan's options by timing them on ``field`` (a device tensor):
-    coordinate descent over TUNABLE from the defaults, keeping a change only
-    when it is faster by more than 2%.  The choice is cached per (N, L, edges,
-    precision, library build, device)."""
+def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE, batch=None) -> Dict[str, float]:
+    """Pick the plan's options by timing them on ``field`` (a device tensor),
+    or on batched calls over the list ``batch`` of device tensors: coordinate
+    descent over TUNABLE from the defaults, keeping a change only when it is
+    faster by more than 2% (batched calls: the options they use, pipeline
+    step, pair assignment and warp roles).  The choice is cached per (N, L,
+    edges, precision, batch size, library build, device)."""
     import torch
-    key = _key(plan.N, plan.L, plan.edges, plan.precision)
+    key = _key(plan.N, plan.L, plan.edges, plan.precision) + ("|batch%d" % len(batch) if batch else "")
     table = {}
     if os.path.exists(cache):
         try:
@@ -74,17 +76,20 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> D
     if key in table:
         _apply(plan, table[key]["choice"])
         return table[key]
-    B = torch.empty(plan.ntrip, dtype=torch.float64, device=field.device)
-    P = torch.empty(plan.nbins, dtype=torch.float64, device=field.device)
+    nf = len(batch) if batch else 1
+    B = torch.empty((nf, plan.ntrip), dtype=torch.float64, device=field.device)
+    P = torch.empty((nf, plan.nbins), dtype=torch.float64, device=field.device)
+    run = (lambda: plan.bispectrum_batch(batch, B, P)) if batch else (lambda: plan.bispectrum(field, B[0], P[0]))
+    tunable = [t for t in TUNABLE if not batch or t[0] in ("chunk", "pairs", "roles")]
 
     def timed(choice):
         _apply(plan, choice)
-        plan.bispectrum(field, B, P)  # warm-up (builds the option's tables)
+        run()  # warm-up (builds the option's tables)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(repeats):
-            plan.bispectrum(field, B, P)
+            run()
         e1.record()
         torch.cuda.synchronize()
         plan.check()
@@ -95,7 +100,7 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> D
     best_ms = timed(best)
     tried[json.dumps(best, sort_keys=True)] = best_ms
     if plan.precision != "fp32":
-        for name, _, vals in TUNABLE:
+        for name, _, vals in tunable:
             for v in vals[1:]:
                 cand = dict(best, **{name: v})
                 k = json.dumps(cand, sort_keys=True)
@@ -103,7 +108,7 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> D
                     tried[k] = timed(cand)
                 if tried[k] < 0.98 * best_ms:
                     best, best_ms = cand, tried[k]
-    else:  # the FP32 contraction has no tensor-core options: slabs only
+    elif not batch:  # the FP32 contraction has no tensor-core options: slabs only
         for v in TUNABLE[-1][2][1:]:
             cand = dict(best, slab=v)
             ms = timed(cand)
@@ -122,8 +127,13 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE) -> D
 
 
 class GraphBatch:
-    """Capture the bispectra of many realisations into one CUDA graph.
+    """Many realisations of uneven grid sizes in one CUDA graph of batched
+    launches.
 
+    Realisations are grouped by grid size; each group is one plan and one
+    fbs_bispectrum_batch call, so every stage runs once per group for all of
+    its realisations (the field taken from a grid dimension), and the graph
+    holds a few dozen launches however many realisations there are.
     fields: sequence of float32 [N][N][N] arrays/tensors (any mix of N).
     edges_for: callable N -> bin edges (physical k units) for that grid.
     """
@@ -136,37 +146,52 @@ class GraphBatch:
         self.fields = [f if isinstance(f, torch.Tensor) and f.is_cuda
                        else torch.as_tensor(np.ascontiguousarray(f, dtype=np.float32)).to(self.dev)
                        for f in fields]
-        self.plans: Dict[Tuple, Plan] = {}
-        self.items: List[Tuple[Plan, object, object, object]] = []
+        self.groups: Dict[int, dict] = {}
+        self.where: List[Tuple[int, int]] = []  # realisation -> (grid, index in its group)
         self.tuning = {}
         for f in self.fields:
             N = f.shape[0]
-            key = (N,)
-            if key not in self.plans:
-                pl = Plan(N, L_for(N), edges_for(N), precision=precision, stream=self.stream)
-                if tune:
-                    with torch.cuda.stream(self.stream):
-                        self.tuning[N] = autotune(pl, f)
-                self.plans[key] = pl
-            pl = self.plans[key]
-            B = torch.empty(pl.ntrip, dtype=torch.float64, device=self.dev)
-            P = torch.empty(pl.nbins, dtype=torch.float64, device=self.dev)
-            self.items.append((pl, f, B, P))
+            if N not in self.groups:
+                self.groups[N] = {"plan": Plan(N, L_for(N), edges_for(N), precision=precision, stream=self.stream),
+                                  "fields": []}
+            g = self.groups[N]
+            self.where.append((N, len(g["fields"])))
+            g["fields"].append(f)
+        for N, g in self.groups.items():
+            pl, nf = g["plan"], len(g["fields"])
+            g["B"] = torch.empty((nf, pl.ntrip), dtype=torch.float64, device=self.dev)
+            g["P"] = torch.empty((nf, pl.nbins), dtype=torch.float64, device=self.dev)
+            if tune:
+                with torch.cuda.stream(self.stream):
+                    self.tuning[N] = autotune(pl, g["fields"][0], batch=g["fields"])
         self.graph = None
 
+    @property
+    def plans(self):
+        return {N: g["plan"] for N, g in self.groups.items()}
+
     def run_eager(self):
+        """One batched call per grid size (the same launches the graph holds)."""
         with self.torch.cuda.stream(self.stream):
-            for pl, f, B, P in self.items:
-                pl.bispectrum(f, B, P)
+            for g in self.groups.values():
+                g["plan"].bispectrum_batch(g["fields"], g["B"], g["P"])
+
+    def run_one_at_a_time(self, precision=None):
+        """The same realisations with one fbs_bispectrum call each (comparison)."""
+        with self.torch.cuda.stream(self.stream):
+            for g in self.groups.values():
+                pl = g["plan"]
+                for i, f in enumerate(g["fields"]):
+                    pl.bispectrum(f, g["B"][i], g["P"][i])
 
     def capture(self):
         torch = self.torch
-        self.run_eager()  # warm-up: every plan's first call happens outside the capture
+        self.run_eager()  # warm-up: buffers and field lists exist before the capture
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=self.stream, capture_error_mode="relaxed"):
-            for pl, f, B, P in self.items:
-                pl.bispectrum(f, B, P)
+            for grp in self.groups.values():
+                grp["plan"].bispectrum_batch(grp["fields"], grp["B"], grp["P"])
         self.graph = g
         return g
 
@@ -174,12 +199,14 @@ class GraphBatch:
         self.graph.replay()
 
     def results(self):
+        """(triplets, B, P) of every realisation, in input order."""
         self.torch.cuda.synchronize()
-        return [(pl.triplets, B.cpu().numpy(), P.cpu().numpy()) for pl, f, B, P in self.items]
+        host = {N: (g["B"].cpu().numpy(), g["P"].cpu().numpy()) for N, g in self.groups.items()}
+        return [(self.groups[N]["plan"].triplets, host[N][0][i], host[N][1][i]) for N, i in self.where]
 
     def close(self):
         self.torch.cuda.synchronize()
         self.graph = None
-        for pl in self.plans.values():
-            pl.close()
-        self.plans.clear()
+        for g in self.groups.values():
+            g["plan"].close()
+        self.groups.clear()

@@ -26,9 +26,11 @@ __global__ void __launch_bounds__(kCThreads) contract_fp32_kernel(
     const float *__restrict__ I, long long bin_stride, long long npts, int nbins,
     const int *__restrict__ pb, const int *__restrict__ pc, const int *__restrict__ pstart,
     const int *__restrict__ ia, const int *__restrict__ ib, const int *__restrict__ iout,
-    const int *__restrict__ grp_pair0, int nitems_total, double *__restrict__ part, int chunk) {
+    const int *__restrict__ grp_pair0, int nitems_total, double *__restrict__ part, int chunk, int part_rows) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int g = blockIdx.y;
+    // field blockIdx.z of a batch: its bins follow the previous fields' in I
+    I += (long long)blockIdx.z * nbins * bin_stride;
     const int p0 = grp_pair0[g], p1 = grp_pair0[g + 1];
     const int it0 = pstart[p0], it1 = pstart[p1];
     const int nloc = it1 - it0;
@@ -119,17 +121,21 @@ __global__ void __launch_bounds__(kCThreads) contract_fp32_kernel(
         }
     }
     __syncthreads();
-    double *row = part + (long long)blockIdx.x * nitems_total;
+    double *row = part + ((long long)blockIdx.z * part_rows + blockIdx.x) * nitems_total;
     for (int i = threadIdx.x; i < nloc; i += blockDim.x) row[iout[it0 + i]] += acc[i];
 }
 
 // ------------------------------------------------------------------ reduce
 // out[map[i]] = scale * sum_r part[r*ld + i], i < n (rows summed in a fixed
 // order, deterministic); map == nullptr: out[i].
+// Field blockIdx.y of a batch: its partials at part + y*sfs, its outputs at out + y*ofs.
 __global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, int n, int ld,
-                                   double *__restrict__ out, double scale, const int *__restrict__ map) {
+                                   double *__restrict__ out, double scale, const int *__restrict__ map,
+                                   long long sfs, long long ofs) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    part += blockIdx.y * sfs;
+    out += blockIdx.y * ofs;
     double s = 0.0;
     for (int r = 0; r < rows; ++r) s += part[(long long)r * ld + i];
     out[map ? map[i] : i] = scale * s;
@@ -140,10 +146,13 @@ __global__ void reduce_rows_kernel(const double *__restrict__ part, int rows, in
 // for a given launch shape).
 __global__ void __launch_bounds__(256) reduce_cols_kernel(const double *__restrict__ part, int rows,
                                                           double *__restrict__ out, double scale,
-                                                          const int *__restrict__ map) {
+                                                          const int *__restrict__ map, long long sfs,
+                                                          long long ofs) {
     __shared__ double red[256];
     const int j = blockIdx.x;
     if (map[j] < 0) return;
+    part += blockIdx.y * sfs;  // field blockIdx.y of a batch
+    out += blockIdx.y * ofs;
     double s = 0.0;
     for (int r = threadIdx.x; r < rows; r += blockDim.x) s += part[(long long)j * rows + r];
     red[threadIdx.x] = s;
@@ -165,6 +174,12 @@ __global__ void normalise_kernel(const double *__restrict__ tnum, const int64_t 
                                  int nbins, double L, int N, double *__restrict__ B,
                                  double *__restrict__ P, double *__restrict__ T,
                                  const int *__restrict__ err, int *__restrict__ sticky) {
+    // field blockIdx.y of a batch: its sums and outputs follow the previous fields'
+    const long long f = blockIdx.y;
+    tnum += f * ntrip;
+    sumsq += f * nbins;
+    if (B) B += f * ntrip;
+    if (P) P += f * nbins;
     const double V = L * L * L;
     const double npix = (double)N * N * N;
     const double cB = V * V / (npix * npix * npix);
@@ -364,7 +379,7 @@ std::vector<int> item_groups(const TaskList &t, int cap) {
 }
 
 void launch_contract_fp32(Plan &p, const float *islab, long long npts, long long slab_stride,
-                          bool quads) {
+                          bool quads, int nf, double *part_batch) {
     const TaskList &t = quads ? p.qtask : p.ttask;
     if (t.nitems == 0) return;
     const std::vector<int> &grp = quads ? p.qgrp : p.tgrp;
@@ -378,19 +393,21 @@ void launch_contract_fp32(Plan &p, const float *islab, long long npts, long long
     while (chunk > 128 && (size_t)p.nbins * chunk * 4 + (size_t)maxloc * 8 > 200 * 1024) chunk /= 2;
     const size_t sm = (((size_t)maxloc * 8 + 15) & ~(size_t)15) + (size_t)p.nbins * chunk * 4;
     KTimer tm(p, quads ? KC_QUAD : KC_CONTRACT);
-    dim3 grid(p.part_blocks, ngrp);
+    dim3 grid(std::max(1, p.part_blocks / nf), ngrp, nf);
     if (quads) {
         auto k = contract_fp32_kernel<true>;
         FBS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k<<<grid, kCThreads, sm, p.stream>>>(islab, slab_stride, npts, p.nbins, p.d_qpb, p.d_qpc,
                                              p.d_qps, p.d_qia, p.d_qib, p.d_qout, d_grp,
-                                             t.nitems, p.d_qpart, chunk);
+                                             t.nitems, part_batch ? part_batch : p.d_qpart, chunk,
+                                             p.part_blocks);
     } else {
         auto k = contract_fp32_kernel<false>;
         FBS_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         k<<<grid, kCThreads, sm, p.stream>>>(islab, slab_stride, npts, p.nbins, p.d_tpb, p.d_tpc,
                                              p.d_tps, p.d_tia, nullptr, p.d_tout, d_grp,
-                                             t.nitems, p.d_tpart, chunk);
+                                             t.nitems, part_batch ? part_batch : p.d_tpart, chunk,
+                                             p.part_blocks);
     }
     FBS_CUDA(cudaGetLastError());
 }
@@ -417,15 +434,25 @@ void zero_partials(Plan &p, bool quads) {
 // output maps, sums of squares of the bins whose P this level provides.
 void launch_level_reduce(Plan &p, bool quads) {
     Plan &R = p.root();
+    launch_level_reduce_batch(p, quads, 1, p.fused_active ? p.d_fpart : p.d_tpart, p.d_sumsq_part, R.d_tnum,
+                              R.d_sumsq);
+}
+
+// The sums of nf fields (partials tpart: per field part_blocks rows; sumsq
+// partials: per field nbins blocks) into tnum[nf][ntrip], sumsq[nf][nbins].
+void launch_level_reduce_batch(Plan &p, bool quads, int nf, const double *tpart, const double *sq,
+                               double *tnum, double *sumsq) {
+    Plan &R = p.root();
     KTimer tm(p, KC_REDUCE);
     const double r = (double)R.N / (double)p.M;
     const double scale = r * r * r;
+    const int rows = p.M * zstage_row_groups(p.M);
     int n = p.ttask.nitems;
     if (n > 0) {
-        const double *src = p.fused_active ? p.d_fpart : p.d_tpart;
         const int ld = p.fused_active ? n + p.qtask.nitems : n;
-        reduce_rows_kernel<<<(n + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, n, ld, R.d_tnum, scale,
-                                                                  p.d_gtrip);
+        dim3 grid((n + 255) / 256, nf);
+        reduce_rows_kernel<<<grid, 256, 0, p.stream>>>(tpart, p.part_blocks, n, ld, tnum, scale, p.d_gtrip,
+                                                       (long long)p.part_blocks * ld, (long long)R.ntri.size());
         FBS_CUDA(cudaGetLastError());
     }
     if (quads && p.qtask.nitems > 0) {
@@ -433,21 +460,27 @@ void launch_level_reduce(Plan &p, bool quads) {
         const double *src = p.fused_active ? p.d_fpart + p.ttask.nitems : p.d_qpart;
         const int ld = p.fused_active ? m + p.ttask.nitems : m;
         reduce_rows_kernel<<<(m + 255) / 256, 256, 0, p.stream>>>(src, p.part_blocks, m, ld, R.d_qnum, scale,
-                                                                  p.d_gquad);
+                                                                  p.d_gquad, 0, 0);
         FBS_CUDA(cudaGetLastError());
     }
-    const int rows = p.M * zstage_row_groups(p.M);
-    reduce_cols_kernel<<<p.nbins, 256, 0, p.stream>>>(p.d_sumsq_part, rows, R.d_sumsq, scale, p.d_pbin);
+    dim3 gc(p.nbins, nf);
+    reduce_cols_kernel<<<gc, 256, 0, p.stream>>>(sq, rows, sumsq, scale, p.d_pbin, (long long)p.nbins * rows,
+                                                 (long long)R.nbins);
     FBS_CUDA(cudaGetLastError());
 }
 
-void launch_normalise(Plan &p, bool quads) {
+void launch_normalise(Plan &p, bool quads) { launch_normalise_batch(p, quads, 1, p.d_tnum, p.d_sumsq, p.d_B, p.d_P); }
+
+// B[nf][ntrip], P[nf][nbins] from tnum[nf][ntrip], sumsq[nf][nbins]; T (single field only).
+void launch_normalise_batch(Plan &p, bool quads, int nf, const double *tnum, const double *sumsq, double *B,
+                            double *P) {
     KTimer tm(p, KC_REDUCE);
     int ntrip = (int)p.ntri.size(), nquad = quads ? (int)p.nquad.size() : 0;
     int n_all = std::max(std::max(ntrip, nquad), p.nbins);
-    normalise_kernel<<<(n_all + 255) / 256, 256, 0, p.stream>>>(
-        p.d_tnum, p.d_ntri, ntrip, p.d_qnum, p.d_nquad, nquad, p.d_sumsq, p.d_shell, p.nbins,
-        p.L, p.N, p.d_B, p.d_P, quads ? p.d_T : nullptr,
+    dim3 grid((n_all + 255) / 256, nf);
+    normalise_kernel<<<grid, 256, 0, p.stream>>>(
+        tnum, p.d_ntri, ntrip, p.d_qnum, p.d_nquad, nquad, sumsq, p.d_shell, p.nbins,
+        p.L, p.N, B, P, quads ? p.d_T : nullptr,
         p.precision != FBS_PREC_FP32 ? tc_error_flag(p) : nullptr,
         p.precision != FBS_PREC_FP32 ? tc_sticky_flag(p) : nullptr);
     FBS_CUDA(cudaGetLastError());
@@ -481,7 +514,7 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
     count_kernel<<<g, 256, sm, p.stream>>>(noct, nbins_all, H, d_items, arity, nitems, grp, part);
     FBS_CUDA(cudaGetLastError());
     reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, nitems, d_den, 1.0,
-                                                                   nullptr);
+                                                                   nullptr, 0, 0);
     FBS_CUDA(cudaGetLastError());
 }
 

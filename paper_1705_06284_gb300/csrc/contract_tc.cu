@@ -384,7 +384,7 @@ __global__ void __maxnreg__(112)  // 576 threads x 112 registers fit one SM
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
-                       int *__restrict__ err, long long wait_limit) {
+                       int *__restrict__ err, long long wait_limit, int part_rows) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
     static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
@@ -491,8 +491,10 @@ __global__ void __maxnreg__(112)  // 576 threads x 112 registers fit one SM
                 const int x = (int)(ci * KCH);
                 mbar_expect_tx(&bars.sfull[rs.slot], bytes);
 #pragma unroll
+                // field blockIdx.z of a batch: its bins are rows nbins * blockIdx.z of the map
                 for (int h = 0; h < 2 * KA; ++h)
-                    tma_load_2d(dst + h * half_bytes, &fmap, x + 32 * h, 0, &bars.sfull[rs.slot]);
+                    tma_load_2d(dst + h * half_bytes, &fmap, x + 32 * h, (int)blockIdx.z * nbins,
+                                &bars.sfull[rs.slot]);
                 rs.next();
                 ++issued;
             }
@@ -696,7 +698,7 @@ __global__ void __maxnreg__(112)  // 576 threads x 112 registers fit one SM
     tc_fence_after();
     if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
-    double *row = part + (long long)blockIdx.x * nitems_total;
+    double *row = part + ((long long)blockIdx.z * part_rows + blockIdx.x) * nitems_total;
     for (int i = tid; i < nloc; i += kTcThreads) row[iout[it0 + i]] += (double)acc[i].x - (double)acc[i].y;
 }
 
@@ -1346,14 +1348,15 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Tensor map of one slab of shell fields: x = point (npts valid, contiguous),
 // y = bin (stride slab_stride floats); boxes of 32 points x all bins in the
 // 128-byte swizzle; points past npts read as zero.
-static CUtensorMap field_tensor_map(const float *islab, long long npts, long long slab_stride, int nbins) {
+static CUtensorMap field_tensor_map(const float *islab, long long npts, long long slab_stride, int nbins,
+                                    int rows) {
     auto enc = tensor_map_encoder();
     if (!enc) throw Failure{FBS_ERR_CUDA, "cuTensorMapEncodeTiled is not available"};
     if ((reinterpret_cast<uintptr_t>(islab) & 15) || ((slab_stride * 4) & 15) || nbins < 1 || nbins > 256 ||
-        npts < 1 || npts >= (1LL << 31))
+        rows < nbins || npts < 1 || npts >= (1LL << 31))
         throw Failure{FBS_ERR_ARG, "shell-field slab does not meet the TMA layout rules"};
     CUtensorMap m;
-    cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)nbins};
+    cuuint64_t dims[2] = {(cuuint64_t)npts, (cuuint64_t)rows};  // rows: nbins per field of a batch
     cuuint64_t strides[1] = {(cuuint64_t)slab_stride * 4};
     cuuint32_t box[2] = {32u, (cuuint32_t)nbins};
     cuuint32_t es[2] = {1u, 1u};
@@ -1365,13 +1368,14 @@ static CUtensorMap field_tensor_map(const float *islab, long long npts, long lon
 }
 
 static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, long long slab_stride,
-                       double *part, int nitems_total, int kclass) {
+                       double *part, int nitems_total, int kclass, int nf) {
     TcState &st = tc_state(p);
     const int ngrp = (int)job.grp.size() - 1;
     int sms = 0, dev = 0;
     FBS_CUDA(cudaGetDevice(&dev));
     FBS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int G = std::max(1, sms / ngrp);
+    // CTAs per field and tile group: one wave of one CTA per SM over all of them
+    int G = std::max(1, sms / (ngrp * nf));
     if (G > p.part_blocks) G = p.part_blocks;
     // 16 warps form the pair products and build operand B in turn (measured
     // faster at both headline passes); 8 + 8 concurrent roles on request
@@ -1389,9 +1393,9 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     const int nstg = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 4, ka) <= 220 * 1024 ? 4 : 2;
     const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, nstg, ka);
     const int flush_every = 16 / ka;  // 1024 points in FP32 per flush
-    const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins);
+    const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins, nf * p.nbins);
     KTimer tm(p, kclass);
-    dim3 grid(G, ngrp);
+    dim3 grid(G, ngrp, nf);
     const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
 #define FBS_TC_LAUNCH(A, S, W, K)                                                                     \
     if (nst == A && nstg == S && aw == W && ka == K) {                                                \
@@ -1401,7 +1405,7 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
         contract_tc_kernel<A, S, W, K><<<grid, kTcThreads, sm, p.stream>>>(                          \
             fmap, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner, job.d_pairs, \
             job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err,         \
-            tc_wait_limit(p));                                                                        \
+            tc_wait_limit(p), p.part_blocks);                                                         \
     }
     bool launched = false;
     FBS_TC_LAUNCH(2, 2, 16, 1)
@@ -1421,18 +1425,19 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     FBS_CUDA(cudaGetLastError());
 }
 
-void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads) {
+void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads,
+                        int nf, double *part) {
     const TaskList &t = quads ? p.qtask : p.ttask;
     if (t.nitems == 0) return;
-    if (launch_wide(p, islab, npts, slab_stride, quads)) return;
+    if (nf == 1 && launch_wide(p, islab, npts, slab_stride, quads)) return;  // batches: narrow only
     TcState &st = tc_state(p);
     TcJob &job = quads ? st.quad : st.trip;
     if (job.built && !quads && job.variant != p.tc_pairs) job = TcJob{};  // option changed: rebuild
     if (!job.built) build_job(p, t, quads, job);
     if (!job.usable)
         throw Failure{FBS_ERR_ARG, "tensor-core contraction: more than 256 inner rows or shared memory exceeded"};
-    launch_job(p, job, islab, npts, slab_stride, quads ? p.d_qpart : p.d_tpart, t.nitems,
-               quads ? KC_QUAD_TC : KC_CONTRACT_TC);
+    launch_job(p, job, islab, npts, slab_stride, part ? part : (quads ? p.d_qpart : p.d_tpart), t.nitems,
+               quads ? KC_QUAD_TC : KC_CONTRACT_TC, nf);
 }
 
 bool tc_fused_usable(Plan &p) {
@@ -1446,7 +1451,7 @@ bool tc_fused_usable(Plan &p) {
 void launch_contract_tc_fused(Plan &p, const float *islab, long long npts, long long slab_stride) {
     TcState &st = tc_state(p);
     launch_job(p, st.fused, islab, npts, slab_stride, p.d_fpart, p.ttask.nitems + p.qtask.nitems,
-               KC_QUAD_TC);
+               KC_QUAD_TC, 1);
 }
 
 void free_tc_state(Plan &p) {

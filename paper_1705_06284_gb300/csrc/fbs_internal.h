@@ -37,10 +37,13 @@ FftFactors make_factors(int n);
 //   Dzb   : bin box extent along z (Rb+1, or N/2+1).
 //   A_off : offset (complex elements) of the bin's x-stage output A_b[x][jy][jz].
 //   G_off : offset (complex elements) of the bin's y-stage output per slab.
+//   box_off: offset (complex elements) of the spectrum box the bin reads (a
+//            field's own box in batched evaluations; 0 otherwise).
 struct BinGeom {
     int Rb, Db, Dzb, empty;
     long long thr_lo, thr_hi;
     long long A_off, G_off;
+    long long box_off;
 };
 
 // Device-side description of the spectrum box (forward output):
@@ -92,9 +95,15 @@ struct Plan;
 // fft.cu
 void upload_forward_twiddles(Plan &root);
 void upload_eval_twiddles(Plan &level);
-void launch_forward(Plan &p, const float *d_field);
+// Forward transforms of one field (d_field) or of nf fields (d_fields, a
+// device array of nf pointers) into nf consecutive zbuf / ybuf / box blocks.
+void launch_forward(Plan &p, const float *d_field, const float *const *d_fields, int nf, float2 *zbuf,
+                    float2 *ybuf, float2 *box);
 void launch_inverse_x(Plan &p, bool indicator_fp64);
+void launch_inverse_x_geom(Plan &p, const BinGeom *geom, int nb, int nvb);
 void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab);
+void launch_inverse_yz_slab_geom(Plan &p, int x0, int nx, float *islab, const BinGeom *geom, int nb, int nvb,
+                                 double *sq);
 int zstage_row_groups(int N);
 void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
                                    double2 *G64, const BinGeom *d_geom_grp);
@@ -102,15 +111,22 @@ void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, doub
 void launch_count_contraction(Plan &p, const double *noct, int nb_in_group, int bin0,
                               const int *d_items, int nitems, int arity, double *d_sums);
 // contract.cu
+// nf > 1: a batch of nf fields, field f's bins at rows f*nbins.. of islab and
+// its partial rows at part_batch + f*part_blocks*items (nullptr: the plan's).
 void launch_contract_fp32(Plan &p, const float *islab, long long npts, long long slab_stride,
-                          bool quads);
-void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads);
+                          bool quads, int nf = 1, double *part_batch = nullptr);
+void launch_contract_tc(Plan &p, const float *islab, long long npts, long long slab_stride, bool quads,
+                        int nf = 1, double *part_batch = nullptr);
 bool tc_quads_usable(Plan &p);
 // Triplets and quadruplets of a trispectrum plan in one tensor-core pass.
 bool tc_fused_usable(Plan &p);
 void launch_contract_tc_fused(Plan &p, const float *islab, long long npts, long long slab_stride);
 void launch_level_reduce(Plan &level, bool quads);
+void launch_level_reduce_batch(Plan &level, bool quads, int nf, const double *tpart, const double *sq,
+                               double *tnum, double *sumsq);
 void launch_normalise(Plan &root, bool quads);
+void launch_normalise_batch(Plan &root, bool quads, int nf, const double *tnum, const double *sumsq, double *B,
+                            double *P);
 // Connected trispectrum of the last evaluation into d_Tc[nquad] (root).
 void launch_connected(Plan &root, double *d_Tc);
 std::vector<int> fast_grids();  // grids with compile-time-radix kernels for every inverse stage
@@ -227,6 +243,7 @@ struct Plan {
     long long *d_shell = nullptr;
     // tensor-core path
     void *tc = nullptr;           // opaque state of contract_tc.cu
+    void *batch = nullptr;        // root only: buffers of batched evaluations (plan.cpp)
 
     // timing
     std::vector<cudaEvent_t> evs;  // 2 per pending launch, created once and reused

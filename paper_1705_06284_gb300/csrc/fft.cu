@@ -50,11 +50,16 @@ static void allow_smem(K kernel, size_t bytes) {
 
 // ------------------------------------------------------------------ forward
 // z pass: rows r = x*N + y, packed pairs (r0, r0+1) as re/im of one line.
+// Batched evaluations: field blockIdx.y reads fields[blockIdx.y] (when given)
+// and writes its own zbuf (stride zstride).
 template <int... Rs>
-__global__ void __launch_bounds__(kThreads) fwd_z_kernel(const float *__restrict__ field,
-                                                         float2 *__restrict__ zbuf, int N, int Dz,
-                                                         int nl, FftFactors f,
+__global__ void __launch_bounds__(kThreads) fwd_z_kernel(const float *__restrict__ field_one,
+                                                         const float *const *__restrict__ fields,
+                                                         float2 *__restrict__ zbuf_all, long long zstride,
+                                                         int N, int Dz, int nl, FftFactors f,
                                                          const float2 *__restrict__ tw) {
+    const float *__restrict__ field = fields ? fields[blockIdx.y] : field_one;
+    float2 *__restrict__ zbuf = zbuf_all + (long long)blockIdx.y * zstride;
     extern __shared__ float2 sm[];
     float2 *a = sm;
     const int ld = N + 1;
@@ -85,10 +90,12 @@ __global__ void __launch_bounds__(kThreads) fwd_z_kernel(const float *__restrict
 
 // y pass: lines (x, jz); input zbuf[x][y][jz], output ybuf[x][jy][jz].
 template <int... Rs>
-__global__ void __launch_bounds__(kThreads) fwd_y_kernel(const float2 *__restrict__ zbuf,
-                                                         float2 *__restrict__ ybuf, int N, int D,
-                                                         int Dz, int nl, FftFactors f,
-                                                         const float2 *__restrict__ tw) {
+__global__ void __launch_bounds__(kThreads) fwd_y_kernel(const float2 *__restrict__ zbuf_all,
+                                                         float2 *__restrict__ ybuf_all, long long zstride,
+                                                         long long ystride, int N, int D, int Dz, int nl,
+                                                         FftFactors f, const float2 *__restrict__ tw) {
+    const float2 *__restrict__ zbuf = zbuf_all + (long long)blockIdx.z * zstride;  // field blockIdx.z
+    float2 *__restrict__ ybuf = ybuf_all + (long long)blockIdx.z * ystride;
     extern __shared__ float2 sm[];
     float2 *a = sm;
     const int ld = N + 1;
@@ -114,10 +121,12 @@ __global__ void __launch_bounds__(kThreads) fwd_y_kernel(const float2 *__restric
 
 // x pass: lines (jy, jz); input ybuf[x][jy][jz], output box[jx][jy][jz].
 template <int... Rs>
-__global__ void __launch_bounds__(kThreads) fwd_x_kernel(const float2 *__restrict__ ybuf,
-                                                         float2 *__restrict__ box, int N, int D,
-                                                         int Dz, int nl, FftFactors f,
-                                                         const float2 *__restrict__ tw) {
+__global__ void __launch_bounds__(kThreads) fwd_x_kernel(const float2 *__restrict__ ybuf_all,
+                                                         float2 *__restrict__ box_all, long long ystride,
+                                                         long long bstride, int N, int D, int Dz, int nl,
+                                                         FftFactors f, const float2 *__restrict__ tw) {
+    const float2 *__restrict__ ybuf = ybuf_all + (long long)blockIdx.z * ystride;  // field blockIdx.z
+    float2 *__restrict__ box = box_all + (long long)blockIdx.z * bstride;
     extern __shared__ float2 sm[];
     float2 *a = sm;
     const int ld = N + 1;
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) inv_x_kernel(const float2 *__restric
         if (IND) {
             v = C{T(1), T(0)};
         } else {
-            float2 d = box[((long long)jx * bg.D + gjy) * bg.Dz + mz];
+            float2 d = box[g.box_off + ((long long)jx * bg.D + gjy) * bg.Dz + mz];
             v = C{T(d.x), T(d.y)};
         }
         a[l * ld + (mx + N) % N] = v;
@@ -574,8 +583,10 @@ std::vector<int> fast_grids() {
     return g;
 }
 
-void launch_forward(Plan &p, const float *d_field) {
+void launch_forward(Plan &p, const float *d_field, const float *const *d_fields, int nf, float2 *zbuf,
+                    float2 *ybuf, float2 *box) {
     const int N = p.N, D = p.box.D, Dz = p.box.Dz;
+    const long long zs = (long long)N * N * Dz, ys = (long long)N * D * Dz, bs = (long long)D * D * Dz;
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
     auto kz = fwd_z_kernel<>;
@@ -593,22 +604,22 @@ void launch_forward(Plan &p, const float *d_field) {
         KTimer t(p, KC_FWD_Z);
         allow_smem(kz, sm);
         long long rows = (long long)N * N;
-        int grid = (int)((rows + 2 * nl - 1) / (2 * nl));
-        kz<<<grid, kThreads, sm, p.stream>>>(d_field, p.d_zbuf, N, Dz, nl, p.fN, p.d_tw);
+        dim3 grid((int)((rows + 2 * nl - 1) / (2 * nl)), nf);
+        kz<<<grid, kThreads, sm, p.stream>>>(d_field, d_fields, zbuf, zs, N, Dz, nl, p.fN, p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
     {
         KTimer t(p, KC_FWD_Y);
         allow_smem(ky, sm);
-        dim3 grid((Dz + nl - 1) / nl, N);
-        ky<<<grid, kThreads, sm, p.stream>>>(p.d_zbuf, p.d_ybuf, N, D, Dz, nl, p.fN, p.d_tw);
+        dim3 grid((Dz + nl - 1) / nl, N, nf);
+        ky<<<grid, kThreads, sm, p.stream>>>(zbuf, ybuf, zs, ys, N, D, Dz, nl, p.fN, p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
     {
         KTimer t(p, KC_FWD_X);
         allow_smem(kx, sm);
-        dim3 grid((Dz + nl - 1) / nl, D);
-        kx<<<grid, kThreads, sm, p.stream>>>(p.d_ybuf, p.d_box, N, D, Dz, nl, p.fN, p.d_tw);
+        dim3 grid((Dz + nl - 1) / nl, D, nf);
+        kx<<<grid, kThreads, sm, p.stream>>>(ybuf, box, ys, bs, N, D, Dz, nl, p.fN, p.d_tw);
         FBS_CUDA(cudaGetLastError());
     }
 }
@@ -630,7 +641,11 @@ static int max_dzb(const Plan &p, int bin0, int nb) {
     return m;
 }
 
-void launch_inverse_x(Plan &p, bool) {
+void launch_inverse_x(Plan &p, bool) { launch_inverse_x_geom(p, p.d_geom, p.nbins, p.nbins); }
+
+// x stage over `nvb` (virtual) bins of geometry table `geom`; bins i and
+// i mod nb share their extents (batched fields repeat the level's bins).
+void launch_inverse_x_geom(Plan &p, const BinGeom *geom, int nb, int nvb) {
     const int N = p.M;  // inverse transforms run on the evaluation grid
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
@@ -641,12 +656,19 @@ void launch_inverse_x(Plan &p, bool) {
     FBS_RADICES(FBS_PICK)
 #undef FBS_PICK
     allow_smem(k, sm);
-    dim3 grid(max_inv_x_grid(p, 0, p.nbins, nl), p.nbins);
-    k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, p.d_geom, 0, p.d_A, nl, p.fM, p.d_twM);
+    dim3 grid(max_inv_x_grid(p, 0, nb, nl), nvb);
+    k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, geom, 0, p.d_A, nl, p.fM, p.d_twM);
     FBS_CUDA(cudaGetLastError());
 }
 
 void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
+    launch_inverse_yz_slab_geom(p, x0, nx, islab, p.d_geom, p.nbins, p.nbins, p.d_sumsq_part);
+}
+
+// y and z stages of one slab over `nvb` (virtual) bins of `geom` (see
+// launch_inverse_x_geom); shell fields to islab[vbin], partials to sq.
+void launch_inverse_yz_slab_geom(Plan &p, int x0, int nx, float *islab, const BinGeom *geom, int nb, int nvb,
+                                 double *sq) {
     const int N = p.M;  // evaluation grid
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
@@ -660,18 +682,18 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
 #undef FBS_PICK
         if (getenv("FBS_GENERIC_Y")) k = inv_y_kernel<float>;
         allow_smem(k, sm);
-        dim3 grid((max_dzb(p, 0, p.nbins) + nl - 1) / nl, nx, p.nbins);
-        k<<<grid, kThreads, sm, p.stream>>>(p.d_A, p.d_geom, 0, N, x0, p.d_G, 0, nl, p.fM, p.d_twM);
+        dim3 grid((max_dzb(p, 0, nb) + nl - 1) / nl, nx, nvb);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_A, geom, 0, N, x0, p.d_G, 0, nl, p.fM, p.d_twM);
         FBS_CUDA(cudaGetLastError());
     }
     if (zfast_ok(N) && !getenv("FBS_GENERIC_Z")) {
         KTimer t(p, KC_INV_Z);
-        dim3 grid(zstage_row_groups(N), nx, p.nbins);
+        dim3 grid(zstage_row_groups(N), nx, nvb);
         const long long obs = (long long)p.slab * N * N;
 #define FBS_ZL(n, t, lp, a, b, c, d)                                                          \
     if (N == n)                                                                               \
         inv_z_fast_kernel<n, t, lp, a, b, c, d><<<grid, t * lp, 0, p.stream>>>(                \
-            p.d_G, p.d_geom, x0, islab, obs, p.d_sumsq_part, p.d_twM);
+            p.d_G, geom, x0, islab, obs, sq, p.d_twM);
         FBS_ZFAST_LIST(FBS_ZL)
 #undef FBS_ZL
         FBS_CUDA(cudaGetLastError());
@@ -679,9 +701,9 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab) {
         KTimer t(p, KC_INV_Z);
         auto k = inv_z_kernel<float, false>;
         allow_smem(k, sm);
-        dim3 grid((N + 2 * nl - 1) / (2 * nl), nx, p.nbins);
-        k<<<grid, kThreads, sm, p.stream>>>(p.d_G, p.d_geom, 0, N, x0, islab,
-                                            (long long)p.slab * N * N, p.d_sumsq_part, nl, p.fM,
+        dim3 grid((N + 2 * nl - 1) / (2 * nl), nx, nvb);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_G, geom, 0, N, x0, islab,
+                                            (long long)p.slab * N * N, sq, nl, p.fM,
                                             p.d_twM);
         FBS_CUDA(cudaGetLastError());
     }

@@ -902,7 +902,7 @@ static void run_field(Plan &p, const float *field, bool quads) {
     }
     const bool tc = p.precision != FBS_PREC_FP32;
     if (tc) FBS_CUDA(cudaMemsetAsync(p.d_errbuf, 0, sizeof(int), p.stream));
-    launch_forward(p, d_in);
+    launch_forward(p, d_in, nullptr, 1, p.d_zbuf, p.d_ybuf, p.d_box);
     if (staged) {
         FBS_CUDA(cudaEventRecord(p.ev_field_free, p.stream));
         p.field_free_recorded = true;
@@ -940,6 +940,150 @@ static void run_field(Plan &p, const float *field, bool quads) {
         launch_level_reduce(lv, quads);
     }
     launch_normalise(p, quads);
+}
+
+// ---------------------------------------------------------------- batches
+// Buffers of batched evaluations (fbs_bispectrum_batch): every field of a
+// batch gets its own forward scratch and spectrum box, and every level
+// evaluates (field, bin) pairs as "virtual bins": bin b of field f is entry
+// f * nbins + b of a geometry table whose offsets point into the field's own
+// box, x-stage, y-stage and shell-field blocks.  The contraction and the
+// reductions take the field from a grid dimension.
+struct BatchLevel {
+    BinGeom *d_vgeom = nullptr;
+    int slab = 0, nslabs = 0;
+    double *tpart = nullptr, *sq = nullptr;
+};
+
+struct BatchState {
+    int cap = 0;
+    float2 *zbuf = nullptr, *ybuf = nullptr, *box = nullptr, *A = nullptr, *G = nullptr;
+    float *I = nullptr;
+    double *tnum = nullptr, *sumsq = nullptr, *B = nullptr, *P = nullptr;
+    const float **d_fptrs = nullptr;
+    std::vector<const float *> ptrs;  // the pointer list last uploaded
+    std::vector<BatchLevel> lv;
+};
+
+static BatchState &ensure_batch(Plan &p, int nf) {
+    if (!p.batch) p.batch = new BatchState();
+    BatchState &bs = *reinterpret_cast<BatchState *>(p.batch);
+    if (bs.cap >= nf) return bs;
+    // (re)allocate for nf fields; buffers of a smaller earlier batch stay with the plan
+    const int N = p.N, D = p.box.D, Dz = p.box.Dz;
+    const long long box_el = (long long)D * D * Dz;
+    bs.zbuf = (float2 *)p.dalloc((size_t)nf * N * N * Dz * sizeof(float2));
+    bs.ybuf = (float2 *)p.dalloc((size_t)nf * N * D * Dz * sizeof(float2));
+    bs.box = (float2 *)p.dalloc((size_t)nf * box_el * sizeof(float2));
+    FBS_CUDA(cudaMemsetAsync(bs.box, 0, (size_t)nf * box_el * sizeof(float2), p.stream));
+    const size_t ntrip = std::max<size_t>(1, p.ntri.size());
+    bs.tnum = (double *)p.dalloc((size_t)nf * ntrip * sizeof(double));
+    bs.B = (double *)p.dalloc((size_t)nf * ntrip * sizeof(double));
+    bs.sumsq = (double *)p.dalloc((size_t)nf * p.nbins * sizeof(double));
+    bs.P = (double *)p.dalloc((size_t)nf * p.nbins * sizeof(double));
+    bs.d_fptrs = (const float **)p.dalloc((size_t)nf * sizeof(float *));
+    bs.ptrs.clear();
+    long long maxA = 1, maxG = 1, maxI = 1;
+    bs.lv.assign(p.levels.size(), BatchLevel{});
+    const long long budget = slab_budget_bytes();
+    for (size_t l = 0; l < p.levels.size(); ++l) {
+        Plan &lv = *p.levels[l];
+        BatchLevel &bl = bs.lv[l];
+        const int M = lv.M, nb = lv.nbins;
+        const long long per_plane = ((long long)nb * M * M * 4 + lv.G_plane * 8) * nf;
+        int slab = (int)std::max<long long>(1, std::min<long long>(lv.slab_planned,
+                                                                   budget / std::max<long long>(1, per_plane)));
+        bl.nslabs = (M + slab - 1) / slab;
+        bl.slab = (M + bl.nslabs - 1) / bl.nslabs;
+        std::vector<BinGeom> vg((size_t)nf * nb);
+        const long long gfield = lv.G_plane * bl.slab;
+        for (int f = 0; f < nf; ++f) {
+            long long goff = 0;
+            for (int b = 0; b < nb; ++b) {
+                BinGeom g = lv.geom[b];
+                g.A_off += (long long)f * lv.A_elems;
+                g.G_off = (long long)f * gfield + goff;
+                g.box_off = (long long)f * box_el;
+                goff += (long long)bl.slab * M * lv.geom[b].Dzb;
+                vg[(size_t)f * nb + b] = g;
+            }
+        }
+        bl.d_vgeom = upload(p, vg);
+        bl.tpart = (double *)p.dalloc((size_t)nf * lv.part_blocks * std::max<size_t>(1, lv.ntri.size()) *
+                                      sizeof(double));
+        bl.sq = (double *)p.dalloc((size_t)nf * nb * M * zstage_row_groups(M) * sizeof(double));
+        maxA = std::max(maxA, (long long)nf * lv.A_elems);
+        maxG = std::max(maxG, nf * gfield);
+        maxI = std::max(maxI, (long long)nf * nb * bl.slab * M * M);
+    }
+    bs.A = (float2 *)p.dalloc((size_t)maxA * sizeof(float2));
+    bs.G = (float2 *)p.dalloc((size_t)maxG * sizeof(float2));
+    bs.I = (float *)p.dalloc((size_t)maxI * sizeof(float));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));  // the host geometry tables go out of scope
+    bs.cap = nf;
+    return bs;
+}
+
+static void free_batch(Plan &p) {
+    delete reinterpret_cast<BatchState *>(p.batch);  // device buffers belong to the plan's allocation list
+    p.batch = nullptr;
+}
+
+static void run_batch(Plan &p, const float *const *fields, int nf) {
+    BatchState &bs = ensure_batch(p, nf);
+    std::vector<const float *> ptrs(fields, fields + nf);
+    if (ptrs != bs.ptrs) {  // upload the pointer list only when it changes
+        FBS_CUDA(cudaMemcpyAsync(bs.d_fptrs, ptrs.data(), nf * sizeof(float *), cudaMemcpyHostToDevice, p.stream));
+        FBS_CUDA(cudaStreamSynchronize(p.stream));
+        bs.ptrs = ptrs;
+    }
+    const bool tc = p.precision != FBS_PREC_FP32;
+    if (tc) FBS_CUDA(cudaMemsetAsync(p.d_errbuf, 0, sizeof(int), p.stream));
+    launch_forward(p, nullptr, bs.d_fptrs, nf, bs.zbuf, bs.ybuf, bs.box);
+    for (size_t l = 0; l < p.levels.size(); ++l) {
+        Plan &lv = *p.levels[l];
+        const BatchLevel &bl = bs.lv[l];
+        // the level's stages on the batch buffers and slabs, then back
+        float2 *A0 = lv.d_A, *G0 = lv.d_G;
+        const int slab0 = lv.slab, nslabs0 = lv.nslabs;
+        lv.d_A = bs.A;
+        lv.d_G = bs.G;
+        lv.slab = bl.slab;
+        lv.nslabs = bl.nslabs;
+        lv.fused_active = false;
+        try {
+            const int M = lv.M, nb = lv.nbins;
+            FBS_CUDA(cudaMemsetAsync(bl.tpart, 0, (size_t)nf * lv.part_blocks * std::max<size_t>(1, lv.ntri.size()) *
+                                                      sizeof(double), p.stream));
+            FBS_CUDA(cudaMemsetAsync(bl.sq, 0, (size_t)nf * nb * M * zstage_row_groups(M) * sizeof(double),
+                                     p.stream));
+            launch_inverse_x_geom(lv, bl.d_vgeom, nb, nf * nb);
+            const long long plane = (long long)M * M;
+            for (int s = 0; s < bl.nslabs; ++s) {
+                const int x0 = s * bl.slab;
+                const int nx = std::min(bl.slab, M - x0);
+                if (nx <= 0) break;
+                launch_inverse_yz_slab_geom(lv, x0, nx, bs.I, bl.d_vgeom, nb, nf * nb, bl.sq);
+                const long long npts = (long long)nx * plane, stride = (long long)bl.slab * plane;
+                if (tc)
+                    launch_contract_tc(lv, bs.I, npts, stride, false, nf, bl.tpart);
+                else
+                    launch_contract_fp32(lv, bs.I, npts, stride, false, nf, bl.tpart);
+            }
+            launch_level_reduce_batch(lv, false, nf, bl.tpart, bl.sq, bs.tnum, bs.sumsq);
+        } catch (...) {
+            lv.d_A = A0;
+            lv.d_G = G0;
+            lv.slab = slab0;
+            lv.nslabs = nslabs0;
+            throw;
+        }
+        lv.d_A = A0;
+        lv.d_G = G0;
+        lv.slab = slab0;
+        lv.nslabs = nslabs0;
+    }
+    launch_normalise_batch(p, false, nf, bs.tnum, bs.sumsq, bs.B, bs.P);
 }
 
 // A tensor-core wait that gave up leaves a flag on the device; the outputs
@@ -1131,6 +1275,7 @@ void fbs_plan_free(fbs_plan *plan) {
     if (plan->copy_stream) cudaStreamSynchronize(plan->copy_stream);
     cudaGetLastError();
     free_tc_state(*plan);
+    free_batch(*plan);
     for (Plan *lv : plan->levels) {
         free_tc_state(*lv);
         delete lv;
@@ -1286,6 +1431,31 @@ fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double
     copy_out(*plan, T, plan->d_T, plan->nquad.size(), host);
     copy_out(*plan, B, plan->d_B, plan->ntri.size(), host);
     copy_out(*plan, P, plan->d_P, plan->nbins, host);
+    if (host) {
+        FBS_CUDA(cudaStreamSynchronize(plan->stream));
+        check_device_errors(*plan);
+    }
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_bispectrum_batch(fbs_plan *plan, const float *const *fields, int nfields, double *B, double *P) {
+    if (!plan || !fields || nfields < 1 || nfields > 65535 / std::max(1, plan->nbins)) {
+        set_error("bad plan, field list or batch size");
+        return FBS_ERR_ARG;
+    }
+    for (int f = 0; f < nfields; ++f)
+        if (!fields[f] || !is_device_ptr(fields[f])) {
+            set_error("batched fields must be device pointers");
+            return FBS_ERR_ARG;
+        }
+    FBS_GUARD_BEGIN
+    poll_device_errors(*plan);
+    run_batch(*plan, fields, nfields);
+    BatchState &bs = *reinterpret_cast<BatchState *>(plan->batch);
+    bool host = false;
+    copy_out(*plan, B, bs.B, (size_t)nfields * plan->ntri.size(), host);
+    copy_out(*plan, P, bs.P, (size_t)nfields * plan->nbins, host);
     if (host) {
         FBS_CUDA(cudaStreamSynchronize(plan->stream));
         check_device_errors(*plan);
