@@ -275,6 +275,36 @@ fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double
 fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double *Tc, double *T, double *B,
                                      double *P);
 
+/*
+ * fbs_plan_triangle_average -- a model averaged over each closed triplet's
+ * exact set of triangles, as the paper compares theory with its measurements
+ * (theory evaluated for every triangle contributing to a bin and averaged,
+ * Sec. 3.3): for triplet (a <= b <= c),
+ *   out[t] = (1/N_tri) sum over ordered closed (m1, m2, m3) in S_a x S_b x S_c
+ *            of sum_k coef[k] f_{terms[3k]}(|m1|) f_{terms[3k+1]}(|m2|) f_{terms[3k+2]}(|m3|).
+ * Models whose bispectrum is a sum of such separable terms (a product of
+ * functions of k1, k2, k3 each) are covered exactly: the local-type
+ * 2 f (P1 P2 + cyc), the equal-radius bubble model's W(k1 R) W(k2 R) W(k3 R)
+ * (Eq. BharBk), and tree-level perturbation theory (Eq. PT_Bi), whose kernel
+ * is a polynomial in k1.k2 = (k3^2 - k1^2 - k2^2)/2 over powers of k1 k2.
+ * By the Kronecker-delta identity of Sec. 2 each term is the FP64 sum over the
+ * evaluation grid of three weighted count fields (the inverse transforms of
+ * f(|m|) on the shells, the count fields of Eq. delta_nr with weights), so
+ * no triangle is enumerated.
+ *   w     : host double[nfunc * nw]; f_i(|m|) tabulated at integer |m|^2 = s,
+ *           w[i*nw + s], nw >= the plan's top threshold (fbs_plan_shells).
+ *   terms : host int32[3 * nterms], function of each position; coef: host double[nterms].
+ *   out   : host double[ntrip], the order of fbs_plan_triplets.
+ * Synchronous; allocates FP64 fields for the functions in use (transient).
+ */
+fbs_status fbs_plan_triangle_average(fbs_plan *plan, const double *w, int nfunc, int64_t nw, const int32_t *terms,
+                                     const double *coef, int nterms, double *out);
+
+/* Average of w(|m|) over the modes of each bin: out[b] = sum_{m in S_b}
+ * w[|m|^2] / |S_b| (NaN for empty bins); w tabulated at integer |m|^2 up to
+ * at least the top threshold (nw).  Host computation. */
+fbs_status fbs_plan_shell_average(const fbs_plan *plan, const double *w, int64_t nw, double *out);
+
 /* Unpaired ordered quadruple counts N_conn[nquad] of the connected
  * trispectrum (FP64; exact integers where the quadruple counts are). */
 fbs_status fbs_plan_quads_connected(const fbs_plan *plan, double *nconn);

@@ -90,6 +90,9 @@ def _load():
             lib.oracle_closed_triplets.restype = None
             lib.oracle_closed_triplets.argtypes = [ctypes.c_int, ctypes.c_int, i64p, ctypes.c_int,
                                                    i32p, i32p]
+            lib.oracle_triangle_sums.restype = None
+            lib.oracle_triangle_sums.argtypes = [ctypes.c_int, ctypes.c_int, i64p, ctypes.c_int, i32p, ctypes.c_int,
+                                                 ctypes.c_int64, dp, ctypes.c_int, i32p, dp, dp, i64p]
             lib.oracle_direct_trispectrum.restype = None
             lib.oracle_direct_trispectrum.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
                                                       dp, dp, i64p, ctypes.c_int]
@@ -448,6 +451,55 @@ def rebinned_bispectrum(field, L: float, edges, k_edges, mu_edges, k_rep=None):
     with np.errstate(invalid="ignore", divide="ignore"):
         B = np.where(cc > 0, (V * V / npix ** 3) * cn / np.maximum(cc, 1), np.nan)
     return B, cc, cn
+
+
+def triangle_average(N: int, L: float, edges, triplets, tables, terms, coef):
+    """Separable models averaged over each triplet's closed triangles (the
+    paper's theory points are the theory evaluated on every triangle of a bin
+    and averaged, Sec. 3.3): out[t] = (1/N_tri) sum over ordered closed
+    (m1, m2, m3) in S_a x S_b x S_c of sum_k coef[k] f_i(|m1|) f_j(|m2|)
+    f_l(|m3|), with f tabulated at integer |m|^2 (``tables`` [nfunc][nw]).
+    Plain enumeration of the triangles.  Returns (average, N_tri)."""
+    thr = np.ascontiguousarray(thresholds(edges, L))
+    abc = np.ascontiguousarray(np.asarray(triplets, dtype=np.int32).reshape(-1, 3))
+    w = np.ascontiguousarray(tables, dtype=np.float64)
+    t = np.ascontiguousarray(terms, dtype=np.int32).reshape(-1, 3)
+    c = np.ascontiguousarray(coef, dtype=np.float64).ravel()
+    if w.shape[1] <= 3 * (N // 2) ** 2:
+        raise ValueError("tables must cover every |m|^2 of the grid")
+    out = np.zeros(len(abc))
+    cnt = np.zeros(len(abc), dtype=np.int64)
+    _load().oracle_triangle_sums(N, len(thr) - 1, _p(thr, ctypes.c_int64), len(abc), _p(abc, ctypes.c_int32),
+                                 w.shape[0], w.shape[1], _p(w, ctypes.c_double), len(c), _p(t, ctypes.c_int32),
+                                 _p(c, ctypes.c_double), _p(out, ctypes.c_double), _p(cnt, ctypes.c_int64))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return out / cnt, cnt
+
+
+def triangle_average_direct(N: int, L: float, edges, triplets, model):
+    """Any model B(k1_vec, k2_vec, k3_vec) (physical wave vectors, arrays of
+    shape (n, 3)) averaged over each triplet's closed ordered triangles by
+    evaluating it on every triangle: the definition, for checking separable
+    forms.  Small grids only.  Returns (average, N_tri)."""
+    thr = thresholds(edges, L)
+    kf = k_fundamental(L)
+    f = np.fft.fftfreq(N, d=1.0 / N).astype(np.int64)
+    g = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1).reshape(-1, 3)
+    b = bin_index(N, thr).ravel()
+    out, cnt = [], []
+    for a_, b_, c_ in np.asarray(triplets).reshape(-1, 3):
+        m1 = g[b == a_]
+        m2 = g[b == b_]
+        p1 = np.repeat(m1, len(m2), axis=0)
+        p2 = np.tile(m2, (len(m1), 1))
+        m3 = -(p1 + p2)
+        m3 = (m3 + N // 2) % N - N // 2  # wrapped into [-N/2, N/2)
+        s3 = np.sum(m3 * m3, axis=1)
+        in_c = (s3 >= thr[c_]) & (s3 < thr[c_ + 1])
+        v = model(kf * p1[in_c], kf * p2[in_c], kf * m3[in_c])
+        out.append(float(np.sum(v)) / max(1, int(in_c.sum())))
+        cnt.append(int(in_c.sum()))
+    return np.array(out), np.array(cnt, dtype=np.int64)
 
 
 def power_spectrum(field, L: float, edges):

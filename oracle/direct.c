@@ -348,3 +348,55 @@ void oracle_closed_triplets(int N, int nbins, const int64_t *thr, int ntrip, con
     free(start);
     free(M);
 }
+
+/*
+ * Separable models summed over each requested triplet's closed triangles:
+ * for (a, b, c) = abc[3t..], out[t] = sum over ordered (m1, m2, m3) with
+ * m1 in S_a, m2 in S_b, m3 = -(m1+m2) (mod N) in S_c of
+ *   sum_k coef[k] w[terms[3k]][|m1|^2] w[terms[3k+1]][|m2|^2] w[terms[3k+2]][|m3|^2]
+ * and cnt[t] the number of those triangles (the theory averaged over the
+ * exact triangle set of a bin, as the paper's theory points are).
+ *   w : nfunc tables of nw values at integer |m|^2.
+ */
+void oracle_triangle_sums(int N, int nbins, const int64_t *thr, int ntrip, const int32_t *abc, int nfunc,
+                          int64_t nw, const double *w, int nterms, const int32_t *terms, const double *coef,
+                          double *out, int64_t *cnt) {
+    mode_t_ *M = NULL;
+    int64_t nm = collect_modes(N, nbins, thr, &M);
+    int64_t *start = (int64_t *)calloc((size_t)nbins + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < nm; ++i) start[M[i].bin + 1]++;
+    for (int b = 0; b < nbins; ++b) start[b + 1] += start[b];
+    int64_t *fill = (int64_t *)malloc((size_t)nbins * sizeof(int64_t));
+    memcpy(fill, start, (size_t)nbins * sizeof(int64_t));
+    int64_t *order = (int64_t *)malloc((size_t)(nm ? nm : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < nm; ++i) order[fill[M[i].bin]++] = i;
+    (void)nfunc;
+    for (int t = 0; t < ntrip; ++t) {
+        int A = abc[3 * t], B = abc[3 * t + 1], C = abc[3 * t + 2];
+        double s = 0.0;
+        int64_t sc = 0;
+#pragma omp parallel for reduction(+ : s, sc) schedule(dynamic, 16)
+        for (int64_t p = start[A]; p < start[A + 1]; ++p) {
+            const mode_t_ a = M[order[p]];
+            const int64_t s1 = (int64_t)a.mx * a.mx + (int64_t)a.my * a.my + (int64_t)a.mz * a.mz;
+            for (int64_t q = start[B]; q < start[B + 1]; ++q) {
+                const mode_t_ b = M[order[q]];
+                int x = wrap(-(a.mx + b.mx), N);
+                int y = wrap(-(a.my + b.my), N);
+                int z = wrap(-(a.mz + b.mz), N);
+                int64_t s3 = (int64_t)x * x + (int64_t)y * y + (int64_t)z * z;
+                if (bin_of(s3, nbins, thr) != C) continue;
+                const int64_t s2 = (int64_t)b.mx * b.mx + (int64_t)b.my * b.my + (int64_t)b.mz * b.mz;
+                double v = 0.0;
+                for (int k = 0; k < nterms; ++k)
+                    v += coef[k] * w[(int64_t)terms[3 * k] * nw + s1] * w[(int64_t)terms[3 * k + 1] * nw + s2] *
+                         w[(int64_t)terms[3 * k + 2] * nw + s3];
+                s += v;
+                sc += 1;
+            }
+        }
+        out[t] = s;
+        cnt[t] = sc;
+    }
+    free(order); free(fill); free(start); free(M);
+}

@@ -83,6 +83,9 @@ _SIGS = [
     ("fbs_trispectrum_connected", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("fbs_bispectrum_batch", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
     ("fbs_plan_quads_connected", ctypes.c_int, [_vp, _vp]),
+    ("fbs_plan_shell_average", ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
+    ("fbs_plan_triangle_average", ctypes.c_int, [_vp, _vp, ctypes.c_int, ctypes.c_int64, _vp, _vp,
+                                                  ctypes.c_int, _vp]),
     ("fbs_num_kernel_classes", ctypes.c_int, []),
     ("fbs_kernel_class_name", ctypes.c_char_p, [ctypes.c_int]),
     ("fbs_plan_kernel_times", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int]),
@@ -345,6 +348,25 @@ class Plan:
         _check(lib().fbs_bispectrum_batch(_vp(self._h), ctypes.cast(ptrs, _vp), nf, _vp(B.data_ptr()),
                                           _vp(P.data_ptr())))
         return B, P
+
+    def triangle_average(self, tables, terms, coef):
+        """Average of sum_k coef[k] f_i(|m1|) f_j(|m2|) f_l(|m3|) over each closed
+        triplet's ordered triangles (see fbs_plan_triangle_average).
+        tables: (nfunc, nw) FP64 values at integer |m|^2; terms: (nterms, 3)."""
+        w = np.ascontiguousarray(tables, dtype=np.float64)
+        t = np.ascontiguousarray(terms, dtype=np.int32).reshape(-1, 3)
+        c = np.ascontiguousarray(coef, dtype=np.float64).ravel()
+        out = np.zeros(self.ntrip)
+        _check(lib().fbs_plan_triangle_average(_vp(self._h), w.ctypes.data, w.shape[0], w.shape[1], t.ctypes.data,
+                                               c.ctypes.data, len(c), out.ctypes.data))
+        return out
+
+    def shell_average(self, table):
+        """Average of table[|m|^2] over the modes of each bin (NaN if empty)."""
+        w = np.ascontiguousarray(table, dtype=np.float64)
+        out = np.zeros(self.nbins)
+        _check(lib().fbs_plan_shell_average(_vp(self._h), w.ctypes.data, len(w), out.ctypes.data))
+        return out
 
     def trispectrum_connected(self, field, Tc=None, T=None, B=None, P=None):
         """(Tc, T, B, P): the connected trispectrum (paired quadruples left

@@ -292,11 +292,11 @@ void launch_connected(Plan &p, double *d_Tc) {
 // den[item] = sum over the octant 0 <= x,y,z <= N/2 of w(x)w(y)w(z) prod N_i,
 // w(v) = 1 for v in {0, N/2} and 2 otherwise (the reflections m_j -> -m_j map
 // the octant onto the whole grid).  items: arity bins per item (3 or 4).
-static constexpr int kCntChunk = 128;
+// kCntChunk: octant points staged per pass (fewer for many field rows).
 __global__ void __launch_bounds__(256) count_kernel(const double *__restrict__ noct, int nbins, int H,
                                                     const int *__restrict__ items, int arity,
                                                     int nitems, int grp_items,
-                                                    double *__restrict__ part) {
+                                                    double *__restrict__ part, int kCntChunk) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int it0 = blockIdx.y * grp_items;
     const int nloc = min(grp_items, nitems - it0);
@@ -336,9 +336,11 @@ __global__ void __launch_bounds__(256) count_kernel(const double *__restrict__ n
             const double *rc = sN + (size_t)it[2] * kCntChunk;
             double s = 0.0;
             if (arity == 3) {
+#pragma unroll 8
                 for (int k = 0; k < kCntChunk; ++k) s = fma(sw[k] * ra[k], rb[k] * rc[k], s);
             } else {
                 const double *rd = sN + (size_t)it[3] * kCntChunk;
+#pragma unroll 8
                 for (int k = 0; k < kCntChunk; ++k) s = fma(sw[k] * ra[k] * rb[k], rc[k] * rd[k], s);
             }
             acc[i] += s;
@@ -497,13 +499,12 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
                               int nitems, int arity, double *d_den) {
     if (nitems == 0) return;
     const int H = p.M / 2 + 1;  // count fields are on the evaluation grid's octant
-    int grp = 4096;
-    size_t sm = (size_t)grp * 8 + (size_t)nbins_all * kCntChunk * 8 + kCntChunk * 8;
-    while (sm > 200 * 1024 && grp > 256) {
-        grp /= 2;
-        sm = (size_t)grp * 8 + (size_t)nbins_all * kCntChunk * 8 + kCntChunk * 8;
-    }
-    if (sm > 220 * 1024) throw Failure{FBS_ERR_ARG, "too many bins for the count kernel"};
+    int grp = 4096, kCntChunk = 128;
+    auto smem = [&] { return (size_t)grp * 8 + (size_t)nbins_all * kCntChunk * 8 + kCntChunk * 8; };
+    while (smem() > 200 * 1024 && kCntChunk > 16) kCntChunk /= 2;
+    while (smem() > 200 * 1024 && grp > 256) grp /= 2;
+    const size_t sm = smem();
+    if (sm > 220 * 1024) throw Failure{FBS_ERR_ARG, "too many field rows for the count kernel"};
     const int ngrp = (nitems + grp - 1) / grp;
     const int blocks = 2 * num_sms();
     AsyncBuf pbuf((size_t)blocks * nitems * sizeof(double), p.stream, "count partials");
@@ -511,7 +512,7 @@ void launch_count_contraction(Plan &p, const double *noct, int nbins_all, int, c
     KTimer tm(p, KC_COUNT);
     FBS_CUDA(cudaFuncSetAttribute(count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 g(blocks, ngrp);
-    count_kernel<<<g, 256, sm, p.stream>>>(noct, nbins_all, H, d_items, arity, nitems, grp, part);
+    count_kernel<<<g, 256, sm, p.stream>>>(noct, nbins_all, H, d_items, arity, nitems, grp, part, kCntChunk);
     FBS_CUDA(cudaGetLastError());
     reduce_rows_kernel<<<(nitems + 255) / 256, 256, 0, p.stream>>>(part, blocks, nitems, nitems, d_den, 1.0,
                                                                    nullptr, 0, 0);

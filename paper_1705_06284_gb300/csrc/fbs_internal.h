@@ -105,8 +105,9 @@ void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab);
 void launch_inverse_yz_slab_geom(Plan &p, int x0, int nx, float *islab, const BinGeom *geom, int nb, int nvb,
                                  double *sq);
 int zstage_row_groups(int N);
+// FP64 count fields N_b on the octant (wtab: weights w(|m|^2) instead of 1).
 void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
-                                   double2 *G64, const BinGeom *d_geom_grp);
+                                   double2 *G64, const BinGeom *d_geom_grp, const double *wtab = nullptr);
 // contract.cu (FP64 count sums)
 void launch_count_contraction(Plan &p, const double *noct, int nb_in_group, int bin0,
                               const int *d_items, int nitems, int arity, double *d_sums);

@@ -153,12 +153,14 @@ __global__ void __launch_bounds__(kThreads) fwd_x_kernel(const float2 *__restric
 // ------------------------------------------------------------------ inverse
 // x stage.  CTA = (bin b = bin0 + blockIdx.y, column jy, group of nl jz).
 // IND = true: the spectrum is the shell indicator (count fields, FP64).
+// IND with wtab: the indicator weighted by wtab[|m|^2] (a function of |m|).
 template <typename T, bool IND, int... Rs>
 __global__ void __launch_bounds__(kThreads) inv_x_kernel(const float2 *__restrict__ box, BoxGeom bg,
                                                          const BinGeom *__restrict__ geom, int bin0,
                                                          typename V2<T>::t *__restrict__ A, int nl,
                                                          FftFactors f,
-                                                         const typename V2<T>::t *__restrict__ tw) {
+                                                         const typename V2<T>::t *__restrict__ tw,
+                                                         const double *__restrict__ wtab = nullptr) {
     typedef typename V2<T>::t C;
     extern __shared__ __align__(16) unsigned char smraw[];
     C *a = reinterpret_cast<C *>(smraw);
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) inv_x_kernel(const float2 *__restric
         if (s < g.thr_lo || s >= g.thr_hi) continue;
         C v;
         if (IND) {
-            v = C{T(1), T(0)};
+            v = C{T(wtab ? wtab[s] : 1.0), T(0)};
         } else {
             float2 d = box[g.box_off + ((long long)jx * bg.D + gjy) * bg.Dz + mz];
             v = C{T(d.x), T(d.y)};
@@ -657,7 +659,7 @@ void launch_inverse_x_geom(Plan &p, const BinGeom *geom, int nb, int nvb) {
 #undef FBS_PICK
     allow_smem(k, sm);
     dim3 grid(max_inv_x_grid(p, 0, nb, nl), nvb);
-    k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, geom, 0, p.d_A, nl, p.fM, p.d_twM);
+    k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, geom, 0, p.d_A, nl, p.fM, p.d_twM, nullptr);
     FBS_CUDA(cudaGetLastError());
 }
 
@@ -713,7 +715,7 @@ void launch_inverse_yz_slab_geom(Plan &p, int x0, int nx, float *islab, const Bi
 // ([bin - bin0][x][y][z], side H = N/2+1).  Uses scratch A64/G64 sized for
 // the group (allocated by the caller through the plan, freed after).
 void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
-                                   double2 *G64, const BinGeom *d_geom_grp) {
+                                   double2 *G64, const BinGeom *d_geom_grp, const double *wtab) {
     const int N = p.M;  // count fields live on the evaluation grid
     const int H = N / 2 + 1;
     const int nl = lines_per_cta<double>(N);
@@ -723,7 +725,7 @@ void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, doub
         auto k = inv_x_kernel<double, true>;
         allow_smem(k, sm);
         dim3 grid(max_inv_x_grid(p, bin0, nb, nl), nb);
-        k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, d_geom_grp, 0, A64, nl, p.fM, p.d_tw64);
+        k<<<grid, kThreads, sm, p.stream>>>(p.d_box, p.boxM, d_geom_grp, 0, A64, nl, p.fM, p.d_tw64, wtab);
         FBS_CUDA(cudaGetLastError());
     }
     {

@@ -317,61 +317,68 @@ static void candidates(const Plan &p, const std::vector<long long> &mn,
     }
 }
 
-// FP64 count fields on the octant, then the count sums of all candidates.
-static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<int> &qc,
-                         std::vector<double> &tden, std::vector<double> &qden) {
+// FP64 fields on the octant of the level's grid -- for every weight table
+// (nullptr: the plain shell indicator, the count field N_b of Eq. delta_nr)
+// and every bin of the level, row f * nbins + b -- then the octant sums of
+// the products of the rows each item names (arity rows per item).
+static void octant_sums(Plan &p, const std::vector<const double *> &wtabs, const std::vector<int> &items,
+                        int arity, std::vector<double> &den) {
     const int N = p.M, H = N / 2 + 1;  // the evaluation grid (exact for these products)
     const long long H3 = (long long)H * H * H;
-    const int nb = p.nbins;
-    AsyncBuf noct_buf((size_t)nb * H3 * sizeof(double), p.stream, "count fields");
+    const int nb = p.nbins, nf = (int)wtabs.size();
+    const int n = (int)(items.size() / arity);
+    den.assign(n, 0.0);
+    if (n == 0) return;
+    AsyncBuf noct_buf((size_t)nf * nb * H3 * sizeof(double), p.stream, "octant fields");
     double *noct = noct_buf.as<double>();
     // bin groups bounded by ~2 GB of FP64 scratch
     const long long budget = 2LL << 30;
-    int b0 = 0;
-    while (b0 < nb) {
-        long long a_el = 0, g_el = 0;
-        int b1 = b0;
-        std::vector<BinGeom> gg;
-        while (b1 < nb) {
-            const BinGeom &g = p.geom[b1];
-            long long da = g.empty ? 0 : (long long)N * g.Db * g.Dzb;
-            long long dg = g.empty ? 0 : (long long)H * N * g.Dzb;
-            if (b1 > b0 && (a_el + da + g_el + dg) * 16 > budget) break;
-            BinGeom q = g;
-            q.A_off = a_el;
-            q.G_off = g_el;
-            gg.push_back(q);
-            a_el += da;
-            g_el += dg;
-            ++b1;
+    for (int f = 0; f < nf; ++f) {
+        int b0 = 0;
+        while (b0 < nb) {
+            long long a_el = 0, g_el = 0;
+            int b1 = b0;
+            std::vector<BinGeom> gg;
+            while (b1 < nb) {
+                const BinGeom &g = p.geom[b1];
+                long long da = g.empty ? 0 : (long long)N * g.Db * g.Dzb;
+                long long dg = g.empty ? 0 : (long long)H * N * g.Dzb;
+                if (b1 > b0 && (a_el + da + g_el + dg) * 16 > budget) break;
+                BinGeom q = g;
+                q.A_off = a_el;
+                q.G_off = g_el;
+                gg.push_back(q);
+                a_el += da;
+                g_el += dg;
+                ++b1;
+            }
+            {
+                AsyncBuf A64(std::max<long long>(1, a_el) * 16, p.stream, "count scratch");
+                AsyncBuf G64(std::max<long long>(1, g_el) * 16, p.stream, "count scratch");
+                AsyncBuf dgeom(gg.size() * sizeof(BinGeom), p.stream, "count scratch");
+                FBS_CUDA(cudaMemcpyAsync(dgeom.ptr, gg.data(), gg.size() * sizeof(BinGeom), cudaMemcpyHostToDevice,
+                                         p.stream));
+                launch_count_fields_fp64_impl(p, noct + ((long long)f * nb + b0) * H3, b0, b1 - b0,
+                                              A64.as<double2>(), G64.as<double2>(), dgeom.as<BinGeom>(), wtabs[f]);
+            }
+            FBS_CUDA(cudaStreamSynchronize(p.stream));  // gg goes out of scope
+            b0 = b1;
         }
-        {
-            AsyncBuf A64(std::max<long long>(1, a_el) * 16, p.stream, "count scratch");
-            AsyncBuf G64(std::max<long long>(1, g_el) * 16, p.stream, "count scratch");
-            AsyncBuf dgeom(gg.size() * sizeof(BinGeom), p.stream, "count scratch");
-            FBS_CUDA(cudaMemcpyAsync(dgeom.ptr, gg.data(), gg.size() * sizeof(BinGeom), cudaMemcpyHostToDevice,
-                                     p.stream));
-            launch_count_fields_fp64_impl(p, noct + (long long)b0 * H3, b0, b1 - b0, A64.as<double2>(),
-                                          G64.as<double2>(), dgeom.as<BinGeom>());
-        }
-        FBS_CUDA(cudaStreamSynchronize(p.stream));  // gg goes out of scope
-        b0 = b1;
     }
-    auto run = [&](const std::vector<int> &items, int arity, std::vector<double> &den) {
-        int n = (int)(items.size() / arity);
-        den.assign(n, 0.0);
-        if (n == 0) return;
-        AsyncBuf items_buf(items.size() * sizeof(int), p.stream, "count items");
-        AsyncBuf den_buf(n * sizeof(double), p.stream, "count items");
-        FBS_CUDA(cudaMemcpyAsync(items_buf.ptr, items.data(), items.size() * sizeof(int),
-                                 cudaMemcpyHostToDevice, p.stream));
-        launch_count_contraction(p, noct, nb, 0, items_buf.as<int>(), n, arity, den_buf.as<double>());
-        FBS_CUDA(cudaMemcpyAsync(den.data(), den_buf.ptr, n * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
-        FBS_CUDA(cudaStreamSynchronize(p.stream));
-    };
-    run(tc, 3, tden);
-    run(qc, 4, qden);
+    AsyncBuf items_buf(items.size() * sizeof(int), p.stream, "count items");
+    AsyncBuf den_buf(n * sizeof(double), p.stream, "count items");
+    FBS_CUDA(cudaMemcpyAsync(items_buf.ptr, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             p.stream));
+    launch_count_contraction(p, noct, nf * nb, 0, items_buf.as<int>(), n, arity, den_buf.as<double>());
+    FBS_CUDA(cudaMemcpyAsync(den.data(), den_buf.ptr, n * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
     FBS_CUDA(cudaStreamSynchronize(p.stream));
+}
+
+// FP64 count fields on the octant, then the count sums of all candidates.
+static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<int> &qc,
+                         std::vector<double> &tden, std::vector<double> &qden) {
+    octant_sums(p, {nullptr}, tc, 3, tden);
+    octant_sums(p, {nullptr}, qc, 4, qden);
 }
 
 // Round sum_n N..N / N_pix to the count.  The FP64 sum carries rounding
@@ -1489,6 +1496,87 @@ fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double 
     }
     return FBS_OK;
     FBS_GUARD_END
+}
+
+fbs_status fbs_plan_triangle_average(fbs_plan *plan, const double *w, int nfunc, int64_t nw, const int32_t *terms,
+                                     const double *coef, int nterms, double *out) {
+    if (!plan || !w || nfunc < 1 || !terms || !coef || nterms < 1 || !out) {
+        set_error("fbs_plan_triangle_average: bad argument");
+        return FBS_ERR_ARG;
+    }
+    if (nw < plan->thr[plan->nbins]) {
+        set_error("weight tables must cover every |m|^2 below the top edge (nw >= " +
+                  std::to_string(plan->thr[plan->nbins]) + ")");
+        return FBS_ERR_ARG;
+    }
+    for (int k = 0; k < 3 * nterms; ++k)
+        if (terms[k] < 0 || terms[k] >= nfunc) {
+            set_error("fbs_plan_triangle_average: term names a function outside [0, nfunc)");
+            return FBS_ERR_ARG;
+        }
+    FBS_GUARD_BEGIN
+    FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    // the tables, on the device for the weighted count fields
+    AsyncBuf wbuf((size_t)nfunc * nw * sizeof(double), plan->stream, "weight tables");
+    FBS_CUDA(cudaMemcpyAsync(wbuf.ptr, w, (size_t)nfunc * nw * sizeof(double), cudaMemcpyHostToDevice, plan->stream));
+    std::vector<double> acc(plan->ntri.size(), 0.0);
+    for (Plan *lp : plan->levels) {
+        Plan &lv = *lp;
+        const int nt = (int)lv.ntri.size();
+        if (nt == 0) continue;
+        // only the functions some term uses get fields
+        std::vector<int> fmap(nfunc, -1);
+        std::vector<const double *> tabs;
+        for (int k = 0; k < 3 * nterms; ++k)
+            if (fmap[terms[k]] < 0) {
+                fmap[terms[k]] = (int)tabs.size();
+                tabs.push_back(wbuf.as<double>() + (size_t)terms[k] * nw);
+            }
+        std::vector<int> items;
+        items.reserve((size_t)nt * nterms * 3);
+        for (int t = 0; t < nt; ++t)
+            for (int k = 0; k < nterms; ++k)
+                for (int j = 0; j < 3; ++j) items.push_back(fmap[terms[3 * k + j]] * lv.nbins + lv.trip[3 * t + j]);
+        std::vector<double> sums;
+        octant_sums(lv, tabs, items, 3, sums);
+        // sum over the M^3 grid / M^3 = the sum over the closed ordered triples
+        const double npix = (double)lv.M * lv.M * lv.M;
+        for (int t = 0; t < nt; ++t) {
+            double v = 0.0;
+            for (int k = 0; k < nterms; ++k) v += coef[k] * sums[(size_t)t * nterms + k];
+            acc[lv.gtrip[t]] = v / npix / (double)lv.ntri[t];
+        }
+    }
+    memcpy(out, acc.data(), acc.size() * sizeof(double));
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_plan_shell_average(const fbs_plan *plan, const double *w, int64_t nw, double *out) {
+    if (!plan || !w || !out) return FBS_ERR_ARG;
+    const int N = plan->N, nb = plan->nbins;
+    const long long top = plan->thr[nb];
+    if (nw < top) {
+        set_error("the table must cover every |m|^2 below the top edge");
+        return FBS_ERR_ARG;
+    }
+    // every lattice mode with components in [-N/2, N/2), by bin
+    std::vector<double> sum(nb, 0.0);
+    std::vector<long long> cnt(nb, 0);
+    std::vector<int> lut((size_t)std::max<long long>(top, 1), -1);
+    for (int b = 0; b < nb; ++b)
+        for (long long v = plan->thr[b]; v < plan->thr[b + 1]; ++v) lut[v] = b;
+    const int Rm = std::min(isqrt_floor(top - 1), N / 2);
+    for (int x = -Rm; x <= std::min(Rm, N / 2 - 1); ++x)
+        for (int y = -Rm; y <= std::min(Rm, N / 2 - 1); ++y)
+            for (int z = -Rm; z <= std::min(Rm, N / 2 - 1); ++z) {
+                const long long v = (long long)x * x + (long long)y * y + (long long)z * z;
+                if (v >= top || lut[v] < 0) continue;
+                sum[lut[v]] += w[v];
+                cnt[lut[v]] += 1;
+            }
+    for (int b = 0; b < nb; ++b) out[b] = cnt[b] ? sum[b] / (double)cnt[b] : nan("");
+    return FBS_OK;
 }
 
 fbs_status fbs_plan_quads_connected(const fbs_plan *plan, double *nconn) {

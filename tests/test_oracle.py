@@ -665,3 +665,78 @@ def test_rebinned_single_cell_is_the_count_weighted_mean():
     w = sum(len(set(itertools.permutations(t))) * n * b for t, n, b in zip(d["triplets"], d["N_tri"], d["B"]))
     c = sum(len(set(itertools.permutations(t))) * n for t, n in zip(d["triplets"], d["N_tri"]))
     assert abs(B[0, 0, 0] - w / c) <= 1e-12 * abs(B[0, 0, 0])
+
+
+# ---------------------------------------------------------------- theory over exact triangles
+def _tables(N, L, funcs):
+    kf = 2 * math.pi / L
+    s = np.arange(3 * (N // 2) ** 2 + 1, dtype=np.float64)
+    k = kf * np.sqrt(s)
+    return np.stack([f(k) for f in funcs])
+
+
+def test_triangle_average_of_one_is_one_and_counts_match():
+    N, L = 12, 40.0
+    edges = fields.linear_edges(N, L, 4)
+    d = oracle.direct_bispectrum(fields.lognormal(N, 0.5, -1.0, seed=41), L, edges)
+    avg, cnt = oracle.triangle_average(N, L, edges, d["triplets"], _tables(N, L, [np.ones_like]), [(0, 0, 0)], [1.0])
+    assert np.array_equal(cnt, d["N_tri"])
+    assert np.allclose(avg, 1.0, rtol=1e-15, atol=0)
+
+
+def test_triangle_average_local_model_equals_fft_route():
+    # 2f sum_closed [P1 P2 + P2 P3 + P3 P1] / N_tri by enumeration, against
+    # (1/N_pix) sum_x (W_a W_b C_c + ...) with W the inverse DFT of P on the
+    # shell and C the count field (the Kronecker-delta identity of Sec. 2)
+    N, L, f = 16, 60.0, 0.7
+    edges = fields.linear_edges(N, L, 4)
+    thr = oracle.thresholds(edges, L)
+    trip = oracle.closed_triplets(N, L, edges)
+    Pk = lambda k: np.where(k > 0, 1.0 / np.maximum(k, 1e-30) ** 1.5, 0.0)
+    avg, cnt = oracle.triangle_average(N, L, edges, trip, _tables(N, L, [Pk, np.ones_like]),
+                                       [(0, 0, 1), (1, 0, 0), (0, 1, 0)], [2 * f] * 3)
+    bins = oracle.bin_index(N, thr)
+    kf = 2 * math.pi / L
+    kk = kf * np.sqrt(oracle.mode_squares(N).astype(float))
+    npix = float(N ** 3)
+    W = {b: (np.fft.ifftn(np.where(bins == b, Pk(kk), 0.0)) * npix).real for b in range(len(thr) - 1)}
+    C = {b: (np.fft.ifftn((bins == b).astype(float)) * npix).real for b in range(len(thr) - 1)}
+    for (a, b, c), v, n in zip(trip, avg, cnt):
+        ref = 2 * f * (np.sum(W[a] * W[b] * C[c]) + np.sum(C[a] * W[b] * W[c]) + np.sum(W[a] * C[b] * W[c])) / npix / n
+        assert abs(v - ref) <= 1e-10 * abs(ref)
+
+
+def test_tree_level_separable_form_equals_per_triangle_kernel():
+    # Eq. PT_Bi evaluated with the wave vectors of every triangle, against
+    # its separable form in u = k^2 (k1.k2 = (k3^2 - k1^2 - k2^2)/2 on a
+    # closed triangle), both averaged over the same triangles
+    N, L, kappa = 12, 30.0, 3.0 / 7.0
+    edges = fields.linear_edges(N, L, 3)
+    trip = oracle.closed_triplets(N, L, edges)
+    Pk = lambda k: np.where(k > 0, 1.0 / (1.0 + np.maximum(k, 1e-30) ** 2), 0.0)
+
+    def F(x, y):
+        kx, ky = np.linalg.norm(x, axis=1), np.linalg.norm(y, axis=1)
+        mu = np.sum(x * y, axis=1) / (kx * ky)
+        return (1 + kappa) / 2 + mu / 2 * (kx / ky + ky / kx) + (1 - kappa) / 2 * mu * mu
+
+    def model(k1, k2, k3):
+        P1, P2, P3 = (Pk(np.linalg.norm(k, axis=1)) for k in (k1, k2, k3))
+        return 2 * F(k1, k2) * P1 * P2 + 2 * F(k2, k3) * P2 * P3 + 2 * F(k3, k1) * P3 * P1
+
+    ref, cnt = oracle.triangle_average_direct(N, L, edges, trip, model)
+    u = lambda k: k * k
+    funcs = [Pk, lambda k: np.where(k > 0, Pk(k) / np.maximum(u(k), 1e-30), 0.0), u, lambda k: Pk(k) * u(k),
+             lambda k: u(k) ** 2, np.ones_like]
+    one = [(0, 0, 5, (1 + kappa) / 2), (0, 1, 2, kappa / 2), (1, 0, 2, kappa / 2), (3, 1, 5, -(1 + kappa) / 4),
+           (1, 3, 5, -(1 + kappa) / 4), (1, 1, 4, (1 - kappa) / 4)]
+    terms, coef = [], []
+    for cyc in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        for fx, fy, fz, c in one:
+            t = [0, 0, 0]
+            t[cyc[0]], t[cyc[1]], t[cyc[2]] = fx, fy, fz
+            terms.append(t)
+            coef.append(c)
+    avg, cnt2 = oracle.triangle_average(N, L, edges, trip, _tables(N, L, funcs), terms, coef)
+    assert np.array_equal(cnt, cnt2)
+    assert np.allclose(avg, ref, rtol=1e-9, atol=1e-12 * np.max(np.abs(ref)))
