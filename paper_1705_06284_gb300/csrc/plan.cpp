@@ -467,7 +467,13 @@ static long long slab_budget_bytes() {
 }
 
 // ---------------------------------------------------------------- levels
-static constexpr int kMinLevelGrid = 128;
+// Smallest level grid of multi-level plans.  BF16x3 products carry ~2^-17
+// relative rounding each; a level's sums average it over M^3 points, so the
+// error of a cancelling item grows like (N/M)^(3/2) on smaller grids.  Over
+// every triplet of 256^3 workloads (32 linear and 48 log bins, gated on the
+// FP64 cancellation-free scale) the worst BF16x3 error was 1.1e-4 with
+// levels down to M = 32 and 3.8e-5 with M >= 64, against the 2e-4 gate.
+static constexpr int kMinLevelGrid = 64;
 
 // Plan-time results carried over from an exported plan: the closed items
 // (global bins, ascending) and their exact counts.
@@ -651,8 +657,8 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
     std::vector<int> Rb(nb, -1);
     for (int b = 0; b < nb; ++b)
         if (p.shell[b]) Rb[b] = R[b];
-    // FBS_LEVEL_COST overrides the model's fixed cost per level (0 lets small
-    // plans split into levels too, as tests do)
+    // FBS_LEVEL_COST overrides the model's fixed cost per level (a negative
+    // cost makes even small plans split into levels, as tests do)
     double per_level = 1e8;
     if (const char *e = getenv("FBS_LEVEL_COST")) per_level = atof(e);
     // the smallest level grid (FBS_MIN_LEVEL_GRID overrides): BF16 split
@@ -660,7 +666,9 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
     // over enough points for it to average out on cancelling items
     int min_grid = kMinLevelGrid;
     if (const char *e = getenv("FBS_MIN_LEVEL_GRID")) min_grid = atoi(e);
-    const LevelChoice lc = choose_levels(N, nb, Rb, items, single_M, fast_grids(), 4, per_level, min_grid);
+    // (a single-grid plan keeps its documented grid M > pR)
+    const LevelChoice lc = choose_levels(N, nb, Rb, items, single_M, fast_grids(), 4, per_level,
+                                         single_M > 0 ? 0 : min_grid);
     const std::vector<int> &grids = lc.grids;
     for (int M : grids) new_level(p, M);
     std::vector<std::vector<int>> lt(grids.size()), lq(grids.size());  // candidate (global) items per level

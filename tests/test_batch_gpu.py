@@ -65,7 +65,7 @@ def test_graph_of_batches_equals_eager_and_single_calls(tmp_path, monkeypatch, p
 
 def test_batch_on_multi_level_plans(monkeypatch):
     import torch
-    monkeypatch.setenv("FBS_LEVEL_COST", "0")
+    monkeypatch.setenv("FBS_LEVEL_COST", "-1e15")
     monkeypatch.setenv("FBS_MIN_LEVEL_GRID", "0")
     N, L = 48, 60.0
     edges = fields.log_edges(N, L, 8)

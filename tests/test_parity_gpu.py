@@ -307,10 +307,10 @@ def test_pinned_host_outputs_filled_once_the_stream_passes():
 def test_levels_match_single_grid_and_oracle(monkeypatch, N, L, kind, nb, precision, quads):
     """Items summed on per-level grids (each M above the item's degree
     R_a + R_b + R_c (+ R_d)) give the same B, P, T as one grid for all, and the
-    oracle's.  FBS_LEVEL_COST=0 and FBS_MIN_LEVEL_GRID=0 let these small plans
-    split into levels."""
+    oracle's.  A negative FBS_LEVEL_COST and FBS_MIN_LEVEL_GRID=0 make these
+    small plans split into levels."""
     import torch
-    monkeypatch.setenv("FBS_LEVEL_COST", "0")
+    monkeypatch.setenv("FBS_LEVEL_COST", "-1e15")
     monkeypatch.setenv("FBS_MIN_LEVEL_GRID", "0")
     edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
     f32 = _field("quadratic", N, 61).astype(np.float32)

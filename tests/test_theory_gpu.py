@@ -65,7 +65,7 @@ def test_models_match_per_triangle_average(N, L, nb, kind):
 
 def test_theory_on_a_multi_level_plan(monkeypatch):
     # items on several evaluation grids: each level sums its own triplets
-    monkeypatch.setenv("FBS_LEVEL_COST", "0")
+    monkeypatch.setenv("FBS_LEVEL_COST", "-1e15")
     monkeypatch.setenv("FBS_MIN_LEVEL_GRID", "0")
     N, L = 32, 80.0
     edges = fields.log_edges(N, L, 8)
