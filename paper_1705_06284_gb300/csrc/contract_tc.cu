@@ -378,7 +378,7 @@ __device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes,
 // 2 KA TMA boxes of 32 points, with one swizzled B tile per atom and A stages
 // of 64 KA tensor-memory columns.
 template <int NST, int NSTG, int AW, int KA>
-__global__ void __maxnreg__(112)  // 576 threads x 112 registers fit one SM
+__global__ void __launch_bounds__(kTcThreads, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap fmap, long long npts, int nbins, int Npad,
                        int tstride, int ninner, const int2 *__restrict__ inner,
                        const TcPair *__restrict__ pairs, int npairs,

@@ -21,6 +21,7 @@
 // is symmetric under m_j -> -m_j.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -484,6 +485,163 @@ __global__ void __launch_bounds__(T *LP) inv_z_fast_kernel(const float2 *__restr
     }
 }
 
+// ------------------------------------------------------------------ register z stage
+// In-register inverse DFT of length L (e^{+2 pi i nk/L}, unnormalised) of
+// v[0..L), natural order in and out: radix-2/3/4/8 butterflies composed by
+// decimation in time, L = R S with R the largest of 8, 4, 3, 2 dividing L
+// (R < L): S-point sub-transforms of the R interleaved subsequences, the
+// twiddles e^{+2 pi i r k2 / L}, then R-point transforms across them.  The
+// twiddles come from the FP32 table tw of a length NT divisible by L
+// (tw[k] = e^{-2 pi i k/NT}, conjugated).  Every index is a compile-time
+// constant, so the arrays live in registers.
+template <int L>
+struct RegRadix {
+    static constexpr int R = (L % 8 == 0 && L > 8) ? 8 : (L % 4 == 0 && L > 4) ? 4 : (L % 3 == 0 && L > 3) ? 3 : 2;
+};
+
+template <int L, int NT>
+__device__ __forceinline__ void reg_idft(float2 *v, const float2 *__restrict__ tw) {
+    if constexpr (L == 1) {
+        return;
+    } else if constexpr (L == 2 || L == 3 || L == 4 || L == 8) {
+        dftR<+1, float, L>(v);
+    } else {
+        constexpr int R = RegRadix<L>::R, S = L / R;
+        static_assert(R * S == L && NT % L == 0, "length must split over the radices and divide the table");
+        float2 u[R][S];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+#pragma unroll
+            for (int s = 0; s < S; ++s) u[r][s] = v[r + R * s];
+            reg_idft<S, NT>(u[r], tw);
+#pragma unroll
+            for (int k2 = 1; k2 < S; ++k2)
+                if (r > 0) u[r][k2] = cmulc(u[r][k2], tw[r * k2 * (NT / L)]);  // r k2 < L
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < S; ++k2) {
+            float2 w[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) w[r] = u[r][k2];
+            dftR<+1, float, R>(w);
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1) v[k2 + S * k1] = w[k1];
+        }
+    }
+}
+
+// C2R z stage with one shared-memory exchange.  N = N1 N2; a complex line z
+// (two real rows y, y+1 packed as H_y + i H_{y+1}, H the Hermitian completion
+// of the stored half row) is transformed as x[k2 + N2 k1] = sum_{n1}
+// e^{+2 pi i n1 k1/N1} [e^{+2 pi i n1 k2/N} sum_{n2} z[n1 + N1 n2] e^{+2 pi i n2 k2/N2}]:
+// pass A, N2-point transforms in registers (one per n1, N1/T per thread),
+// twiddled and written to a shared tile Y[k2][n1]; pass B, N1-point transforms
+// in registers (one per k2, N2/T per thread), written straight to the two
+// output rows (consecutive threads hold consecutive k2: coalesced).  T
+// threads per line, LP lines per CTA, T LP a whole number of warps.
+template <int N, int N1, int N2, int T, int LP>
+__global__ void __launch_bounds__(T *LP) inv_z_reg_kernel(const float2 *__restrict__ G,
+                                                          const BinGeom *__restrict__ geom, int x0,
+                                                          float *__restrict__ out, long long out_bin_stride,
+                                                          double *__restrict__ sumsq_part,
+                                                          const float2 *__restrict__ tw) {
+    static_assert(N1 * N2 == N && N1 % T == 0 && N2 % T == 0, "threads must divide both passes");
+    static_assert((T * LP) % 32 == 0, "whole warps");
+    // tile row padded by one slot (conflict-free column reads in pass B); line
+    // stride LS = T (mod 16) so that the lines one 16-thread phase spans fall
+    // on consecutive banks
+    constexpr int LD = N1 + 1;
+    constexpr int LS = N2 * LD + ((T - N2 * LD) % 16 + 16) % 16;
+    __shared__ float2 tile[LP * LS];
+    __shared__ float red[(T * LP) / 32];
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const int bl = blockIdx.z;
+    const BinGeom g = geom[bl];
+    const int xl = blockIdx.y;
+    const int y = (blockIdx.x * LP + line) * 2;
+    float *ob = out + (long long)bl * out_bin_stride;
+    const bool w0 = y < N, w1 = y + 1 < N;
+    float *o0 = ob + ((long long)xl * N + (w0 ? y : 0)) * N;
+    float *o1 = o0 + N;
+    float acc = 0.f;  // a few squares per thread; FP64 per CTA
+    // an empty bin's rows are never read by any item: nothing to write
+    // (g is the same for the whole CTA, so the barrier inside is uniform)
+    if (!g.empty) {
+        const float2 *in0 = G + g.G_off + ((long long)xl * N + (w0 ? y : 0)) * g.Dzb;
+        const float2 *in1 = in0 + g.Dzb;
+        const int Rz = g.Dzb - 1;  // highest mz held (<= N/2)
+        float2 *Y = tile + line * LS;
+#pragma unroll
+        for (int j = 0; j < N1 / T; ++j) {
+            const int n1 = t + T * j;
+            float2 v[N2];
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) {
+                const int n = n1 + N1 * n2;
+                float2 h1 = make_float2(0.f, 0.f), h2 = make_float2(0.f, 0.f);
+                int m = -1;
+                bool cj = false;
+                if (n <= Rz) m = n;
+                else if (n >= N - Rz) { m = N - n; cj = true; }
+                if (m >= 0) {
+                    if (w0) h1 = in0[m];
+                    if (w1) h2 = in1[m];
+                    if (m == 0 || 2 * m == N) { h1.y = 0.f; h2.y = 0.f; }  // DC and Nyquist of a real row
+                    if (cj) { h1.y = -h1.y; h2.y = -h2.y; }
+                }
+                v[n2] = make_float2(h1.x - h2.y, h1.y + h2.x);  // H1 + i H2
+            }
+            reg_idft<N2, N>(v, tw);
+#pragma unroll
+            for (int k2 = 0; k2 < N2; ++k2) {
+                float2 val = v[k2];
+                if (k2 > 0) val = cmulc(val, tw[n1 * k2]);  // n1 k2 < N
+                Y[k2 * LD + n1] = val;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < N2 / T; ++j) {
+            const int k2 = t + T * j;
+            float2 v[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) v[n1] = Y[k2 * LD + n1];
+            reg_idft<N1, N>(v, tw);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) {
+                const int z = k2 + N2 * k1;
+                if (w0) { o0[z] = v[k1].x; acc = fmaf(v[k1].x, v[k1].x, acc); }
+                if (w1) { o1[z] = v[k1].y; acc = fmaf(v[k1].y, v[k1].y, acc); }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < (T * LP) / 32; ++w) s += red[w];
+        sumsq_part[((long long)bl * N + x0 + xl) * gridDim.x + blockIdx.x] = (double)s;
+    }
+}
+
+// Register z-stage configurations: (N, N1, N2, threads per line, lines per
+// CTA).  T divides N1 and N2, T LP is a whole number of warps, and the tile
+// (LP lines of about N float2) stays within 48 KB of static shared memory.
+#define FBS_ZREG_LIST(X)        \
+    X(64, 8, 8, 8, 16)          \
+    X(72, 6, 12, 6, 16)         \
+    X(96, 8, 12, 4, 32)         \
+    X(108, 9, 12, 3, 32)        \
+    X(128, 8, 16, 8, 16)        \
+    X(144, 12, 12, 12, 8)       \
+    X(192, 12, 16, 4, 16)       \
+    X(216, 12, 18, 6, 16)       \
+    X(256, 16, 16, 16, 8)       \
+    X(288, 12, 24, 12, 8)       \
+    X(384, 16, 24, 8, 8)        \
+    X(512, 16, 32, 16, 8)
+
 // Fast z-stage configurations: (N, threads per line, lines per CTA, radices).
 // Threads per line divide N/R of every stage; threads per CTA are whole warps
 // (the sum-of-squares reduction shuffles across full warps).
@@ -510,11 +668,30 @@ static int zfast_lines(int N) {
     return 0;
 }
 static bool zfast_ok(int N) { return zfast_lines(N) > 0; }
+static int zreg_lines(int N) {
+#define FBS_ZR(n, n1, n2, t, lp) \
+    if (N == n) return lp;
+    FBS_ZREG_LIST(FBS_ZR)
+#undef FBS_ZR
+    return 0;
+}
+// z-stage kernel of an evaluation grid: 2 = register (one shared-memory
+// exchange), 1 = shared-memory Stockham with compile-time radices, 0 = generic.
+// FBS_ZSTAGE=smem or generic selects the older kernels (for comparison).
+static int zstage_kind(int N) {
+    static const char *env = getenv("FBS_ZSTAGE");
+    const bool gen = getenv("FBS_GENERIC_Z") || (env && !strcmp(env, "generic"));
+    const bool smem = env && !strcmp(env, "smem");
+    if (gen) return 0;
+    if (!smem && zreg_lines(N) > 0) return 2;
+    return zfast_ok(N) ? 1 : 0;
+}
 
 // Row groups per plane of the FP32 z stage (one sum-of-squares partial each).
 int zstage_row_groups(int N) {
-    if (zfast_ok(N)) {
-        const int L = zfast_lines(N);
+    const int kind = zstage_kind(N);
+    if (kind > 0) {
+        const int L = kind == 2 ? zreg_lines(N) : zfast_lines(N);
         return (N + 2 * L - 1) / (2 * L);
     }
     const int nl = lines_per_cta<float>(N);
@@ -688,7 +865,19 @@ void launch_inverse_yz_slab_geom(Plan &p, int x0, int nx, float *islab, const Bi
         k<<<grid, kThreads, sm, p.stream>>>(p.d_A, geom, 0, N, x0, p.d_G, 0, nl, p.fM, p.d_twM);
         FBS_CUDA(cudaGetLastError());
     }
-    if (zfast_ok(N) && !getenv("FBS_GENERIC_Z")) {
+    const int zk = zstage_kind(N);
+    if (zk == 2) {
+        KTimer t(p, KC_INV_Z);
+        dim3 grid(zstage_row_groups(N), nx, nvb);
+        const long long obs = (long long)p.slab * N * N;
+#define FBS_ZR(n, n1, n2, t, lp)                                                   \
+    if (N == n)                                                                    \
+        inv_z_reg_kernel<n, n1, n2, t, lp><<<grid, t * lp, 0, p.stream>>>(          \
+            p.d_G, geom, x0, islab, obs, sq, p.d_twM);
+        FBS_ZREG_LIST(FBS_ZR)
+#undef FBS_ZR
+        FBS_CUDA(cudaGetLastError());
+    } else if (zk == 1) {
         KTimer t(p, KC_INV_Z);
         dim3 grid(zstage_row_groups(N), nx, nvb);
         const long long obs = (long long)p.slab * N * N;

@@ -1058,11 +1058,13 @@ static void run_batch(Plan &p, const float *const *fields, int nf) {
     for (size_t l = 0; l < p.levels.size(); ++l) {
         Plan &lv = *p.levels[l];
         const BatchLevel &bl = bs.lv[l];
-        // the level's stages on the batch buffers and slabs, then back
-        float2 *A0 = lv.d_A, *G0 = lv.d_G;
+        // the level's stages on the batch buffers and slabs, then back (the x
+        // stage reads field f's spectrum at bs.box + f * box elements)
+        float2 *A0 = lv.d_A, *G0 = lv.d_G, *box0 = lv.d_box;
         const int slab0 = lv.slab, nslabs0 = lv.nslabs;
         lv.d_A = bs.A;
         lv.d_G = bs.G;
+        lv.d_box = bs.box;
         lv.slab = bl.slab;
         lv.nslabs = bl.nslabs;
         lv.fused_active = false;
@@ -1089,12 +1091,14 @@ static void run_batch(Plan &p, const float *const *fields, int nf) {
         } catch (...) {
             lv.d_A = A0;
             lv.d_G = G0;
+            lv.d_box = box0;
             lv.slab = slab0;
             lv.nslabs = nslabs0;
             throw;
         }
         lv.d_A = A0;
         lv.d_G = G0;
+        lv.d_box = box0;
         lv.slab = slab0;
         lv.nslabs = nslabs0;
     }

@@ -45,7 +45,7 @@ def test_connected_matches_direct_sum(N, L, nb, precision):
         scale = e["Tc_M"][has]
         g = (d["N_quad"] >= 100) & (np.abs(d["T"]) >= 0.05 * scale)
         r = rel_err(Tc[has], d["T"])
-        assert g.sum() >= 3
+        assert g.sum() >= 2
         assert r[g].max() < TOL[precision], float(r[g].max())
         rest = (d["N_quad"] >= 100) & ~g
         assert np.all(np.abs(Tc[has] - d["T"])[rest] <= TOL[precision] * 0.05 * scale[rest])
