@@ -740,3 +740,53 @@ def test_tree_level_separable_form_equals_per_triangle_kernel():
     avg, cnt2 = oracle.triangle_average(N, L, edges, trip, _tables(N, L, funcs), terms, coef)
     assert np.array_equal(cnt, cnt2)
     assert np.allclose(avg, ref, rtol=1e-9, atol=1e-12 * np.max(np.abs(ref)))
+
+
+# ---------------------------------------------------------------- exact quadruple counts
+QUAD_COUNT_CASES = [("lin", 8, 40.0, 3), ("log", 10, 25.0, 4), ("lin", 12, 30.0, 4), ("aliased", 10, 20.0, 3),
+                    ("full", 8, 10.0, None)]
+
+
+@pytest.mark.parametrize("kind,N,L,nb", QUAD_COUNT_CASES)
+def test_quad_counts_exact_equal_brute_force(kind, N, L, nb):
+    """The pair-count route gives the brute-force ordered quadruple counts of
+    every candidate (a <= b <= c <= d), including the zero ones."""
+    edges = _subset_case(kind, N, L, nb)
+    f = fields.lognormal(N, 0.5, -1.5, seed=11)
+    d = oracle.direct_trispectrum(f, L, edges)
+    cnt = d["ordered_cnt"]
+    k = cnt.shape[0]
+    cand = [q for q in itertools.combinations_with_replacement(range(k), 4)]
+    ex = oracle.quad_counts_exact(N, L, edges, cand)
+    assert ex == [int(cnt[q]) for q in cand]
+    assert any(v == 0 for v in ex) or kind in ("full", "aliased")  # wrapped sums close every candidate
+
+
+def test_quad_counts_exact_sum_rule_full_cover():
+    """Every mode in a bin: the ordered counts over all bin 4-tuples add up to
+    the number of closed mode quadruples, N_pix^3."""
+    N, L = 8, 10.0
+    edges = _full_cover_edges(N, L)
+    nb = len(edges) - 1
+    cand = list(itertools.combinations_with_replacement(range(nb), 4))
+    ex = oracle.quad_counts_exact(N, L, edges, cand)
+    total = 0
+    for q, v in zip(cand, ex):
+        perms = math.factorial(4)
+        for b in set(q):
+            perms //= math.factorial(q.count(b))
+        total += perms * v
+    assert total == (N ** 3) ** 3
+
+
+def test_quad_counts_exact_match_rounded_fft_sums():
+    """Below 2^53 the rounded FP64 count-field sums of the FFT estimator are
+    the same integers."""
+    N, L = 24, 60.0
+    edges = fields.log_edges(N, L, 6)
+    f = fields.lognormal(N, 0.5, -1.5, seed=12)
+    quads = list(itertools.combinations_with_replacement(range(6), 4))
+    e = oracle.fft_estimator(f, L, edges, triplets=[], quads=quads)
+    ex = oracle.quad_counts_exact(N, L, edges, quads)
+    assert max(ex) < 2 ** 53
+    assert ex == [int(v) for v in e["N_quad"]]
