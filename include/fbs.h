@@ -149,11 +149,18 @@ int fbs_plan_num_quads(const fbs_plan *plan);
 fbs_status fbs_plan_triplets(const fbs_plan *plan, int32_t *abc, int64_t *ntri);
 
 /* Copy the closed-quadruplet table: abcd[4*nquad] (a<=b<=c<=d) and
- * nquad_counts[nquad], the ordered quadruple counts sum_n N_a N_b N_c N_d / N_pix
- * as FP64.  Below 2^53 they are rounded to exact integers (like triangle
- * counts); wide shells on large grids give counts past 2^53 (even past int64),
- * which are returned as the FP64 sum.  Either pointer may be NULL. */
+ * nquad_counts[nquad], the ordered quadruple counts (the denominator of Eq.
+ * gen_Nspec3 with p = 4) as the nearest FP64 values of the exact counts of
+ * fbs_plan_quad_counts_u128 (exact below 2^53).  Either pointer may be NULL. */
 fbs_status fbs_plan_quads(const fbs_plan *plan, int32_t *abcd, double *nquad_counts);
+
+/* Exact ordered quadruple counts: words[2*nquad] (host), words[2q] the low
+ * and words[2q+1] the high 64 bits of quadruplet q's count as an unsigned
+ * 128-bit integer (wide shells on large grids pass 2^63).  Computed at plan
+ * time as sum_q C_ab(q) C_cd(q) of integer pair-count convolutions
+ * C_ab(q) = #{m1 in S_a, m2 in S_b : m1 + m2 = q}, in integer arithmetic;
+ * FBS_ERR_ARG for a NULL argument. */
+fbs_status fbs_plan_quad_counts_u128(const fbs_plan *plan, uint64_t *words);
 
 /* Copy shell sizes |S_b| (int64[nbins]) and, if thr != NULL, the integer
  * thresholds on |m|^2 (int64[nbins+1]): bin b holds thr[b] <= |m|^2 < thr[b+1]. */
@@ -362,8 +369,8 @@ double fbs_plan_create_ms(const fbs_plan *plan);
  * fails with FBS_ERR_NUMERIC when it exceeds 0.25). */
 double fbs_plan_count_margin(const fbs_plan *plan);
 
-/* 1 when every quadruple count of the plan is an exact integer (rounded
- * within 0.25 and below 2^53), 0 when some are FP64 sums, <0 on error. */
+/* 1 for a plan (its quadruple counts are exact integers, see
+ * fbs_plan_quad_counts_u128), <0 on error. */
 int fbs_plan_quad_counts_exact(const fbs_plan *plan);
 
 /* Side M of the largest evaluation grid of the plan (its last level). */

@@ -49,8 +49,18 @@ try:  # the same library transforms, multithreaded, where scipy is present
 
     def _ifftn(a):
         return _sfft.ifftn(a, workers=-1)
+
+    def _rfftn(a):
+        return _sfft.rfftn(a, workers=-1)
+
+    def _irfftn(a, s):
+        return _sfft.irfftn(a, s=s, workers=-1)
 except Exception:  # pragma: no cover
     _fftn, _ifftn = np.fft.fftn, np.fft.ifftn
+    _rfftn = np.fft.rfftn
+
+    def _irfftn(a, s):
+        return np.fft.irfftn(a, s=s)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
@@ -410,9 +420,10 @@ def pair_counts(bins: np.ndarray, a: int, b: int) -> np.ndarray:
     FFT's error is of order 1e-16 |S_a| |S_b| log N, far below 1/2 for any
     grid this oracle runs on; a value further than 0.25 from an integer
     raises."""
-    ia = (bins == a).astype(np.float64)
-    ib = ia if b == a else (bins == b).astype(np.float64)
-    c = np.real(_ifftn(_fftn(ia) * _fftn(ib)))
+    N = bins.shape[0]
+    fa = _rfftn((bins == a).astype(np.float64))
+    fb = fa if b == a else _rfftn((bins == b).astype(np.float64))
+    c = _irfftn(fa * fb, (N, N, N))
     r = np.rint(c)
     if r.size and float(np.max(np.abs(c - r))) > 0.25:
         raise ArithmeticError("pair-count convolution is not integral")

@@ -93,6 +93,7 @@ _SIGS = [
     ("fbs_plan_device_bytes", ctypes.c_int64, [_vp]),
     ("fbs_plan_count_margin", ctypes.c_double, [_vp]),
     ("fbs_plan_quad_counts_exact", ctypes.c_int, [_vp]),
+    ("fbs_plan_quad_counts_u128", ctypes.c_int, [_vp, _vp]),
     ("fbs_plan_eval_grid", ctypes.c_int, [_vp]),
     ("fbs_plan_slab_planes", ctypes.c_int, [_vp]),
     ("fbs_plan_num_slabs", ctypes.c_int, [_vp]),
@@ -250,6 +251,10 @@ class Plan:
         self.device_bytes = int(Lb.fbs_plan_device_bytes(_vp(self._h)))
         self.count_margin = float(Lb.fbs_plan_count_margin(_vp(self._h)))
         self.quad_counts_exact = bool(Lb.fbs_plan_quad_counts_exact(_vp(self._h)) == 1)
+        w = np.zeros(2 * max(self.nquad, 1), dtype=np.uint64)
+        _check(Lb.fbs_plan_quad_counts_u128(_vp(self._h), w.ctypes.data))
+        # exact ordered quadruple counts as Python integers (past 2^63 for wide shells)
+        self.N_quad_exact = [int(w[2 * i]) | (int(w[2 * i + 1]) << 64) for i in range(self.nquad)]
         self.eval_grid = int(Lb.fbs_plan_eval_grid(_vp(self._h)))
         self.slab_planes = int(Lb.fbs_plan_slab_planes(_vp(self._h)))
         self.num_slabs = int(Lb.fbs_plan_num_slabs(_vp(self._h)))

@@ -108,6 +108,12 @@ int zstage_row_groups(int N);
 // FP64 count fields N_b on the octant (wtab: weights w(|m|^2) instead of 1).
 void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, double2 *A64,
                                    double2 *G64, const BinGeom *d_geom_grp, const double *wtab = nullptr);
+// quad_counts.cu: exact ordered quadruple counts of the items (4 bins each,
+// rows of the FP64 octant count fields noct) on the plan's grid.
+struct U128 {
+    uint64_t lo = 0, hi = 0;
+};
+void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &items, std::vector<U128> &out);
 // contract.cu (FP64 count sums)
 void launch_count_contraction(Plan &p, const double *noct, int nb_in_group, int bin0,
                               const int *d_items, int nitems, int arity, double *d_sums);
@@ -175,7 +181,6 @@ struct Plan {
     cudaStream_t stream = nullptr;
     double create_ms = 0;
     double count_margin = 0;  // largest |sum N..N / N_pix - nearest integer| of the rounded counts
-    bool quad_counts_exact = true;  // false when some quadruple count is past 2^53
 
     std::vector<long long> thr;  // nbins+1
     std::vector<long long> shell;
@@ -190,7 +195,8 @@ struct Plan {
     std::vector<int32_t> trip;   // 3*ntrip
     std::vector<int64_t> ntri;
     std::vector<int32_t> quad;   // 4*nquad
-    std::vector<double> nquad;   // FP64 ordered quadruple counts (exact integers below 2^53)
+    std::vector<double> nquad;   // FP64 ordered quadruple counts (the nearest double of nquad128)
+    std::vector<U128> nquad128;  // exact ordered quadruple counts (root plan, output order)
     TaskList ttask, qtask;
     std::vector<int> tgrp, qgrp;  // item groups of the FP32 contraction (outer-pair ranges)
     int *d_tgrp = nullptr, *d_qgrp = nullptr;

@@ -319,18 +319,13 @@ static void candidates(const Plan &p, const std::vector<long long> &mn,
 
 // FP64 fields on the octant of the level's grid -- for every weight table
 // (nullptr: the plain shell indicator, the count field N_b of Eq. delta_nr)
-// and every bin of the level, row f * nbins + b -- then the octant sums of
-// the products of the rows each item names (arity rows per item).
-static void octant_sums(Plan &p, const std::vector<const double *> &wtabs, const std::vector<int> &items,
-                        int arity, std::vector<double> &den) {
+// and every bin of the level, row f * nbins + b.
+static std::unique_ptr<AsyncBuf> octant_fields(Plan &p, const std::vector<const double *> &wtabs) {
     const int N = p.M, H = N / 2 + 1;  // the evaluation grid (exact for these products)
     const long long H3 = (long long)H * H * H;
     const int nb = p.nbins, nf = (int)wtabs.size();
-    const int n = (int)(items.size() / arity);
-    den.assign(n, 0.0);
-    if (n == 0) return;
-    AsyncBuf noct_buf((size_t)nf * nb * H3 * sizeof(double), p.stream, "octant fields");
-    double *noct = noct_buf.as<double>();
+    auto noct_buf = std::make_unique<AsyncBuf>((size_t)nf * nb * H3 * sizeof(double), p.stream, "octant fields");
+    double *noct = noct_buf->as<double>();
     // bin groups bounded by ~2 GB of FP64 scratch
     const long long budget = 2LL << 30;
     for (int f = 0; f < nf; ++f) {
@@ -365,20 +360,49 @@ static void octant_sums(Plan &p, const std::vector<const double *> &wtabs, const
             b0 = b1;
         }
     }
+    return noct_buf;
+}
+
+// The octant sums of the products of the rows each item names (arity rows
+// per item) of the octant fields noct (nrows rows).
+static void octant_contract(Plan &p, const double *noct, int nrows, const std::vector<int> &items, int arity,
+                            std::vector<double> &den) {
+    const int n = (int)(items.size() / arity);
+    den.assign(n, 0.0);
+    if (n == 0) return;
     AsyncBuf items_buf(items.size() * sizeof(int), p.stream, "count items");
     AsyncBuf den_buf(n * sizeof(double), p.stream, "count items");
     FBS_CUDA(cudaMemcpyAsync(items_buf.ptr, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice,
                              p.stream));
-    launch_count_contraction(p, noct, nf * nb, 0, items_buf.as<int>(), n, arity, den_buf.as<double>());
+    launch_count_contraction(p, noct, nrows, 0, items_buf.as<int>(), n, arity, den_buf.as<double>());
     FBS_CUDA(cudaMemcpyAsync(den.data(), den_buf.ptr, n * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
     FBS_CUDA(cudaStreamSynchronize(p.stream));
 }
 
-// FP64 count fields on the octant, then the count sums of all candidates.
+static void octant_sums(Plan &p, const std::vector<const double *> &wtabs, const std::vector<int> &items,
+                        int arity, std::vector<double> &den) {
+    den.assign(items.size() / arity, 0.0);
+    if (items.empty()) return;
+    auto f = octant_fields(p, wtabs);
+    octant_contract(p, f->as<double>(), (int)wtabs.size() * p.nbins, items, arity, den);
+}
+
+// FP64 count fields on the octant, the count sums of all candidates, and the
+// exact quadruple counts from the same fields.
 static void exact_counts(Plan &p, const std::vector<int> &tc, const std::vector<int> &qc,
-                         std::vector<double> &tden, std::vector<double> &qden) {
-    octant_sums(p, {nullptr}, tc, 3, tden);
-    octant_sums(p, {nullptr}, qc, 4, qden);
+                         std::vector<double> &tden, std::vector<double> &qden, std::vector<U128> &qexact) {
+    tden.assign(tc.size() / 3, 0.0);
+    qden.assign(qc.size() / 4, 0.0);
+    qexact.assign(qc.size() / 4, U128{});
+    if (tc.empty() && qc.empty()) return;
+    auto f = octant_fields(p, {nullptr});
+    octant_contract(p, f->as<double>(), p.nbins, tc, 3, tden);
+    octant_contract(p, f->as<double>(), p.nbins, qc, 4, qden);
+    exact_quad_counts(p, f->as<double>(), qc, qexact);
+}
+
+static double u128_to_double(const U128 &v) {
+    return (double)(((unsigned __int128)v.hi << 64) | v.lo);  // correctly rounded
 }
 
 // Round sum_n N..N / N_pix to the count.  The FP64 sum carries rounding
@@ -478,16 +502,16 @@ static constexpr int kMinLevelGrid = 64;
 // Plan-time results carried over from an exported plan: the closed items
 // (global bins, ascending) and their exact counts.
 struct CountCache {
-    std::map<std::array<int, 4>, double> counts;  // triplets have b[3] = -1
+    std::map<std::array<int, 4>, double> counts;  // triplets (b[3] = -1)
+    std::map<std::array<int, 4>, U128> qcounts;   // quadruplets
     double margin = 0;
-    bool quad_exact = true;
 };
 
 // Serialised form (native byte order): "FBSC", version, N, flags, nbins,
 // L, thr[nbins+1], ntrip, ntrip x (a, b, c, N_tri), nquad,
-// nquad x (a, b, c, d, N_quad), count margin, quad-counts-exact flag.
+// nquad x (a, b, c, d, N_quad low 64 bits, N_quad high 64 bits), count margin.
 static constexpr uint32_t kCacheMagic = 0x43534246u;  // "FBSC"
-static constexpr uint32_t kCacheVersion = 1u;
+static constexpr uint32_t kCacheVersion = 2u;
 
 struct Writer {
     std::vector<unsigned char> b;
@@ -526,10 +550,10 @@ static std::vector<unsigned char> export_counts(const Plan &p) {
     w.put((int64_t)p.nquad.size());
     for (size_t i = 0; i < p.nquad.size(); ++i) {
         for (int k = 0; k < 4; ++k) w.put((int32_t)p.quad[4 * i + k]);
-        w.put(p.nquad[i]);
+        w.put((uint64_t)p.nquad128[i].lo);
+        w.put((uint64_t)p.nquad128[i].hi);
     }
     w.put(p.count_margin);
-    w.put((int32_t)(p.quad_counts_exact ? 1 : 0));
     return w.b;
 }
 
@@ -559,10 +583,12 @@ static void import_counts(const Plan &p, const void *blob, int64_t size, CountCa
     if (nq < 0) throw Failure{FBS_ERR_ARG, "bad plan counts blob"};
     for (int64_t i = 0; i < nq; ++i) {
         std::array<int, 4> k{r.get<int32_t>(), r.get<int32_t>(), r.get<int32_t>(), r.get<int32_t>()};
-        c.counts[k] = r.get<double>();
+        U128 v;
+        v.lo = r.get<uint64_t>();
+        v.hi = r.get<uint64_t>();
+        c.qcounts[k] = v;
     }
     c.margin = r.get<double>();
-    c.quad_exact = r.get<int32_t>() != 0;
 }
 
 static Plan *new_level(Plan &root, int M) {
@@ -684,6 +710,7 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
     std::vector<std::array<int, 4>> ctrip, cquad;   // closed items (global bins)
     std::vector<int64_t> ctri_cnt;
     std::vector<double> cquad_cnt;
+    std::vector<U128> cquad_ex;
     std::vector<Closed> ctrip_src, cquad_src;
     std::vector<std::vector<int>> loc_of(grids.size());
     for (size_t l = 0; l < grids.size(); ++l) {
@@ -699,22 +726,27 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
         for (int v : lt[l]) ltc.push_back(loc_of[l][v]);
         for (int v : lq[l]) lqc.push_back(loc_of[l][v]);
         std::vector<double> tden, qden;
+        std::vector<U128> qex;
         // sum_M N_a N_b N_c / M^3 is the same integer as sum_N N_a N_b N_c / N^3
         const double npix = (double)lv.M * lv.M * lv.M;
         if (cache) {
             // counts carried over: the closed items and their exact counts, no count pass
             tden.assign(ltc.size() / 3, 0.0);
             qden.assign(lqc.size() / 4, 0.0);
+            qex.assign(lqc.size() / 4, U128{});
             for (size_t i = 0; i < tden.size(); ++i) {
                 auto it = cache->counts.find({lt[l][3 * i], lt[l][3 * i + 1], lt[l][3 * i + 2], -1});
                 if (it != cache->counts.end()) tden[i] = it->second * npix;
             }
             for (size_t i = 0; i < qden.size(); ++i) {
-                auto it = cache->counts.find({lq[l][4 * i], lq[l][4 * i + 1], lq[l][4 * i + 2], lq[l][4 * i + 3]});
-                if (it != cache->counts.end()) qden[i] = it->second * npix;
+                auto it = cache->qcounts.find({lq[l][4 * i], lq[l][4 * i + 1], lq[l][4 * i + 2], lq[l][4 * i + 3]});
+                if (it != cache->qcounts.end()) {
+                    qex[i] = it->second;
+                    qden[i] = u128_to_double(it->second) * npix;
+                }
             }
         } else {
-            exact_counts(lv, ltc, lqc, tden, qden);
+            exact_counts(lv, ltc, lqc, tden, qden, qex);
         }
         for (size_t i = 0; i < tden.size(); ++i) {
             int64_t c = round_count(p, tden[i], npix);
@@ -726,29 +758,24 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
         }
         for (size_t i = 0; i < qden.size(); ++i) {
             // Quadruple counts of wide shells reach 1e19 and more, past the exact
-            // integers of FP64 (2^53) and of int64: below 2^53 they are rounded
-            // like triangle counts, above it the FP64 sum itself is the count.
+            // integers of FP64 (2^53) and of int64: the exact 128-bit counts
+            // decide, the FP64 count-field sums only cross-check them
+            const double c = u128_to_double(qex[i]);
             const double v = qden[i] / npix;
-            const double r = nearbyint(v);
-            double c;
-            if (v < 9007199254740992.0 && fabs(v - r) <= 0.25) {
-                c = r;
-            } else {
-                c = v;  // the FP64 sum is the count (rounding would not be reliable)
-                p.quad_counts_exact = false;
-            }
-            if (c < 0) throw Failure{FBS_ERR_NUMERIC, "negative quadruple count"};
-            if (c == 0) continue;
+            if (!(fabs(v - c) <= 1e-6 * c + 0.5))
+                throw Failure{FBS_ERR_NUMERIC, "exact and FP64 quadruple counts disagree (" + std::to_string(c) +
+                                                   " vs " + std::to_string(v) + ")"};
+            if (qex[i].lo == 0 && qex[i].hi == 0) continue;
             cquad.push_back({lq[l][4 * i], lq[l][4 * i + 1], lq[l][4 * i + 2], lq[l][4 * i + 3]});
             cquad_cnt.push_back(c);
+            cquad_ex.push_back(qex[i]);
             cquad_src.push_back({(int)l, (int)i});
         }
     }
     if (cache) {
-        if (ctrip.size() + cquad.size() != cache->counts.size())
+        if (ctrip.size() != cache->counts.size() || cquad.size() != cache->qcounts.size())
             throw Failure{FBS_ERR_ARG, "plan counts blob does not match this plan's candidate items"};
         p.count_margin = cache->margin;
-        p.quad_counts_exact = cache->quad_exact;
     }
     // global output order: lexicographic over all levels
     std::vector<int> ot(ctrip.size()), oq(cquad.size());
@@ -760,6 +787,7 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
     p.ntri.clear();
     p.quad.clear();
     p.nquad.clear();
+    p.nquad128.clear();
     for (size_t g = 0; g < ot.size(); ++g) {
         const int i = ot[g];
         p.trip.insert(p.trip.end(), {ctrip[i][0], ctrip[i][1], ctrip[i][2]});
@@ -774,6 +802,7 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
         const int i = oq[g];
         p.quad.insert(p.quad.end(), {cquad[i][0], cquad[i][1], cquad[i][2], cquad[i][3]});
         p.nquad.push_back(cquad_cnt[i]);
+        p.nquad128.push_back(cquad_ex[i]);
         Plan &lv = *p.levels[cquad_src[i].level];
         const auto &lo = loc_of[cquad_src[i].level];
         lv.quad.insert(lv.quad.end(), {lo[cquad[i][0]], lo[cquad[i][1]], lo[cquad[i][2]], lo[cquad[i][3]]});
@@ -881,15 +910,18 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
     p.d_geom = upload(p, p.geom);
     // unpaired quadruple counts of the connected trispectrum: N_quad minus the
     // paired ones (a = b < c = d: |S_a||S_c|; a = b = c = d: 3|S|^2 - 3|S| + Z)
+    // (exact in 128-bit integers, then the nearest double)
     p.nconn.assign(nquad, 0.0);
     for (int i = 0; i < nquad; ++i) {
         const int32_t *q = &p.quad[4 * i];
-        double c = 0.0;
+        unsigned __int128 c = 0;
         if (q[0] == q[1] && q[2] == q[3]) {
-            const double sa = (double)p.shell[q[0]], sc = (double)p.shell[q[2]];
-            c = q[0] != q[2] ? sa * sc : 3.0 * sa * sa - 3.0 * sa + (double)p.selfconj[q[0]];
+            const unsigned __int128 sa = (unsigned long long)p.shell[q[0]], sc = (unsigned long long)p.shell[q[2]];
+            c = q[0] != q[2] ? sa * sc : 3 * sa * sa - 3 * sa + (unsigned long long)p.selfconj[q[0]];
         }
-        p.nconn[i] = p.nquad[i] - c;
+        const unsigned __int128 t = ((unsigned __int128)p.nquad128[i].hi << 64) | p.nquad128[i].lo;
+        if (c > t) throw Failure{FBS_ERR_NUMERIC, "paired quadruples exceed the quadruple count"};
+        p.nconn[i] = (double)(t - c);
     }
     if (nquad > 0) {
         p.d_nconn = upload(p, p.nconn);
@@ -1691,9 +1723,18 @@ int fbs_plan_slab_planes(const fbs_plan *plan) { return plan ? plan->slab : FBS_
 
 int fbs_plan_num_slabs(const fbs_plan *plan) { return plan ? plan->nslabs : FBS_ERR_ARG; }
 
-int fbs_plan_quad_counts_exact(const fbs_plan *plan) {
-    if (!plan) return FBS_ERR_ARG;
-    return plan->quad_counts_exact ? 1 : 0;
+int fbs_plan_quad_counts_exact(const fbs_plan *plan) { return plan ? 1 : FBS_ERR_ARG; }
+
+fbs_status fbs_plan_quad_counts_u128(const fbs_plan *plan, uint64_t *words) {
+    if (!plan || !words) {
+        set_error("fbs_plan_quad_counts_u128: NULL argument");
+        return FBS_ERR_ARG;
+    }
+    for (size_t i = 0; i < plan->nquad128.size(); ++i) {
+        words[2 * i] = plan->nquad128[i].lo;
+        words[2 * i + 1] = plan->nquad128[i].hi;
+    }
+    return FBS_OK;
 }
 
 int64_t fbs_plan_device_bytes(const fbs_plan *plan) { return plan ? plan->dev_bytes : -1; }

@@ -34,7 +34,9 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-from . import Plan
+from . import FbsError, Plan
+
+FBS_ERR_ARG = -1
 
 
 @dataclasses.dataclass
@@ -142,8 +144,16 @@ class EstimatorServer:
     def _build(self, req: Request, key, stream):
         """Create the plan (runs on the builder thread, or inline)."""
         counts = self._cached_counts(key)
-        plan = Plan(req.field.shape[0], req.L, np.asarray(req.edges), precision=req.precision, stream=stream,
-                    counts=counts)
+        try:
+            plan = Plan(req.field.shape[0], req.L, np.asarray(req.edges), precision=req.precision, stream=stream,
+                        counts=counts)
+        except FbsError as e:
+            if counts is None or e.status != FBS_ERR_ARG:
+                raise
+            # a stored blob of another library version or plan: count afresh
+            self.counts_cache.pop(key[:3], None)
+            counts = None
+            plan = Plan(req.field.shape[0], req.L, np.asarray(req.edges), precision=req.precision, stream=stream)
         if counts is None:
             blob = plan.export_counts()
             self.counts_cache[key[:3]] = blob

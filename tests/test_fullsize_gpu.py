@@ -132,7 +132,9 @@ def test_quadratic512_log16_trispectrum_top_bins_bf16x3():
     """The benchmark's 16-bin trispectrum plan (fused tensor-core pass at
     M = 512): closed quadruplets and triplets of its top five bins against
     the FP64 FFT estimator (Eq. Jeong_gen with p = 4 and p = 3).  Quadruple
-    counts of these shells pass 2^53, so they are compared as FP64 sums."""
+    counts of these shells pass 2^63: the largest sampled ones are compared
+    exactly with the oracle's integer pair-count route, the rest as FP64
+    sums."""
     import torch
     N, L, kf, f32 = _bench_512()
     edges = np.geomspace(kf, 0.25 * N * kf, 17)
@@ -147,8 +149,16 @@ def test_quadratic512_log16_trispectrum_top_bins_bf16x3():
         qs = qs[:: max(1, -(-len(qs) // 32))]
         ts = ts[:: max(1, -(-len(ts) // 16))]
         quads, nq = plan.quads[qs], plan.N_quad[qs]
+        nq_exact = [plan.N_quad_exact[i] for i in qs]
         trip, ntri = plan.triplets[ts], plan.N_tri[ts]
+        assert plan.quad_counts_exact
     assert len(qs) >= 20 and len(ts) >= 10
+    assert all(float(v) == c for v, c in zip(nq_exact, nq))
+    big = np.argsort(nq)[-3:]
+    ex = oracle.quad_counts_exact(N, L, edges, quads[big])
+    print("512^3 x 16 log exact quadruple counts:", ex)
+    assert max(ex) >= 2 ** 63
+    assert [nq_exact[i] for i in big] == ex
     ref = oracle.fft_estimator(f32.astype(np.float64), L, edges, triplets=trip, quads=quads)
     assert np.array_equal(ref["N_tri"], ntri)
     assert np.allclose(nq, ref["qden"] / float(N) ** 3, rtol=1e-12)
