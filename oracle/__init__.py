@@ -103,6 +103,9 @@ def _load():
             lib.oracle_triangle_sums.restype = None
             lib.oracle_triangle_sums.argtypes = [ctypes.c_int, ctypes.c_int, i64p, ctypes.c_int, i32p, ctypes.c_int,
                                                  ctypes.c_int64, dp, ctypes.c_int, i32p, dp, dp, i64p]
+            lib.oracle_direct_trispectrum_diag.restype = None
+            lib.oracle_direct_trispectrum_diag.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p, ctypes.c_int,
+                                                           i64p, dp, dp, i64p]
             lib.oracle_direct_trispectrum.restype = None
             lib.oracle_direct_trispectrum.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, i64p,
                                                       dp, dp, i64p, ctypes.c_int]
@@ -465,6 +468,91 @@ def quad_counts_exact(N: int, L: float, edges, quads) -> list:
                     total += sum(int(u) * int(v) for u, v in zip(Cab[x, y], neg[x, y]))
         out.append(total)
     return out
+
+
+def direct_trispectrum_diagonal(field, L: float, edges, diag_edges):
+    """Diagonal-resolved trispectrum by direct measurement (tiny grids): the
+    ordered closed quadruples of Eq. gen_Nspec3 (p = 4) split by the bin D of
+    their diagonal q = k1 + k2 (shells on |q| like the bins, thresholds from
+    ``diag_edges``).  Returns the ordered arrays num, num_im, cnt of shape
+    (nb, nb, nb, nb, nD)."""
+    lib = _load()
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    D = spectrum(field)
+    re = np.ascontiguousarray(D.real)
+    im = np.ascontiguousarray(D.imag)
+    thr = np.ascontiguousarray(thresholds(edges, L))
+    dthr = np.ascontiguousarray(thresholds(diag_edges, L))
+    nb, nd = len(thr) - 1, len(dthr) - 1
+    num = np.zeros(nb ** 4 * nd)
+    numi = np.zeros(nb ** 4 * nd)
+    cnt = np.zeros(nb ** 4 * nd, dtype=np.int64)
+    lib.oracle_direct_trispectrum_diag(N, _p(re, ctypes.c_double), _p(im, ctypes.c_double), nb,
+                                       _p(thr, ctypes.c_int64), nd, _p(dthr, ctypes.c_int64),
+                                       _p(num, ctypes.c_double), _p(numi, ctypes.c_double),
+                                       _p(cnt, ctypes.c_int64))
+    sh = (nb,) * 4 + (nd,)
+    return {"num": num.reshape(sh), "num_im": numi.reshape(sh), "cnt": cnt.reshape(sh)}
+
+
+def diagonal_trispectrum(field, L: float, edges, diag_edges, quads):
+    """Diagonal-resolved trispectrum, the FFT route (FP64 NumPy).  For a
+    quadruplet (a, b, c, d) and a diagonal bin D, the closed quadruples with
+    k1 + k2 = q in shell D:
+      num_D = sum_{q in S_D} F_ab(q) F_cd(-q),  F_ab(q) = sum_{m1 + m2 = q} D(m1) D(m2),
+    and F_ab is the forward DFT of the product of two shell fields divided by
+    N_pix (F_ab = DFT[I_a I_b] / N_pix, the Kronecker-delta identity of Sec. 2
+    applied to the pair); the count is sum_{q in S_D} C_ab(q) C_cd(-q) of the
+    integer pair counts (:func:`pair_counts`).  T_D = V^3/N_pix^4 num_D / N_D
+    (the normalisation of Eq. Jeong_gen with p = 4), NaN where N_D = 0.
+    Returns dict with ``num`` (nq, nD) FP64 real parts, ``num_im``, ``cnt``
+    (nq, nD) Python integers, ``T`` (nq, nD)."""
+    field = np.asarray(field, dtype=np.float64)
+    N = field.shape[0]
+    npix = float(N) ** 3
+    V = float(L) ** 3
+    thr = thresholds(edges, L)
+    dthr = thresholds(diag_edges, L)
+    nd = len(dthr) - 1
+    bins = bin_index(N, thr)
+    dbin = bin_index(N, dthr)
+    Dk = spectrum(field)
+    neg = lambda A: np.roll(A[::-1, ::-1, ::-1], 1, axis=(0, 1, 2))  # A(-q mod N)
+    I, F, C = {}, {}, {}
+
+    def shell(b):
+        if b not in I:
+            I[b] = shell_field(Dk, bins, b)
+        return I[b]
+
+    def pair_spec(a, b):
+        if (a, b) not in F:
+            F[(a, b)] = _fftn(shell(a) * shell(b)) / npix
+        return F[(a, b)]
+
+    def pair_cnt(a, b):
+        if (a, b) not in C:
+            C[(a, b)] = pair_counts(bins, a, b)
+        return C[(a, b)]
+
+    q = np.asarray(quads, dtype=np.int64).reshape(-1, 4)
+    num = np.zeros((len(q), nd))
+    numi = np.zeros((len(q), nd))
+    cnt = [[0] * nd for _ in range(len(q))]
+    for i, (a, b, c, d) in enumerate(q):
+        prod = pair_spec(int(a), int(b)) * neg(pair_spec(int(c), int(d)))
+        cc = pair_cnt(int(a), int(b)) * neg(pair_cnt(int(c), int(d)))
+        for D in range(nd):
+            sel = dbin == D
+            num[i, D] = float(np.sum(prod.real[sel]))
+            numi[i, D] = float(np.sum(prod.imag[sel]))
+            cnt[i][D] = int(np.sum(cc[sel], dtype=np.int64)) if int(cc.max(initial=0)) * cc.size < 2 ** 62 \
+                else sum(int(v) for v in cc[sel])
+    nc = np.array([[float(v) for v in row] for row in cnt]).reshape(len(q), nd)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        T = np.where(nc > 0, (V ** 3 / npix ** 4) * num / np.where(nc > 0, nc, 1.0), np.nan)
+    return {"num": num, "num_im": numi, "cnt": cnt, "T": T}
 
 
 def rebinned_bispectrum(field, L: float, edges, k_edges, mu_edges, k_rep=None):

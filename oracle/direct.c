@@ -302,6 +302,68 @@ void oracle_direct_trispectrum(int N, const double *re, const double *im, int nb
 }
 
 /*
+ * Diagonal-resolved trispectrum sums (ordered quadruples, tiny grids): as
+ * oracle_direct_trispectrum, and the quadruple also goes by the bin D of its
+ * diagonal q = m1 + m2 (wrapped into [-N/2, N/2) per component), dthr[ndiag+1]
+ * integer thresholds on |q|^2; quadruples whose |q|^2 is in no diagonal bin
+ * are left out.  Arrays [a][b][c][d][D].
+ */
+void oracle_direct_trispectrum_diag(int N, const double *re, const double *im, int nbins,
+                                    const int64_t *thr, int ndiag, const int64_t *dthr, double *num,
+                                    double *num_im, int64_t *cnt) {
+    mode_t_ *M = NULL;
+    int64_t nm = collect_modes(N, nbins, thr, &M);
+    const int64_t n5 = (int64_t)nbins * nbins * nbins * nbins * ndiag;
+    memset(num, 0, (size_t)n5 * sizeof(double));
+    memset(num_im, 0, (size_t)n5 * sizeof(double));
+    memset(cnt, 0, (size_t)n5 * sizeof(int64_t));
+#pragma omp parallel
+    {
+        double *ln = (double *)calloc((size_t)n5, sizeof(double));
+        double *li = (double *)calloc((size_t)n5, sizeof(double));
+        int64_t *lc = (int64_t *)calloc((size_t)n5, sizeof(int64_t));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < nm; ++i) {
+            const mode_t_ a = M[i];
+            for (int64_t j = 0; j < nm; ++j) {
+                const mode_t_ b = M[j];
+                const int qx = wrap(a.mx + b.mx, N), qy = wrap(a.my + b.my, N), qz = wrap(a.mz + b.mz, N);
+                const int D = bin_of((int64_t)qx * qx + (int64_t)qy * qy + (int64_t)qz * qz, ndiag, dthr);
+                if (D < 0) continue;
+                double pr = re[a.idx] * re[b.idx] - im[a.idx] * im[b.idx];
+                double pi = re[a.idx] * im[b.idx] + im[a.idx] * re[b.idx];
+                for (int64_t k = 0; k < nm; ++k) {
+                    const mode_t_ c = M[k];
+                    int x = wrap(-(a.mx + b.mx + c.mx), N);
+                    int y = wrap(-(a.my + b.my + c.my), N);
+                    int z = wrap(-(a.mz + b.mz + c.mz), N);
+                    int64_t m2 = (int64_t)x * x + (int64_t)y * y + (int64_t)z * z;
+                    int d = bin_of(m2, nbins, thr);
+                    if (d < 0) continue;
+                    int64_t k4 = flat(x, y, z, N);
+                    double qr = pr * re[c.idx] - pi * im[c.idx];
+                    double qi = pr * im[c.idx] + pi * re[c.idx];
+                    int64_t o = ((((int64_t)a.bin * nbins + b.bin) * nbins + c.bin) * nbins + d) * ndiag + D;
+                    ln[o] += qr * re[k4] - qi * im[k4];
+                    li[o] += qr * im[k4] + qi * re[k4];
+                    lc[o] += 1;
+                }
+            }
+        }
+#pragma omp critical
+        {
+            for (int64_t o = 0; o < n5; ++o) {
+                num[o] += ln[o];
+                num_im[o] += li[o];
+                cnt[o] += lc[o];
+            }
+        }
+        free(ln); free(li); free(lc);
+    }
+    free(M);
+}
+
+/*
  * Closure of bin triples (a, b, c): flag[t] = 1 when some ordered triple
  * m1 in S_a, m2 in S_b, m3 = -(m1+m2) (mod N) in S_c exists, i.e. when
  * N_tri > 0.  A witness search that stops at the first closed triple; the

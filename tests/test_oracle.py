@@ -790,3 +790,65 @@ def test_quad_counts_exact_match_rounded_fft_sums():
     ex = oracle.quad_counts_exact(N, L, edges, quads)
     assert max(ex) < 2 ** 53
     assert ex == [int(v) for v in e["N_quad"]]
+
+
+# ---------------------------------------------------------------- diagonal-resolved trispectrum
+def _diag_edges(N, L, top=None):
+    """Diagonal shells from 0 (the paired q = 0 alone first) to beyond the
+    corner of the grid."""
+    kf = 2 * math.pi / L
+    top = top if top is not None else 3 * (N // 2) ** 2 + 1
+    sq = [0.0, 0.5, 2.5, 6.5, 12.5, float(top) + 0.5]
+    return [kf * math.sqrt(s) for s in sq]
+
+
+@pytest.mark.parametrize("N,L,kind,nb,seed", [(8, 40.0, "lin", 3, 21), (10, 25.0, "log", 4, 22)])
+def test_diagonal_trispectrum_fft_route_equals_brute_force(N, L, kind, nb, seed):
+    edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
+    dedges = _diag_edges(N, L)
+    f = fields.quadratic_local(N, 1.0, -1.5, 0.3, seed=seed)
+    d = oracle.direct_trispectrum_diagonal(f, L, edges, dedges)
+    k = d["cnt"].shape[0]
+    quads = list(itertools.combinations_with_replacement(range(k), 4))
+    e = oracle.diagonal_trispectrum(f, L, edges, dedges, quads)
+    scale = max(1e-300, float(np.abs(d["num"]).max()))
+    for i, q in enumerate(quads):
+        assert e["cnt"][i] == [int(v) for v in d["cnt"][q]]
+        assert np.allclose(e["num"][i], d["num"][q], rtol=1e-10, atol=1e-12 * scale)
+        assert np.allclose(e["num_im"][i], 0.0, atol=1e-10 * scale)  # real field: the sums are real
+
+
+def test_diagonal_bins_add_up_to_the_raw_trispectrum():
+    """Diagonal shells covering every |k1 + k2|: the diagonal sums and counts
+    add up to the plain four-shell sum and count of each quadruplet."""
+    N, L = 8, 40.0
+    edges = fields.linear_edges(N, L, 3)
+    f = fields.lognormal(N, 0.5, -1.5, seed=23)
+    raw = oracle.direct_trispectrum(f, L, edges)
+    e = oracle.diagonal_trispectrum(f, L, edges, _diag_edges(N, L), raw["quads"])
+    assert [sum(row) for row in e["cnt"]] == [int(v) for v in raw["N_quad"]]
+    assert np.allclose(e["num"].sum(axis=1), raw["num"], rtol=1e-10, atol=1e-12 * np.abs(raw["num"]).max())
+
+
+def test_diagonal_zero_shell_is_the_paired_term():
+    """The shell holding only q = k1 + k2 = 0: for (a, a, c, c) its
+    quadruples are m2 = -m1, m4 = -m3, so the sum is S2_a S2_c (S2 the
+    shell's sum of |D|^2) and the count |S_a| |S_c|; other quadruplets have
+    none."""
+    N, L = 10, 30.0
+    edges = fields.linear_edges(N, L, 3)
+    f = fields.lognormal(N, 0.5, -1.5, seed=24)
+    thr = oracle.thresholds(edges, L)
+    bins = oracle.bin_index(N, thr)
+    D = oracle.spectrum(f)
+    a2 = np.abs(D) ** 2
+    S2 = [float(a2[bins == b].sum()) for b in range(3)]
+    S = [int((bins == b).sum()) for b in range(3)]
+    quads = list(itertools.combinations_with_replacement(range(3), 4))
+    e = oracle.diagonal_trispectrum(f, L, edges, _diag_edges(N, L), quads)
+    for i, (a, b, c, d) in enumerate(quads):
+        if a == b and c == d:
+            assert e["cnt"][i][0] == S[a] * S[c]
+            assert math.isclose(e["num"][i, 0], S2[a] * S2[c], rel_tol=1e-12)
+        else:
+            assert e["cnt"][i][0] == 0 and abs(e["num"][i, 0]) <= 1e-12 * max(S2) ** 2  # FFT rounding only
