@@ -283,6 +283,40 @@ fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double 
                                      double *P);
 
 /*
+ * Diagonal-resolved trispectrum (FBS_FLAG_TRISPECTRUM plans).  Every closed
+ * quadruple (m1, m2, m3, m4) of quadruplet (a <= b <= c <= d) has the
+ * diagonal q = m1 + m2 = -(m3 + m4) of its quadrilateral; the diagonal bins
+ * split the quadruples by |q| into shells diag_edges[D] <= |q| k_f <
+ * diag_edges[D+1] (the same integer-threshold rule as the bins; an edge of 0
+ * admits q = 0, the paired quadruples m2 = -m1 of a = b, c = d):
+ *   T_D = V^3/N_pix^4 num_D / N_D,
+ *   num_D = sum_{q in S_D} F_ab(q) F_cd(-q),  F_ab(q) = sum_{m1 + m2 = q} D(m1) D(m2),
+ *   N_D   = sum_{q in S_D} C_ab(q) C_cd(-q),  C_ab(q) = #{m1 + m2 = q}.
+ * Over diagonal shells that cover every |q|, the num_D and N_D add up to the
+ * four-shell sum and count of Eq. Jeong_gen (p = 4).
+ *
+ * fbs_plan_set_diagonal -- set ndiag >= 1 diagonal bins (host array
+ * diag_edges[ndiag+1], ascending, physical k units) and compute the exact
+ * counts N_D at plan time (FP64 count fields and integer pair counts, as the
+ * quadruple counts).  May be called again; the device tables of an earlier
+ * call are released with the plan.  FBS_ERR_STATE without FBS_FLAG_TRISPECTRUM.
+ * fbs_plan_num_diagonal_bins -- ndiag, 0 before fbs_plan_set_diagonal.
+ * fbs_plan_diagonal_counts -- counts[nquad*ndiag] as FP64 (nearest double)
+ * and/or words[2*nquad*ndiag] as unsigned 128-bit integers (low, high),
+ * quadruplet-major; either may be NULL.
+ * fbs_trispectrum_diagonal -- TD[nquad*ndiag] (quadruplet-major, NaN where
+ * N_D = 0) of one field (device or host, as fbs_bispectrum).  The shell
+ * fields of each level are held on the whole evaluation grid at once (bins x
+ * M^3 FP32), the products I_a I_b of the distinct first and second pairs of
+ * the quadruplets are forward transformed on that grid (FP32), and num_D is
+ * accumulated in FP64 over the half spectrum.  TD: device or host.
+ */
+fbs_status fbs_plan_set_diagonal(fbs_plan *plan, const double *diag_edges, int ndiag);
+int fbs_plan_num_diagonal_bins(const fbs_plan *plan);
+fbs_status fbs_plan_diagonal_counts(const fbs_plan *plan, double *counts, uint64_t *words);
+fbs_status fbs_trispectrum_diagonal(fbs_plan *plan, const float *field, double *TD);
+
+/*
  * fbs_plan_triangle_average -- a model averaged over each closed triplet's
  * exact set of triangles, as the paper compares theory with its measurements
  * (theory evaluated for every triangle contributing to a bin and averaged,

@@ -507,7 +507,8 @@ def diagonal_trispectrum(field, L: float, edges, diag_edges, quads):
     integer pair counts (:func:`pair_counts`).  T_D = V^3/N_pix^4 num_D / N_D
     (the normalisation of Eq. Jeong_gen with p = 4), NaN where N_D = 0.
     Returns dict with ``num`` (nq, nD) FP64 real parts, ``num_im``, ``cnt``
-    (nq, nD) Python integers, ``T`` (nq, nD)."""
+    (nq, nD) Python integers, ``T`` (nq, nD) and ``mag`` (nq, nD), the
+    cancellation-free scale sum_{q in S_D} |F_ab(q)| |F_cd(-q)|."""
     field = np.asarray(field, dtype=np.float64)
     N = field.shape[0]
     npix = float(N) ** 3
@@ -539,20 +540,23 @@ def diagonal_trispectrum(field, L: float, edges, diag_edges, quads):
     q = np.asarray(quads, dtype=np.int64).reshape(-1, 4)
     num = np.zeros((len(q), nd))
     numi = np.zeros((len(q), nd))
+    mag = np.zeros((len(q), nd))
     cnt = [[0] * nd for _ in range(len(q))]
     for i, (a, b, c, d) in enumerate(q):
         prod = pair_spec(int(a), int(b)) * neg(pair_spec(int(c), int(d)))
+        aprod = np.abs(prod)
         cc = pair_cnt(int(a), int(b)) * neg(pair_cnt(int(c), int(d)))
         for D in range(nd):
             sel = dbin == D
             num[i, D] = float(np.sum(prod.real[sel]))
+            mag[i, D] = float(np.sum(aprod[sel]))
             numi[i, D] = float(np.sum(prod.imag[sel]))
             cnt[i][D] = int(np.sum(cc[sel], dtype=np.int64)) if int(cc.max(initial=0)) * cc.size < 2 ** 62 \
                 else sum(int(v) for v in cc[sel])
     nc = np.array([[float(v) for v in row] for row in cnt]).reshape(len(q), nd)
     with np.errstate(invalid="ignore", divide="ignore"):
         T = np.where(nc > 0, (V ** 3 / npix ** 4) * num / np.where(nc > 0, nc, 1.0), np.nan)
-    return {"num": num, "num_im": numi, "cnt": cnt, "T": T}
+    return {"num": num, "num_im": numi, "cnt": cnt, "T": T, "mag": mag}
 
 
 def rebinned_bispectrum(field, L: float, edges, k_edges, mu_edges, k_rep=None):

@@ -81,6 +81,10 @@ _SIGS = [
     ("fbs_trispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("fbs_plan_sums", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("fbs_trispectrum_connected", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("fbs_plan_set_diagonal", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    ("fbs_plan_num_diagonal_bins", ctypes.c_int, [_vp]),
+    ("fbs_plan_diagonal_counts", ctypes.c_int, [_vp, _vp, _vp]),
+    ("fbs_trispectrum_diagonal", ctypes.c_int, [_vp, _vp, _vp]),
     ("fbs_bispectrum_batch", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _vp]),
     ("fbs_plan_quads_connected", ctypes.c_int, [_vp, _vp]),
     ("fbs_plan_shell_average", ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
@@ -384,6 +388,30 @@ class Plan:
         ptrs = [_ptr(x) for x in (field, Tc, T, B, P)]
         _check(lib().fbs_trispectrum_connected(_vp(self._h), *[_vp(p) for p, _ in ptrs]))
         return Tc, T, B, P
+
+    def set_diagonal(self, diag_edges):
+        """Diagonal bins of the quadrilateral diagonal |k1 + k2| (see
+        fbs_plan_set_diagonal); sets ``N_D`` (nquad, ndiag) FP64 and
+        ``N_D_exact`` (Python integers) from the exact plan-time counts."""
+        e = np.ascontiguousarray(diag_edges, dtype=np.float64)
+        nd = len(e) - 1
+        _check(lib().fbs_plan_set_diagonal(_vp(self._h), e.ctypes.data, nd))
+        self.ndiag = nd
+        self.N_D = np.zeros((self.nquad, nd), dtype=np.float64)
+        w = np.zeros(2 * max(1, self.nquad * nd), dtype=np.uint64)
+        _check(lib().fbs_plan_diagonal_counts(_vp(self._h), self.N_D.ctypes.data, w.ctypes.data))
+        self.N_D_exact = [[int(w[2 * (q * nd + d)]) | (int(w[2 * (q * nd + d) + 1]) << 64) for d in range(nd)]
+                          for q in range(self.nquad)]
+
+    def trispectrum_diagonal(self, field, TD=None):
+        """TD (nquad, ndiag): the trispectrum of every closed quadruplet split
+        by the diagonal bin of k1 + k2 (see fbs_trispectrum_diagonal)."""
+        self._check_field(field)
+        n = self.nquad * getattr(self, "ndiag", 0)
+        TD = self._outputs(field, n) if TD is None else TD
+        ptrs = [_ptr(x) for x in (field, TD)]
+        _check(lib().fbs_trispectrum_diagonal(_vp(self._h), *[_vp(p) for p, _ in ptrs]))
+        return TD.reshape(self.nquad, -1) if n else TD
 
     def _check_field(self, f):
         n = self.N

@@ -99,6 +99,9 @@ void upload_eval_twiddles(Plan &level);
 // device array of nf pointers) into nf consecutive zbuf / ybuf / box blocks.
 void launch_forward(Plan &p, const float *d_field, const float *const *d_fields, int nf, float2 *zbuf,
                     float2 *ybuf, float2 *box);
+void launch_forward_grid(Plan &p, int N, const BoxGeom &bx, const FftFactors &fN, const float2 *tw,
+                         const float *d_field, const float *const *d_fields, int nf, float2 *zbuf, float2 *ybuf,
+                         float2 *box);
 void launch_inverse_x(Plan &p, bool indicator_fp64);
 void launch_inverse_x_geom(Plan &p, const BinGeom *geom, int nb, int nvb);
 void launch_inverse_yz_slab(Plan &p, int x0, int nx, float *islab);
@@ -113,7 +116,15 @@ void launch_count_fields_fp64_impl(Plan &p, double *noct, int bin0, int nb, doub
 struct U128 {
     uint64_t lo = 0, hi = 0;
 };
-void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &items, std::vector<U128> &out);
+// With dthr (thresholds on |q|^2 of nd diagonal shells) also the counts split
+// by the shell of the diagonal q = m1 + m2: dout[item * nd + D].
+void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &items, std::vector<U128> &out,
+                       const std::vector<long long> *dthr = nullptr, std::vector<U128> *dout = nullptr);
+// diagonal.cu (diagonal-resolved trispectrum)
+void launch_field_product(Plan &p, const float *a, const float *b, float *out, long long n);
+void launch_diag_gram(Plan &p, const float2 *F0, const float2 *F1, const long long *d_offs, int nq, const int *d_idx,
+                      const float *d_w, const int *d_dstart, int nd, const int *d_qout, double scale, double *out);
+void launch_diag_normalise(Plan &p, const double *num, const double *cnt, long long n, double cT, double *TD);
 // contract.cu (FP64 count sums)
 void launch_count_contraction(Plan &p, const double *noct, int nb_in_group, int bin0,
                               const int *d_items, int nitems, int arity, double *d_sums);
@@ -251,6 +262,7 @@ struct Plan {
     // tensor-core path
     void *tc = nullptr;           // opaque state of contract_tc.cu
     void *batch = nullptr;        // root only: buffers of batched evaluations (plan.cpp)
+    void *diag = nullptr;         // root only: diagonal-resolved trispectrum tables (plan.cpp)
 
     // timing
     std::vector<cudaEvent_t> evs;  // 2 per pending launch, created once and reused

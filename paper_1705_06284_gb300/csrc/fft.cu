@@ -764,7 +764,15 @@ std::vector<int> fast_grids() {
 
 void launch_forward(Plan &p, const float *d_field, const float *const *d_fields, int nf, float2 *zbuf,
                     float2 *ybuf, float2 *box) {
-    const int N = p.N, D = p.box.D, Dz = p.box.Dz;
+    launch_forward_grid(p, p.N, p.box, p.fN, p.d_tw, d_field, d_fields, nf, zbuf, ybuf, box);
+}
+
+// Forward transform of real fields on an N^3 grid (the input grid, or an
+// evaluation grid for products of shell fields), pruned to the box bx.
+void launch_forward_grid(Plan &p, int N, const BoxGeom &bx, const FftFactors &fN, const float2 *tw,
+                         const float *d_field, const float *const *d_fields, int nf, float2 *zbuf, float2 *ybuf,
+                         float2 *box) {
+    const int D = bx.D, Dz = bx.Dz;
     const long long zs = (long long)N * N * Dz, ys = (long long)N * D * Dz, bs = (long long)D * D * Dz;
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
@@ -784,21 +792,21 @@ void launch_forward(Plan &p, const float *d_field, const float *const *d_fields,
         allow_smem(kz, sm);
         long long rows = (long long)N * N;
         dim3 grid((int)((rows + 2 * nl - 1) / (2 * nl)), nf);
-        kz<<<grid, kThreads, sm, p.stream>>>(d_field, d_fields, zbuf, zs, N, Dz, nl, p.fN, p.d_tw);
+        kz<<<grid, kThreads, sm, p.stream>>>(d_field, d_fields, zbuf, zs, N, Dz, nl, fN, tw);
         FBS_CUDA(cudaGetLastError());
     }
     {
         KTimer t(p, KC_FWD_Y);
         allow_smem(ky, sm);
         dim3 grid((Dz + nl - 1) / nl, N, nf);
-        ky<<<grid, kThreads, sm, p.stream>>>(zbuf, ybuf, zs, ys, N, D, Dz, nl, p.fN, p.d_tw);
+        ky<<<grid, kThreads, sm, p.stream>>>(zbuf, ybuf, zs, ys, N, D, Dz, nl, fN, tw);
         FBS_CUDA(cudaGetLastError());
     }
     {
         KTimer t(p, KC_FWD_X);
         allow_smem(kx, sm);
         dim3 grid((Dz + nl - 1) / nl, D, nf);
-        kx<<<grid, kThreads, sm, p.stream>>>(ybuf, box, ys, bs, N, D, Dz, nl, p.fN, p.d_tw);
+        kx<<<grid, kThreads, sm, p.stream>>>(ybuf, box, ys, bs, N, D, Dz, nl, fN, tw);
         FBS_CUDA(cudaGetLastError());
     }
 }

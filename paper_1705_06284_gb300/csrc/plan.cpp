@@ -932,28 +932,35 @@ static void create_plan(Plan &p, const double *edges, const void *blob = nullptr
     FBS_CUDA(cudaStreamSynchronize(p.stream));
 }
 
-static void run_field(Plan &p, const float *field, bool quads) {
+// A host field is copied into the plan's staging buffer on the plan's own
+// copy stream: it need not wait for kernels already queued on the plan's
+// stream (another plan's evaluation, say), only for the previous forward
+// transform to be done with the buffer.  Returns the device field.
+static const float *stage_field(Plan &p, const float *field, bool &staged) {
+    staged = !is_device_ptr(field);
+    if (!staged) return field;
     const int N = p.N;
-    const float *d_in = field;
-    const bool staged = !is_device_ptr(field);
-    if (staged) {
-        // Copy on the plan's own copy stream: it need not wait for kernels
-        // already queued on the plan's stream (another plan's evaluation, say),
-        // only for the previous forward transform to be done with the buffer.
-        if (p.field_free_recorded) FBS_CUDA(cudaStreamWaitEvent(p.copy_stream, p.ev_field_free, 0));
-        FBS_CUDA(cudaMemcpyAsync(p.d_field, field, (size_t)N * N * N * sizeof(float), cudaMemcpyDefault,
-                                 p.copy_stream));
-        FBS_CUDA(cudaEventRecord(p.ev_field_ready, p.copy_stream));
-        FBS_CUDA(cudaStreamWaitEvent(p.stream, p.ev_field_ready, 0));
-        d_in = p.d_field;
-    }
+    if (p.field_free_recorded) FBS_CUDA(cudaStreamWaitEvent(p.copy_stream, p.ev_field_free, 0));
+    FBS_CUDA(cudaMemcpyAsync(p.d_field, field, (size_t)N * N * N * sizeof(float), cudaMemcpyDefault, p.copy_stream));
+    FBS_CUDA(cudaEventRecord(p.ev_field_ready, p.copy_stream));
+    FBS_CUDA(cudaStreamWaitEvent(p.stream, p.ev_field_ready, 0));
+    return p.d_field;
+}
+
+// After the forward transform has read a staged field.
+static void release_field(Plan &p, bool staged) {
+    if (!staged) return;
+    FBS_CUDA(cudaEventRecord(p.ev_field_free, p.stream));
+    p.field_free_recorded = true;
+}
+
+static void run_field(Plan &p, const float *field, bool quads) {
+    bool staged = false;
+    const float *d_in = stage_field(p, field, staged);
     const bool tc = p.precision != FBS_PREC_FP32;
     if (tc) FBS_CUDA(cudaMemsetAsync(p.d_errbuf, 0, sizeof(int), p.stream));
     launch_forward(p, d_in, nullptr, 1, p.d_zbuf, p.d_ybuf, p.d_box);
-    if (staged) {
-        FBS_CUDA(cudaEventRecord(p.ev_field_free, p.stream));
-        p.field_free_recorded = true;
-    }
+    release_field(p, staged);
     for (Plan *lp : p.levels) {
         Plan &lv = *lp;
         lv.fused_active = quads && tc && tc_fused_usable(lv);
@@ -1135,6 +1142,225 @@ static void run_batch(Plan &p, const float *const *fields, int nf) {
         lv.nslabs = nslabs0;
     }
     launch_normalise_batch(p, false, nf, bs.tnum, bs.sumsq, bs.B, bs.P);
+}
+
+// ---------------------------------------------------------------- diagonal-resolved trispectrum
+// Per level: the pair-spectrum box (|q_j| <= Rq on the level grid), the
+// half-box modes of every diagonal shell, a geometry whose y-stage offsets
+// hold the whole grid in one slab, and the distinct pairs of the level's
+// quadruplets (split (a, b) | (c, d)).
+struct DiagLevel {
+    BoxGeom bx{};
+    int *d_idx = nullptr, *d_dstart = nullptr;
+    float *d_w = nullptr;
+    BinGeom *d_geom_full = nullptr;
+    long long G_full = 0;
+    std::vector<std::pair<int, int>> pairs;
+    std::vector<std::array<int, 2>> qp;
+};
+
+struct DiagState {
+    int nd = 0;
+    std::vector<long long> thr;  // nd+1 thresholds on |q|^2
+    std::vector<U128> cnt128;    // [nquad][nd] exact counts, plan order
+    std::vector<double> cnt;
+    double *d_cnt = nullptr, *d_num = nullptr, *d_TD = nullptr;
+    std::vector<DiagLevel> lv;
+};
+
+static void free_diag(Plan &p) {
+    delete reinterpret_cast<DiagState *>(p.diag);  // device buffers belong to the plan's allocation list
+    p.diag = nullptr;
+}
+
+static void set_diagonal(Plan &p, const double *edges, int nd) {
+    std::vector<long long> thr(nd + 1);
+    for (int i = 0; i <= nd; ++i) {
+        if (!(edges[i] >= 0.0) || (i > 0 && !(edges[i] > edges[i - 1])))
+            throw Failure{FBS_ERR_ARG, "diagonal edges must be non-negative and ascending"};
+        thr[i] = edges[i] > 0.0 ? edge_threshold(edges[i], p.L) : 0;
+    }
+    free_diag(p);
+    DiagState *ds = new DiagState();
+    p.diag = ds;
+    ds->nd = nd;
+    ds->thr = thr;
+    const int nq = (int)p.nquad.size();
+    ds->cnt128.assign((size_t)nq * nd, U128{});
+    ds->lv.assign(p.levels.size(), DiagLevel{});
+    for (size_t l = 0; l < p.levels.size(); ++l) {
+        Plan &lv = *p.levels[l];
+        DiagLevel &dl = ds->lv[l];
+        const int nql = (int)lv.nquad.size();
+        if (nql == 0) continue;
+        const int M = lv.M;
+        {
+            // exact counts split by diagonal shell, from the level's count fields
+            auto f = octant_fields(lv, {nullptr});
+            std::vector<int> items(lv.quad.begin(), lv.quad.end());
+            std::vector<U128> tot, dc;
+            exact_quad_counts(lv, f->as<double>(), items, tot, &thr, &dc);
+            for (int i = 0; i < nql; ++i)
+                for (int D = 0; D < nd; ++D) ds->cnt128[(size_t)lv.gquad[i] * nd + D] = dc[(size_t)i * nd + D];
+        }
+        const long long top = thr[nd];
+        int Rq = 0;
+        while ((long long)(Rq + 1) * (Rq + 1) <= top - 1) ++Rq;
+        Rq = std::min(Rq, M / 2);
+        dl.bx.N = M;
+        dl.bx.R = Rq;
+        dl.bx.D = 2 * Rq + 1 > M ? M : 2 * Rq + 1;
+        dl.bx.Dz = std::min(Rq, M / 2) + 1;
+        std::vector<std::vector<int>> li(nd);
+        std::vector<std::vector<float>> lw(nd);
+        for (int jx = 0; jx < dl.bx.D; ++jx)
+            for (int jy = 0; jy < dl.bx.D; ++jy)
+                for (int jz = 0; jz < dl.bx.Dz; ++jz) {
+                    const long long qx = box_freq(jx, dl.bx.D, M), qy = box_freq(jy, dl.bx.D, M);
+                    const long long s2 = qx * qx + qy * qy + (long long)jz * jz;
+                    if (s2 < thr[0] || s2 >= top) continue;
+                    const int D = (int)(std::upper_bound(thr.begin(), thr.end(), s2) - thr.begin()) - 1;
+                    li[D].push_back((int)(((long long)jx * dl.bx.D + jy) * dl.bx.Dz + jz));
+                    lw[D].push_back(jz == 0 || 2 * jz == M ? 1.f : 2.f);
+                }
+        std::vector<int> idx, start(1, 0);
+        std::vector<float> w;
+        for (int D = 0; D < nd; ++D) {
+            idx.insert(idx.end(), li[D].begin(), li[D].end());
+            w.insert(w.end(), lw[D].begin(), lw[D].end());
+            start.push_back((int)idx.size());
+        }
+        dl.d_idx = upload(lv, idx);
+        dl.d_w = upload(lv, w);
+        dl.d_dstart = upload(lv, start);
+        std::vector<BinGeom> g = lv.geom;
+        long long goff = 0;
+        for (int b = 0; b < lv.nbins; ++b) {
+            g[b].G_off = goff;
+            if (!g[b].empty) goff += (long long)M * M * g[b].Dzb;
+        }
+        dl.G_full = std::max<long long>(1, goff);
+        dl.d_geom_full = upload(lv, g);
+        std::map<std::pair<int, int>, int> pid;
+        dl.qp.assign(nql, {0, 0});
+        for (int i = 0; i < nql; ++i)
+            for (int h = 0; h < 2; ++h) {
+                const std::pair<int, int> k{lv.quad[4 * i + 2 * h], lv.quad[4 * i + 2 * h + 1]};
+                auto it = pid.find(k);
+                if (it == pid.end()) {
+                    it = pid.emplace(k, (int)dl.pairs.size()).first;
+                    dl.pairs.push_back(k);
+                }
+                dl.qp[i][h] = it->second;
+            }
+        FBS_CUDA(cudaStreamSynchronize(lv.stream));  // the host tables go out of scope
+    }
+    ds->cnt.resize(ds->cnt128.size());
+    for (size_t i = 0; i < ds->cnt.size(); ++i) ds->cnt[i] = u128_to_double(ds->cnt128[i]);
+    ds->d_cnt = upload(p, ds->cnt);
+    ds->d_num = (double *)p.dalloc(std::max<size_t>(1, ds->cnt.size()) * sizeof(double));
+    ds->d_TD = (double *)p.dalloc(std::max<size_t>(1, ds->cnt.size()) * sizeof(double));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));
+}
+
+// Shell fields of every bin of a level on its whole grid, then per group of
+// pairs the forward transforms of their products, then the Gram products.
+static void run_diagonal(Plan &p, const float *field) {
+    DiagState &ds = *reinterpret_cast<DiagState *>(p.diag);
+    const int nd = ds.nd;
+    bool staged = false;
+    const float *d_in = stage_field(p, field, staged);
+    launch_forward(p, d_in, nullptr, 1, p.d_zbuf, p.d_ybuf, p.d_box);
+    release_field(p, staged);
+    FBS_CUDA(cudaMemsetAsync(ds.d_num, 0, std::max<size_t>(1, ds.cnt.size()) * sizeof(double), p.stream));
+    for (size_t l = 0; l < p.levels.size(); ++l) {
+        Plan &lv = *p.levels[l];
+        DiagLevel &dl = ds.lv[l];
+        const int np = (int)dl.pairs.size();
+        if (np == 0) continue;
+        const int M = lv.M, nb = lv.nbins;
+        const long long M3 = (long long)M * M * M;
+        AsyncBuf Ifull((size_t)nb * M3 * sizeof(float), p.stream, "diagonal shell fields");
+        AsyncBuf Gfull((size_t)dl.G_full * sizeof(float2), p.stream, "diagonal shell fields");
+        AsyncBuf sq((size_t)nb * M * zstage_row_groups(M) * sizeof(double), p.stream, "diagonal shell fields");
+        float2 *G0 = lv.d_G;
+        const int slab0 = lv.slab;
+        lv.d_G = Gfull.as<float2>();
+        lv.slab = M;
+        try {
+            launch_inverse_x(lv, false);
+            launch_inverse_yz_slab_geom(lv, 0, M, Ifull.as<float>(), dl.d_geom_full, nb, nb, sq.as<double>());
+        } catch (...) {
+            lv.d_G = G0;
+            lv.slab = slab0;
+            throw;
+        }
+        lv.d_G = G0;
+        lv.slab = slab0;
+        const long long per = (long long)dl.bx.D * dl.bx.D * dl.bx.Dz;  // complex elements of one pair spectrum
+        const int K = (int)std::max<long long>(1, std::min<long long>(np, (4LL << 30) / (per * 8)));
+        const int ng = (np + K - 1) / K;
+        AsyncBuf prod((size_t)M3 * sizeof(float), p.stream, "diagonal scratch");
+        AsyncBuf zb((size_t)M * M * dl.bx.Dz * sizeof(float2), p.stream, "diagonal scratch");
+        AsyncBuf yb((size_t)M * dl.bx.D * dl.bx.Dz * sizeof(float2), p.stream, "diagonal scratch");
+        AsyncBuf FA((size_t)std::min(np, K) * per * sizeof(float2), p.stream, "pair spectra");
+        AsyncBuf FB(ng > 1 ? (size_t)K * per * sizeof(float2) : 16, p.stream, "pair spectra");
+        const float *If = Ifull.as<float>();
+        auto compute = [&](int g, float2 *dst) {
+            for (int j = g * K; j < std::min(np, (g + 1) * K); ++j) {
+                launch_field_product(lv, If + (long long)dl.pairs[j].first * M3, If + (long long)dl.pairs[j].second * M3,
+                                     prod.as<float>(), M3);
+                launch_forward_grid(lv, M, dl.bx, lv.fM, lv.d_twM, prod.as<float>(), nullptr, 1, zb.as<float2>(),
+                                    yb.as<float2>(), dst + (long long)(j - g * K) * per);
+            }
+        };
+        const double scale = 1.0 / ((double)M3 * (double)M3);  // DFT_M of a pair product is M^3 F_ab
+        const int nql = (int)lv.nquad.size();
+        for (int gi = 0; gi < ng; ++gi) {
+            compute(gi, FA.as<float2>());
+            for (int gj = gi; gj < ng; ++gj) {
+                std::vector<long long> offs;
+                std::vector<int> qout;
+                for (int i = 0; i < nql; ++i) {
+                    const int g0 = dl.qp[i][0] / K, g1 = dl.qp[i][1] / K;
+                    int u, v;
+                    if (g0 == gi && g1 == gj) {
+                        u = dl.qp[i][0];
+                        v = dl.qp[i][1];
+                    } else if (g1 == gi && g0 == gj) {
+                        u = dl.qp[i][1];
+                        v = dl.qp[i][0];
+                    } else {
+                        continue;
+                    }
+                    offs.push_back((long long)(u - gi * K) * per);
+                    offs.push_back((long long)(v - gj * K) * per);
+                    qout.push_back(lv.gquad[i]);
+                }
+                if (qout.empty()) continue;
+                const float2 *Bp = FA.as<float2>();
+                if (gj != gi) {
+                    compute(gj, FB.as<float2>());
+                    Bp = FB.as<float2>();
+                }
+                for (size_t c0 = 0; c0 < qout.size(); c0 += 65535) {
+                    const int nc = (int)std::min<size_t>(65535, qout.size() - c0);
+                    AsyncBuf d_offs((size_t)nc * 2 * sizeof(long long), p.stream, "diagonal scratch");
+                    AsyncBuf d_q((size_t)nc * sizeof(int), p.stream, "diagonal scratch");
+                    FBS_CUDA(cudaMemcpyAsync(d_offs.ptr, offs.data() + 2 * c0, (size_t)nc * 2 * sizeof(long long),
+                                             cudaMemcpyHostToDevice, p.stream));
+                    FBS_CUDA(cudaMemcpyAsync(d_q.ptr, qout.data() + c0, (size_t)nc * sizeof(int),
+                                             cudaMemcpyHostToDevice, p.stream));
+                    launch_diag_gram(lv, FA.as<float2>(), Bp, d_offs.as<long long>(), nc, dl.d_idx, dl.d_w,
+                                     dl.d_dstart, nd, d_q.as<int>(), scale, ds.d_num);
+                    FBS_CUDA(cudaStreamSynchronize(p.stream));  // offs and qout go out of scope
+                }
+            }
+        }
+    }
+    const double V = p.L * p.L * p.L, npix = (double)p.N * p.N * p.N;
+    launch_diag_normalise(p, ds.d_num, ds.d_cnt, (long long)ds.cnt.size(), V * V * V / (npix * npix * npix * npix),
+                          ds.d_TD);
 }
 
 // A tensor-core wait that gave up leaves a flag on the device; the outputs
@@ -1327,6 +1553,7 @@ void fbs_plan_free(fbs_plan *plan) {
     cudaGetLastError();
     free_tc_state(*plan);
     free_batch(*plan);
+    free_diag(*plan);
     for (Plan *lv : plan->levels) {
         free_tc_state(*lv);
         delete lv;
@@ -1511,6 +1738,63 @@ fbs_status fbs_bispectrum_batch(fbs_plan *plan, const float *const *fields, int 
         FBS_CUDA(cudaStreamSynchronize(plan->stream));
         check_device_errors(*plan);
     }
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+fbs_status fbs_plan_set_diagonal(fbs_plan *plan, const double *diag_edges, int ndiag) {
+    if (!plan || !diag_edges || ndiag < 1 || ndiag > 4096) {
+        set_error("fbs_plan_set_diagonal: bad argument");
+        return FBS_ERR_ARG;
+    }
+    if (!(plan->flags & FBS_FLAG_TRISPECTRUM)) {
+        set_error("plan was created without FBS_FLAG_TRISPECTRUM");
+        return FBS_ERR_STATE;
+    }
+    FBS_GUARD_BEGIN
+    FBS_CUDA(cudaStreamSynchronize(plan->stream));
+    set_diagonal(*plan, diag_edges, ndiag);
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
+int fbs_plan_num_diagonal_bins(const fbs_plan *plan) {
+    if (!plan) return FBS_ERR_ARG;
+    return plan->diag ? reinterpret_cast<const DiagState *>(plan->diag)->nd : 0;
+}
+
+fbs_status fbs_plan_diagonal_counts(const fbs_plan *plan, double *counts, uint64_t *words) {
+    if (!plan || !plan->diag) {
+        set_error("fbs_plan_diagonal_counts: no diagonal bins set");
+        return plan ? FBS_ERR_STATE : FBS_ERR_ARG;
+    }
+    const DiagState &ds = *reinterpret_cast<const DiagState *>(plan->diag);
+    for (size_t i = 0; i < ds.cnt128.size(); ++i) {
+        if (counts) counts[i] = ds.cnt[i];
+        if (words) {
+            words[2 * i] = ds.cnt128[i].lo;
+            words[2 * i + 1] = ds.cnt128[i].hi;
+        }
+    }
+    return FBS_OK;
+}
+
+fbs_status fbs_trispectrum_diagonal(fbs_plan *plan, const float *field, double *TD) {
+    if (!plan || !field || !TD) {
+        set_error("fbs_trispectrum_diagonal: NULL argument");
+        return FBS_ERR_ARG;
+    }
+    if (!plan->diag) {
+        set_error("fbs_trispectrum_diagonal: call fbs_plan_set_diagonal first");
+        return FBS_ERR_STATE;
+    }
+    FBS_GUARD_BEGIN
+    poll_device_errors(*plan);
+    run_diagonal(*plan, field);
+    const DiagState &ds = *reinterpret_cast<const DiagState *>(plan->diag);
+    bool host = false;
+    copy_out(*plan, TD, ds.d_TD, ds.cnt.size(), host);
+    if (host) FBS_CUDA(cudaStreamSynchronize(plan->stream));
     return FBS_OK;
     FBS_GUARD_END
 }

@@ -157,9 +157,82 @@ __global__ void __launch_bounds__(kThr) quad_dot_kernel(const uint32_t *__restri
     }
 }
 
+// Diagonal-resolved counts: out[(q nd + D) 2 + {0, 1}] = low and high words of
+// sum over the octant points of diagonal shell D (list oidx, 2^oshift each,
+// dstart[D]..dstart[D+1]) of C0[off0 + i] C1[off1 + i]; block (D, q).
+__global__ void __launch_bounds__(kThr) diag_dot_kernel(const uint32_t *__restrict__ C0,
+                                                        const uint32_t *__restrict__ C1,
+                                                        const long long *__restrict__ offs,
+                                                        const int *__restrict__ oidx,
+                                                        const unsigned char *__restrict__ oshift,
+                                                        const int *__restrict__ dstart, int nd,
+                                                        unsigned long long *__restrict__ out) {
+    __shared__ unsigned long long slo[kThr], shi[kThr];
+    const int D = blockIdx.x, q = blockIdx.y;
+    const uint32_t *x = C0 + offs[2 * q];
+    const uint32_t *y = C1 + offs[2 * q + 1];
+    unsigned long long lo = 0, hi = 0;
+    for (int e = dstart[D] + threadIdx.x; e < dstart[D + 1]; e += blockDim.x) {
+        const int i = oidx[e], s = oshift[e];
+        const unsigned long long p = (unsigned long long)x[i] * (unsigned long long)y[i];
+        const unsigned long long plo = p << s, phi = s ? (p >> (64 - s)) : 0ull;
+        lo += plo;
+        hi += phi + (lo < plo ? 1ull : 0ull);
+    }
+    slo[threadIdx.x] = lo;
+    shi[threadIdx.x] = hi;
+    __syncthreads();
+    for (int w = kThr / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            const unsigned long long a0 = slo[threadIdx.x], s0 = a0 + slo[threadIdx.x + w];
+            shi[threadIdx.x] += shi[threadIdx.x + w] + (s0 < a0 ? 1ull : 0ull);
+            slo[threadIdx.x] = s0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[((long long)q * nd + D) * 2] = slo[0];
+        out[((long long)q * nd + D) * 2 + 1] = shi[0];
+    }
+}
+
 }  // namespace
 
-void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &items, std::vector<U128> &out) {
+// Octant points of every diagonal shell: |q|^2 = ix^2 + iy^2 + iz^2 in
+// [thr[D], thr[D+1]) with octant coordinates below H, weight 2^(coordinates
+// off the planes 0 and H-1), grouped by shell.
+static void octant_shell_lists(int H, const std::vector<long long> &thr, std::vector<int> &idx,
+                               std::vector<unsigned char> &shift, std::vector<int> &start) {
+    const int nd = (int)thr.size() - 1;
+    std::vector<std::vector<int>> li(nd);
+    std::vector<std::vector<unsigned char>> ls(nd);
+    const long long top = thr[nd];
+    for (int ix = 0; ix < H; ++ix)
+        for (int iy = 0; iy < H; ++iy) {
+            const long long r2 = (long long)ix * ix + (long long)iy * iy;
+            if (r2 >= top) break;
+            for (int iz = 0; iz < H; ++iz) {
+                const long long s2 = r2 + (long long)iz * iz;
+                if (s2 >= top) break;
+                if (s2 < thr[0]) continue;
+                const int D = (int)(std::upper_bound(thr.begin(), thr.end(), s2) - thr.begin()) - 1;
+                li[D].push_back((int)(((long long)ix * H + iy) * H + iz));
+                ls[D].push_back((unsigned char)((ix != 0 && ix != H - 1) + (iy != 0 && iy != H - 1) +
+                                                (iz != 0 && iz != H - 1)));
+            }
+        }
+    idx.clear();
+    shift.clear();
+    start.assign(1, 0);
+    for (int D = 0; D < nd; ++D) {
+        idx.insert(idx.end(), li[D].begin(), li[D].end());
+        shift.insert(shift.end(), ls[D].begin(), ls[D].end());
+        start.push_back((int)idx.size());
+    }
+}
+
+void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &items, std::vector<U128> &out,
+                       const std::vector<long long> *dthr, std::vector<U128> *dout) {
     const int n = (int)(items.size() / 4);
     out.assign(n, U128{});
     if (n == 0) return;
@@ -188,6 +261,26 @@ void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &item
     AsyncBuf bufA((size_t)std::min(np, K) * per, p.stream, "pair-count fields");
     AsyncBuf bufB(ng > 1 ? (size_t)K * per : 16, p.stream, "pair-count fields");
     AsyncBuf dist(sizeof(unsigned long long), p.stream, "quadruple-count scratch");
+    // diagonal shells (optional): octant point lists on the device
+    const int nd = dthr ? (int)dthr->size() - 1 : 0;
+    std::vector<int> didx, dstart;
+    std::vector<unsigned char> dshift;
+    if (nd > 0) {
+        octant_shell_lists(H, *dthr, didx, dshift, dstart);
+        dout->assign((size_t)n * nd, U128{});
+    }
+    AsyncBuf d_didx(std::max<size_t>(1, didx.size()) * sizeof(int), p.stream, "diagonal shells");
+    AsyncBuf d_dshift(std::max<size_t>(1, dshift.size()), p.stream, "diagonal shells");
+    AsyncBuf d_dstart(std::max<size_t>(1, dstart.size()) * sizeof(int), p.stream, "diagonal shells");
+    if (nd > 0) {
+        if (!didx.empty()) {
+            FBS_CUDA(cudaMemcpyAsync(d_didx.ptr, didx.data(), didx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                     p.stream));
+            FBS_CUDA(cudaMemcpyAsync(d_dshift.ptr, dshift.data(), dshift.size(), cudaMemcpyHostToDevice, p.stream));
+        }
+        FBS_CUDA(cudaMemcpyAsync(d_dstart.ptr, dstart.data(), dstart.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 p.stream));
+    }
     FBS_CUDA(cudaMemsetAsync(dist.ptr, 0, sizeof(unsigned long long), p.stream));
     const int nl = std::max(1, std::min(16, (96 * 1024) / (2 * M * (int)sizeof(double2))));
     const size_t esm = 2 * (size_t)nl * M * sizeof(double2);
@@ -215,7 +308,7 @@ void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &item
     const int gx = (int)std::max<long long>(1, std::min<long long>(128, (H3 + kThr - 1) / kThr));
     constexpr int kChunk = 32768;  // quadruplets per dot launch (grid y)
     AsyncBuf offs_buf((size_t)std::min(n, kChunk) * 2 * sizeof(long long), p.stream, "quadruple-count scratch");
-    AsyncBuf part_buf((size_t)std::min(n, kChunk) * gx * 2 * sizeof(unsigned long long), p.stream,
+    AsyncBuf part_buf((size_t)std::min(n, kChunk) * std::max(gx, nd) * 2 * sizeof(unsigned long long), p.stream,
                       "quadruple-count scratch");
     std::vector<long long> offs;
     std::vector<int> which;
@@ -268,6 +361,22 @@ void exact_quad_counts(Plan &p, const double *noct, const std::vector<int> &item
                     U128 &o = out[which[c0 + k]];
                     o.lo = (uint64_t)s;
                     o.hi = (uint64_t)(s >> 64);
+                }
+                if (nd > 0) {
+                    diag_dot_kernel<<<dim3(nd, nc), kThr, 0, p.stream>>>(
+                        bufA.as<uint32_t>(), Bp, offs_buf.as<long long>(), d_didx.as<int>(),
+                        d_dshift.as<unsigned char>(), d_dstart.as<int>(), nd, part_buf.as<unsigned long long>());
+                    FBS_CUDA(cudaGetLastError());
+                    part.resize((size_t)nc * nd * 2);
+                    FBS_CUDA(cudaMemcpyAsync(part.data(), part_buf.ptr, part.size() * sizeof(unsigned long long),
+                                             cudaMemcpyDeviceToHost, p.stream));
+                    FBS_CUDA(cudaStreamSynchronize(p.stream));
+                    for (int k = 0; k < nc; ++k)
+                        for (int D = 0; D < nd; ++D) {
+                            U128 &o = (*dout)[(size_t)which[c0 + k] * nd + D];
+                            o.lo = part[((size_t)k * nd + D) * 2];
+                            o.hi = part[((size_t)k * nd + D) * 2 + 1];
+                        }
                 }
             }
         }
