@@ -559,6 +559,116 @@ def diagonal_trispectrum(field, L: float, edges, diag_edges, quads):
     return {"num": num, "num_im": numi, "cnt": cnt, "T": T, "mag": mag}
 
 
+# --------------------------------------------------------------------------
+# Non-cubic boxes and complex fields (Sec. 2: the footnote on non-cubic data
+# and the remark that Eq. Jeong_gen applies to complex data through complex
+# DFTs).  Grid N_x x N_y x N_z, box L_x x L_y x L_z, mode m with components
+# in FFT order; k = 2 pi (m_x/L_x, m_y/L_y, m_z/L_z); V = L_x L_y L_z and
+# N_pix = N_x N_y N_z take the places of L^3 and N^3.
+# --------------------------------------------------------------------------
+
+def general_mode_s(shape, Ls) -> np.ndarray:
+    """s(m) = (m_x/L_x)^2 + (m_y/L_y)^2 + (m_z/L_z)^2 = |k|^2 / (2 pi)^2 on the
+    grid (FFT order), evaluated in that order in FP64."""
+    f = [np.fft.fftfreq(n, d=1.0 / n) for n in shape]
+    ux = f[0] / float(Ls[0])
+    uy = f[1] / float(Ls[1])
+    uz = f[2] / float(Ls[2])
+    return (ux[:, None, None] * ux[:, None, None] + uy[None, :, None] * uy[None, :, None]) + \
+        uz[None, None, :] * uz[None, None, :]
+
+
+def general_thresholds(edges) -> np.ndarray:
+    """t_b = (edge_b / (2 pi))^2: bin b holds t_b <= s(m) < t_{b+1}."""
+    out = []
+    for e in np.asarray(edges, dtype=np.float64):
+        u = float(e) / (2.0 * math.pi)
+        out.append(u * u)
+    return np.array(out)
+
+
+def general_bin_index(shape, Ls, edges) -> np.ndarray:
+    t = general_thresholds(edges)
+    s = general_mode_s(shape, Ls)
+    b = np.searchsorted(t, s, side="right") - 1
+    b[(s < t[0]) | (s >= t[-1])] = -1
+    return b
+
+
+def general_bispectrum(field, Ls, edges):
+    """The FFT estimator on a non-cubic grid for a real or complex field
+    (Eqs. delta_nr, Jeong_PS, Jeong_BI with complex DFTs), FP64:
+      D = DFT[delta] (complex, no Hermitian half), I_b = unnormalised inverse
+      DFT of D on S_b (complex), N_b the same of the indicator (real: every
+      shell is symmetric under m -> -m modulo the grid),
+      B = V^2/N_pix^3 sum_n I_a I_b I_c / (N_pix N_tri)   (complex),
+      P = V/N_pix^2   sum_n I_b I_b / (N_pix |S_b|)        (complex: for a
+          complex field Eq. Jeong_PS pairs D(m) with D(-m)),
+    over every a <= b <= c of non-empty bins with N_tri > 0 (closure modulo
+    the grid along each axis).  Returns dict with triplets, N_tri, num
+    (complex ordered sums sum_n I_a I_b I_c / N_pix), B, P, shell."""
+    field = np.asarray(field)
+    shape = field.shape
+    npix = float(np.prod(shape))
+    V = float(Ls[0]) * float(Ls[1]) * float(Ls[2])
+    bins = general_bin_index(shape, Ls, edges)
+    nb = len(edges) - 1
+    D = _fftn(field.astype(np.complex128))
+    S = np.bincount(bins[bins >= 0].ravel(), minlength=nb).astype(np.int64)
+    I = {b: _ifftn(np.where(bins == b, D, 0.0)) * npix for b in range(nb) if S[b]}
+    C = {b: (_ifftn((bins == b).astype(np.complex128)) * npix).real for b in range(nb) if S[b]}
+    P = np.full(nb, np.nan + 0j)
+    for b in I:
+        P[b] = (V / npix ** 2) * complex(np.sum(I[b] * I[b])) / (npix * S[b])
+    trip, cnt, num = [], [], []
+    for a in I:
+        for b in I:
+            if b < a:
+                continue
+            for c in I:
+                if c < b:
+                    continue
+                n = float(np.sum(C[a] * C[b] * C[c])) / npix
+                r = round(n)
+                if abs(n - r) > 0.25:
+                    raise ArithmeticError("count sum is not an integer")
+                if r > 0:
+                    trip.append((a, b, c))
+                    cnt.append(r)
+                    num.append(complex(np.sum(I[a] * I[b] * I[c])) / npix)
+    cnt = np.array(cnt, dtype=np.int64)
+    num = np.array(num, dtype=np.complex128)
+    B = (V * V / npix ** 3) * num / np.maximum(cnt, 1)
+    return {"triplets": np.array(trip, dtype=np.int32).reshape(-1, 3), "N_tri": cnt, "num": num, "B": B, "P": P,
+            "shell": S}
+
+
+def general_direct_sums(field, Ls, edges):
+    """Ordered all-pairs sums by the definition (tiny grids): for every m1, m2
+    with m3 = -(m1 + m2) modulo the grid along each axis, D(m1) D(m2) D(m3)
+    and 1 added to (bin m1, bin m2, bin m3).  Returns (num complex, cnt) of
+    shape (nb, nb, nb)."""
+    field = np.asarray(field)
+    shape = field.shape
+    nb = len(edges) - 1
+    bins = general_bin_index(shape, Ls, edges)
+    D = _fftn(field.astype(np.complex128))
+    idx = np.argwhere(bins >= 0)
+    num = np.zeros((nb, nb, nb), dtype=np.complex128)
+    cnt = np.zeros((nb, nb, nb), dtype=np.int64)
+    n = np.array(shape)
+    for m1 in idx:
+        m3 = (-(m1[None, :] + idx)) % n
+        b3 = bins[m3[:, 0], m3[:, 1], m3[:, 2]]
+        ok = b3 >= 0
+        a = bins[tuple(m1)]
+        b2 = bins[idx[ok, 0], idx[ok, 1], idx[ok, 2]]
+        v = D[tuple(m1)] * D[idx[ok, 0], idx[ok, 1], idx[ok, 2]] * D[m3[ok, 0], m3[ok, 1], m3[ok, 2]]
+        np.add.at(num, (a, b2, b3[ok]), v)
+        np.add.at(cnt, (a, b2, b3[ok]), 1)
+    return num, cnt
+
+
 def rebinned_bispectrum(field, L: float, edges, k_edges, mu_edges, k_rep=None):
     """Fine bins, then (k1, k2, cos theta) cells (Sec. 3.1: bin finely, then
     rebin; theta is the triangle's internal angle between k1 and k2, the

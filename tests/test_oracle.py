@@ -852,3 +852,64 @@ def test_diagonal_zero_shell_is_the_paired_term():
             assert math.isclose(e["num"][i, 0], S2[a] * S2[c], rel_tol=1e-12)
         else:
             assert e["cnt"][i][0] == 0 and abs(e["num"][i, 0]) <= 1e-12 * max(S2) ** 2  # FFT rounding only
+
+
+# ---------------------------------------------------------------- non-cubic boxes, complex fields
+def _complex_field(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+GENERAL_CASES = [((6, 8, 10), (30.0, 40.0, 55.0), "complex", 31), ((8, 8, 12), (20.0, 20.0, 33.0), "real", 32),
+                 ((5, 9, 6), (10.0, 21.0, 13.0), "complex", 33)]
+
+
+def _general_edges(shape, Ls, nb):
+    kmin = 2 * math.pi / max(Ls)
+    kmax = 2 * math.pi * min(n / 4.0 / L for n, L in zip(shape, Ls))
+    return np.geomspace(0.9 * kmin, kmax, nb + 1)
+
+
+@pytest.mark.parametrize("shape,Ls,kind,seed", GENERAL_CASES)
+def test_general_fft_route_equals_brute_force(shape, Ls, kind, seed):
+    f = _complex_field(shape, seed)
+    if kind == "real":
+        f = f.real
+    edges = _general_edges(shape, Ls, 4)
+    e = oracle.general_bispectrum(f, Ls, edges)
+    num, cnt = oracle.general_direct_sums(f, Ls, edges)
+    closed = [tuple(t) for t in np.argwhere(cnt > 0) if t[0] <= t[1] <= t[2]]
+    assert [tuple(t) for t in e["triplets"]] == sorted(closed)
+    for t, (a, b, c) in enumerate(e["triplets"]):
+        assert e["N_tri"][t] == cnt[a, b, c]
+        assert abs(e["num"][t] - num[a, b, c]) <= 1e-10 * np.abs(num).max()
+    if kind == "real":
+        assert np.abs(e["num"].imag).max() <= 1e-10 * np.abs(e["num"]).max()
+
+
+def test_general_cubic_real_case_is_the_cubic_estimator():
+    N, L = 16, 40.0
+    f = fields.lognormal(N, 0.5, -1.5, seed=34)
+    edges = fields.log_edges(N, L, 5) * 1.0001  # away from |m|^2 ties
+    g = oracle.general_bispectrum(f, (L, L, L), edges)
+    c = oracle.fft_estimator(f, L, edges, triplets=g["triplets"])
+    assert np.array_equal(g["N_tri"], c["N_tri"])
+    assert np.allclose(g["B"].real, c["B"], rtol=1e-10, atol=1e-12 * np.abs(c["B"]).max())
+    ok = np.isfinite(c["P"])
+    assert np.allclose(g["P"].real[ok], c["P"][ok], rtol=1e-10)
+
+
+def test_general_axis_permutation_and_conjugation():
+    shape, Ls = (6, 8, 10), (30.0, 40.0, 55.0)
+    f = _complex_field(shape, 35)
+    edges = _general_edges(shape, Ls, 4)
+    e = oracle.general_bispectrum(f, Ls, edges)
+    # the same data with the axes relabelled
+    t = oracle.general_bispectrum(np.transpose(f, (1, 2, 0)), (Ls[1], Ls[2], Ls[0]), edges)
+    assert np.array_equal(t["triplets"], e["triplets"]) and np.array_equal(t["N_tri"], e["N_tri"])
+    assert np.allclose(t["B"], e["B"], rtol=1e-10, atol=1e-12 * np.abs(e["B"]).max())
+    # conj(delta) has D'(m) = conj D(-m): B and P become their conjugates
+    c = oracle.general_bispectrum(np.conj(f), Ls, edges)
+    assert np.allclose(c["B"], np.conj(e["B"]), rtol=1e-10, atol=1e-12 * np.abs(e["B"]).max())
+    ok = np.isfinite(e["P"].real)
+    assert np.allclose(c["P"][ok], np.conj(e["P"][ok]), rtol=1e-10)
