@@ -317,6 +317,42 @@ fbs_status fbs_plan_diagonal_counts(const fbs_plan *plan, double *counts, uint64
 fbs_status fbs_trispectrum_diagonal(fbs_plan *plan, const float *field, double *TD);
 
 /*
+ * Non-cubic grids and complex fields (Sec. 2: its footnote on non-cubic data,
+ * and the remark that Eq. Jeong_gen applies to complex data through complex
+ * DFTs).  A separate plan type on the whole grid, FP32 transforms and
+ * products with FP64 sums, bispectrum and power spectrum.
+ *
+ * fbs_gplan_create -- grid n[3] = (N_x, N_y, N_z), each 2^a 3^b in 2..512;
+ * box L[3] = (L_x, L_y, L_z) > 0; edges[nbins+1] ascending, physical k.  Mode
+ * m (components in FFT order) has k = 2 pi (m_x/L_x, m_y/L_y, m_z/L_z) and is
+ * in bin b when t_b <= s(m) < t_{b+1}, s(m) = (m_x/L_x)^2 + (m_y/L_y)^2 +
+ * (m_z/L_z)^2 and t_b = (edges[b] / 2 pi)^2 (FP64, in that order).  Closed
+ * triplets a <= b <= c close modulo the grid along each axis; unless flags
+ * holds FBS_FLAG_ALLOW_ALIASED every mode of every bin must have |m_j| <
+ * N_j/4 (FBS_ERR_ARG otherwise), where that is exact closure.  Exact
+ * triangle counts from FP64 count fields at plan time (FBS_ERR_NUMERIC if a
+ * count sum is not within 0.25 of an integer).  Other flags are ignored.
+ * fbs_gplan_num_triplets / fbs_gplan_triplets (abc[3*ntrip], ntri[ntrip],
+ * either may be NULL) / fbs_gplan_shells (sizes[nbins]) -- host copies.
+ * fbs_gplan_bispectrum -- field: complex64 interleaved (re, im) floats,
+ * [N_x][N_y][N_z], device or host (a real field: imaginary parts zero).
+ * B[2*ntrip] = (Re, Im) of V^2/N_pix^3 sum_n I_a I_b I_c / (N_pix N_tri) and
+ * P[2*nbins] = (Re, Im) of V/N_pix^2 sum_n I_b I_b / (N_pix |S_b|) (NaN for
+ * empty bins), V = L_x L_y L_z, N_pix = N_x N_y N_z, I_b the unnormalised
+ * inverse DFT of the spectrum on S_b; device or host, either may be NULL.
+ * Synchronous (returns with the outputs written).
+ * fbs_gplan_free -- releases the plan (NULL is a no-op).
+ */
+typedef struct fbs_gplan fbs_gplan;
+fbs_status fbs_gplan_create(fbs_gplan **out, const int32_t *n, const double *L, const double *edges, int nbins,
+                            uint32_t flags);
+int fbs_gplan_num_triplets(const fbs_gplan *g);
+fbs_status fbs_gplan_triplets(const fbs_gplan *g, int32_t *abc, int64_t *ntri);
+fbs_status fbs_gplan_shells(const fbs_gplan *g, int64_t *sizes);
+fbs_status fbs_gplan_bispectrum(fbs_gplan *g, const float *field, double *B, double *P);
+void fbs_gplan_free(fbs_gplan *g);
+
+/*
  * fbs_plan_triangle_average -- a model averaged over each closed triplet's
  * exact set of triangles, as the paper compares theory with its measurements
  * (theory evaluated for every triangle contributing to a bin and averaged,

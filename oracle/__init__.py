@@ -570,7 +570,7 @@ def diagonal_trispectrum(field, L: float, edges, diag_edges, quads):
 def general_mode_s(shape, Ls) -> np.ndarray:
     """s(m) = (m_x/L_x)^2 + (m_y/L_y)^2 + (m_z/L_z)^2 = |k|^2 / (2 pi)^2 on the
     grid (FFT order), evaluated in that order in FP64."""
-    f = [np.fft.fftfreq(n, d=1.0 / n) for n in shape]
+    f = [np.concatenate([np.arange(0, (n + 1) // 2), np.arange(-(n // 2), 0)]).astype(np.float64) for n in shape]
     ux = f[0] / float(Ls[0])
     uy = f[1] / float(Ls[1])
     uz = f[2] / float(Ls[2])

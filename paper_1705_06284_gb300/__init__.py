@@ -109,6 +109,12 @@ _SIGS = [
     ("fbs_rebin_bispectrum", ctypes.c_int, [_vp, _vp, _vp]),
     ("fbs_rebin_counts", ctypes.c_int, [_vp, _vp]),
     ("fbs_rebin_free", None, [_vp]),
+    ("fbs_gplan_create", ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_uint32]),
+    ("fbs_gplan_num_triplets", ctypes.c_int, [_vp]),
+    ("fbs_gplan_triplets", ctypes.c_int, [_vp, _vp, _vp]),
+    ("fbs_gplan_shells", ctypes.c_int, [_vp, _vp]),
+    ("fbs_gplan_bispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("fbs_gplan_free", None, [_vp]),
     ("fbs_set_device_budget", ctypes.c_int, [ctypes.c_int64]),
     ("fbs_device_bytes_in_use", ctypes.c_int64, []),
     ("fbs_triple_sums_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
@@ -449,6 +455,65 @@ class Plan:
         _check(lib().fbs_plan_kernel_times(_vp(self._h), ms.ctypes.data, cnt.ctypes.data,
                                            1 if reset else 0))
         return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(kernel_class_names())}
+
+
+class GeneralPlan:
+    """Bispectrum and power spectrum on a non-cubic grid of a real or complex
+    field (fbs_gplan_*): shape (N_x, N_y, N_z), box (L_x, L_y, L_z), edges in
+    physical k.  ``bispectrum`` returns complex B[ntrip] and P[nbins]."""
+
+    def __init__(self, shape, Ls, edges, allow_aliased=False):
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        self.shape = tuple(int(v) for v in shape)
+        self.Ls = tuple(float(v) for v in Ls)
+        self.nbins = len(e) - 1
+        n = (ctypes.c_int32 * 3)(*self.shape)
+        L = (ctypes.c_double * 3)(*self.Ls)
+        h = ctypes.c_void_p()
+        Lb = lib()
+        _check(Lb.fbs_gplan_create(ctypes.byref(h), ctypes.cast(n, _vp), ctypes.cast(L, _vp), e.ctypes.data,
+                                   self.nbins, FBS_FLAG_ALLOW_ALIASED if allow_aliased else 0))
+        self._h = h
+        self.ntrip = int(Lb.fbs_gplan_num_triplets(_vp(h)))
+        self.triplets = np.zeros((self.ntrip, 3), dtype=np.int32)
+        self.N_tri = np.zeros(self.ntrip, dtype=np.int64)
+        _check(Lb.fbs_gplan_triplets(_vp(h), self.triplets.ctypes.data, self.N_tri.ctypes.data))
+        self.shell = np.zeros(self.nbins, dtype=np.int64)
+        _check(Lb.fbs_gplan_shells(_vp(h), self.shell.ctypes.data))
+
+    def bispectrum(self, field):
+        """field: NumPy array (real or complex) or a CUDA tensor (real or
+        complex) of the plan's shape; returns (B, P) as complex128 NumPy arrays."""
+        if tuple(field.shape) != self.shape:
+            raise ValueError("field must have shape %s" % (self.shape,))
+        if isinstance(field, np.ndarray):
+            buf = np.ascontiguousarray(field, dtype=np.complex64)
+            fp = buf.ctypes.data
+        else:
+            import torch
+            buf = field.to(torch.complex64).contiguous()
+            fp = buf.data_ptr()
+        B = np.zeros(2 * max(1, self.ntrip))
+        P = np.zeros(2 * self.nbins)
+        _check(lib().fbs_gplan_bispectrum(_vp(self._h), _vp(fp), B.ctypes.data, P.ctypes.data))
+        return B[: 2 * self.ntrip].view(np.complex128), P.view(np.complex128)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fbs_gplan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Rebin:

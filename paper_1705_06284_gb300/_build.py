@@ -19,7 +19,8 @@ LIB = os.path.join(HERE, "libfbs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["plan.cpp", "pair_cover.cpp", "levels.cpp", "fft.cu", "contract.cu", "contract_tc.cu", "rebin.cu",
-           "quad_counts.cu", "diagonal.cu", "noalloc.cu"]
+           "quad_counts.cu", "diagonal.cu", "general.cu",
+           "noalloc.cu"]
 
 
 def _nvcc() -> str:
