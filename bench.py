@@ -29,6 +29,17 @@ import time
 
 import numpy as np
 
+_T0 = time.perf_counter()
+_PHASES = {}
+
+
+def _phase(name):
+    """Progress on stderr (the JSON line stays alone on stdout) and the time
+    each phase began, for the line's ``phase_s``."""
+    t = time.perf_counter() - _T0
+    _PHASES[name] = round(t, 1)
+    print("[bench +%.1fs] %s" % (t, name), file=sys.stderr, flush=True)
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -241,6 +252,7 @@ def main():
     field = torch.from_numpy(f32).to(dev)
     eB, eT = edges(N, args.nb), edges(N, args.nbt)
     t0 = time.perf_counter()
+    _phase("plans")
     planB = fbs.Plan(N, L_BOX, eB, precision=args.precision, timing=True, stream=stream)
     planT = fbs.Plan(N, L_BOX, eT, precision=args.precision, trispectrum=True, timing=True, stream=stream)
     plan_s = time.perf_counter() - t0
@@ -255,6 +267,7 @@ def main():
         planT.trispectrum(fld, outs[2], outs[3], outs[4])
 
     outs_dev = (B, P, T, B16, P16)
+    _phase("warmup and timed steps")
     for _ in range(args.warmup):
         step(field, outs_dev)
     torch.cuda.synchronize()
@@ -289,6 +302,7 @@ def main():
     # the host.
     e2e = None
     if not args.no_e2e:
+        _phase("e2e")
         hfield = torch.from_numpy(f32).pin_memory()
         sizes = (planB.ntrip, planB.nbins, planT.nquad, planT.ntrip, planT.nbins)
         outs_sets = [tuple(torch.empty(n, dtype=torch.float64).pin_memory() for n in sizes) for _ in range(2)]
@@ -354,6 +368,7 @@ def main():
         e2e.pop("_s", None)
         line["e2e"] = e2e
     if rank == 0 and not args.no_plain and world == 1:
+        _phase("plain_fp32_gpu")
         # plain FP32 GPU path on the same field (comparison only)
         try:
             thrB = np.asarray(planB.thresholds)
@@ -376,6 +391,7 @@ def main():
         except Exception as ex:
             line["plain_fp32_gpu"] = {"value": None, "error": str(ex)[:200]}
     if rank == 0 and not args.no_plain and world == 1:
+        _phase("cufft_fft_stage")
         try:
             ms_cu, nb_cu = cufft_fft_stage(field, N, np.asarray(planB.thresholds), dev)
             ours_fft = sum(kB.get(c, (0, 0))[0] for c in FFT_CLASSES) / args.steps
@@ -387,6 +403,7 @@ def main():
         except Exception as ex:
             line["cufft_fft_stage"] = {"value": None, "error": str(ex)[:200]}
     if rank == 0 and not args.no_workloads and world == 1:
+        _phase("workloads")
         try:
             import fields
             wl = {}
@@ -400,16 +417,19 @@ def main():
         except Exception as ex:
             line["workloads"] = {"error": str(ex)[:200]}
     if rank == 0 and not args.no_batch and world == 1:
+        _phase("batched")
         try:
             line["batched"] = batched_run(precision=args.precision)
         except Exception as ex:
             line["batched"] = {"value": None, "error": str(ex)[:200]}
     if rank == 0 and not args.no_serve and world == 1:
+        _phase("serving")
         try:
             line["serving"] = serving_run(precision=args.precision)
         except Exception as ex:
             line["serving"] = {"value": None, "error": str(ex)[:200]}
     if rank == 0 and not args.no_cpu_baseline and world == 1:
+        _phase("cpu_baseline")
         try:
             t_full, info = cpu_baseline(args, seconds=15.0)
             line["cpu_baseline"] = {"value": planB.ntrip / t_full, "unit": "triangle-bins/s",
@@ -421,6 +441,8 @@ def main():
         except Exception as ex:  # the baseline must not sink the bench line
             line["cpu_baseline"] = {"value": None, "error": str(ex)[:200]}
     if rank == 0:
+        _phase("done")
+        line["phase_s"] = dict(_PHASES)
         print(json.dumps(line), flush=True)
     planB.close()
     planT.close()
@@ -456,7 +478,7 @@ def _serving_requests(n_req, rate, seed, precision):
 
 
 def serving_run(n_req=1000, n_warm=200, rate=200.0, seed=7, budget=120 << 30, slots=4, precision="bf16x3",
-                plain_max_s=60.0):
+                plain_max_s=60.0, deadline_s=90.0):
     """Continuous-batching serving of a Poisson request stream (config 5), in
     `precision` and in the library's FP32, against the plain FP32 GPU path on
     the same stream.  A warm-up stream of `n_warm` requests (other seed) runs
@@ -464,24 +486,31 @@ def serving_run(n_req=1000, n_warm=200, rate=200.0, seed=7, budget=120 << 30, sl
     server in steady state has them.  The plain path serves the stream's
     requests one after another in arrival order (it has no overlap), given each
     request's closed triplets (plan-time information), until `plain_max_s` of
-    wall time."""
+    wall time.  Each stream is refused past `deadline_s` (requests not yet
+    admitted then count as refused), which bounds the phase; the two servers
+    share the plan-time counts cache."""
     import torch
     from paper_1705_06284_gb300.serve import EstimatorServer, latency_percentiles
     out = {"requests": n_req, "warmup_requests": n_warm, "arrival_rate_per_s": rate, "slots": slots,
-           "hbm_budget_gib": budget >> 30}
+           "hbm_budget_gib": budget >> 30, "deadline_s": deadline_s}
     ref = {}
+    counts = {}
     for prec in ([precision, "fp32"] if precision != "fp32" else ["fp32"]):
         srv = EstimatorServer(hbm_budget=budget, slots=slots)
-        srv.run(_serving_requests(n_warm, rate, seed + 1000, prec), realtime=True)
+        srv.counts_cache = counts
+        _phase("serving warm-up (%s)" % prec)
+        srv.run(_serving_requests(n_warm, rate, seed + 1000, prec), realtime=True, deadline_s=deadline_s)
         created0, cached0 = srv.plan_creations, srv.plans_from_cache
         reqs = _serving_requests(n_req, rate, seed, prec)
+        _phase("serving timed stream (%s)" % prec)
         t0 = time.perf_counter()
-        res = srv.run(reqs, realtime=True)
+        res = srv.run(reqs, realtime=True, deadline_s=deadline_s)
         wall = time.perf_counter() - t0
         ok = [r for r in res if r.error is None]
         tri = sum(len(r.B) for r in ok)
         d = {"value": tri / wall, "unit": "triangle-bins/s", "wall_s": wall, "served": len(ok),
-             "refused": len(res) - len(ok), "plans_created": srv.plan_creations - created0,
+             "refused": len(res) - len(ok), "refused_deadline": sum(1 for r in res if r.error == "deadline"),
+             "plans_created": srv.plan_creations - created0,
              "plans_from_cached_counts": srv.plans_from_cache - cached0,
              "plans_created_in_warmup": created0}
         d.update(latency_percentiles(res))
@@ -489,6 +518,7 @@ def serving_run(n_req=1000, n_warm=200, rate=200.0, seed=7, budget=120 << 30, sl
         out["ours_" + prec] = d
         ref[prec] = {r.rid: r for r in ok}
     # the plain FP32 GPU path on the same stream, one request after another
+    _phase("serving plain FP32 path")
     reqs = _serving_requests(n_req, rate, seed, "fp32")
     dev = torch.device("cuda")
     base = ref.get("fp32") or ref[precision]

@@ -258,20 +258,27 @@ class EstimatorServer:
         return Result(req.rid, np.zeros((0, 3), dtype=np.int32), np.zeros(0, dtype=np.int64), empty, empty,
                       req.arrival if realtime else 0.0, t, t, error=why)
 
-    def run(self, requests: Sequence[Request], realtime: bool = True) -> List[Result]:
+    def run(self, requests: Sequence[Request], realtime: bool = True,
+            deadline_s: Optional[float] = None) -> List[Result]:
         """Serve ``requests`` (sorted by arrival).  With ``realtime`` a request
         is not admitted before its arrival time; otherwise arrivals are
         ignored (all requests are available at once).  A request whose plan
         and buffers cannot fit the budget even with every idle plan evicted
         is refused (Result.error) instead of holding up the queue.  Requests
         wait in arrival order for a free slot; one whose plan is being built
-        lets later requests with ready plans go first."""
+        lets later requests with ready plans go first.  With ``deadline_s``,
+        requests not admitted within that many seconds of the start are
+        refused ("deadline"); admitted ones run to the end."""
         pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
         waiting: List[Request] = []
         results: List[Result] = []
         t0 = time.perf_counter()
         while pending or waiting or any(s.busy for s in self.slots) or self._building:
             now = time.perf_counter() - t0
+            if deadline_s is not None and now > deadline_s and (pending or waiting):
+                for r in list(waiting) + list(pending):
+                    results.append(self._refuse(r, "deadline", realtime, t0))
+                waiting, pending = [], collections.deque()
             while pending and (not realtime or pending[0].arrival <= now):
                 waiting.append(pending.popleft())
             if self._cancelled and waiting:

@@ -2,8 +2,9 @@
 evaluated with one fbs_bispectrum_batch per group (one launch per stage for
 all of a group's fields), captured into one CUDA graph.  The graph gives
 exactly the eager batched results; the batched results equal one call per
-field up to the rounding of the contraction's point ranges, and the oracle's
-within the precision's tolerance; multi-level plans batch too."""
+field up to the rounding of the contraction's point ranges (1e-5 of the
+field's largest |B|), and the oracle's within the precision's tolerance on
+the gated triplets; multi-level plans batch too."""
 import numpy as np
 import pytest
 
@@ -49,8 +50,9 @@ def test_graph_of_batches_equals_eager_and_single_calls(tmp_path, monkeypatch, p
     for (t1, B1, P1), (t2, B2, P2), (t3, B3, P3) in zip(eager, graph, single):
         assert np.array_equal(B1, B2) and np.array_equal(P1, P2, equal_nan=True)
         assert np.array_equal(P1, P3, equal_nan=True)  # same z-stage partials, same order
-        big = np.abs(B3) > 1e-3 * np.max(np.abs(B3))
-        assert np.all(rel_err(B1[big], B3[big]) < 1e-5)
+        # the contraction's point ranges differ (CTAs per field): rounding of the
+        # order of the precision, far below the largest |B| of the field
+        assert np.all(np.abs(B1 - B3) <= 1e-5 * np.max(np.abs(B3)))
     # every realisation of one grid against the oracle
     for k, f in enumerate(fl[:4]):
         f64 = f.astype(np.float64)
@@ -80,5 +82,4 @@ def test_batch_on_multi_level_plans(monkeypatch):
             torch.cuda.synchronize()
             Bs, Ps = Bs.cpu().numpy(), Ps.cpu().numpy()
             assert np.array_equal(P[i].cpu().numpy(), Ps, equal_nan=True)
-            big = np.abs(Bs) > 1e-3 * np.max(np.abs(Bs))
-            assert np.all(rel_err(B[i].cpu().numpy()[big], Bs[big]) < 1e-5)
+            assert np.all(np.abs(B[i].cpu().numpy() - Bs) <= 1e-5 * np.max(np.abs(Bs)))

@@ -167,3 +167,20 @@ def test_rebuilt_plans_take_their_counts_from_the_cache(monkeypatch):
     assert e2 is not None and FakePlan.closed == [8]
     e3 = srv._plan_for(_req(3, 8), "s3")          # the first key again: from its counts
     assert FakePlan.counts_seen[-1] == b"counts-8" and srv.plans_from_cache == 1
+
+
+def test_deadline_refuses_requests_not_yet_admitted(monkeypatch):
+    f8 = 2 * 8 ** 3 * 4
+    srv = _server(4 * (8000 + f8), monkeypatch)
+    srv.slots = [_FakeSlot()]
+    served = []
+
+    def fake_submit(slot, req, entry, t0):
+        served.append(req.rid)
+
+    monkeypatch.setattr(srv, "_submit", fake_submit)
+    reqs = [_req(1, 8), _req(2, 8, nb=5)]
+    reqs[1].arrival = 0.5  # arrives after the deadline
+    res = srv.run(reqs, realtime=True, deadline_s=0.05)
+    errs = {r.rid: r.error for r in res}
+    assert served == [1] and errs == {2: "deadline"}  # the stand-in submit leaves no result for 1
