@@ -462,11 +462,13 @@ def main():
         dist.destroy_process_group()
 
 
-def _serving_requests(n_req, rate, seed, precision):
+def _serving_requests(n_req, rate, seed, precision, every_key=False):
     """Config-5 request stream: Poisson arrivals at `rate`, grids uniform over
     {64, 128, 192, 256, 384}, lognormal or bubble fields (50/50), 8..48
     linear bins.  A small seeded pool of fields per grid (pinned host memory)
-    is cycled; requests differ in field, bins and arrival."""
+    is cycled; requests differ in field, bins and arrival.  `every_key`: one
+    request for each (grid, bin count) in a seeded random order instead (a
+    warm-up that leaves every plan's counts cached)."""
     import torch
     import fields
     from paper_1705_06284_gb300.serve import Request
@@ -478,10 +480,17 @@ def _serving_requests(n_req, rate, seed, precision):
                    torch.from_numpy(fields.bubbles(N, max(3.0, N / 40), 0.5, seed=seed + 2 * N)
                                     .astype(np.float32)).pin_memory()]
     t, reqs = 0.0, []
+    keys = [(N, nb) for N in grids for nb in range(8, 49)]
+    if every_key:
+        keys = [keys[i] for i in rng.permutation(len(keys))]
+        n_req = len(keys)
     for i in range(n_req):
         t += rng.exponential(1.0 / rate)
-        N = int(rng.choice(grids))
-        nb = int(rng.integers(8, 49))
+        if every_key:
+            N, nb = keys[i]
+        else:
+            N = int(rng.choice(grids))
+            nb = int(rng.integers(8, 49))
         L = float(N)
         reqs.append(Request(i, pool[N][int(rng.integers(0, 2))].numpy(), L,
                             tuple(np.linspace(2 * math.pi / L, 0.25 * N * 2 * math.pi / L, nb + 1)),
@@ -489,13 +498,13 @@ def _serving_requests(n_req, rate, seed, precision):
     return reqs
 
 
-def serving_run(n_req=1000, n_warm=200, rate=200.0, seed=7, budget=120 << 30, slots=4, precision="bf16x3",
-                plain_max_s=60.0, deadline_s=90.0):
+def serving_run(n_req=1000, rate=200.0, seed=7, budget=120 << 30, slots=4, precision="bf16x3",
+                plain_max_s=60.0, deadline_s=90.0, warm_deadline_s=150.0):
     """Continuous-batching serving of a Poisson request stream (config 5), in
     `precision` and in the library's FP32, against the plain FP32 GPU path on
-    the same stream.  A warm-up stream of `n_warm` requests (other seed) runs
-    first; it leaves plans resident and their plan-time counts cached, as a
-    server in steady state has them.  The plain path serves the stream's
+    the same stream.  A warm-up stream with one request per (grid, bin count)
+    (205 plan keys, other seed) runs first; it leaves plans resident and every
+    plan's counts cached, as a server in steady state has them.  The plain path serves the stream's
     requests one after another in arrival order (it has no overlap), given each
     request's closed triplets (plan-time information), until `plain_max_s` of
     wall time.  Each stream is refused past `deadline_s` (requests not yet
@@ -503,15 +512,18 @@ def serving_run(n_req=1000, n_warm=200, rate=200.0, seed=7, budget=120 << 30, sl
     share the plan-time counts cache."""
     import torch
     from paper_1705_06284_gb300.serve import EstimatorServer, latency_percentiles
-    out = {"requests": n_req, "warmup_requests": n_warm, "arrival_rate_per_s": rate, "slots": slots,
-           "hbm_budget_gib": budget >> 30, "deadline_s": deadline_s}
+    out = {"requests": n_req, "warmup": "one request per (grid, bin count)", "arrival_rate_per_s": rate,
+           "slots": slots, "hbm_budget_gib": budget >> 30, "deadline_s": deadline_s,
+           "plan_slab_gib": 1}
     ref = {}
     counts = {}
     for prec in ([precision, "fp32"] if precision != "fp32" else ["fp32"]):
         srv = EstimatorServer(hbm_budget=budget, slots=slots)
         srv.counts_cache = counts
         _phase("serving warm-up (%s)" % prec)
-        srv.run(_serving_requests(n_warm, rate, seed + 1000, prec), realtime=True, deadline_s=deadline_s)
+        warm = srv.run(_serving_requests(0, rate, seed + 1000, prec, every_key=True), realtime=True,
+                       deadline_s=warm_deadline_s)
+        out["warmup_served_" + prec] = sum(1 for r in warm if r.error is None)
         created0, cached0 = srv.plan_creations, srv.plans_from_cache
         reqs = _serving_requests(n_req, rate, seed, prec)
         _phase("serving timed stream (%s)" % prec)

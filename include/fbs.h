@@ -421,6 +421,16 @@ fbs_status fbs_set_device_budget(int64_t bytes);
 int64_t fbs_device_bytes_in_use(void);
 
 /*
+ * fbs_set_slab_budget -- process-wide default (bytes) of the shell-field slab
+ * buffer of plans created after the call (0 restores the default, 8 GiB; the
+ * environment variable FBS_SLAB_MB, when set, takes precedence).  A smaller
+ * slab holds fewer planes of the evaluation grid at once: less memory per
+ * plan (a server keeps more plans resident), more launches per evaluation.
+ * FBS_ERR_ARG for a negative value.
+ */
+fbs_status fbs_set_slab_budget(int64_t bytes);
+
+/*
  * fbs_plan_kernel_times -- with FBS_FLAG_TIMING, the CUDA-event time (ms) and
  * launch count accumulated per kernel class since the last reset, in the
  * order of fbs_kernel_class_name(0..n-1).  ms and launches are host arrays of

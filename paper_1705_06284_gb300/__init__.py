@@ -116,6 +116,7 @@ _SIGS = [
     ("fbs_gplan_bispectrum", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("fbs_gplan_free", None, [_vp]),
     ("fbs_set_device_budget", ctypes.c_int, [ctypes.c_int64]),
+    ("fbs_set_slab_budget", ctypes.c_int, [ctypes.c_int64]),
     ("fbs_device_bytes_in_use", ctypes.c_int64, []),
     ("fbs_triple_sums_noalloc", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                                 _vp, ctypes.c_int, _vp, _vp]),
@@ -199,6 +200,11 @@ def fbs_plan_check(h):
 def fbs_set_device_budget(nbytes):
     """Process-wide cap on the device bytes all plans may hold (0: none)."""
     _check(lib().fbs_set_device_budget(int(nbytes)))
+
+
+def fbs_set_slab_budget(nbytes):
+    """Process-wide default slab buffer of plans created afterwards (0: 8 GiB)."""
+    _check(lib().fbs_set_slab_budget(int(nbytes)))
 
 
 def fbs_device_bytes_in_use():
@@ -473,7 +479,7 @@ class GeneralPlan:
         Lb = lib()
         _check(Lb.fbs_gplan_create(ctypes.byref(h), ctypes.cast(n, _vp), ctypes.cast(L, _vp), e.ctypes.data,
                                    self.nbins, FBS_FLAG_ALLOW_ALIASED if allow_aliased else 0))
-        self._h = h
+        self._h = h = h.value
         self.ntrip = int(Lb.fbs_gplan_num_triplets(_vp(h)))
         self.triplets = np.zeros((self.ntrip, 3), dtype=np.int32)
         self.N_tri = np.zeros(self.ntrip, dtype=np.int64)
@@ -500,7 +506,7 @@ class GeneralPlan:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().fbs_gplan_free(self._h)
+            lib().fbs_gplan_free(_vp(self._h))
             self._h = None
 
     def __del__(self):

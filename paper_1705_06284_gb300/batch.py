@@ -196,7 +196,10 @@ class GraphBatch:
         return g
 
     def replay(self):
-        self.graph.replay()
+        """Launch the captured graph on the batch's stream (where the eager
+        calls and the timing events run)."""
+        with self.torch.cuda.stream(self.stream):
+            self.graph.replay()
 
     def results(self):
         """(triplets, B, P) of every realisation, in input order."""

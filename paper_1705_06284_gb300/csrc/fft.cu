@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(T *LP) inv_z_reg_kernel(const float2 *__restri
         const float2 *in1 = in0 + g.Dzb;
         const int Rz = g.Dzb - 1;  // highest mz held (<= N/2)
         float2 *Y = tile + line * LS;
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < N1 / T; ++j) {
             const int n1 = t + T * j;
             float2 v[N2];
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(T *LP) inv_z_reg_kernel(const float2 *__restri
             }
         }
         __syncthreads();
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < N2 / T; ++j) {
             const int k2 = t + T * j;
             float2 v[N1];
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(T *LP) inv_z_reg_kernel(const float2 *__restri
     X(108, 9, 12, 3, 32)        \
     X(128, 8, 16, 8, 16)        \
     X(144, 12, 12, 12, 8)       \
-    X(192, 12, 16, 4, 16)       \
+    X(192, 8, 24, 8, 16)        \
     X(216, 12, 18, 6, 16)       \
     X(256, 16, 16, 16, 8)       \
     X(288, 12, 24, 12, 8)       \

@@ -484,10 +484,13 @@ static void build_tasks(Plan &p) {
     }
 }
 
+static std::atomic<long long> g_slab_default{0};  // 0: 8 GiB
+
 static long long slab_budget_bytes() {
     const char *e = getenv("FBS_SLAB_MB");
     if (e && atoll(e) > 0) return atoll(e) << 20;
-    return 8LL << 30;
+    const long long d = g_slab_default.load();
+    return d > 0 ? d : 8LL << 30;
 }
 
 // ---------------------------------------------------------------- levels
@@ -1950,6 +1953,15 @@ fbs_status fbs_set_device_budget(int64_t bytes) {
 }
 
 int64_t fbs_device_bytes_in_use(void) { return g_in_use.load(); }
+
+fbs_status fbs_set_slab_budget(int64_t bytes) {
+    if (bytes < 0) {
+        set_error("slab budget must be >= 0");
+        return FBS_ERR_ARG;
+    }
+    g_slab_default.store(bytes);
+    return FBS_OK;
+}
 
 fbs_status fbs_plan_kernel_times(fbs_plan *plan, double *ms, int64_t *launches, int reset) {
     if (!plan) return FBS_ERR_ARG;

@@ -34,7 +34,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-from . import FbsError, Plan
+from . import FbsError, Plan, fbs_set_slab_budget
 
 FBS_ERR_ARG = -1
 
@@ -89,14 +89,20 @@ class EstimatorServer:
     slots: concurrent requests in flight (one CUDA stream each).
     build_async: build plans on a builder thread (default) instead of inline.
     count_cache_dir: directory for the plan-time counts (optional).
+    slab_bytes: shell-field slab buffer of the server's plans (smaller slabs
+    keep more plans resident); set process-wide while the server is open.
     """
 
     NEVER = "never"  # _plan_for: the request cannot fit even with every idle plan evicted
 
+    FRESH_S = 5.0  # a new plan is not evicted before its first use (or this long)
+
     def __init__(self, hbm_budget: int = 120 << 30, slots: int = 4, device: int = 0,
-                 build_async: bool = True, count_cache_dir: Optional[str] = None):
+                 build_async: bool = True, count_cache_dir: Optional[str] = None, slab_bytes: int = 1 << 30):
         import torch
         self.torch = torch
+        self.slab_bytes = int(slab_bytes)
+        fbs_set_slab_budget(self.slab_bytes)
         self.dev = torch.device("cuda", device)
         self.budget = int(hbm_budget)
         self.slots = [_Slot(torch, self.dev) for _ in range(slots)]
@@ -119,7 +125,9 @@ class EstimatorServer:
         return (req.field.shape[0], float(req.L), tuple(float(e) for e in req.edges), req.precision)
 
     def _evict_for(self, need: int) -> bool:
-        idle = [(e["last"], k, e) for k, lst in self.plans.items() for e in lst if not e["busy"]]
+        now = time.perf_counter()
+        idle = [(e["last"], k, e) for k, lst in self.plans.items() for e in lst
+                if not e["busy"] and e.get("fresh_until", 0.0) <= now]
         idle.sort(key=lambda t: t[0])
         while self.held + need > self.budget and idle:
             _, k, e = idle.pop(0)
@@ -169,7 +177,8 @@ class EstimatorServer:
         self.plan_creations += 1
         self.plans_from_cache += int(from_cache)
         e = {"plan": plan, "bytes": plan.device_bytes + field_bytes, "busy": False,
-             "last": time.perf_counter(), "dfield": None}
+             "last": time.perf_counter(), "dfield": None,
+             "fresh_until": time.perf_counter() + self.FRESH_S}  # kept for the request it was built for
         self.held += e["bytes"] - reserved
         self.plans[key].append(e)
         return e
@@ -200,11 +209,17 @@ class EstimatorServer:
         if key in self._failed:
             return self.NEVER
         N = req.field.shape[0]
-        need = plan_bytes_estimate(N, len(req.edges) - 1) + 2 * req.field.nbytes
+        if self._pool is not None and self._building:
+            return None  # one build at a time: the next starts when this one is done
+        need = plan_bytes_estimate(N, len(req.edges) - 1, self.slab_bytes) + 2 * req.field.nbytes
         if need > self.budget:
             return self.NEVER
         if not self._evict_for(need):
-            busy = any(e["busy"] for lst in self.plans.values() for e in lst) or bool(self._building)
+            # busy plans, plans kept for their first request and builds in
+            # flight free up later: wait; otherwise it can never fit
+            now = time.perf_counter()
+            busy = any(e["busy"] or e.get("fresh_until", 0.0) > now for lst in self.plans.values() for e in lst) \
+                or bool(self._building)
             return None if busy else self.NEVER
         if self._pool is not None:
             self.held += need  # reserved until the plan exists
@@ -229,6 +244,7 @@ class EstimatorServer:
         plan = entry["plan"]
         N = req.field.shape[0]
         entry["busy"] = True
+        entry["fresh_until"] = 0.0
         with torch.cuda.stream(slot.stream):
             if entry["dfield"] is None or entry["dfield"].shape[0] != N:
                 entry["dfield"] = torch.empty((N, N, N), dtype=torch.float32, device=self.dev)
@@ -345,6 +361,7 @@ class EstimatorServer:
                 e["plan"].close()
         self.plans.clear()
         self.held = 0
+        fbs_set_slab_budget(0)  # plans created after the server get the default slab again
 
 
 def latency_percentiles(results: Sequence[Result]) -> Dict[str, float]:

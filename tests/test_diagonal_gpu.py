@@ -54,7 +54,8 @@ def test_diagonal_trispectrum_matches_oracle(N, L, kind, nb, nd, precision):
     assert g.sum() >= 10
     assert r[g].max() < 1e-4
     V, npix = L ** 3, float(N) ** 3
-    assert np.all(err_rest[rest] <= 1e-4 * 1e-3 * V ** 3 / npix ** 4)
+    # elsewhere |num_D - ref| <= 1e-6 of the cancellation-free scale (FP32 pair spectra)
+    assert np.all(err_rest[rest] <= 1e-6 * V ** 3 / npix ** 4)
 
 
 def test_diagonal_trispectrum_on_levels(monkeypatch):

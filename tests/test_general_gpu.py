@@ -66,7 +66,7 @@ def test_general_plan_matches_oracle(shape, Ls, kind, seed):
 
 def test_general_plan_rejects_wrapped_bins_unless_allowed():
     shape, Ls = (16, 16, 32), (10.0, 10.0, 10.0)
-    edges = [0.5, 2.0, 4.0, 2 * math.pi * 0.3 * 16 / 10.0]  # past N_x k_f / 4 along x
+    edges = [0.5, 1.0, 2.0, 3.0]  # past N_x k_f,x / 4 = 2.51 along x
     with pytest.raises(fbs.FbsError):
         fbs.GeneralPlan(shape, Ls, edges)
     with fbs.GeneralPlan(shape, Ls, edges, allow_aliased=True) as plan:

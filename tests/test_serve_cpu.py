@@ -43,7 +43,8 @@ def _server(budget, monkeypatch, pool=None):
     srv.budget, srv.held, srv.plan_creations, srv.plans_from_cache = budget, 0, 0, 0
     srv.plans = collections.defaultdict(list)
     srv.slots, srv._cancelled = [], set()
-    srv.counts_cache, srv.count_cache_dir = {}, None
+    srv.counts_cache, srv.count_cache_dir, srv.slab_bytes = {}, None, 1 << 30
+    srv.FRESH_S = 0.0  # new plans evictable at once (the pin has its own test)
     srv._building, srv._pool, srv._build_stream, srv._failed = {}, pool, None, {}
     FakePlan.closed, FakePlan.counts_seen, FakePlan.gate = [], [], None
     return srv
@@ -184,3 +185,19 @@ def test_deadline_refuses_requests_not_yet_admitted(monkeypatch):
     res = srv.run(reqs, realtime=True, deadline_s=0.05)
     errs = {r.rid: r.error for r in res}
     assert served == [1] and errs == {2: "deadline"}  # the stand-in submit leaves no result for 1
+
+
+def test_new_plans_are_kept_for_their_request(monkeypatch):
+    """A plan built for a waiting request is not evicted for another request's
+    plan before its first use (no build-evict cycles under a tight budget)."""
+    f8 = 2 * 8 ** 3 * 4
+    srv = _server(8000 + f8, monkeypatch)
+    srv.FRESH_S = 60.0
+    a = srv._plan_for(_req(1, 8), "s1")
+    assert a is not None
+    # a second key needs the same room: it must wait, the fresh plan stays
+    assert srv._plan_for(_req(2, 8, nb=5), "s2") is None  # waits, is not refused
+    assert FakePlan.closed == []
+    a["fresh_until"] = 0.0  # used once: evictable again
+    b = srv._plan_for(_req(2, 8, nb=5), "s2")
+    assert b is not None and FakePlan.closed == [8]
