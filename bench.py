@@ -135,7 +135,7 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-CPU_SAMPLE_M1 = 192  # m1 modes of the oracle's timed sample (both CPU legs)
+CPU_SAMPLE_M1 = 1536  # m1 modes of the oracle's timed sample (about 15 s on 16 Grace cores at 512^3)
 
 
 def cpu_baseline(args, n_sample=CPU_SAMPLE_M1):
@@ -180,8 +180,10 @@ def run_reference(args, ntrip_hint=None):
     import fields  # noqa: F401
     times = []
     info = None
-    # the same fixed sample every step (the cpu_baseline leg times it too)
-    n_sample = max(16, min(CPU_SAMPLE_M1, int(CPU_SAMPLE_M1 * 13 / max(1, args.steps + args.warmup))))
+    # a fixed strided sample each step, sized so the whole run takes about a
+    # minute of sampling (a quarter of the cpu_baseline leg's sample at the
+    # default 13 steps)
+    n_sample = max(16, min(CPU_SAMPLE_M1, int(CPU_SAMPLE_M1 * 13 / 4 / max(1, args.steps + args.warmup))))
     for i in range(args.warmup + args.steps):
         t_full, info = cpu_baseline(args, n_sample=n_sample)
         if i >= args.warmup:
