@@ -371,6 +371,7 @@ def main():
                                                 precision_T=args.precision, parallelism="replicas%d" % world),
             "roofline": roof, "roofline_fft": roof_fft, "clocks": clocks, "gpu_launches": int(launches),
             "levels": {"B": [l["M"] for l in planB.levels], "T": [l["M"] for l in planT.levels]},
+            "levels_detail": {"B": planB.levels, "T": planT.levels},
             "plan_s": plan_s, "count_margin": [planB.count_margin, planT.count_margin],
             "quad_counts_exact": planT.quad_counts_exact,
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in allk.items() if v[1]}}
@@ -693,16 +694,11 @@ def _closed_triplets_oracle(N, thr):
 
 
 # DRAM bytes of one launch (dram__bytes_read.sum + dram__bytes_write.sum from
-# one ncu capture of the current kernel) per algorithmic byte of the launch
-# (every bin's shell-field value of the slab read once); scaled to the bench's
-# launch by its points.  Source: the profile summary named beside the value.
+# one ncu capture of the current kernel build) per algorithmic byte of the
+# launch (every bin's shell-field value of the slab read once); scaled to the
+# bench's launch by its points.  A kernel class without a capture of its
+# current build has no entry (the roofline's traffic is then null).
 NCU_TRAFFIC_RATIO = {
-    "contract_tc": ((916.344576e6 + 3.036160e6) / (64 * 3538944 * 4.0),
-                    "ncu DRAM bytes of the bispectrum pass at 256^3, 64 log bins, 3.54M points "
-                    "(the contraction traffic capture), scaled by points"),
-    "contract_quad_tc": ((540.110080e6 + 0.122624e6) / (16 * 8388608 * 4.0),
-                         "ncu DRAM bytes of the fused triplet+quadruplet pass at 256^3, 16 log bins, "
-                         "8.39M points (the contraction traffic capture), scaled by points"),
 }
 
 
