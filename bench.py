@@ -266,6 +266,10 @@ def main():
     _phase("plans")
     planB = fbs.Plan(N, L_BOX, eB, precision=args.precision, timing=True, stream=stream)
     planT = fbs.Plan(N, L_BOX, eT, precision=args.precision, trispectrum=True, timing=True, stream=stream)
+    # one upload and one forward transform of the field serve both plans
+    # (fbs_plan_follow: the trispectrum plan reads the bispectrum plan's
+    # spectrum on the shared stream)
+    planT.follow(planB)
     plan_s = time.perf_counter() - t0
     B = torch.empty(planB.ntrip, dtype=torch.float64, device=dev)
     P = torch.empty(planB.nbins, dtype=torch.float64, device=dev)
@@ -275,7 +279,7 @@ def main():
 
     def step(fld, outs):
         planB.bispectrum(fld, outs[0], outs[1])
-        planT.trispectrum(fld, outs[2], outs[3], outs[4])
+        planT.trispectrum(None, outs[2], outs[3], outs[4])
 
     outs_dev = (B, P, T, B16, P16)
     _phase("warmup and timed steps")
@@ -306,9 +310,10 @@ def main():
 
     # e2e: pinned host field in, pinned host outputs back, through the C ABI,
     # as a streaming caller would run it: both plans' calls of step k are
-    # enqueued (each plan copies the field on its own copy stream), then the
-    # host waits for the results of step k-1 (two output sets), so the field
-    # copies of step k run under the kernels of step k-1.  Every step copies
+    # enqueued (the bispectrum plan copies the field on its copy stream, the
+    # trispectrum plan follows its spectrum), then the host waits for the
+    # results of step k-1 (two output sets), so the field copy of step k runs
+    # under the kernels of step k-1.  Every step copies
     # its field in and its results out; the loop ends with every result on
     # the host.
     e2e = None
@@ -340,7 +345,7 @@ def main():
         e2e_s = (time.perf_counter() - t0) / args.steps
         planB.kernel_times(reset=True)
         planT.kernel_times(reset=True)
-        h2d = 2 * f32.nbytes
+        h2d = f32.nbytes  # one upload per step for both plans
         d2h = 8 * (planB.ntrip + planB.nbins + planT.nquad + planT.ntrip + planT.nbins)
         e2e = {"value": None, "unit": "triangle-bins/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "_s": e2e_s,
@@ -754,10 +759,11 @@ def shell_field_bytes_per_step(plan):
     return sum(4.0 * nb * float(M) ** 3 for M, nb, _, _ in _level_sets(plan))
 
 
-def fft_stage_bytes_per_step(plan, N):
+def fft_stage_bytes_per_step(plan, N, forward=True):
     """Algorithmic HBM bytes of one evaluation's FFT stage (forward R2C of the
-    field, the pruned spectrum box written, every shell's modes read once per
-    level that evaluates it, every shell field written)."""
+    field and the pruned spectrum box written, unless the plan follows
+    another plan's spectrum; every shell's modes read once per level that
+    evaluates it; every shell field written)."""
     thr = np.asarray(plan.thresholds)
     R = int(np.floor(np.sqrt(max(int(thr[-1]) - 1, 0))))
     box = (2 * R + 1) ** 2 * (R + 1) * 8.0
@@ -765,7 +771,7 @@ def fft_stage_bytes_per_step(plan, N):
     for M, nb, tr, qd in _level_sets(plan):  # the modes of every bin a level's items use
         bins = set(np.unique(tr).tolist()) | set(np.unique(qd).tolist())
         shell_read += 8.0 * sum(int(plan.shell[b]) for b in bins)
-    return 4.0 * N ** 3 + box + shell_read + shell_field_bytes_per_step(plan)
+    return (4.0 * N ** 3 + box if forward else 0.0) + shell_read + shell_field_bytes_per_step(plan)
 
 
 def roofline(top, planB, planT, N, pk, pk_src, clocks, steps):
@@ -801,7 +807,8 @@ def roofline(top, planB, planT, N, pk, pk_src, clocks, steps):
                     "traffic_source": ratio[1] if ratio else None,
                     "peak_source": "bf16_tflops_sustained (%s)" % pk_src})
     else:
-        byts = shell_field_bytes_per_step(plan) if cls == "inv_z" else fft_stage_bytes_per_step(plan, N)
+        byts = shell_field_bytes_per_step(plan) if cls == "inv_z" else \
+            fft_stage_bytes_per_step(plan, N, forward=getattr(plan, "leader", None) is None)
         ach = byts / (ms_step * 1e-3) / 1e9
         out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                     "frac": ach / hbm, "traffic": None, "peak_source": "hbm_gbs (%s)" % pk_src})
@@ -816,7 +823,8 @@ def roofline_fft(kB, kT, planB, planT, N, pk, pk_src, steps):
     plans) against HBM: algorithmic bytes / summed FFT kernel time."""
     hbm = _find(pk, "hbm_gbs", "hbm_GBs", "copy_gbs") or 6800.0
     ms = sum(kB.get(c, (0, 0))[0] + kT.get(c, (0, 0))[0] for c in FFT_CLASSES) / steps
-    byts = fft_stage_bytes_per_step(planB, N) + fft_stage_bytes_per_step(planT, N)
+    byts = fft_stage_bytes_per_step(planB, N, forward=getattr(planB, "leader", None) is None) + \
+        fft_stage_bytes_per_step(planT, N, forward=getattr(planT, "leader", None) is None)
     ach = byts / (ms * 1e-3) / 1e9
     zb = shell_field_bytes_per_step(planB) + shell_field_bytes_per_step(planT)
     zms = (kB.get("inv_z", (0, 0))[0] + kT.get("inv_z", (0, 0))[0]) / steps
@@ -825,7 +833,7 @@ def roofline_fft(kB, kT, planB, planT, N, pk, pk_src, steps):
             "inv_z": {"achieved": zb / (zms * 1e-3) / 1e9, "frac": zb / (zms * 1e-3) / 1e9 / hbm,
                       "bytes_per_step": zb, "ms_per_step": zms},
             "peak_source": "hbm_gbs (%s)" % pk_src,
-            "what": "fwd_z/y/x + inv_x/y/z of both plans; bytes: field read, spectrum box written, "
+            "what": "fwd_z/y/x (once: the trispectrum plan follows the bispectrum plan's spectrum) + inv_x/y/z of both plans; bytes: field read, spectrum box written, "
                     "shell modes read per level, shell fields written"}
 
 

@@ -283,6 +283,23 @@ fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double 
                                      double *P);
 
 /*
+ * fbs_plan_follow -- make `follower` evaluate the spectrum of `leader`'s most
+ * recent evaluation instead of transforming a field of its own: one field
+ * upload and one forward transform serve both plans (a bispectrum plan and a
+ * trispectrum plan of the same field, say).  Requirements (FBS_ERR_ARG /
+ * FBS_ERR_STATE otherwise): the same grid N, a leader spectrum box at least
+ * as large as the follower's (top edge at least as high), the same stream
+ * (the follower's kernels are ordered after the leader's forward transform
+ * and before its next one by the stream), and a leader that does not follow
+ * another plan.  A following plan's evaluation calls take field = NULL
+ * (a non-NULL field is FBS_ERR_STATE) and read the leader's box as the
+ * leader's last call on the stream left it.  The leader must outlive the
+ * follower or be detached first: leader = NULL restores the follower's own
+ * box.  Batched evaluations (fbs_bispectrum_batch) are not affected.
+ */
+fbs_status fbs_plan_follow(fbs_plan *follower, const fbs_plan *leader);
+
+/*
  * Diagonal-resolved trispectrum (FBS_FLAG_TRISPECTRUM plans).  Every closed
  * quadruple (m1, m2, m3, m4) of quadruplet (a <= b <= c <= d) has the
  * diagonal q = m1 + m2 = -(m3 + m4) of its quadrilateral; the diagonal bins

@@ -82,6 +82,7 @@ _SIGS = [
     ("fbs_plan_sums", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("fbs_trispectrum_connected", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("fbs_plan_set_diagonal", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    ("fbs_plan_follow", ctypes.c_int, [_vp, _vp]),
     ("fbs_plan_num_diagonal_bins", ctypes.c_int, [_vp]),
     ("fbs_plan_diagonal_counts", ctypes.c_int, [_vp, _vp, _vp]),
     ("fbs_trispectrum_diagonal", ctypes.c_int, [_vp, _vp, _vp]),
@@ -219,7 +220,9 @@ def fbs_triple_sums_noalloc(fields_ptr, nfields, bin_stride, npts, abc_ptr, ntri
 
 # ---------------------------------------------------------------- convenience
 def _ptr(a):
-    """(pointer, keepalive) for a torch tensor or NumPy array."""
+    """(pointer, keepalive) for a torch tensor or NumPy array (NULL for None)."""
+    if a is None:
+        return 0, None
     if isinstance(a, np.ndarray):
         return a.ctypes.data, a
     return a.data_ptr(), a
@@ -329,11 +332,20 @@ class Plan:
         if isinstance(like, np.ndarray):
             return np.empty(n, dtype=np.float64)
         import torch
-        return torch.empty(n, dtype=torch.float64, device=like.device)
+        dev = like.device if like is not None else torch.device("cuda", torch.cuda.current_device())
+        return torch.empty(n, dtype=torch.float64, device=dev)
+
+    def follow(self, leader):
+        """Evaluate ``leader``'s spectrum (its last evaluation on the shared
+        stream) instead of a field of this plan's own: pass ``None`` as the
+        field afterwards (see fbs_plan_follow).  ``leader=None`` detaches."""
+        _check(lib().fbs_plan_follow(_vp(self._h), _vp(leader._h if leader is not None else 0)))
+        self.leader = leader
 
     def bispectrum(self, field, B=None, P=None):
         """B[ntrip], P[nbins] for an N^3 float32 field (torch CUDA tensor or
-        NumPy array).  Outputs live where the field lives unless given."""
+        NumPy array; None for a following plan).  Outputs live where the
+        field lives unless given (on the current CUDA device for None)."""
         self._check_field(field)
         B = self._outputs(field, self.ntrip) if B is None else B
         P = self._outputs(field, self.nbins) if P is None else P
@@ -426,6 +438,10 @@ class Plan:
         return TD.reshape(self.nquad, -1) if n else TD
 
     def _check_field(self, f):
+        if f is None:
+            if getattr(self, "leader", None) is None:
+                raise ValueError("field is None but the plan follows no other plan")
+            return
         n = self.N
         if tuple(f.shape) != (n, n, n):
             raise ValueError("field must have shape (%d, %d, %d)" % (n, n, n))

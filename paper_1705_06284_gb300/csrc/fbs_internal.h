@@ -263,6 +263,11 @@ struct Plan {
     void *tc = nullptr;           // opaque state of contract_tc.cu
     void *batch = nullptr;        // root only: buffers of batched evaluations (plan.cpp)
     void *diag = nullptr;         // root only: diagonal-resolved trispectrum tables (plan.cpp)
+    // root only: evaluate the spectrum box of another plan (fbs_plan_follow);
+    // the plan's own box and its geometry are kept to detach
+    const Plan *leader = nullptr;
+    float2 *own_box = nullptr;
+    BoxGeom own_boxgeom{};
 
     // timing
     std::vector<cudaEvent_t> evs;  // 2 per pending launch, created once and reused

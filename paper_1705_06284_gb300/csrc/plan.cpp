@@ -957,13 +957,27 @@ static void release_field(Plan &p, bool staged) {
     p.field_free_recorded = true;
 }
 
-static void run_field(Plan &p, const float *field, bool quads) {
+// The spectrum box of this evaluation: the field's forward transform, or a
+// followed plan's box (field NULL) as its last evaluation on the shared
+// stream left it.
+static void forward_or_follow(Plan &p, const float *field) {
+    if (p.leader) {
+        if (field) throw Failure{FBS_ERR_STATE, "a following plan evaluates its leader's field: pass NULL"};
+        if (p.leader->stream != p.stream)
+            throw Failure{FBS_ERR_STATE, "a following plan must share its leader's stream"};
+        return;
+    }
+    if (!field) throw Failure{FBS_ERR_ARG, "field is NULL"};
     bool staged = false;
     const float *d_in = stage_field(p, field, staged);
-    const bool tc = p.precision != FBS_PREC_FP32;
-    if (tc) FBS_CUDA(cudaMemsetAsync(p.d_errbuf, 0, sizeof(int), p.stream));
     launch_forward(p, d_in, nullptr, 1, p.d_zbuf, p.d_ybuf, p.d_box);
     release_field(p, staged);
+}
+
+static void run_field(Plan &p, const float *field, bool quads) {
+    const bool tc = p.precision != FBS_PREC_FP32;
+    if (tc) FBS_CUDA(cudaMemsetAsync(p.d_errbuf, 0, sizeof(int), p.stream));
+    forward_or_follow(p, field);
     for (Plan *lp : p.levels) {
         Plan &lv = *lp;
         lv.fused_active = quads && tc && tc_fused_usable(lv);
@@ -1271,10 +1285,7 @@ static void set_diagonal(Plan &p, const double *edges, int nd) {
 static void run_diagonal(Plan &p, const float *field) {
     DiagState &ds = *reinterpret_cast<DiagState *>(p.diag);
     const int nd = ds.nd;
-    bool staged = false;
-    const float *d_in = stage_field(p, field, staged);
-    launch_forward(p, d_in, nullptr, 1, p.d_zbuf, p.d_ybuf, p.d_box);
-    release_field(p, staged);
+    forward_or_follow(p, field);
     FBS_CUDA(cudaMemsetAsync(ds.d_num, 0, std::max<size_t>(1, ds.cnt.size()) * sizeof(double), p.stream));
     for (size_t l = 0; l < p.levels.size(); ++l) {
         Plan &lv = *p.levels[l];
@@ -1677,8 +1688,44 @@ fbs_status fbs_plan_set_stream(fbs_plan *plan, void *stream) {
     FBS_GUARD_END
 }
 
+fbs_status fbs_plan_follow(fbs_plan *follower, const fbs_plan *leader) {
+    if (!follower || follower == leader) {
+        set_error("fbs_plan_follow: bad plan");
+        return FBS_ERR_ARG;
+    }
+    FBS_GUARD_BEGIN
+    FBS_CUDA(cudaStreamSynchronize(follower->stream));
+    Plan &f = *follower;
+    if (!f.own_box) {
+        f.own_box = f.d_box;
+        f.own_boxgeom = f.box;
+    }
+    if (!leader) {  // detach: the plan's own box again
+        f.leader = nullptr;
+        f.d_box = f.own_box;
+        f.box = f.own_boxgeom;
+    } else {
+        if (leader->leader) throw Failure{FBS_ERR_ARG, "fbs_plan_follow: the leader follows another plan"};
+        if (leader->N != f.N) throw Failure{FBS_ERR_ARG, "fbs_plan_follow: grids differ"};
+        if (leader->box.R < f.own_boxgeom.R)
+            throw Failure{FBS_ERR_ARG, "fbs_plan_follow: the leader's spectrum box is smaller than the follower's"};
+        if (leader->stream != f.stream) throw Failure{FBS_ERR_STATE, "fbs_plan_follow: the plans' streams differ"};
+        f.leader = leader;
+        f.d_box = leader->d_box;
+        f.box = leader->box;
+    }
+    for (Plan *lv : f.levels) {
+        lv->d_box = f.d_box;
+        lv->box = f.box;
+        lv->boxM = f.box;
+        lv->boxM.N = lv->M;
+    }
+    return FBS_OK;
+    FBS_GUARD_END
+}
+
 fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double *P) {
-    if (!plan || !field) {
+    if (!plan || (!field && !plan->leader)) {
         set_error("plan or field is NULL");
         return FBS_ERR_ARG;
     }
@@ -1697,7 +1744,7 @@ fbs_status fbs_bispectrum(fbs_plan *plan, const float *field, double *B, double 
 }
 
 fbs_status fbs_trispectrum(fbs_plan *plan, const float *field, double *T, double *B, double *P) {
-    if (!plan || !field) {
+    if (!plan || (!field && !plan->leader)) {
         set_error("plan or field is NULL");
         return FBS_ERR_ARG;
     }
@@ -1783,7 +1830,7 @@ fbs_status fbs_plan_diagonal_counts(const fbs_plan *plan, double *counts, uint64
 }
 
 fbs_status fbs_trispectrum_diagonal(fbs_plan *plan, const float *field, double *TD) {
-    if (!plan || !field || !TD) {
+    if (!plan || (!field && !plan->leader) || !TD) {
         set_error("fbs_trispectrum_diagonal: NULL argument");
         return FBS_ERR_ARG;
     }
@@ -1804,7 +1851,7 @@ fbs_status fbs_trispectrum_diagonal(fbs_plan *plan, const float *field, double *
 
 fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double *Tc, double *T, double *B,
                                      double *P) {
-    if (!plan || !field) {
+    if (!plan || (!field && !plan->leader)) {
         set_error("plan or field is NULL");
         return FBS_ERR_ARG;
     }
