@@ -209,7 +209,14 @@ enum {
                             free its tensor memory and return; the evaluation's
                             B and T are then NaN and FBS_ERR_TIMEOUT is
                             reported (see fbs_plan_check).  Meant for testing
-                            that path; any value >= 0 is accepted. */
+                            that path; any value >= 0 is accepted. */,
+    FBS_OPT_TC_MERGE = 7      /* BF16x3 products of the tensor-core contraction:
+                            0 (default): where the doubled accumulators fit in
+                            tensor memory, the hi and lo rows of the inner
+                            operand go into one MMA (N = 2 Npad: hi*hi and
+                            hi*lo side by side) and lo*hi into a second, two
+                            MMAs per K step instead of three; 1: always three.
+                            The sums agree within the precision's rounding. */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */

@@ -43,6 +43,7 @@ FBS_OPT_TC_CHUNK = 3
 FBS_OPT_TC_PAIRS = 4
 FBS_OPT_TC_WAIT_LIMIT = 5
 FBS_OPT_SLAB_PLANES = 6
+FBS_OPT_TC_MERGE = 7
 
 _PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
 

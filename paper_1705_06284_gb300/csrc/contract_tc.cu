@@ -336,7 +336,7 @@ __device__ __forceinline__ const float4 *stage_at(const unsigned char *st, int h
 // row's values (a single bin, or the product of two bins) split into BF16
 // hi/lo, stored in the 128-byte-swizzled K-major tile of K-atom j / 8.
 __device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_bytes, const int2 *s_inner, int row,
-                                             int j, unsigned char *bh, unsigned char *bl, int b_tile) {
+                                             int j, unsigned char *bh, unsigned char *bl, int atom_stride) {
     const int2 in = s_inner[row];
     const float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
     const float4 v1 = *stage_at(st, half_bytes, in.x, 2 * j + 1);
@@ -351,7 +351,7 @@ __device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_b
         split2(make_float2(v1.x, v1.y), h[2], l[2]);
         split2(make_float2(v1.z, v1.w), h[3], l[3]);
     }
-    const uint32_t off = (uint32_t)((j >> 3) * b_tile) + sw128_off(row, j & 7);
+    const uint32_t off = (uint32_t)((j >> 3) * atom_stride) + sw128_off(row, j & 7);
     *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4 *>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
@@ -361,12 +361,12 @@ __device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_b
 // inner rows to their lanes, with no division in the loop.
 template <int W, int KA>
 __device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes, const int2 *s_inner, int ninner,
-                                        int wb, int lane, unsigned char *bh, unsigned char *bl, int b_tile) {
+                                        int wb, int lane, unsigned char *bh, unsigned char *bl, int atom_stride) {
     constexpr int C = 8 * KA;
     static_assert(W % C == 0, "operand-B warps must cover the eight-point groups evenly");
     const int j = wb % C;
     for (int row = lane + 32 * (wb / C); row < ninner; row += 32 * (W / C))
-        build_b_unit(st, half_bytes, s_inner, row, j, bh, bl, b_tile);
+        build_b_unit(st, half_bytes, s_inner, row, j, bh, bl, atom_stride);
 }
 
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
-                       int *__restrict__ err, long long wait_limit, int part_rows) {
+                       int *__restrict__ err, long long wait_limit, int part_rows, int merged) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
     static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
@@ -415,8 +415,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uintptr_t base = (reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023;
     unsigned char *sm = reinterpret_cast<unsigned char *>(base);
     const int b_tile = Npad * 128;      // one K-atom of operand B (hi or lo)
-    const int b_stage = KA * b_tile;    // one B stage (hi or lo), atoms consecutive
-    unsigned char *const Bh0 = sm, *const Bl0 = sm + 2 * b_stage;
+    // one B stage holds, per K-atom, the hi rows then the lo rows (one tile of
+    // 2 Npad rows: a single MMA with N = 2 Npad multiplies both halves)
+    const int b_stage = KA * b_tile;    // hi (or lo) part of one B stage
+    const int b_atom2 = 2 * b_tile;     // one K-atom: hi tile, then lo tile
+    unsigned char *const Bh0 = sm;      // stage sb at Bh0 + 2 sb b_stage
     const int half_bytes = ((nbins + 7) & ~7) * 128;  // one 32-point TMA box of all bins
     const int stage_bytes = 2 * KA * half_bytes;
     unsigned char *const stg = sm + 4 * b_stage;
@@ -508,6 +511,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ================= MMA issuer (one thread) =================
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(128, Npad);
+            const uint32_t idesc2 = idesc_bf16(128, 2 * Npad);  // hi and lo rows of B together
             Ring<NST> ra;
             Ring<2> rb;
             long long nfl = 0;
@@ -518,9 +522,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (long long ci = c0; ci < c1; ++ci) {
                 const int sb = rb.slot;
                 const bool okb = role_wait(&bars.bfull[sb], rb.phase, abortp, err, 11, wait_limit);
-                const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + sb * b_stage));
-                const uint64_t dbl = sdesc_sw128(smem_u32(Bl0 + sb * b_stage));
-                const uint64_t datom = (uint64_t)((unsigned)b_tile >> 4);  // next K-atom's tile
+                const uint64_t dbh = sdesc_sw128(smem_u32(Bh0 + 2 * sb * b_stage));
+                const uint64_t dbl = dbh + (uint64_t)((unsigned)b_tile >> 4);  // the atom's lo rows
+                const uint64_t datom = (uint64_t)((unsigned)b_atom2 >> 4);     // next K-atom
                 for (int lt = 0; lt < ntl; ++lt) {
                     const int as = ra.slot;
                     const bool oka = role_wait(&bars.full[as], ra.phase, abortp, err, 12, wait_limit);
@@ -529,21 +533,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const uint32_t d = tmem + (uint32_t)(lt * tstride);
                         const uint32_t ah = tmem + (uint32_t)(acc_cols + as * ACOLS);
                         const uint32_t al = ah + 32u * KA;
-                        // k-step k: A columns 8k; B atom k/4 (tile start + b_tile),
-                        // start address field + 2 (k mod 4) within the atom (32 bytes)
-                        if (fresh) mma_ts<false>(d, ah, dbh, idesc);
-                        else mma_ts<true>(d, ah, dbh, idesc);
-                        if (x3) {
-                            mma_ts<true>(d, ah, dbl, idesc);
+                        // k-step k: A columns 8k; B atom k/4 (tile start + 2 b_tile),
+                        // start address field + 2 (k mod 4) within the atom (32 bytes).
+                        // merged: A_hi x [B_hi; B_lo] (N = 2 Npad) accumulates hi*hi in
+                        // columns [0, Npad) and hi*lo in [Npad, 2 Npad); A_lo x B_hi adds
+                        // lo*hi to the first half: two MMAs per k-step instead of three.
+                        if (merged) {
+                            if (fresh) mma_ts<false>(d, ah, dbh, idesc2);
+                            else mma_ts<true>(d, ah, dbh, idesc2);
                             mma_ts<true>(d, al, dbh, idesc);
-                        }
 #pragma unroll
-                        for (int k = 1; k < 4 * KA; ++k) {
-                            const uint64_t bo = datom * (uint64_t)(k >> 2) + 2u * (k & 3);
-                            mma_ts<true>(d, ah + 8u * k, dbh + bo, idesc);
-                            if (x3) {
-                                mma_ts<true>(d, ah + 8u * k, dbl + bo, idesc);
+                            for (int k = 1; k < 4 * KA; ++k) {
+                                const uint64_t bo = datom * (uint64_t)(k >> 2) + 2u * (k & 3);
+                                mma_ts<true>(d, ah + 8u * k, dbh + bo, idesc2);
                                 mma_ts<true>(d, al + 8u * k, dbh + bo, idesc);
+                            }
+                        } else {
+                            if (fresh) mma_ts<false>(d, ah, dbh, idesc);
+                            else mma_ts<true>(d, ah, dbh, idesc);
+                            if (x3) {
+                                mma_ts<true>(d, ah, dbl, idesc);
+                                mma_ts<true>(d, al, dbh, idesc);
+                            }
+#pragma unroll
+                            for (int k = 1; k < 4 * KA; ++k) {
+                                const uint64_t bo = datom * (uint64_t)(k >> 2) + 2u * (k & 3);
+                                mma_ts<true>(d, ah + 8u * k, dbh + bo, idesc);
+                                if (x3) {
+                                    mma_ts<true>(d, ah + 8u * k, dbl + bo, idesc);
+                                    mma_ts<true>(d, al + 8u * k, dbh + bo, idesc);
+                                }
                             }
                         }
                     }
@@ -578,7 +597,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 25, wait_limit);
             // (8 KA when BW = 0 only keeps the never-taken instantiation well formed)
             build_b<(BW > 0 ? BW : 8 * KA), KA>(st, half_bytes, s_inner, ninner, warp - AW, lane,
-                                                 Bh0 + sb * b_stage, Bl0 + sb * b_stage, b_tile);
+                                                 Bh0 + 2 * sb * b_stage, Bh0 + 2 * sb * b_stage + b_tile, b_atom2);
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.bfull[sb]);
@@ -604,8 +623,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
                 const int sb = rb.slot;
                 if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21, wait_limit);
-                build_b<AW, KA>(st, half_bytes, s_inner, ninner, warp, lane, Bh0 + sb * b_stage, Bl0 + sb * b_stage,
-                                b_tile);
+                build_b<AW, KA>(st, half_bytes, s_inner, ninner, warp, lane, Bh0 + 2 * sb * b_stage,
+                                Bh0 + 2 * sb * b_stage + b_tile, b_atom2);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bars.bfull[sb]);
@@ -672,6 +691,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (AW / 4)) {
                             float v[8];
                             tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
+                            if (merged) {  // hi*lo sits Npad columns further: one FP32 sum per item
+                                float u[8];
+                                tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + Npad + c8), u);
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) v[i] = __fadd_rn(v[i], u[i]);
+                            }
                             if (!valid) continue;
                             const int wsel = c8 >> 5;
                             const unsigned wm = __ldg(&pp->mask[wsel]);
@@ -1383,7 +1408,21 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     // 128-point chunks (half the hand-offs per point) when two 128-column A
     // stages fit beside the accumulators in tensor memory and shared memory
     // holds the doubled stages; 64-point chunks otherwise
-    const int acc_cols_max = (((job.maxtiles * tile_stride(job.Npad)) + 31) / 32) * 32;
+    // BF16x3 with the hi and lo rows of B in one MMA (N = 2 Npad; two MMAs per
+    // k-step instead of three) when the doubled accumulators still leave room
+    // for two 128-column A stages in tensor memory
+    const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
+    int tstr = tile_stride(job.Npad);
+    int acc_cols_max = (((job.maxtiles * tstr) + 31) / 32) * 32;
+    int merged = 0;
+    if (x3 && p.tc_merge != 1 && 2 * job.Npad <= 256) {
+        const int acc2 = (((job.maxtiles * tile_stride(2 * job.Npad)) + 31) / 32) * 32;
+        if (acc2 + 2 * 2 * kAStageCols <= 512) {
+            merged = 1;
+            tstr = tile_stride(2 * job.Npad);
+            acc_cols_max = acc2;
+        }
+    }
     const bool fits2 = acc_cols_max + 2 * 2 * kAStageCols <= 512 &&
                        tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 2, 2) <= 220 * 1024;
     const int ka = (fits2 && p.tc_chunk != 1 && aw == 16) ? 2 : 1;
@@ -1396,16 +1435,15 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins, nf * p.nbins);
     KTimer tm(p, kclass);
     dim3 grid(G, ngrp, nf);
-    const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
 #define FBS_TC_LAUNCH(A, S, W, K)                                                                     \
     if (nst == A && nstg == S && aw == W && ka == K) {                                                \
         launched = true;                                                                              \
         FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S, W, K>,                                 \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));          \
         contract_tc_kernel<A, S, W, K><<<grid, kTcThreads, sm, p.stream>>>(                          \
-            fmap, npts, p.nbins, job.Npad, tile_stride(job.Npad), job.ninner, job.d_inner, job.d_pairs, \
-            job.npairs, job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err,         \
-            tc_wait_limit(p), p.part_blocks);                                                         \
+            fmap, npts, p.nbins, job.Npad, tstr, job.ninner, job.d_inner, job.d_pairs, job.npairs,      \
+            job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err, tc_wait_limit(p),     \
+            p.part_blocks, merged);                                                                   \
     }
     bool launched = false;
     FBS_TC_LAUNCH(2, 2, 16, 1)

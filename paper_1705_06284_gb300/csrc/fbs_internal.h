@@ -188,6 +188,7 @@ struct Plan {
     int tc_roles = 0;            // FBS_OPT_TC_ROLES: 0 auto, 1 = 16 A warps, 2 = 8 A + 8 B warps
     int tc_chunk = 0;            // FBS_OPT_TC_CHUNK: 0 auto, 1 = 64-point chunks, 2 = 128 where they fit
     int tc_pairs = 0;            // FBS_OPT_TC_PAIRS: 0 greedy pair cover, 1 = pairs (b, c)
+    int tc_merge = 0;            // FBS_OPT_TC_MERGE: 0 hi and lo rows of B in one MMA where it fits, 1 = never
     long long tc_wait_limit = 0; // FBS_OPT_TC_WAIT_LIMIT: hand-off wait limit in cycles (0 = default)
     cudaStream_t stream = nullptr;
     double create_ms = 0;

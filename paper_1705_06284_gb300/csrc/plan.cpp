@@ -608,6 +608,7 @@ static Plan *new_level(Plan &root, int M) {
     lv->tc_roles = root.tc_roles;
     lv->tc_chunk = root.tc_chunk;
     lv->tc_pairs = root.tc_pairs;
+    lv->tc_merge = root.tc_merge;
     lv->tc_wait_limit = root.tc_wait_limit;
     lv->d_box = root.d_box;
     root.levels.push_back(lv);
@@ -1656,6 +1657,10 @@ static bool set_plan_option(Plan *plan, int option, int value) {
     }
     if (option == FBS_OPT_TC_CHUNK && value >= 0 && value <= 2) {
         plan->tc_chunk = value;
+        return true;
+    }
+    if (option == FBS_OPT_TC_MERGE && (value == 0 || value == 1)) {
+        plan->tc_merge = value;
         return true;
     }
     if (option == FBS_OPT_TC_PAIRS && (value == 0 || value == 1)) {

@@ -228,3 +228,35 @@ def test_pair_cover_trispectrum_matches_oracle():
             out[pairs] = T.cpu().numpy()
             check_trispectrum(plan, out[pairs], f32, L, edges, 2e-4)
             check_bispectrum(plan, B.cpu().numpy(), P.cpu().numpy(), f32, L, edges, "bf16x3", ref=ref)
+
+
+@pytest.mark.parametrize("quads,N,nb", [(False, 64, 16), (True, 48, 10), (True, 96, 8)])
+def test_merged_hi_lo_products_match_oracle(quads, N, nb):
+    """FBS_OPT_TC_MERGE 0 (hi and lo rows of the inner operand in one MMA of
+    N = 2 Npad, lo*hi in a second) and 1 (three MMAs per K step) both meet the
+    BF16x3 gate against the oracle; the 96^3 case runs several accumulator
+    flushes per CTA."""
+    import torch
+    L = float(N)
+    edges = fields.linear_edges(N, L, nb)
+    f32 = _field("quadratic", N, 34).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    out = {}
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        for merge in (0, 1):
+            plan.set_option(fbs.FBS_OPT_TC_MERGE, merge)
+            if quads:
+                T, B, P = plan.trispectrum(f)
+            else:
+                B, P = plan.bispectrum(f)
+                T = None
+            torch.cuda.synchronize()
+            plan.check()
+            out[merge] = (B.cpu().numpy(), P.cpu().numpy(), None if T is None else T.cpu().numpy())
+            if N <= 64:
+                check_bispectrum(plan, out[merge][0], out[merge][1], f32, L, edges, "bf16x3")
+            if quads:
+                check_trispectrum(plan, out[merge][2], f32, L, edges, 2e-4)
+        # the two assignments of the products round differently, nothing more
+        big = np.abs(out[1][0]) > 1e-3 * np.abs(out[1][0]).max()
+        assert np.all(np.abs(out[0][0] - out[1][0])[big] <= 2e-4 * np.abs(out[1][0][big]) + 1e-6 * np.abs(out[1][0]).max())
