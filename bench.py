@@ -382,6 +382,7 @@ def main():
             "roofline": roof, "roofline_fft": roof_fft, "clocks": clocks, "gpu_launches": int(launches),
             "levels": {"B": [l["M"] for l in planB.levels], "T": [l["M"] for l in planT.levels]},
             "levels_detail": {"B": planB.levels, "T": planT.levels},
+            "tc_jobs": {"B": planB.tc_info(), "T": planT.tc_info()},
             "plan_s": plan_s, "count_margin": [planB.count_margin, planT.count_margin],
             "quad_counts_exact": planT.quad_counts_exact,
             "kernel_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in allk.items() if v[1]}}

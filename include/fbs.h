@@ -290,6 +290,17 @@ fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double 
                                      double *P);
 
 /*
+ * fbs_plan_tc_info -- diagnostics of level `level`'s tensor-core job `which`
+ * (0: triplets, 1: quadruplets, 2: the fused triplet + quadruplet pass),
+ * available after an evaluation has built it: info[7] = {built, usable, outer
+ * 128-row tiles of the largest CTA group, inner rows, inner rows padded (N of
+ * the MMA), 1 when the latest launch put the hi and lo rows in one MMA
+ * (FBS_OPT_TC_MERGE) else 0 (-1 before any launch), 64-point K-atoms per
+ * pipeline step of that launch}.  FBS_ERR_ARG for a bad level or job.
+ */
+fbs_status fbs_plan_tc_info(const fbs_plan *plan, int level, int which, int32_t *info);
+
+/*
  * fbs_plan_follow -- make `follower` evaluate the spectrum of `leader`'s most
  * recent evaluation instead of transforming a field of its own: one field
  * upload and one forward transform serve both plans (a bispectrum plan and a

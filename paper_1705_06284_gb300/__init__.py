@@ -84,6 +84,7 @@ _SIGS = [
     ("fbs_trispectrum_connected", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     ("fbs_plan_set_diagonal", ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     ("fbs_plan_follow", ctypes.c_int, [_vp, _vp]),
+    ("fbs_plan_tc_info", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
     ("fbs_plan_num_diagonal_bins", ctypes.c_int, [_vp]),
     ("fbs_plan_diagonal_counts", ctypes.c_int, [_vp, _vp, _vp]),
     ("fbs_trispectrum_diagonal", ctypes.c_int, [_vp, _vp, _vp]),
@@ -335,6 +336,20 @@ class Plan:
         import torch
         dev = like.device if like is not None else torch.device("cuda", torch.cuda.current_device())
         return torch.empty(n, dtype=torch.float64, device=dev)
+
+    def tc_info(self):
+        """Tensor-core job shapes per level (after an evaluation): a list of
+        {job: dict(tiles, inner, Npad, merged, ka)} for the built jobs."""
+        out = []
+        for lvl in range(len(self.levels)):
+            d = {}
+            for which, name in enumerate(("triplets", "quadruplets", "fused")):
+                a = (ctypes.c_int32 * 7)()
+                _check(lib().fbs_plan_tc_info(_vp(self._h), lvl, which, ctypes.cast(a, _vp)))
+                if a[0] and a[1]:
+                    d[name] = {"tiles": a[2], "inner": a[3], "Npad": a[4], "merged": a[5], "ka": a[6]}
+            out.append(d)
+        return out
 
     def follow(self, leader):
         """Evaluate ``leader``'s spectrum (its last evaluation on the shared

@@ -50,6 +50,7 @@ TUNABLE = (
     ("wide", 1, (0, 1)),        # FBS_OPT_TC_WIDE: pair products on M / stacked left rows on M
     ("roles", 2, (0, 2)),       # FBS_OPT_TC_ROLES: 16 product warps / 8 + 8 concurrent roles
     ("slab", 6, (0, 32, 8)),    # FBS_OPT_SLAB_PLANES: planned slabs / at most 32 or 8 planes
+    ("merge", 7, (0, 1)),       # FBS_OPT_TC_MERGE: hi and lo rows of B in one MMA where they fit / never
 )
 
 
@@ -63,7 +64,7 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE, batc
     or on batched calls over the list ``batch`` of device tensors: coordinate
     descent over TUNABLE from the defaults, keeping a change only when it is
     faster by more than 2% (batched calls: the options they use, pipeline
-    step, pair assignment and warp roles).  The choice is cached per (N, L,
+    step, pair assignment, warp roles and the merged hi/lo products).  The choice is cached per (N, L,
     edges, precision, batch size, library build, device)."""
     import torch
     key = _key(plan.N, plan.L, plan.edges, plan.precision) + ("|batch%d" % len(batch) if batch else "")
@@ -80,7 +81,7 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE, batc
     B = torch.empty((nf, plan.ntrip), dtype=torch.float64, device=field.device)
     P = torch.empty((nf, plan.nbins), dtype=torch.float64, device=field.device)
     run = (lambda: plan.bispectrum_batch(batch, B, P)) if batch else (lambda: plan.bispectrum(field, B[0], P[0]))
-    tunable = [t for t in TUNABLE if not batch or t[0] in ("chunk", "pairs", "roles")]
+    tunable = [t for t in TUNABLE if not batch or t[0] in ("chunk", "pairs", "roles", "merge")]
 
     def timed(choice):
         _apply(plan, choice)

@@ -70,6 +70,7 @@ struct TcJob {
     int *d_grp = nullptr;
     bool built = false, usable = false;
     int variant = 0;       // pair assignment the tables were built with (FBS_OPT_TC_PAIRS)
+    int last_merged = -1, last_ka = 0;  // MMA shape of the latest launch (diagnostics)
 };
 
 struct WideRight {
@@ -1344,6 +1345,23 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
     return true;
 }
 
+// Shape of a level's tensor-core job (which: 0 triplets, 1 quadruplets, 2
+// fused): built, usable, outer tiles (largest CTA group), inner rows, Npad,
+// and of its latest launch the merged flag and points per step / 64.
+void tc_job_info(Plan &p, int which, int32_t *out) {
+    for (int i = 0; i < 7; ++i) out[i] = 0;
+    if (!p.tc) return;
+    TcState &st = *reinterpret_cast<TcState *>(p.tc);
+    const TcJob &j = which == 0 ? st.trip : which == 1 ? st.quad : st.fused;
+    out[0] = j.built;
+    out[1] = j.usable;
+    out[2] = j.maxtiles;
+    out[3] = j.ninner;
+    out[4] = j.Npad;
+    out[5] = j.last_merged;
+    out[6] = j.last_ka;
+}
+
 int *tc_error_flag(Plan &p) { return p.root().d_errbuf; }
 int *tc_sticky_flag(Plan &p) { return p.root().d_errbuf ? p.root().d_errbuf + 1 : nullptr; }
 
@@ -1414,18 +1432,18 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     const int x3 = p.precision == FBS_PREC_BF16 ? 0 : 1;
     int tstr = tile_stride(job.Npad);
     int acc_cols_max = (((job.maxtiles * tstr) + 31) / 32) * 32;
+    const bool fits2 = acc_cols_max + 2 * 2 * kAStageCols <= 512 &&
+                       tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 2, 2) <= 220 * 1024;
+    const int ka = (fits2 && p.tc_chunk != 1 && aw == 16) ? 2 : 1;
     int merged = 0;
     if (x3 && p.tc_merge != 1 && 2 * job.Npad <= 256) {
         const int acc2 = (((job.maxtiles * tile_stride(2 * job.Npad)) + 31) / 32) * 32;
-        if (acc2 + 2 * 2 * kAStageCols <= 512) {
+        if (acc2 + 2 * ka * kAStageCols <= 512) {
             merged = 1;
             tstr = tile_stride(2 * job.Npad);
             acc_cols_max = acc2;
         }
     }
-    const bool fits2 = acc_cols_max + 2 * 2 * kAStageCols <= 512 &&
-                       tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 2, 2) <= 220 * 1024;
-    const int ka = (fits2 && p.tc_chunk != 1 && aw == 16) ? 2 : 1;
     // pipeline depths: 3 A stages when tensor memory allows, 4 field stages
     // when shared memory allows
     const int nst = acc_cols_max + 3 * ka * kAStageCols <= 512 ? 3 : 2;
@@ -1435,6 +1453,8 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins, nf * p.nbins);
     KTimer tm(p, kclass);
     dim3 grid(G, ngrp, nf);
+    job.last_merged = merged;
+    job.last_ka = ka;
 #define FBS_TC_LAUNCH(A, S, W, K)                                                                     \
     if (nst == A && nstg == S && aw == W && ka == K) {                                                \
         launched = true;                                                                              \

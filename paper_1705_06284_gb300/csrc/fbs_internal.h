@@ -292,6 +292,7 @@ struct KTimer {
 
 void free_tc_state(Plan &p);
 int *tc_error_flag(Plan &p);   // device flag set by a timed-out tensor-core wait (or nullptr)
+void tc_job_info(Plan &p, int which, int32_t *out);  // job shape diagnostics (fbs_plan_tc_info)
 int *tc_sticky_flag(Plan &p);  // device copy of that flag kept until reported (or nullptr)
 
 // Process-wide device-memory budget of all plans (fbs_set_device_budget):

@@ -1693,6 +1693,15 @@ fbs_status fbs_plan_set_stream(fbs_plan *plan, void *stream) {
     FBS_GUARD_END
 }
 
+fbs_status fbs_plan_tc_info(const fbs_plan *plan, int level, int which, int32_t *info) {
+    if (!plan || !info || level < 0 || level >= (int)plan->levels.size() || which < 0 || which > 2) {
+        set_error("fbs_plan_tc_info: bad argument");
+        return FBS_ERR_ARG;
+    }
+    tc_job_info(*plan->levels[level], which, info);
+    return FBS_OK;
+}
+
 fbs_status fbs_plan_follow(fbs_plan *follower, const fbs_plan *leader) {
     if (!follower || follower == leader) {
         set_error("fbs_plan_follow: bad plan");
