@@ -625,6 +625,96 @@ __global__ void __launch_bounds__(T *LP) inv_z_reg_kernel(const float2 *__restri
     }
 }
 
+// ------------------------------------------------------------------ register y stage
+// The y stage of one plane x (blockIdx.y) and bin (blockIdx.z) for LP
+// consecutive columns jz (blockIdx.x): per column the line over y with
+// z[n] = A_b[x][jy(n)][jz] on the bin's box (|m_y| <= R_b and inside the disk
+// the x stage wrote), zero elsewhere, transformed as the z stage does (N = N1 N2,
+// N2-point transforms in registers, one twiddled exchange through a shared
+// tile, N1-point transforms in registers) and written to G_b[xl][y][jz].
+// Thread (t, l) has the column l fastest: the global loads and stores and the
+// tile [k2][n1][l] are contiguous across l.
+template <int N, int N1, int N2, int T, int LP>
+__global__ void __launch_bounds__(T *LP) inv_y_reg_kernel(const float2 *__restrict__ A,
+                                                          const BinGeom *__restrict__ geom, int x0,
+                                                          float2 *__restrict__ G, const float2 *__restrict__ tw) {
+    static_assert(N1 * N2 == N && N1 % T == 0 && N2 % T == 0, "threads must divide both passes");
+    __shared__ float2 tile[N * LP];
+    const BinGeom g = geom[blockIdx.z];
+    if (g.empty) return;
+    const int jz0 = blockIdx.x * LP;
+    if (jz0 >= g.Dzb) return;  // uniform over the CTA
+    const int l = threadIdx.x % LP, t = threadIdx.x / LP;
+    const int mz = jz0 + l;
+    const bool col = mz < g.Dzb;
+    const int xl = blockIdx.y, x = x0 + xl;
+    const float2 *in = A + g.A_off + (long long)x * g.Db * g.Dzb;
+    const bool full = g.Db == N;  // the bin's box spans the whole axis
+    const int Rb = (g.Db - 1) / 2;
+    const long long mz2 = (long long)mz * mz;
+#pragma unroll 1
+    for (int j = 0; j < N1 / T; ++j) {
+        const int n1 = t + T * j;
+        float2 v[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const int n = n1 + N1 * n2;
+            int my, jy;
+            if (full) {
+                jy = n;
+                my = n < N / 2 ? n : n - N;
+            } else if (n <= Rb) {
+                jy = n;
+                my = n;
+            } else if (n >= N - Rb) {
+                my = n - N;
+                jy = my + g.Db;
+            } else {
+                jy = -1;
+                my = 0;
+            }
+            v[n2] = make_float2(0.f, 0.f);
+            if (col && jy >= 0 && (long long)my * my + mz2 < g.thr_hi) v[n2] = in[(long long)jy * g.Dzb + mz];
+        }
+        reg_idft<N2, N>(v, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            float2 val = v[k2];
+            if (k2 > 0) val = cmulc(val, tw[n1 * k2]);  // n1 k2 < N
+            tile[(k2 * N1 + n1) * LP + l] = val;
+        }
+    }
+    __syncthreads();
+    float2 *out = G + g.G_off + (long long)xl * N * g.Dzb + mz;
+#pragma unroll 1
+    for (int j = 0; j < N2 / T; ++j) {
+        const int k2 = t + T * j;
+        float2 v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = tile[(k2 * N1 + n1) * LP + l];
+        reg_idft<N1, N>(v, tw);
+        if (col) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) out[(long long)(k2 + N2 * k1) * g.Dzb] = v[k1];
+        }
+    }
+}
+
+// Register y-stage configurations: (N, N1, N2, threads per line, columns per CTA).
+#define FBS_YREG_LIST(X)        \
+    X(64, 8, 8, 8, 8)           \
+    X(72, 6, 12, 6, 16)         \
+    X(96, 8, 12, 4, 16)         \
+    X(108, 9, 12, 3, 32)        \
+    X(128, 8, 16, 8, 8)         \
+    X(144, 12, 12, 12, 8)       \
+    X(192, 8, 24, 8, 8)         \
+    X(216, 12, 18, 6, 16)       \
+    X(256, 16, 16, 16, 8)       \
+    X(288, 12, 24, 12, 8)       \
+    X(384, 16, 24, 8, 8)        \
+    X(512, 16, 32, 16, 8)
+
 // Register z-stage configurations: (N, N1, N2, threads per line, lines per
 // CTA).  T divides N1 and N2, T LP is a whole number of warps, and the tile
 // (LP lines of about N float2) stays within 48 KB of static shared memory.
@@ -859,7 +949,19 @@ void launch_inverse_yz_slab_geom(Plan &p, int x0, int nx, float *islab, const Bi
     const int N = p.M;  // evaluation grid
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
-    {
+    static const char *yenv = getenv("FBS_YSTAGE");
+    const bool yreg = !getenv("FBS_GENERIC_Y") && !(yenv && !strcmp(yenv, "smem")) && yreg_lines(N) > 0;
+    if (yreg) {
+        KTimer t(p, KC_INV_Y);
+        const int lp = yreg_lines(N);
+        dim3 grid((max_dzb(p, 0, nb) + lp - 1) / lp, nx, nvb);
+#define FBS_YR(n, n1, n2, t, lp_)                                                        \
+    if (N == n) inv_y_reg_kernel<n, n1, n2, t, lp_><<<grid, t * lp_, 0, p.stream>>>(      \
+                    p.d_A, geom, x0, p.d_G, p.d_twM);
+        FBS_YREG_LIST(FBS_YR)
+#undef FBS_YR
+        FBS_CUDA(cudaGetLastError());
+    } else {
         KTimer t(p, KC_INV_Y);
         // compile-time radices for the common evaluation grids, run-time otherwise
         auto k = inv_y_kernel<float>;
