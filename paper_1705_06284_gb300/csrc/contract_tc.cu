@@ -15,7 +15,10 @@
 //     into tensor memory (operand A) with tcgen05.st;
 //   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32) for
 //     hi*hi + hi*lo + lo*hi (BF16x3; hi*hi alone for plain BF16) into FP32
-//     accumulators in tensor memory, one 128 x Npad block per pair tile;
+//     accumulators in tensor memory, one 128 x Npad block per pair tile; the
+//     hi and lo rows of B sit side by side in each K-atom, so where the
+//     doubled accumulators fit, A_hi x [B_hi; B_lo] (N = 2 Npad) and A_lo x
+//     B_hi take two MMAs per K step instead of three;
 //   * every 1,024 points the producers read the accumulators back
 //     (tcgen05.ld) into compensated (Kahan) FP32 sums per item in shared
 //     memory.

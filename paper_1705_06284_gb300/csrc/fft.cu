@@ -758,6 +758,13 @@ static int zfast_lines(int N) {
     return 0;
 }
 static bool zfast_ok(int N) { return zfast_lines(N) > 0; }
+static int yreg_lines(int N) {
+#define FBS_YR(n, n1, n2, t, lp) \
+    if (N == n) return lp;
+    FBS_YREG_LIST(FBS_YR)
+#undef FBS_YR
+    return 0;
+}
 static int zreg_lines(int N) {
 #define FBS_ZR(n, n1, n2, t, lp) \
     if (N == n) return lp;
