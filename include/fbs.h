@@ -216,7 +216,13 @@ enum {
                             operand go into one MMA (N = 2 Npad: hi*hi and
                             hi*lo side by side) and lo*hi into a second, two
                             MMAs per K step instead of three; 1: always three.
-                            The sums agree within the precision's rounding. */
+                            The sums agree within the precision's rounding. */,
+    FBS_OPT_TC_BSTAGES = 8    /* shared-memory stages of the tensor-core
+                            contraction's inner operand: 0 (default) the first
+                            of (B, field) stage depths (4, 4), (3, 4), (3, 2),
+                            (2, 4), (2, 2) that fits in shared memory; 2, 3 or
+                            4: that many B stages where they fit (else the
+                            default).  Sums are identical. */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */
@@ -292,11 +298,13 @@ fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double 
 /*
  * fbs_plan_tc_info -- diagnostics of level `level`'s tensor-core job `which`
  * (0: triplets, 1: quadruplets, 2: the fused triplet + quadruplet pass),
- * available after an evaluation has built it: info[7] = {built, usable, outer
- * 128-row tiles of the largest CTA group, inner rows, inner rows padded (N of
- * the MMA), 1 when the latest launch put the hi and lo rows in one MMA
+ * available after an evaluation has built it: info[10] = {built, usable,
+ * outer 128-row tiles of the largest CTA group, inner rows, inner rows padded
+ * (N of the MMA), 1 when the latest launch put the hi and lo rows in one MMA
  * (FBS_OPT_TC_MERGE) else 0 (-1 before any launch), 64-point K-atoms per
- * pipeline step of that launch}.  FBS_ERR_ARG for a bad level or job.
+ * pipeline step of that launch, its operand-A stages in tensor memory, its
+ * operand-B stages and its field stages in shared memory}.  FBS_ERR_ARG for
+ * a bad level or job.
  */
 fbs_status fbs_plan_tc_info(const fbs_plan *plan, int level, int which, int32_t *info);
 

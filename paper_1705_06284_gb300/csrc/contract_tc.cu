@@ -74,6 +74,7 @@ struct TcJob {
     bool built = false, usable = false;
     int variant = 0;       // pair assignment the tables were built with (FBS_OPT_TC_PAIRS)
     int last_merged = -1, last_ka = 0;  // MMA shape of the latest launch (diagnostics)
+    int last_nsb = 0, last_nstg = 0, last_nst = 0;  // its B, field and A stage counts
 };
 
 struct WideRight {
@@ -232,10 +233,11 @@ constexpr int kTcThreads = (kProdWarps + 2) * 32;
 constexpr int kAStageCols = 64;           // per K-atom: 32 columns hi + 32 columns lo (64 BF16 per row each)
 constexpr int kMaxAStages = 3;
 constexpr int kMaxFieldStages = 4;
+constexpr int kMaxBStages = 4;
 
 struct TcBars {
     uint64_t sfull[kMaxFieldStages], sempty[kMaxFieldStages];
-    uint64_t full[kMaxAStages], empty[kMaxAStages], bfull[2], bempty[2], accr, accf;
+    uint64_t full[kMaxAStages], empty[kMaxAStages], bfull[kMaxBStages], bempty[kMaxBStages], accr, accf;
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -287,6 +289,21 @@ struct Ring {
     bool warm = false;
     __device__ __forceinline__ void next() {
         if (++slot == S) {
+            slot = 0;
+            phase ^= 1u;
+            warm = true;
+        }
+    }
+};
+
+// The same for a ring whose size is a launch parameter.
+struct RingN {
+    int slot = 0, n;
+    uint32_t phase = 0;
+    bool warm = false;
+    __device__ explicit RingN(int size) : n(size) {}
+    __device__ __forceinline__ void next() {
+        if (++slot == n) {
             slot = 0;
             phase ^= 1u;
             warm = true;
@@ -374,7 +391,8 @@ __device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes,
 }
 
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
-// NST: A stages in tensor memory; NSTG: field stages in shared memory.
+// NST: A stages in tensor memory; NSTG: field stages in shared memory;
+// nsb (launch parameter, 2..4): operand-B stages in shared memory.
 // AW: warps forming the pair products of operand A (4 per TMEM lane quarter
 // x 16 points, or 2 x 32 points); with AW = 16 they also build operand B,
 // with AW = 8 the other 8 producer warps build operand B concurrently.
@@ -388,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
-                       int *__restrict__ err, long long wait_limit, int part_rows, int merged) {
+                       int *__restrict__ err, long long wait_limit, int part_rows, int merged, int nsb) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
     static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
@@ -423,10 +441,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // 2 Npad rows: a single MMA with N = 2 Npad multiplies both halves)
     const int b_stage = KA * b_tile;    // hi (or lo) part of one B stage
     const int b_atom2 = 2 * b_tile;     // one K-atom: hi tile, then lo tile
-    unsigned char *const Bh0 = sm;      // stage sb at Bh0 + 2 sb b_stage
+    unsigned char *const Bh0 = sm;      // stage sb (< nsb) at Bh0 + 2 sb b_stage
     const int half_bytes = ((nbins + 7) & ~7) * 128;  // one 32-point TMA box of all bins
     const int stage_bytes = 2 * KA * half_bytes;
-    unsigned char *const stg = sm + 4 * b_stage;
+    unsigned char *const stg = sm + 2 * nsb * b_stage;
     float2 *acc = reinterpret_cast<float2 *>(stg + NSTG * stage_bytes);
     int2 *pbc = reinterpret_cast<int2 *>(acc + nloc);  // (b, c) of every row of every tile
 
@@ -444,7 +462,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(&bars.full[i], AW);
             mbar_init(&bars.empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < nsb; ++i) {
             mbar_init(&bars.bfull[i], BW > 0 ? BW : AW);
             mbar_init(&bars.bempty[i], 1);
         }
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int p = p_first + i;
         pbc[i] = p < npairs ? make_int2(pairs[p].b, pairs[p].c) : make_int2(-1, -1);
     }
-    for (int i = tid; i < 4 * b_stage / 16; i += kTcThreads) {  // padding rows of B stay zero
+    for (int i = tid; i < 2 * nsb * b_stage / 16; i += kTcThreads) {  // padding rows of B stay zero
         int o = i % (b_tile / 16);
         if ((o * 16) / 128 >= ninner) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     }
@@ -517,7 +535,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const uint32_t idesc = idesc_bf16(128, Npad);
             const uint32_t idesc2 = idesc_bf16(128, 2 * Npad);  // hi and lo rows of B together
             Ring<NST> ra;
-            Ring<2> rb;
+            RingN rb(nsb);
             long long nfl = 0;
             int last_slot = -1;
             uint32_t last_phase = 0;
@@ -593,7 +611,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else if (BW > 0 && warp >= AW) {
         // ================= operand-B warps (AW .. 15) =================
         Ring<NSTG> rs;
-        Ring<2> rb;
+        RingN rb(nsb);
         for (long long ci = c0; ci < c1; ++ci) {
             role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 24, wait_limit);
             const unsigned char *st = stg + rs.slot * stage_bytes;
@@ -617,9 +635,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int ptid = tid;                    // 0 .. 32*AW-1
         Ring<NSTG> rs;
         Ring<NST> ra;
-        Ring<2> rb;
+        RingN rb(nsb);
         long long nfl = 0;
         int since = 0;
+        bool pend = false;  // a flush point has passed; its flush is still due
+        auto flush = [&]() {
+            role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 23, wait_limit);
+            tc_fence_after();
+            if (!*abortp) {
+                for (int lt = 0; lt < ntl; ++lt) {
+                    const int p = (t0 + lt) * 128 + r;
+                    const bool valid = p < npairs;
+                    const TcPair *pp = pairs + (valid ? p : 0);
+                    for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (AW / 4)) {
+                        float v[8];
+                        tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
+                        if (merged) {  // hi*lo sits Npad columns further: one FP32 sum per item
+                            float u[8];
+                            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + Npad + c8), u);
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) v[i] = __fadd_rn(v[i], u[i]);
+                        }
+                        if (!valid) continue;
+                        const int wsel = c8 >> 5;
+                        const unsigned wm = __ldg(&pp->mask[wsel]);
+                        const unsigned w = (wm >> (c8 & 31)) & 0xffu;
+                        if (!w) continue;
+                        int idx = __ldg(&pp->first) - it0 + __popc(wm & ((1u << (c8 & 31)) - 1u));
+                        for (int m = 0; m < wsel; ++m) idx += __popc(__ldg(&pp->mask[m]));
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if ((w >> i) & 1u) kahan_add(acc[idx++], v[i]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars.accf);
+            ++nfl;
+        };
         for (long long ci = c0; ci < c1; ++ci) {
             role_wait(&bars.sfull[rs.slot], rs.phase, abortp, err, 20, wait_limit);
             const unsigned char *st = stg + rs.slot * stage_bytes;
@@ -683,42 +737,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars.sempty[rs.slot]);
             rs.next();
-            // ---- flush: accumulators -> compensated FP32 sums
-            if (++since == flush_every || ci == c1 - 1) {
-                role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 23, wait_limit);
-                tc_fence_after();
-                if (!*abortp) {
-                    for (int lt = 0; lt < ntl; ++lt) {
-                        const int p = (t0 + lt) * 128 + r;
-                        const bool valid = p < npairs;
-                        const TcPair *pp = pairs + (valid ? p : 0);
-                        for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (AW / 4)) {
-                            float v[8];
-                            tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + c8), v);
-                            if (merged) {  // hi*lo sits Npad columns further: one FP32 sum per item
-                                float u[8];
-                                tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lt * tstride + Npad + c8), u);
-#pragma unroll
-                                for (int i = 0; i < 8; ++i) v[i] = __fadd_rn(v[i], u[i]);
-                            }
-                            if (!valid) continue;
-                            const int wsel = c8 >> 5;
-                            const unsigned wm = __ldg(&pp->mask[wsel]);
-                            const unsigned w = (wm >> (c8 & 31)) & 0xffu;
-                            if (!w) continue;
-                            int idx = __ldg(&pp->first) - it0 + __popc(wm & ((1u << (c8 & 31)) - 1u));
-                            for (int m = 0; m < wsel; ++m) idx += __popc(__ldg(&pp->mask[m]));
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-                                if ((w >> i) & 1u) kahan_add(acc[idx++], v[i]);
-                        }
-                    }
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bars.accf);
-                ++nfl;
+            // ---- flush: accumulators -> compensated FP32 sums.  A flush point's
+            // flush runs after the next step's operands are handed off (the MMAs
+            // of that step wait for it), so forming them overlaps the drain of
+            // the MMAs before the flush point.  Only when a step's tiles fit in
+            // the A ring (ntl <= NST): their stages are then freed by MMAs of
+            // steps before the flush point, never by the next step's own MMAs,
+            // which wait for the flush.  The last step flushes at once.
+            const bool point = ++since == flush_every || ci == c1 - 1;
+            if (pend) {
+                flush();
+                pend = false;
+            }
+            if (point) {
                 since = 0;
+                if (ci == c1 - 1 || ntl > NST) flush();
+                else pend = true;
             }
         }
     }
@@ -998,9 +1032,9 @@ __global__ void __launch_bounds__(kWideThreads, 1)
 // ------------------------------------------------------------------ host side
 // Dynamic shared memory of the narrow kernel: B tiles, nstg field stages,
 // compensated sums, pair bins.
-static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl, int nstg, int ka = 1) {
+static size_t tc_smem_bytes(int nbins, int Npad, int nloc, int ntl, int nstg, int ka = 1, int nsb = 2) {
     const size_t half = (size_t)((nbins + 7) & ~7) * 128;
-    size_t b = 1024 + 4 * (size_t)ka * Npad * 128 + (size_t)nstg * 2 * ka * half + (size_t)nloc * 8 +
+    size_t b = 1024 + 2 * (size_t)nsb * ka * Npad * 128 + (size_t)nstg * 2 * ka * half + (size_t)nloc * 8 +
                (size_t)ntl * 128 * 8;
     return std::max<size_t>(b, 116 * 1024);  // > half the SM's shared memory: one CTA per SM
 }
@@ -1352,7 +1386,7 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
 // fused): built, usable, outer tiles (largest CTA group), inner rows, Npad,
 // and of its latest launch the merged flag and points per step / 64.
 void tc_job_info(Plan &p, int which, int32_t *out) {
-    for (int i = 0; i < 7; ++i) out[i] = 0;
+    for (int i = 0; i < 10; ++i) out[i] = 0;
     if (!p.tc) return;
     TcState &st = *reinterpret_cast<TcState *>(p.tc);
     const TcJob &j = which == 0 ? st.trip : which == 1 ? st.quad : st.fused;
@@ -1363,6 +1397,9 @@ void tc_job_info(Plan &p, int which, int32_t *out) {
     out[4] = j.Npad;
     out[5] = j.last_merged;
     out[6] = j.last_ka;
+    out[7] = j.last_nst;
+    out[8] = j.last_nsb;
+    out[9] = j.last_nstg;
 }
 
 int *tc_error_flag(Plan &p) { return p.root().d_errbuf; }
@@ -1447,17 +1484,37 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
             acc_cols_max = acc2;
         }
     }
-    // pipeline depths: 3 A stages when tensor memory allows, 4 field stages
-    // when shared memory allows
+    // pipeline depths: 3 A stages when tensor memory allows; operand-B and
+    // field stages as shared memory allows, the first of (B, field) = (4, 4),
+    // (3, 4), (3, 2), (2, 4), (2, 2) that fits (FBS_OPT_TC_BSTAGES asks for a
+    // B depth)
     const int nst = acc_cols_max + 3 * ka * kAStageCols <= 512 ? 3 : 2;
-    const int nstg = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, 4, ka) <= 220 * 1024 ? 4 : 2;
-    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, nstg, ka);
+    const int want_nsb = p.tc_bstages;
+    const auto fits = [&](int b, int f) {
+        return tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, f, ka, b) <= 220 * 1024;
+    };
+    static const int order[5][2] = {{4, 4}, {3, 4}, {3, 2}, {2, 4}, {2, 2}};
+    int nsb = 2, nstg = 2;  // fits: the job's tables were sized for it
+    const auto pick = [&](int want) {
+        for (const auto &o : order)
+            if ((!want || o[0] == want) && fits(o[0], o[1])) {
+                nsb = o[0];
+                nstg = o[1];
+                return true;
+            }
+        return false;
+    };
+    if (!pick(want_nsb)) pick(0);
+    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, nstg, ka, nsb);
     const int flush_every = 16 / ka;  // 1024 points in FP32 per flush
     const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins, nf * p.nbins);
     KTimer tm(p, kclass);
     dim3 grid(G, ngrp, nf);
     job.last_merged = merged;
     job.last_ka = ka;
+    job.last_nsb = nsb;
+    job.last_nstg = nstg;
+    job.last_nst = nst;
 #define FBS_TC_LAUNCH(A, S, W, K)                                                                     \
     if (nst == A && nstg == S && aw == W && ka == K) {                                                \
         launched = true;                                                                              \
@@ -1466,7 +1523,7 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
         contract_tc_kernel<A, S, W, K><<<grid, kTcThreads, sm, p.stream>>>(                          \
             fmap, npts, p.nbins, job.Npad, tstr, job.ninner, job.d_inner, job.d_pairs, job.npairs,      \
             job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err, tc_wait_limit(p),     \
-            p.part_blocks, merged);                                                                   \
+            p.part_blocks, merged, nsb);                                                              \
     }
     bool launched = false;
     FBS_TC_LAUNCH(2, 2, 16, 1)

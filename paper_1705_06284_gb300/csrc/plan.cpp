@@ -609,6 +609,7 @@ static Plan *new_level(Plan &root, int M) {
     lv->tc_chunk = root.tc_chunk;
     lv->tc_pairs = root.tc_pairs;
     lv->tc_merge = root.tc_merge;
+    lv->tc_bstages = root.tc_bstages;
     lv->tc_wait_limit = root.tc_wait_limit;
     lv->d_box = root.d_box;
     root.levels.push_back(lv);
@@ -1661,6 +1662,10 @@ static bool set_plan_option(Plan *plan, int option, int value) {
     }
     if (option == FBS_OPT_TC_MERGE && (value == 0 || value == 1)) {
         plan->tc_merge = value;
+        return true;
+    }
+    if (option == FBS_OPT_TC_BSTAGES && (value == 0 || (value >= 2 && value <= 4))) {
+        plan->tc_bstages = value;
         return true;
     }
     if (option == FBS_OPT_TC_PAIRS && (value == 0 || value == 1)) {

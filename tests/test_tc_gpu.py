@@ -260,3 +260,47 @@ def test_merged_hi_lo_products_match_oracle(quads, N, nb):
         # the two assignments of the products round differently, nothing more
         big = np.abs(out[1][0]) > 1e-3 * np.abs(out[1][0]).max()
         assert np.all(np.abs(out[0][0] - out[1][0])[big] <= 2e-4 * np.abs(out[1][0][big]) + 1e-6 * np.abs(out[1][0]).max())
+
+
+@pytest.mark.parametrize("quads,N,nb,roles", [(False, 64, 16, 1), (False, 64, 28, 1), (False, 96, 64, 1),
+                                              (True, 96, 8, 1), (True, 48, 10, 2)])
+def test_operand_b_stage_depths_give_identical_sums(quads, N, nb, roles):
+    """FBS_OPT_TC_BSTAGES 2, 3 and 4 (the depth of the operand-B ring in
+    shared memory; each accumulator flush deferred until the next step's
+    operands are handed off) issue the same MMAs into the same accumulators in
+    the same order: bit-identical sums, tensor-core job diagnostics that name
+    the depth used, and the oracle's values.  96^3 runs several flushes per
+    CTA, 64^3 one deferred flush and the last; 28 and 64 bins give CTAs with
+    several pair tiles (up to the A ring's depth the flush is deferred, past
+    it not); roles 2 has the operand-B warps apart from the pair-product
+    warps."""
+    import torch
+    L = float(N)
+    edges = fields.linear_edges(N, L, nb)
+    f32 = _field("quadratic", N, 35).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    out = {}
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        plan.set_option(fbs.FBS_OPT_TC_ROLES, roles)
+        for depth in (2, 3, 4):
+            plan.set_option(fbs.FBS_OPT_TC_BSTAGES, depth)
+            if quads:
+                T, B, P = plan.trispectrum(f)
+            else:
+                B, P = plan.bispectrum(f)
+                T = None
+            torch.cuda.synchronize()
+            plan.check()
+            used = [j["stages"][1] for lvl in plan.tc_info() for j in lvl.values()]
+            assert used and all(2 <= u <= depth for u in used)
+            if depth == 2:
+                assert all(u == 2 for u in used)
+            out[depth] = (B.cpu().numpy(), P.cpu().numpy(), None if T is None else T.cpu().numpy())
+        for depth in (3, 4):
+            assert np.array_equal(out[2][0], out[depth][0])
+            if quads:
+                assert np.array_equal(out[2][2], out[depth][2])
+        if quads:
+            check_trispectrum(plan, out[4][2], f32, L, edges, 2e-4)
+        if N <= 64 and nb <= 16:
+            check_bispectrum(plan, out[4][0], out[4][1], f32, L, edges, "bf16x3")
