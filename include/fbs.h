@@ -222,7 +222,15 @@ enum {
                             of (B, field) stage depths (4, 4), (3, 4), (3, 2),
                             (2, 4), (2, 2) that fits in shared memory; 2, 3 or
                             4: that many B stages where they fit (else the
-                            default).  Sums are identical. */
+                            default).  Sums are identical. */,
+    FBS_OPT_TC_BFROMA = 9     /* inner pair rows of the tensor-core contraction
+                            (the trispectrum pass's I_a I_b): 0 (default) where
+                            the job has one pair tile and every inner pair is
+                            also an outer row, the operand-A warps store that
+                            product into operand B as well, so operand B is
+                            built from the field stage for the single-bin rows
+                            only; 1: every inner row is built from the field
+                            stage.  Sums are identical. */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */
@@ -298,13 +306,14 @@ fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double 
 /*
  * fbs_plan_tc_info -- diagnostics of level `level`'s tensor-core job `which`
  * (0: triplets, 1: quadruplets, 2: the fused triplet + quadruplet pass),
- * available after an evaluation has built it: info[10] = {built, usable,
+ * available after an evaluation has built it: info[11] = {built, usable,
  * outer 128-row tiles of the largest CTA group, inner rows, inner rows padded
  * (N of the MMA), 1 when the latest launch put the hi and lo rows in one MMA
  * (FBS_OPT_TC_MERGE) else 0 (-1 before any launch), 64-point K-atoms per
  * pipeline step of that launch, its operand-A stages in tensor memory, its
- * operand-B stages and its field stages in shared memory}.  FBS_ERR_ARG for
- * a bad level or job.
+ * operand-B stages and its field stages in shared memory, 1 when it took the
+ * inner pair rows from operand A (FBS_OPT_TC_BFROMA)}.  FBS_ERR_ARG for a bad
+ * level or job.
  */
 fbs_status fbs_plan_tc_info(const fbs_plan *plan, int level, int which, int32_t *info);
 

@@ -45,6 +45,7 @@ FBS_OPT_TC_WAIT_LIMIT = 5
 FBS_OPT_SLAB_PLANES = 6
 FBS_OPT_TC_MERGE = 7
 FBS_OPT_TC_BSTAGES = 8
+FBS_OPT_TC_BFROMA = 9
 
 _PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
 
@@ -341,16 +342,17 @@ class Plan:
     def tc_info(self):
         """Tensor-core job shapes per level (after an evaluation): a list of
         {job: dict(tiles, inner, Npad, merged, ka, stages)} for the built jobs
-        (stages: operand-A, operand-B and field pipeline depths)."""
+        (stages: operand-A, operand-B and field pipeline depths; b_from_a:
+        inner pair rows stored by the operand-A warps)."""
         out = []
         for lvl in range(len(self.levels)):
             d = {}
             for which, name in enumerate(("triplets", "quadruplets", "fused")):
-                a = (ctypes.c_int32 * 10)()
+                a = (ctypes.c_int32 * 11)()
                 _check(lib().fbs_plan_tc_info(_vp(self._h), lvl, which, ctypes.cast(a, _vp)))
                 if a[0] and a[1]:
                     d[name] = {"tiles": a[2], "inner": a[3], "Npad": a[4], "merged": a[5], "ka": a[6],
-                               "stages": [a[7], a[8], a[9]]}
+                               "stages": [a[7], a[8], a[9]], "b_from_a": a[10]}
             out.append(d)
         return out
 

@@ -52,6 +52,7 @@ TUNABLE = (
     ("slab", 6, (0, 32, 8)),    # FBS_OPT_SLAB_PLANES: planned slabs / at most 32 or 8 planes
     ("merge", 7, (0, 1)),       # FBS_OPT_TC_MERGE: hi and lo rows of B in one MMA where they fit / never
     ("bstages", 8, (0, 2)),     # FBS_OPT_TC_BSTAGES: deepest operand-B ring that fits / two stages
+    ("bfroma", 9, (0, 1)),      # FBS_OPT_TC_BFROMA: inner pair rows from operand A where it applies / never
 )
 
 

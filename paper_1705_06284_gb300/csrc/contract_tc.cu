@@ -73,7 +73,10 @@ struct TcJob {
     int *d_grp = nullptr;
     bool built = false, usable = false;
     int variant = 0;       // pair assignment the tables were built with (FBS_OPT_TC_PAIRS)
+    int *d_ifeed = nullptr;  // single-tile jobs: per outer row, the inner pair row of the same product, or -1
+    int nsingle = 0;         // inner rows built from the field stage with d_ifeed (a prefix of the inner rows)
     int last_merged = -1, last_ka = 0;  // MMA shape of the latest launch (diagnostics)
+    int last_bfa = 0;                   // the latest launch took inner pair rows from operand A
     int last_nsb = 0, last_nstg = 0, last_nst = 0;  // its B, field and A stage counts
 };
 
@@ -345,54 +348,75 @@ __device__ __forceinline__ void kahan_add(float2 &a, float v) {
     a.x = t;
 }
 
-// Address of points 4j..4j+3 of bin row b in a field stage: two halves of 32
-// points, each [rows][128 B] in the TMA 128-byte swizzle (16-byte chunk j of
-// row b stored at chunk j ^ (b mod 8)).
-__device__ __forceinline__ const float4 *stage_at(const unsigned char *st, int half_bytes, int b, int j) {
-    return reinterpret_cast<const float4 *>(st + (j >> 3) * half_bytes + b * 128 +
-                                            (((j & 7) ^ (b & 7)) << 4));
+// A field stage holds 64 KA points of every bin as 2 KA boxes of 32 points,
+// each [rows][128 B] in the TMA 128-byte swizzle: 16-byte chunk J (points
+// 4J..4J+3) of bin row b at chunk (J mod 8) ^ (b mod 8) of the row in box J / 8.
+
+// The values of one operand-B unit (inner row with bins `in`, 8-point group
+// of the step whose 16-byte chunks 2j, 2j + 1 sit in the 32-point box at
+// `box`, chunk 2j at position jp before the swizzle): the x bin's 8 values
+// and, for a pair row, the y bin's.  Chunk 2j + 1 of a row is chunk 2j with
+// bit 4 of the offset flipped (jp is even).
+struct BUnit {
+    float4 x0, x1, y0, y1;
+};
+
+__device__ __forceinline__ void b_unit_load(const unsigned char *box, int jp, int2 in, BUnit &u) {
+    const uint32_t ox = (uint32_t)in.x * 128u + ((uint32_t)(jp ^ (in.x & 7)) << 4);
+    u.x0 = *reinterpret_cast<const float4 *>(box + ox);
+    u.x1 = *reinterpret_cast<const float4 *>(box + (ox ^ 16u));
+    if (in.y >= 0) {
+        const uint32_t oy = (uint32_t)in.y * 128u + ((uint32_t)(jp ^ (in.y & 7)) << 4);
+        u.y0 = *reinterpret_cast<const float4 *>(box + oy);
+        u.y1 = *reinterpret_cast<const float4 *>(box + (oy ^ 16u));
+    }
 }
 
-// One operand-B unit (inner row `row`, 8-point group j of the step): the
-// row's values (a single bin, or the product of two bins) split into BF16
-// hi/lo, stored in the 128-byte-swizzled K-major tile of K-atom j / 8.
-__device__ __forceinline__ void build_b_unit(const unsigned char *st, int half_bytes, const int2 *s_inner, int row,
-                                             int j, unsigned char *bh, unsigned char *bl, int atom_stride) {
-    const int2 in = s_inner[row];
-    const float4 v0 = *stage_at(st, half_bytes, in.x, 2 * j);
-    const float4 v1 = *stage_at(st, half_bytes, in.x, 2 * j + 1);
+// The unit's values (a single bin, or the product of two bins) split into
+// BF16 hi/lo and stored at byte offset `off` of the hi and lo tiles.
+__device__ __forceinline__ void b_unit_store(const BUnit &u, bool pair, unsigned char *bh, unsigned char *bl,
+                                             uint32_t off) {
     uint32_t h[4], l[4];
-    if (in.y >= 0) {
-        const float4 w0 = *stage_at(st, half_bytes, in.y, 2 * j);
-        const float4 w1 = *stage_at(st, half_bytes, in.y, 2 * j + 1);
-        mul_split8(v0, v1, w0, w1, h, l);
+    if (pair) {
+        mul_split8(u.x0, u.x1, u.y0, u.y1, h, l);
     } else {
-        split2(make_float2(v0.x, v0.y), h[0], l[0]);
-        split2(make_float2(v0.z, v0.w), h[1], l[1]);
-        split2(make_float2(v1.x, v1.y), h[2], l[2]);
-        split2(make_float2(v1.z, v1.w), h[3], l[3]);
+        split2(make_float2(u.x0.x, u.x0.y), h[0], l[0]);
+        split2(make_float2(u.x0.z, u.x0.w), h[1], l[1]);
+        split2(make_float2(u.x1.x, u.x1.y), h[2], l[2]);
+        split2(make_float2(u.x1.z, u.x1.w), h[3], l[3]);
     }
-    const uint32_t off = (uint32_t)((j >> 3) * atom_stride) + sw128_off(row, j & 7);
     *reinterpret_cast<uint4 *>(bh + off) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4 *>(bl + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Operand B of one pipeline step by W warps (wb = 0..W-1 among them): the
-// C = 8 KA eight-point groups go to the warps (W / C warps per group), the
-// inner rows to their lanes, with no division in the loop.
+// C = 8 KA eight-point groups go to the warps (W / C warps per group), inner
+// rows 0..nrows-1 to their lanes.  Each unit is split into BF16 hi/lo in the
+// 128-byte-swizzled K-major tile of K-atom j / 8.
 template <int W, int KA>
-__device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes, const int2 *s_inner, int ninner,
+__device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes, const int2 *s_inner, int nrows,
                                         int wb, int lane, unsigned char *bh, unsigned char *bl, int atom_stride) {
     constexpr int C = 8 * KA;
     static_assert(W % C == 0, "operand-B warps must cover the eight-point groups evenly");
     const int j = wb % C;
-    for (int row = lane + 32 * (wb / C); row < ninner; row += 32 * (W / C))
-        build_b_unit(st, half_bytes, s_inner, row, j, bh, bl, atom_stride);
+    const unsigned char *box = st + ((2 * j) >> 3) * half_bytes;
+    const int jp = (2 * j) & 7;
+    const uint32_t dj = (uint32_t)((j >> 3) * atom_stride);
+    for (int row = lane + 32 * (wb / C); row < nrows; row += 32 * (W / C)) {
+        const int2 in = s_inner[row];
+        BUnit u;
+        b_unit_load(box, jp, in, u);
+        b_unit_store(u, in.y >= 0, bh, bl, dj + sw128_off(row, j & 7));
+    }
 }
 
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
 // NST: A stages in tensor memory; NSTG: field stages in shared memory;
 // nsb (launch parameter, 2..4): operand-B stages in shared memory.
+// ifeed (null, or with a single pair tile and AW = 16): per outer row, the
+// inner pair row with the same product (-1: none); the operand-A thread of
+// that row also stores its hi/lo values into operand B, and the operand-B
+// build covers inner rows 0..nbuild-1 only.
 // AW: warps forming the pair products of operand A (4 per TMEM lane quarter
 // x 16 points, or 2 x 32 points); with AW = 16 they also build operand B,
 // with AW = 8 the other 8 producer warps build operand B concurrently.
@@ -406,7 +430,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        const TcPair *__restrict__ pairs, int npairs,
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
-                       int *__restrict__ err, long long wait_limit, int part_rows, int merged, int nsb) {
+                       int *__restrict__ err, long long wait_limit, int part_rows, int merged, int nsb,
+                       const int *__restrict__ ifeed, int nbuild) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
     static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
@@ -495,6 +520,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     volatile int *abortp = &abort_flag;
 
     const long long nchunks = (npts + KCH - 1) / KCH;
+    const bool bfa = BW == 0 && ifeed != nullptr;  // the host passes ifeed with one pair tile only
     const long long c0 = nchunks * blockIdx.x / gridDim.x;
     const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
 
@@ -632,7 +658,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // ================= operand-A warps (0 .. AW-1) =================
         const int q = warp & 3, kq = warp >> 2;  // lane quarter, PPT-point slice of the chunk
         const int r = 32 * q + lane;             // operand-A row (TMEM lane) of this thread
-        const int ptid = tid;                    // 0 .. 32*AW-1
+        const int feed = bfa ? ifeed[r] : -1;    // inner row with this row's product (single tile)
         Ring<NSTG> rs;
         Ring<NST> ra;
         RingN rb(nsb);
@@ -681,12 +707,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 // ---- operand B: split every inner row into BF16 hi/lo (swizzled K-major)
                 const int sb = rb.slot;
                 if (rb.warm) role_wait(&bars.bempty[sb], rb.phase ^ 1u, abortp, err, 21, wait_limit);
-                build_b<AW, KA>(st, half_bytes, s_inner, ninner, warp, lane, Bh0 + 2 * sb * b_stage,
+                build_b<AW, KA>(st, half_bytes, s_inner, nbuild, warp, lane, Bh0 + 2 * sb * b_stage,
                                 Bh0 + 2 * sb * b_stage + b_tile, b_atom2);
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bars.bfull[sb]);
-                rb.next();
+                if (!bfa) {  // else operand B is complete once the pair products below are stored
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bars.bfull[sb]);
+                    rb.next();
+                }
             }
             // ---- operand A: pair products of this thread's row, PPT points, into TMEM
             for (int lt = 0; lt < ntl; ++lt) {
@@ -726,11 +754,30 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     tmem_st8a(lanebase + col + 8u * c, hw);
                     tmem_st8a(lanebase + col + 32u * KA + 8u * c, lw);
+                    if (BW == 0 && feed >= 0) {
+                        // the same product is inner row `feed`: its 8-point groups
+                        // PPT kq / 8 + 2c (hw[0..3]) and + 1 (hw[4..7]) go to operand B
+                        unsigned char *bh = Bh0 + 2 * rb.slot * b_stage;
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int u = (PPT / 8) * kq + 2 * c + h2;
+                            const uint32_t off = (uint32_t)((u >> 3) * b_atom2) + sw128_off(feed, u & 7);
+                            *reinterpret_cast<uint4 *>(bh + off) =
+                                make_uint4(hw[4 * h2], hw[4 * h2 + 1], hw[4 * h2 + 2], hw[4 * h2 + 3]);
+                            *reinterpret_cast<uint4 *>(bh + b_tile + off) =
+                                make_uint4(lw[4 * h2], lw[4 * h2 + 1], lw[4 * h2 + 2], lw[4 * h2 + 3]);
+                        }
+                    }
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
+                if (BW == 0 && bfa) fence_proxy_async_smem();  // operand B's stores, for the MMAs
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bars.full[as]);
+                if (lane == 0) {
+                    if (BW == 0 && bfa) mbar_arrive(&bars.bfull[rb.slot]);
+                    mbar_arrive(&bars.full[as]);
+                }
+                if (BW == 0 && bfa) rb.next();
                 ra.next();
             }
             // ---- the stage is consumed: hand it back to the loader
@@ -1209,6 +1256,32 @@ static void build_job(Plan &p, const TaskList &t, bool quads, TcJob &job) {
     finish_job(p, job, hp, inner, t.iout);
 }
 
+// A job with a single pair tile whose inner rows from nbuild on are pair
+// rows that are outer rows too (the same product I_x I_y): the operand-A
+// thread of such an outer row also stores the row's BF16 hi/lo values into
+// operand B, and only inner rows 0..nbuild-1 are built from the field stage.
+// The products are the same FP32 multiplications, so the sums are
+// bit-identical.
+static void attach_feed(Plan &p, TcJob &job, const std::vector<TcPair> &hp, const std::vector<int2> &inner,
+                        int nbuild) {
+    if (job.ntiles != 1 || nbuild >= (int)inner.size()) return;
+    std::map<std::pair<int, int>, int> outer_row;
+    for (int i = 0; i < (int)hp.size(); ++i)
+        outer_row.emplace(std::make_pair(std::min(hp[i].b, hp[i].c), std::max(hp[i].b, hp[i].c)), i);
+    std::vector<int> feed(128, -1);
+    for (int n = nbuild; n < (int)inner.size(); ++n) {
+        if (inner[n].y < 0) return;
+        auto it = outer_row.find({std::min(inner[n].x, inner[n].y), std::max(inner[n].x, inner[n].y)});
+        if (it == outer_row.end() || feed[it->second] >= 0) return;
+        feed[it->second] = n;
+    }
+    job.nsingle = nbuild;
+    job.d_ifeed = (int *)p.dalloc(feed.size() * sizeof(int));
+    FBS_CUDA(cudaMemcpyAsync(job.d_ifeed, feed.data(), feed.size() * sizeof(int), cudaMemcpyHostToDevice,
+                             p.stream));
+    FBS_CUDA(cudaStreamSynchronize(p.stream));
+}
+
 // The triplets and quadruplets of a trispectrum plan as one contraction over
 // the same shell fields: outer rows are the union of the triplets' pairs
 // (b, c) and the quadruplets' pairs (c, d); inner rows are the triplets'
@@ -1239,18 +1312,41 @@ static void build_fused_job(Plan &p, TcJob &job) {
     std::vector<int> bin_row(nb, -1), pair_row((size_t)nb * nb, -1);
     for (int e = 0; e < tt.nitems; ++e) bin_row[tt.ia[e]] = 0;
     for (int e = 0; e < qt.nitems; ++e) pair_row[qassign[e].first] = 0;
+    // outer rows (unordered pairs); an inner pair that is an outer row too is
+    // "fed" (operand A forms its product).  While one tile holds them all,
+    // the other inner pairs join the outer rows without items.
+    std::vector<char> is_outer((size_t)nb * nb, 0);
+    auto mark = [&](int x, int y) { is_outer[(size_t)std::min(x, y) * nb + std::max(x, y)] = 1; };
+    size_t nouter = 0;
+    for (int i = 0; i < tt.npairs; ++i) mark(tt.pb[i], tt.pc[i]);
+    for (int e = 0; e < qt.nitems; ++e) mark(qassign[e].second / nb, qassign[e].second % nb);
+    for (char c : is_outer) nouter += c;
+    std::vector<std::pair<int, int>> extra;
+    auto fed = [&](int a, int b) { return is_outer[(size_t)std::min(a, b) * nb + std::max(a, b)] != 0; };
+    for (int a = 0; a < nb; ++a)
+        for (int b = 0; b < nb; ++b)
+            if (pair_row[(size_t)a * nb + b] >= 0 && !fed(a, b)) extra.push_back({std::min(a, b), std::max(a, b)});
+    std::sort(extra.begin(), extra.end());
+    extra.erase(std::unique(extra.begin(), extra.end()), extra.end());
+    const bool add_extra = nouter + extra.size() <= 128;
+    if (add_extra)
+        for (const auto &k : extra) mark(k.first, k.second);
+    // inner rows: single bins, then the pairs built from the field stage, then the fed pairs
     std::vector<int2> inner;
     for (int b = 0; b < nb; ++b)
         if (bin_row[b] >= 0) {
             bin_row[b] = (int)inner.size();
             inner.push_back(make_int2(b, -1));
         }
-    for (int a = 0; a < nb; ++a)
-        for (int b = 0; b < nb; ++b)
-            if (pair_row[(size_t)a * nb + b] >= 0) {
-                pair_row[(size_t)a * nb + b] = (int)inner.size();
-                inner.push_back(make_int2(a, b));
-            }
+    for (int pass = 0; pass < 2; ++pass)
+        for (int a = 0; a < nb; ++a)
+            for (int b = 0; b < nb; ++b)
+                if (pair_row[(size_t)a * nb + b] >= 0 && fed(a, b) == (pass == 1)) {
+                    pair_row[(size_t)a * nb + b] = (int)inner.size();
+                    inner.push_back(make_int2(a, b));
+                }
+    int nbuild = 0;
+    while (nbuild < (int)inner.size() && (inner[nbuild].y < 0 || !fed(inner[nbuild].x, inner[nbuild].y))) ++nbuild;
     if ((int)inner.size() > kMaxInner) return;
     std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> outer;  // (x, y) -> (inner row, column)
     for (int i = 0; i < tt.npairs; ++i)
@@ -1259,6 +1355,9 @@ static void build_fused_job(Plan &p, TcJob &job) {
     for (int e = 0; e < qt.nitems; ++e)
         outer[{qassign[e].second / nb, qassign[e].second % nb}].push_back({pair_row[qassign[e].first],
                                                                           tt.nitems + qt.iout[e]});
+    if (add_extra)
+        for (const auto &k : extra)
+            if (!outer.count(k) && !outer.count({k.second, k.first})) outer[k];
     std::vector<TcPair> hp;
     std::vector<int> iout;
     hp.reserve(outer.size());
@@ -1282,6 +1381,7 @@ static void build_fused_job(Plan &p, TcJob &job) {
     finish_job(p, job, hp, inner, iout);
     if (job.usable)
         p.d_fpart = (double *)p.dalloc((size_t)p.part_blocks * (tt.nitems + qt.nitems) * sizeof(double));
+    if (job.usable) attach_feed(p, job, hp, inner, nbuild);
 }
 
 // Wide orientation tables: left rows (<= 64), right rows, items ordered by
@@ -1386,7 +1486,7 @@ static bool launch_wide(Plan &p, const float *islab, long long npts, long long s
 // fused): built, usable, outer tiles (largest CTA group), inner rows, Npad,
 // and of its latest launch the merged flag and points per step / 64.
 void tc_job_info(Plan &p, int which, int32_t *out) {
-    for (int i = 0; i < 10; ++i) out[i] = 0;
+    for (int i = 0; i < 11; ++i) out[i] = 0;
     if (!p.tc) return;
     TcState &st = *reinterpret_cast<TcState *>(p.tc);
     const TcJob &j = which == 0 ? st.trip : which == 1 ? st.quad : st.fused;
@@ -1400,6 +1500,7 @@ void tc_job_info(Plan &p, int which, int32_t *out) {
     out[7] = j.last_nst;
     out[8] = j.last_nsb;
     out[9] = j.last_nstg;
+    out[10] = j.last_bfa;
 }
 
 int *tc_error_flag(Plan &p) { return p.root().d_errbuf; }
@@ -1515,6 +1616,10 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     job.last_nsb = nsb;
     job.last_nstg = nstg;
     job.last_nst = nst;
+    // inner pair rows from operand A: one pair tile (so one CTA group), 16 producer warps
+    const int *ifeed = (job.d_ifeed && p.tc_bfroma == 0 && aw == 16 && ngrp == 1) ? job.d_ifeed : nullptr;
+    const int nbuild = ifeed ? job.nsingle : job.ninner;
+    job.last_bfa = ifeed ? 1 : 0;
 #define FBS_TC_LAUNCH(A, S, W, K)                                                                     \
     if (nst == A && nstg == S && aw == W && ka == K) {                                                \
         launched = true;                                                                              \
@@ -1523,7 +1628,7 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
         contract_tc_kernel<A, S, W, K><<<grid, kTcThreads, sm, p.stream>>>(                          \
             fmap, npts, p.nbins, job.Npad, tstr, job.ninner, job.d_inner, job.d_pairs, job.npairs,      \
             job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err, tc_wait_limit(p),     \
-            p.part_blocks, merged, nsb);                                                              \
+            p.part_blocks, merged, nsb, ifeed, nbuild);                                               \
     }
     bool launched = false;
     FBS_TC_LAUNCH(2, 2, 16, 1)

@@ -610,6 +610,7 @@ static Plan *new_level(Plan &root, int M) {
     lv->tc_pairs = root.tc_pairs;
     lv->tc_merge = root.tc_merge;
     lv->tc_bstages = root.tc_bstages;
+    lv->tc_bfroma = root.tc_bfroma;
     lv->tc_wait_limit = root.tc_wait_limit;
     lv->d_box = root.d_box;
     root.levels.push_back(lv);
@@ -1666,6 +1667,10 @@ static bool set_plan_option(Plan *plan, int option, int value) {
     }
     if (option == FBS_OPT_TC_BSTAGES && (value == 0 || (value >= 2 && value <= 4))) {
         plan->tc_bstages = value;
+        return true;
+    }
+    if (option == FBS_OPT_TC_BFROMA && (value == 0 || value == 1)) {
+        plan->tc_bfroma = value;
         return true;
     }
     if (option == FBS_OPT_TC_PAIRS && (value == 0 || value == 1)) {

@@ -304,3 +304,31 @@ def test_operand_b_stage_depths_give_identical_sums(quads, N, nb, roles):
             check_trispectrum(plan, out[4][2], f32, L, edges, 2e-4)
         if N <= 64 and nb <= 16:
             check_bispectrum(plan, out[4][0], out[4][1], f32, L, edges, "bf16x3")
+
+
+@pytest.mark.parametrize("N,nb,kind", [(48, 10, "lin"), (96, 8, "lin"), (64, 16, "log")])
+def test_inner_pairs_from_operand_a_are_identical(N, nb, kind):
+    """FBS_OPT_TC_BFROMA 0 (in a one-tile trispectrum pass the operand-A
+    warps also store each inner pair row's product into operand B) and 1
+    (every inner row built from the field stage) form the same FP32 products
+    and splits: bit-identical sums that match the oracle, and diagnostics
+    that say which launch took the inner pairs from operand A."""
+    import torch
+    L = float(N)
+    edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
+    f32 = _field("quadratic", N, 36).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    out, used = {}, {}
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=True) as plan:
+        for opt in (0, 1):
+            plan.set_option(fbs.FBS_OPT_TC_BFROMA, opt)
+            T, B, P = plan.trispectrum(f)
+            torch.cuda.synchronize()
+            plan.check()
+            out[opt] = (B.cpu().numpy(), T.cpu().numpy())
+            used[opt] = [lvl["fused"]["b_from_a"] for lvl in plan.tc_info() if "fused" in lvl]
+        assert used[1] and not any(used[1])
+        assert any(used[0]), used
+        assert np.array_equal(out[0][0], out[1][0])
+        assert np.array_equal(out[0][1], out[1][1])
+        check_trispectrum(plan, out[0][1], f32, L, edges, 2e-4)
