@@ -39,7 +39,9 @@
 
 #include <algorithm>
 #include <array>
+#include <iterator>
 #include <map>
+#include <set>
 #include <utility>
 
 #include "fbs_internal.h"
@@ -423,7 +425,7 @@ __device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes,
 // KA: 64-point K-atoms per chunk (1 or 2): a chunk is 64 KA points, staged as
 // 2 KA TMA boxes of 32 points, with one swizzled B tile per atom and A stages
 // of 64 KA tensor-memory columns.
-template <int NST, int NSTG, int AW, int KA>
+template <int NST, int NSTG, int AW, int KA, bool FEED>
 __global__ void __launch_bounds__(kTcThreads, 1)
     contract_tc_kernel(const __grid_constant__ CUtensorMap fmap, long long npts, int nbins, int Npad,
                        int tstride, int ninner, const int2 *__restrict__ inner,
@@ -433,6 +435,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        int *__restrict__ err, long long wait_limit, int part_rows, int merged, int nsb,
                        const int *__restrict__ ifeed, int nbuild) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
+    static_assert(!FEED || AW == 16, "inner pair rows from operand A: the A warps build operand B");
     static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
     constexpr int KCH = KC * KA;          // points per chunk
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     volatile int *abortp = &abort_flag;
 
     const long long nchunks = (npts + KCH - 1) / KCH;
-    const bool bfa = BW == 0 && ifeed != nullptr;  // the host passes ifeed with one pair tile only
+    constexpr bool bfa = FEED;  // the host launches FEED with ifeed and one pair tile only
     const long long c0 = nchunks * blockIdx.x / gridDim.x;
     const long long c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
 
@@ -754,7 +757,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     }
                     tmem_st8a(lanebase + col + 8u * c, hw);
                     tmem_st8a(lanebase + col + 32u * KA + 8u * c, lw);
-                    if (BW == 0 && feed >= 0) {
+                    if (FEED && feed >= 0) {
                         // the same product is inner row `feed`: its 8-point groups
                         // PPT kq / 8 + 2c (hw[0..3]) and + 1 (hw[4..7]) go to operand B
                         unsigned char *bh = Bh0 + 2 * rb.slot * b_stage;
@@ -771,13 +774,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
-                if (BW == 0 && bfa) fence_proxy_async_smem();  // operand B's stores, for the MMAs
+                if (FEED) fence_proxy_async_smem();  // operand B's stores, for the MMAs
                 __syncwarp();
                 if (lane == 0) {
-                    if (BW == 0 && bfa) mbar_arrive(&bars.bfull[rb.slot]);
+                    if (FEED) mbar_arrive(&bars.bfull[rb.slot]);
                     mbar_arrive(&bars.full[as]);
                 }
-                if (BW == 0 && bfa) rb.next();
+                if (FEED) rb.next();
                 ra.next();
             }
             // ---- the stage is consumed: hand it back to the loader
@@ -1331,20 +1334,45 @@ static void build_fused_job(Plan &p, TcJob &job) {
     const bool add_extra = nouter + extra.size() <= 128;
     if (add_extra)
         for (const auto &k : extra) mark(k.first, k.second);
-    // inner rows: single bins, then the pairs built from the field stage, then the fed pairs
+    // inner rows: single bins, then the pairs built from the field stage, then
+    // the fed pairs in the order of their outer rows (the outer rows are the
+    // keys of `outer` below in ascending order), so that the operand-A lanes
+    // of a warp store consecutive inner rows (distinct swizzle positions)
+    std::set<std::pair<int, int>> okeys;
+    for (int i = 0; i < tt.npairs; ++i) okeys.insert({tt.pb[i], tt.pc[i]});
+    for (int e = 0; e < qt.nitems; ++e) okeys.insert({qassign[e].second / nb, qassign[e].second % nb});
+    if (add_extra)
+        for (const auto &k : extra)
+            if (!okeys.count(k) && !okeys.count({k.second, k.first})) okeys.insert(k);
     std::vector<int2> inner;
     for (int b = 0; b < nb; ++b)
         if (bin_row[b] >= 0) {
             bin_row[b] = (int)inner.size();
             inner.push_back(make_int2(b, -1));
         }
-    for (int pass = 0; pass < 2; ++pass)
+    for (int a = 0; a < nb; ++a)
+        for (int b = 0; b < nb; ++b)
+            if (pair_row[(size_t)a * nb + b] >= 0 && !fed(a, b)) {
+                pair_row[(size_t)a * nb + b] = (int)inner.size();
+                inner.push_back(make_int2(a, b));
+            }
+    {
+        std::vector<std::pair<int, int>> fed_pairs;  // (outer rank, a * nb + b)
         for (int a = 0; a < nb; ++a)
             for (int b = 0; b < nb; ++b)
-                if (pair_row[(size_t)a * nb + b] >= 0 && fed(a, b) == (pass == 1)) {
-                    pair_row[(size_t)a * nb + b] = (int)inner.size();
-                    inner.push_back(make_int2(a, b));
+                if (pair_row[(size_t)a * nb + b] >= 0 && fed(a, b)) {
+                    auto it = okeys.find({a, b});
+                    if (it == okeys.end()) it = okeys.find({b, a});
+                    fed_pairs.push_back({it == okeys.end() ? (int)okeys.size()
+                                                           : (int)std::distance(okeys.begin(), it),
+                                         a * nb + b});
                 }
+        std::sort(fed_pairs.begin(), fed_pairs.end());
+        for (const auto &f : fed_pairs) {
+            pair_row[(size_t)f.second] = (int)inner.size();
+            inner.push_back(make_int2(f.second / nb, f.second % nb));
+        }
+    }
     int nbuild = 0;
     while (nbuild < (int)inner.size() && (inner[nbuild].y < 0 || !fed(inner[nbuild].x, inner[nbuild].y))) ++nbuild;
     if ((int)inner.size() > kMaxInner) return;
@@ -1616,33 +1644,38 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     job.last_nsb = nsb;
     job.last_nstg = nstg;
     job.last_nst = nst;
-    // inner pair rows from operand A: one pair tile (so one CTA group), 16 producer warps
-    const int *ifeed = (job.d_ifeed && p.tc_bfroma == 0 && aw == 16 && ngrp == 1) ? job.d_ifeed : nullptr;
+    // inner pair rows from operand A: one pair tile (so one CTA group), 16
+    // producer warps, 128-point steps
+    const int *ifeed = (job.d_ifeed && p.tc_bfroma == 0 && aw == 16 && ka == 2 && ngrp == 1) ? job.d_ifeed : nullptr;
     const int nbuild = ifeed ? job.nsingle : job.ninner;
     job.last_bfa = ifeed ? 1 : 0;
-#define FBS_TC_LAUNCH(A, S, W, K)                                                                     \
-    if (nst == A && nstg == S && aw == W && ka == K) {                                                \
+#define FBS_TC_LAUNCH(A, S, W, K, F)                                                                  \
+    if (nst == A && nstg == S && aw == W && ka == K && (ifeed != nullptr) == F) {                   \
         launched = true;                                                                              \
-        FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S, W, K>,                                 \
+        FBS_CUDA(cudaFuncSetAttribute(contract_tc_kernel<A, S, W, K, F>,                                 \
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));          \
-        contract_tc_kernel<A, S, W, K><<<grid, kTcThreads, sm, p.stream>>>(                          \
+        contract_tc_kernel<A, S, W, K, F><<<grid, kTcThreads, sm, p.stream>>>(                          \
             fmap, npts, p.nbins, job.Npad, tstr, job.ninner, job.d_inner, job.d_pairs, job.npairs,      \
             job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err, tc_wait_limit(p),     \
             p.part_blocks, merged, nsb, ifeed, nbuild);                                               \
     }
     bool launched = false;
-    FBS_TC_LAUNCH(2, 2, 16, 1)
-    FBS_TC_LAUNCH(2, 4, 16, 1)
-    FBS_TC_LAUNCH(3, 2, 16, 1)
-    FBS_TC_LAUNCH(3, 4, 16, 1)
-    FBS_TC_LAUNCH(2, 2, 8, 1)
-    FBS_TC_LAUNCH(2, 4, 8, 1)
-    FBS_TC_LAUNCH(3, 2, 8, 1)
-    FBS_TC_LAUNCH(3, 4, 8, 1)
-    FBS_TC_LAUNCH(2, 2, 16, 2)
-    FBS_TC_LAUNCH(2, 4, 16, 2)
-    FBS_TC_LAUNCH(3, 2, 16, 2)
-    FBS_TC_LAUNCH(3, 4, 16, 2)
+    FBS_TC_LAUNCH(2, 2, 16, 1, false)
+    FBS_TC_LAUNCH(2, 4, 16, 1, false)
+    FBS_TC_LAUNCH(3, 2, 16, 1, false)
+    FBS_TC_LAUNCH(3, 4, 16, 1, false)
+    FBS_TC_LAUNCH(2, 2, 8, 1, false)
+    FBS_TC_LAUNCH(2, 4, 8, 1, false)
+    FBS_TC_LAUNCH(3, 2, 8, 1, false)
+    FBS_TC_LAUNCH(3, 4, 8, 1, false)
+    FBS_TC_LAUNCH(2, 2, 16, 2, false)
+    FBS_TC_LAUNCH(2, 2, 16, 2, true)
+    FBS_TC_LAUNCH(2, 4, 16, 2, false)
+    FBS_TC_LAUNCH(2, 4, 16, 2, true)
+    FBS_TC_LAUNCH(3, 2, 16, 2, false)
+    FBS_TC_LAUNCH(3, 2, 16, 2, true)
+    FBS_TC_LAUNCH(3, 4, 16, 2, false)
+    FBS_TC_LAUNCH(3, 4, 16, 2, true)
 #undef FBS_TC_LAUNCH
     if (!launched) throw Failure{FBS_ERR_STATE, "tensor-core contraction: no kernel for this pipeline shape"};
     FBS_CUDA(cudaGetLastError());
