@@ -230,7 +230,15 @@ enum {
                             product into operand B as well, so operand B is
                             built from the field stage for the single-bin rows
                             only; 1: every inner row is built from the field
-                            stage.  Sums are identical. */
+                            stage.  Sums are identical. */,
+    FBS_OPT_TC_STACK = 10     /* BF16x3 tensor-core contraction of a job with one
+                            tile of at most 64 outer pairs: 0 (default) operand
+                            A holds the pairs' hi parts in rows 0..63 and their
+                            lo parts in rows 64..127, so one MMA per K step
+                            (N = 2 Npad) forms hi*hi, hi*lo, lo*hi and lo*lo;
+                            1: two MMAs per K step (hi*hi, hi*lo, lo*hi).  The
+                            sums agree within the precision's rounding (the
+                            stacked form adds the lo*lo products). */
 };
 
 /* Set a plan option; FBS_ERR_ARG for an unknown option or value. */
@@ -309,11 +317,12 @@ fbs_status fbs_trispectrum_connected(fbs_plan *plan, const float *field, double 
  * available after an evaluation has built it: info[11] = {built, usable,
  * outer 128-row tiles of the largest CTA group, inner rows, inner rows padded
  * (N of the MMA), 1 when the latest launch put the hi and lo rows in one MMA
- * (FBS_OPT_TC_MERGE) else 0 (-1 before any launch), 64-point K-atoms per
+ * (FBS_OPT_TC_MERGE), 2 when it also stacked operand A's hi and lo rows on M
+ * (FBS_OPT_TC_STACK), else 0 (-1 before any launch), 64-point K-atoms per
  * pipeline step of that launch, its operand-A stages in tensor memory, its
- * operand-B stages and its field stages in shared memory, 1 when it took the
- * inner pair rows from operand A (FBS_OPT_TC_BFROMA)}.  FBS_ERR_ARG for a bad
- * level or job.
+ * operand-B stages and its field stages in shared memory, the number of
+ * inner pair rows it took from operand A (FBS_OPT_TC_BFROMA; 0: none)}.
+ * FBS_ERR_ARG for a bad level or job.
  */
 fbs_status fbs_plan_tc_info(const fbs_plan *plan, int level, int which, int32_t *info);
 

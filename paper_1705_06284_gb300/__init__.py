@@ -46,6 +46,7 @@ FBS_OPT_SLAB_PLANES = 6
 FBS_OPT_TC_MERGE = 7
 FBS_OPT_TC_BSTAGES = 8
 FBS_OPT_TC_BFROMA = 9
+FBS_OPT_TC_STACK = 10
 
 _PREC = {"fp32": FBS_PREC_FP32, "bf16x3": FBS_PREC_BF16X3, "bf16": FBS_PREC_BF16}
 
@@ -343,7 +344,7 @@ class Plan:
         """Tensor-core job shapes per level (after an evaluation): a list of
         {job: dict(tiles, inner, Npad, merged, ka, stages)} for the built jobs
         (stages: operand-A, operand-B and field pipeline depths; b_from_a:
-        inner pair rows stored by the operand-A warps)."""
+        the inner pair rows stored by the operand-A warps)."""
         out = []
         for lvl in range(len(self.levels)):
             d = {}

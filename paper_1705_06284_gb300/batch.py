@@ -53,6 +53,7 @@ TUNABLE = (
     ("merge", 7, (0, 1)),       # FBS_OPT_TC_MERGE: hi and lo rows of B in one MMA where they fit / never
     ("bstages", 8, (0, 2)),     # FBS_OPT_TC_BSTAGES: deepest operand-B ring that fits / two stages
     ("bfroma", 9, (0, 1)),      # FBS_OPT_TC_BFROMA: inner pair rows from operand A where it applies / never
+    ("stack", 10, (0, 1)),      # FBS_OPT_TC_STACK: A's hi and lo stacked on M where it applies / never
 )
 
 
@@ -112,7 +113,7 @@ def autotune(plan: Plan, field, repeats: int = 3, cache: str = _TUNE_CACHE, batc
                 if tried[k] < 0.98 * best_ms:
                     best, best_ms = cand, tried[k]
     elif not batch:  # the FP32 contraction has no tensor-core options: slabs only
-        for v in TUNABLE[-1][2][1:]:
+        for v in next(vals for name, _, vals in TUNABLE if name == "slab")[1:]:
             cand = dict(best, slab=v)
             ms = timed(cand)
             if ms < 0.98 * best_ms:

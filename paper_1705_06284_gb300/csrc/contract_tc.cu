@@ -18,10 +18,18 @@
 //     accumulators in tensor memory, one 128 x Npad block per pair tile; the
 //     hi and lo rows of B sit side by side in each K-atom, so where the
 //     doubled accumulators fit, A_hi x [B_hi; B_lo] (N = 2 Npad) and A_lo x
-//     B_hi take two MMAs per K step instead of three;
+//     B_hi take two MMAs per K step instead of three, and a single tile of
+//     at most 64 pairs stacks A's hi and lo rows on M for one MMA per K step
+//     (which also forms lo*lo);
 //   * every 1,024 points the producers read the accumulators back
 //     (tcgen05.ld) into compensated (Kahan) FP32 sums per item in shared
-//     memory.
+//     memory, after the next step's operands are handed off.
+// An MMA of M = 128 and K = 16 occupies the issuing thread for about 100
+// cycles whatever N is up to 160 (measured), so the fewer and wider the MMAs
+// the better; the producers run up to three steps ahead of them (operand-B
+// ring of up to 4 stages).  In a single-tile trispectrum pass the inner pair
+// rows that are outer rows too are stored into operand B by the operand-A
+// warps that form the same products.
 // Each CTA owns a contiguous range of points; its sums go to its own row of
 // the FP64 partial buffer, reduced across CTAs in a fixed order.  Which of a
 // triplet's (or quadruplet's) pairs forms the outer row is chosen by a greedy
@@ -78,7 +86,7 @@ struct TcJob {
     int *d_ifeed = nullptr;  // single-tile jobs: per outer row, the inner pair row of the same product, or -1
     int nsingle = 0;         // inner rows built from the field stage with d_ifeed (a prefix of the inner rows)
     int last_merged = -1, last_ka = 0;  // MMA shape of the latest launch (diagnostics)
-    int last_bfa = 0;                   // the latest launch took inner pair rows from operand A
+    int last_bfa = 0;                   // inner pair rows the latest launch took from operand A
     int last_nsb = 0, last_nstg = 0, last_nst = 0;  // its B, field and A stage counts
 };
 
@@ -415,6 +423,11 @@ __device__ __forceinline__ void build_b(const unsigned char *st, int half_bytes,
 // grid: (G point-range CTAs, groups of pair tiles).  One CTA per SM.
 // NST: A stages in tensor memory; NSTG: field stages in shared memory;
 // nsb (launch parameter, 2..4): operand-B stages in shared memory.
+// stacked (one pair tile of at most 64 pairs, BF16x3, merged B): operand A
+// holds hi of pair r in row r and lo of pair r in row r + 64 (the warps of
+// lane quarters 2 and 3 form the same products), so one MMA per K step with
+// N = 2 Npad gives hi*hi, hi*lo (rows 0..63) and lo*hi, lo*lo (rows
+// 64..127); rows r + 64 are summed into a second set of compensated sums.
 // ifeed (null, or with a single pair tile and AW = 16): per outer row, the
 // inner pair row with the same product (-1: none); the operand-A thread of
 // that row also stores its hi/lo values into operand B, and the operand-B
@@ -433,11 +446,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                        const int *__restrict__ grp_tile0, const int *__restrict__ iout,
                        int nitems_total, double *__restrict__ part, int x3, int flush_every,
                        int *__restrict__ err, long long wait_limit, int part_rows, int merged, int nsb,
-                       const int *__restrict__ ifeed, int nbuild) {
+                       const int *__restrict__ ifeed, int nbuild, int stacked_arg) {
     static_assert(AW == 16 || AW == 8, "A-operand warps: 16 or 8");
     static_assert(!FEED || AW == 16, "inner pair rows from operand A: the A warps build operand B");
     static_assert(KA == 1 || KA == 2, "K-atoms per chunk: 1 or 2");
     constexpr int BW = kProdWarps - AW;   // operand-B warps (0: the A warps build it)
+    const int stacked = FEED ? 0 : stacked_arg;  // the host never stacks with the feed
     constexpr int KCH = KC * KA;          // points per chunk
     constexpr int PPT = 4 * KCH / AW;     // points of a row per A thread per tile
     constexpr int ACOLS = kAStageCols * KA;  // tensor-memory columns of one A stage
@@ -474,7 +488,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int stage_bytes = 2 * KA * half_bytes;
     unsigned char *const stg = sm + 2 * nsb * b_stage;
     float2 *acc = reinterpret_cast<float2 *>(stg + NSTG * stage_bytes);
-    int2 *pbc = reinterpret_cast<int2 *>(acc + nloc);  // (b, c) of every row of every tile
+    float2 *acc2 = acc + nloc;  // stacked: the sums of rows 64..127 (lo * B)
+    int2 *pbc = reinterpret_cast<int2 *>(acc + (stacked ? 2 : 1) * nloc);  // (b, c) of every row of every tile
 
     const int acc_cols = ((ntl * tstride + 31) / 32) * 32;
     const int tmem_cols_needed = acc_cols + NST * ACOLS;
@@ -506,7 +521,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < nloc; i += kTcThreads) acc[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < (stacked ? 2 : 1) * nloc; i += kTcThreads) acc[i] = make_float2(0.f, 0.f);
     for (int i = tid; i < ninner; i += kTcThreads) s_inner[i] = inner[i];
     for (int i = tid; i < ntl * 128; i += kTcThreads) {
         const int p = p_first + i;
@@ -589,7 +604,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         // merged: A_hi x [B_hi; B_lo] (N = 2 Npad) accumulates hi*hi in
                         // columns [0, Npad) and hi*lo in [Npad, 2 Npad); A_lo x B_hi adds
                         // lo*hi to the first half: two MMAs per k-step instead of three.
-                        if (merged) {
+                        if (stacked) {  // rows 0..63 hi, 64..127 lo of A: one MMA per k-step
+                            if (fresh) mma_ts<false>(d, ah, dbh, idesc2);
+                            else mma_ts<true>(d, ah, dbh, idesc2);
+#pragma unroll
+                            for (int k = 1; k < 4 * KA; ++k) {
+                                const uint64_t bo = datom * (uint64_t)(k >> 2) + 2u * (k & 3);
+                                mma_ts<true>(d, ah + 8u * k, dbh + bo, idesc2);
+                            }
+                        } else if (merged) {
                             if (fresh) mma_ts<false>(d, ah, dbh, idesc2);
                             else mma_ts<true>(d, ah, dbh, idesc2);
                             mma_ts<true>(d, al, dbh, idesc);
@@ -662,6 +685,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int q = warp & 3, kq = warp >> 2;  // lane quarter, PPT-point slice of the chunk
         const int r = 32 * q + lane;             // operand-A row (TMEM lane) of this thread
         const int feed = bfa ? ifeed[r] : -1;    // inner row with this row's product (single tile)
+        // A warp whose 32 rows are all padding of the only pair tile zeroes its
+        // lanes of every A stage once here; nothing rewrites them (the MMAs only
+        // read A), so in the loop it takes part in the hand-offs only.
+        const bool idle = !stacked && ntl == 1 && 32 * q >= npairs - t0 * 128;
         Ring<NSTG> rs;
         Ring<NST> ra;
         RingN rb(nsb);
@@ -671,9 +698,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         auto flush = [&]() {
             role_wait(&bars.accr, (uint32_t)(nfl & 1), abortp, err, 23, wait_limit);
             tc_fence_after();
-            if (!*abortp) {
+            if (!*abortp && !idle) {
+                float2 *const sums = stacked && r >= 64 ? acc2 : acc;
                 for (int lt = 0; lt < ntl; ++lt) {
-                    const int p = (t0 + lt) * 128 + r;
+                    const int p = (t0 + lt) * 128 + (stacked ? (r & 63) : r);
                     const bool valid = p < npairs;
                     const TcPair *pp = pairs + (valid ? p : 0);
                     for (int c8 = 8 * kq; c8 < Npad; c8 += 8 * (AW / 4)) {
@@ -694,7 +722,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int m = 0; m < wsel; ++m) idx += __popc(__ldg(&pp->mask[m]));
 #pragma unroll
                         for (int i = 0; i < 8; ++i)
-                            if ((w >> i) & 1u) kahan_add(acc[idx++], v[i]);
+                            if ((w >> i) & 1u) kahan_add(sums[idx++], v[i]);
                     }
                 }
             }
@@ -724,55 +752,63 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int as = ra.slot;
                 if (ra.warm) role_wait(&bars.empty[as], ra.phase ^ 1u, abortp, err, 22, wait_limit);
                 tc_fence_after();
-                const int2 bc = pbc[lt * 128 + r];
-                const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
-                const uint32_t col = (uint32_t)(acc_cols + as * ACOLS + (PPT / 2) * kq);
-                // This thread's 16-byte chunks of the step are J0 + k, k < PPT / 4,
-                // J0 = (PPT/4) kq a multiple of 4 that never carries into the next
-                // 32-point box.  The stage row of bin b holds chunk J at
-                // ((J & 7) ^ (b & 7)) << 4 of box J >> 3, so every address is the
-                // row's base XOR a compile-time offset.
-                const int J0 = (PPT / 4) * kq;
-                const unsigned char *rb0 = st + (J0 >> 3) * half_bytes + (bc.x >= 0 ? bc.x : 0) * 128;
-                const unsigned char *rc0 = st + (J0 >> 3) * half_bytes + (bc.y >= 0 ? bc.y : 0) * 128;
-                const uint32_t xb = (uint32_t)(((bc.x & 7) ^ (J0 & 7)) << 4);
-                const uint32_t xc = (uint32_t)(((bc.y & 7) ^ (J0 & 7)) << 4);
-                // 16 points (8 columns of hi, 8 of lo) at a time
+                if (!idle) {
+                    const int2 bc = pbc[lt * 128 + (stacked ? (r & 63) : r)];
+                    const uint32_t lanebase = tmem + ((uint32_t)(32 * q) << 16);
+                    const uint32_t col = (uint32_t)(acc_cols + as * ACOLS + (PPT / 2) * kq);
+                    // This thread's 16-byte chunks of the step are J0 + k, k < PPT / 4,
+                    // J0 = (PPT/4) kq a multiple of 4 that never carries into the next
+                    // 32-point box.  The stage row of bin b holds chunk J at
+                    // ((J & 7) ^ (b & 7)) << 4 of box J >> 3, so every address is the
+                    // row's base XOR a compile-time offset.
+                    const int J0 = (PPT / 4) * kq;
+                    const unsigned char *rb0 = st + (J0 >> 3) * half_bytes + (bc.x >= 0 ? bc.x : 0) * 128;
+                    const unsigned char *rc0 = st + (J0 >> 3) * half_bytes + (bc.y >= 0 ? bc.y : 0) * 128;
+                    const uint32_t xb = (uint32_t)(((bc.x & 7) ^ (J0 & 7)) << 4);
+                    const uint32_t xc = (uint32_t)(((bc.y & 7) ^ (J0 & 7)) << 4);
+                    // 16 points (8 columns of hi, 8 of lo) at a time
 #pragma unroll
-                for (int c = 0; c < PPT / 16; ++c) {
-                    uint32_t hw[8], lw[8];
-                    if (bc.x >= 0) {
+                    for (int c = 0; c < PPT / 16; ++c) {
+                        uint32_t hw[8], lw[8];
+                        if (bc.x >= 0) {
 #pragma unroll
-                        for (int j = 0; j < 2; ++j) {
-                            const uint32_t k0 = (uint32_t)((4 * c + 2 * j) << 4), k1 = k0 + 16u;
-                            const float4 b0 = *reinterpret_cast<const float4 *>(rb0 + (k0 ^ xb));
-                            const float4 b1 = *reinterpret_cast<const float4 *>(rb0 + (k1 ^ xb));
-                            const float4 e0 = *reinterpret_cast<const float4 *>(rc0 + (k0 ^ xc));
-                            const float4 e1 = *reinterpret_cast<const float4 *>(rc0 + (k1 ^ xc));
-                            mul_split8(b0, b1, e0, e1, hw + 4 * j, lw + 4 * j);
+                            for (int j = 0; j < 2; ++j) {
+                                const uint32_t k0 = (uint32_t)((4 * c + 2 * j) << 4), k1 = k0 + 16u;
+                                const float4 b0 = *reinterpret_cast<const float4 *>(rb0 + (k0 ^ xb));
+                                const float4 b1 = *reinterpret_cast<const float4 *>(rb0 + (k1 ^ xb));
+                                const float4 e0 = *reinterpret_cast<const float4 *>(rc0 + (k0 ^ xc));
+                                const float4 e1 = *reinterpret_cast<const float4 *>(rc0 + (k1 ^ xc));
+                                mul_split8(b0, b1, e0, e1, hw + 4 * j, lw + 4 * j);
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) hw[j] = lw[j] = 0u;
                         }
-                    } else {
+                        if (!stacked) {
+                            tmem_st8a(lanebase + col + 8u * c, hw);
+                            tmem_st8a(lanebase + col + 32u * KA + 8u * c, lw);
+                        } else if (q < 2) {  // stacked: the hi words in rows 0..63, the lo words in 64..127
+                            tmem_st8a(lanebase + col + 8u * c, hw);
+                        } else {
+                            tmem_st8a(lanebase + col + 8u * c, lw);
+                        }
+                        if (FEED && feed >= 0) {
+                            // the same product is inner row `feed`: its 8-point groups
+                            // PPT kq / 8 + 2c (hw[0..3]) and + 1 (hw[4..7]) go to operand B
+                            unsigned char *bh = Bh0 + 2 * rb.slot * b_stage;
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) hw[j] = lw[j] = 0u;
-                    }
-                    tmem_st8a(lanebase + col + 8u * c, hw);
-                    tmem_st8a(lanebase + col + 32u * KA + 8u * c, lw);
-                    if (FEED && feed >= 0) {
-                        // the same product is inner row `feed`: its 8-point groups
-                        // PPT kq / 8 + 2c (hw[0..3]) and + 1 (hw[4..7]) go to operand B
-                        unsigned char *bh = Bh0 + 2 * rb.slot * b_stage;
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {
-                            const int u = (PPT / 8) * kq + 2 * c + h2;
-                            const uint32_t off = (uint32_t)((u >> 3) * b_atom2) + sw128_off(feed, u & 7);
-                            *reinterpret_cast<uint4 *>(bh + off) =
-                                make_uint4(hw[4 * h2], hw[4 * h2 + 1], hw[4 * h2 + 2], hw[4 * h2 + 3]);
-                            *reinterpret_cast<uint4 *>(bh + b_tile + off) =
-                                make_uint4(lw[4 * h2], lw[4 * h2 + 1], lw[4 * h2 + 2], lw[4 * h2 + 3]);
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                const int u = (PPT / 8) * kq + 2 * c + h2;
+                                const uint32_t off = (uint32_t)((u >> 3) * b_atom2) + sw128_off(feed, u & 7);
+                                *reinterpret_cast<uint4 *>(bh + off) =
+                                    make_uint4(hw[4 * h2], hw[4 * h2 + 1], hw[4 * h2 + 2], hw[4 * h2 + 3]);
+                                *reinterpret_cast<uint4 *>(bh + b_tile + off) =
+                                    make_uint4(lw[4 * h2], lw[4 * h2 + 1], lw[4 * h2 + 2], lw[4 * h2 + 3]);
+                            }
                         }
                     }
+                    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 }
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 if (FEED) fence_proxy_async_smem();  // operand B's stores, for the MMAs
                 __syncwarp();
@@ -812,7 +848,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == kMmaWarp)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
     double *row = part + ((long long)blockIdx.z * part_rows + blockIdx.x) * nitems_total;
-    for (int i = tid; i < nloc; i += kTcThreads) row[iout[it0 + i]] += (double)acc[i].x - (double)acc[i].y;
+    for (int i = tid; i < nloc; i += kTcThreads)
+        row[iout[it0 + i]] += ((double)acc[i].x - (double)acc[i].y) +
+                              (stacked ? (double)acc2[i].x - (double)acc2[i].y : 0.0);
 }
 
 
@@ -1613,6 +1651,16 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
             acc_cols_max = acc2;
         }
     }
+    // inner pair rows from operand A: one pair tile (so one CTA group), 16
+    // producer warps, 128-point steps
+    const int *ifeed = (job.d_ifeed && p.tc_bfroma == 0 && aw == 16 && ka == 2 && ngrp == 1) ? job.d_ifeed : nullptr;
+    // A's hi and lo stacked on M (one MMA per k-step, the lo*lo products too):
+    // one tile of at most 64 pairs with merged B, 16 producer warps, no feed;
+    // its second set of compensated sums doubles the item sums in shared memory
+    int stacked = (merged && !ifeed && p.tc_stack == 0 && aw == 16 && job.ntiles == 1 && ngrp == 1 &&
+                   job.npairs <= 64) ? 1 : 0;
+    if (stacked && tc_smem_bytes(p.nbins, job.Npad, 2 * job.maxloc, job.maxtiles, 2, ka, 2) > 220 * 1024) stacked = 0;
+    const int sums = (stacked ? 2 : 1) * job.maxloc;
     // pipeline depths: 3 A stages when tensor memory allows; operand-B and
     // field stages as shared memory allows, the first of (B, field) = (4, 4),
     // (3, 4), (3, 2), (2, 4), (2, 2) that fits (FBS_OPT_TC_BSTAGES asks for a
@@ -1620,10 +1668,10 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     const int nst = acc_cols_max + 3 * ka * kAStageCols <= 512 ? 3 : 2;
     const int want_nsb = p.tc_bstages;
     const auto fits = [&](int b, int f) {
-        return tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, f, ka, b) <= 220 * 1024;
+        return tc_smem_bytes(p.nbins, job.Npad, sums, job.maxtiles, f, ka, b) <= 220 * 1024;
     };
     static const int order[5][2] = {{4, 4}, {3, 4}, {3, 2}, {2, 4}, {2, 2}};
-    int nsb = 2, nstg = 2;  // fits: the job's tables were sized for it
+    int nsb = 2, nstg = 2;  // fits: the job's tables (and the stacked sums) were sized for it
     const auto pick = [&](int want) {
         for (const auto &o : order)
             if ((!want || o[0] == want) && fits(o[0], o[1])) {
@@ -1634,21 +1682,18 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
         return false;
     };
     if (!pick(want_nsb)) pick(0);
-    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, job.maxloc, job.maxtiles, nstg, ka, nsb);
+    const size_t sm = tc_smem_bytes(p.nbins, job.Npad, sums, job.maxtiles, nstg, ka, nsb);
     const int flush_every = 16 / ka;  // 1024 points in FP32 per flush
     const CUtensorMap fmap = field_tensor_map(islab, npts, slab_stride, p.nbins, nf * p.nbins);
     KTimer tm(p, kclass);
     dim3 grid(G, ngrp, nf);
-    job.last_merged = merged;
+    job.last_merged = stacked ? 2 : merged;
     job.last_ka = ka;
     job.last_nsb = nsb;
     job.last_nstg = nstg;
     job.last_nst = nst;
-    // inner pair rows from operand A: one pair tile (so one CTA group), 16
-    // producer warps, 128-point steps
-    const int *ifeed = (job.d_ifeed && p.tc_bfroma == 0 && aw == 16 && ka == 2 && ngrp == 1) ? job.d_ifeed : nullptr;
     const int nbuild = ifeed ? job.nsingle : job.ninner;
-    job.last_bfa = ifeed ? 1 : 0;
+    job.last_bfa = ifeed ? job.ninner - job.nsingle : 0;
 #define FBS_TC_LAUNCH(A, S, W, K, F)                                                                  \
     if (nst == A && nstg == S && aw == W && ka == K && (ifeed != nullptr) == F) {                   \
         launched = true;                                                                              \
@@ -1657,7 +1702,7 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
         contract_tc_kernel<A, S, W, K, F><<<grid, kTcThreads, sm, p.stream>>>(                          \
             fmap, npts, p.nbins, job.Npad, tstr, job.ninner, job.d_inner, job.d_pairs, job.npairs,      \
             job.d_grp, job.d_iout, nitems_total, part, x3, flush_every, st.d_err, tc_wait_limit(p),     \
-            p.part_blocks, merged, nsb, ifeed, nbuild);                                               \
+            p.part_blocks, merged, nsb, ifeed, nbuild, stacked);                                      \
     }
     bool launched = false;
     FBS_TC_LAUNCH(2, 2, 16, 1, false)

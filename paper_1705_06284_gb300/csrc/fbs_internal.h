@@ -191,6 +191,7 @@ struct Plan {
     int tc_merge = 0;            // FBS_OPT_TC_MERGE: 0 hi and lo rows of B in one MMA where it fits, 1 = never
     int tc_bstages = 0;          // FBS_OPT_TC_BSTAGES: 0 auto, 2..4 operand-B stages where they fit
     int tc_bfroma = 0;           // FBS_OPT_TC_BFROMA: 0 inner pair rows from operand A where it applies, 1 = never
+    int tc_stack = 0;            // FBS_OPT_TC_STACK: 0 A's hi and lo stacked on M where it applies, 1 = never
     long long tc_wait_limit = 0; // FBS_OPT_TC_WAIT_LIMIT: hand-off wait limit in cycles (0 = default)
     cudaStream_t stream = nullptr;
     double create_ms = 0;

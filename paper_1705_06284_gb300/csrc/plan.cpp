@@ -611,6 +611,7 @@ static Plan *new_level(Plan &root, int M) {
     lv->tc_merge = root.tc_merge;
     lv->tc_bstages = root.tc_bstages;
     lv->tc_bfroma = root.tc_bfroma;
+    lv->tc_stack = root.tc_stack;
     lv->tc_wait_limit = root.tc_wait_limit;
     lv->d_box = root.d_box;
     root.levels.push_back(lv);
@@ -1671,6 +1672,10 @@ static bool set_plan_option(Plan *plan, int option, int value) {
     }
     if (option == FBS_OPT_TC_BFROMA && (value == 0 || value == 1)) {
         plan->tc_bfroma = value;
+        return true;
+    }
+    if (option == FBS_OPT_TC_STACK && (value == 0 || value == 1)) {
+        plan->tc_stack = value;
         return true;
     }
     if (option == FBS_OPT_TC_PAIRS && (value == 0 || value == 1)) {

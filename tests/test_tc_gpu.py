@@ -136,6 +136,7 @@ def test_warp_roles_give_identical_results(quads):
     out = {}
     with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
         plan.set_option(fbs.FBS_OPT_TC_CHUNK, 1)  # the same 64-point steps for both
+        plan.set_option(fbs.FBS_OPT_TC_STACK, 1)  # the same MMAs (stacking needs 16 product warps)
         for roles in (1, 2):
             plan.set_option(fbs.FBS_OPT_TC_ROLES, roles)
             if quads:
@@ -320,6 +321,7 @@ def test_inner_pairs_from_operand_a_are_identical(N, nb, kind):
     f = torch.from_numpy(f32).cuda()
     out, used = {}, {}
     with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=True) as plan:
+        plan.set_option(fbs.FBS_OPT_TC_STACK, 1)  # the same MMAs (without the feed a small job stacks)
         for opt in (0, 1):
             plan.set_option(fbs.FBS_OPT_TC_BFROMA, opt)
             T, B, P = plan.trispectrum(f)
@@ -332,3 +334,40 @@ def test_inner_pairs_from_operand_a_are_identical(N, nb, kind):
         assert np.array_equal(out[0][0], out[1][0])
         assert np.array_equal(out[0][1], out[1][1])
         check_trispectrum(plan, out[0][1], f32, L, edges, 2e-4)
+
+
+@pytest.mark.parametrize("quads,N,nb,kind", [(False, 48, 10, "lin"), (False, 64, 12, "log"), (True, 48, 8, "lin")])
+def test_stacked_operand_a_matches_oracle(quads, N, nb, kind):
+    """FBS_OPT_TC_STACK 0 (a tile of at most 64 outer pairs: operand A's hi
+    rows in 0..63 and lo rows in 64..127, one MMA per K step that also forms
+    the lo*lo products) and 1 (two MMAs per K step) both meet the BF16x3 gate
+    against the oracle and agree to rounding; the diagnostics report the
+    stacked launches (merged = 2).  The trispectrum case turns the operand-A
+    feed off (the two exclude each other)."""
+    import torch
+    L = float(N)
+    edges = fields.linear_edges(N, L, nb) if kind == "lin" else fields.log_edges(N, L, nb)
+    f32 = _field("quadratic", N, 37).astype(np.float32)
+    f = torch.from_numpy(f32).cuda()
+    out, shape = {}, {}
+    with fbs.Plan(N, L, edges, precision="bf16x3", trispectrum=quads) as plan:
+        plan.set_option(fbs.FBS_OPT_TC_BFROMA, 1)
+        for stack in (0, 1):
+            plan.set_option(fbs.FBS_OPT_TC_STACK, stack)
+            if quads:
+                T, B, P = plan.trispectrum(f)
+            else:
+                B, P = plan.bispectrum(f)
+                T = None
+            torch.cuda.synchronize()
+            plan.check()
+            out[stack] = (B.cpu().numpy(), P.cpu().numpy(), None if T is None else T.cpu().numpy())
+            shape[stack] = [j["merged"] for lvl in plan.tc_info() for j in lvl.values()]
+        assert 2 in shape[0], shape
+        assert 2 not in shape[1], shape
+        for stack in (0, 1):
+            check_bispectrum(plan, out[stack][0], out[stack][1], f32, L, edges, "bf16x3")
+            if quads:
+                check_trispectrum(plan, out[stack][2], f32, L, edges, 2e-4)
+        big = np.abs(out[1][0]) > 1e-3 * np.abs(out[1][0]).max()
+        assert np.all(np.abs(out[0][0] - out[1][0])[big] <= 2e-4 * np.abs(out[1][0][big]) + 1e-6 * np.abs(out[1][0]).max())
