@@ -711,10 +711,10 @@ def _closed_triplets_oracle(N, thr):
 # bench's launch by its points.  A kernel class without a capture of its
 # current build has no entry (the roofline's traffic is then null).
 NCU_TRAFFIC_RATIO = {
-    "contract_tc": ((768.712448e6 + 3.629824e6) / (54 * 3538944 * 4.0),
+    "contract_tc": ((768.424448e6 + 3.262976e6) / (54 * 3538944 * 4.0),
                     "ncu DRAM bytes of the bispectrum pass at 256^3, level M = 192, 54 bins, 3,538,944 points "
                     "(the bispectrum-pass capture of the current build), scaled by points"),
-    "contract_quad_tc": ((540.189952e6 + 3.630080e6) / (16 * 8388608 * 4.0),
+    "contract_quad_tc": ((540.220672e6 + 3.666944e6) / (16 * 8388608 * 4.0),
                          "ncu DRAM bytes of the fused triplet+quadruplet pass at 256^3, 16 log bins, "
                          "8,388,608 points (the trispectrum-pass capture of the current build), scaled by points"),
 }

@@ -219,8 +219,8 @@ enum {
                             The sums agree within the precision's rounding. */,
     FBS_OPT_TC_BSTAGES = 8    /* shared-memory stages of the tensor-core
                             contraction's inner operand: 0 (default) the first
-                            of (B, field) stage depths (4, 4), (3, 4), (3, 2),
-                            (2, 4), (2, 2) that fits in shared memory; 2, 3 or
+                            of (B, field) stage depths (4, 4), (3, 4), (2, 4),
+                            (3, 2), (2, 2) that fits in shared memory; 2, 3 or
                             4: that many B stages where they fit (else the
                             default).  Sums are identical. */,
     FBS_OPT_TC_BFROMA = 9     /* inner pair rows of the tensor-core contraction

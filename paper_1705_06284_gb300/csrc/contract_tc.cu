@@ -1663,14 +1663,15 @@ static void launch_job(Plan &p, TcJob &job, const float *islab, long long npts, 
     const int sums = (stacked ? 2 : 1) * job.maxloc;
     // pipeline depths: 3 A stages when tensor memory allows; operand-B and
     // field stages as shared memory allows, the first of (B, field) = (4, 4),
-    // (3, 4), (3, 2), (2, 4), (2, 2) that fits (FBS_OPT_TC_BSTAGES asks for a
-    // B depth)
+    // (3, 4), (2, 4), (3, 2), (2, 2) that fits (FBS_OPT_TC_BSTAGES asks for a
+    // B depth; with many bins four field stages measured faster than a third
+    // B stage)
     const int nst = acc_cols_max + 3 * ka * kAStageCols <= 512 ? 3 : 2;
     const int want_nsb = p.tc_bstages;
     const auto fits = [&](int b, int f) {
         return tc_smem_bytes(p.nbins, job.Npad, sums, job.maxtiles, f, ka, b) <= 220 * 1024;
     };
-    static const int order[5][2] = {{4, 4}, {3, 4}, {3, 2}, {2, 4}, {2, 2}};
+    static const int order[5][2] = {{4, 4}, {3, 4}, {2, 4}, {3, 2}, {2, 2}};
     int nsb = 2, nstg = 2;  // fits: the job's tables (and the stacked sums) were sized for it
     const auto pick = [&](int want) {
         for (const auto &o : order)
