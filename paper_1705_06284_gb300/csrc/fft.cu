@@ -700,6 +700,77 @@ __global__ void __launch_bounds__(T *LP) inv_y_reg_kernel(const float2 *__restri
     }
 }
 
+// ------------------------------------------------------------------ register x stage
+// The x stage of one column jy and LP consecutive z columns jz (blockIdx.x
+// enumerates (jy, group of LP jz) of the bin's box) of bin blockIdx.y: per
+// column the line over x with z[n] = D(m_x, m_y, m_z), m_x the frequency of
+// line position n, on the bin's shell (thr_lo <= |m|^2 < thr_hi, inside the
+// spectrum box) and zero elsewhere (Eqs. gen_Nspec3 and delta_nr: the masked
+// box is never stored), transformed as the y stage does (N = N1 N2, one
+// twiddled exchange through a shared tile) and written to A_b[x][jy][jz].
+// The column index is fastest across threads: the box loads and the output
+// stores are contiguous across columns.
+template <int N, int N1, int N2, int T, int LP>
+__global__ void __launch_bounds__(T *LP) inv_x_reg_kernel(const float2 *__restrict__ box, BoxGeom bg,
+                                                          const BinGeom *__restrict__ geom,
+                                                          float2 *__restrict__ A, const float2 *__restrict__ tw) {
+    static_assert(N1 * N2 == N && N1 % T == 0 && N2 % T == 0, "threads must divide both passes");
+    __shared__ float2 tile[N * LP];
+    const BinGeom g = geom[blockIdx.y];
+    if (g.empty) return;
+    const int ngz = (g.Dzb + LP - 1) / LP;
+    if ((int)blockIdx.x >= g.Db * ngz) return;  // uniform over the CTA
+    const int jy = blockIdx.x / ngz;
+    const int jz0 = (blockIdx.x - jy * ngz) * LP;
+    const int my = box_freq(jy, g.Db, N);
+    // every line of this CTA outside the shell (the smallest |m|^2 of its lines)
+    if ((long long)my * my + (long long)jz0 * jz0 >= g.thr_hi) return;
+    const int l = threadIdx.x % LP, t = threadIdx.x / LP;
+    const int mz = jz0 + l;
+    const bool col = mz < g.Dzb;
+    const long long r2 = (long long)my * my + (long long)mz * mz;
+    const float2 *in = box + g.box_off + (long long)box_index(my, bg.D) * bg.Dz + (col ? mz : 0);
+    const long long xs = (long long)bg.D * bg.Dz;  // box stride along x
+    const bool fullx = bg.D == N;
+    const int R = bg.D / 2;  // the box holds |m_x| <= R when it does not span the axis
+#pragma unroll 1
+    for (int j = 0; j < N1 / T; ++j) {
+        const int n1 = t + T * j;
+        float2 v[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const int n = n1 + N1 * n2;
+            const int mx = n < N / 2 ? n : n - N;
+            const int jx = fullx ? n : (mx >= -R && mx <= R ? box_index(mx, bg.D) : -1);
+            const long long s2 = (long long)mx * mx + r2;
+            v[n2] = make_float2(0.f, 0.f);
+            if (col && jx >= 0 && s2 >= g.thr_lo && s2 < g.thr_hi) v[n2] = in[(long long)jx * xs];
+        }
+        reg_idft<N2, N>(v, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            float2 val = v[k2];
+            if (k2 > 0) val = cmulc(val, tw[n1 * k2]);  // n1 k2 < N
+            tile[(k2 * N1 + n1) * LP + l] = val;
+        }
+    }
+    __syncthreads();
+    float2 *out = A + g.A_off + (long long)jy * g.Dzb + mz;
+    const long long os = (long long)g.Db * g.Dzb;  // A_b stride along x
+#pragma unroll 1
+    for (int j = 0; j < N2 / T; ++j) {
+        const int k2 = t + T * j;
+        float2 v[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) v[n1] = tile[(k2 * N1 + n1) * LP + l];
+        reg_idft<N1, N>(v, tw);
+        if (col) {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) out[(long long)(k2 + N2 * k1) * os] = v[k1];
+        }
+    }
+}
+
 // Register y-stage configurations: (N, N1, N2, threads per line, columns per CTA).
 #define FBS_YREG_LIST(X)        \
     X(64, 8, 8, 8, 8)           \
@@ -934,6 +1005,23 @@ void launch_inverse_x_geom(Plan &p, const BinGeom *geom, int nb, int nvb) {
     const int nl = lines_per_cta<float>(N);
     const size_t sm = 2 * (size_t)nl * (N + 1) * sizeof(float2);
     KTimer t(p, KC_INV_X);
+    // register x stage (the y stage's configurations); FBS_XSTAGE=smem selects
+    // the shared-memory Stockham kernel below
+    static const char *xenv = getenv("FBS_XSTAGE");
+    const int lp = yreg_lines(N);
+    if (lp > 0 && !(xenv && !strcmp(xenv, "smem"))) {
+        int gx = 1;
+        for (int b = 0; b < nb; ++b)
+            if (!p.geom[b].empty) gx = std::max(gx, p.geom[b].Db * ((p.geom[b].Dzb + lp - 1) / lp));
+        dim3 grid(gx, nvb);
+#define FBS_XR(n, n1, n2, t_, lp_)                                                    \
+    if (N == n) inv_x_reg_kernel<n, n1, n2, t_, lp_><<<grid, t_ * lp_, 0, p.stream>>>( \
+                    p.d_box, p.boxM, geom, p.d_A, p.d_twM);
+        FBS_YREG_LIST(FBS_XR)
+#undef FBS_XR
+        FBS_CUDA(cudaGetLastError());
+        return;
+    }
     auto k = inv_x_kernel<float, false>;
 #define FBS_PICK(n, ...) \
     if (N == n) k = inv_x_kernel<float, false, __VA_ARGS__>;

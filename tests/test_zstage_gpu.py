@@ -1,8 +1,9 @@
-"""The z stage (C2R of two real rows per complex line, Eq. delta_nr) at every
-evaluation grid with a compile-time kernel, against the FP64 oracle.
+"""The register x, y and z stages (the z stage a C2R of two real rows per
+complex line, Eq. delta_nr) at every evaluation grid with a compile-time
+kernel, against the FP64 oracle.
 
 Full-grid plans put the inverse transforms on the input grid N itself, so
-each N below runs the register z stage of that length.  P depends on the z
+each N below runs the register x, y and z stages of that length.  P depends on the z
 stage's own sums of squares and B on the shell fields it writes: both are
 compared with the oracle's FFT estimator (FP32 path, so the contraction adds
 no BF16 rounding), B on the triplets gated on the cancellation-free scale.
