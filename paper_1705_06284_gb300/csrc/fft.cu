@@ -700,6 +700,80 @@ __global__ void __launch_bounds__(T *LP) inv_y_reg_kernel(const float2 *__restri
     }
 }
 
+// ------------------------------------------------------------------ register forward z pass
+// R2C z pass with one shared-memory exchange (Eq. DeltaFFTtoDelta): rows r,
+// r + 1 of the field packed as one complex line v = delta_r + i delta_{r+1},
+// whose forward DFT Z(m) = sum_n v_n e^{-2 pi i n m/N} is conj(IDFT(conj v)):
+// the conjugated line goes through the z stage's inverse register transforms
+// (N2-point transforms in registers, a twiddled exchange through a shared
+// tile, N1-point transforms), the result returns to the tile in natural
+// order, and X_r(m) = (Z(m) + conj Z(N-m))/2, X_{r+1}(m) = (Z(m) - conj
+// Z(N-m))/(2i) for the kept m < Dz go to zbuf[r][m].  T threads per line, LP
+// lines per CTA; batched evaluations read fields[blockIdx.y].
+template <int N, int N1, int N2, int T, int LP>
+__global__ void __launch_bounds__(T *LP) fwd_z_reg_kernel(const float *__restrict__ field_one,
+                                                          const float *const *__restrict__ fields,
+                                                          float2 *__restrict__ zbuf_all, long long zstride, int Dz,
+                                                          const float2 *__restrict__ tw) {
+    static_assert(N1 * N2 == N && N1 % T == 0 && N2 % T == 0, "threads must divide both passes");
+    static_assert((T * LP) % 32 == 0, "whole warps");
+    constexpr int LD = N1 + 1;
+    constexpr int LS = N2 * LD + ((T - N2 * LD) % 16 + 16) % 16;  // >= N: the tile also holds the line
+    __shared__ float2 tile[LP * LS];
+    const float *__restrict__ field = fields ? fields[blockIdx.y] : field_one;
+    float2 *__restrict__ zbuf = zbuf_all + (long long)blockIdx.y * zstride;
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const long long nrows = (long long)N * N;
+    const long long r = ((long long)blockIdx.x * LP + line) * 2;
+    const bool w0 = r < nrows, w1 = r + 1 < nrows;
+    const float *f0 = field + (w0 ? r : 0) * N;
+    const float *f1 = f0 + (w1 ? N : 0);
+    float2 *Y = tile + line * LS;
+#pragma unroll 1
+    for (int j = 0; j < N1 / T; ++j) {
+        const int n1 = t + T * j;
+        float2 v[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+            const int n = n1 + N1 * n2;
+            v[n2] = make_float2(w0 ? f0[n] : 0.f, w1 ? -f1[n] : 0.f);  // conj of the packed line
+        }
+        reg_idft<N2, N>(v, tw);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+            float2 val = v[k2];
+            if (k2 > 0) val = cmulc(val, tw[n1 * k2]);  // n1 k2 < N
+            Y[k2 * LD + n1] = val;
+        }
+    }
+    __syncthreads();
+    float2 res[N2 / T][N1];
+#pragma unroll
+    for (int j = 0; j < N2 / T; ++j) {
+        const int k2 = t + T * j;
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) res[j][n1] = Y[k2 * LD + n1];
+        reg_idft<N1, N>(res[j], tw);
+    }
+    __syncthreads();  // every read of the exchange tile is done
+#pragma unroll
+    for (int j = 0; j < N2 / T; ++j) {
+        const int k2 = t + T * j;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) Y[k2 + N2 * k1] = res[j][k1];  // conj Z in natural order
+    }
+    __syncthreads();
+    for (int m = t; m < Dz; m += T) {
+        const float2 ym = Y[m], yn = Y[m == 0 ? 0 : N - m];
+        const float2 zm = make_float2(ym.x, -ym.y), zn = make_float2(yn.x, -yn.y);
+        // X0 = (Z(m) + conj Z(N-m))/2,  X1 = (Z(m) - conj Z(N-m))/(2i)
+        const float2 x0 = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
+        const float2 x1 = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
+        if (w0) zbuf[r * Dz + m] = x0;
+        if (w1) zbuf[(r + 1) * Dz + m] = x1;
+    }
+}
+
 // ------------------------------------------------------------------ register x stage
 // The x stage of one column jy and LP consecutive z columns jz (blockIdx.x
 // enumerates (jy, group of LP jz) of the bin's box) of bin blockIdx.y: per
@@ -957,10 +1031,23 @@ void launch_forward_grid(Plan &p, int N, const BoxGeom &bx, const FftFactors &fN
 #undef FBS_PICK
     {
         KTimer t(p, KC_FWD_Z);
-        allow_smem(kz, sm);
-        long long rows = (long long)N * N;
-        dim3 grid((int)((rows + 2 * nl - 1) / (2 * nl)), nf);
-        kz<<<grid, kThreads, sm, p.stream>>>(d_field, d_fields, zbuf, zs, N, Dz, nl, fN, tw);
+        const long long rows = (long long)N * N;
+        // register z pass where the z stage has a configuration for N;
+        // FBS_FWDZ=smem selects the shared-memory Stockham kernel
+        static const char *fenv = getenv("FBS_FWDZ");
+        const int lp = zreg_lines(N);
+        if (lp > 0 && !(fenv && !strcmp(fenv, "smem"))) {
+            dim3 grid((int)((rows + 2 * lp - 1) / (2 * lp)), nf);
+#define FBS_FZ(n, n1, n2, t_, lp_)                                                    \
+    if (N == n) fwd_z_reg_kernel<n, n1, n2, t_, lp_><<<grid, t_ * lp_, 0, p.stream>>>( \
+                    d_field, d_fields, zbuf, zs, Dz, tw);
+            FBS_ZREG_LIST(FBS_FZ)
+#undef FBS_FZ
+        } else {
+            allow_smem(kz, sm);
+            dim3 grid((int)((rows + 2 * nl - 1) / (2 * nl)), nf);
+            kz<<<grid, kThreads, sm, p.stream>>>(d_field, d_fields, zbuf, zs, N, Dz, nl, fN, tw);
+        }
         FBS_CUDA(cudaGetLastError());
     }
     {
