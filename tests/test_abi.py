@@ -85,3 +85,21 @@ def test_device_budget_arguments(libfbs):
     fbs.fbs_set_device_budget(0)
     assert fbs.fbs_device_bytes_in_use() >= 0
     assert libfbs.fbs_plan_check(None) == -1
+
+
+def test_enum_values_match_the_binding():
+    """Every FBS_OPT_* and FBS_PREC_* value of include/fbs.h is the binding's
+    constant of the same name (the options are passed as plain ints), and the
+    autotuner's options are among them."""
+    txt = open(os.path.join(ROOT, "include", "fbs.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    found = dict((k, int(v)) for k, v in re.findall(r"\b(FBS_(?:OPT|PREC)_[A-Z0-9_]+)\s*=\s*(\d+)", txt))
+    assert "FBS_OPT_TC_STACK" in found and "FBS_OPT_TC_BSTAGES" in found
+    for name, value in found.items():
+        if hasattr(fbs, name):
+            assert getattr(fbs, name) == value, name
+    opts = {v for k, v in found.items() if k.startswith("FBS_OPT_")}
+    for fbs_name in [k for k in found if k.startswith("FBS_OPT_")]:
+        assert hasattr(fbs, fbs_name), fbs_name
+    from paper_1705_06284_gb300 import batch
+    assert {opt for _, opt, _ in batch.TUNABLE} <= opts
